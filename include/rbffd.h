@@ -1,0 +1,251 @@
+/*
+ * rbffd.h -- C ABI of the GB300 (sm_103a) implementation of the
+ * semi-implicit PHS-RBF-FD incompressible Navier-Stokes method of
+ * Shahane & Vanka, "A Semi-Implicit Meshless Method for Incompressible Flows
+ * in Complex Geometries" (arXiv 2106.07616).
+ *
+ * Conventions for every call:
+ *   - Return value: RBFFD_OK (0) or a negative RBFFD_E* code.  No C++
+ *     exception crosses this boundary.  rbffd_last_error() gives a
+ *     thread-local text for the last failure on the calling thread.
+ *   - Pointers documented as "device" must point to device memory of the
+ *     context's GPU; "host or device" pointers may be either (the library
+ *     copies with cudaMemcpyDefault, which needs unified addressing, true on
+ *     every 64-bit CUDA platform).  The caller owns every buffer it passes;
+ *     the library owns what it allocates behind a handle.
+ *   - Work is issued on the context's stream.  Calls that return a host
+ *     value (a norm, a count, a status) synchronise that stream.
+ *   - Handles are not thread-safe: serialise calls on one context.
+ *   - Arrays of per-point data are indexed by point number 0..n-1; stencil
+ *     arrays are row-major n x q (row i = the cloud of point i).
+ */
+#ifndef RBFFD_H
+#define RBFFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RBFFD_OK = 0,
+  RBFFD_EINVAL = -1,     /* bad argument (sizes, q < m, q > n, null pointer) */
+  RBFFD_ENOMEM = -2,     /* device allocation failed or HBM budget exceeded */
+  RBFFD_ESINGULAR = -3,  /* a local collocation matrix had an exactly zero pivot */
+  RBFFD_ENOCONV = -4,    /* a Krylov solve or the outer loop hit its limit */
+  RBFFD_EDIVERGED = -5,  /* a non-finite value appeared */
+  RBFFD_ETIMEOUT = -6,   /* a bounded device-side wait gave up */
+  RBFFD_ECUDA = -7,      /* a CUDA runtime call failed */
+  RBFFD_ENOTIMPL = -8
+};
+
+/* Boundary tags (Sec. 3.1 of the paper). */
+enum {
+  RBFFD_TAG_INTERIOR = 0,
+  RBFFD_TAG_DIRICHLET = 1 /* wall / inlet: velocity prescribed, p' homogeneous Neumann */
+};
+
+/* Operators of the problem (rbffd_apply, rbffd_get_operators). */
+enum {
+  RBFFD_OP_DX = 0,        /* d/dx weights */
+  RBFFD_OP_DY = 1,        /* d/dy weights */
+  RBFFD_OP_LAP = 2,       /* Laplacian weights */
+  RBFFD_OP_PCORR = 3,     /* pressure-correction matrix */
+  RBFFD_OP_MOMENTUM = 4   /* momentum matrix of the last outer iteration */
+};
+
+/* Fields of a problem (rbffd_get_field / rbffd_set_field). */
+enum {
+  RBFFD_FIELD_U = 0, RBFFD_FIELD_V = 1, RBFFD_FIELD_P = 2,   /* current iterate */
+  RBFFD_FIELD_UN = 3, RBFFD_FIELD_VN = 4,                     /* time level n */
+  RBFFD_FIELD_UNM1 = 5, RBFFD_FIELD_VNM1 = 6,                 /* time level n-1 */
+  RBFFD_FIELD_UT = 7, RBFFD_FIELD_VT = 8,                     /* u~, v~ of the last iteration */
+  RBFFD_FIELD_PC = 9,                                         /* p' of the last iteration */
+  RBFFD_FIELD_UBC = 10, RBFFD_FIELD_VBC = 11                  /* prescribed boundary velocity */
+};
+
+/* Arithmetic of the Krylov solves. */
+enum {
+  RBFFD_PREC_FP64 = 0,  /* FP64 operators and Krylov vectors throughout */
+  RBFFD_PREC_MIXED = 1  /* FP32 matrices/Krylov inside FP64 defect correction */
+};
+
+typedef struct rbffd_ctx rbffd_ctx;
+typedef struct rbffd_problem rbffd_problem;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps what
+ * problems of this context may allocate (0 = no cap).  cuda_stream is a
+ * cudaStream_t to issue work on, or NULL for a stream owned by the context.
+ * Errors: RBFFD_EINVAL (bad device), RBFFD_ECUDA. */
+int rbffd_ctx_create(rbffd_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream);
+void rbffd_ctx_destroy(rbffd_ctx *ctx);
+/* Text of the last failure on the calling thread ("" if none). */
+const char *rbffd_last_error(void);
+/* Number of kernel launches this context has issued (for accounting). */
+int64_t rbffd_ctx_launch_count(const rbffd_ctx *ctx);
+
+/* ------------------------------------------------------- S1: the clouds */
+
+/* Cloud selection (paper Sec. 2, "a cloud of neighboring points", and
+ * Sec. 3.1, one-sided clouds at boundaries).  For every point i, writes
+ * idx[i*q .. i*q+q-1]: i itself first, then the q-1 nearest candidates in
+ * the order (d^2, index) ascending, with d^2 = dx*dx + dy*dy evaluated in
+ * FP64 without fused multiply-add (so the result is reproducible bit for
+ * bit).  Candidates of a point whose tag is not RBFFD_TAG_INTERIOR are the
+ * interior points only (its cloud is one-sided); tag == NULL treats all
+ * points as interior.
+ *   x, y: device, n doubles.  tag: device, n int8, or NULL.
+ *   idx:  device, n*q int32 (output).
+ * Errors: RBFFD_EINVAL if n < 1, q < 1, q > n, or a boundary point has
+ * fewer than q-1 interior candidates; RBFFD_ENOMEM; RBFFD_ECUDA. */
+int rbffd_build_stencils(rbffd_ctx *ctx, int32_t n, const double *x, const double *y,
+                         const int8_t *tag, int32_t q, int32_t *idx);
+
+/* -------------------------------------------------- S2: operator weights */
+
+/* PHS-RBF-FD weights (paper Sec. 2, Eqs. RBF_interp .. RBF_interp_mat_vec_L_solve):
+ * phi(r) = r^3 with the m = (k+1)(k+2)/2 monomials of degree <= k appended.
+ * For cloud i, with local coordinates xi = (x - x_i)/h, h = max distance
+ * in the cloud, the collocation system A c = [L phi(|x_i - x_j|)]_j ++
+ * [L P(x_i)] (A = [Phi P; P^T 0], symmetric) is solved by LU with partial
+ * pivoting in FP64, and the first q entries of c, rescaled by 1/h (d/dx,
+ * d/dy) or 1/h^2 (Laplacian), are the weights B1 of the cloud.
+ *   idx: device n*q int32 (from rbffd_build_stencils).
+ *   wx, wy, wl: device n*q doubles (outputs; any may be NULL to skip).
+ *   first_singular: host int32 (nullable): lowest point index whose matrix
+ *   had an exactly zero pivot, or -1.
+ * Errors: RBFFD_EINVAL (q < m, q + m > 96, degree < 0, degree > 8),
+ * RBFFD_ESINGULAR (weights of those clouds are set to 0), RBFFD_ECUDA. */
+int rbffd_weights(rbffd_ctx *ctx, int32_t n, const double *x, const double *y, int32_t q,
+                  const int32_t *idx, int32_t degree, double *wx, double *wy, double *wl,
+                  int32_t *first_singular);
+
+/* ------------------------------------------------------- flow problems */
+
+typedef struct {
+  int32_t n;       /* points */
+  int32_t q;       /* cloud size */
+  int32_t degree;  /* appended polynomial degree k */
+  int32_t pin;     /* boundary point whose p' row is the identity (fixes the
+                      free constant of the pure-Neumann p' equation) */
+  double rho, mu;  /* density, dynamic viscosity */
+  int32_t precision; /* RBFFD_PREC_* */
+  /* host or device arrays of n entries (copied at create / reload): */
+  const double *x, *y;
+  const int8_t *tag;     /* RBFFD_TAG_* */
+  const double *nx, *ny; /* outward unit normal at boundary points (0 inside) */
+  const double *ubc, *vbc; /* prescribed velocity at boundary points */
+} rbffd_problem_desc;
+
+/* Allocate a problem and build everything that depends only on the points
+ * (S1 clouds, S2 weights, S3 packed operators, the pressure-correction
+ * matrix: Laplacian rows inside, n . grad rows at Dirichlet-velocity
+ * boundary points, identity at `pin`).  Initial state: u = v = p = 0 in the
+ * interior, boundary velocity on the boundary, flat time history.
+ * Errors: RBFFD_EINVAL, RBFFD_ENOMEM (allocation or budget), RBFFD_ESINGULAR,
+ * RBFFD_ECUDA. */
+int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *desc, rbffd_problem **out);
+/* Same as create for a problem of identical n, q, degree and precision,
+ * reusing its memory (no allocation): re-copies the inputs, rebuilds the
+ * clouds, weights and operators, and resets the state. */
+int rbffd_problem_reload(rbffd_problem *prob, const rbffd_problem_desc *desc);
+void rbffd_problem_destroy(rbffd_problem *prob);
+/* Device bytes held by the problem. */
+size_t rbffd_problem_bytes(const rbffd_problem *prob);
+
+typedef struct {
+  double dt;             /* time step */
+  double alpha[3];       /* BDF2: 1.5, -2, 0.5 (paper Sec. 3) */
+  double krylov_tol;     /* relative residual of each Krylov solve */
+  int32_t krylov_maxit;  /* iteration cap of each Krylov solve */
+} rbffd_step_params;
+
+typedef struct {
+  int32_t iters[3];   /* BiCGSTAB iterations: u~, v~, p' */
+  double relres[3];   /* final relative residuals */
+} rbffd_iter_stats;
+
+/* One outer iteration (paper Sec. 3.2 steps 2-7):
+ *   2. momentum predictor, Eqs. (u:tilde), (v:tilde): advection linearised
+ *      with the current iterate, diffusion implicit, grad p at the current
+ *      iterate; identity rows with the boundary velocity at Dirichlet
+ *      points; right-Jacobi BiCGSTAB for u~ and v~ (one matrix, two
+ *      right-hand sides, initial guess u^r, v^r);
+ *   3. pressure correction, Eq. (pressure poisson), right-Jacobi BiCGSTAB
+ *      from p' = 0;
+ *   4. p += p' at interior points, Eq. (p:correction);
+ *   5. boundary pressure from the normal momentum equation, Eq. (normal
+ *      momentum), with convection and diffusion of (u~, v~) and the BDF2
+ *      time derivative of the boundary velocity;
+ *   6. velocity correction, Eqs. (u:correction), (v:correction), at
+ *      interior points;
+ *   7. delta_out (host) = mean|u^{r+1} - u^r| + mean|v^{r+1} - v^r|.
+ * stats (host, nullable).  Errors: RBFFD_ENOCONV (a Krylov solve hit its
+ * cap), RBFFD_EDIVERGED, RBFFD_ETIMEOUT, RBFFD_ECUDA. */
+int simple_iterate(rbffd_problem *prob, const rbffd_step_params *params, double *delta_out,
+                   rbffd_iter_stats *stats);
+
+typedef struct {
+  double dt;
+  double resid_tol;       /* steady: stop when R <= resid_tol */
+  int32_t max_steps;      /* steady: cap on time steps */
+  int32_t max_outer;      /* cap on outer iterations per time step */
+  double krylov_tol;
+  int32_t krylov_maxit;
+} rbffd_solve_params;
+
+typedef struct {
+  int32_t steps;
+  int64_t outer_iters;
+  int64_t krylov_iters[3]; /* totals: u~, v~, p' */
+  double resid[3];         /* R_m, R_c, R of the final state (steady only) */
+  double change;           /* mean|u^{n+1}-u^n| + mean|v^{n+1}-v^n| of the last step */
+} rbffd_solve_stats;
+
+/* One BDF2 time step (paper Sec. 3.2 steps 1-8): outer iterations from the
+ * state of level n until delta < tol_outer or max_outer, then
+ * [u^{n-1}, u^n] <- [u^n, u^{n+1}].  outer_iters, change: host, nullable. */
+int rbffd_time_step(rbffd_problem *prob, const rbffd_solve_params *params, double tol_outer,
+                    int32_t *outer_iters, double *change);
+
+/* Steady solve by BDF2 pseudo-time marching from the current state.  Outer
+ * tolerance 1e-4 for the first step, then min(1e-4, dt * eps_s) with
+ * dt * eps_s = the change of the previous step (paper Sec. 3.2).  Stops when
+ * R = max(R_m, R_c) <= resid_tol (rbffd_steady_residual).  Errors:
+ * RBFFD_ENOCONV if max_steps ran out first. */
+int solve_steady(rbffd_problem *prob, const rbffd_solve_params *params, rbffd_solve_stats *stats);
+
+/* n_steps BDF2 steps with the same adaptive outer tolerance.  on_step
+ * (nullable) runs on the host after every step; a non-zero return stops
+ * the march and is returned. */
+int solve_unsteady(rbffd_problem *prob, const rbffd_solve_params *params, int32_t n_steps,
+                   int (*on_step)(void *user, int32_t step, double t), void *user,
+                   rbffd_solve_stats *stats);
+
+/* Relative residual of the discrete steady equations over interior rows,
+ * vector norms over both components:
+ *   R_m = |rho (u.grad)u - mu lap u + grad p| / (|rho (u.grad)u| + |mu lap u| + |grad p|)
+ *   R_c = |Dx u + Dy v| / |grad u|
+ * R3 (host, 3 doubles) = R_m, R_c, max of the two. */
+int rbffd_steady_residual(rbffd_problem *prob, double *R3);
+
+/* Copy a field (RBFFD_FIELD_*) out of / into the problem; n doubles, host
+ * or device.  Setting U, V or P leaves the time history untouched. */
+int rbffd_get_field(rbffd_problem *prob, int32_t which, double *out);
+int rbffd_set_field(rbffd_problem *prob, int32_t which, const double *in);
+
+/* Stencil indices and weights, row-major n*q, host or device (any NULL). */
+int rbffd_get_operators(rbffd_problem *prob, int32_t *idx, double *wx, double *wy, double *wl,
+                        double *pcorr);
+
+/* y = W x for one operator (RBFFD_OP_*); x, y: device, n doubles. */
+int rbffd_apply(rbffd_problem *prob, int32_t which, const double *x, double *y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBFFD_H */

@@ -1,0 +1,105 @@
+// context.cu -- context lifetime, error text, budgeted allocation.
+#include <cstring>
+
+#include "common.cuh"
+
+namespace rbffd {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int dev_alloc(rbffd_ctx *ctx, void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return RBFFD_OK;
+  if (ctx->budget && ctx->used + bytes > ctx->budget) {
+    set_error("device budget exceeded: %zu + %zu > %zu bytes", ctx->used, bytes, ctx->budget);
+    return RBFFD_ENOMEM;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return RBFFD_ENOMEM;
+  }
+  ctx->used += bytes;
+  return RBFFD_OK;
+}
+
+void dev_free(rbffd_ctx *ctx, void *p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  ctx->used -= bytes;
+}
+
+int pinned(rbffd_ctx *ctx, size_t bytes, void **out) {
+  if (ctx->pinned_bytes < bytes) {
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
+    ctx->pinned_bytes = 0;
+    RBFFD_CK(cudaMallocHost(&ctx->pinned, bytes));
+    ctx->pinned_bytes = bytes;
+  }
+  *out = ctx->pinned;
+  return RBFFD_OK;
+}
+
+}  // namespace rbffd
+
+using namespace rbffd;
+
+extern "C" const char *rbffd_last_error(void) { return g_err; }
+
+extern "C" int rbffd_ctx_create(rbffd_ctx **out, int device, size_t hbm_budget_bytes,
+                                void *cuda_stream) {
+  if (!out) return RBFFD_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  RBFFD_CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) {
+    set_error("device %d out of range (%d devices)", device, ndev);
+    return RBFFD_EINVAL;
+  }
+  RBFFD_CK(cudaSetDevice(device));
+  rbffd_ctx *c = new rbffd_ctx();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete c;
+    set_error("cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+    return RBFFD_ECUDA;
+  }
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      set_error("cudaStreamCreate: %s", cudaGetErrorString(e));
+      return RBFFD_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return RBFFD_OK;
+}
+
+extern "C" void rbffd_ctx_destroy(rbffd_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx;
+}
+
+extern "C" int64_t rbffd_ctx_launch_count(const rbffd_ctx *ctx) { return ctx ? ctx->launches : 0; }

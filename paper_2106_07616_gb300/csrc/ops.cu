@@ -1,0 +1,427 @@
+// ops.cu -- row kernels of the outer iteration (paper Sec. 3) on the packed
+// operators: packing (S3), momentum assembly (S4), divergence right-hand
+// side (S6), pressure update + boundary pressure (S8/S9), velocity
+// correction with the Delta partials (S8/S10), time-level rotation, the
+// steady residual and a plain SpMV.
+//
+// Layout: every operator is an ELL array in column-major order [q][ldn]
+// (entry j of row i at j*ldn + i), so a warp reading slot j of 32
+// consecutive rows issues one coalesced 256-byte load; all operators share
+// one int32 column array because they share the clouds.  Slot 0 of every
+// row is the point itself (the clouds put it first).
+#include "common.cuh"
+#include "ops.cuh"
+
+namespace rbffd {
+
+constexpr int RT = 256;
+
+__global__ void k_pack(int n, int q, int ldn, int pin, const int32_t *__restrict__ idx_rm,
+                       const double *__restrict__ wx_rm, const double *__restrict__ wy_rm,
+                       const double *__restrict__ wl_rm, const int8_t *__restrict__ tag,
+                       const double *__restrict__ nx, const double *__restrict__ ny,
+                       int32_t *__restrict__ col, double *__restrict__ Wx,
+                       double *__restrict__ Wy, double *__restrict__ Wl,
+                       double *__restrict__ Pp, double *__restrict__ pdinv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ldn) return;
+  if (i >= n) {  // padding rows: self-loops with zero weight, never read
+    for (int j = 0; j < q; ++j) {
+      int64_t e = (int64_t)j * ldn + i;
+      col[e] = 0;
+      Wx[e] = Wy[e] = Wl[e] = Pp[e] = 0.0;
+    }
+    pdinv[i] = 1.0;
+    return;
+  }
+  const bool interior = tag[i] == 0;
+  const double ni = nx[i], mi = ny[i];
+  double diag = 0.0;
+  for (int j = 0; j < q; ++j) {
+    int64_t r = (int64_t)i * q + j, e = (int64_t)j * ldn + i;
+    int c = idx_rm[r];
+    double a = wx_rm[r], b = wy_rm[r], l = wl_rm[r];
+    col[e] = c;
+    Wx[e] = a;
+    Wy[e] = b;
+    Wl[e] = l;
+    double pv;
+    if (i == pin)
+      pv = (c == i) ? 1.0 : 0.0;
+    else if (interior)
+      pv = l;
+    else
+      pv = ni * a + mi * b;
+    Pp[e] = pv;
+    if (c == i) diag += pv;
+  }
+  pdinv[i] = 1.0 / (diag == 0.0 ? 1.0 : diag);
+}
+
+// S4: momentum matrix and right-hand sides, Eqs. (u:tilde), (v:tilde):
+//   rho a1/dt u~ + rho u^r Dx u~ + rho v^r Dy u~ - mu Lap u~
+//       = -rho (a2 u^n + a3 u^{n-1}) / dt - (Dx p^r)
+// at interior rows; identity rows with the boundary value elsewhere.  The
+// initial guesses of the momentum solve are set to the current iterate.
+__global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ col,
+                           const double *__restrict__ Wx, const double *__restrict__ Wy,
+                           const double *__restrict__ Wl, const int8_t *__restrict__ tag,
+                           const double *__restrict__ u, const double *__restrict__ v,
+                           const double *__restrict__ p, const double *__restrict__ un,
+                           const double *__restrict__ vn, const double *__restrict__ unm1,
+                           const double *__restrict__ vnm1, const double *__restrict__ ubc,
+                           const double *__restrict__ vbc, double rho, double mu, double dt,
+                           double a1, double a2, double a3, double *__restrict__ Am,
+                           double *__restrict__ mdinv, double *__restrict__ bu,
+                           double *__restrict__ bv, double *__restrict__ ut,
+                           double *__restrict__ vt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool interior = tag[i] == 0;
+  const double ui = u[i], vi = v[i];
+  ut[i] = ui;
+  vt[i] = vi;
+  if (!interior) {
+    for (int j = 0; j < q; ++j) Am[(int64_t)j * ldn + i] = (j == 0) ? 1.0 : 0.0;
+    mdinv[i] = 1.0;
+    bu[i] = ubc[i];
+    bv[i] = vbc[i];
+    return;
+  }
+  const double ru = rho * ui, rv = rho * vi, dd = rho * a1 / dt;
+  double gx = 0.0, gy = 0.0, diag = 0.0;
+#pragma unroll 4
+  for (int j = 0; j < q; ++j) {
+    int64_t e = (int64_t)j * ldn + i;
+    const int c = col[e];
+    const double a = Wx[e], b = Wy[e];
+    const double pc = p[c];
+    gx += a * pc;
+    gy += b * pc;
+    double val = ru * a + rv * b - mu * Wl[e];
+    if (c == i) {
+      val += dd;
+      diag += val;
+    }
+    Am[e] = val;
+  }
+  mdinv[i] = 1.0 / (diag == 0.0 ? 1.0 : diag);
+  bu[i] = -rho * (a2 * un[i] + a3 * unm1[i]) / dt - gx;
+  bv[i] = -rho * (a2 * vn[i] + a3 * vnm1[i]) / dt - gy;
+}
+
+// S6: right-hand side of Eq. (pressure poisson) at interior rows, zero at
+// the Neumann rows and at the pinned row.
+__global__ void k_divergence(int n, int q, int ldn, const int32_t *__restrict__ col,
+                             const double *__restrict__ Wx, const double *__restrict__ Wy,
+                             const int8_t *__restrict__ tag, const double *__restrict__ ut,
+                             const double *__restrict__ vt, double coef,
+                             double *__restrict__ bp, double *__restrict__ pc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  pc[i] = 0.0;  // initial guess of the p' solve
+  if (tag[i] != 0) {
+    bp[i] = 0.0;
+    return;
+  }
+  double dx = 0.0, dy = 0.0;
+#pragma unroll 4
+  for (int j = 0; j < q; ++j) {
+    int64_t e = (int64_t)j * ldn + i;
+    const int c = col[e];
+    dx += Wx[e] * ut[c];
+    dy += Wy[e] * vt[c];
+  }
+  bp[i] = coef * (dx + dy);
+}
+
+// S8 (p += p' inside) fused with S9 (boundary pressure, Eq. normal momentum):
+// for a boundary point i with G = nx Wx + ny Wy (row i),
+//   sum_j G_ij p_j = N . [ -rho (a1 u~ + a2 u^n + a3 u^{n-1})/dt
+//                          - rho (u~ . grad) u~ + mu Lap u~ ]_i,
+// solved for p_i with every other p_j at its value after the interior
+// update (p_j + p'_j inside, old p_j on the boundary).  Writes p_out.
+__global__ void k_pressure(int n, int q, int ldn, const int32_t *__restrict__ col,
+                           const double *__restrict__ Wx, const double *__restrict__ Wy,
+                           const double *__restrict__ Wl, const int8_t *__restrict__ tag,
+                           const double *__restrict__ nx, const double *__restrict__ ny,
+                           const double *__restrict__ p, const double *__restrict__ pc,
+                           const double *__restrict__ ut, const double *__restrict__ vt,
+                           const double *__restrict__ un, const double *__restrict__ vn,
+                           const double *__restrict__ unm1, const double *__restrict__ vnm1,
+                           double rho, double mu, double dt, double a1, double a2, double a3,
+                           double *__restrict__ p_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (tag[i] == 0) {
+    p_out[i] = p[i] + pc[i];
+    return;
+  }
+  const double ni = nx[i], mi = ny[i];
+  double gxu = 0, gyu = 0, lu = 0, gxv = 0, gyv = 0, lv = 0, gii = 0, off = 0;
+  for (int j = 0; j < q; ++j) {
+    int64_t e = (int64_t)j * ldn + i;
+    const int c = col[e];
+    const double a = Wx[e], b = Wy[e], l = Wl[e];
+    const double uc = ut[c], vc = vt[c];
+    gxu += a * uc;
+    gyu += b * uc;
+    lu += l * uc;
+    gxv += a * vc;
+    gyv += b * vc;
+    lv += l * vc;
+    const double g = ni * a + mi * b;
+    if (c == i) {
+      gii += g;
+    } else {
+      const double pj = tag[c] == 0 ? p[c] + pc[c] : p[c];
+      off += g * pj;
+    }
+  }
+  const double uti = ut[i], vti = vt[i];
+  const double fx = -rho * (a1 * uti + a2 * un[i] + a3 * unm1[i]) / dt -
+                    rho * (uti * gxu + vti * gyu) + mu * lu;
+  const double fy = -rho * (a1 * vti + a2 * vn[i] + a3 * vnm1[i]) / dt -
+                    rho * (uti * gxv + vti * gyv) + mu * lv;
+  p_out[i] = (ni * fx + mi * fy - off) / gii;
+}
+
+// S8 velocity correction, Eqs. (u:correction), (v:correction), at interior
+// rows, with the block partials of sum|du| and sum|dv| for Delta (S10).
+__global__ void __launch_bounds__(RT) k_correct(
+    int n, int q, int ldn, const int32_t *__restrict__ col, const double *__restrict__ Wx,
+    const double *__restrict__ Wy, const int8_t *__restrict__ tag,
+    const double *__restrict__ pc, const double *__restrict__ ut,
+    const double *__restrict__ vt, double c, double *__restrict__ u, double *__restrict__ v,
+    double *__restrict__ part) {
+  __shared__ double sred[RT / 32];
+  double su = 0.0, sv = 0.0;
+  for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
+    double unew = ut[i], vnew = vt[i];
+    if (tag[i] == 0) {
+      double gx = 0.0, gy = 0.0;
+#pragma unroll 4
+      for (int j = 0; j < q; ++j) {
+        int64_t e = (int64_t)j * ldn + i;
+        const double pj = pc[col[e]];
+        gx += Wx[e] * pj;
+        gy += Wy[e] * pj;
+      }
+      unew = unew - c * gx;
+      vnew = vnew - c * gy;
+    }
+    su += fabs(unew - u[i]);
+    sv += fabs(vnew - v[i]);
+    u[i] = unew;
+    v[i] = vnew;
+  }
+  su = block_sum<RT>(su, sred);
+  sv = block_sum<RT>(sv, sred);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = su;
+    part[gridDim.x + blockIdx.x] = sv;
+  }
+}
+
+// End of a time step: change partials (sum|u - u^n|, sum|v - v^n|), then
+// u^{n-1} <- u^n, u^n <- u (the caller swaps the n / n-1 pointers first, so
+// `old_n` is the previous level n and `dst_n` receives the new one).
+__global__ void __launch_bounds__(RT) k_rotate(int n, const double *__restrict__ u,
+                                               const double *__restrict__ v,
+                                               const double *__restrict__ old_un,
+                                               const double *__restrict__ old_vn,
+                                               double *__restrict__ dst_un,
+                                               double *__restrict__ dst_vn,
+                                               double *__restrict__ part) {
+  __shared__ double sred[RT / 32];
+  double su = 0.0, sv = 0.0;
+  for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
+    const double a = u[i], b = v[i];
+    su += fabs(a - old_un[i]);
+    sv += fabs(b - old_vn[i]);
+    dst_un[i] = a;
+    dst_vn[i] = b;
+  }
+  su = block_sum<RT>(su, sred);
+  sv = block_sum<RT>(sv, sred);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = su;
+    part[gridDim.x + blockIdx.x] = sv;
+  }
+}
+
+// Steady residual partials over interior rows (see rbffd_steady_residual):
+// slots 0 |r|^2, 1 |rho (u.grad)u|^2, 2 |mu Lap u|^2, 3 |grad p|^2,
+// 4 |div u|^2, 5 |grad u|^2.
+__global__ void __launch_bounds__(RT) k_resid(int n, int q, int ldn,
+                                              const int32_t *__restrict__ col,
+                                              const double *__restrict__ Wx,
+                                              const double *__restrict__ Wy,
+                                              const double *__restrict__ Wl,
+                                              const int8_t *__restrict__ tag,
+                                              const double *__restrict__ u,
+                                              const double *__restrict__ v,
+                                              const double *__restrict__ p, double rho,
+                                              double mu, double *__restrict__ part) {
+  __shared__ double sred[RT / 32];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
+    if (tag[i] != 0) continue;
+    double gxu = 0, gyu = 0, lu = 0, gxv = 0, gyv = 0, lv = 0, gpx = 0, gpy = 0;
+    for (int j = 0; j < q; ++j) {
+      int64_t e = (int64_t)j * ldn + i;
+      const int c = col[e];
+      const double a = Wx[e], b = Wy[e], l = Wl[e];
+      const double uc = u[c], vc = v[c], pcv = p[c];
+      gxu += a * uc; gyu += b * uc; lu += l * uc;
+      gxv += a * vc; gyv += b * vc; lv += l * vc;
+      gpx += a * pcv; gpy += b * pcv;
+    }
+    const double ui = u[i], vi = v[i];
+    const double au = rho * (ui * gxu + vi * gyu), av = rho * (ui * gxv + vi * gyv);
+    const double du = mu * lu, dv = mu * lv;
+    const double ru = au - du + gpx, rv = av - dv + gpy;
+    acc[0] += ru * ru + rv * rv;
+    acc[1] += au * au + av * av;
+    acc[2] += du * du + dv * dv;
+    acc[3] += gpx * gpx + gpy * gpy;
+    const double dc = gxu + gyv;
+    acc[4] += dc * dc;
+    acc[5] += gxu * gxu + gyu * gyu + gxv * gxv + gyv * gyv;
+  }
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    double t = block_sum<RT>(acc[s], sred);
+    if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Fixed-order sums of the partials into the iteration record.
+// mode 0: delta = (S0 + S1) / n   mode 1: change = (S0 + S1) / n
+// mode 2: steady residual from the six sums of k_resid.
+__global__ void k_finalize(const double *__restrict__ part, int nb, int n, int mode,
+                           IterRecord *rec) {
+  if (threadIdx.x >= 32) return;
+  if (mode == 0 || mode == 1) {
+    double a = warp_sum_array(part, nb);
+    double b = warp_sum_array(part + nb, nb);
+    if (threadIdx.x == 0) {
+      double d = a / n + b / n;
+      if (mode == 0)
+        rec->delta = d;
+      else
+        rec->change = d;
+    }
+  } else {
+    double s[6];
+    for (int k = 0; k < 6; ++k) s[k] = warp_sum_array(part + k * nb, nb);
+    if (threadIdx.x == 0) {
+      double dm = sqrt(s[1]) + sqrt(s[2]) + sqrt(s[3]);
+      double dc = sqrt(s[5]);
+      double rm = dm > 0 ? sqrt(s[0]) / dm : sqrt(s[0]);
+      double rc = dc > 0 ? sqrt(s[4]) / dc : sqrt(s[4]);
+      rec->resid[0] = rm;
+      rec->resid[1] = rc;
+      rec->resid[2] = rm > rc ? rm : rc;
+    }
+  }
+}
+
+__global__ void k_spmv(int n, int q, int ldn, const int32_t *__restrict__ col,
+                       const double *__restrict__ val, const double *__restrict__ x,
+                       double *__restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+#pragma unroll 4
+  for (int j = 0; j < q; ++j) {
+    int64_t e = (int64_t)j * ldn + i;
+    s += val[e] * x[col[e]];
+  }
+  y[i] = s;
+}
+
+// ------------------------------------------------------------------ host
+
+static inline int grid_of(int n) { return (n + RT - 1) / RT; }
+
+int ops_pack(rbffd_problem *P) {
+  k_pack<<<(P->ldn + RT - 1) / RT, RT, 0, P->ctx->stream>>>(
+      P->n, P->q, P->ldn, P->pin, P->idx_rm, P->wx_rm, P->wy_rm, P->wl_rm, P->tag, P->nx, P->ny,
+      P->col, P->Wx, P->Wy, P->Wl, P->Pp, P->p_dinv);
+  return after_launch(P->ctx, "k_pack");
+}
+
+int ops_momentum(rbffd_problem *P, const rbffd_step_params *sp) {
+  k_momentum<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(
+      P->n, P->q, P->ldn, P->col, P->Wx, P->Wy, P->Wl, P->tag, P->u, P->v, P->p, P->un, P->vn,
+      P->unm1, P->vnm1, P->ubc, P->vbc, P->rho, P->mu, sp->dt, sp->alpha[0], sp->alpha[1],
+      sp->alpha[2], P->Am, P->m_dinv, P->bu, P->bv, P->ut, P->vt);
+  return after_launch(P->ctx, "k_momentum");
+}
+
+int ops_divergence(rbffd_problem *P, const rbffd_step_params *sp) {
+  double coef = P->rho * sp->alpha[0] / sp->dt;
+  k_divergence<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(P->n, P->q, P->ldn, P->col, P->Wx,
+                                                          P->Wy, P->tag, P->ut, P->vt, coef,
+                                                          P->bp, P->pc);
+  return after_launch(P->ctx, "k_divergence");
+}
+
+int ops_pressure(rbffd_problem *P, const rbffd_step_params *sp) {
+  k_pressure<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(
+      P->n, P->q, P->ldn, P->col, P->Wx, P->Wy, P->Wl, P->tag, P->nx, P->ny, P->p, P->pc,
+      P->ut, P->vt, P->un, P->vn, P->unm1, P->vnm1, P->rho, P->mu, sp->dt, sp->alpha[0],
+      sp->alpha[1], sp->alpha[2], P->p2);
+  RBFFD_TRY(after_launch(P->ctx, "k_pressure"));
+  double *t = P->p;
+  P->p = P->p2;
+  P->p2 = t;
+  return RBFFD_OK;
+}
+
+int ops_correct(rbffd_problem *P, const rbffd_step_params *sp) {
+  double c = sp->dt / (P->rho * sp->alpha[0]);
+  k_correct<<<P->rblocks, RT, 0, P->ctx->stream>>>(P->n, P->q, P->ldn, P->col, P->Wx, P->Wy,
+                                                   P->tag, P->pc, P->ut, P->vt, c, P->u, P->v,
+                                                   P->rpart);
+  RBFFD_TRY(after_launch(P->ctx, "k_correct"));
+  k_finalize<<<1, 32, 0, P->ctx->stream>>>(P->rpart, P->rblocks, P->n, 0, P->rec);
+  return after_launch(P->ctx, "k_finalize");
+}
+
+int ops_rotate(rbffd_problem *P) {
+  double *t = P->unm1;
+  P->unm1 = P->un;
+  P->un = t;
+  t = P->vnm1;
+  P->vnm1 = P->vn;
+  P->vn = t;
+  k_rotate<<<P->rblocks, RT, 0, P->ctx->stream>>>(P->n, P->u, P->v, P->unm1, P->vnm1, P->un,
+                                                  P->vn, P->rpart);
+  RBFFD_TRY(after_launch(P->ctx, "k_rotate"));
+  k_finalize<<<1, 32, 0, P->ctx->stream>>>(P->rpart, P->rblocks, P->n, 1, P->rec);
+  return after_launch(P->ctx, "k_finalize");
+}
+
+int ops_resid(rbffd_problem *P) {
+  k_resid<<<P->rblocks, RT, 0, P->ctx->stream>>>(P->n, P->q, P->ldn, P->col, P->Wx, P->Wy,
+                                                 P->Wl, P->tag, P->u, P->v, P->p, P->rho, P->mu,
+                                                 P->rpart);
+  RBFFD_TRY(after_launch(P->ctx, "k_resid"));
+  k_finalize<<<1, 32, 0, P->ctx->stream>>>(P->rpart, P->rblocks, P->n, 2, P->rec);
+  return after_launch(P->ctx, "k_finalize");
+}
+
+int ops_spmv(rbffd_problem *P, const double *val, const double *x, double *y) {
+  k_spmv<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(P->n, P->q, P->ldn, P->col, val, x, y);
+  return after_launch(P->ctx, "k_spmv");
+}
+
+int ops_reduce_blocks(rbffd_ctx *ctx, int n) {
+  int b = grid_of(n);
+  int cap = ctx->num_sms * 4;
+  return b < cap ? b : cap;
+}
+
+}  // namespace rbffd

@@ -1,0 +1,15 @@
+// ops.cuh -- internal interface of the outer-iteration row kernels.
+#pragma once
+#include "problem.cuh"
+
+namespace rbffd {
+int ops_pack(rbffd_problem *P);
+int ops_momentum(rbffd_problem *P, const rbffd_step_params *sp);
+int ops_divergence(rbffd_problem *P, const rbffd_step_params *sp);
+int ops_pressure(rbffd_problem *P, const rbffd_step_params *sp);
+int ops_correct(rbffd_problem *P, const rbffd_step_params *sp);
+int ops_rotate(rbffd_problem *P);
+int ops_resid(rbffd_problem *P);
+int ops_spmv(rbffd_problem *P, const double *val, const double *x, double *y);
+int ops_reduce_blocks(rbffd_ctx *ctx, int n);
+}  // namespace rbffd

@@ -1,0 +1,523 @@
+// problem.cu -- problem lifetime and the outer-iteration / time-step /
+// steady and unsteady drivers (paper Sec. 3.2), behind the C ABI.
+#include <cmath>
+#include <cstring>
+
+#include "ops.cuh"
+#include "problem.cuh"
+#include "weights.cuh"
+
+using namespace rbffd;
+
+namespace {
+
+struct Carver {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    size_t at = off;
+    off += (count * sizeof(T) + 255) / 256 * 256;
+    return at;
+  }
+};
+
+__global__ void k_init_state(int n, const int8_t *__restrict__ tag, const double *__restrict__ ubc,
+                             const double *__restrict__ vbc, double *u, double *v, double *p,
+                             double *un, double *vn, double *unm1, double *vnm1, double *pc,
+                             double *ut, double *vt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = tag[i] == 0 ? 0.0 : ubc[i];
+  double b = tag[i] == 0 ? 0.0 : vbc[i];
+  u[i] = un[i] = unm1[i] = ut[i] = a;
+  v[i] = vn[i] = vnm1[i] = vt[i] = b;
+  p[i] = 0.0;
+  pc[i] = 0.0;
+}
+
+int check_desc(const rbffd_problem_desc *d) {
+  if (!d || !d->x || !d->y || !d->tag || !d->nx || !d->ny || !d->ubc || !d->vbc) {
+    set_error("problem desc: null array");
+    return RBFFD_EINVAL;
+  }
+  if (weights_check_args(d->n, d->q, d->degree) != RBFFD_OK) {
+    set_error("problem desc: bad n=%d q=%d degree=%d", d->n, d->q, d->degree);
+    return RBFFD_EINVAL;
+  }
+  if (d->pin < 0 || d->pin >= d->n) {
+    set_error("problem desc: pin %d out of range", d->pin);
+    return RBFFD_EINVAL;
+  }
+  if (d->precision != RBFFD_PREC_FP64 && d->precision != RBFFD_PREC_MIXED) {
+    set_error("problem desc: unknown precision %d", d->precision);
+    return RBFFD_EINVAL;
+  }
+  if (!(d->rho > 0) || !(d->mu >= 0)) {
+    set_error("problem desc: rho must be > 0 and mu >= 0");
+    return RBFFD_EINVAL;
+  }
+  return RBFFD_OK;
+}
+
+// Copy the inputs, build clouds, weights and operators, reset the state.
+int build(rbffd_problem *P, const rbffd_problem_desc *d) {
+  rbffd_ctx *ctx = P->ctx;
+  cudaStream_t st = ctx->stream;
+  const size_t nb = (size_t)d->n * sizeof(double);
+  RBFFD_CK(cudaMemcpyAsync(P->x, d->x, nb, cudaMemcpyDefault, st));
+  RBFFD_CK(cudaMemcpyAsync(P->y, d->y, nb, cudaMemcpyDefault, st));
+  RBFFD_CK(cudaMemcpyAsync(P->nx, d->nx, nb, cudaMemcpyDefault, st));
+  RBFFD_CK(cudaMemcpyAsync(P->ny, d->ny, nb, cudaMemcpyDefault, st));
+  RBFFD_CK(cudaMemcpyAsync(P->ubc, d->ubc, nb, cudaMemcpyDefault, st));
+  RBFFD_CK(cudaMemcpyAsync(P->vbc, d->vbc, nb, cudaMemcpyDefault, st));
+  RBFFD_CK(cudaMemcpyAsync(P->tag, d->tag, (size_t)d->n, cudaMemcpyDefault, st));
+  // the pinned row must be a boundary row: check on the host copy of its tag
+  int8_t pin_tag = 0;
+  RBFFD_CK(cudaMemcpyAsync(&pin_tag, P->tag + d->pin, 1, cudaMemcpyDeviceToHost, st));
+  P->rho = d->rho;
+  P->mu = d->mu;
+  P->pin = d->pin;
+  RBFFD_TRY(knn_run(ctx, P->knn_ws, P->knn_lay, P->n, P->x, P->y, P->tag, P->q, P->idx_rm));
+  if (pin_tag == RBFFD_TAG_INTERIOR) {
+    set_error("problem desc: pin %d is not a boundary point", d->pin);
+    return RBFFD_EINVAL;
+  }
+  int big = 0x7fffffff;
+  RBFFD_CK(cudaMemcpyAsync(P->d_first_singular, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+  RBFFD_TRY(weights_run(ctx, P->n, P->x, P->y, P->q, P->idx_rm, P->degree, P->wx_rm, P->wy_rm,
+                        P->wl_rm, P->d_first_singular));
+  RBFFD_TRY(ops_pack(P));
+  k_init_state<<<(P->n + 255) / 256, 256, 0, st>>>(P->n, P->tag, P->ubc, P->vbc, P->u, P->v,
+                                                   P->p, P->un, P->vn, P->unm1, P->vnm1, P->pc,
+                                                   P->ut, P->vt);
+  RBFFD_TRY(after_launch(ctx, "k_init_state"));
+  int hfs = big;
+  RBFFD_CK(cudaMemcpyAsync(&hfs, P->d_first_singular, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RBFFD_CK(cudaStreamSynchronize(st));
+  if (hfs != big) {
+    set_error("singular collocation matrix at point %d", hfs);
+    return RBFFD_ESINGULAR;
+  }
+  return RBFFD_OK;
+}
+
+int krylov_status_code(int s) {
+  switch (s) {
+    case KRY_OK: return RBFFD_OK;
+    case KRY_NOCONV: return RBFFD_ENOCONV;
+    case KRY_DIVERGED: return RBFFD_EDIVERGED;
+    case KRY_TIMEOUT: return RBFFD_ETIMEOUT;
+    default: return RBFFD_ECUDA;
+  }
+}
+
+// Issue one outer iteration (no host synchronisation).
+int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
+  rbffd_ctx *ctx = P->ctx;
+  RBFFD_TRY(ops_momentum(P, sp));
+  KrylovArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = P->n;
+  a.q = P->q;
+  a.ldn = P->ldn;
+  a.col = P->col;
+  a.part = P->part;
+  a.bar = P->bar;
+  a.tol = sp->krylov_tol;
+  a.maxit = sp->krylov_maxit;
+  // momentum predictor: one matrix, two right-hand sides
+  a.val = P->Am;
+  a.dinv = P->m_dinv;
+  a.b[0] = P->bu;
+  a.b[1] = P->bv;
+  a.x[0] = P->ut;
+  a.x[1] = P->vt;
+  a.w[0] = P->kv[0];
+  a.w[1] = P->kv[1];
+  a.out = P->kout;
+  RBFFD_TRY(krylov_launch(ctx, 2, P->kblocks2, a));
+  RBFFD_TRY(ops_divergence(P, sp));
+  // pressure correction
+  a.val = P->Pp;
+  a.dinv = P->p_dinv;
+  a.b[0] = P->bp;
+  a.b[1] = nullptr;
+  a.x[0] = P->pc;
+  a.x[1] = nullptr;
+  a.out = P->kout + 2;
+  RBFFD_TRY(krylov_launch(ctx, 1, P->kblocks1, a));
+  RBFFD_TRY(ops_pressure(P, sp));
+  RBFFD_TRY(ops_correct(P, sp));
+  return RBFFD_OK;
+}
+
+struct Readback {
+  IterRecord rec;
+  KrylovOut kout[3];
+};
+
+int read_back(rbffd_problem *P, Readback *out) {
+  void *h = nullptr;
+  RBFFD_TRY(pinned(P->ctx, sizeof(Readback), &h));
+  // rec and kout are adjacent in the allocation
+  RBFFD_CK(cudaMemcpyAsync(h, P->rec, sizeof(Readback), cudaMemcpyDeviceToHost, P->ctx->stream));
+  RBFFD_CK(cudaStreamSynchronize(P->ctx->stream));
+  memcpy(out, h, sizeof(Readback));
+  return RBFFD_OK;
+}
+
+int check_params(const rbffd_step_params *sp) {
+  if (!sp || !(sp->dt > 0) || !(sp->krylov_tol > 0) || sp->krylov_maxit < 1 ||
+      sp->alpha[0] == 0.0) {
+    set_error("step params: need dt > 0, krylov_tol > 0, krylov_maxit >= 1, alpha[0] != 0");
+    return RBFFD_EINVAL;
+  }
+  return RBFFD_OK;
+}
+
+rbffd_step_params step_from(const rbffd_solve_params *s) {
+  rbffd_step_params sp;
+  sp.dt = s->dt;
+  sp.alpha[0] = 1.5;
+  sp.alpha[1] = -2.0;
+  sp.alpha[2] = 0.5;
+  sp.krylov_tol = s->krylov_tol;
+  sp.krylov_maxit = s->krylov_maxit;
+  return sp;
+}
+
+}  // namespace
+
+extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
+                                    rbffd_problem **out) {
+  if (!ctx || !out) return RBFFD_EINVAL;
+  *out = nullptr;
+  RBFFD_TRY(check_desc(d));
+  RBFFD_CK(cudaSetDevice(ctx->device));
+  rbffd_problem *P = new rbffd_problem();
+  P->ctx = ctx;
+  P->n = d->n;
+  P->q = d->q;
+  P->degree = d->degree;
+  P->precision = d->precision;
+  P->ldn = (int)round_up(d->n, 128);
+  const int n = P->n, q = P->q;
+  const size_t nq = (size_t)n * q, lq = (size_t)P->ldn * q;
+  knn_workspace_bytes(n, &P->knn_lay);
+  P->kblocks1 = krylov_blocks_for(ctx, n, 1);
+  P->kblocks2 = krylov_blocks_for(ctx, n, 2);
+  P->rblocks = ops_reduce_blocks(ctx, n);
+  size_t npart = krylov_partials_doubles(2, P->kblocks2);
+  size_t np1 = krylov_partials_doubles(1, P->kblocks1);
+  if (np1 > npart) npart = np1;
+  Carver c;
+  size_t o_x = c.take<double>(n), o_y = c.take<double>(n), o_nx = c.take<double>(n),
+         o_ny = c.take<double>(n), o_ubc = c.take<double>(n), o_vbc = c.take<double>(n),
+         o_tag = c.take<int8_t>(n);
+  size_t o_idx = c.take<int32_t>(nq), o_wx = c.take<double>(nq), o_wy = c.take<double>(nq),
+         o_wl = c.take<double>(nq);
+  size_t o_col = c.take<int32_t>(lq), o_Wx = c.take<double>(lq), o_Wy = c.take<double>(lq),
+         o_Wl = c.take<double>(lq), o_Pp = c.take<double>(lq), o_Am = c.take<double>(lq);
+  size_t o_pd = c.take<double>(P->ldn), o_md = c.take<double>(P->ldn);
+  size_t o_f[14];
+  for (int k = 0; k < 14; ++k) o_f[k] = c.take<double>(n);
+  size_t o_kv[16];
+  for (int k = 0; k < 16; ++k) o_kv[k] = c.take<double>(n);
+  size_t o_part = c.take<double>(npart), o_rpart = c.take<double>(6 * (size_t)P->rblocks);
+  size_t o_bar = c.take<GridBarrier>(1);
+  size_t o_rec = c.take<Readback>(1);
+  size_t o_fs = c.take<int>(1);
+  size_t o_knn = c.take<char>(P->knn_lay.bytes);
+  P->bytes = c.off;
+  int rc = dev_alloc(ctx, &P->mem, P->bytes);
+  if (rc != RBFFD_OK) {
+    delete P;
+    return rc;
+  }
+  char *b = (char *)P->mem;
+  P->x = (double *)(b + o_x);
+  P->y = (double *)(b + o_y);
+  P->nx = (double *)(b + o_nx);
+  P->ny = (double *)(b + o_ny);
+  P->ubc = (double *)(b + o_ubc);
+  P->vbc = (double *)(b + o_vbc);
+  P->tag = (int8_t *)(b + o_tag);
+  P->idx_rm = (int32_t *)(b + o_idx);
+  P->wx_rm = (double *)(b + o_wx);
+  P->wy_rm = (double *)(b + o_wy);
+  P->wl_rm = (double *)(b + o_wl);
+  P->col = (int32_t *)(b + o_col);
+  P->Wx = (double *)(b + o_Wx);
+  P->Wy = (double *)(b + o_Wy);
+  P->Wl = (double *)(b + o_Wl);
+  P->Pp = (double *)(b + o_Pp);
+  P->Am = (double *)(b + o_Am);
+  P->p_dinv = (double *)(b + o_pd);
+  P->m_dinv = (double *)(b + o_md);
+  double **f[14] = {&P->u,  &P->v,  &P->p,  &P->p2, &P->un, &P->vn, &P->unm1,
+                    &P->vnm1, &P->ut, &P->vt, &P->pc, &P->bu, &P->bv, &P->bp};
+  for (int k = 0; k < 14; ++k) *f[k] = (double *)(b + o_f[k]);
+  for (int r = 0; r < 2; ++r) {
+    double **w[8] = {&P->kv[r].r, &P->kv[r].rh, &P->kv[r].p, &P->kv[r].v,
+                     &P->kv[r].ph, &P->kv[r].s, &P->kv[r].sh, &P->kv[r].t};
+    for (int k = 0; k < 8; ++k) *w[k] = (double *)(b + o_kv[r * 8 + k]);
+  }
+  P->part = (double *)(b + o_part);
+  P->rpart = (double *)(b + o_rpart);
+  P->bar = (GridBarrier *)(b + o_bar);
+  P->rec = (IterRecord *)(b + o_rec);
+  P->kout = (KrylovOut *)((char *)P->rec + sizeof(IterRecord));
+  P->d_first_singular = (int *)(b + o_fs);
+  P->knn_ws = (void *)(b + o_knn);
+  if (cudaMemsetAsync(P->mem, 0, P->bytes, ctx->stream) != cudaSuccess) {
+    set_error("cudaMemsetAsync failed");
+    rbffd_problem_destroy(P);
+    return RBFFD_ECUDA;
+  }
+  rc = build(P, d);
+  if (rc != RBFFD_OK) {
+    rbffd_problem_destroy(P);
+    return rc;
+  }
+  *out = P;
+  return RBFFD_OK;
+}
+
+extern "C" int rbffd_problem_reload(rbffd_problem *P, const rbffd_problem_desc *d) {
+  if (!P) return RBFFD_EINVAL;
+  RBFFD_TRY(check_desc(d));
+  if (d->n != P->n || d->q != P->q || d->degree != P->degree || d->precision != P->precision) {
+    set_error("reload: n, q, degree and precision must match the problem");
+    return RBFFD_EINVAL;
+  }
+  RBFFD_CK(cudaSetDevice(P->ctx->device));
+  return build(P, d);
+}
+
+extern "C" void rbffd_problem_destroy(rbffd_problem *P) {
+  if (!P) return;
+  cudaSetDevice(P->ctx->device);
+  cudaStreamSynchronize(P->ctx->stream);
+  dev_free(P->ctx, P->mem, P->bytes);
+  delete P;
+}
+
+extern "C" size_t rbffd_problem_bytes(const rbffd_problem *P) { return P ? P->bytes : 0; }
+
+extern "C" int simple_iterate(rbffd_problem *P, const rbffd_step_params *sp, double *delta_out,
+                              rbffd_iter_stats *stats) {
+  if (!P) return RBFFD_EINVAL;
+  RBFFD_TRY(check_params(sp));
+  RBFFD_CK(cudaSetDevice(P->ctx->device));
+  RBFFD_TRY(issue_outer(P, sp));
+  Readback r;
+  RBFFD_TRY(read_back(P, &r));
+  if (stats) {
+    for (int k = 0; k < 3; ++k) {
+      stats->iters[k] = r.kout[k].iters;
+      stats->relres[k] = r.kout[k].relres;
+    }
+  }
+  if (delta_out) *delta_out = r.rec.delta;
+  static const char *names[3] = {"momentum u", "momentum v", "pressure correction"};
+  for (int k = 0; k < 3; ++k) {
+    int code = krylov_status_code(r.kout[k].status);
+    if (code != RBFFD_OK) {
+      set_error("%s solve failed (status %d after %d iterations, relres %.3e)", names[k],
+                r.kout[k].status, r.kout[k].iters, r.kout[k].relres);
+      return code;
+    }
+  }
+  if (!std::isfinite(r.rec.delta)) {
+    set_error("outer iteration produced a non-finite delta");
+    return RBFFD_EDIVERGED;
+  }
+  return RBFFD_OK;
+}
+
+extern "C" int rbffd_time_step(rbffd_problem *P, const rbffd_solve_params *s, double tol_outer,
+                               int32_t *outer_iters, double *change) {
+  if (!P || !s || s->max_outer < 1) return RBFFD_EINVAL;
+  rbffd_step_params sp = step_from(s);
+  int it = 0, rc = RBFFD_OK;
+  while (it < s->max_outer) {
+    double d = 0.0;
+    rc = simple_iterate(P, &sp, &d, nullptr);
+    ++it;
+    if (rc != RBFFD_OK) break;
+    if (d < tol_outer) break;
+  }
+  if (outer_iters) *outer_iters = it;
+  if (rc != RBFFD_OK) return rc;
+  RBFFD_TRY(ops_rotate(P));
+  Readback r;
+  RBFFD_TRY(read_back(P, &r));
+  if (change) *change = r.rec.change;
+  return RBFFD_OK;
+}
+
+extern "C" int rbffd_steady_residual(rbffd_problem *P, double *R3) {
+  if (!P || !R3) return RBFFD_EINVAL;
+  RBFFD_CK(cudaSetDevice(P->ctx->device));
+  RBFFD_TRY(ops_resid(P));
+  Readback r;
+  RBFFD_TRY(read_back(P, &r));
+  for (int k = 0; k < 3; ++k) R3[k] = r.rec.resid[k];
+  return RBFFD_OK;
+}
+
+static int march(rbffd_problem *P, const rbffd_solve_params *s, int32_t n_steps, bool steady,
+                 int (*on_step)(void *, int32_t, double), void *user, rbffd_solve_stats *st) {
+  if (!P || !s || !(s->dt > 0) || s->max_outer < 1) return RBFFD_EINVAL;
+  rbffd_solve_stats loc;
+  memset(&loc, 0, sizeof(loc));
+  double tol = 1e-4;
+  int rc = RBFFD_OK;
+  rbffd_step_params sp = step_from(s);
+  for (int32_t k = 0; k < n_steps; ++k) {
+    int it = 0;
+    double d = 0.0;
+    while (it < s->max_outer) {
+      rbffd_iter_stats is;
+      rc = simple_iterate(P, &sp, &d, &is);
+      ++it;
+      if (rc != RBFFD_OK) break;
+      for (int j = 0; j < 3; ++j) loc.krylov_iters[j] += is.iters[j];
+      if (d < tol) break;
+    }
+    loc.outer_iters += it;
+    if (rc != RBFFD_OK) break;
+    rc = ops_rotate(P);
+    if (rc != RBFFD_OK) break;
+    Readback r;
+    rc = read_back(P, &r);
+    if (rc != RBFFD_OK) break;
+    loc.change = r.rec.change;
+    loc.steps = k + 1;
+    tol = loc.change < 1e-4 ? loc.change : 1e-4;
+    if (steady) {
+      rc = rbffd_steady_residual(P, loc.resid);
+      if (rc != RBFFD_OK) break;
+      if (!std::isfinite(loc.resid[2])) {
+        set_error("steady residual is not finite");
+        rc = RBFFD_EDIVERGED;
+        break;
+      }
+      if (loc.resid[2] <= s->resid_tol) break;
+    }
+    if (on_step) {
+      int u = on_step(user, k + 1, (k + 1) * s->dt);
+      if (u != 0) {
+        rc = u;
+        break;
+      }
+    }
+  }
+  if (rc == RBFFD_OK && steady && !(loc.resid[2] <= s->resid_tol)) {
+    set_error("steady residual %.3e above %.3e after %d steps", loc.resid[2], s->resid_tol,
+              loc.steps);
+    rc = RBFFD_ENOCONV;
+  }
+  if (st) *st = loc;
+  return rc;
+}
+
+extern "C" int solve_steady(rbffd_problem *P, const rbffd_solve_params *s,
+                            rbffd_solve_stats *st) {
+  if (!s) return RBFFD_EINVAL;
+  return march(P, s, s->max_steps, true, nullptr, nullptr, st);
+}
+
+extern "C" int solve_unsteady(rbffd_problem *P, const rbffd_solve_params *s, int32_t n_steps,
+                              int (*on_step)(void *, int32_t, double), void *user,
+                              rbffd_solve_stats *st) {
+  return march(P, s, n_steps, false, on_step, user, st);
+}
+
+static double *field_ptr(rbffd_problem *P, int which) {
+  switch (which) {
+    case RBFFD_FIELD_U: return P->u;
+    case RBFFD_FIELD_V: return P->v;
+    case RBFFD_FIELD_P: return P->p;
+    case RBFFD_FIELD_UN: return P->un;
+    case RBFFD_FIELD_VN: return P->vn;
+    case RBFFD_FIELD_UNM1: return P->unm1;
+    case RBFFD_FIELD_VNM1: return P->vnm1;
+    case RBFFD_FIELD_UT: return P->ut;
+    case RBFFD_FIELD_VT: return P->vt;
+    case RBFFD_FIELD_PC: return P->pc;
+    case RBFFD_FIELD_UBC: return P->ubc;
+    case RBFFD_FIELD_VBC: return P->vbc;
+    default: return nullptr;
+  }
+}
+
+extern "C" int rbffd_get_field(rbffd_problem *P, int32_t which, double *out) {
+  if (!P || !out) return RBFFD_EINVAL;
+  double *f = field_ptr(P, which);
+  if (!f) return RBFFD_EINVAL;
+  RBFFD_CK(cudaSetDevice(P->ctx->device));
+  RBFFD_CK(cudaMemcpyAsync(out, f, sizeof(double) * P->n, cudaMemcpyDefault, P->ctx->stream));
+  RBFFD_CK(cudaStreamSynchronize(P->ctx->stream));
+  return RBFFD_OK;
+}
+
+extern "C" int rbffd_set_field(rbffd_problem *P, int32_t which, const double *in) {
+  if (!P || !in) return RBFFD_EINVAL;
+  double *f = field_ptr(P, which);
+  if (!f) return RBFFD_EINVAL;
+  RBFFD_CK(cudaSetDevice(P->ctx->device));
+  RBFFD_CK(cudaMemcpyAsync(f, in, sizeof(double) * P->n, cudaMemcpyDefault, P->ctx->stream));
+  RBFFD_CK(cudaStreamSynchronize(P->ctx->stream));
+  return RBFFD_OK;
+}
+
+namespace {
+__global__ void k_unpack(int n, int q, int ldn, const double *__restrict__ ell,
+                         double *__restrict__ rm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int j = 0; j < q; ++j) rm[(int64_t)i * q + j] = ell[(int64_t)j * ldn + i];
+}
+}  // namespace
+
+extern "C" int rbffd_get_operators(rbffd_problem *P, int32_t *idx, double *wx, double *wy,
+                                   double *wl, double *pcorr) {
+  if (!P) return RBFFD_EINVAL;
+  RBFFD_CK(cudaSetDevice(P->ctx->device));
+  cudaStream_t st = P->ctx->stream;
+  size_t nq = (size_t)P->n * P->q;
+  if (idx) RBFFD_CK(cudaMemcpyAsync(idx, P->idx_rm, nq * 4, cudaMemcpyDefault, st));
+  if (wx) RBFFD_CK(cudaMemcpyAsync(wx, P->wx_rm, nq * 8, cudaMemcpyDefault, st));
+  if (wy) RBFFD_CK(cudaMemcpyAsync(wy, P->wy_rm, nq * 8, cudaMemcpyDefault, st));
+  if (wl) RBFFD_CK(cudaMemcpyAsync(wl, P->wl_rm, nq * 8, cudaMemcpyDefault, st));
+  if (pcorr) {
+    // row-major copy of the packed pressure-correction matrix via p2 scratch
+    double *tmp = nullptr;
+    RBFFD_TRY(dev_alloc(P->ctx, (void **)&tmp, nq * 8));
+    k_unpack<<<(P->n + 255) / 256, 256, 0, st>>>(P->n, P->q, P->ldn, P->Pp, tmp);
+    int rc = after_launch(P->ctx, "k_unpack");
+    if (rc == RBFFD_OK &&
+        cudaMemcpyAsync(pcorr, tmp, nq * 8, cudaMemcpyDefault, st) != cudaSuccess)
+      rc = RBFFD_ECUDA;
+    cudaStreamSynchronize(st);
+    dev_free(P->ctx, tmp, nq * 8);
+    RBFFD_TRY(rc);
+  }
+  RBFFD_CK(cudaStreamSynchronize(st));
+  return RBFFD_OK;
+}
+
+extern "C" int rbffd_apply(rbffd_problem *P, int32_t which, const double *x, double *y) {
+  if (!P || !x || !y) return RBFFD_EINVAL;
+  const double *val = which == RBFFD_OP_DX ? P->Wx
+                      : which == RBFFD_OP_DY ? P->Wy
+                      : which == RBFFD_OP_LAP ? P->Wl
+                      : which == RBFFD_OP_PCORR ? P->Pp
+                      : which == RBFFD_OP_MOMENTUM ? P->Am : nullptr;
+  if (!val) return RBFFD_EINVAL;
+  RBFFD_CK(cudaSetDevice(P->ctx->device));
+  RBFFD_TRY(ops_spmv(P, val, x, y));
+  RBFFD_CK(cudaStreamSynchronize(P->ctx->stream));
+  return RBFFD_OK;
+}

@@ -1,0 +1,48 @@
+// problem.cuh -- device-resident state of one flow problem.
+#pragma once
+#include "common.cuh"
+#include "knn.cuh"
+#include "krylov.cuh"
+
+// Outer-iteration record read back by the host once per outer iteration.
+struct IterRecord {
+  double delta;
+  double change;
+  double resid[3];
+  double pad[3];
+};
+
+struct rbffd_problem {
+  rbffd_ctx *ctx = nullptr;
+  int n = 0, q = 0, degree = 0, pin = 0, precision = 0;
+  int ldn = 0;  // padded row count of the column-major ELL arrays
+  double rho = 1.0, mu = 1.0;
+  // inputs
+  double *x, *y, *nx, *ny, *ubc, *vbc;
+  int8_t *tag;
+  // clouds and weights, row-major n x q (as built)
+  int32_t *idx_rm;
+  double *wx_rm, *wy_rm, *wl_rm;
+  // packed operators, column-major [q][ldn], one shared index array
+  int32_t *col;
+  double *Wx, *Wy, *Wl, *Pp, *Am;
+  double *p_dinv, *m_dinv;
+  // fields
+  double *u, *v, *p, *p2, *un, *vn, *unm1, *vnm1, *ut, *vt, *pc, *bu, *bv, *bp;
+  // Krylov workspace: 8 vectors x 2 right-hand sides
+  rbffd::KrylovVecs kv[2];
+  double *part;       // Krylov partials
+  double *rpart;      // partials of the outer-loop reductions
+  rbffd::GridBarrier *bar;
+  rbffd::KrylovOut *kout;  // [0..1] momentum, [2] pressure correction
+  IterRecord *rec;         // device copy of the iteration record
+  int *d_first_singular;
+  // cloud-builder workspace
+  void *knn_ws;
+  rbffd::KnnLayout knn_lay;
+  int kblocks1 = 0, kblocks2 = 0;  // cooperative grid sizes (1 and 2 RHS)
+  int rblocks = 0;                 // grid of the row kernels with reductions
+  // one allocation holds everything above
+  void *mem = nullptr;
+  size_t bytes = 0;
+};

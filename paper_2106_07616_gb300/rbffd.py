@@ -1,0 +1,296 @@
+"""Thin ctypes binding of ``librbffd.so`` (argument marshalling only).
+
+Every step of the method runs in the library's CUDA kernels; this module
+only converts Python arguments into the pointers and sizes of the C ABI
+declared in ``include/rbffd.h`` and raises ``RbffdError`` on a non-zero
+status.  Device buffers are torch CUDA tensors (PyTorch supplies device
+memory and streams); host buffers are numpy arrays.  There is no CPU
+fallback: if the library is missing or was not built, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librbffd.so")
+
+OK, EINVAL, ENOMEM, ESINGULAR, ENOCONV, EDIVERGED, ETIMEOUT, ECUDA, ENOTIMPL = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+TAG_INTERIOR, TAG_DIRICHLET = 0, 1
+OP_DX, OP_DY, OP_LAP, OP_PCORR, OP_MOMENTUM = 0, 1, 2, 3, 4
+FIELDS = {"u": 0, "v": 1, "p": 2, "un": 3, "vn": 4, "unm1": 5, "vnm1": 6, "ut": 7, "vt": 8,
+          "pc": 9, "ubc": 10, "vbc": 11}
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class RbffdError(RuntimeError):
+    def __init__(self, code, where, detail):
+        super().__init__(f"{where} failed with status {code}: {detail}")
+        self.code = code
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("q", C.c_int32), ("degree", C.c_int32), ("pin", C.c_int32),
+                ("rho", C.c_double), ("mu", C.c_double), ("precision", C.c_int32),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("tag", C.c_void_p), ("nx", C.c_void_p),
+                ("ny", C.c_void_p), ("ubc", C.c_void_p), ("vbc", C.c_void_p)]
+
+
+class StepParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("alpha", C.c_double * 3), ("krylov_tol", C.c_double),
+                ("krylov_maxit", C.c_int32)]
+
+
+class IterStats(C.Structure):
+    _fields_ = [("iters", C.c_int32 * 3), ("relres", C.c_double * 3)]
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("resid_tol", C.c_double), ("max_steps", C.c_int32),
+                ("max_outer", C.c_int32), ("krylov_tol", C.c_double),
+                ("krylov_maxit", C.c_int32)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("outer_iters", C.c_int64),
+                ("krylov_iters", C.c_int64 * 3), ("resid", C.c_double * 3),
+                ("change", C.c_double)]
+
+
+STEP_CB = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int32, C.c_double)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+    L = C.CDLL(path)
+    vp, i32, i64, dbl, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+    sig = {
+        "rbffd_ctx_create": (C.c_int, [C.POINTER(vp), C.c_int, sz, vp]),
+        "rbffd_ctx_destroy": (None, [vp]),
+        "rbffd_last_error": (C.c_char_p, []),
+        "rbffd_ctx_launch_count": (i64, [vp]),
+        "rbffd_build_stencils": (C.c_int, [vp, i32, vp, vp, vp, i32, vp]),
+        "rbffd_weights": (C.c_int, [vp, i32, vp, vp, i32, vp, i32, vp, vp, vp,
+                                    C.POINTER(i32)]),
+        "rbffd_problem_create": (C.c_int, [vp, C.POINTER(ProblemDesc), C.POINTER(vp)]),
+        "rbffd_problem_reload": (C.c_int, [vp, C.POINTER(ProblemDesc)]),
+        "rbffd_problem_destroy": (None, [vp]),
+        "rbffd_problem_bytes": (sz, [vp]),
+        "simple_iterate": (C.c_int, [vp, C.POINTER(StepParams), C.POINTER(dbl),
+                                     C.POINTER(IterStats)]),
+        "rbffd_time_step": (C.c_int, [vp, C.POINTER(SolveParams), dbl, C.POINTER(i32),
+                                      C.POINTER(dbl)]),
+        "solve_steady": (C.c_int, [vp, C.POINTER(SolveParams), C.POINTER(SolveStats)]),
+        "solve_unsteady": (C.c_int, [vp, C.POINTER(SolveParams), i32, STEP_CB, vp,
+                                     C.POINTER(SolveStats)]),
+        "rbffd_steady_residual": (C.c_int, [vp, C.POINTER(dbl)]),
+        "rbffd_get_field": (C.c_int, [vp, i32, vp]),
+        "rbffd_set_field": (C.c_int, [vp, i32, vp]),
+        "rbffd_get_operators": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+        "rbffd_apply": (C.c_int, [vp, i32, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise RbffdError(rc, where, load().rbffd_last_error().decode(errors="replace"))
+
+
+def ptr(a):
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+class Context:
+    """A device context: device, HBM budget and the stream work goes to."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, stream=None):
+        L = load()
+        h = C.c_void_p()
+        s = None if stream is None else C.c_void_p(stream)
+        _check(L.rbffd_ctx_create(C.byref(h), device, hbm_budget, s), "rbffd_ctx_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            load().rbffd_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launches(self) -> int:
+        return int(load().rbffd_ctx_launch_count(self.h))
+
+
+def rbffd_build_stencils(ctx, x, y, tag, q, idx):
+    n = int(x.shape[0])
+    _check(load().rbffd_build_stencils(ctx.h, n, ptr(x), ptr(y), ptr(tag), int(q), ptr(idx)),
+           "rbffd_build_stencils")
+
+
+def rbffd_weights(ctx, x, y, q, idx, degree, wx, wy, wl):
+    n = int(x.shape[0])
+    fs = C.c_int32(-1)
+    rc = load().rbffd_weights(ctx.h, n, ptr(x), ptr(y), int(q), ptr(idx), int(degree), ptr(wx),
+                              ptr(wy), ptr(wl), C.byref(fs))
+    if rc == ESINGULAR:
+        return fs.value
+    _check(rc, "rbffd_weights")
+    return -1
+
+
+def make_desc(fp, precision=PREC_FP64, keep=None):
+    """ProblemDesc for a FlowProblem (host numpy arrays, copied by the
+    library at create/reload).  `keep` receives the arrays to keep alive."""
+    arrs = {
+        "x": np.ascontiguousarray(fp.x, np.float64), "y": np.ascontiguousarray(fp.y, np.float64),
+        "tag": np.ascontiguousarray(fp.tag, np.int8),
+        "nx": np.ascontiguousarray(fp.nx, np.float64),
+        "ny": np.ascontiguousarray(fp.ny, np.float64),
+        "ubc": np.ascontiguousarray(fp.ubc, np.float64),
+        "vbc": np.ascontiguousarray(fp.vbc, np.float64)}
+    if keep is not None:
+        keep.update(arrs)
+    d = ProblemDesc()
+    d.n, d.q, d.degree, d.pin = fp.n, fp.q, fp.degree, int(fp.pin)
+    d.rho, d.mu, d.precision = float(fp.rho), float(fp.mu), int(precision)
+    for k, a in arrs.items():
+        setattr(d, k, a.ctypes.data)
+    return d
+
+
+def desc_from_pointers(n, q, degree, pin, rho, mu, precision, x, y, tag, nx, ny, ubc, vbc):
+    """ProblemDesc from raw host or device buffers (tensors or arrays)."""
+    d = ProblemDesc()
+    d.n, d.q, d.degree, d.pin = int(n), int(q), int(degree), int(pin)
+    d.rho, d.mu, d.precision = float(rho), float(mu), int(precision)
+    for k, a in (("x", x), ("y", y), ("tag", tag), ("nx", nx), ("ny", ny), ("ubc", ubc),
+                 ("vbc", vbc)):
+        setattr(d, k, ptr(a))
+    return d
+
+
+class Problem:
+    """A device-resident flow problem (clouds, weights, operators, fields)."""
+
+    def __init__(self, ctx, fp=None, precision=PREC_FP64, desc=None):
+        self.ctx = ctx
+        keep = {}
+        d = desc if desc is not None else make_desc(fp, precision, keep)
+        h = C.c_void_p()
+        _check(load().rbffd_problem_create(ctx.h, C.byref(d), C.byref(h)), "rbffd_problem_create")
+        self.h = h
+        self.n, self.q = int(d.n), int(d.q)
+
+    def reload(self, fp=None, precision=PREC_FP64, desc=None):
+        keep = {}
+        d = desc if desc is not None else make_desc(fp, precision, keep)
+        _check(load().rbffd_problem_reload(self.h, C.byref(d)), "rbffd_problem_reload")
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            load().rbffd_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nbytes(self) -> int:
+        return int(load().rbffd_problem_bytes(self.h))
+
+    def get(self, name, out=None):
+        out = np.zeros(self.n) if out is None else out
+        _check(load().rbffd_get_field(self.h, FIELDS[name], ptr(out)), "rbffd_get_field")
+        return out
+
+    def set(self, name, arr):
+        if isinstance(arr, np.ndarray):
+            arr = np.ascontiguousarray(arr, np.float64)
+        _check(load().rbffd_set_field(self.h, FIELDS[name], ptr(arr)), "rbffd_set_field")
+
+    def operators(self):
+        n, q = self.n, self.q
+        idx = np.zeros((n, q), np.int32)
+        wx, wy, wl, pc = (np.zeros((n, q)) for _ in range(4))
+        _check(load().rbffd_get_operators(self.h, ptr(idx), ptr(wx), ptr(wy), ptr(wl), ptr(pc)),
+               "rbffd_get_operators")
+        return {"idx": idx, "wx": wx, "wy": wy, "wl": wl, "pval": pc}
+
+    def apply(self, which, x, y):
+        _check(load().rbffd_apply(self.h, int(which), ptr(x), ptr(y)), "rbffd_apply")
+
+    def simple_iterate(self, dt, alpha=(1.5, -2.0, 0.5), krylov_tol=1e-12, krylov_maxit=10000):
+        sp = StepParams(dt, (C.c_double * 3)(*alpha), krylov_tol, krylov_maxit)
+        d = C.c_double(0)
+        st = IterStats()
+        _check(load().simple_iterate(self.h, C.byref(sp), C.byref(d), C.byref(st)),
+               "simple_iterate")
+        return d.value, {"iters": list(st.iters), "relres": list(st.relres)}
+
+    def time_step(self, dt, tol_outer, max_outer=20, krylov_tol=1e-12, krylov_maxit=10000):
+        sp = SolveParams(dt, 0.0, 1, max_outer, krylov_tol, krylov_maxit)
+        it = C.c_int32(0)
+        ch = C.c_double(0)
+        _check(load().rbffd_time_step(self.h, C.byref(sp), tol_outer, C.byref(it), C.byref(ch)),
+               "rbffd_time_step")
+        return it.value, ch.value
+
+    def steady_residual(self):
+        r = (C.c_double * 3)()
+        _check(load().rbffd_steady_residual(self.h, r), "rbffd_steady_residual")
+        return np.array(list(r))
+
+    def solve_steady(self, dt, resid_tol=1e-8, max_steps=10000, max_outer=20, krylov_tol=1e-12,
+                     krylov_maxit=10000, check=True):
+        sp = SolveParams(dt, resid_tol, max_steps, max_outer, krylov_tol, krylov_maxit)
+        st = SolveStats()
+        rc = load().solve_steady(self.h, C.byref(sp), C.byref(st))
+        if check:
+            _check(rc, "solve_steady")
+        return rc, _stats(st)
+
+    def solve_unsteady(self, dt, n_steps, max_outer=20, krylov_tol=1e-12, krylov_maxit=10000,
+                       on_step=None):
+        sp = SolveParams(dt, 0.0, 0, max_outer, krylov_tol, krylov_maxit)
+        st = SolveStats()
+        cb = STEP_CB(on_step) if on_step is not None else STEP_CB()
+        _check(load().solve_unsteady(self.h, C.byref(sp), int(n_steps), cb, None, C.byref(st)),
+               "solve_unsteady")
+        return _stats(st)
+
+
+def _stats(st):
+    return {"steps": st.steps, "outer": st.outer_iters, "krylov": list(st.krylov_iters),
+            "resid": list(st.resid), "change": st.change}
