@@ -88,6 +88,40 @@ const char *rbffd_last_error(void);
 /* Number of kernel launches this context has issued (for accounting). */
 int64_t rbffd_ctx_launch_count(const rbffd_ctx *ctx);
 
+/* Live per-kernel timing.  While enabled, the context brackets the launches
+ * of the classes below with CUDA events on its own stream (the stream the
+ * kernels run on) and accumulates, per class: launches, device time, the
+ * units of work processed and the algorithmic bytes (or flops) those units
+ * move.  Units and bytes per unit:
+ *   KRYLOV_P    (pressure-correction BiCGSTAB, 1 right-hand side):
+ *               unit = one row in one iteration; bytes = 2q(s_w + s_i) + 14 s_v
+ *   KRYLOV_MOM  (momentum BiCGSTAB, 2 right-hand sides sharing the matrix):
+ *               unit = one row in one iteration; bytes = 2q(s_w + s_i) + 28 s_v
+ *   WEIGHTS     unit = one cloud; "bytes" holds FP64 flops: 2N^3/3 + 2 N^2 (3 rhs)
+ *               + the matrix build, N = q + m
+ *   KNN         unit = one point; bytes = 24 (coordinates in, q indices out)
+ *   OUTER       one outer iteration (whole simple_iterate, GPU time)
+ * s_w, s_i, s_v: bytes of a matrix value, a column index, a vector entry
+ * (8, 4, 8 in the FP64 path; 4, 4, 4 for the FP32 inner iterations of the
+ * mixed path, whose few FP64 residual sweeps are not counted as units).
+ * rbffd_ctx_profile(ctx, 1) resets the counters and enables timing; 0 stops. */
+enum {
+  RBFFD_KSTAT_KRYLOV_P = 0,
+  RBFFD_KSTAT_KRYLOV_MOM = 1,
+  RBFFD_KSTAT_WEIGHTS = 2,
+  RBFFD_KSTAT_KNN = 3,
+  RBFFD_KSTAT_OUTER = 4,
+  RBFFD_KSTAT_COUNT = 5
+};
+typedef struct {
+  int64_t launches;
+  double ms;     /* summed device time */
+  double units;  /* units of work processed */
+  double bytes;  /* algorithmic bytes (flops for WEIGHTS) */
+} rbffd_kernel_stat;
+int rbffd_ctx_profile(rbffd_ctx *ctx, int enable);
+int rbffd_ctx_kernel_stat(const rbffd_ctx *ctx, int32_t which, rbffd_kernel_stat *out);
+
 /* ------------------------------------------------------- S1: the clouds */
 
 /* Cloud selection (paper Sec. 2, "a cloud of neighboring points", and
@@ -160,13 +194,18 @@ size_t rbffd_problem_bytes(const rbffd_problem *prob);
 typedef struct {
   double dt;             /* time step */
   double alpha[3];       /* BDF2: 1.5, -2, 0.5 (paper Sec. 3) */
-  double krylov_tol;     /* relative residual of each Krylov solve */
+  double krylov_tol;     /* FP64 relative residual of each Krylov solve */
   int32_t krylov_maxit;  /* iteration cap of each Krylov solve */
+  /* RBFFD_PREC_MIXED only (0 = default): relative reduction asked of each
+     FP32 inner solve (default 1e-3) and its iteration cap (default 4000) */
+  double inner_tol;
+  int32_t inner_maxit;
 } rbffd_step_params;
 
 typedef struct {
-  int32_t iters[3];   /* BiCGSTAB iterations: u~, v~, p' */
-  double relres[3];   /* final relative residuals */
+  int32_t iters[3];   /* BiCGSTAB iterations: u~, v~, p' (inner FP32 ones if mixed) */
+  double relres[3];   /* final FP64 relative residuals */
+  int32_t sweeps[3];  /* defect-correction sweeps (mixed precision; 0 otherwise) */
 } rbffd_iter_stats;
 
 /* One outer iteration (paper Sec. 3.2 steps 2-7):
@@ -196,6 +235,8 @@ typedef struct {
   int32_t max_outer;      /* cap on outer iterations per time step */
   double krylov_tol;
   int32_t krylov_maxit;
+  double inner_tol;       /* as in rbffd_step_params */
+  int32_t inner_maxit;
 } rbffd_solve_params;
 
 typedef struct {

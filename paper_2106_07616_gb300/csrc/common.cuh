@@ -2,6 +2,7 @@
 // errors, launch accounting, deterministic reductions, bounded grid barrier).
 #pragma once
 
+#include <cuda/atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,6 +22,10 @@ struct rbffd_ctx {
   // pinned host scratch for small read-backs
   void *pinned = nullptr;
   size_t pinned_bytes = 0;
+  // live kernel timing (rbffd_ctx_profile)
+  bool prof = false;
+  cudaEvent_t ev[8] = {};
+  rbffd_kernel_stat kst[RBFFD_KSTAT_COUNT] = {};
 };
 
 namespace rbffd {
@@ -62,6 +67,28 @@ int pinned(rbffd_ctx *ctx, size_t bytes, void **out);
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+// Event pair k (0..3) brackets a launch when profiling is on.
+inline void prof_begin(rbffd_ctx *ctx, int k) {
+  if (ctx->prof) cudaEventRecord(ctx->ev[2 * k], ctx->stream);
+}
+inline void prof_end(rbffd_ctx *ctx, int k) {
+  if (ctx->prof) cudaEventRecord(ctx->ev[2 * k + 1], ctx->stream);
+}
+// After the stream has been synchronised: add pair k to class `cls`.
+inline void prof_collect(rbffd_ctx *ctx, int k, int cls, double units, double bytes) {
+  if (!ctx->prof) return;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, ctx->ev[2 * k], ctx->ev[2 * k + 1]) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  rbffd_kernel_stat &s = ctx->kst[cls];
+  s.launches += 1;
+  s.ms += ms;
+  s.units += units;
+  s.bytes += bytes;
+}
+
 // ------------------------------------------------------------------------
 // Device helpers
 
@@ -102,33 +129,33 @@ struct GridBarrier {
   int pad;
 };
 
-// Grid-wide barrier for a cooperative launch.  Every wait is bounded: after
-// ~2^31 clock cycles (about a second) the block records a timeout in
+// Grid-wide barrier for a cooperative launch: arrive with a release
+// fetch_add, the last arriver publishes the next generation with a release
+// store, the others poll it with acquire loads.  Every wait is bounded:
+// after ~2^31 clock cycles (about a second) the block records a timeout in
 // bar->err and goes on; callers test the return value and leave the kernel.
 __device__ __forceinline__ bool grid_sync(GridBarrier *bar, unsigned int nblocks,
                                           unsigned int &gen) {
-  __syncthreads();
   __shared__ int s_ok;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned int arrived = atomicAdd(&bar->count, 1u);
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar->count);
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> g(bar->gen);
+    cuda::atomic_ref<int, cuda::thread_scope_device> er(bar->err);
+    unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
     if (arrived == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicExch(&bar->gen, gen + 1);
+      cnt.store(0u, cuda::memory_order_relaxed);
+      g.store(gen + 1, cuda::memory_order_release);
     } else {
       long long t0 = clock64();
-      volatile unsigned int *vg = &bar->gen;
-      while (*vg == gen) {
+      while (g.load(cuda::memory_order_acquire) == gen) {
         if (clock64() - t0 > (1ll << 31)) {
-          atomicExch(&bar->err, 1);
+          er.store(1, cuda::memory_order_relaxed);
           break;
         }
-        __nanosleep(20);
       }
     }
-    __threadfence();
-    s_ok = (*(volatile int *)&bar->err) == 0;
+    s_ok = er.load(cuda::memory_order_relaxed) == 0;
   }
   gen++;
   __syncthreads();

@@ -99,7 +99,26 @@ extern "C" void rbffd_ctx_destroy(rbffd_ctx *ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  for (int k = 0; k < 8; ++k)
+    if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
   delete ctx;
+}
+
+extern "C" int rbffd_ctx_profile(rbffd_ctx *ctx, int enable) {
+  if (!ctx) return RBFFD_EINVAL;
+  RBFFD_CK(cudaSetDevice(ctx->device));
+  if (enable && !ctx->ev[0]) {
+    for (int k = 0; k < 8; ++k) RBFFD_CK(cudaEventCreate(&ctx->ev[k]));
+  }
+  memset(ctx->kst, 0, sizeof(ctx->kst));
+  ctx->prof = enable != 0;
+  return RBFFD_OK;
+}
+
+extern "C" int rbffd_ctx_kernel_stat(const rbffd_ctx *ctx, int32_t which, rbffd_kernel_stat *out) {
+  if (!ctx || !out || which < 0 || which >= RBFFD_KSTAT_COUNT) return RBFFD_EINVAL;
+  *out = ctx->kst[which];
+  return RBFFD_OK;
 }
 
 extern "C" int64_t rbffd_ctx_launch_count(const rbffd_ctx *ctx) { return ctx ? ctx->launches : 0; }

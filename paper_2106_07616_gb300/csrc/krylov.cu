@@ -3,427 +3,419 @@
 // systems (Sec. 3), as ONE persistent cooperative kernel per solve.
 //
 // Rows are spread over a grid that is resident all at once (cooperative
-// launch); the five grid-wide dependencies of an iteration are crossed with
-// a bounded grid barrier (common.cuh).  Dot products are block partials
-// followed by a fixed-order sum that every block evaluates redundantly, so
-// all blocks hold bit-identical scalars and a solve is deterministic.
-// NR = 2 runs two independent recurrences (u~ and v~) that share the
-// matrix: one pass over the ELL arrays feeds both SpMVs.
+// launch, one 1024-thread block per SM for one right-hand side, 512 for
+// two); the five grid-wide dependencies of an iteration are crossed with a
+// bounded acquire/release grid barrier (common.cuh).  A solve of a few
+// tens of thousands of rows is latency-bound, so the SpMV spreads each row
+// over T threads (T = 1..8, chosen from the thread count per row) to keep
+// many independent gathers in flight.
 //
-// Vectors written inside the kernel are read with __ldcg (L2, coherent
-// across SMs); the matrix, which never changes during a solve, goes
-// through the read-only path.
+// Dot products: block partials, then a fixed-order sum that every block
+// evaluates redundantly, so all blocks hold bit-identical scalars and a
+// solve is deterministic run to run.  NR = 2 runs two independent
+// recurrences (u~ and v~) that share the matrix: one pass over the ELL
+// arrays feeds both SpMVs.
+//
+// Vectors written inside the kernel and gathered by other rows are read
+// with __ldcg (L2, coherent across SMs); row-local vectors are only ever
+// touched by the thread that owns the row; the matrix never changes during
+// a solve and goes through the read-only path.
 #include "common.cuh"
 #include "krylov.cuh"
+#include "krylov_dev.cuh"
 
 namespace rbffd {
 
 namespace {
 
-constexpr int NT = 256;
-
 // slots of the partials array (x NR for the right-hand sides)
-enum { S_BB = 0, S_RR, S_RHV, S_SS, S_TT, S_TS, S_RHR, S_COUNT };
+enum { S_BB = 0, S_RR, S_RHV, S_SS, S_RHS, S_TT, S_TS, S_RHT, S_COUNT };
 
-template <int NR>
-struct RowSpmv {
-  __device__ __forceinline__ static void run(int i, int q, int ldn, const int32_t *__restrict__ col,
-                                             const double *__restrict__ val, double *const *xs,
-                                             double *out) {
-#pragma unroll
-    for (int k = 0; k < NR; ++k) out[k] = 0.0;
-#pragma unroll 4
-    for (int j = 0; j < q; ++j) {
-      const int64_t e = (int64_t)j * ldn + i;
-      const int c = __ldg(col + e);
-      const double a = __ldg(val + e);
-#pragma unroll
-      for (int k = 0; k < NR; ++k) out[k] += a * __ldcg(xs[k] + c);
-    }
-  }
-};
+using kdev::MAXB;
 
 }  // namespace
 
-template <int NR>
+// Scalar state of one recurrence.  Thread 0 of each block updates it from
+// the grid totals; the other threads read it after a __syncthreads, so the
+// FP64 divisions and square roots run once per block, not once per thread
+// (GB300 issues FP64 at a small fraction of its FP32 rate).
+struct KScalars {
+  double bnorm, rho, rho_prev, alpha, omega, beta, relres, snorm;
+  int it, restarts, state, need_init, first, half, run;
+};
+
+// One BiCGSTAB iteration as four grid exchanges:
+//   A: v = A p^,            partial (r^, v)                -> alpha
+//   B: s = r - alpha v, s^ = s/d  (rows only)               -> barrier
+//   C: t = A s^,            partials (s,s) (t,t) (t,s) (r^,s) (r^,t)
+//                                                           -> omega, rho' = (r^,s) - omega (r^,t)
+//   D: x += alpha p^ + omega s^, r = s - omega t, and already the next
+//      p = r + beta (p - omega v), p^ = p/d with beta = (rho'/rho)(alpha/omega);
+//      partial (r, r)                                      -> |r| test
+// The next direction is formed before the |r| test; if the test stops the
+// solve it is simply unused.  rho' equals (r^, r) in exact arithmetic.
+template <int NR, int NT>
 __global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
-  __shared__ double sred[NT / 32];
-  const int nb = gridDim.x;
+  __shared__ double sred[5 * NR * (NT / 32)];  // block_partials of up to 5 NR values
+  __shared__ double stot[16];
+  __shared__ KScalars ks[NR];
+  __shared__ int s_flags[2];
   const int tid = blockIdx.x * NT + threadIdx.x;
-  const int stride = nb * NT;
-  const int n = A.n, q = A.q, ldn = A.ldn;
-  unsigned int gen = *(volatile unsigned int *)&A.bar->gen;
+  const int stride = gridDim.x * NT;
+  const int wglobal = tid >> 5, nwarps = stride >> 5;
+  const int n = A.n, q = A.q, ldn = A.ldn, T = A.tpr;
+  const int nb = gridDim.x;
+  unsigned int epoch = 1;
   double *part = A.part;
   auto P = [&](int slot, int k) { return part + (size_t)(slot * NR + k) * nb; };
+  const bool leader = threadIdx.x == 0;
+  int *err = &A.bar->err;
 
-  double bnorm[NR], rho[NR], rho_prev[NR], alpha[NR], omega[NR], relres[NR], snorm[NR];
-  int it[NR], restarts[NR], state[NR];
-  bool need_init[NR], first[NR], have_bnorm[NR], half[NR], zero_x[NR];
+  if (leader) {
 #pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    bnorm[k] = rho[k] = rho_prev[k] = alpha[k] = omega[k] = 1.0;
-    relres[k] = snorm[k] = 0.0;
-    it[k] = restarts[k] = 0;
-    state[k] = KRY_RUNNING;
-    need_init[k] = true;
-    first[k] = true;
-    have_bnorm[k] = false;
-    half[k] = false;
-    zero_x[k] = false;
+    for (int k = 0; k < NR; ++k) {
+      KScalars &c = ks[k];
+      c.bnorm = c.rho = c.rho_prev = c.alpha = c.omega = 1.0;
+      c.beta = c.relres = c.snorm = 0.0;
+      c.it = c.restarts = 0;
+      c.state = KRY_RUNNING;
+      c.need_init = 1;
+      c.first = 1;
+      c.half = 0;
+      c.run = 1;
+    }
   }
+  __syncthreads();
   bool ok = true;
+  bool have_bnorm = false;
 
   for (;;) {
-    // ---------------- (re)start: r = b - A x, r^ = r, p = v = 0
-    bool any_init = false;
+    // ---------------- (re)start: r = b - A x, r^ = r, p = r, p^ = r / d
+    bool ini[NR], any_init = false;
 #pragma unroll
-    for (int k = 0; k < NR; ++k) any_init |= (state[k] == KRY_RUNNING && need_init[k]);
+    for (int k = 0; k < NR; ++k) {
+      ini[k] = ks[k].state == KRY_RUNNING && ks[k].need_init;
+      any_init |= ini[k];
+    }
+    __syncthreads();
     if (any_init) {
-      double pbb[NR], prr[NR];
+      double acc[2 * NR];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) pbb[k] = prr[k] = 0.0;
-      for (int i = tid; i < n; i += stride) {
-        double ax[NR];
-        RowSpmv<NR>::run(i, q, ldn, A.col, A.val, A.x, ax);
+      for (int k = 0; k < 2 * NR; ++k) acc[k] = 0.0;
+      kdev::spmv_rows<NR, double>(n, q, ldn, T, A.col, A.val, A.x, wglobal, nwarps,
+                    [&](int i, const double *ax) {
+                      const double di = __ldg(A.dinv + i);
+#pragma unroll
+                      for (int k = 0; k < NR; ++k) {
+                        if (!ini[k]) continue;
+                        const double bi = A.b[k][i];
+                        const double ri = bi - ax[k];
+                        A.w[k].r[i] = ri;
+                        A.w[k].rh[i] = ri;
+                        A.w[k].p[i] = ri;
+                        A.w[k].ph[i] = ri * di;
+                        acc[2 * k] += bi * bi;
+                        acc[2 * k + 1] += ri * ri;
+                      }
+                    });
+      double *outs[2 * NR];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        outs[2 * k] = ini[k] ? P(S_BB, k) : nullptr;
+        outs[2 * k + 1] = ini[k] ? P(S_RR, k) : nullptr;
+      }
+      kdev::block_partials<NT, 2 * NR>(acc, sred, outs);
+      double tot[2 * NR];
+      ok = kdev::exchange<2 * NR>(A.flags, err, epoch++, outs, tot, stot);
+      if (!ok) break;
+      int zero_any = 0;
+      if (leader) {
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-          if (state[k] != KRY_RUNNING || !need_init[k]) continue;
-          const double bi = A.b[k][i];
-          const double ri = bi - ax[k];
-          A.w[k].r[i] = ri;
-          A.w[k].rh[i] = ri;
-          A.w[k].p[i] = 0.0;
-          A.w[k].v[i] = 0.0;
-          pbb[k] += bi * bi;
-          prr[k] += ri * ri;
+          KScalars &c = ks[k];
+          if (!ini[k]) continue;
+          c.need_init = 0;
+          const double bb = tot[2 * k], rr = tot[2 * k + 1];
+          if (c.it == 0 && c.restarts == 0) c.bnorm = sqrt(bb);
+          if (c.bnorm == 0.0) {
+            c.relres = 0.0;
+            c.state = KRY_OK;
+            zero_any |= 1 << k;
+            continue;
+          }
+          c.relres = sqrt(rr) / c.bnorm;
+          if (!(c.relres == c.relres)) { c.state = KRY_DIVERGED; continue; }
+          if (c.relres <= A.tol) { c.state = KRY_OK; continue; }
+          c.rho = rr;  // (r^, r) with r^ = r
+          if (c.rho == 0.0) c.state = KRY_NOCONV;
         }
+        s_flags[1] = zero_any;
       }
-#pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        if (state[k] != KRY_RUNNING || !need_init[k]) continue;
-        double sb = block_sum<NT>(pbb[k], sred);
-        double sr = block_sum<NT>(prr[k], sred);
-        if (threadIdx.x == 0) {
-          P(S_BB, k)[blockIdx.x] = sb;
-          P(S_RR, k)[blockIdx.x] = sr;
-        }
-      }
-      ok = grid_sync(A.bar, nb, gen);
-      if (!ok) break;
-      bool any_zero = false;
-#pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        if (state[k] != KRY_RUNNING || !need_init[k]) continue;
-        need_init[k] = false;
-        double bb = 0.0, rr = 0.0;
-        if (threadIdx.x < 32) {
-          bb = warp_sum_array(P(S_BB, k), nb);
-          rr = warp_sum_array(P(S_RR, k), nb);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) { sred[0] = bb; sred[1] = rr; }
-        __syncthreads();
-        bb = sred[0];
-        rr = sred[1];
-        __syncthreads();
-        if (!have_bnorm[k]) {
-          bnorm[k] = sqrt(bb);
-          have_bnorm[k] = true;
-        }
-        if (bnorm[k] == 0.0) {
-          zero_x[k] = true;
-          relres[k] = 0.0;
-          state[k] = KRY_OK;
-          any_zero = true;
-          continue;
-        }
-        const double rn = sqrt(rr);
-        relres[k] = rn / bnorm[k];
-        if (!(relres[k] == relres[k])) { state[k] = KRY_DIVERGED; continue; }
-        if (relres[k] <= A.tol) { state[k] = KRY_OK; continue; }
-        rho[k] = rr;  // (r^, r) with r^ = r
-        first[k] = true;
-      }
-      if (any_zero) {
+      __syncthreads();
+      zero_any = s_flags[1];
+      if (zero_any) {
         for (int i = tid; i < n; i += stride) {
 #pragma unroll
           for (int k = 0; k < NR; ++k)
-            if (zero_x[k]) A.x[k][i] = 0.0;
-        }
-#pragma unroll
-        for (int k = 0; k < NR; ++k) zero_x[k] = false;
-      }
-    }
-    bool any_run = false;
-#pragma unroll
-    for (int k = 0; k < NR; ++k) any_run |= (state[k] == KRY_RUNNING);
-    if (!any_run) break;
-
-    // breakdown rho == 0: restart (at most 3 times)
-    bool restart = false;
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-      if (state[k] != KRY_RUNNING) continue;
-      if (rho[k] == 0.0) {
-        if (restarts[k] >= 3) {
-          state[k] = KRY_NOCONV;
-        } else {
-          restarts[k]++;
-          need_init[k] = true;
-          restart = true;
+            if (zero_any & (1 << k)) A.x[k][i] = 0.0;
         }
       }
+      (void)have_bnorm;
     }
-    if (restart) continue;
-
-    // ---------------- P1: p = r + beta (p - omega v); p^ = p / d
-    double beta[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k)
-      beta[k] = first[k] ? 0.0 : (rho[k] / rho_prev[k]) * (alpha[k] / omega[k]);
-    for (int i = tid; i < n; i += stride) {
-      const double di = __ldg(A.dinv + i);
+    if (leader) {
+      int running = 0;
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
-        if (state[k] != KRY_RUNNING) continue;
-        const double ri = A.w[k].r[i];
-        const double pi = first[k] ? ri : ri + beta[k] * (A.w[k].p[i] - omega[k] * A.w[k].v[i]);
-        A.w[k].p[i] = pi;
-        A.w[k].ph[i] = pi * di;
+        ks[k].run = ks[k].state == KRY_RUNNING;
+        running |= ks[k].run;
       }
+      s_flags[0] = running;
     }
-    ok = grid_sync(A.bar, nb, gen);
-    if (!ok) break;
-
-    // ---------------- P2: v = A p^, partial (r^, v)
-    {
-      double prv[NR];
+    __syncthreads();
+    if (!s_flags[0]) break;
+    bool run[NR];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) prv[k] = 0.0;
+    for (int k = 0; k < NR; ++k) run[k] = ks[k].run != 0;
+
+    // ---------------- A: v = A p^, partial (r^, v)
+    {
+      double acc[NR];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) acc[k] = 0.0;
       double *phs[NR];
 #pragma unroll
       for (int k = 0; k < NR; ++k) phs[k] = A.w[k].ph;
-      for (int i = tid; i < n; i += stride) {
-        double av[NR];
-        RowSpmv<NR>::run(i, q, ldn, A.col, A.val, phs, av);
+      kdev::spmv_rows<NR, double>(n, q, ldn, T, A.col, A.val, phs, wglobal, nwarps,
+                    [&](int i, const double *av) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-          if (state[k] != KRY_RUNNING) continue;
-          A.w[k].v[i] = av[k];
-          prv[k] += A.w[k].rh[i] * av[k];
-        }
-      }
+                      for (int k = 0; k < NR; ++k) {
+                        if (!run[k]) continue;
+                        A.w[k].v[i] = av[k];
+                        acc[k] += A.w[k].rh[i] * av[k];
+                      }
+                    });
+      double *outs[NR];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        if (state[k] != KRY_RUNNING) continue;
-        double s = block_sum<NT>(prv[k], sred);
-        if (threadIdx.x == 0) P(S_RHV, k)[blockIdx.x] = s;
+      for (int k = 0; k < NR; ++k) outs[k] = run[k] ? P(S_RHV, k) : nullptr;
+      kdev::block_partials<NT, NR>(acc, sred, outs);
+      double tot[NR];
+      ok = kdev::exchange<NR>(A.flags, err, epoch++, outs, tot, stot);
+      if (!ok) break;
+      if (leader) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+          if (run[k]) ks[k].alpha = ks[k].rho / tot[k];
       }
+      __syncthreads();
     }
-    ok = grid_sync(A.bar, nb, gen);
-    if (!ok) break;
 
-    // ---------------- P3: alpha = rho / (r^, v); s = r - alpha v; s^ = s / d
+    // ---------------- B: s = r - alpha v; s^ = s / d
     {
-      double rv[NR];
+      double alp[NR];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        rv[k] = 0.0;
-        if (state[k] != KRY_RUNNING) continue;
-        double t = 0.0;
-        if (threadIdx.x < 32) t = warp_sum_array(P(S_RHV, k), nb);
-        __syncthreads();
-        if (threadIdx.x == 0) sred[0] = t;
-        __syncthreads();
-        rv[k] = sred[0];
-        __syncthreads();
-        alpha[k] = rho[k] / rv[k];
-      }
-      double pss[NR];
-#pragma unroll
-      for (int k = 0; k < NR; ++k) pss[k] = 0.0;
+      for (int k = 0; k < NR; ++k) alp[k] = ks[k].alpha;
       for (int i = tid; i < n; i += stride) {
         const double di = __ldg(A.dinv + i);
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-          if (state[k] != KRY_RUNNING) continue;
-          const double si = A.w[k].r[i] - alpha[k] * A.w[k].v[i];
+          if (!run[k]) continue;
+          const double si = A.w[k].r[i] - alp[k] * A.w[k].v[i];
           A.w[k].s[i] = si;
           A.w[k].sh[i] = si * di;
-          pss[k] += si * si;
         }
       }
-#pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        if (state[k] != KRY_RUNNING) continue;
-        double s = block_sum<NT>(pss[k], sred);
-        if (threadIdx.x == 0) P(S_SS, k)[blockIdx.x] = s;
-      }
+      ok = kdev::exchange<0, double>(A.flags, err, epoch++, nullptr, nullptr, stot);
+      if (!ok) break;
     }
-    ok = grid_sync(A.bar, nb, gen);
-    if (!ok) break;
 
-    // ---------------- P4: t = A s^, partials (t, t), (t, s)
+    // ---------------- C: t = A s^, partials (s,s) (t,t) (t,s) (r^,s) (r^,t)
     {
-      double ptt[NR], pts[NR];
+      double acc[5 * NR];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) ptt[k] = pts[k] = 0.0;
+      for (int k = 0; k < 5 * NR; ++k) acc[k] = 0.0;
       double *shs[NR];
 #pragma unroll
       for (int k = 0; k < NR; ++k) shs[k] = A.w[k].sh;
-      for (int i = tid; i < n; i += stride) {
-        double at[NR];
-        RowSpmv<NR>::run(i, q, ldn, A.col, A.val, shs, at);
+      kdev::spmv_rows<NR, double>(n, q, ldn, T, A.col, A.val, shs, wglobal, nwarps,
+                    [&](int i, const double *at) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-          if (state[k] != KRY_RUNNING) continue;
-          A.w[k].t[i] = at[k];
-          ptt[k] += at[k] * at[k];
-          pts[k] += at[k] * A.w[k].s[i];
-        }
-      }
+                      for (int k = 0; k < NR; ++k) {
+                        if (!run[k]) continue;
+                        const double si = A.w[k].s[i], rhi = A.w[k].rh[i];
+                        A.w[k].t[i] = at[k];
+                        acc[5 * k + 0] += si * si;
+                        acc[5 * k + 1] += at[k] * at[k];
+                        acc[5 * k + 2] += at[k] * si;
+                        acc[5 * k + 3] += rhi * si;
+                        acc[5 * k + 4] += rhi * at[k];
+                      }
+                    });
+      double *outs[5 * NR];
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
-        if (state[k] != KRY_RUNNING) continue;
-        double a = block_sum<NT>(ptt[k], sred);
-        double b = block_sum<NT>(pts[k], sred);
-        if (threadIdx.x == 0) {
-          P(S_TT, k)[blockIdx.x] = a;
-          P(S_TS, k)[blockIdx.x] = b;
+        outs[5 * k + 0] = run[k] ? P(S_SS, k) : nullptr;
+        outs[5 * k + 1] = run[k] ? P(S_TT, k) : nullptr;
+        outs[5 * k + 2] = run[k] ? P(S_TS, k) : nullptr;
+        outs[5 * k + 3] = run[k] ? P(S_RHS, k) : nullptr;
+        outs[5 * k + 4] = run[k] ? P(S_RHT, k) : nullptr;
+      }
+      kdev::block_partials<NT, 5 * NR>(acc, sred, outs);
+      double tot[5 * NR];
+      ok = kdev::exchange<5 * NR>(A.flags, err, epoch++, outs, tot, stot);
+      if (!ok) break;
+      if (leader) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+          KScalars &c = ks[k];
+          c.half = 0;
+          if (!run[k]) continue;
+          const double ss = tot[5 * k + 0], tt = tot[5 * k + 1], ts = tot[5 * k + 2];
+          const double rhs = tot[5 * k + 3], rht = tot[5 * k + 4];
+          c.it++;
+          c.snorm = sqrt(ss);
+          if (!(c.snorm == c.snorm)) {
+            c.state = KRY_DIVERGED;
+            c.run = 0;
+            continue;
+          }
+          if (c.snorm / c.bnorm <= A.tol) {
+            c.half = 1;
+            continue;
+          }
+          c.omega = tt == 0.0 ? 0.0 : ts / tt;
+          const double rho_new = rhs - c.omega * rht;
+          c.beta = (c.omega == 0.0) ? 0.0 : (rho_new / c.rho) * (c.alpha / c.omega);
+          c.rho_prev = c.rho;
+          c.rho = rho_new;
         }
       }
+      __syncthreads();
     }
-    ok = grid_sync(A.bar, nb, gen);
-    if (!ok) break;
 
-    // ---------------- P5: half-step test on |s|; omega; x and r updates
+    // ---------------- D: x and r updates, next direction, partial (r, r)
     {
+      bool half[NR];
+      double alp[NR], omg[NR], bet[NR];
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
-        half[k] = false;
-        if (state[k] != KRY_RUNNING) continue;
-        double ss = 0.0, tt = 0.0, ts = 0.0;
-        if (threadIdx.x < 32) {
-          ss = warp_sum_array(P(S_SS, k), nb);
-          tt = warp_sum_array(P(S_TT, k), nb);
-          ts = warp_sum_array(P(S_TS, k), nb);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) { sred[0] = ss; sred[1] = tt; sred[2] = ts; }
-        __syncthreads();
-        ss = sred[0];
-        tt = sred[1];
-        ts = sred[2];
-        __syncthreads();
-        it[k]++;
-        snorm[k] = sqrt(ss);
-        if (!(snorm[k] == snorm[k])) { state[k] = KRY_DIVERGED; continue; }
-        if (snorm[k] / bnorm[k] <= A.tol) {
-          half[k] = true;
-        } else {
-          omega[k] = tt == 0.0 ? 0.0 : ts / tt;
-        }
+        run[k] = ks[k].run != 0;
+        half[k] = ks[k].half != 0;
+        alp[k] = ks[k].alpha;
+        omg[k] = ks[k].omega;
+        bet[k] = ks[k].beta;
       }
-      double prr[NR], prh[NR];
+      double acc[NR];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) prr[k] = prh[k] = 0.0;
+      for (int k = 0; k < NR; ++k) acc[k] = 0.0;
       for (int i = tid; i < n; i += stride) {
+        const double di = __ldg(A.dinv + i);
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-          if (state[k] != KRY_RUNNING) continue;
+          if (!run[k]) continue;
+          const double phi = A.w[k].ph[i];
           if (half[k]) {
-            A.x[k][i] = A.x[k][i] + alpha[k] * A.w[k].ph[i];
+            A.x[k][i] = A.x[k][i] + alp[k] * phi;
           } else {
-            A.x[k][i] = A.x[k][i] + alpha[k] * A.w[k].ph[i] + omega[k] * A.w[k].sh[i];
-            const double ri = A.w[k].s[i] - omega[k] * A.w[k].t[i];
+            const double shi = A.w[k].sh[i];
+            A.x[k][i] = A.x[k][i] + alp[k] * phi + omg[k] * shi;
+            const double ri = A.w[k].s[i] - omg[k] * A.w[k].t[i];
             A.w[k].r[i] = ri;
-            prr[k] += ri * ri;
-            prh[k] += A.w[k].rh[i] * ri;
+            acc[k] += ri * ri;
+            const double pi = ri + bet[k] * (A.w[k].p[i] - omg[k] * A.w[k].v[i]);
+            A.w[k].p[i] = pi;
+            A.w[k].ph[i] = pi * di;
           }
         }
       }
+      double *outs[NR];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        if (state[k] != KRY_RUNNING || half[k]) continue;
-        double a = block_sum<NT>(prr[k], sred);
-        double b = block_sum<NT>(prh[k], sred);
-        if (threadIdx.x == 0) {
-          P(S_RR, k)[blockIdx.x] = a;
-          P(S_RHR, k)[blockIdx.x] = b;
+      for (int k = 0; k < NR; ++k) outs[k] = (run[k] && !half[k]) ? P(S_RR, k) : nullptr;
+      kdev::block_partials<NT, NR>(acc, sred, outs);
+      double tot[NR];
+      ok = kdev::exchange<NR>(A.flags, err, epoch++, outs, tot, stot);
+      if (!ok) break;
+      if (leader) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+          KScalars &c = ks[k];
+          if (!run[k]) continue;
+          if (half[k]) {
+            c.relres = c.snorm / c.bnorm;
+            c.state = KRY_OK;
+            continue;
+          }
+          const double rn = sqrt(tot[k]);
+          c.relres = rn / c.bnorm;
+          if (!(rn == rn)) { c.state = KRY_DIVERGED; continue; }
+          if (c.relres <= A.tol) { c.state = KRY_OK; continue; }
+          if (c.omega == 0.0 || c.rho == 0.0) {
+            // breakdown: restart from the current x (at most 3 times)
+            if (c.restarts >= 3) {
+              c.state = KRY_NOCONV;
+            } else {
+              c.restarts++;
+              c.need_init = 1;
+            }
+            continue;
+          }
+          if (c.it >= A.maxit) { c.state = KRY_NOCONV; continue; }
         }
       }
-    }
-    ok = grid_sync(A.bar, nb, gen);
-    if (!ok) break;
-
-    // ---------------- end of iteration: |r| test, next rho
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-      if (state[k] != KRY_RUNNING) continue;
-      if (half[k]) {
-        relres[k] = snorm[k] / bnorm[k];
-        state[k] = KRY_OK;
-        continue;
-      }
-      double rr = 0.0, rh = 0.0;
-      if (threadIdx.x < 32) {
-        rr = warp_sum_array(P(S_RR, k), nb);
-        rh = warp_sum_array(P(S_RHR, k), nb);
-      }
       __syncthreads();
-      if (threadIdx.x == 0) { sred[0] = rr; sred[1] = rh; }
-      __syncthreads();
-      rr = sred[0];
-      rh = sred[1];
-      __syncthreads();
-      const double rn = sqrt(rr);
-      relres[k] = rn / bnorm[k];
-      if (!(rn == rn)) { state[k] = KRY_DIVERGED; continue; }
-      if (relres[k] <= A.tol) { state[k] = KRY_OK; continue; }
-      if (omega[k] == 0.0) {
-        if (restarts[k] >= 3) {
-          state[k] = KRY_NOCONV;
-        } else {
-          restarts[k]++;
-          need_init[k] = true;
-        }
-        continue;
-      }
-      if (it[k] >= A.maxit) { state[k] = KRY_NOCONV; continue; }
-      rho_prev[k] = rho[k];
-      rho[k] = rh;
-      first[k] = false;
     }
   }
 
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && leader) {
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-      A.out[k].iters = it[k];
-      A.out[k].restarts = restarts[k];
-      A.out[k].status = ok ? state[k] : KRY_TIMEOUT;
-      A.out[k].relres = relres[k];
+      A.out[k].iters = ks[k].it;
+      A.out[k].restarts = ks[k].restarts;
+      A.out[k].status = ok ? ks[k].state : KRY_TIMEOUT;
+      A.out[k].relres = ks[k].relres;
     }
   }
 }
+
+namespace {
+constexpr int NT1 = 1024;  // threads per block, one right-hand side
+constexpr int NT2 = 512;   // two right-hand sides (more registers per thread)
+
+inline int nt_for(int nr) { return nr == 1 ? NT1 : NT2; }
+}  // namespace
 
 int krylov_max_blocks(rbffd_ctx *ctx, int nr) {
   int per_sm = 0;
   cudaError_t e;
   if (nr == 1)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab<1>, NT, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab<1, NT1>, NT1, 0);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab<2>, NT, 0);
-  if (e != cudaSuccess || per_sm < 1) return 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab<2, NT2>, NT2, 0);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
   return per_sm * ctx->num_sms;
 }
 
 int krylov_blocks_for(rbffd_ctx *ctx, int n, int nr) {
+  const int nt = nt_for(nr);
   int cap = krylov_max_blocks(ctx, nr);
-  int want = (n + NT - 1) / NT;
-  if (want > ctx->num_sms) want = ctx->num_sms;
+  if (cap > ctx->num_sms) cap = ctx->num_sms;  // one block per SM
+  if (cap > MAXB) cap = MAXB;
+  // aim at 8 threads per row before spreading over fewer SMs
+  long long want = ((long long)n * 8 + nt - 1) / nt;
   if (want < 1) want = 1;
-  return want < cap ? want : cap;
+  return (int)(want < cap ? want : cap);
+}
+
+// Largest T <= 8 whose groups (32 / T per warp) still cover every row in
+// one pass; 1 when the rows outnumber the threads.
+int krylov_threads_per_row(int n, int nr, int nblocks) {
+  const long long warps = (long long)nblocks * nt_for(nr) / 32;
+  int best = 1;
+  for (int T = 2; T <= 8; ++T)
+    if ((long long)(32 / T) * warps >= n) best = T;
+  return best;
 }
 
 int krylov_launch(rbffd_ctx *ctx, int nr, int nblocks, const KrylovArgs &args) {
@@ -431,15 +423,20 @@ int krylov_launch(rbffd_ctx *ctx, int nr, int nblocks, const KrylovArgs &args) {
     set_error("krylov_launch: no co-resident blocks available");
     return RBFFD_ECUDA;
   }
+  if (nblocks > MAXB) {
+    set_error("krylov_launch: %d blocks exceed the limit %d", nblocks, MAXB);
+    return RBFFD_EINVAL;
+  }
   RBFFD_CK(cudaMemsetAsync(args.bar, 0, sizeof(GridBarrier), ctx->stream));
+  RBFFD_CK(cudaMemsetAsync(args.flags, 0, sizeof(unsigned int) * nblocks, ctx->stream));
   void *kargs[] = {(void *)&args};
   cudaError_t e;
   if (nr == 1)
-    e = cudaLaunchCooperativeKernel((const void *)k_bicgstab<1>, dim3(nblocks), dim3(NT), kargs,
-                                    0, ctx->stream);
+    e = cudaLaunchCooperativeKernel((const void *)k_bicgstab<1, NT1>, dim3(nblocks), dim3(NT1),
+                                    kargs, 0, ctx->stream);
   else
-    e = cudaLaunchCooperativeKernel((const void *)k_bicgstab<2>, dim3(nblocks), dim3(NT), kargs,
-                                    0, ctx->stream);
+    e = cudaLaunchCooperativeKernel((const void *)k_bicgstab<2, NT2>, dim3(nblocks), dim3(NT2),
+                                    kargs, 0, ctx->stream);
   ctx->launches++;
   if (e != cudaSuccess) {
     set_error("cooperative launch of k_bicgstab failed: %s", cudaGetErrorString(e));

@@ -1,0 +1,154 @@
+// krylov_dev.cuh -- device building blocks of the persistent Krylov
+// kernels: a T-threads-per-row ELL SpMV, block partial sums and the
+// grid-wide publish/wait/reduce exchange.
+#pragma once
+#include "common.cuh"
+
+namespace rbffd {
+namespace kdev {
+
+constexpr int CH = 12;                   // gathers batched per lane before the FMAs
+constexpr int MAXB = 160;                // blocks a launch may use
+constexpr int BPL = (MAXB + 31) / 32;    // flags / partials per lane
+
+template <typename T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// y_k(i) = sum_j A(i,j) x_k(j), accumulated in AT, T threads per row
+// (T = 1..8, any value; the last 32 mod T lanes of a warp idle).  The
+// column indices and values of a chunk of CH entries are loaded first, then
+// the CH gathers, so a row costs two dependent memory round trips per
+// chunk.  f(i, y) runs on the group leader; all 32 lanes execute the same
+// trip count and shuffles.  Gathered vectors go through __ldcg (coherent
+// L2) because other blocks of the same launch write them.
+template <int NR, typename AT, typename VT, typename XT, typename F>
+__device__ __forceinline__ void spmv_rows(int n, int q, int ldn, int T,
+                                          const int32_t *__restrict__ col,
+                                          const VT *__restrict__ val, XT *const *xs, int wglobal,
+                                          int nwarps, F &&f) {
+  const int lane = threadIdx.x & 31;
+  const int gpw = 32 / T;
+  const int g = lane / T;
+  const int lg = lane - g * T;
+  const bool active = g < gpw;
+  for (int base = wglobal * gpw; base < n; base += nwarps * gpw) {
+    const int i = base + g;
+    const bool valid = active && i < n;
+    AT s[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) s[k] = AT(0);
+    if (valid) {
+      for (int j0 = lg; j0 < q; j0 += CH * T) {
+        int c[CH];
+        VT a[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          const int j = j0 + u * T;
+          const int64_t e = (int64_t)j * ldn + i;
+          c[u] = j < q ? __ldg(col + e) : -1;
+          a[u] = j < q ? __ldg(val + e) : VT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          if (c[u] >= 0) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k) s[k] += AT(a[u]) * AT(__ldcg(xs[k] + c[u]));
+          }
+        }
+      }
+    }
+    AT tot[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) tot[k] = s[k];
+    for (int u = 1; u < T; ++u) {
+#pragma unroll
+      for (int k = 0; k < NR; ++k) tot[k] += __shfl_sync(0xffffffffu, s[k], (lane + u) & 31);
+    }
+    if (valid && lg == 0) f(i, tot);
+  }
+}
+
+// Block-reduce V values per thread into V partials written at outs[v][b].
+template <int NT, int V, typename AT>
+__device__ __forceinline__ void block_partials(AT (&val)[V], AT *sh, AT *const *outs) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    AT t = wsum(val[v]);
+    if (l == 0) sh[v * (NT / 32) + w] = t;
+  }
+  __syncthreads();
+  if (w < V) {
+    AT t = (l < NT / 32) ? sh[w * (NT / 32) + l] : AT(0);
+    t = wsum(t);
+    if (l == 0 && outs[w] != nullptr) outs[w][blockIdx.x] = t;
+  }
+}
+
+// Grid-wide exchange: publish this block's writes (rows and partials) with
+// a release store of flags[b] = epoch, wait (acquire, bounded) until every
+// block has published epoch, then reduce the V partial arrays in a fixed
+// order, one warp per array.  Every block computes bit-identical totals.
+// V = 0 is a plain barrier.
+template <int V, typename AT>
+__device__ __forceinline__ bool exchange(unsigned int *flags, int *err, unsigned int epoch,
+                                         AT *const *arrs, AT *tot, AT *sh) {
+  __shared__ int s_ok;
+  const int nb = gridDim.x;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(flags[blockIdx.x]);
+    f.store(epoch, cuda::memory_order_release);
+  }
+  if (w == 0) {
+    // every lane polls up to BPL flags at once; the warp leaves together
+    long long t0 = clock64();
+    bool ok = true;
+    for (;;) {
+      bool mine = true;
+#pragma unroll
+      for (int u = 0; u < BPL; ++u) {
+        const int b = l + 32 * u;
+        if (b < nb) {
+          cuda::atomic_ref<unsigned int, cuda::thread_scope_device> g(flags[b]);
+          mine &= g.load(cuda::memory_order_acquire) >= epoch;
+        }
+      }
+      if (__all_sync(0xffffffffu, mine)) break;
+      if (clock64() - t0 > (1ll << 31)) {
+        ok = false;
+        break;
+      }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && l == 0) atomicExch(err, 1);
+    if (l == 0) s_ok = ok && (*(volatile int *)err == 0);
+  }
+  __syncthreads();
+  if (V > 0 && w < V) {
+    AT t = AT(0);
+    if (arrs[w] != nullptr) {
+#pragma unroll
+      for (int u = 0; u < BPL; ++u) {
+        const int b = l + 32 * u;
+        if (b < nb) t += __ldcg(arrs[w] + b);
+      }
+    }
+    t = wsum(t);
+    if (l == 0) sh[w] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < V; ++v) tot[v] = sh[v];
+  const bool ok = s_ok != 0;
+  __syncthreads();
+  return ok;
+}
+
+}  // namespace kdev
+}  // namespace rbffd

@@ -22,7 +22,8 @@ __global__ void k_pack(int n, int q, int ldn, int pin, const int32_t *__restrict
                        const double *__restrict__ nx, const double *__restrict__ ny,
                        int32_t *__restrict__ col, double *__restrict__ Wx,
                        double *__restrict__ Wy, double *__restrict__ Wl,
-                       double *__restrict__ Pp, double *__restrict__ pdinv) {
+                       double *__restrict__ Pp, double *__restrict__ pdinv,
+                       float *__restrict__ Pp32, float *__restrict__ pdinv32) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ldn) return;
   if (i >= n) {  // padding rows: self-loops with zero weight, never read
@@ -30,8 +31,10 @@ __global__ void k_pack(int n, int q, int ldn, int pin, const int32_t *__restrict
       int64_t e = (int64_t)j * ldn + i;
       col[e] = 0;
       Wx[e] = Wy[e] = Wl[e] = Pp[e] = 0.0;
+      if (Pp32) Pp32[e] = 0.f;
     }
     pdinv[i] = 1.0;
+    if (pdinv32) pdinv32[i] = 1.f;
     return;
   }
   const bool interior = tag[i] == 0;
@@ -53,9 +56,11 @@ __global__ void k_pack(int n, int q, int ldn, int pin, const int32_t *__restrict
     else
       pv = ni * a + mi * b;
     Pp[e] = pv;
+    if (Pp32) Pp32[e] = (float)pv;
     if (c == i) diag += pv;
   }
   pdinv[i] = 1.0 / (diag == 0.0 ? 1.0 : diag);
+  if (pdinv32) pdinv32[i] = (float)pdinv[i];
 }
 
 // S4: momentum matrix and right-hand sides, Eqs. (u:tilde), (v:tilde):
@@ -74,7 +79,8 @@ __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ co
                            double a1, double a2, double a3, double *__restrict__ Am,
                            double *__restrict__ mdinv, double *__restrict__ bu,
                            double *__restrict__ bv, double *__restrict__ ut,
-                           double *__restrict__ vt) {
+                           double *__restrict__ vt, float *__restrict__ Am32,
+                           float *__restrict__ mdinv32) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const bool interior = tag[i] == 0;
@@ -82,8 +88,12 @@ __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ co
   ut[i] = ui;
   vt[i] = vi;
   if (!interior) {
-    for (int j = 0; j < q; ++j) Am[(int64_t)j * ldn + i] = (j == 0) ? 1.0 : 0.0;
+    for (int j = 0; j < q; ++j) {
+      Am[(int64_t)j * ldn + i] = (j == 0) ? 1.0 : 0.0;
+      if (Am32) Am32[(int64_t)j * ldn + i] = (j == 0) ? 1.f : 0.f;
+    }
     mdinv[i] = 1.0;
+    if (mdinv32) mdinv32[i] = 1.f;
     bu[i] = ubc[i];
     bv[i] = vbc[i];
     return;
@@ -104,8 +114,10 @@ __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ co
       diag += val;
     }
     Am[e] = val;
+    if (Am32) Am32[e] = (float)val;
   }
   mdinv[i] = 1.0 / (diag == 0.0 ? 1.0 : diag);
+  if (mdinv32) mdinv32[i] = (float)mdinv[i];
   bu[i] = -rho * (a2 * un[i] + a3 * unm1[i]) / dt - gx;
   bv[i] = -rho * (a2 * vn[i] + a3 * vnm1[i]) / dt - gy;
 }
@@ -348,7 +360,7 @@ static inline int grid_of(int n) { return (n + RT - 1) / RT; }
 int ops_pack(rbffd_problem *P) {
   k_pack<<<(P->ldn + RT - 1) / RT, RT, 0, P->ctx->stream>>>(
       P->n, P->q, P->ldn, P->pin, P->idx_rm, P->wx_rm, P->wy_rm, P->wl_rm, P->tag, P->nx, P->ny,
-      P->col, P->Wx, P->Wy, P->Wl, P->Pp, P->p_dinv);
+      P->col, P->Wx, P->Wy, P->Wl, P->Pp, P->p_dinv, P->Pp32, P->p_dinv32);
   return after_launch(P->ctx, "k_pack");
 }
 
@@ -356,7 +368,7 @@ int ops_momentum(rbffd_problem *P, const rbffd_step_params *sp) {
   k_momentum<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(
       P->n, P->q, P->ldn, P->col, P->Wx, P->Wy, P->Wl, P->tag, P->u, P->v, P->p, P->un, P->vn,
       P->unm1, P->vnm1, P->ubc, P->vbc, P->rho, P->mu, sp->dt, sp->alpha[0], sp->alpha[1],
-      sp->alpha[2], P->Am, P->m_dinv, P->bu, P->bv, P->ut, P->vt);
+      sp->alpha[2], P->Am, P->m_dinv, P->bu, P->bv, P->ut, P->vt, P->Am32, P->m_dinv32);
   return after_launch(P->ctx, "k_momentum");
 }
 

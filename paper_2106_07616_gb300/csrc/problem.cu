@@ -77,15 +77,19 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
   P->rho = d->rho;
   P->mu = d->mu;
   P->pin = d->pin;
+  prof_begin(ctx, 3);
   RBFFD_TRY(knn_run(ctx, P->knn_ws, P->knn_lay, P->n, P->x, P->y, P->tag, P->q, P->idx_rm));
+  prof_end(ctx, 3);
   if (pin_tag == RBFFD_TAG_INTERIOR) {
     set_error("problem desc: pin %d is not a boundary point", d->pin);
     return RBFFD_EINVAL;
   }
   int big = 0x7fffffff;
   RBFFD_CK(cudaMemcpyAsync(P->d_first_singular, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+  prof_begin(ctx, 0);
   RBFFD_TRY(weights_run(ctx, P->n, P->x, P->y, P->q, P->idx_rm, P->degree, P->wx_rm, P->wy_rm,
                         P->wl_rm, P->d_first_singular));
+  prof_end(ctx, 0);
   RBFFD_TRY(ops_pack(P));
   k_init_state<<<(P->n + 255) / 256, 256, 0, st>>>(P->n, P->tag, P->ubc, P->vbc, P->u, P->v,
                                                    P->p, P->un, P->vn, P->unm1, P->vnm1, P->pc,
@@ -94,6 +98,12 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
   int hfs = big;
   RBFFD_CK(cudaMemcpyAsync(&hfs, P->d_first_singular, sizeof(int), cudaMemcpyDeviceToHost, st));
   RBFFD_CK(cudaStreamSynchronize(st));
+  if (ctx->prof) {
+    const double N = P->q + (P->degree + 1) * (P->degree + 2) / 2;
+    const double flops = 2.0 * N * N * N / 3.0 + 6.0 * N * N + 10.0 * P->q * P->q;
+    prof_collect(ctx, 3, RBFFD_KSTAT_KNN, P->n, 24.0 * P->n);
+    prof_collect(ctx, 0, RBFFD_KSTAT_WEIGHTS, P->n, flops * P->n);
+  }
   if (hfs != big) {
     set_error("singular collocation matrix at point %d", hfs);
     return RBFFD_ESINGULAR;
@@ -114,6 +124,7 @@ int krylov_status_code(int s) {
 // Issue one outer iteration (no host synchronisation).
 int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   rbffd_ctx *ctx = P->ctx;
+  prof_begin(ctx, 2);
   RBFFD_TRY(ops_momentum(P, sp));
   KrylovArgs a;
   memset(&a, 0, sizeof(a));
@@ -123,8 +134,57 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   a.col = P->col;
   a.part = P->part;
   a.bar = P->bar;
+  a.flags = P->flags;
   a.tol = sp->krylov_tol;
   a.maxit = sp->krylov_maxit;
+  if (P->precision == RBFFD_PREC_MIXED) {
+    MixedArgs m;
+    memset(&m, 0, sizeof(m));
+    m.n = P->n;
+    m.q = P->q;
+    m.ldn = P->ldn;
+    m.col = P->col;
+    m.part64 = P->part64;
+    m.part32 = P->part32;
+    m.bar = P->bar;
+    m.flags = P->flags;
+    m.tol = sp->krylov_tol;
+    m.maxit = sp->krylov_maxit;
+    m.inner_tol = sp->inner_tol > 0 ? sp->inner_tol : 1e-3;
+    m.inner_maxit = sp->inner_maxit > 0 ? sp->inner_maxit : 4000;
+    m.max_sweeps = 60;
+    m.val64 = P->Am;
+    m.val32 = P->Am32;
+    m.dinv32 = P->m_dinv32;
+    m.b[0] = P->bu;
+    m.b[1] = P->bv;
+    m.x[0] = P->ut;
+    m.x[1] = P->vt;
+    m.w[0] = P->mv[0];
+    m.w[1] = P->mv[1];
+    m.out = P->kout;
+    m.tpr = krylov_threads_per_row(P->n, 2, P->kblocks2);
+    prof_begin(ctx, 0);
+    RBFFD_TRY(krylov_ir_launch(ctx, 2, P->kblocks2, m));
+    prof_end(ctx, 0);
+    RBFFD_TRY(ops_divergence(P, sp));
+    m.val64 = P->Pp;
+    m.val32 = P->Pp32;
+    m.dinv32 = P->p_dinv32;
+    m.b[0] = P->bp;
+    m.b[1] = nullptr;
+    m.x[0] = P->pc;
+    m.x[1] = nullptr;
+    m.out = P->kout + 2;
+    m.tpr = krylov_threads_per_row(P->n, 1, P->kblocks1);
+    prof_begin(ctx, 1);
+    RBFFD_TRY(krylov_ir_launch(ctx, 1, P->kblocks1, m));
+    prof_end(ctx, 1);
+    RBFFD_TRY(ops_pressure(P, sp));
+    RBFFD_TRY(ops_correct(P, sp));
+    prof_end(ctx, 2);
+    return RBFFD_OK;
+  }
   // momentum predictor: one matrix, two right-hand sides
   a.val = P->Am;
   a.dinv = P->m_dinv;
@@ -135,7 +195,10 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   a.w[0] = P->kv[0];
   a.w[1] = P->kv[1];
   a.out = P->kout;
+  a.tpr = krylov_threads_per_row(P->n, 2, P->kblocks2);
+  prof_begin(ctx, 0);
   RBFFD_TRY(krylov_launch(ctx, 2, P->kblocks2, a));
+  prof_end(ctx, 0);
   RBFFD_TRY(ops_divergence(P, sp));
   // pressure correction
   a.val = P->Pp;
@@ -145,9 +208,13 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   a.x[0] = P->pc;
   a.x[1] = nullptr;
   a.out = P->kout + 2;
+  a.tpr = krylov_threads_per_row(P->n, 1, P->kblocks1);
+  prof_begin(ctx, 1);
   RBFFD_TRY(krylov_launch(ctx, 1, P->kblocks1, a));
+  prof_end(ctx, 1);
   RBFFD_TRY(ops_pressure(P, sp));
   RBFFD_TRY(ops_correct(P, sp));
+  prof_end(ctx, 2);
   return RBFFD_OK;
 }
 
@@ -183,6 +250,8 @@ rbffd_step_params step_from(const rbffd_solve_params *s) {
   sp.alpha[2] = 0.5;
   sp.krylov_tol = s->krylov_tol;
   sp.krylov_maxit = s->krylov_maxit;
+  sp.inner_tol = s->inner_tol;
+  sp.inner_maxit = s->inner_maxit;
   return sp;
 }
 
@@ -206,6 +275,12 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   knn_workspace_bytes(n, &P->knn_lay);
   P->kblocks1 = krylov_blocks_for(ctx, n, 1);
   P->kblocks2 = krylov_blocks_for(ctx, n, 2);
+  const bool mixed = d->precision == RBFFD_PREC_MIXED;
+  if (mixed) {
+    int c1 = krylov_ir_max_blocks(ctx, 1), c2 = krylov_ir_max_blocks(ctx, 2);
+    if (P->kblocks1 > c1) P->kblocks1 = c1;
+    if (P->kblocks2 > c2) P->kblocks2 = c2;
+  }
   P->rblocks = ops_reduce_blocks(ctx, n);
   size_t npart = krylov_partials_doubles(2, P->kblocks2);
   size_t np1 = krylov_partials_doubles(1, P->kblocks1);
@@ -225,9 +300,21 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   for (int k = 0; k < 16; ++k) o_kv[k] = c.take<double>(n);
   size_t o_part = c.take<double>(npart), o_rpart = c.take<double>(6 * (size_t)P->rblocks);
   size_t o_bar = c.take<GridBarrier>(1);
+  size_t o_flags = c.take<unsigned int>(256);
   size_t o_rec = c.take<Readback>(1);
   size_t o_fs = c.take<int>(1);
   size_t o_knn = c.take<char>(P->knn_lay.bytes);
+  size_t o_p32 = 0, o_a32 = 0, o_pd32 = 0, o_md32 = 0, o_mv[18] = {}, o_part64 = 0, o_part32 = 0;
+  if (mixed) {
+    o_p32 = c.take<float>(lq);
+    o_a32 = c.take<float>(lq);
+    o_pd32 = c.take<float>(P->ldn);
+    o_md32 = c.take<float>(P->ldn);
+    for (int k = 0; k < 18; ++k) o_mv[k] = c.take<float>(n);
+    int kb = P->kblocks1 > P->kblocks2 ? P->kblocks1 : P->kblocks2;
+    o_part64 = c.take<double>(krylov_ir_partials64(2, kb));
+    o_part32 = c.take<float>(krylov_ir_partials32(2, kb));
+  }
   P->bytes = c.off;
   int rc = dev_alloc(ctx, &P->mem, P->bytes);
   if (rc != RBFFD_OK) {
@@ -265,10 +352,24 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   P->part = (double *)(b + o_part);
   P->rpart = (double *)(b + o_rpart);
   P->bar = (GridBarrier *)(b + o_bar);
+  P->flags = (unsigned int *)(b + o_flags);
   P->rec = (IterRecord *)(b + o_rec);
   P->kout = (KrylovOut *)((char *)P->rec + sizeof(IterRecord));
   P->d_first_singular = (int *)(b + o_fs);
   P->knn_ws = (void *)(b + o_knn);
+  if (mixed) {
+    P->Pp32 = (float *)(b + o_p32);
+    P->Am32 = (float *)(b + o_a32);
+    P->p_dinv32 = (float *)(b + o_pd32);
+    P->m_dinv32 = (float *)(b + o_md32);
+    for (int r = 0; r < 2; ++r) {
+      float **w[9] = {&P->mv[r].r, &P->mv[r].rh, &P->mv[r].p, &P->mv[r].v, &P->mv[r].ph,
+                      &P->mv[r].s, &P->mv[r].sh, &P->mv[r].t, &P->mv[r].d};
+      for (int k = 0; k < 9; ++k) *w[k] = (float *)(b + o_mv[r * 9 + k]);
+    }
+    P->part64 = (double *)(b + o_part64);
+    P->part32 = (float *)(b + o_part32);
+  }
   if (cudaMemsetAsync(P->mem, 0, P->bytes, ctx->stream) != cudaSuccess) {
     set_error("cudaMemsetAsync failed");
     rbffd_problem_destroy(P);
@@ -312,10 +413,22 @@ extern "C" int simple_iterate(rbffd_problem *P, const rbffd_step_params *sp, dou
   RBFFD_TRY(issue_outer(P, sp));
   Readback r;
   RBFFD_TRY(read_back(P, &r));
+  if (P->ctx->prof) {
+    // inner iterations of the mixed path move FP32 values and vectors
+    const bool mx = P->precision == RBFFD_PREC_MIXED;
+    const double sw = mx ? 4.0 : 8.0, si = 4.0, sv = mx ? 4.0 : 8.0, q = P->q, n = P->n;
+    int im = r.kout[0].iters > r.kout[1].iters ? r.kout[0].iters : r.kout[1].iters;
+    double um = n * im, upc = n * r.kout[2].iters;
+    prof_collect(P->ctx, 0, RBFFD_KSTAT_KRYLOV_MOM, um, um * (2 * q * (sw + si) + 28 * sv));
+    prof_collect(P->ctx, 1, RBFFD_KSTAT_KRYLOV_P, upc, upc * (2 * q * (sw + si) + 14 * sv));
+    prof_collect(P->ctx, 2, RBFFD_KSTAT_OUTER, 1.0, 0.0);
+  }
   if (stats) {
+    const bool mixed = P->precision == RBFFD_PREC_MIXED;
     for (int k = 0; k < 3; ++k) {
       stats->iters[k] = r.kout[k].iters;
       stats->relres[k] = r.kout[k].relres;
+      stats->sweeps[k] = mixed ? r.kout[k].restarts : 0;
     }
   }
   if (delta_out) *delta_out = r.rec.delta;

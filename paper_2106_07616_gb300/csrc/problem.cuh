@@ -27,6 +27,11 @@ struct rbffd_problem {
   int32_t *col;
   double *Wx, *Wy, *Wl, *Pp, *Am;
   double *p_dinv, *m_dinv;
+  // FP32 copies for the mixed-precision solves (null in the FP64 path)
+  float *Pp32 = nullptr, *Am32 = nullptr, *p_dinv32 = nullptr, *m_dinv32 = nullptr;
+  rbffd::MixedVecs mv[2] = {};
+  double *part64 = nullptr;
+  float *part32 = nullptr;
   // fields
   double *u, *v, *p, *p2, *un, *vn, *unm1, *vnm1, *ut, *vt, *pc, *bu, *bv, *bp;
   // Krylov workspace: 8 vectors x 2 right-hand sides
@@ -34,6 +39,7 @@ struct rbffd_problem {
   double *part;       // Krylov partials
   double *rpart;      // partials of the outer-loop reductions
   rbffd::GridBarrier *bar;
+  unsigned int *flags;     // Krylov publish flags (one per block)
   rbffd::KrylovOut *kout;  // [0..1] momentum, [2] pressure correction
   IterRecord *rec;         // device copy of the iteration record
   int *d_first_singular;

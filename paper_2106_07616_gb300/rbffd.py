@@ -41,17 +41,20 @@ class ProblemDesc(C.Structure):
 
 class StepParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("alpha", C.c_double * 3), ("krylov_tol", C.c_double),
-                ("krylov_maxit", C.c_int32)]
+                ("krylov_maxit", C.c_int32), ("inner_tol", C.c_double),
+                ("inner_maxit", C.c_int32)]
 
 
 class IterStats(C.Structure):
-    _fields_ = [("iters", C.c_int32 * 3), ("relres", C.c_double * 3)]
+    _fields_ = [("iters", C.c_int32 * 3), ("relres", C.c_double * 3),
+                ("sweeps", C.c_int32 * 3)]
 
 
 class SolveParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("resid_tol", C.c_double), ("max_steps", C.c_int32),
                 ("max_outer", C.c_int32), ("krylov_tol", C.c_double),
-                ("krylov_maxit", C.c_int32)]
+                ("krylov_maxit", C.c_int32), ("inner_tol", C.c_double),
+                ("inner_maxit", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -59,6 +62,13 @@ class SolveStats(C.Structure):
                 ("krylov_iters", C.c_int64 * 3), ("resid", C.c_double * 3),
                 ("change", C.c_double)]
 
+
+class KernelStat(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("ms", C.c_double), ("units", C.c_double),
+                ("bytes", C.c_double)]
+
+
+KSTAT = {"krylov_p": 0, "krylov_mom": 1, "weights": 2, "knn": 3, "outer": 4}
 
 STEP_CB = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int32, C.c_double)
 
@@ -79,6 +89,8 @@ def load(path: str = LIB_PATH):
         "rbffd_ctx_destroy": (None, [vp]),
         "rbffd_last_error": (C.c_char_p, []),
         "rbffd_ctx_launch_count": (i64, [vp]),
+        "rbffd_ctx_profile": (C.c_int, [vp, C.c_int]),
+        "rbffd_ctx_kernel_stat": (C.c_int, [vp, i32, C.POINTER(KernelStat)]),
         "rbffd_build_stencils": (C.c_int, [vp, i32, vp, vp, vp, i32, vp]),
         "rbffd_weights": (C.c_int, [vp, i32, vp, vp, i32, vp, i32, vp, vp, vp,
                                     C.POINTER(i32)]),
@@ -148,6 +160,15 @@ class Context:
     @property
     def launches(self) -> int:
         return int(load().rbffd_ctx_launch_count(self.h))
+
+    def profile(self, enable: bool = True):
+        _check(load().rbffd_ctx_profile(self.h, int(enable)), "rbffd_ctx_profile")
+
+    def kernel_stat(self, name: str) -> dict:
+        st = KernelStat()
+        _check(load().rbffd_ctx_kernel_stat(self.h, KSTAT[name], C.byref(st)),
+               "rbffd_ctx_kernel_stat")
+        return {"launches": st.launches, "ms": st.ms, "units": st.units, "bytes": st.bytes}
 
 
 def rbffd_build_stencils(ctx, x, y, tag, q, idx):
@@ -251,16 +272,20 @@ class Problem:
     def apply(self, which, x, y):
         _check(load().rbffd_apply(self.h, int(which), ptr(x), ptr(y)), "rbffd_apply")
 
-    def simple_iterate(self, dt, alpha=(1.5, -2.0, 0.5), krylov_tol=1e-12, krylov_maxit=10000):
-        sp = StepParams(dt, (C.c_double * 3)(*alpha), krylov_tol, krylov_maxit)
+    def simple_iterate(self, dt, alpha=(1.5, -2.0, 0.5), krylov_tol=1e-12, krylov_maxit=10000,
+                       inner_tol=0.0, inner_maxit=0):
+        sp = StepParams(dt, (C.c_double * 3)(*alpha), krylov_tol, krylov_maxit, inner_tol,
+                        inner_maxit)
         d = C.c_double(0)
         st = IterStats()
         _check(load().simple_iterate(self.h, C.byref(sp), C.byref(d), C.byref(st)),
                "simple_iterate")
-        return d.value, {"iters": list(st.iters), "relres": list(st.relres)}
+        return d.value, {"iters": list(st.iters), "relres": list(st.relres),
+                         "sweeps": list(st.sweeps)}
 
-    def time_step(self, dt, tol_outer, max_outer=20, krylov_tol=1e-12, krylov_maxit=10000):
-        sp = SolveParams(dt, 0.0, 1, max_outer, krylov_tol, krylov_maxit)
+    def time_step(self, dt, tol_outer, max_outer=20, krylov_tol=1e-12, krylov_maxit=10000,
+                  inner_tol=0.0, inner_maxit=0):
+        sp = SolveParams(dt, 0.0, 1, max_outer, krylov_tol, krylov_maxit, inner_tol, inner_maxit)
         it = C.c_int32(0)
         ch = C.c_double(0)
         _check(load().rbffd_time_step(self.h, C.byref(sp), tol_outer, C.byref(it), C.byref(ch)),
@@ -273,8 +298,9 @@ class Problem:
         return np.array(list(r))
 
     def solve_steady(self, dt, resid_tol=1e-8, max_steps=10000, max_outer=20, krylov_tol=1e-12,
-                     krylov_maxit=10000, check=True):
-        sp = SolveParams(dt, resid_tol, max_steps, max_outer, krylov_tol, krylov_maxit)
+                     krylov_maxit=10000, check=True, inner_tol=0.0, inner_maxit=0):
+        sp = SolveParams(dt, resid_tol, max_steps, max_outer, krylov_tol, krylov_maxit, inner_tol,
+                         inner_maxit)
         st = SolveStats()
         rc = load().solve_steady(self.h, C.byref(sp), C.byref(st))
         if check:
@@ -282,8 +308,8 @@ class Problem:
         return rc, _stats(st)
 
     def solve_unsteady(self, dt, n_steps, max_outer=20, krylov_tol=1e-12, krylov_maxit=10000,
-                       on_step=None):
-        sp = SolveParams(dt, 0.0, 0, max_outer, krylov_tol, krylov_maxit)
+                       on_step=None, inner_tol=0.0, inner_maxit=0):
+        sp = SolveParams(dt, 0.0, 0, max_outer, krylov_tol, krylov_maxit, inner_tol, inner_maxit)
         st = SolveStats()
         cb = STEP_CB(on_step) if on_step is not None else STEP_CB()
         _check(load().solve_unsteady(self.h, C.byref(sp), int(n_steps), cb, None, C.byref(st)),

@@ -177,3 +177,33 @@ def test_bad_arguments_rejected():
     fp.pin = 70  # an interior point
     with pytest.raises(rbffd.RbffdError):
         rbffd.Problem(ctx(), fp)
+
+
+@pytest.mark.parametrize("kind", ["kovasznay", "cavity"])
+def test_mixed_precision_outer_iterations_match_oracle(kind):
+    """FP32 BiCGSTAB inside FP64 defect correction stops on the same FP64
+    relative residual as the FP64 solver, so the outer iterates agree with
+    the FP64 oracle to the same tolerance."""
+    fp = clouds.kovasznay(30, dt=0.4) if kind == "kovasznay" else clouds.cavity(40, dt=0.05)
+    P = rbffd.Problem(ctx(), fp, rbffd.PREC_MIXED)
+    O = oracle.Problem(fp, krylov_tol=1e-12)
+    for r in range(3):
+        dg, sg = P.simple_iterate(fp.dt, krylov_tol=1e-12)
+        do, so = O.simple_iterate(fp.dt)
+        assert max(sg["relres"]) <= 1e-12
+        assert sg["sweeps"][2] >= 1
+        assert abs(dg - do) <= 1e-8 * abs(do), (r, dg, do)
+        for k in ("u", "v", "p"):
+            e = rel_l2(P.get(k), O.get(k))
+            assert e <= 1e-8, (r, k, e)
+
+
+def test_mixed_and_fp64_paths_agree_on_steps():
+    fp = clouds.kovasznay(30, dt=0.4)
+    A = rbffd.Problem(ctx(), fp, rbffd.PREC_FP64)
+    B = rbffd.Problem(ctx(), fp, rbffd.PREC_MIXED)
+    for _ in range(2):
+        A.time_step(fp.dt, 1e-4, max_outer=3)
+        B.time_step(fp.dt, 1e-4, max_outer=3)
+    for k in ("u", "v", "p"):
+        assert rel_l2(B.get(k), A.get(k)) <= 1e-8
