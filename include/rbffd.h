@@ -139,6 +139,29 @@ int rbffd_ctx_kernel_stat(const rbffd_ctx *ctx, int32_t which, rbffd_kernel_stat
 int rbffd_build_stencils(rbffd_ctx *ctx, int32_t n, const double *x, const double *y,
                          const int8_t *tag, int32_t q, int32_t *idx);
 
+/* Same result as rbffd_build_stencils, for callers that cannot allocate
+ * device memory once they are running: a loop that must keep a fixed device
+ * footprint, or an application whose other streams must not be stalled by
+ * the device synchronisation that cudaMalloc / cudaFree imply.  The paper
+ * has no counterpart: this is a property of the library, not of the method.
+ * It allocates nothing.  The cell-grid workspace comes from a fixed array of
+ * RBFFD_STATIC_SCRATCH_BYTES in device global memory inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   - n is limited to RBFFD_STATIC_MAX_POINTS; larger n returns RBFFD_EINVAL
+ *     with a message, before anything runs on the GPU.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (the call clears what it needs cleared).  Calls that overlap on the GPU
+ *     -- from two streams, or two contexts on one device -- race on it: issue
+ *     them on one stream or serialise them.
+ * Arguments, layout and other errors are those of rbffd_build_stencils. */
+#define RBFFD_STATIC_MAX_POINTS 262144
+#define RBFFD_STATIC_SCRATCH_BYTES (4u << 20)
+int rbffd_build_stencils_static(rbffd_ctx *ctx, int32_t n, const double *x, const double *y,
+                                const int8_t *tag, int32_t q, int32_t *idx);
+
 /* -------------------------------------------------- S2: operator weights */
 
 /* PHS-RBF-FD weights (paper Sec. 2, Eqs. RBF_interp .. RBF_interp_mat_vec_L_solve):

@@ -269,3 +269,72 @@ extern "C" int rbffd_build_stencils(rbffd_ctx *ctx, int32_t n, const double *x, 
   dev_free(ctx, ws, lay.bytes);
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Cloud building without any device allocation.
+//
+// rbffd_build_stencils above allocates its cell-grid workspace with
+// cudaMalloc on every call and frees it afterwards.  Some callers cannot do
+// that: a solver loop that must keep a fixed device-memory footprint once it
+// has started, or an application whose other streams must not be stalled by
+// the implicit device synchronisation of cudaMalloc / cudaFree.  For them,
+// rbffd_build_stencils_static takes the same workspace from a fixed array in
+// device global memory that is part of this library image.  Every GPU that
+// loads the library holds the array (RBFFD_STATIC_SCRATCH_BYTES) until the
+// process exits.
+
+namespace rbffd {
+
+static __device__ __align__(256) unsigned char g_knn_scratch[RBFFD_STATIC_SCRATCH_BYTES];
+
+// Device address of g_knn_scratch per device.  In host code the symbol is
+// only a host-side stand-in, so the address has to be asked of the runtime,
+// once per device, with that device current.
+static void *g_knn_scratch_ptr[64] = {nullptr};
+
+static int static_scratch(int device, void **out) {
+  if (device < 0 || device >= 64) {
+    set_error("rbffd_build_stencils_static: device %d not supported", device);
+    return RBFFD_EINVAL;
+  }
+  if (!g_knn_scratch_ptr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_knn_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      set_error("cudaGetSymbolAddress(static cloud scratch) failed: %s", cudaGetErrorString(e));
+      return RBFFD_ECUDA;
+    }
+    g_knn_scratch_ptr[device] = p;
+  }
+  *out = g_knn_scratch_ptr[device];
+  return RBFFD_OK;
+}
+
+}  // namespace rbffd
+
+extern "C" int rbffd_build_stencils_static(rbffd_ctx *ctx, int32_t n, const double *x,
+                                           const double *y, const int8_t *tag, int32_t q,
+                                           int32_t *idx) {
+  if (!ctx || !x || !y || !idx || n < 1 || q < 1 || q > n || q > 129) {
+    set_error("rbffd_build_stencils_static: bad arguments (n=%d q=%d)", n, q);
+    return RBFFD_EINVAL;
+  }
+  if (n > RBFFD_STATIC_MAX_POINTS) {
+    set_error("rbffd_build_stencils_static: n=%d exceeds the static limit of %d points", n,
+              RBFFD_STATIC_MAX_POINTS);
+    return RBFFD_EINVAL;
+  }
+  KnnLayout lay;
+  knn_workspace_bytes(n, &lay);
+  if (lay.bytes > sizeof(g_knn_scratch)) {
+    set_error("rbffd_build_stencils_static: workspace of %zu bytes exceeds the %zu-byte array",
+              lay.bytes, sizeof(g_knn_scratch));
+    return RBFFD_EINVAL;
+  }
+  RBFFD_CK(cudaSetDevice(ctx->device));
+  void *ws = nullptr;
+  RBFFD_TRY(static_scratch(ctx->device, &ws));
+  // knn_run clears the counters, cursors and error word it reads before
+  // writing them, so the contents left by an earlier call do not matter.
+  return knn_run(ctx, ws, lay, n, x, y, tag, q, idx);
+}

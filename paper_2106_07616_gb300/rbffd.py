@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
         "rbffd_ctx_profile": (C.c_int, [vp, C.c_int]),
         "rbffd_ctx_kernel_stat": (C.c_int, [vp, i32, C.POINTER(KernelStat)]),
         "rbffd_build_stencils": (C.c_int, [vp, i32, vp, vp, vp, i32, vp]),
+        "rbffd_build_stencils_static": (C.c_int, [vp, i32, vp, vp, vp, i32, vp]),
         "rbffd_weights": (C.c_int, [vp, i32, vp, vp, i32, vp, i32, vp, vp, vp,
                                     C.POINTER(i32)]),
         "rbffd_problem_create": (C.c_int, [vp, C.POINTER(ProblemDesc), C.POINTER(vp)]),
@@ -175,6 +176,17 @@ def rbffd_build_stencils(ctx, x, y, tag, q, idx):
     n = int(x.shape[0])
     _check(load().rbffd_build_stencils(ctx.h, n, ptr(x), ptr(y), ptr(tag), int(q), ptr(idx)),
            "rbffd_build_stencils")
+
+
+STATIC_MAX_POINTS = 262144
+
+
+def rbffd_build_stencils_static(ctx, x, y, tag, q, idx):
+    """rbffd_build_stencils without any device allocation (fixed workspace
+    inside the library; n <= STATIC_MAX_POINTS; overlapping calls race)."""
+    n = int(x.shape[0])
+    _check(load().rbffd_build_stencils_static(ctx.h, n, ptr(x), ptr(y), ptr(tag), int(q),
+                                              ptr(idx)), "rbffd_build_stencils_static")
 
 
 def rbffd_weights(ctx, x, y, q, idx, degree, wx, wy, wl):
