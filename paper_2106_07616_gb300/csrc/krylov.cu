@@ -56,7 +56,7 @@ struct KScalars {
 // solve it is simply unused.  rho' equals (r^, r) in exact arithmetic.
 template <int NR, int NT>
 __global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
-  __shared__ double sred[5 * NR * (NT / 32)];  // block_partials of up to 5 NR values
+  __shared__ double sred[5 * NR * NT];  // block_partials of up to 5 NR values
   __shared__ double stot[16];
   __shared__ KScalars ks[NR];
   __shared__ int s_flags[2];

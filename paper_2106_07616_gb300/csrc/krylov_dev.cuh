@@ -73,26 +73,30 @@ __device__ __forceinline__ void spmv_rows(int n, int q, int ldn, int T,
 }
 
 // Block-reduce V values per thread into V partials written at outs[v][b].
+// The values go through shared memory (sh holds V * NT entries) and warp v
+// sums value v over the block in a fixed order: NT/32 + 5 dependent adds on
+// one warp, instead of 5 butterfly levels on every warp.  On GB300 an FP64
+// warp-wide add occupies the FP64 pipe for ~32 cycles, so the number of
+// FP64 warp instructions, not their latency, is what a reduction costs.
 template <int NT, int V, typename AT>
 __device__ __forceinline__ void block_partials(AT (&val)[V], AT *sh, AT *const *outs) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    AT t = wsum(val[v]);
-    if (l == 0) sh[v * (NT / 32) + w] = t;
-  }
+  for (int v = 0; v < V; ++v) sh[v * NT + threadIdx.x] = val[v];
   __syncthreads();
   if (w < V) {
-    AT t = (l < NT / 32) ? sh[w * (NT / 32) + l] : AT(0);
+    AT t = AT(0);
+#pragma unroll 8
+    for (int k = 0; k < NT / 32; ++k) t += sh[w * NT + k * 32 + l];
     t = wsum(t);
     if (l == 0 && outs[w] != nullptr) outs[w][blockIdx.x] = t;
   }
 }
 
 // Grid-wide exchange: publish this block's writes (rows and partials) with
-// a release store of flags[b] = epoch, wait (acquire, bounded) until every
-// block has published epoch, then reduce the V partial arrays in a fixed
-// order, one warp per array.  Every block computes bit-identical totals.
+// a release store of flags[b] = epoch, wait (acquire loads, bounded) until
+// every block has published epoch, then reduce the V partial arrays in a
+// fixed order, one warp per array.  Every block computes bit-identical totals.
 // V = 0 is a plain barrier.
 template <int V, typename AT>
 __device__ __forceinline__ bool exchange(unsigned int *flags, int *err, unsigned int epoch,

@@ -34,8 +34,8 @@ struct IRS {
 
 template <int NR, int NT>
 __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
-  __shared__ float sr32[5 * NR * (NT / 32)];
-  __shared__ double sr64[2 * NR * (NT / 32)];
+  __shared__ float sr32[5 * NR * NT];
+  __shared__ double sr64[2 * NR * NT];
   __shared__ float st32[16];
   __shared__ double st64[16];
   __shared__ IRS ks[NR];
