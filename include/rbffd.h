@@ -66,10 +66,15 @@ enum {
   RBFFD_FIELD_UBC = 10, RBFFD_FIELD_VBC = 11                  /* prescribed boundary velocity */
 };
 
-/* Arithmetic of the Krylov solves. */
+/* Arithmetic of the Krylov solves.  Every mode stops on the same FP64
+ * relative residual (krylov_tol); the mixed modes run their inner iterations
+ * on the FP32 pipe and correct in FP64 (defect correction). */
 enum {
-  RBFFD_PREC_FP64 = 0,  /* FP64 operators and Krylov vectors throughout */
-  RBFFD_PREC_MIXED = 1  /* FP32 matrices/Krylov inside FP64 defect correction */
+  RBFFD_PREC_FP64 = 0,     /* FP64 operators and Krylov vectors throughout */
+  RBFFD_PREC_MIXED = 1,    /* FP32 inner BiCGSTAB inside FP64 defect correction;
+                              converges while cond(A) * 6e-8 < 1 */
+  RBFFD_PREC_MIXED_FF = 2  /* float-float (FP32 pairs, ~1e-14) inner BiCGSTAB inside
+                              FP64 defect correction */
 };
 
 typedef struct rbffd_ctx rbffd_ctx;
@@ -102,8 +107,9 @@ int64_t rbffd_ctx_launch_count(const rbffd_ctx *ctx);
  *   KNN         unit = one point; bytes = 24 (coordinates in, q indices out)
  *   OUTER       one outer iteration (whole simple_iterate, GPU time)
  * s_w, s_i, s_v: bytes of a matrix value, a column index, a vector entry
- * (8, 4, 8 in the FP64 path; 4, 4, 4 for the FP32 inner iterations of the
- * mixed path, whose few FP64 residual sweeps are not counted as units).
+ * (8, 4, 8 in the FP64 path and for the 8-byte float-float inner values;
+ * 4, 4, 4 for the FP32 inner iterations; the few FP64 residual sweeps of
+ * the mixed paths are not counted as units).
  * rbffd_ctx_profile(ctx, 1) resets the counters and enables timing; 0 stops. */
 enum {
   RBFFD_KSTAT_KRYLOV_P = 0,

@@ -35,37 +35,43 @@ struct KrylovArgs {
   int tpr;              // threads per row in the SpMV phases (1, 2, 4 or 8)
 };
 
-// FP32 vectors of the mixed-precision solve (d = the sweep's correction).
+// Inner arithmetic of the mixed-precision solve.
+enum { INNER_F32 = 0, INNER_FF = 1 };
+
+// Vectors of the mixed-precision solve, in the inner arithmetic's storage
+// type (float for INNER_F32, a float pair for INNER_FF); d = the sweep's
+// correction.
 struct MixedVecs {
-  float *r, *rh, *p, *v, *ph, *s, *sh, *t, *d;
+  void *r, *rh, *p0, *p1, *v0, *v1, *s, *t, *d;  // p, v double-buffered
 };
 
 struct MixedArgs {
   int n, q, ldn, tpr;
+  int inner;             // INNER_F32 or INNER_FF
   const int32_t *col;
   const double *val64;   // FP64 operator (residuals)
-  const float *val32;    // FP32 copy (inner iterations)
-  const float *dinv32;   // FP32 1 / diagonal
+  const void *valin;     // operator in the inner arithmetic
+  const void *dinvin;    // 1 / diagonal in the inner arithmetic
   const double *b[2];
   double *x[2];
   MixedVecs w[2];
   double *part64;        // krylov_ir_partials64(nr, nblocks)
-  float *part32;         // krylov_ir_partials32(nr, nblocks)
+  void *partin;          // krylov_ir_partials_inner_bytes(nr, nblocks, inner)
   GridBarrier *bar;
   unsigned int *flags;
   KrylovOut *out;        // iters = inner iterations, restarts = sweeps
   double tol;            // FP64 relative residual to reach
   int maxit;             // cap on inner iterations over all sweeps
-  double inner_tol;      // relative reduction asked of each FP32 solve
+  double inner_tol;      // relative reduction asked of each inner solve
   int inner_maxit;       // cap on inner iterations per sweep
   int max_sweeps;
 };
 
 int krylov_max_blocks(rbffd_ctx *ctx, int nr);
-int krylov_ir_max_blocks(rbffd_ctx *ctx, int nr);
+int krylov_ir_max_blocks(rbffd_ctx *ctx, int nr, int inner);
 int krylov_ir_launch(rbffd_ctx *ctx, int nr, int nblocks, const MixedArgs &args);
 size_t krylov_ir_partials64(int nr, int nblocks);
-size_t krylov_ir_partials32(int nr, int nblocks);
+size_t krylov_ir_partials_inner_bytes(int nr, int nblocks, int inner);
 int krylov_blocks_for(rbffd_ctx *ctx, int n, int nr);
 int krylov_threads_per_row(int n, int nr, int nblocks);
 int krylov_launch(rbffd_ctx *ctx, int nr, int nblocks, const KrylovArgs &args);

@@ -3,6 +3,7 @@
 // grid-wide publish/wait/reduce exchange.
 #pragma once
 #include "common.cuh"
+#include "inner_arith.cuh"
 
 namespace rbffd {
 namespace kdev {
@@ -16,6 +17,21 @@ __device__ __forceinline__ T wsum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+__device__ __forceinline__ ff wsum(ff v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = ff_add(v, ff(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)));
+  return v;
+}
+
+// coherent (L2) loads of the partial-sum types
+__device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ ff ld_cg(const ff *p) {
+  const float2 t = __ldcg(reinterpret_cast<const float2 *>(p));
+  return ff(t.x, t.y);
 }
 
 // y_k(i) = sum_j A(i,j) x_k(j), accumulated in AT, T threads per row
@@ -140,7 +156,7 @@ __device__ __forceinline__ bool exchange(unsigned int *flags, int *err, unsigned
 #pragma unroll
       for (int u = 0; u < BPL; ++u) {
         const int b = l + 32 * u;
-        if (b < nb) t += __ldcg(arrs[w] + b);
+        if (b < nb) t += ld_cg(arrs[w] + b);
       }
     }
     t = wsum(t);

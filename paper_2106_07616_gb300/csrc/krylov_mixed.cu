@@ -5,10 +5,13 @@
 // A sweep computes the FP64 residual r = b - A x with the FP64 operator,
 // stops when |r| <= tol |b| (the same test as the FP64 solver, so both
 // paths stop at the same FP64 accuracy), and otherwise solves A d = r to a
-// loose relative tolerance with BiCGSTAB on FP32 copies of the operator and
-// Jacobi diagonal, FP32 vectors and FP32 dot products, then x += d in FP64.
-// The refinement converges while cond(A) * eps_fp32 < 1; each sweep gains
-// about -log10(max(inner_tol, cond * eps_fp32)) digits.
+// looser relative tolerance with BiCGSTAB on a copy of the operator and
+// Jacobi diagonal held in the inner arithmetic (inner_arith.cuh), then
+// x += d in FP64.  The refinement converges while cond(A) * eps_inner < 1;
+// each sweep gains about -log10(max(inner_tol, cond * eps_inner)) digits.
+//   ArithF32: eps 6e-8 -- enough for well-conditioned systems (momentum);
+//   ArithFF:  float-float, eps ~1e-14 -- converges like FP64 on the
+//             pressure-correction systems too.
 //
 // Why on GB300: the FP64 pipe issues 2 lanes per clock per SM against 128
 // for FP32, so FP64 SpMV and reductions are ALU-bound there; the inner
@@ -16,6 +19,7 @@
 // and move half the bytes.
 #include "common.cuh"
 #include "krylov.cuh"
+#include "inner_arith.cuh"
 #include "krylov_dev.cuh"
 
 namespace rbffd {
@@ -32,11 +36,127 @@ struct IRS {
 
 }  // namespace
 
-template <int NR, int NT>
+// y_k(i) = sum_j A(i,j) x_k(j) in the inner arithmetic IA, T threads per
+// row; the same batching and group sums as kdev::spmv_rows.
+template <int NR, class IA, typename F>
+__device__ __forceinline__ void spmv_rows_ia(int n, int q, int ldn, int T,
+                                             const int32_t *__restrict__ col,
+                                             const typename IA::S *__restrict__ val,
+                                             typename IA::S *const *xs, int wglobal, int nwarps,
+                                             F &&f) {
+  using S = typename IA::S;
+  using AC = typename IA::A;
+  constexpr int CH = kdev::CH;
+  const int lane = threadIdx.x & 31;
+  const int gpw = 32 / T;
+  const int g = lane / T;
+  const int lg = lane - g * T;
+  const bool active = g < gpw;
+  for (int base = wglobal * gpw; base < n; base += nwarps * gpw) {
+    const int i = base + g;
+    const bool valid = active && i < n;
+    AC s[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) s[k] = IA::zero();
+    if (valid) {
+      for (int j0 = lg; j0 < q; j0 += CH * T) {
+        int c[CH];
+        S a[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          const int j = j0 + u * T;
+          const int64_t e = (int64_t)j * ldn + i;
+          c[u] = j < q ? __ldg(col + e) : -1;
+          a[u] = j < q ? IA::ldg(val + e) : IA::szero();
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          if (c[u] >= 0) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k) IA::madd(s[k], a[u], IA::ldcg(xs[k] + c[u]));
+          }
+        }
+      }
+    }
+    AC tot[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) tot[k] = s[k];
+    for (int u = 1; u < T; ++u) {
+#pragma unroll
+      for (int k = 0; k < NR; ++k) tot[k] = IA::add(tot[k], IA::shfl(s[k], (lane + u) & 31));
+    }
+    if (valid && lg == 0) f(i, tot);
+  }
+}
+
+// y_k(i) = sum_j A(i,j) g(k, j) where the operand g is formed on the fly
+// from several gathered vectors (the "fused" SpMVs below).  Same thread
+// layout as spmv_rows_ia; g runs once per stored entry.
+template <int NR, class IA, typename G, typename F>
+__device__ __forceinline__ void spmv_rows_gen(int n, int q, int ldn, int T,
+                                              const int32_t *__restrict__ col,
+                                              const typename IA::S *__restrict__ val, G &&g,
+                                              int wglobal, int nwarps, F &&f) {
+  using S = typename IA::S;
+  using AC = typename IA::A;
+  constexpr int CH = kdev::CH;
+  const int lane = threadIdx.x & 31;
+  const int gpw = 32 / T;
+  const int gi = lane / T;
+  const int lg = lane - gi * T;
+  const bool active = gi < gpw;
+  for (int base = wglobal * gpw; base < n; base += nwarps * gpw) {
+    const int i = base + gi;
+    const bool valid = active && i < n;
+    AC s[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) s[k] = IA::zero();
+    if (valid) {
+      for (int j0 = lg; j0 < q; j0 += CH * T) {
+        int c[CH];
+        S a[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          const int j = j0 + u * T;
+          const int64_t e = (int64_t)j * ldn + i;
+          c[u] = j < q ? __ldg(col + e) : -1;
+          a[u] = j < q ? IA::ldg(val + e) : IA::szero();
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          if (c[u] >= 0) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k) IA::madd(s[k], a[u], g(k, c[u]));
+          }
+        }
+      }
+    }
+    AC tot[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) tot[k] = s[k];
+    for (int u = 1; u < T; ++u) {
+#pragma unroll
+      for (int k = 0; k < NR; ++k) tot[k] = IA::add(tot[k], IA::shfl(s[k], (lane + u) & 31));
+    }
+    if (valid && lg == 0) f(i, tot);
+  }
+}
+
+template <int NR, int NT, class IA>
 __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
-  __shared__ float sr32[5 * NR * NT];
-  __shared__ double sr64[2 * NR * NT];
-  __shared__ float st32[16];
+  using S = typename IA::S;
+  using AC = typename IA::A;
+  using PT = typename IA::P;
+  using CF = typename IA::C;
+  // block-partial staging for the inner sums (5 NR values) and the FP64
+  // residual sums (2 NR values); never live at the same time
+  constexpr size_t SB = (5 * NR * NT * sizeof(PT) > 2 * NR * NT * sizeof(double))
+                            ? 5 * NR * NT * sizeof(PT)
+                            : 2 * NR * NT * sizeof(double);
+  __shared__ __align__(16) unsigned char sbuf[SB];
+  PT *sr32 = reinterpret_cast<PT *>(sbuf);
+  double *sr64 = reinterpret_cast<double *>(sbuf);
+  __shared__ PT st32[16];
   __shared__ double st64[16];
   __shared__ IRS ks[NR];
   __shared__ int s_any;
@@ -48,8 +168,26 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
   unsigned int epoch = 1;
   const bool leader = threadIdx.x == 0;
   int *err = &A.bar->err;
+  const S *val = reinterpret_cast<const S *>(A.valin);
+  const S *dinv = reinterpret_cast<const S *>(A.dinvin);
+  // p and v are double-buffered: an iteration reads the previous direction
+  // of its neighbours while it writes its own new one
+  S *r[NR], *rh[NR], *pb[2][NR], *vb[2][NR], *sv[NR], *t[NR], *d[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    r[k] = (S *)A.w[k].r;
+    rh[k] = (S *)A.w[k].rh;
+    pb[0][k] = (S *)A.w[k].p0;
+    pb[1][k] = (S *)A.w[k].p1;
+    vb[0][k] = (S *)A.w[k].v0;
+    vb[1][k] = (S *)A.w[k].v1;
+    sv[k] = (S *)A.w[k].s;
+    t[k] = (S *)A.w[k].t;
+    d[k] = (S *)A.w[k].d;
+  }
+  PT *part32 = reinterpret_cast<PT *>(A.partin);
   auto P64 = [&](int slot, int k) { return A.part64 + (size_t)(slot * NR + k) * nb; };
-  auto P32 = [&](int slot, int k) { return A.part32 + (size_t)(slot * NR + k) * nb; };
+  auto P32 = [&](int slot, int k) { return part32 + (size_t)(slot * NR + k) * nb; };
 
   if (leader) {
 #pragma unroll
@@ -66,7 +204,7 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
   bool ok = true;
 
   for (;;) {
-    // ---------------- R: FP64 residual, r32 = r, r^ = r, p = r, p^ = r/d, d = 0
+    // ---------------- R: FP64 residual, then r = r^ = p = residual, p^ = r/d, d = 0
     bool part[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) part[k] = ks[k].state == KRY_RUNNING;
@@ -77,18 +215,22 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
       for (int k = 0; k < 2 * NR; ++k) acc[k] = 0.0;
       kdev::spmv_rows<NR, double>(n, q, ldn, T, A.col, A.val64, A.x, wglobal, nwarps,
                                   [&](int i, const double *ax) {
-                                    const float di = __ldg(A.dinv32 + i);
+                                    const S di = IA::ldg(dinv + i);
 #pragma unroll
                                     for (int k = 0; k < NR; ++k) {
                                       if (!part[k]) continue;
                                       const double bi = A.b[k][i];
                                       const double ri = bi - ax[k];
-                                      const float rf = (float)ri;
-                                      A.w[k].r[i] = rf;
-                                      A.w[k].rh[i] = rf;
-                                      A.w[k].p[i] = rf;
-                                      A.w[k].ph[i] = rf * di;
-                                      A.w[k].d[i] = 0.0f;
+                                      const S rf = IA::from_double(ri);
+                                      (void)di;
+                                      // the first inner iteration forms
+                                      // r = s - 0 t and p = r + 0 (p - 0 v)
+                                      sv[k][i] = rf;
+                                      rh[k][i] = rf;
+                                      t[k][i] = IA::szero();
+                                      pb[0][k][i] = IA::szero();
+                                      vb[0][k][i] = IA::szero();
+                                      d[k][i] = IA::szero();
                                       acc[2 * k] += bi * bi;
                                       acc[2 * k + 1] += ri * ri;
                                     }
@@ -128,6 +270,8 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
           c.inner_it = 0;
           c.rho = rr;
           c.r0 = sqrt(rr);
+          c.alpha = c.omega = c.beta = 0.0;
+          c.half = 0;
           any = 1;
         }
         s_any = any;
@@ -141,7 +285,19 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
       if (!s_any) break;
     }
 
-    // ---------------- inner FP32 BiCGSTAB on A d = r
+    // ---------------- inner BiCGSTAB on A d = r in the inner arithmetic,
+    // two grid exchanges per iteration:
+    //   A: with alpha, omega of the previous iteration and the new beta,
+    //      each row forms r = s - omega t, advances d by alpha p^ + omega s^,
+    //      forms p = r + beta (p - omega v), and the SpMV builds
+    //      p^_j = d_j (s_j - omega t_j + beta (p_j - omega v_j)) on the fly
+    //      from its neighbours' previous vectors: v = A p^; partials (r^,v), (r,r)
+    //   C: s = r - alpha v; t = A s^ with s^_j = d_j (r_j - alpha v_j) formed
+    //      on the fly; partials (s,s) (t,t) (t,s) (r^,s) (r^,t) give omega,
+    //      rho' = (r^,s) - omega (r^,t) and beta.
+    // On the FP32 pipe the extra operand arithmetic is cheap; what it saves
+    // is two of the four grid-wide round trips of the textbook order.
+    int pv = 0;  // buffer holding the previous p and v
     for (;;) {
       bool run[NR], anyrun = false;
 #pragma unroll
@@ -151,100 +307,131 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
       }
       __syncthreads();
       if (!anyrun) break;
+      const int cu = pv ^ 1;
 
-      // A: v = A p^, partial (r^, v)
+      // A
       {
-        float acc[NR];
+        CF alp[NR], omg[NR], nomg[NR], bet[NR];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) acc[k] = 0.f;
-        float *phs[NR];
+        for (int k = 0; k < NR; ++k) {
+          alp[k] = IA::coef(ks[k].alpha);
+          omg[k] = IA::coef(ks[k].omega);
+          nomg[k] = IA::coef(-ks[k].omega);
+          bet[k] = IA::coef(ks[k].beta);
+        }
+        AC acc[2 * NR];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) phs[k] = A.w[k].ph;
-        kdev::spmv_rows<NR, float>(n, q, ldn, T, A.col, A.val32, phs, wglobal, nwarps,
-                                   [&](int i, const float *av) {
+        for (int k = 0; k < 2 * NR; ++k) acc[k] = IA::zero();
+        auto g = [&](int k, int j) {
+          const S rj = IA::axpy(IA::ldcg(sv[k] + j), nomg[k], IA::ldcg(t[k] + j));
+          const S qj = IA::axpy(IA::ldcg(pb[pv][k] + j), nomg[k], IA::ldcg(vb[pv][k] + j));
+          return IA::mul(IA::axpy(rj, bet[k], qj), IA::ldg(dinv + j));
+        };
+        spmv_rows_gen<NR, IA>(n, q, ldn, T, A.col, val, g, wglobal, nwarps,
+                              [&](int i, const AC *av) {
+                                const S di = IA::ldg(dinv + i);
 #pragma unroll
-                                     for (int k = 0; k < NR; ++k) {
-                                       if (!run[k]) continue;
-                                       A.w[k].v[i] = av[k];
-                                       acc[k] += A.w[k].rh[i] * av[k];
-                                     }
-                                   });
-        float *outs[NR];
+                                for (int k = 0; k < NR; ++k) {
+                                  if (!run[k]) continue;
+                                  const S si = sv[k][i], ti = t[k][i];
+                                  const S pi = pb[pv][k][i], vi = vb[pv][k][i];
+                                  const S ri = IA::axpy(si, nomg[k], ti);
+                                  r[k][i] = ri;
+                                  d[k][i] = IA::axpy(IA::axpy(d[k][i], alp[k], IA::mul(pi, di)),
+                                                     omg[k], IA::mul(si, di));
+                                  pb[cu][k][i] = IA::axpy(ri, bet[k], IA::axpy(pi, nomg[k], vi));
+                                  const S vn = IA::from_acc(av[k]);
+                                  vb[cu][k][i] = vn;
+                                  IA::madd(acc[2 * k], rh[k][i], vn);
+                                  IA::madd(acc[2 * k + 1], ri, ri);
+                                }
+                              });
+        PT pa[2 * NR];
+        PT *outs[2 * NR];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) outs[k] = run[k] ? P32(F_RHV, k) : nullptr;
-        kdev::block_partials<NT, NR>(acc, sr32, outs);
-        float tot[NR];
-        ok = kdev::exchange<NR>(A.flags, err, epoch++, outs, tot, st32);
+        for (int k = 0; k < NR; ++k) {
+          pa[2 * k] = IA::part(acc[2 * k]);
+          pa[2 * k + 1] = IA::part(acc[2 * k + 1]);
+          outs[2 * k] = run[k] ? P32(F_RHV, k) : nullptr;
+          outs[2 * k + 1] = run[k] ? P32(F_RR, k) : nullptr;
+        }
+        kdev::block_partials<NT, 2 * NR>(pa, sr32, outs);
+        PT tot[2 * NR];
+        ok = kdev::exchange<2 * NR>(A.flags, err, epoch++, outs, tot, st32);
         if (!ok) break;
         if (leader) {
 #pragma unroll
           for (int k = 0; k < NR; ++k) {
+            IRS &c = ks[k];
             if (!run[k]) continue;
-            const double al = ks[k].rho / (double)tot[k];
-            // a (near) breakdown of the FP32 recurrence ends the sweep with
-            // the correction accumulated so far; FP64 refinement goes on
-            if (!isfinite(al) || fabs(al) > 1e30) {
-              ks[k].inner = 0;
+            const double rn = sqrt(IA::pd(tot[2 * k + 1]));
+            // d now holds every step up to the previous iteration
+            if (!isfinite(rn) || (c.inner_it > 0 && rn <= A.inner_tol * c.r0) ||
+                rn > 1e3 * c.r0 || c.inner_it >= A.inner_maxit || c.it >= A.maxit) {
+              c.inner = 0;
               continue;
             }
-            ks[k].alpha = al;
+            const double al = c.rho / IA::pd(tot[2 * k]);
+            if (!isfinite(al) || fabs(al) > 1e30) {
+              c.inner = 0;  // breakdown: keep the correction so far
+              continue;
+            }
+            c.alpha = al;
           }
         }
         __syncthreads();
+        pv = cu;
 #pragma unroll
         for (int k = 0; k < NR; ++k) run[k] = ks[k].inner != 0;
       }
-      // B: s = r - alpha v, s^ = s / d
+      bool anyc = false;
+#pragma unroll
+      for (int k = 0; k < NR; ++k) anyc |= run[k];
+      if (!anyc) continue;
+
+      // C
       {
-        float alp[NR];
+        CF nalp[NR];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) alp[k] = (float)ks[k].alpha;
-        for (int i = tid; i < n; i += stride) {
-          const float di = __ldg(A.dinv32 + i);
+        for (int k = 0; k < NR; ++k) nalp[k] = IA::coef(-ks[k].alpha);
+        AC acc[5 * NR];
 #pragma unroll
-          for (int k = 0; k < NR; ++k) {
-            if (!run[k]) continue;
-            const float si = A.w[k].r[i] - alp[k] * A.w[k].v[i];
-            A.w[k].s[i] = si;
-            A.w[k].sh[i] = si * di;
-          }
-        }
-        ok = kdev::exchange<0, float>(A.flags, err, epoch++, nullptr, nullptr, st32);
-        if (!ok) break;
-      }
-      // C: t = A s^, partials (s,s) (t,t) (t,s) (r^,s) (r^,t)
-      {
-        float acc[5 * NR];
+        for (int k = 0; k < 5 * NR; ++k) acc[k] = IA::zero();
+        auto g = [&](int k, int j) {
+          return IA::mul(IA::axpy(IA::ldcg(r[k] + j), nalp[k], IA::ldcg(vb[pv][k] + j)),
+                         IA::ldg(dinv + j));
+        };
+        spmv_rows_gen<NR, IA>(n, q, ldn, T, A.col, val, g, wglobal, nwarps,
+                              [&](int i, const AC *at) {
 #pragma unroll
-        for (int k = 0; k < 5 * NR; ++k) acc[k] = 0.f;
-        float *shs[NR];
-#pragma unroll
-        for (int k = 0; k < NR; ++k) shs[k] = A.w[k].sh;
-        kdev::spmv_rows<NR, float>(n, q, ldn, T, A.col, A.val32, shs, wglobal, nwarps,
-                                   [&](int i, const float *at) {
-#pragma unroll
-                                     for (int k = 0; k < NR; ++k) {
-                                       if (!run[k]) continue;
-                                       const float si = A.w[k].s[i], rhi = A.w[k].rh[i];
-                                       A.w[k].t[i] = at[k];
-                                       acc[5 * k + 0] += si * si;
-                                       acc[5 * k + 1] += at[k] * at[k];
-                                       acc[5 * k + 2] += at[k] * si;
-                                       acc[5 * k + 3] += rhi * si;
-                                       acc[5 * k + 4] += rhi * at[k];
-                                     }
-                                   });
-        float *outs[5 * NR];
+                                for (int k = 0; k < NR; ++k) {
+                                  if (!run[k]) continue;
+                                  const S si = IA::axpy(r[k][i], nalp[k], vb[pv][k][i]);
+                                  sv[k][i] = si;
+                                  const S ti = IA::from_acc(at[k]);
+                                  t[k][i] = ti;
+                                  const S rhi = rh[k][i];
+                                  IA::madd(acc[5 * k + 0], si, si);
+                                  IA::madd(acc[5 * k + 1], ti, ti);
+                                  IA::madd(acc[5 * k + 2], ti, si);
+                                  IA::madd(acc[5 * k + 3], rhi, si);
+                                  IA::madd(acc[5 * k + 4], rhi, ti);
+                                }
+                              });
+        PT pa[5 * NR];
+        PT *outs[5 * NR];
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
+#pragma unroll
+          for (int j = 0; j < 5; ++j) pa[5 * k + j] = IA::part(acc[5 * k + j]);
           outs[5 * k + 0] = run[k] ? P32(F_SS, k) : nullptr;
           outs[5 * k + 1] = run[k] ? P32(F_TT, k) : nullptr;
           outs[5 * k + 2] = run[k] ? P32(F_TS, k) : nullptr;
           outs[5 * k + 3] = run[k] ? P32(F_RHS, k) : nullptr;
           outs[5 * k + 4] = run[k] ? P32(F_RHT, k) : nullptr;
         }
-        kdev::block_partials<NT, 5 * NR>(acc, sr32, outs);
-        float tot[5 * NR];
+        kdev::block_partials<NT, 5 * NR>(pa, sr32, outs);
+        PT tot[5 * NR];
         ok = kdev::exchange<5 * NR>(A.flags, err, epoch++, outs, tot, st32);
         if (!ok) break;
         if (leader) {
@@ -253,108 +440,74 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
             IRS &c = ks[k];
             c.half = 0;
             if (!run[k]) continue;
-            const double ss = tot[5 * k + 0], tt = tot[5 * k + 1], ts = tot[5 * k + 2];
-            const double rhs = tot[5 * k + 3], rht = tot[5 * k + 4];
+            const double ss = IA::pd(tot[5 * k + 0]), tt = IA::pd(tot[5 * k + 1]);
+            const double ts = IA::pd(tot[5 * k + 2]);
+            const double rhs = IA::pd(tot[5 * k + 3]), rht = IA::pd(tot[5 * k + 4]);
             c.it++;
             c.inner_it++;
             c.snorm = sqrt(ss);
-            if (!isfinite(c.snorm) || !isfinite(tt) || !isfinite(ts) || c.snorm > 1e3 * c.r0) {
-              // the FP32 recurrence went astray: end the sweep, keep d
+            const double om = tt == 0.0 ? 0.0 : ts / tt;
+            const double rho_new = rhs - om * rht;
+            const double be = (om == 0.0 || c.rho == 0.0) ? 0.0 : (rho_new / c.rho) * (c.alpha / om);
+            if (!isfinite(c.snorm) || c.snorm > 1e3 * c.r0 || c.snorm <= A.inner_tol * c.r0 ||
+                !isfinite(om) || !isfinite(be) || fabs(be) > 1e30 || om == 0.0 ||
+                rho_new == 0.0) {
+              // stop after the half step d += alpha p^ (valid whenever alpha
+              // is finite); a non-finite s drops the step altogether
+              c.half = isfinite(c.snorm) && c.snorm <= 1e3 * c.r0 ? 1 : 2;
               c.inner = 0;
               continue;
             }
-            if (c.snorm <= A.inner_tol * c.r0) {
-              c.half = 1;
-              continue;
-            }
-            c.omega = tt == 0.0 ? 0.0 : ts / tt;
-            const double rho_new = rhs - c.omega * rht;
-            double be = (c.omega == 0.0 || c.rho == 0.0)
-                            ? 0.0
-                            : (rho_new / c.rho) * (c.alpha / c.omega);
-            if (!isfinite(be) || !isfinite(rho_new) || fabs(be) > 1e30) {
-              // apply this step's update, then end the sweep
-              be = 0.0;
-              c.omega = isfinite(c.omega) ? c.omega : 0.0;
-              c.half = 2;
-            }
+            c.omega = om;
             c.beta = be;
             c.rho = rho_new;
           }
         }
         __syncthreads();
-      }
-      // D: d += alpha p^ + omega s^, r = s - omega t, next direction, partial (r, r)
-      {
-        bool half[NR];
-        float alp[NR], omg[NR], bet[NR];
+        // half step of the iterations that stopped here
+        bool fin[NR], anyfin = false;
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-          run[k] = ks[k].inner != 0;
-          half[k] = ks[k].half == 1;
-          alp[k] = (float)ks[k].alpha;
-          omg[k] = (float)ks[k].omega;
-          bet[k] = (float)ks[k].beta;
+          fin[k] = run[k] && ks[k].half == 1;
+          anyfin |= fin[k];
         }
-        float acc[NR];
+        if (anyfin) {
+          CF alp[NR];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) acc[k] = 0.f;
-        for (int i = tid; i < n; i += stride) {
-          const float di = __ldg(A.dinv32 + i);
+          for (int k = 0; k < NR; ++k) alp[k] = IA::coef(ks[k].alpha);
+          const int stride_g = (32 / T) * nwarps;
+          const int lane = threadIdx.x & 31, gi = lane / T, lg = lane - gi * T;
+          // the rows this thread owns are the ones its SpMV leader lane wrote
+          for (int base = wglobal * (32 / T); base < n; base += stride_g) {
+            const int i = base + gi;
+            if (gi < 32 / T && lg == 0 && i < n) {
+              const S di = IA::ldg(dinv + i);
 #pragma unroll
-          for (int k = 0; k < NR; ++k) {
-            if (!run[k]) continue;
-            const float phi = A.w[k].ph[i];
-            if (half[k]) {
-              A.w[k].d[i] += alp[k] * phi;
-            } else {
-              A.w[k].d[i] += alp[k] * phi + omg[k] * A.w[k].sh[i];
-              const float ri = A.w[k].s[i] - omg[k] * A.w[k].t[i];
-              A.w[k].r[i] = ri;
-              acc[k] += ri * ri;
-              const float pi = ri + bet[k] * (A.w[k].p[i] - omg[k] * A.w[k].v[i]);
-              A.w[k].p[i] = pi;
-              A.w[k].ph[i] = pi * di;
+              for (int k = 0; k < NR; ++k)
+                if (fin[k]) d[k][i] = IA::axpy(d[k][i], alp[k], IA::mul(pb[pv][k][i], di));
             }
           }
         }
-        float *outs[NR];
-#pragma unroll
-        for (int k = 0; k < NR; ++k) outs[k] = (run[k] && !half[k]) ? P32(F_RR, k) : nullptr;
-        kdev::block_partials<NT, NR>(acc, sr32, outs);
-        float tot[NR];
-        ok = kdev::exchange<NR>(A.flags, err, epoch++, outs, tot, st32);
-        if (!ok) break;
-        if (leader) {
-#pragma unroll
-          for (int k = 0; k < NR; ++k) {
-            IRS &c = ks[k];
-            if (!run[k]) continue;
-            if (half[k] || c.half == 2) {
-              c.inner = 0;
-              continue;
-            }
-            const double rn = sqrt((double)tot[k]);
-            if (!isfinite(rn) || rn <= A.inner_tol * c.r0 || rn > 1e3 * c.r0 ||
-                c.omega == 0.0 || c.rho == 0.0 || c.inner_it >= A.inner_maxit ||
-                c.it >= A.maxit)
-              c.inner = 0;  // end of this sweep (converged, breakdown or cap)
-          }
-        }
-        __syncthreads();
       }
     }
     if (!ok) break;
-    // ---------------- x += d (FP64)
+    // ---------------- x += d (FP64); every step that could make d non-finite
+    // ended the sweep before its update
     {
       bool upd[NR];
 #pragma unroll
       for (int k = 0; k < NR; ++k) upd[k] = ks[k].in_sweep != 0;
-      for (int i = tid; i < n; i += stride) {
+      {
+        // d of a row was written by its SpMV leader lane: update x there too
+        const int lane = threadIdx.x & 31, gi = lane / T, lg = lane - gi * T;
+        for (int base = wglobal * (32 / T); base < n; base += (32 / T) * nwarps) {
+          const int i = base + gi;
+          if (gi < 32 / T && lg == 0 && i < n) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k)
-          if (upd[k]) A.x[k][i] = A.x[k][i] + (double)A.w[k].d[i];  // d is finite: every
-          // step that could make it non-finite ended the sweep before its update
+            for (int k = 0; k < NR; ++k)
+              if (upd[k]) A.x[k][i] = A.x[k][i] + IA::to_double(d[k][i]);
+          }
+        }
       }
       if (leader) {
 #pragma unroll
@@ -380,37 +533,44 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
 namespace {
 constexpr int MT1 = 1024;
 constexpr int MT2 = 512;
-}  // namespace
 
-int krylov_ir_max_blocks(rbffd_ctx *ctx, int nr) {
+template <class IA>
+int max_blocks_ia(rbffd_ctx *ctx, int nr) {
   int per_sm = 0;
   cudaError_t e;
   if (nr == 1)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_ir<1, MT1>, MT1, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_ir<1, MT1, IA>, MT1, 0);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_ir<2, MT2>, MT2, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_ir<2, MT2, IA>, MT2, 0);
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return 0;
   }
   return per_sm * ctx->num_sms;
 }
+}  // namespace
+
+int krylov_ir_max_blocks(rbffd_ctx *ctx, int nr, int inner) {
+  return inner == INNER_FF ? max_blocks_ia<ArithFF>(ctx, nr) : max_blocks_ia<ArithF32>(ctx, nr);
+}
 
 int krylov_ir_launch(rbffd_ctx *ctx, int nr, int nblocks, const MixedArgs &args) {
-  if (nblocks < 1 || nblocks > kdev::MAXB || nblocks > krylov_ir_max_blocks(ctx, nr)) {
+  if (nblocks < 1 || nblocks > kdev::MAXB || nblocks > krylov_ir_max_blocks(ctx, nr, args.inner)) {
     set_error("krylov_ir_launch: %d blocks not co-resident", nblocks);
     return RBFFD_EINVAL;
   }
   RBFFD_CK(cudaMemsetAsync(args.bar, 0, sizeof(GridBarrier), ctx->stream));
   RBFFD_CK(cudaMemsetAsync(args.flags, 0, sizeof(unsigned int) * nblocks, ctx->stream));
   void *kargs[] = {(void *)&args};
-  cudaError_t e;
-  if (nr == 1)
-    e = cudaLaunchCooperativeKernel((const void *)k_bicgstab_ir<1, MT1>, dim3(nblocks), dim3(MT1),
-                                    kargs, 0, ctx->stream);
+  const void *fn;
+  const int nt = nr == 1 ? MT1 : MT2;
+  if (args.inner == INNER_FF)
+    fn = nr == 1 ? (const void *)k_bicgstab_ir<1, MT1, ArithFF>
+                 : (const void *)k_bicgstab_ir<2, MT2, ArithFF>;
   else
-    e = cudaLaunchCooperativeKernel((const void *)k_bicgstab_ir<2, MT2>, dim3(nblocks), dim3(MT2),
-                                    kargs, 0, ctx->stream);
+    fn = nr == 1 ? (const void *)k_bicgstab_ir<1, MT1, ArithF32>
+                 : (const void *)k_bicgstab_ir<2, MT2, ArithF32>;
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(nt), kargs, 0, ctx->stream);
   ctx->launches++;
   if (e != cudaSuccess) {
     set_error("cooperative launch of k_bicgstab_ir failed: %s", cudaGetErrorString(e));
@@ -420,6 +580,9 @@ int krylov_ir_launch(rbffd_ctx *ctx, int nr, int nblocks, const MixedArgs &args)
 }
 
 size_t krylov_ir_partials64(int nr, int nblocks) { return (size_t)M_COUNT64 * nr * nblocks; }
-size_t krylov_ir_partials32(int nr, int nblocks) { return (size_t)F_COUNT32 * nr * nblocks; }
+// bytes of the inner partials (double for float-float, float for FP32)
+size_t krylov_ir_partials_inner_bytes(int nr, int nblocks, int inner) {
+  return (size_t)F_COUNT32 * nr * nblocks * (inner == INNER_FF ? sizeof(double) : sizeof(float));
+}
 
 }  // namespace rbffd

@@ -22,8 +22,7 @@ __global__ void k_pack(int n, int q, int ldn, int pin, const int32_t *__restrict
                        const double *__restrict__ nx, const double *__restrict__ ny,
                        int32_t *__restrict__ col, double *__restrict__ Wx,
                        double *__restrict__ Wy, double *__restrict__ Wl,
-                       double *__restrict__ Pp, double *__restrict__ pdinv,
-                       float *__restrict__ Pp32, float *__restrict__ pdinv32) {
+                       double *__restrict__ Pp, double *__restrict__ pdinv) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ldn) return;
   if (i >= n) {  // padding rows: self-loops with zero weight, never read
@@ -31,10 +30,8 @@ __global__ void k_pack(int n, int q, int ldn, int pin, const int32_t *__restrict
       int64_t e = (int64_t)j * ldn + i;
       col[e] = 0;
       Wx[e] = Wy[e] = Wl[e] = Pp[e] = 0.0;
-      if (Pp32) Pp32[e] = 0.f;
     }
     pdinv[i] = 1.0;
-    if (pdinv32) pdinv32[i] = 1.f;
     return;
   }
   const bool interior = tag[i] == 0;
@@ -56,11 +53,9 @@ __global__ void k_pack(int n, int q, int ldn, int pin, const int32_t *__restrict
     else
       pv = ni * a + mi * b;
     Pp[e] = pv;
-    if (Pp32) Pp32[e] = (float)pv;
     if (c == i) diag += pv;
   }
   pdinv[i] = 1.0 / (diag == 0.0 ? 1.0 : diag);
-  if (pdinv32) pdinv32[i] = (float)pdinv[i];
 }
 
 // S4: momentum matrix and right-hand sides, Eqs. (u:tilde), (v:tilde):
@@ -79,8 +74,7 @@ __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ co
                            double a1, double a2, double a3, double *__restrict__ Am,
                            double *__restrict__ mdinv, double *__restrict__ bu,
                            double *__restrict__ bv, double *__restrict__ ut,
-                           double *__restrict__ vt, float *__restrict__ Am32,
-                           float *__restrict__ mdinv32) {
+                           double *__restrict__ vt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const bool interior = tag[i] == 0;
@@ -88,12 +82,8 @@ __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ co
   ut[i] = ui;
   vt[i] = vi;
   if (!interior) {
-    for (int j = 0; j < q; ++j) {
-      Am[(int64_t)j * ldn + i] = (j == 0) ? 1.0 : 0.0;
-      if (Am32) Am32[(int64_t)j * ldn + i] = (j == 0) ? 1.f : 0.f;
-    }
+    for (int j = 0; j < q; ++j) Am[(int64_t)j * ldn + i] = (j == 0) ? 1.0 : 0.0;
     mdinv[i] = 1.0;
-    if (mdinv32) mdinv32[i] = 1.f;
     bu[i] = ubc[i];
     bv[i] = vbc[i];
     return;
@@ -114,10 +104,8 @@ __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ co
       diag += val;
     }
     Am[e] = val;
-    if (Am32) Am32[e] = (float)val;
   }
   mdinv[i] = 1.0 / (diag == 0.0 ? 1.0 : diag);
-  if (mdinv32) mdinv32[i] = (float)mdinv[i];
   bu[i] = -rho * (a2 * un[i] + a3 * unm1[i]) / dt - gx;
   bv[i] = -rho * (a2 * vn[i] + a3 * vnm1[i]) / dt - gy;
 }
@@ -339,6 +327,20 @@ __global__ void k_finalize(const double *__restrict__ part, int nb, int n, int m
   }
 }
 
+// FP64 array -> the inner arithmetic of the mixed-precision solve: FP32
+// (round to nearest) or float-float (hi = rn(v), lo = rn(v - hi)).
+__global__ void k_to_inner(int64_t m, const double *__restrict__ src, void *__restrict__ dst,
+                           int ff) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const double v = src[i];
+  const float h = __double2float_rn(v);
+  if (ff)
+    reinterpret_cast<float2 *>(dst)[i] = make_float2(h, __double2float_rn(v - (double)h));
+  else
+    reinterpret_cast<float *>(dst)[i] = h;
+}
+
 __global__ void k_spmv(int n, int q, int ldn, const int32_t *__restrict__ col,
                        const double *__restrict__ val, const double *__restrict__ x,
                        double *__restrict__ y) {
@@ -360,7 +362,7 @@ static inline int grid_of(int n) { return (n + RT - 1) / RT; }
 int ops_pack(rbffd_problem *P) {
   k_pack<<<(P->ldn + RT - 1) / RT, RT, 0, P->ctx->stream>>>(
       P->n, P->q, P->ldn, P->pin, P->idx_rm, P->wx_rm, P->wy_rm, P->wl_rm, P->tag, P->nx, P->ny,
-      P->col, P->Wx, P->Wy, P->Wl, P->Pp, P->p_dinv, P->Pp32, P->p_dinv32);
+      P->col, P->Wx, P->Wy, P->Wl, P->Pp, P->p_dinv);
   return after_launch(P->ctx, "k_pack");
 }
 
@@ -368,7 +370,7 @@ int ops_momentum(rbffd_problem *P, const rbffd_step_params *sp) {
   k_momentum<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(
       P->n, P->q, P->ldn, P->col, P->Wx, P->Wy, P->Wl, P->tag, P->u, P->v, P->p, P->un, P->vn,
       P->unm1, P->vnm1, P->ubc, P->vbc, P->rho, P->mu, sp->dt, sp->alpha[0], sp->alpha[1],
-      sp->alpha[2], P->Am, P->m_dinv, P->bu, P->bv, P->ut, P->vt, P->Am32, P->m_dinv32);
+      sp->alpha[2], P->Am, P->m_dinv, P->bu, P->bv, P->ut, P->vt);
   return after_launch(P->ctx, "k_momentum");
 }
 
@@ -428,6 +430,12 @@ int ops_resid(rbffd_problem *P) {
 int ops_spmv(rbffd_problem *P, const double *val, const double *x, double *y) {
   k_spmv<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(P->n, P->q, P->ldn, P->col, val, x, y);
   return after_launch(P->ctx, "k_spmv");
+}
+
+int ops_to_inner(rbffd_problem *P, const double *src, void *dst, int64_t m) {
+  int ff = P->inner == INNER_FF;
+  k_to_inner<<<(unsigned)((m + RT - 1) / RT), RT, 0, P->ctx->stream>>>(m, src, dst, ff);
+  return after_launch(P->ctx, "k_to_inner");
 }
 
 int ops_reduce_blocks(rbffd_ctx *ctx, int n) {

@@ -12,4 +12,5 @@ int ops_rotate(rbffd_problem *P);
 int ops_resid(rbffd_problem *P);
 int ops_spmv(rbffd_problem *P, const double *val, const double *x, double *y);
 int ops_reduce_blocks(rbffd_ctx *ctx, int n);
+int ops_to_inner(rbffd_problem *P, const double *src, void *dst, int64_t m);
 }  // namespace rbffd

@@ -48,7 +48,8 @@ int check_desc(const rbffd_problem_desc *d) {
     set_error("problem desc: pin %d out of range", d->pin);
     return RBFFD_EINVAL;
   }
-  if (d->precision != RBFFD_PREC_FP64 && d->precision != RBFFD_PREC_MIXED) {
+  if (d->precision != RBFFD_PREC_FP64 && d->precision != RBFFD_PREC_MIXED &&
+      d->precision != RBFFD_PREC_MIXED_FF) {
     set_error("problem desc: unknown precision %d", d->precision);
     return RBFFD_EINVAL;
   }
@@ -91,6 +92,10 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
                         P->wl_rm, P->d_first_singular));
   prof_end(ctx, 0);
   RBFFD_TRY(ops_pack(P));
+  if (P->precision != RBFFD_PREC_FP64) {
+    RBFFD_TRY(ops_to_inner(P, P->Pp, P->Pin, (int64_t)P->ldn * P->q));
+    RBFFD_TRY(ops_to_inner(P, P->p_dinv, P->pdin, P->ldn));
+  }
   k_init_state<<<(P->n + 255) / 256, 256, 0, st>>>(P->n, P->tag, P->ubc, P->vbc, P->u, P->v,
                                                    P->p, P->un, P->vn, P->unm1, P->vnm1, P->pc,
                                                    P->ut, P->vt);
@@ -137,15 +142,18 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   a.flags = P->flags;
   a.tol = sp->krylov_tol;
   a.maxit = sp->krylov_maxit;
-  if (P->precision == RBFFD_PREC_MIXED) {
+  if (P->precision != RBFFD_PREC_FP64) {
+    RBFFD_TRY(ops_to_inner(P, P->Am, P->Ain, (int64_t)P->ldn * P->q));
+    RBFFD_TRY(ops_to_inner(P, P->m_dinv, P->mdin, P->ldn));
     MixedArgs m;
     memset(&m, 0, sizeof(m));
+    m.inner = P->inner;
     m.n = P->n;
     m.q = P->q;
     m.ldn = P->ldn;
     m.col = P->col;
     m.part64 = P->part64;
-    m.part32 = P->part32;
+    m.partin = P->partin;
     m.bar = P->bar;
     m.flags = P->flags;
     m.tol = sp->krylov_tol;
@@ -154,8 +162,8 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
     m.inner_maxit = sp->inner_maxit > 0 ? sp->inner_maxit : 4000;
     m.max_sweeps = 60;
     m.val64 = P->Am;
-    m.val32 = P->Am32;
-    m.dinv32 = P->m_dinv32;
+    m.valin = P->Ain;
+    m.dinvin = P->mdin;
     m.b[0] = P->bu;
     m.b[1] = P->bv;
     m.x[0] = P->ut;
@@ -169,8 +177,8 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
     prof_end(ctx, 0);
     RBFFD_TRY(ops_divergence(P, sp));
     m.val64 = P->Pp;
-    m.val32 = P->Pp32;
-    m.dinv32 = P->p_dinv32;
+    m.valin = P->Pin;
+    m.dinvin = P->pdin;
     m.b[0] = P->bp;
     m.b[1] = nullptr;
     m.x[0] = P->pc;
@@ -275,9 +283,11 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   knn_workspace_bytes(n, &P->knn_lay);
   P->kblocks1 = krylov_blocks_for(ctx, n, 1);
   P->kblocks2 = krylov_blocks_for(ctx, n, 2);
-  const bool mixed = d->precision == RBFFD_PREC_MIXED;
+  const bool mixed = d->precision != RBFFD_PREC_FP64;
+  P->inner = d->precision == RBFFD_PREC_MIXED_FF ? INNER_FF : INNER_F32;
+  const size_t es = P->inner == INNER_FF ? 8 : 4;  // bytes per inner value
   if (mixed) {
-    int c1 = krylov_ir_max_blocks(ctx, 1), c2 = krylov_ir_max_blocks(ctx, 2);
+    int c1 = krylov_ir_max_blocks(ctx, 1, P->inner), c2 = krylov_ir_max_blocks(ctx, 2, P->inner);
     if (P->kblocks1 > c1) P->kblocks1 = c1;
     if (P->kblocks2 > c2) P->kblocks2 = c2;
   }
@@ -306,14 +316,14 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   size_t o_knn = c.take<char>(P->knn_lay.bytes);
   size_t o_p32 = 0, o_a32 = 0, o_pd32 = 0, o_md32 = 0, o_mv[18] = {}, o_part64 = 0, o_part32 = 0;
   if (mixed) {
-    o_p32 = c.take<float>(lq);
-    o_a32 = c.take<float>(lq);
-    o_pd32 = c.take<float>(P->ldn);
-    o_md32 = c.take<float>(P->ldn);
-    for (int k = 0; k < 18; ++k) o_mv[k] = c.take<float>(n);
+    o_p32 = c.take<char>(lq * es);
+    o_a32 = c.take<char>(lq * es);
+    o_pd32 = c.take<char>(P->ldn * es);
+    o_md32 = c.take<char>(P->ldn * es);
+    for (int k = 0; k < 18; ++k) o_mv[k] = c.take<char>((size_t)n * es);
     int kb = P->kblocks1 > P->kblocks2 ? P->kblocks1 : P->kblocks2;
     o_part64 = c.take<double>(krylov_ir_partials64(2, kb));
-    o_part32 = c.take<float>(krylov_ir_partials32(2, kb));
+    o_part32 = c.take<char>(krylov_ir_partials_inner_bytes(2, kb, P->inner));
   }
   P->bytes = c.off;
   int rc = dev_alloc(ctx, &P->mem, P->bytes);
@@ -358,17 +368,17 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   P->d_first_singular = (int *)(b + o_fs);
   P->knn_ws = (void *)(b + o_knn);
   if (mixed) {
-    P->Pp32 = (float *)(b + o_p32);
-    P->Am32 = (float *)(b + o_a32);
-    P->p_dinv32 = (float *)(b + o_pd32);
-    P->m_dinv32 = (float *)(b + o_md32);
+    P->Pin = (void *)(b + o_p32);
+    P->Ain = (void *)(b + o_a32);
+    P->pdin = (void *)(b + o_pd32);
+    P->mdin = (void *)(b + o_md32);
     for (int r = 0; r < 2; ++r) {
-      float **w[9] = {&P->mv[r].r, &P->mv[r].rh, &P->mv[r].p, &P->mv[r].v, &P->mv[r].ph,
-                      &P->mv[r].s, &P->mv[r].sh, &P->mv[r].t, &P->mv[r].d};
-      for (int k = 0; k < 9; ++k) *w[k] = (float *)(b + o_mv[r * 9 + k]);
+      void **w[9] = {&P->mv[r].r, &P->mv[r].rh, &P->mv[r].p0, &P->mv[r].p1, &P->mv[r].v0,
+                     &P->mv[r].v1, &P->mv[r].s, &P->mv[r].t, &P->mv[r].d};
+      for (int k = 0; k < 9; ++k) *w[k] = (void *)(b + o_mv[r * 9 + k]);
     }
     P->part64 = (double *)(b + o_part64);
-    P->part32 = (float *)(b + o_part32);
+    P->partin = (void *)(b + o_part32);
   }
   if (cudaMemsetAsync(P->mem, 0, P->bytes, ctx->stream) != cudaSuccess) {
     set_error("cudaMemsetAsync failed");
@@ -414,7 +424,7 @@ extern "C" int simple_iterate(rbffd_problem *P, const rbffd_step_params *sp, dou
   Readback r;
   RBFFD_TRY(read_back(P, &r));
   if (P->ctx->prof) {
-    // inner iterations of the mixed path move FP32 values and vectors
+    // inner iterations of the FP32 mixed path move 4-byte values and vectors
     const bool mx = P->precision == RBFFD_PREC_MIXED;
     const double sw = mx ? 4.0 : 8.0, si = 4.0, sv = mx ? 4.0 : 8.0, q = P->q, n = P->n;
     int im = r.kout[0].iters > r.kout[1].iters ? r.kout[0].iters : r.kout[1].iters;
@@ -424,7 +434,7 @@ extern "C" int simple_iterate(rbffd_problem *P, const rbffd_step_params *sp, dou
     prof_collect(P->ctx, 2, RBFFD_KSTAT_OUTER, 1.0, 0.0);
   }
   if (stats) {
-    const bool mixed = P->precision == RBFFD_PREC_MIXED;
+    const bool mixed = P->precision != RBFFD_PREC_FP64;
     for (int k = 0; k < 3; ++k) {
       stats->iters[k] = r.kout[k].iters;
       stats->relres[k] = r.kout[k].relres;

@@ -27,11 +27,13 @@ struct rbffd_problem {
   int32_t *col;
   double *Wx, *Wy, *Wl, *Pp, *Am;
   double *p_dinv, *m_dinv;
-  // FP32 copies for the mixed-precision solves (null in the FP64 path)
-  float *Pp32 = nullptr, *Am32 = nullptr, *p_dinv32 = nullptr, *m_dinv32 = nullptr;
+  // copies in the inner arithmetic of the mixed-precision solves (FP32 or
+  // float-float; null in the FP64 path)
+  int inner = 0;  // rbffd::INNER_F32 / INNER_FF
+  void *Pin = nullptr, *Ain = nullptr, *pdin = nullptr, *mdin = nullptr;
   rbffd::MixedVecs mv[2] = {};
   double *part64 = nullptr;
-  float *part32 = nullptr;
+  void *partin = nullptr;
   // fields
   double *u, *v, *p, *p2, *un, *vn, *unm1, *vnm1, *ut, *vt, *pc, *bu, *bv, *bp;
   // Krylov workspace: 8 vectors x 2 right-hand sides

@@ -23,7 +23,7 @@ TAG_INTERIOR, TAG_DIRICHLET = 0, 1
 OP_DX, OP_DY, OP_LAP, OP_PCORR, OP_MOMENTUM = 0, 1, 2, 3, 4
 FIELDS = {"u": 0, "v": 1, "p": 2, "un": 3, "vn": 4, "unm1": 5, "vnm1": 6, "ut": 7, "vt": 8,
           "pc": 9, "ubc": 10, "vbc": 11}
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_FF = 0, 1, 2
 
 
 class RbffdError(RuntimeError):

@@ -179,13 +179,14 @@ def test_bad_arguments_rejected():
         rbffd.Problem(ctx(), fp)
 
 
+@pytest.mark.parametrize("prec", [rbffd.PREC_MIXED, rbffd.PREC_MIXED_FF])
 @pytest.mark.parametrize("kind", ["kovasznay", "cavity"])
-def test_mixed_precision_outer_iterations_match_oracle(kind):
-    """FP32 BiCGSTAB inside FP64 defect correction stops on the same FP64
-    relative residual as the FP64 solver, so the outer iterates agree with
-    the FP64 oracle to the same tolerance."""
+def test_mixed_precision_outer_iterations_match_oracle(kind, prec):
+    """FP32 or float-float BiCGSTAB inside FP64 defect correction stops on
+    the same FP64 relative residual as the FP64 solver, so the outer iterates
+    agree with the FP64 oracle to the same tolerance."""
     fp = clouds.kovasznay(30, dt=0.4) if kind == "kovasznay" else clouds.cavity(40, dt=0.05)
-    P = rbffd.Problem(ctx(), fp, rbffd.PREC_MIXED)
+    P = rbffd.Problem(ctx(), fp, prec)
     O = oracle.Problem(fp, krylov_tol=1e-12)
     for r in range(3):
         dg, sg = P.simple_iterate(fp.dt, krylov_tol=1e-12)
@@ -198,12 +199,29 @@ def test_mixed_precision_outer_iterations_match_oracle(kind):
             assert e <= 1e-8, (r, k, e)
 
 
-def test_mixed_and_fp64_paths_agree_on_steps():
+@pytest.mark.parametrize("prec", [rbffd.PREC_MIXED, rbffd.PREC_MIXED_FF])
+def test_mixed_and_fp64_paths_agree_on_steps(prec):
     fp = clouds.kovasznay(30, dt=0.4)
     A = rbffd.Problem(ctx(), fp, rbffd.PREC_FP64)
-    B = rbffd.Problem(ctx(), fp, rbffd.PREC_MIXED)
+    B = rbffd.Problem(ctx(), fp, prec)
     for _ in range(2):
         A.time_step(fp.dt, 1e-4, max_outer=3)
         B.time_step(fp.dt, 1e-4, max_outer=3)
     for k in ("u", "v", "p"):
         assert rel_l2(B.get(k), A.get(k)) <= 1e-8
+
+
+def test_float_float_path_on_full_cavity_matches_fp64_path():
+    """The 200 x 200 cavity (N = 40 000): the FP32 inner solve cannot reach
+    it (cond * eps_fp32 ~ 1), float-float can; both stop on the same FP64
+    residual as the FP64 path, so the outer iterates agree."""
+    fp = clouds.cavity(200)
+    A = rbffd.Problem(ctx(), fp, rbffd.PREC_FP64)
+    B = rbffd.Problem(ctx(), fp, rbffd.PREC_MIXED_FF)
+    for _ in range(2):
+        da, _ = A.simple_iterate(fp.dt, krylov_tol=1e-12, krylov_maxit=100000)
+        db, sb = B.simple_iterate(fp.dt, krylov_tol=1e-12, krylov_maxit=100000)
+        assert max(sb["relres"]) <= 1e-12
+        assert abs(da - db) <= 1e-8 * abs(da)
+    for k in ("u", "v", "p"):
+        assert rel_l2(B.get(k), A.get(k)) <= 1e-8, k
