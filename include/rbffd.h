@@ -315,6 +315,32 @@ int rbffd_get_operators(rbffd_problem *prob, int32_t *idx, double *wx, double *w
 /* y = W x for one operator (RBFFD_OP_*); x, y: device, n doubles. */
 int rbffd_apply(rbffd_problem *prob, int32_t which, const double *x, double *y);
 
+/* ------------------------------------------------------------- batches */
+
+/* Many independent problems advanced together (the batched workloads; the
+ * paper has one problem at a time).  Every call runs one outer iteration
+ * (the same steps as simple_iterate) for each active member: the row kernels
+ * per member, and the two Krylov solves of all members in one cooperative
+ * launch each, in which every member owns consecutive CTAs and synchronises
+ * only with them.  Members must be RBFFD_PREC_FP64 problems of the batch's
+ * context and stay owned by the caller (destroy the batch first).  A member
+ * solved in a batch matches the same member solved alone to the Krylov
+ * tolerance (the sums are ordered differently, the fixed point is not). */
+typedef struct rbffd_batch rbffd_batch;
+int rbffd_batch_create(rbffd_ctx *ctx, int32_t count, rbffd_problem *const *members,
+                       rbffd_batch **out);
+void rbffd_batch_destroy(rbffd_batch *batch);
+/* active: host int32[count] (nullable = all); deltas: host double[count];
+ * stats: host rbffd_iter_stats[count] (nullable); status: host int32[count]
+ * (nullable).  With status, a member whose solve failed reports its code
+ * there and the call returns RBFFD_OK; without it the first failure is
+ * returned.  Entries of inactive members are left untouched.  Errors:
+ * RBFFD_EINVAL if more members are active than one launch holds CTAs
+ * (several hundred on a GB300), RBFFD_ECUDA. */
+int rbffd_batch_iterate(rbffd_batch *batch, const rbffd_step_params *params,
+                        const int32_t *active, double *deltas, rbffd_iter_stats *stats,
+                        int32_t *status);
+
 #ifdef __cplusplus
 }
 #endif

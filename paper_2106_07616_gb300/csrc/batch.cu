@@ -1,0 +1,328 @@
+// batch.cu -- many independent flow problems advanced together: one outer
+// iteration of every active member per call, with the two Krylov solves of
+// all members in one cooperative launch each (k_bicgstab_batch: each member
+// gets its own consecutive CTAs and synchronises only among them, so members
+// iterate independently and one member's grid-exchange latency is hidden
+// behind the others' work).  The row kernels of the outer iteration are a
+// few microseconds per member and run per member on the same stream.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "batch.cuh"
+#include "ops.cuh"
+#include "problem.cuh"
+
+using namespace rbffd;
+
+namespace {
+
+// Per member result of one batched outer iteration, gathered on the device.
+struct MemberOut {
+  double delta;
+  double relres[3];
+  int iters[3];
+  int status[3];
+};
+
+__global__ void k_gather_out(int m, IterRecord *const *recs, const KrylovOut *const *kouts,
+                             MemberOut *out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  out[i].delta = recs[i]->delta;
+  for (int k = 0; k < 3; ++k) {
+    out[i].relres[k] = kouts[i][k].relres;
+    out[i].iters[k] = kouts[i][k].iters;
+    out[i].status[k] = kouts[i][k].status;
+  }
+}
+
+int status_of(int s) {
+  switch (s) {
+    case KRY_OK: return RBFFD_OK;
+    case KRY_NOCONV: return RBFFD_ENOCONV;
+    case KRY_DIVERGED: return RBFFD_EDIVERGED;
+    case KRY_TIMEOUT: return RBFFD_ETIMEOUT;
+    default: return RBFFD_ECUDA;
+  }
+}
+
+}  // namespace
+
+namespace rbffd {
+
+BatchScratch::~BatchScratch() {
+  if (ctx) {
+    dev_free(ctx, dmem, dbytes);
+    if (hmem) cudaFreeHost(hmem);
+  }
+}
+
+int BatchScratch::reserve(rbffd_ctx *c, int members) {
+  ctx = c;
+  if (members <= cap) return RBFFD_OK;
+  if (dmem) {
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, dmem, dbytes);
+    dmem = nullptr;
+  }
+  if (hmem) {
+    cudaFreeHost(hmem);
+    hmem = nullptr;
+  }
+  cap = std::max(members, 16);
+  maxc = std::max(krylov_batch_max_ctas(ctx, 1), krylov_batch_max_ctas(ctx, 2));
+  // device: sys args, cta tables, flags, barriers, record pointers, outputs
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t a = o;
+    o += (b + 255) / 256 * 256;
+    return a;
+  };
+  off_sys = take(sizeof(KrylovArgs) * cap);
+  off_cta_sys = take(sizeof(int) * maxc);
+  off_cta_first = take(sizeof(int) * cap);
+  off_flags = take(sizeof(unsigned int) * maxc);
+  off_bars = take(sizeof(GridBarrier) * cap);
+  off_recs = take(sizeof(void *) * cap);
+  off_kouts = take(sizeof(void *) * cap);
+  off_out = take(sizeof(MemberOut) * cap);
+  dbytes = o;
+  RBFFD_TRY(dev_alloc(ctx, &dmem, dbytes));
+  hbytes = dbytes;
+  RBFFD_CK(cudaMallocHost(&hmem, hbytes));
+  return RBFFD_OK;
+}
+
+// One batched Krylov launch for the systems args[0..m) (args filled except
+// nblocks, tpr, flags and bar, which are set here).
+static int launch_krylov(BatchScratch &S, int nr, std::vector<KrylovArgs> &args,
+                         const std::vector<int> &rows) {
+  rbffd_ctx *ctx = S.ctx;
+  const int m = (int)args.size();
+  const int cmax = krylov_batch_max_ctas(ctx, nr);
+  if (m > cmax) {
+    set_error("batch: %d members exceed the %d co-resident CTAs of one launch", m, cmax);
+    return RBFFD_EINVAL;
+  }
+  // one CTA each, the rest in proportion to the rows, each capped by what
+  // its partial-sum buffers hold and by 8 threads per row
+  std::vector<int> nb(m, 1);
+  long long total = std::accumulate(rows.begin(), rows.end(), 0LL);
+  int left = cmax - m;
+  for (int i = 0; i < m && total > 0; ++i) {
+    int extra = (int)((double)left * rows[i] / (double)total);
+    int cap = std::min(args[i].nblocks, (int)((rows[i] * 8LL + KB_NT - 1) / KB_NT));
+    cap = std::min(cap, 160);  // the grid exchange polls at most 160 CTAs
+    nb[i] = std::max(1, std::min(1 + extra, cap));
+  }
+  int nctas = std::accumulate(nb.begin(), nb.end(), 0);
+  char *hb = (char *)S.hmem;
+  char *db = (char *)S.dmem;
+  KrylovArgs *hsys = (KrylovArgs *)(hb + S.off_sys);
+  int *hcs = (int *)(hb + S.off_cta_sys);
+  int *hcf = (int *)(hb + S.off_cta_first);
+  unsigned int *dflags = (unsigned int *)(db + S.off_flags);
+  GridBarrier *dbars = (GridBarrier *)(db + S.off_bars);
+  int c = 0;
+  for (int i = 0; i < m; ++i) {
+    KrylovArgs a = args[i];
+    a.nblocks = nb[i];
+    const long long warps = (long long)nb[i] * (KB_NT / 32);
+    int T = 1;
+    for (int t = 2; t <= 8; ++t)
+      if ((long long)(32 / t) * warps >= a.n) T = t;
+    a.tpr = T;
+    a.flags = dflags + c;
+    a.bar = dbars + i;
+    hsys[i] = a;
+    hcf[i] = c;
+    for (int k = 0; k < nb[i]; ++k) hcs[c + k] = i;
+    c += nb[i];
+  }
+  // the host tables are contiguous from off_sys to off_flags
+  RBFFD_CK(cudaMemcpyAsync(db + S.off_sys, hb + S.off_sys, S.off_flags - S.off_sys,
+                           cudaMemcpyHostToDevice, ctx->stream));
+  RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * nctas, ctx->stream));
+  RBFFD_CK(cudaMemsetAsync(dbars, 0, sizeof(GridBarrier) * m, ctx->stream));
+  RBFFD_TRY(krylov_batch_launch(ctx, nr, nctas, (const KrylovArgs *)(db + S.off_sys),
+                                (const int *)(db + S.off_cta_sys),
+                                (const int *)(db + S.off_cta_first)));
+  // the pinned tables are reused by the next launch: wait until copied
+  RBFFD_CK(cudaStreamSynchronize(ctx->stream));
+  return RBFFD_OK;
+}
+
+int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m, const rbffd_step_params *sp,
+                  double *deltas, rbffd_iter_stats *stats, int *status) {
+  if (m <= 0) return RBFFD_OK;
+  rbffd_ctx *ctx = P[0]->ctx;
+  for (int i = 0; i < m; ++i) {
+    if (P[i]->ctx != ctx || P[i]->precision != RBFFD_PREC_FP64) {
+      set_error("batch: members must share one context and use RBFFD_PREC_FP64");
+      return RBFFD_EINVAL;
+    }
+  }
+  RBFFD_TRY(S.reserve(ctx, m));
+  std::vector<int> rows(m);
+  for (int i = 0; i < m; ++i) rows[i] = P[i]->n;
+  // momentum predictor of every member, then one launch for all the solves
+  std::vector<KrylovArgs> a2(m), a1(m);
+  for (int i = 0; i < m; ++i) {
+    RBFFD_TRY(ops_momentum(P[i], sp));
+    KrylovArgs &a = a2[i];
+    memset(&a, 0, sizeof(a));
+    a.n = P[i]->n;
+    a.q = P[i]->q;
+    a.ldn = P[i]->ldn;
+    a.col = P[i]->col;
+    a.part = P[i]->part;
+    a.tol = sp->krylov_tol;
+    a.maxit = sp->krylov_maxit;
+    a.val = P[i]->Am;
+    a.dinv = P[i]->m_dinv;
+    a.b[0] = P[i]->bu;
+    a.b[1] = P[i]->bv;
+    a.x[0] = P[i]->ut;
+    a.x[1] = P[i]->vt;
+    a.w[0] = P[i]->kv[0];
+    a.w[1] = P[i]->kv[1];
+    a.out = P[i]->kout;
+    a.nblocks = std::max(P[i]->kblocks1, P[i]->kblocks2);  // partial-sum capacity
+  }
+  prof_begin(ctx, 0);
+  RBFFD_TRY(launch_krylov(S, 2, a2, rows));
+  prof_end(ctx, 0);
+  for (int i = 0; i < m; ++i) {
+    RBFFD_TRY(ops_divergence(P[i], sp));
+    a1[i] = a2[i];
+    a1[i].val = P[i]->Pp;
+    a1[i].dinv = P[i]->p_dinv;
+    a1[i].b[0] = P[i]->bp;
+    a1[i].b[1] = nullptr;
+    a1[i].x[0] = P[i]->pc;
+    a1[i].x[1] = nullptr;
+    a1[i].out = P[i]->kout + 2;
+    a1[i].nblocks = 2 * std::max(P[i]->kblocks1, P[i]->kblocks2);
+  }
+  prof_begin(ctx, 1);
+  RBFFD_TRY(launch_krylov(S, 1, a1, rows));
+  prof_end(ctx, 1);
+  for (int i = 0; i < m; ++i) {
+    RBFFD_TRY(ops_pressure(P[i], sp));
+    RBFFD_TRY(ops_correct(P[i], sp));
+  }
+  // gather every member's Delta and Krylov outcome with one read-back
+  char *hb = (char *)S.hmem;
+  char *db = (char *)S.dmem;
+  IterRecord **hrec = (IterRecord **)(hb + S.off_recs);
+  KrylovOut **hko = (KrylovOut **)(hb + S.off_kouts);
+  for (int i = 0; i < m; ++i) {
+    hrec[i] = P[i]->rec;
+    hko[i] = P[i]->kout;
+  }
+  RBFFD_CK(cudaMemcpyAsync(db + S.off_recs, hb + S.off_recs, S.off_out - S.off_recs,
+                           cudaMemcpyHostToDevice, ctx->stream));
+  k_gather_out<<<(m + 127) / 128, 128, 0, ctx->stream>>>(
+      m, (IterRecord *const *)(db + S.off_recs), (const KrylovOut *const *)(db + S.off_kouts),
+      (MemberOut *)(db + S.off_out));
+  RBFFD_TRY(after_launch(ctx, "k_gather_out"));
+  RBFFD_CK(cudaMemcpyAsync(hb + S.off_out, db + S.off_out, sizeof(MemberOut) * m,
+                           cudaMemcpyDeviceToHost, ctx->stream));
+  RBFFD_CK(cudaStreamSynchronize(ctx->stream));
+  const MemberOut *mo = (const MemberOut *)(hb + S.off_out);
+  int rc = RBFFD_OK;
+  for (int i = 0; i < m; ++i) {
+    if (deltas) deltas[i] = mo[i].delta;
+    if (stats) {
+      for (int k = 0; k < 3; ++k) {
+        stats[i].iters[k] = mo[i].iters[k];
+        stats[i].relres[k] = mo[i].relres[k];
+        stats[i].sweeps[k] = 0;
+      }
+    }
+    int st = RBFFD_OK;
+    for (int k = 0; k < 3 && st == RBFFD_OK; ++k) st = status_of(mo[i].status[k]);
+    if (st == RBFFD_OK && !std::isfinite(mo[i].delta)) st = RBFFD_EDIVERGED;
+    if (status) status[i] = st;
+    if (st != RBFFD_OK && rc == RBFFD_OK) rc = st;
+  }
+  return status ? RBFFD_OK : rc;
+}
+
+}  // namespace rbffd
+
+// ------------------------------------------------------------------ C ABI
+
+struct rbffd_batch {
+  rbffd_ctx *ctx = nullptr;
+  std::vector<rbffd_problem *> members;
+  BatchScratch scratch;
+};
+
+extern "C" int rbffd_batch_create(rbffd_ctx *ctx, int32_t count, rbffd_problem *const *members,
+                                  rbffd_batch **out) {
+  if (!ctx || !out || count < 1 || !members) return RBFFD_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!members[i] || members[i]->ctx != ctx || members[i]->precision != RBFFD_PREC_FP64) {
+      set_error("rbffd_batch_create: member %d is null, on another context or not FP64", i);
+      return RBFFD_EINVAL;
+    }
+  }
+  rbffd_batch *b = new rbffd_batch();
+  b->ctx = ctx;
+  ctx_ref(ctx);
+  b->members.assign(members, members + count);
+  int rc = b->scratch.reserve(ctx, count);
+  if (rc != RBFFD_OK) {
+    delete b;
+    ctx_unref(ctx);
+    return rc;
+  }
+  *out = b;
+  return RBFFD_OK;
+}
+
+extern "C" void rbffd_batch_destroy(rbffd_batch *b) {
+  if (!b) return;
+  rbffd_ctx *ctx = b->ctx;
+  cudaStreamSynchronize(ctx->stream);
+  delete b;  // frees the scratch through ctx, which is still alive here
+  ctx_unref(ctx);
+}
+
+extern "C" int rbffd_batch_iterate(rbffd_batch *b, const rbffd_step_params *sp,
+                                   const int32_t *active, double *deltas,
+                                   rbffd_iter_stats *stats, int32_t *status) {
+  if (!b || !sp) return RBFFD_EINVAL;
+  if (!(sp->dt > 0) || !(sp->krylov_tol > 0) || sp->krylov_maxit < 1 || sp->alpha[0] == 0.0)
+    return RBFFD_EINVAL;
+  RBFFD_CK(cudaSetDevice(b->ctx->device));
+  const int count = (int)b->members.size();
+  std::vector<rbffd_problem *> act;
+  std::vector<int> where;
+  for (int i = 0; i < count; ++i)
+    if (!active || active[i]) {
+      act.push_back(b->members[i]);
+      where.push_back(i);
+    }
+  std::vector<double> d(act.size());
+  std::vector<rbffd_iter_stats> st(act.size());
+  std::vector<int> sts(act.size());
+  int rc = batch_iterate(b->scratch, act.data(), (int)act.size(), sp, d.data(), st.data(),
+                         sts.data());
+  if (rc != RBFFD_OK) return rc;
+  int worst = RBFFD_OK;
+  for (size_t k = 0; k < act.size(); ++k) {
+    const int i = where[k];
+    if (deltas) deltas[i] = d[k];
+    if (stats) stats[i] = st[k];
+    if (status) status[i] = sts[k];
+    if (sts[k] != RBFFD_OK && worst == RBFFD_OK) worst = sts[k];
+  }
+  if (worst != RBFFD_OK && !status) set_error("a batch member's solve failed (%d)", worst);
+  return status ? RBFFD_OK : worst;
+}

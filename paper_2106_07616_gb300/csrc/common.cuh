@@ -22,6 +22,10 @@ struct rbffd_ctx {
   // pinned host scratch for small read-backs
   void *pinned = nullptr;
   size_t pinned_bytes = 0;
+  // problems and batches alive on this context; rbffd_ctx_destroy waits for
+  // the last one (Python may finalise objects in any order at exit)
+  int refs = 0;
+  bool closing = false;
   // live kernel timing (rbffd_ctx_profile)
   bool prof = false;
   cudaEvent_t ev[8] = {};
@@ -58,6 +62,10 @@ inline int after_launch(rbffd_ctx *ctx, const char *what) {
   }
   return RBFFD_OK;
 }
+
+// Reference counting of the objects that point at a context.
+void ctx_ref(rbffd_ctx *ctx);
+void ctx_unref(rbffd_ctx *ctx);
 
 // Device allocation charged to the context's budget.
 int dev_alloc(rbffd_ctx *ctx, void **p, size_t bytes);

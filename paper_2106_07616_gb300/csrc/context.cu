@@ -93,8 +93,7 @@ extern "C" int rbffd_ctx_create(rbffd_ctx **out, int device, size_t hbm_budget_b
   return RBFFD_OK;
 }
 
-extern "C" void rbffd_ctx_destroy(rbffd_ctx *ctx) {
-  if (!ctx) return;
+static void ctx_free(rbffd_ctx *ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -102,6 +101,19 @@ extern "C" void rbffd_ctx_destroy(rbffd_ctx *ctx) {
   for (int k = 0; k < 8; ++k)
     if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
   delete ctx;
+}
+
+namespace rbffd {
+void ctx_ref(rbffd_ctx *ctx) { ctx->refs++; }
+void ctx_unref(rbffd_ctx *ctx) {
+  if (--ctx->refs == 0 && ctx->closing) ctx_free(ctx);
+}
+}  // namespace rbffd
+
+extern "C" void rbffd_ctx_destroy(rbffd_ctx *ctx) {
+  if (!ctx) return;
+  ctx->closing = true;
+  if (ctx->refs == 0) ctx_free(ctx);
 }
 
 extern "C" int rbffd_ctx_profile(rbffd_ctx *ctx, int enable) {

@@ -54,17 +54,18 @@ struct KScalars {
 //      partial (r, r)                                      -> |r| test
 // The next direction is formed before the |r| test; if the test stops the
 // solve it is simply unused.  rho' equals (r^, r) in exact arithmetic.
+// The solve of one system by the nb CTAs lb = 0..nb-1 that share it (the
+// whole grid for a single system; a subrange of a batched launch).
 template <int NR, int NT>
-__global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
+__device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb, const int nb) {
   __shared__ double sred[5 * NR * NT];  // block_partials of up to 5 NR values
   __shared__ double stot[16];
   __shared__ KScalars ks[NR];
   __shared__ int s_flags[2];
-  const int tid = blockIdx.x * NT + threadIdx.x;
-  const int stride = gridDim.x * NT;
+  const int tid = lb * NT + threadIdx.x;
+  const int stride = nb * NT;
   const int wglobal = tid >> 5, nwarps = stride >> 5;
   const int n = A.n, q = A.q, ldn = A.ldn, T = A.tpr;
-  const int nb = gridDim.x;
   unsigned int epoch = 1;
   double *part = A.part;
   auto P = [&](int slot, int k) { return part + (size_t)(slot * NR + k) * nb; };
@@ -124,9 +125,9 @@ __global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
         outs[2 * k] = ini[k] ? P(S_BB, k) : nullptr;
         outs[2 * k + 1] = ini[k] ? P(S_RR, k) : nullptr;
       }
-      kdev::block_partials<NT, 2 * NR>(acc, sred, outs);
+      kdev::block_partials<NT, 2 * NR>(acc, sred, outs, lb);
       double tot[2 * NR];
-      ok = kdev::exchange<2 * NR>(A.flags, err, epoch++, outs, tot, stot);
+      ok = kdev::exchange<2 * NR>(A.flags, err, epoch++, outs, tot, stot, lb, nb);
       if (!ok) break;
       int zero_any = 0;
       if (leader) {
@@ -197,9 +198,9 @@ __global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
       double *outs[NR];
 #pragma unroll
       for (int k = 0; k < NR; ++k) outs[k] = run[k] ? P(S_RHV, k) : nullptr;
-      kdev::block_partials<NT, NR>(acc, sred, outs);
+      kdev::block_partials<NT, NR>(acc, sred, outs, lb);
       double tot[NR];
-      ok = kdev::exchange<NR>(A.flags, err, epoch++, outs, tot, stot);
+      ok = kdev::exchange<NR>(A.flags, err, epoch++, outs, tot, stot, lb, nb);
       if (!ok) break;
       if (leader) {
 #pragma unroll
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
           A.w[k].sh[i] = si * di;
         }
       }
-      ok = kdev::exchange<0, double>(A.flags, err, epoch++, nullptr, nullptr, stot);
+      ok = kdev::exchange<0, double>(A.flags, err, epoch++, nullptr, nullptr, stot, lb, nb);
       if (!ok) break;
     }
 
@@ -259,9 +260,9 @@ __global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
         outs[5 * k + 3] = run[k] ? P(S_RHS, k) : nullptr;
         outs[5 * k + 4] = run[k] ? P(S_RHT, k) : nullptr;
       }
-      kdev::block_partials<NT, 5 * NR>(acc, sred, outs);
+      kdev::block_partials<NT, 5 * NR>(acc, sred, outs, lb);
       double tot[5 * NR];
-      ok = kdev::exchange<5 * NR>(A.flags, err, epoch++, outs, tot, stot);
+      ok = kdev::exchange<5 * NR>(A.flags, err, epoch++, outs, tot, stot, lb, nb);
       if (!ok) break;
       if (leader) {
 #pragma unroll
@@ -330,9 +331,9 @@ __global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
       double *outs[NR];
 #pragma unroll
       for (int k = 0; k < NR; ++k) outs[k] = (run[k] && !half[k]) ? P(S_RR, k) : nullptr;
-      kdev::block_partials<NT, NR>(acc, sred, outs);
+      kdev::block_partials<NT, NR>(acc, sred, outs, lb);
       double tot[NR];
-      ok = kdev::exchange<NR>(A.flags, err, epoch++, outs, tot, stot);
+      ok = kdev::exchange<NR>(A.flags, err, epoch++, outs, tot, stot, lb, nb);
       if (!ok) break;
       if (leader) {
 #pragma unroll
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
     }
   }
 
-  if (blockIdx.x == 0 && leader) {
+  if (lb == 0 && leader) {
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
       A.out[k].iters = ks[k].it;
@@ -374,6 +375,25 @@ __global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
       A.out[k].relres = ks[k].relres;
     }
   }
+}
+
+template <int NR, int NT>
+__global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
+  bicgstab_body<NR, NT>(A, blockIdx.x, gridDim.x);
+}
+
+// Many independent systems in one cooperative launch: CTA b works on system
+// cta_sys[b]; the CTAs of one system are consecutive and synchronise only
+// with each other, so systems progress (and finish) independently.
+template <int NR, int NT>
+__global__ void __launch_bounds__(NT) k_bicgstab_batch(const KrylovArgs *__restrict__ sys,
+                                                       const int *__restrict__ cta_sys,
+                                                       const int *__restrict__ cta_first) {
+  __shared__ KrylovArgs A;
+  const int s = cta_sys[blockIdx.x];
+  if (threadIdx.x == 0) A = sys[s];
+  __syncthreads();
+  bicgstab_body<NR, NT>(A, blockIdx.x - cta_first[s], A.nblocks);
 }
 
 namespace {
@@ -446,5 +466,40 @@ int krylov_launch(rbffd_ctx *ctx, int nr, int nblocks, const KrylovArgs &args) {
 }
 
 size_t krylov_partials_doubles(int nr, int nblocks) { return (size_t)S_COUNT * nr * nblocks; }
+
+int krylov_batch_max_ctas(rbffd_ctx *ctx, int nr) {
+  int per_sm = 0;
+  cudaError_t e;
+  if (nr == 1)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_batch<1, KB_NT>, KB_NT,
+                                                      0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_batch<2, KB_NT>, KB_NT,
+                                                      0);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * ctx->num_sms;
+}
+
+int krylov_batch_launch(rbffd_ctx *ctx, int nr, int nctas, const KrylovArgs *d_sys,
+                        const int *d_cta_sys, const int *d_cta_first) {
+  if (nctas < 1 || nctas > krylov_batch_max_ctas(ctx, nr)) {
+    set_error("krylov_batch_launch: %d CTAs are not co-resident", nctas);
+    return RBFFD_EINVAL;
+  }
+  void *kargs[] = {(void *)&d_sys, (void *)&d_cta_sys, (void *)&d_cta_first};
+  const void *fn = nr == 1 ? (const void *)k_bicgstab_batch<1, KB_NT>
+                           : (const void *)k_bicgstab_batch<2, KB_NT>;
+  cudaError_t e =
+      cudaLaunchCooperativeKernel(fn, dim3(nctas), dim3(KB_NT), kargs, 0, ctx->stream);
+  ctx->launches++;
+  if (e != cudaSuccess) {
+    set_error("cooperative launch of k_bicgstab_batch failed: %s", cudaGetErrorString(e));
+    return RBFFD_ECUDA;
+  }
+  return RBFFD_OK;
+}
 
 }  // namespace rbffd

@@ -32,8 +32,11 @@ struct KrylovArgs {
   KrylovOut *out;       // nr entries
   double tol;
   int maxit;
-  int tpr;              // threads per row in the SpMV phases (1, 2, 4 or 8)
+  int tpr;              // threads per row in the SpMV phases (1..8)
+  int nblocks;          // CTAs that share the solve (batched launches)
 };
+
+constexpr int KB_NT = 256;  // threads per CTA of batched Krylov launches
 
 // Inner arithmetic of the mixed-precision solve.
 enum { INNER_F32 = 0, INNER_FF = 1 };
@@ -74,6 +77,12 @@ size_t krylov_ir_partials64(int nr, int nblocks);
 size_t krylov_ir_partials_inner_bytes(int nr, int nblocks, int inner);
 int krylov_blocks_for(rbffd_ctx *ctx, int n, int nr);
 int krylov_threads_per_row(int n, int nr, int nblocks);
+int krylov_batch_max_ctas(rbffd_ctx *ctx, int nr);
+// d_sys: device array of per-system arguments (nblocks, flags and partials
+// sized for that many CTAs); d_cta_sys / d_cta_first: per CTA, its system
+// and per system, its first CTA.  Flags and barrier words must be zeroed.
+int krylov_batch_launch(rbffd_ctx *ctx, int nr, int nctas, const KrylovArgs *d_sys,
+                        const int *d_cta_sys, const int *d_cta_first);
 int krylov_launch(rbffd_ctx *ctx, int nr, int nblocks, const KrylovArgs &args);
 size_t krylov_partials_doubles(int nr, int nblocks);
 

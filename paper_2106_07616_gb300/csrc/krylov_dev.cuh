@@ -95,17 +95,19 @@ __device__ __forceinline__ void spmv_rows(int n, int q, int ldn, int T,
 // warp-wide add occupies the FP64 pipe for ~32 cycles, so the number of
 // FP64 warp instructions, not their latency, is what a reduction costs.
 template <int NT, int V, typename AT>
-__device__ __forceinline__ void block_partials(AT (&val)[V], AT *sh, AT *const *outs) {
+__device__ __forceinline__ void block_partials(AT (&val)[V], AT *sh, AT *const *outs,
+                                               int lb = -1) {
+  if (lb < 0) lb = blockIdx.x;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
   for (int v = 0; v < V; ++v) sh[v * NT + threadIdx.x] = val[v];
   __syncthreads();
-  if (w < V) {
+  for (int v = w; v < V; v += NT / 32) {  // more values than warps: warp-strided
     AT t = AT(0);
 #pragma unroll 8
-    for (int k = 0; k < NT / 32; ++k) t += sh[w * NT + k * 32 + l];
+    for (int k = 0; k < NT / 32; ++k) t += sh[v * NT + k * 32 + l];
     t = wsum(t);
-    if (l == 0 && outs[w] != nullptr) outs[w][blockIdx.x] = t;
+    if (l == 0 && outs[v] != nullptr) outs[v][lb] = t;
   }
 }
 
@@ -114,15 +116,30 @@ __device__ __forceinline__ void block_partials(AT (&val)[V], AT *sh, AT *const *
 // every block has published epoch, then reduce the V partial arrays in a
 // fixed order, one warp per array.  Every block computes bit-identical totals.
 // V = 0 is a plain barrier.
+// lb, nb: this CTA's index among, and the number of, the CTAs that share
+// the solve (default: the whole grid).  A single-CTA solve needs no flags.
 template <int V, typename AT>
 __device__ __forceinline__ bool exchange(unsigned int *flags, int *err, unsigned int epoch,
-                                         AT *const *arrs, AT *tot, AT *sh) {
+                                         AT *const *arrs, AT *tot, AT *sh, int lb = -1,
+                                         int nb = -1) {
   __shared__ int s_ok;
-  const int nb = gridDim.x;
+  if (lb < 0) lb = blockIdx.x;
+  if (nb < 0) nb = gridDim.x;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
+  if (nb == 1) {
+    for (int v = w; v < V; v += blockDim.x / 32) {
+      AT t = arrs[v] != nullptr ? arrs[v][0] : AT(0);
+      if (l == 0) sh[v] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < V; ++v) tot[v] = sh[v];
+    __syncthreads();
+    return true;
+  }
   if (threadIdx.x == 0) {
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(flags[blockIdx.x]);
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(flags[lb]);
     f.store(epoch, cuda::memory_order_release);
   }
   if (w == 0) {
@@ -150,17 +167,17 @@ __device__ __forceinline__ bool exchange(unsigned int *flags, int *err, unsigned
     if (l == 0) s_ok = ok && (*(volatile int *)err == 0);
   }
   __syncthreads();
-  if (V > 0 && w < V) {
+  for (int v = w; v < V; v += blockDim.x / 32) {
     AT t = AT(0);
-    if (arrs[w] != nullptr) {
+    if (arrs[v] != nullptr) {
 #pragma unroll
       for (int u = 0; u < BPL; ++u) {
         const int b = l + 32 * u;
-        if (b < nb) t += ld_cg(arrs[w] + b);
+        if (b < nb) t += ld_cg(arrs[v] + b);
       }
     }
     t = wsum(t);
-    if (l == 0) sh[w] = t;
+    if (l == 0) sh[v] = t;
   }
   __syncthreads();
 #pragma unroll

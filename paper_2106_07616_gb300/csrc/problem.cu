@@ -273,6 +273,7 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   RBFFD_CK(cudaSetDevice(ctx->device));
   rbffd_problem *P = new rbffd_problem();
   P->ctx = ctx;
+  ctx_ref(ctx);
   P->n = d->n;
   P->q = d->q;
   P->degree = d->degree;
@@ -329,6 +330,7 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   int rc = dev_alloc(ctx, &P->mem, P->bytes);
   if (rc != RBFFD_OK) {
     delete P;
+    ctx_unref(ctx);
     return rc;
   }
   char *b = (char *)P->mem;
@@ -407,10 +409,12 @@ extern "C" int rbffd_problem_reload(rbffd_problem *P, const rbffd_problem_desc *
 
 extern "C" void rbffd_problem_destroy(rbffd_problem *P) {
   if (!P) return;
-  cudaSetDevice(P->ctx->device);
-  cudaStreamSynchronize(P->ctx->stream);
-  dev_free(P->ctx, P->mem, P->bytes);
+  rbffd_ctx *ctx = P->ctx;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  dev_free(ctx, P->mem, P->bytes);
   delete P;
+  ctx_unref(ctx);
 }
 
 extern "C" size_t rbffd_problem_bytes(const rbffd_problem *P) { return P ? P->bytes : 0; }

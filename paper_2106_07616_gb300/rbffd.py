@@ -111,6 +111,9 @@ def load(path: str = LIB_PATH):
         "rbffd_set_field": (C.c_int, [vp, i32, vp]),
         "rbffd_get_operators": (C.c_int, [vp, vp, vp, vp, vp, vp]),
         "rbffd_apply": (C.c_int, [vp, i32, vp, vp]),
+        "rbffd_batch_create": (C.c_int, [vp, i32, C.POINTER(vp), C.POINTER(vp)]),
+        "rbffd_batch_destroy": (None, [vp]),
+        "rbffd_batch_iterate": (C.c_int, [vp, C.POINTER(StepParams), vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -327,6 +330,45 @@ class Problem:
         _check(load().solve_unsteady(self.h, C.byref(sp), int(n_steps), cb, None, C.byref(st)),
                "solve_unsteady")
         return _stats(st)
+
+
+class Batch:
+    """Problems advanced together: one outer iteration of every active
+    member per call, the Krylov solves of all members in one launch each."""
+
+    def __init__(self, ctx, problems):
+        self.ctx = ctx
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        h = C.c_void_p()
+        _check(load().rbffd_batch_create(ctx.h, len(self.problems), arr, C.byref(h)),
+               "rbffd_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            load().rbffd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def iterate(self, dt, active=None, alpha=(1.5, -2.0, 0.5), krylov_tol=1e-12,
+                krylov_maxit=10000):
+        m = len(self.problems)
+        sp = StepParams(dt, (C.c_double * 3)(*alpha), krylov_tol, krylov_maxit, 0.0, 0)
+        act = None if active is None else np.ascontiguousarray(active, np.int32)
+        d = np.zeros(m)
+        st = (IterStats * m)()
+        status = np.zeros(m, np.int32)
+        _check(load().rbffd_batch_iterate(self.h, C.byref(sp), ptr(act), ptr(d),
+                                          C.cast(st, C.c_void_p), ptr(status)),
+               "rbffd_batch_iterate")
+        its = np.array([list(s.iters) for s in st])
+        return d, its, status
 
 
 def _stats(st):

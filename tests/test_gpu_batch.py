@@ -1,0 +1,77 @@
+"""Batched outer iterations: many problems, one Krylov launch per solve.
+Each member must give the same result in the mix as alone (to the Krylov
+tolerance: only the order of the partial sums differs)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import ctx, rel_l2
+from paper_2106_07616_gb300 import clouds, rbffd
+
+pytestmark = pytest.mark.gpu
+
+
+def members():
+    return [clouds.kovasznay(30, dt=0.4), clouds.cavity(40, dt=0.05),
+            clouds.kovasznay(30, seed=7, dt=0.4), clouds.cavity(24, seed=3, dt=0.05)]
+
+
+def test_batch_matches_members_solved_alone():
+    fps = members()
+    alone = [rbffd.Problem(ctx(), fp) for fp in fps]
+    for fp, P in zip(fps, alone):
+        for r in range(3):
+            P.simple_iterate(fp.dt)
+    # one batch per dt group, three outer iterations each
+    for dt in sorted(set(fp.dt for fp in fps)):
+        idx = [i for i, fp in enumerate(fps) if fp.dt == dt]
+        Bg = rbffd.Batch(ctx(), [rbffd.Problem(ctx(), fps[i]) for i in idx])
+        for r in range(3):
+            d, its, status = Bg.iterate(dt)
+            assert np.all(status == 0)
+        for j, i in enumerate(idx):
+            for k in ("u", "v", "p"):
+                e = rel_l2(Bg.problems[j].get(k), alone[i].get(k))
+                assert e <= 1e-8, (i, k, e)
+        Bg.close()
+
+
+def test_batch_member_matches_oracle():
+    fps = [clouds.kovasznay(30, dt=0.4), clouds.kovasznay(30, seed=5, dt=0.4)]
+    B = rbffd.Batch(ctx(), [rbffd.Problem(ctx(), fp) for fp in fps])
+    O = [oracle.Problem(fp, krylov_tol=1e-12) for fp in fps]
+    for r in range(2):
+        d, its, status = B.iterate(0.4)
+        for i, o in enumerate(O):
+            do, _ = o.simple_iterate(0.4)
+            assert abs(d[i] - do) <= 1e-8 * abs(do)
+    for i, o in enumerate(O):
+        for k in ("u", "v", "p"):
+            assert rel_l2(B.problems[i].get(k), o.get(k)) <= 1e-8
+    B.close()
+
+
+def test_batch_active_mask_leaves_others_untouched():
+    fps = [clouds.kovasznay(30, dt=0.4), clouds.kovasznay(30, seed=8, dt=0.4)]
+    B = rbffd.Batch(ctx(), [rbffd.Problem(ctx(), fp) for fp in fps])
+    before = B.problems[1].get("u").copy()
+    d, its, status = B.iterate(0.4, active=[1, 0])
+    assert np.array_equal(B.problems[1].get("u"), before)
+    assert d[0] > 0
+    B.close()
+
+
+def test_batch_many_small_members():
+    """More members than SMs: every member gets at least one CTA."""
+    fps = [clouds.kovasznay(12 + (i % 5), seed=100 + i, dt=0.05) for i in range(200)]
+    probs = [rbffd.Problem(ctx(), fp) for fp in fps]
+    B = rbffd.Batch(ctx(), probs)
+    d, its, status = B.iterate(0.05)
+    assert np.all(status == 0)
+    # spot-check a few members against a solo solve
+    for i in (0, 57, 199):
+        solo = rbffd.Problem(ctx(), fps[i])
+        ds, _ = solo.simple_iterate(0.05)
+        assert abs(ds - d[i]) <= 1e-8 * abs(ds)
+        assert rel_l2(probs[i].get("p"), solo.get("p")) <= 1e-8
+    B.close()
