@@ -341,6 +341,47 @@ int rbffd_batch_iterate(rbffd_batch *batch, const rbffd_step_params *params,
                         const int32_t *active, double *deltas, rbffd_iter_stats *stats,
                         int32_t *status);
 
+/* -------------------------------------------------------------- serving */
+
+/* A request server with continuous batching (the serving workload; the
+ * paper solves one problem at a time).  Requests are steady solves
+ * (solve_steady semantics, RBFFD_PREC_FP64), submitted from any thread.  A
+ * worker thread owns the context's stream (give the server a context of its
+ * own) and loops: admit queued requests while the context's HBM budget
+ * allows (a request is admitted by building its problem; one that does not
+ * fit waits for running requests to finish), run one outer iteration of
+ * every running request together (as rbffd_batch_iterate), apply each
+ * request's time-step logic and steady-residual test, and retire finished
+ * requests with their fields copied to host memory.  Requests join and
+ * leave at outer-iteration boundaries. */
+typedef struct rbffd_server rbffd_server;
+typedef struct {
+  size_t hbm_budget_bytes; /* admission budget (0: 80% of the free HBM at create) */
+  int32_t max_active;      /* cap on running requests (0: what one launch holds) */
+} rbffd_server_params;
+typedef struct {
+  int32_t state;        /* 0 queued, 1 running, 2 done */
+  int32_t status;       /* when done: RBFFD_OK, or the error that ended it */
+  double queue_s;       /* arrival -> admission (seconds) */
+  double latency_s;     /* arrival -> result (seconds), when done */
+  int32_t steps;        /* time steps taken */
+  int64_t outer_iters;  /* outer iterations taken */
+  double resid[3];      /* R_m, R_c, R at the last step */
+} rbffd_result;
+int rbffd_server_create(rbffd_ctx *ctx, const rbffd_server_params *params, rbffd_server **out);
+/* desc arrays are host pointers, copied before the call returns; ticket
+ * (host) identifies the request.  Errors: RBFFD_EINVAL. */
+int rbffd_server_submit(rbffd_server *server, const rbffd_problem_desc *desc,
+                        const rbffd_solve_params *params, uint64_t *ticket);
+/* Thread-safe.  result: host.  u, v, p: host double[n] (nullable), filled
+ * when the request is done with status RBFFD_OK. */
+int rbffd_server_poll(rbffd_server *server, uint64_t ticket, rbffd_result *result, double *u,
+                      double *v, double *p);
+/* Block until every submitted request is done. */
+int rbffd_server_drain(rbffd_server *server);
+/* Finishes the submitted requests, then stops the worker and frees all. */
+void rbffd_server_destroy(rbffd_server *server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "librbffd.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 
 SOURCES = ["context.cu", "knn.cu", "weights.cu", "krylov.cu", "krylov_mixed.cu", "ops.cu",
-           "problem.cu", "batch.cu"]
+           "problem.cu", "batch.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
           "--expt-relaxed-constexpr"]
@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nv, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-               "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+               "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-lpthread"]
         run(cmd)
         os.replace(tmp, LIB)
     return LIB

@@ -155,8 +155,9 @@ static int launch_krylov(BatchScratch &S, int nr, std::vector<KrylovArgs> &args,
   return RBFFD_OK;
 }
 
-int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m, const rbffd_step_params *sp,
-                  double *deltas, rbffd_iter_stats *stats, int *status) {
+int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
+                  const rbffd_step_params *const *spv, double *deltas, rbffd_iter_stats *stats,
+                  int *status) {
   if (m <= 0) return RBFFD_OK;
   rbffd_ctx *ctx = P[0]->ctx;
   for (int i = 0; i < m; ++i) {
@@ -171,6 +172,7 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m, const rbffd_s
   // momentum predictor of every member, then one launch for all the solves
   std::vector<KrylovArgs> a2(m), a1(m);
   for (int i = 0; i < m; ++i) {
+    const rbffd_step_params *sp = spv[i];
     RBFFD_TRY(ops_momentum(P[i], sp));
     KrylovArgs &a = a2[i];
     memset(&a, 0, sizeof(a));
@@ -196,7 +198,7 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m, const rbffd_s
   RBFFD_TRY(launch_krylov(S, 2, a2, rows));
   prof_end(ctx, 0);
   for (int i = 0; i < m; ++i) {
-    RBFFD_TRY(ops_divergence(P[i], sp));
+    RBFFD_TRY(ops_divergence(P[i], spv[i]));
     a1[i] = a2[i];
     a1[i].val = P[i]->Pp;
     a1[i].dinv = P[i]->p_dinv;
@@ -211,8 +213,8 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m, const rbffd_s
   RBFFD_TRY(launch_krylov(S, 1, a1, rows));
   prof_end(ctx, 1);
   for (int i = 0; i < m; ++i) {
-    RBFFD_TRY(ops_pressure(P[i], sp));
-    RBFFD_TRY(ops_correct(P[i], sp));
+    RBFFD_TRY(ops_pressure(P[i], spv[i]));
+    RBFFD_TRY(ops_correct(P[i], spv[i]));
   }
   // gather every member's Delta and Krylov outcome with one read-back
   char *hb = (char *)S.hmem;
@@ -312,8 +314,9 @@ extern "C" int rbffd_batch_iterate(rbffd_batch *b, const rbffd_step_params *sp,
   std::vector<double> d(act.size());
   std::vector<rbffd_iter_stats> st(act.size());
   std::vector<int> sts(act.size());
-  int rc = batch_iterate(b->scratch, act.data(), (int)act.size(), sp, d.data(), st.data(),
-                         sts.data());
+  std::vector<const rbffd_step_params *> spv(act.size(), sp);
+  int rc = batch_iterate(b->scratch, act.data(), (int)act.size(), spv.data(), d.data(),
+                         st.data(), sts.data());
   if (rc != RBFFD_OK) return rc;
   int worst = RBFFD_OK;
   for (size_t k = 0; k < act.size(); ++k) {

@@ -22,7 +22,10 @@ struct BatchScratch {
 // all FP64 and on one context.  deltas, stats, status: host arrays of m
 // (nullable).  With status, per-member solver failures are reported there
 // and the call returns RBFFD_OK; without it, the first failure is returned.
-int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m, const rbffd_step_params *sp,
-                  double *deltas, rbffd_iter_stats *stats, int *status);
+// spv[i]: the step parameters of member i (dt may differ per member; the
+// Krylov tolerance and cap of member 0 apply to all).
+int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
+                  const rbffd_step_params *const *spv, double *deltas, rbffd_iter_stats *stats,
+                  int *status);
 
 }  // namespace rbffd

@@ -483,6 +483,17 @@ extern "C" int rbffd_time_step(rbffd_problem *P, const rbffd_solve_params *s, do
   return RBFFD_OK;
 }
 
+namespace rbffd {
+// End of a time step: [u^{n-1}, u^n] <- [u^n, u], and the step's change.
+int problem_step_end(rbffd_problem *P, double *change) {
+  RBFFD_TRY(ops_rotate(P));
+  Readback r;
+  RBFFD_TRY(read_back(P, &r));
+  if (change) *change = r.rec.change;
+  return RBFFD_OK;
+}
+}  // namespace rbffd
+
 extern "C" int rbffd_steady_residual(rbffd_problem *P, double *R3) {
   if (!P || !R3) return RBFFD_EINVAL;
   RBFFD_CK(cudaSetDevice(P->ctx->device));

@@ -54,3 +54,9 @@ struct rbffd_problem {
   void *mem = nullptr;
   size_t bytes = 0;
 };
+
+namespace rbffd {
+// End of a BDF2 time step (rotation of the time levels); change = mean
+// |u - u^n| + mean |v - v^n| of the step.  Synchronises the stream.
+int problem_step_end(rbffd_problem *P, double *change);
+}  // namespace rbffd

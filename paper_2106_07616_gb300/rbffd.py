@@ -70,6 +70,16 @@ class KernelStat(C.Structure):
 
 KSTAT = {"krylov_p": 0, "krylov_mom": 1, "weights": 2, "knn": 3, "outer": 4}
 
+class ServerParams(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("queue_s", C.c_double),
+                ("latency_s", C.c_double), ("steps", C.c_int32), ("outer_iters", C.c_int64),
+                ("resid", C.c_double * 3)]
+
+
 STEP_CB = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int32, C.c_double)
 
 _lib = None
@@ -114,6 +124,12 @@ def load(path: str = LIB_PATH):
         "rbffd_batch_create": (C.c_int, [vp, i32, C.POINTER(vp), C.POINTER(vp)]),
         "rbffd_batch_destroy": (None, [vp]),
         "rbffd_batch_iterate": (C.c_int, [vp, C.POINTER(StepParams), vp, vp, vp, vp]),
+        "rbffd_server_create": (C.c_int, [vp, C.POINTER(ServerParams), C.POINTER(vp)]),
+        "rbffd_server_submit": (C.c_int, [vp, C.POINTER(ProblemDesc), C.POINTER(SolveParams),
+                                          C.POINTER(C.c_uint64)]),
+        "rbffd_server_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(Result), vp, vp, vp]),
+        "rbffd_server_drain": (C.c_int, [vp]),
+        "rbffd_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -369,6 +385,59 @@ class Batch:
                "rbffd_batch_iterate")
         its = np.array([list(s.iters) for s in st])
         return d, its, status
+
+
+class Server:
+    """Continuous-batching request server (steady solves)."""
+
+    def __init__(self, ctx, hbm_budget=0, max_active=0):
+        self.ctx = ctx
+        prm = ServerParams(hbm_budget, max_active)
+        h = C.c_void_p()
+        _check(load().rbffd_server_create(ctx.h, C.byref(prm), C.byref(h)), "rbffd_server_create")
+        self.h = h
+        self.n = {}
+
+    def submit(self, fp, dt=None, resid_tol=1e-6, max_steps=2000, max_outer=20,
+               krylov_tol=1e-12, krylov_maxit=10000):
+        keep = {}
+        d = make_desc(fp, PREC_FP64, keep)
+        sp = SolveParams(fp.dt if dt is None else dt, resid_tol, max_steps, max_outer,
+                         krylov_tol, krylov_maxit, 0.0, 0)
+        t = C.c_uint64(0)
+        _check(load().rbffd_server_submit(self.h, C.byref(d), C.byref(sp), C.byref(t)),
+               "rbffd_server_submit")
+        self.n[t.value] = fp.n
+        return t.value
+
+    def poll(self, ticket, fields=False):
+        r = Result()
+        n = self.n[ticket]
+        u = v = p = None
+        if fields:
+            u, v, p = np.zeros(n), np.zeros(n), np.zeros(n)
+        _check(load().rbffd_server_poll(self.h, ticket, C.byref(r), ptr(u), ptr(v), ptr(p)),
+               "rbffd_server_poll")
+        out = {"state": r.state, "status": r.status, "queue_s": r.queue_s,
+               "latency_s": r.latency_s, "steps": r.steps, "outer": r.outer_iters,
+               "resid": list(r.resid)}
+        if fields:
+            out.update(u=u, v=v, p=p)
+        return out
+
+    def drain(self):
+        _check(load().rbffd_server_drain(self.h), "rbffd_server_drain")
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            load().rbffd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _stats(st):
