@@ -75,6 +75,148 @@ def krylov_traffic(precision):
         return None
 
 
+def batch_instances(count=256, seed=4):
+    """Batched workload: independent Kovasznay / cavity instances, N
+    log-uniform on [1k, 64k] (square lattices), degree uniform in {2,3,4,5},
+    q = 2m, dt from a Courant number of about 10."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        n = float(np.exp(rng.uniform(np.log(1000.0), np.log(64000.0))))
+        side = int(np.ceil(np.sqrt(n)))
+        k = int(rng.integers(2, 6))
+        q = (k + 1) * (k + 2)
+        if rng.uniform() < 0.5:
+            out.append(clouds.kovasznay(side, seed=4000 + i, degree=k, q=q, dt=20.0 / (side - 1)))
+        else:
+            out.append(clouds.cavity(side, seed=4000 + i, degree=k, q=q, dt=10.0 / (side - 1)))
+    return out
+
+
+def run_batch(args):
+    """Many instances per step: S1-S3 for every member, then one batched
+    outer iteration (both Krylov solves of all members in one launch each)."""
+    import torch
+
+    from paper_2106_07616_gb300 import _build, rbffd
+    _build.build()
+    fps = batch_instances(args.count)
+    stream = torch.cuda.current_stream()
+    ctx = rbffd.Context(0, stream=stream.cuda_stream)
+    probs = [rbffd.Problem(ctx, fp) for fp in fps]
+    B = rbffd.Batch(ctx, probs)
+    rows = sum(fp.n for fp in fps)
+    nnz = sum(fp.n * fp.q for fp in fps)
+
+    dts = np.array([fp.dt for fp in fps])
+
+    def iterate_all():
+        d, its, st = B.iterate(dts)  # every member with its own dt, one launch per solve
+        return its, int(np.sum(st == 0))
+
+    for _ in range(args.warmup):
+        for P, fp in zip(probs, fps):
+            P.reload(fp)
+        iterate_all()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    total_ms, outer = 0.0, 0
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for P, fp in zip(probs, fps):
+                P.reload(fp)
+            its, ok = iterate_all()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            outer += ok
+    kp = ctx.kernel_stat("krylov_p")
+    km = ctx.kernel_stat("krylov_mom")
+    ctx.profile(False)
+    peak, src = read_peaks()
+    out = {"metric": "SIMPLE outer iters/s (batched instances)", "value": outer / (total_ms / 1e3),
+           "unit": "instance_outer_iter/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "dtype": "f64",
+           "config": {"workload": f"batch{args.count}", "instances": len(fps), "rows": rows,
+                      "nnz_per_operator": nnz,
+                      "description": "Kovasznay/cavity instances, N log-uniform [1k,64k], "
+                                     "degree {2..5}, q=2m; step = S1-S3 for all + one outer "
+                                     "iteration of all (one batched launch per Krylov solve)"},
+           "krylov_p": {"launches": kp["launches"], "ms": kp["ms"],
+                        "algorithmic_GBps": kp["bytes"] / (kp["ms"] / 1e3) / 1e9 if kp["ms"] else None,
+                        "frac_of_hbm": (kp["bytes"] / (kp["ms"] / 1e3) / 1e9) / peak if kp["ms"] else None},
+           "krylov_mom": {"launches": km["launches"], "ms": km["ms"],
+                          "algorithmic_GBps": km["bytes"] / (km["ms"] / 1e3) / 1e9 if km["ms"] else None},
+           "peak_hbm_GBps": peak, "peak_source": src, "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
+def serve_requests(count, seed=5):
+    """Serving workload: Kovasznay (Re 20-60) and cavity (Re 10-100) steady
+    solves, N log-uniform on [1k, 4k], degree {3, 4}, q = 2m, Poisson
+    arrivals at a mean of 20 per second."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    reqs, t = [], 0.0
+    for i in range(count):
+        t += rng.exponential(1.0 / 20.0)
+        n = float(np.exp(rng.uniform(np.log(1000.0), np.log(4000.0))))
+        side = int(np.ceil(np.sqrt(n)))
+        k = int(rng.integers(3, 5))
+        q = (k + 1) * (k + 2)
+        if rng.uniform() < 0.5:
+            re = float(rng.uniform(20.0, 60.0))
+            fp = clouds.kovasznay(side, seed=5000 + i, degree=k, q=q, re=re,
+                                  dt=20.0 / (side - 1))
+        else:
+            re = float(rng.uniform(10.0, 100.0))
+            fp = clouds.cavity(side, seed=5000 + i, degree=k, q=q, re=re, dt=10.0 / (side - 1))
+        reqs.append((t, fp))
+    return reqs
+
+
+def run_serve(args):
+    import torch  # noqa: F401
+
+    from paper_2106_07616_gb300 import _build, rbffd
+    _build.build()
+    reqs = serve_requests(args.count)
+    ctx = rbffd.Context(0)
+    S = rbffd.Server(ctx)
+    t0 = time.perf_counter()
+    tickets = []
+    for t_arr, fp in reqs:
+        wait = t_arr - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        tickets.append(S.submit(fp, resid_tol=args.resid_tol, max_steps=args.max_steps,
+                                criterion=args.criterion))
+    S.drain()
+    wall = time.perf_counter() - t0
+    res = [S.poll(t) for t in tickets]
+    S.close()
+    ok = [r for r in res if r["status"] == 0]
+    lat = np.array([r["latency_s"] for r in ok]) if ok else np.array([np.nan])
+    fails = [{"status": r["status"], "steps": r["steps"], "outer": r["outer"],
+              "R": r["resid"][2]} for r in res if r["status"] != 0]
+    out = {"metric": "served latency to steady state", "unit": "s",
+           "criterion": ("paper steady error (mean|u^{n+1}-u^n|+mean|v^{n+1}-v^n|)/dt"
+                         if args.criterion == 1 else "steady residual R"),
+           "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+           "solves_per_s": len(ok) / wall, "requests": len(res), "ok": len(ok),
+           "failed": {str(s): sum(1 for r in res if r["status"] == s)
+                      for s in sorted(set(r["status"] for r in res)) if s != 0},
+           "resid_tol": args.resid_tol, "wall_s": wall, "failures": fails[:12],
+           "steps_ok": [r["steps"] for r in ok], "outer_ok": [r["outer"] for r in ok],
+           "config": {"workload": f"serve{args.count}",
+                      "description": "Poisson arrivals 20/s; Kovasznay Re 20-60 / cavity "
+                                     "Re 10-100, N log-uniform [1k,4k], degree {3,4}, q=2m; "
+                                     "continuous batching in one server"}}
+    print(json.dumps(out), flush=True)
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -344,11 +486,20 @@ def main():
     ap.add_argument("--workload", default="cavity200")
     ap.add_argument("--outer", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--count", type=int, default=256, help="instances / requests (batch, serve)")
+    ap.add_argument("--resid-tol", type=float, default=1e-5)
+    ap.add_argument("--criterion", type=int, default=1,
+                    help="serve: 0 = steady residual R, 1 = the paper's steady error change/dt")
+    ap.add_argument("--max-steps", type=int, default=3000)
     ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"],
                     help="Krylov arithmetic: FP32 inside FP64 defect correction, or FP64")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_native(args)
 

@@ -266,6 +266,9 @@ typedef struct {
   int32_t krylov_maxit;
   double inner_tol;       /* as in rbffd_step_params */
   int32_t inner_maxit;
+  int32_t criterion;      /* steady stop: 0 = R <= resid_tol; 1 = the paper's steady
+                             error (Sec. 4.1): (mean|u^{n+1}-u^n| + mean|v^{n+1}-v^n|)/dt
+                             <= resid_tol */
 } rbffd_solve_params;
 
 typedef struct {
@@ -285,8 +288,9 @@ int rbffd_time_step(rbffd_problem *prob, const rbffd_solve_params *params, doubl
 /* Steady solve by BDF2 pseudo-time marching from the current state.  Outer
  * tolerance 1e-4 for the first step, then min(1e-4, dt * eps_s) with
  * dt * eps_s = the change of the previous step (paper Sec. 3.2).  Stops when
- * R = max(R_m, R_c) <= resid_tol (rbffd_steady_residual).  Errors:
- * RBFFD_ENOCONV if max_steps ran out first. */
+ * R = max(R_m, R_c) <= resid_tol (rbffd_steady_residual), or with
+ * criterion 1 when the paper's steady error change/dt <= resid_tol.
+ * Errors: RBFFD_ENOCONV if max_steps ran out first. */
 int solve_steady(rbffd_problem *prob, const rbffd_solve_params *params, rbffd_solve_stats *stats);
 
 /* n_steps BDF2 steps with the same adaptive outer tolerance.  on_step
@@ -330,14 +334,15 @@ typedef struct rbffd_batch rbffd_batch;
 int rbffd_batch_create(rbffd_ctx *ctx, int32_t count, rbffd_problem *const *members,
                        rbffd_batch **out);
 void rbffd_batch_destroy(rbffd_batch *batch);
-/* active: host int32[count] (nullable = all); deltas: host double[count];
+/* dt: host double[count] (nullable): each member's time step in place of
+ * params->dt.  active: host int32[count] (nullable = all); deltas: host double[count];
  * stats: host rbffd_iter_stats[count] (nullable); status: host int32[count]
  * (nullable).  With status, a member whose solve failed reports its code
  * there and the call returns RBFFD_OK; without it the first failure is
  * returned.  Entries of inactive members are left untouched.  Errors:
  * RBFFD_EINVAL if more members are active than one launch holds CTAs
  * (several hundred on a GB300), RBFFD_ECUDA. */
-int rbffd_batch_iterate(rbffd_batch *batch, const rbffd_step_params *params,
+int rbffd_batch_iterate(rbffd_batch *batch, const rbffd_step_params *params, const double *dt,
                         const int32_t *active, double *deltas, rbffd_iter_stats *stats,
                         int32_t *status);
 

@@ -72,6 +72,8 @@ def lib():
         L.orc_steady_residual.argtypes = [C.c_void_p, _dp]
         L.orc_solve_steady.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
                                        _dp]
+        L.orc_solve_steady_c.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
+                                         C.c_int, _dp]
         L.orc_solve_unsteady.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_int, _dp]
         L.orc_apply.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
         L.orc_set_threads.argtypes = [C.c_int]
@@ -214,9 +216,9 @@ class Problem:
         lib().orc_steady_residual(self.h, r)
         return r
 
-    def solve_steady(self, dt, resid_tol=1e-8, max_steps=10000, max_outer=20):
+    def solve_steady(self, dt, resid_tol=1e-8, max_steps=10000, max_outer=20, criterion=0):
         out = np.zeros(4)
-        rc = lib().orc_solve_steady(self.h, dt, resid_tol, max_steps, max_outer, out)
+        rc = lib().orc_solve_steady_c(self.h, dt, resid_tol, max_steps, max_outer, criterion, out)
         return rc, {"steps": int(out[0]), "outer": int(out[1]), "R": out[2], "change": out[3]}
 
     def solve_unsteady(self, dt, n_steps, max_outer=20):

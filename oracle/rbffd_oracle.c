@@ -791,8 +791,17 @@ int orc_steady_residual(orc_problem *P, double *R3) {
 /* tolerance 1e-4 for the first step, then min(1e-4, dt*eps_s) (Sec. 3.2).  */
 /* Stops when R = max(R_m, R_c) <= resid_tol.  out (nullable, 4 entries):   */
 /* steps taken, total outer iterations, final R, final change.             */
+int orc_solve_steady_c(orc_problem *P, double dt, double resid_tol, int max_steps, int max_outer,
+                       int criterion, double *out);
 int orc_solve_steady(orc_problem *P, double dt, double resid_tol, int max_steps, int max_outer,
                      double *out) {
+  return orc_solve_steady_c(P, dt, resid_tol, max_steps, max_outer, 0, out);
+}
+
+/* criterion 0: stop when R <= resid_tol; 1: the paper's steady error of
+ * Sec. 4.1, (mean|u^{n+1}-u^n| + mean|v^{n+1}-v^n|) / dt <= resid_tol. */
+int orc_solve_steady_c(orc_problem *P, double dt, double resid_tol, int max_steps, int max_outer,
+                       int criterion, double *out) {
   double tol = 1e-4, R3[3], R = 1.0, change = 0.0;
   int steps = 0;
   long total_outer = 0;
@@ -808,12 +817,13 @@ int orc_solve_steady(orc_problem *P, double dt, double resid_tol, int max_steps,
     orc_steady_residual(P, R3);
     R = R3[2];
     if (!(R == R)) { rc = ORC_EDIVERGED; break; }
-    if (R <= resid_tol) break;
+    if (criterion == 1 ? change / dt <= resid_tol : R <= resid_tol) break;
   }
   if (out) {
     out[0] = steps; out[1] = (double)total_outer; out[2] = R; out[3] = change;
   }
-  if (rc == ORC_OK && R > resid_tol) rc = ORC_ENOCONV;
+  if (rc == ORC_OK && !(criterion == 1 ? change / dt <= resid_tol : R <= resid_tol))
+    rc = ORC_ENOCONV;
   return rc;
 }
 

@@ -235,6 +235,20 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
                            cudaMemcpyDeviceToHost, ctx->stream));
   RBFFD_CK(cudaStreamSynchronize(ctx->stream));
   const MemberOut *mo = (const MemberOut *)(hb + S.off_out);
+  if (ctx->prof) {
+    // units: rows x iterations of every member (the launch's work)
+    double um = 0, up = 0, bm = 0, bp = 0;
+    for (int i = 0; i < m; ++i) {
+      const double n = P[i]->n, q = P[i]->q;
+      const double im = std::max(mo[i].iters[0], mo[i].iters[1]), ip = mo[i].iters[2];
+      um += n * im;
+      up += n * ip;
+      bm += n * im * (2 * q * 12.0 + 28 * 8.0);
+      bp += n * ip * (2 * q * 12.0 + 14 * 8.0);
+    }
+    prof_collect(ctx, 0, RBFFD_KSTAT_KRYLOV_MOM, um, bm);
+    prof_collect(ctx, 1, RBFFD_KSTAT_KRYLOV_P, up, bp);
+  }
   int rc = RBFFD_OK;
   for (int i = 0; i < m; ++i) {
     if (deltas) deltas[i] = mo[i].delta;
@@ -297,7 +311,7 @@ extern "C" void rbffd_batch_destroy(rbffd_batch *b) {
 }
 
 extern "C" int rbffd_batch_iterate(rbffd_batch *b, const rbffd_step_params *sp,
-                                   const int32_t *active, double *deltas,
+                                   const double *dt, const int32_t *active, double *deltas,
                                    rbffd_iter_stats *stats, int32_t *status) {
   if (!b || !sp) return RBFFD_EINVAL;
   if (!(sp->dt > 0) || !(sp->krylov_tol > 0) || sp->krylov_maxit < 1 || sp->alpha[0] == 0.0)
@@ -314,7 +328,15 @@ extern "C" int rbffd_batch_iterate(rbffd_batch *b, const rbffd_step_params *sp,
   std::vector<double> d(act.size());
   std::vector<rbffd_iter_stats> st(act.size());
   std::vector<int> sts(act.size());
-  std::vector<const rbffd_step_params *> spv(act.size(), sp);
+  std::vector<rbffd_step_params> own(act.size(), *sp);
+  std::vector<const rbffd_step_params *> spv(act.size());
+  for (size_t k = 0; k < act.size(); ++k) {
+    if (dt) {
+      if (!(dt[where[k]] > 0)) return RBFFD_EINVAL;
+      own[k].dt = dt[where[k]];
+    }
+    spv[k] = &own[k];
+  }
   int rc = batch_iterate(b->scratch, act.data(), (int)act.size(), spv.data(), d.data(),
                          st.data(), sts.data());
   if (rc != RBFFD_OK) return rc;

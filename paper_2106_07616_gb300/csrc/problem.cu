@@ -504,6 +504,15 @@ extern "C" int rbffd_steady_residual(rbffd_problem *P, double *R3) {
   return RBFFD_OK;
 }
 
+namespace rbffd {
+// The steady test: R <= tol, or (criterion 1) the paper's steady error
+// change / dt <= tol.
+bool steady_done(const rbffd_solve_params *s, double R, double change) {
+  if (s->criterion == 1) return change / s->dt <= s->resid_tol;
+  return R <= s->resid_tol;
+}
+}  // namespace rbffd
+
 static int march(rbffd_problem *P, const rbffd_solve_params *s, int32_t n_steps, bool steady,
                  int (*on_step)(void *, int32_t, double), void *user, rbffd_solve_stats *st) {
   if (!P || !s || !(s->dt > 0) || s->max_outer < 1) return RBFFD_EINVAL;
@@ -541,7 +550,7 @@ static int march(rbffd_problem *P, const rbffd_solve_params *s, int32_t n_steps,
         rc = RBFFD_EDIVERGED;
         break;
       }
-      if (loc.resid[2] <= s->resid_tol) break;
+      if (steady_done(s, loc.resid[2], loc.change)) break;
     }
     if (on_step) {
       int u = on_step(user, k + 1, (k + 1) * s->dt);
@@ -551,9 +560,9 @@ static int march(rbffd_problem *P, const rbffd_solve_params *s, int32_t n_steps,
       }
     }
   }
-  if (rc == RBFFD_OK && steady && !(loc.resid[2] <= s->resid_tol)) {
-    set_error("steady residual %.3e above %.3e after %d steps", loc.resid[2], s->resid_tol,
-              loc.steps);
+  if (rc == RBFFD_OK && steady && !steady_done(s, loc.resid[2], loc.change)) {
+    set_error("steady test (criterion %d) not met after %d steps: R %.3e, change/dt %.3e",
+              s->criterion, loc.steps, loc.resid[2], loc.change / s->dt);
     rc = RBFFD_ENOCONV;
   }
   if (st) *st = loc;

@@ -59,4 +59,6 @@ namespace rbffd {
 // End of a BDF2 time step (rotation of the time levels); change = mean
 // |u - u^n| + mean |v - v^n| of the step.  Synchronises the stream.
 int problem_step_end(rbffd_problem *P, double *change);
+// Steady stopping test of solve_steady and of the request server.
+bool steady_done(const rbffd_solve_params *s, double R, double change);
 }  // namespace rbffd

@@ -157,7 +157,7 @@ struct rbffd_server {
         r->steps++;
         r->outer_in_step = 0;
         r->tol = change < 1e-4 ? change : 1e-4;
-        if (r->resid[2] <= r->sp.resid_tol) {
+        if (steady_done(&r->sp, r->resid[2], change)) {
           finish(r, RBFFD_OK);
           continue;
         }

@@ -54,7 +54,7 @@ class SolveParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("resid_tol", C.c_double), ("max_steps", C.c_int32),
                 ("max_outer", C.c_int32), ("krylov_tol", C.c_double),
                 ("krylov_maxit", C.c_int32), ("inner_tol", C.c_double),
-                ("inner_maxit", C.c_int32)]
+                ("inner_maxit", C.c_int32), ("criterion", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -123,7 +123,7 @@ def load(path: str = LIB_PATH):
         "rbffd_apply": (C.c_int, [vp, i32, vp, vp]),
         "rbffd_batch_create": (C.c_int, [vp, i32, C.POINTER(vp), C.POINTER(vp)]),
         "rbffd_batch_destroy": (None, [vp]),
-        "rbffd_batch_iterate": (C.c_int, [vp, C.POINTER(StepParams), vp, vp, vp, vp]),
+        "rbffd_batch_iterate": (C.c_int, [vp, C.POINTER(StepParams), vp, vp, vp, vp, vp]),
         "rbffd_server_create": (C.c_int, [vp, C.POINTER(ServerParams), C.POINTER(vp)]),
         "rbffd_server_submit": (C.c_int, [vp, C.POINTER(ProblemDesc), C.POINTER(SolveParams),
                                           C.POINTER(C.c_uint64)]),
@@ -316,7 +316,8 @@ class Problem:
 
     def time_step(self, dt, tol_outer, max_outer=20, krylov_tol=1e-12, krylov_maxit=10000,
                   inner_tol=0.0, inner_maxit=0):
-        sp = SolveParams(dt, 0.0, 1, max_outer, krylov_tol, krylov_maxit, inner_tol, inner_maxit)
+        sp = SolveParams(dt, 0.0, 1, max_outer, krylov_tol, krylov_maxit, inner_tol, inner_maxit,
+                         0)
         it = C.c_int32(0)
         ch = C.c_double(0)
         _check(load().rbffd_time_step(self.h, C.byref(sp), tol_outer, C.byref(it), C.byref(ch)),
@@ -329,9 +330,9 @@ class Problem:
         return np.array(list(r))
 
     def solve_steady(self, dt, resid_tol=1e-8, max_steps=10000, max_outer=20, krylov_tol=1e-12,
-                     krylov_maxit=10000, check=True, inner_tol=0.0, inner_maxit=0):
+                     krylov_maxit=10000, check=True, inner_tol=0.0, inner_maxit=0, criterion=0):
         sp = SolveParams(dt, resid_tol, max_steps, max_outer, krylov_tol, krylov_maxit, inner_tol,
-                         inner_maxit)
+                         inner_maxit, criterion)
         st = SolveStats()
         rc = load().solve_steady(self.h, C.byref(sp), C.byref(st))
         if check:
@@ -340,7 +341,8 @@ class Problem:
 
     def solve_unsteady(self, dt, n_steps, max_outer=20, krylov_tol=1e-12, krylov_maxit=10000,
                        on_step=None, inner_tol=0.0, inner_maxit=0):
-        sp = SolveParams(dt, 0.0, 0, max_outer, krylov_tol, krylov_maxit, inner_tol, inner_maxit)
+        sp = SolveParams(dt, 0.0, 0, max_outer, krylov_tol, krylov_maxit, inner_tol, inner_maxit,
+                         0)
         st = SolveStats()
         cb = STEP_CB(on_step) if on_step is not None else STEP_CB()
         _check(load().solve_unsteady(self.h, C.byref(sp), int(n_steps), cb, None, C.byref(st)),
@@ -374,13 +376,18 @@ class Batch:
 
     def iterate(self, dt, active=None, alpha=(1.5, -2.0, 0.5), krylov_tol=1e-12,
                 krylov_maxit=10000):
+        """dt: one time step for all members, or one per member."""
         m = len(self.problems)
+        per = None
+        if np.ndim(dt) > 0:
+            per = np.ascontiguousarray(dt, np.float64)
+            dt = float(per[0])
         sp = StepParams(dt, (C.c_double * 3)(*alpha), krylov_tol, krylov_maxit, 0.0, 0)
         act = None if active is None else np.ascontiguousarray(active, np.int32)
         d = np.zeros(m)
         st = (IterStats * m)()
         status = np.zeros(m, np.int32)
-        _check(load().rbffd_batch_iterate(self.h, C.byref(sp), ptr(act), ptr(d),
+        _check(load().rbffd_batch_iterate(self.h, C.byref(sp), ptr(per), ptr(act), ptr(d),
                                           C.cast(st, C.c_void_p), ptr(status)),
                "rbffd_batch_iterate")
         its = np.array([list(s.iters) for s in st])
@@ -399,11 +406,11 @@ class Server:
         self.n = {}
 
     def submit(self, fp, dt=None, resid_tol=1e-6, max_steps=2000, max_outer=20,
-               krylov_tol=1e-12, krylov_maxit=10000):
+               krylov_tol=1e-12, krylov_maxit=10000, criterion=0):
         keep = {}
         d = make_desc(fp, PREC_FP64, keep)
         sp = SolveParams(fp.dt if dt is None else dt, resid_tol, max_steps, max_outer,
-                         krylov_tol, krylov_maxit, 0.0, 0)
+                         krylov_tol, krylov_maxit, 0.0, 0, criterion)
         t = C.c_uint64(0)
         _check(load().rbffd_server_submit(self.h, C.byref(d), C.byref(sp), C.byref(t)),
                "rbffd_server_submit")

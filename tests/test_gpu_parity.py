@@ -154,6 +154,20 @@ def test_solve_steady_reaches_tolerance_like_oracle():
     assert rel_l2(P.get("u"), O.get("u")) < 1e-3
 
 
+def test_solve_steady_paper_criterion_like_oracle():
+    """Stopping on the paper's steady error (change / dt, Sec. 4.1) gives the
+    oracle's step count within one and the same state."""
+    fp = clouds.kovasznay(30, dt=0.4)
+    P, O = _pair(fp, tol=1e-10)
+    rc, sg = P.solve_steady(fp.dt, resid_tol=2e-3, max_steps=400, krylov_tol=1e-10,
+                            criterion=1)
+    rco, so = O.solve_steady(fp.dt, resid_tol=2e-3, max_steps=400, criterion=1)
+    assert rco == 0
+    assert sg["change"] / fp.dt <= 2e-3
+    assert abs(sg["steps"] - so["steps"]) <= 1
+    assert rel_l2(P.get("u"), O.get("u")) < 1e-3
+
+
 def test_reload_resets_and_matches_fresh():
     fp = clouds.kovasznay(30, dt=0.4)
     P = rbffd.Problem(ctx(), fp)

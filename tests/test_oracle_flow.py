@@ -100,3 +100,29 @@ def test_kovasznay_marches_toward_closed_form():
     assert rc == 0, info
     err = np.abs(P.get("u") - fp.exact["u"]).max()
     assert err < 0.06, err
+
+
+def test_steady_error_criterion_matches_manual_march():
+    """The paper's steady-state test (Sec. 4.1): stop once the mean change
+    of u and v between consecutive steps, divided by dt, is below the
+    tolerance.  A march driven one time step at a time, with the outer
+    tolerance rule of Sec. 3.2 and that stopping test, takes the same number
+    of steps and lands on the same fields."""
+    fp = clouds.kovasznay(30, dt=0.4)
+    tol = 2e-3
+    A = oracle.Problem(fp, krylov_tol=1e-10)
+    rc, info = A.solve_steady(fp.dt, resid_tol=tol, max_steps=400, max_outer=20, criterion=1)
+    assert rc == 0, info
+    assert info["change"] / fp.dt <= tol
+    B = oracle.Problem(fp, krylov_tol=1e-10)
+    tol_outer, steps = 1e-4, 0
+    while True:
+        _, change, _ = B.time_step(fp.dt, tol_outer, 20)
+        steps += 1
+        tol_outer = min(1e-4, change)
+        if change / fp.dt <= tol:
+            break
+        assert steps < 400
+    assert steps == info["steps"]
+    for k in ("u", "v", "p"):
+        np.testing.assert_array_equal(A.get(k), B.get(k))
