@@ -190,7 +190,7 @@ class Problem:
 
     def apply(self, which, x):
         y = np.zeros(self.n)
-        lib().orc_apply(self.h, {"dx": 0, "dy": 1, "lap": 2, "pp": 3, "mom": 4}[which], _f64(x), y)
+        lib().orc_apply(self.h, {"dx": 0, "dy": 1, "lap": 2, "pp": 3, "mom": 4, "momv": 5}[which], _f64(x), y)
         return y
 
     def simple_iterate(self, dt, alpha=(1.5, -2.0, 0.5)):

@@ -55,7 +55,9 @@
 #define ORC_EDIVERGED -5
 
 #define TAG_INTERIOR 0
-#define TAG_DIRICHLET 1
+#define TAG_DIRICHLET 1 /* wall / inlet: u, v prescribed */
+#define TAG_OUTFLOW 2   /* fixed-pressure outlet: p held, p' = 0, du/dn = dv/dn = 0 */
+#define TAG_SYMMETRY 3  /* symmetry line: normal velocity prescribed, tangential d/dn = 0 */
 
 /* ------------------------------------------------------------------------ */
 /* Sec. 2, below Eq. (RBF_interp_poly): m = C(k+d, k) monomials for d = 2.   */
@@ -431,7 +433,7 @@ typedef struct {
   int32_t *idx;
   double *wx, *wy, *wl;
   int64_t *rowptr;
-  csr_t Dx, Dy, Dl, Pp, Am; /* Pp: pressure-correction matrix; Am: momentum */
+  csr_t Dx, Dy, Dl, Pp, Am, Av; /* Pp: pressure correction; Am, Av: momentum u, v */
   /* fields: iterate (u, v, p) and the two previous time levels */
   double *u, *v, *p, *un, *vn, *unm1, *vnm1;
   /* work */
@@ -460,7 +462,7 @@ void orc_problem_destroy(orc_problem *P) {
   if (!P) return;
   free(P->x); free(P->y); free(P->nx); free(P->ny); free(P->ubc); free(P->vbc); free(P->tag);
   free(P->idx); free(P->wx); free(P->wy); free(P->wl); free(P->rowptr);
-  free(P->Pp.val); free(P->Am.val);
+  free(P->Pp.val); free(P->Am.val); free(P->Av.val);
   free(P->u); free(P->v); free(P->p); free(P->un); free(P->vn); free(P->unm1); free(P->vnm1);
   free(P->ut); free(P->vt); free(P->pc); free(P->bu); free(P->bv); free(P->bp);
   free(P->w1); free(P->w2); free(P->w3); free(P->w4);
@@ -469,18 +471,28 @@ void orc_problem_destroy(orc_problem *P) {
 
 /* Build stencils, weights, the operator CSR matrices and the pressure-      */
 /* correction matrix (Sec. 3.1): interior rows = Laplacian weights; rows at  */
-/* walls/inlets (velocity prescribed) = homogeneous Neumann n.grad p' = 0,   */
-/* i.e. nx*Wx + ny*Wy.  With Neumann rows only, p' is defined up to a       */
-/* constant; the Neumann row of one boundary point (pin) is replaced by the */
-/* identity with a zero right-hand side, which fixes that constant.         */
+/* walls, inlets and symmetry lines = homogeneous Neumann n.grad p' = 0,     */
+/* i.e. nx*Wx + ny*Wy; rows at fixed-pressure outlets = identity (p' = 0).   */
+/* With Neumann rows only, p' is defined up to a constant; the Neumann row  */
+/* of one boundary point (pin) is then replaced by the identity with a zero */
+/* right-hand side, which fixes that constant.  pin = -1 is allowed when an */
+/* outlet point exists.  Symmetry points need an axis-aligned normal (the   */
+/* normal velocity component is then u or v).                               */
 int orc_problem_create(int n, int q, int degree, const double *x, const double *y,
                        const int8_t *tag, const double *nx, const double *ny, const double *ubc,
                        const double *vbc, int pin, double rho, double mu, orc_problem **out,
                        int32_t *first_singular) {
   *out = NULL;
   int m = orc_num_monomials(degree);
-  if (n <= 0 || q <= 0 || q > n || q < m || pin < 0 || pin >= n) return ORC_EINVAL;
-  if (tag[pin] == TAG_INTERIOR) return ORC_EINVAL;
+  if (n <= 0 || q <= 0 || q > n || q < m || pin < -1 || pin >= n) return ORC_EINVAL;
+  int n_out = 0;
+  for (int i = 0; i < n; ++i) {
+    if (tag[i] < TAG_INTERIOR || tag[i] > TAG_SYMMETRY) return ORC_EINVAL;
+    if (tag[i] == TAG_OUTFLOW) n_out++;
+    if (tag[i] == TAG_SYMMETRY && fabs(nx[i]) > 1e-12 && fabs(ny[i]) > 1e-12) return ORC_EINVAL;
+  }
+  if (pin < 0 && n_out == 0) return ORC_EINVAL;
+  if (pin >= 0 && (tag[pin] == TAG_INTERIOR || tag[pin] == TAG_OUTFLOW)) return ORC_EINVAL;
   orc_problem *P = (orc_problem *)calloc(1, sizeof(orc_problem));
   if (!P) return ORC_ENOMEM;
   P->n = n; P->q = q; P->degree = degree; P->pin = pin; P->rho = rho; P->mu = mu;
@@ -492,14 +504,15 @@ int orc_problem_create(int n, int q, int degree, const double *x, const double *
   P->idx = (int32_t *)calloc(nq, sizeof(int32_t));
   P->wx = dvec((int)nq); P->wy = dvec((int)nq); P->wl = dvec((int)nq);
   P->rowptr = (int64_t *)calloc(n + 1, sizeof(int64_t));
-  double *pval = dvec((int)nq), *mval = dvec((int)nq);
+  double *pval = dvec((int)nq), *mval = dvec((int)nq), *vval = dvec((int)nq);
   P->u = dvec(n); P->v = dvec(n); P->p = dvec(n); P->un = dvec(n); P->vn = dvec(n);
   P->unm1 = dvec(n); P->vnm1 = dvec(n);
   P->ut = dvec(n); P->vt = dvec(n); P->pc = dvec(n); P->bu = dvec(n); P->bv = dvec(n);
   P->bp = dvec(n); P->w1 = dvec(n); P->w2 = dvec(n); P->w3 = dvec(n); P->w4 = dvec(n);
-  P->Pp.val = pval; P->Am.val = mval;
+  P->Pp.val = pval; P->Am.val = mval; P->Av.val = vval;
   if (!P->x || !P->y || !P->nx || !P->ny || !P->ubc || !P->vbc || !P->tag || !P->idx ||
-      !P->wx || !P->wy || !P->wl || !P->rowptr || !pval || !mval || !P->u || !P->v || !P->p ||
+      !P->wx || !P->wy || !P->wl || !P->rowptr || !pval || !mval || !vval || !P->u || !P->v ||
+      !P->p ||
       !P->un || !P->vn || !P->unm1 || !P->vnm1 || !P->ut || !P->vt || !P->pc || !P->bu ||
       !P->bv || !P->bp || !P->w1 || !P->w2 || !P->w3 || !P->w4) {
     orc_problem_destroy(P);
@@ -520,10 +533,11 @@ int orc_problem_create(int n, int q, int degree, const double *x, const double *
   P->Dl = base; P->Dl.val = P->wl;
   P->Pp.n = n; P->Pp.rowptr = P->rowptr; P->Pp.col = P->idx;
   P->Am.n = n; P->Am.rowptr = P->rowptr; P->Am.col = P->idx;
+  P->Av.n = n; P->Av.rowptr = P->rowptr; P->Av.col = P->idx;
   for (int i = 0; i < n; ++i)
     for (int64_t e = P->rowptr[i]; e < P->rowptr[i + 1]; ++e) {
       double val;
-      if (i == pin)
+      if (i == pin || tag[i] == TAG_OUTFLOW)
         val = (P->idx[e] == i) ? 1.0 : 0.0;
       else if (tag[i] == TAG_INTERIOR)
         val = P->wl[e];
@@ -592,6 +606,28 @@ void orc_set_krylov(orc_problem *P, double tol, int maxit) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Kind of the momentum row of point i for velocity component c (0 = u,     */
+/* 1 = v), Sec. 3.3: the equation itself inside; an identity row with the   */
+/* boundary value where the component is prescribed (walls, inlets, the     */
+/* normal component on a symmetry line); a zero normal derivative           */
+/* n.grad = 0 at outlets and for the tangential component on a symmetry     */
+/* line.                                                                    */
+#define ROW_EQ 0
+#define ROW_ID 1
+#define ROW_NEU 2
+static int row_kind(const orc_problem *P, int i, int c) {
+  switch (P->tag[i]) {
+    case TAG_INTERIOR: return ROW_EQ;
+    case TAG_OUTFLOW: return ROW_NEU;
+    case TAG_SYMMETRY: {
+      int normal_c = fabs(P->nx[i]) > fabs(P->ny[i]) ? 0 : 1;
+      return c == normal_c ? ROW_ID : ROW_NEU;
+    }
+    default: return ROW_ID;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* One outer iteration, Sec. 3.2 steps 2-7, BDF2 coefficients a1, a2, a3.   */
 /* stats (nullable, 6 entries): momentum u iters, v iters, p' iters, and     */
 /* their final relative residuals.                                           */
@@ -603,26 +639,34 @@ int orc_simple_iterate(orc_problem *P, double dt, double a1, double a2, double a
   int rc;
   /* Step 2, Eqs. (u:tilde), (v:tilde): linearised momentum, advection with  */
   /* the previous iterate u^r, diffusion implicit, pressure gradient at p^r. */
-  /* Rows at prescribed-velocity points are identity rows with the BC value. */
+  /* Boundary rows by row_kind: identity with the BC value, or n.grad = 0.  */
   csr_spmv(&P->Dx, P->p, P->w1); /* (dp/dx)^r */
   csr_spmv(&P->Dy, P->p, P->w2); /* (dp/dy)^r */
   for (int i = 0; i < n; ++i) {
-    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
-      double val;
-      if (P->tag[i] == TAG_INTERIOR) {
-        val = rho * P->u[i] * P->wx[e] + rho * P->v[i] * P->wy[e] - mu * P->wl[e];
-        if (P->idx[e] == i) val = val + rho * a1 / dt;
-      } else {
-        val = (P->idx[e] == i) ? 1.0 : 0.0;
+    for (int c = 0; c < 2; ++c) {
+      int kind = row_kind(P, i, c);
+      double *val = c == 0 ? P->Am.val : P->Av.val;
+      for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+        double a;
+        if (kind == ROW_EQ) {
+          a = rho * P->u[i] * P->wx[e] + rho * P->v[i] * P->wy[e] - mu * P->wl[e];
+          if (P->idx[e] == i) a = a + rho * a1 / dt;
+        } else if (kind == ROW_NEU) {
+          a = P->nx[i] * P->wx[e] + P->ny[i] * P->wy[e];
+        } else {
+          a = (P->idx[e] == i) ? 1.0 : 0.0;
+        }
+        val[e] = a;
       }
-      P->Am.val[e] = val;
-    }
-    if (P->tag[i] == TAG_INTERIOR) {
-      P->bu[i] = -rho * (a2 * P->un[i] + a3 * P->unm1[i]) / dt - P->w1[i];
-      P->bv[i] = -rho * (a2 * P->vn[i] + a3 * P->vnm1[i]) / dt - P->w2[i];
-    } else {
-      P->bu[i] = P->ubc[i];
-      P->bv[i] = P->vbc[i];
+      double b;
+      if (kind == ROW_EQ)
+        b = c == 0 ? -rho * (a2 * P->un[i] + a3 * P->unm1[i]) / dt - P->w1[i]
+                   : -rho * (a2 * P->vn[i] + a3 * P->vnm1[i]) / dt - P->w2[i];
+      else if (kind == ROW_NEU)
+        b = 0.0;
+      else
+        b = c == 0 ? P->ubc[i] : P->vbc[i];
+      if (c == 0) P->bu[i] = b; else P->bv[i] = b;
     }
   }
   krylov_stats_t su, sv, sp;
@@ -630,10 +674,10 @@ int orc_simple_iterate(orc_problem *P, double dt, double a1, double a2, double a
   memcpy(P->vt, P->v, sizeof(double) * n);
   rc = bicgstab(&P->Am, P->bu, P->ut, P->ktol, P->kmaxit, &su);
   if (rc) return rc;
-  rc = bicgstab(&P->Am, P->bv, P->vt, P->ktol, P->kmaxit, &sv);
+  rc = bicgstab(&P->Av, P->bv, P->vt, P->ktol, P->kmaxit, &sv);
   if (rc) return rc;
   /* Step 3, Eq. (pressure poisson): lap p' = (rho a1 / dt)(du~/dx + dv~/dy) */
-  /* at interior rows; 0 at the Neumann rows and at the pinned row.         */
+  /* at interior rows; 0 at the Neumann rows, the outlet rows and the pin.  */
   csr_spmv(&P->Dx, P->ut, P->w1);
   csr_spmv(&P->Dy, P->vt, P->w2);
   for (int i = 0; i < n; ++i)
@@ -649,6 +693,7 @@ int orc_simple_iterate(orc_problem *P, double dt, double a1, double a2, double a
   /*   sum_j G_ij p_j = N . [ -rho (a1 u~ + a2 u^n + a3 u^{n-1})/dt          */
   /*                          - rho (u~ . grad) u~ + mu lap u~ ]_i,          */
   /* solved for p_i with the other p_j at their current values (Jacobi).     */
+  /* Outlet points keep their prescribed pressure.                           */
   csr_spmv(&P->Dx, P->ut, P->w1);
   csr_spmv(&P->Dy, P->ut, P->w2);
   csr_spmv(&P->Dl, P->ut, P->w3);
@@ -663,7 +708,7 @@ int orc_simple_iterate(orc_problem *P, double dt, double a1, double a2, double a
   csr_spmv(&P->Dl, P->vt, lv);
   for (int i = 0; i < n; ++i) {
     pnew[i] = P->p[i];
-    if (P->tag[i] == TAG_INTERIOR) continue;
+    if (P->tag[i] == TAG_INTERIOR || P->tag[i] == TAG_OUTFLOW) continue;
     double fx = -rho * (a1 * P->ut[i] + a2 * P->un[i] + a3 * P->unm1[i]) / dt -
                 rho * (P->ut[i] * gxu[i] + P->vt[i] * gyu[i]) + mu * lu[i];
     double fy = -rho * (a1 * P->vt[i] + a2 * P->vn[i] + a3 * P->vnm1[i]) / dt -
@@ -681,21 +726,17 @@ int orc_simple_iterate(orc_problem *P, double dt, double a1, double a2, double a
   }
   for (int i = 0; i < n; ++i) P->p[i] = pnew[i];
   free(gxv); free(gyv); free(lv); free(pnew);
-  /* Step 6, Eqs. (u:correction), (v:correction), at points whose velocity */
-  /* is not prescribed.  Step 7: Delta = mean|u^{r+1}-u^r| + mean|v^{r+1}-v^r|. */
+  /* Step 6, Eqs. (u:correction), (v:correction), for every component that  */
+  /* is not prescribed (interior, outlets, the tangential component on a    */
+  /* symmetry line).  Step 7: Delta = mean|u^{r+1}-u^r| + mean|v^{r+1}-v^r|. */
   csr_spmv(&P->Dx, P->pc, P->w1);
   csr_spmv(&P->Dy, P->pc, P->w2);
   double c = dt / (rho * a1);
   double du = 0.0, dv = 0.0;
   for (int i = 0; i < n; ++i) {
-    double unew, vnew;
-    if (P->tag[i] == TAG_INTERIOR) {
-      unew = P->ut[i] - c * P->w1[i];
-      vnew = P->vt[i] - c * P->w2[i];
-    } else {
-      unew = P->ut[i];
-      vnew = P->vt[i];
-    }
+    double unew = P->ut[i], vnew = P->vt[i];
+    if (row_kind(P, i, 0) != ROW_ID) unew = P->ut[i] - c * P->w1[i];
+    if (row_kind(P, i, 1) != ROW_ID) vnew = P->vt[i] - c * P->w2[i];
     du = du + fabs(unew - P->u[i]);
     dv = dv + fabs(vnew - P->v[i]);
     P->u[i] = unew;
@@ -857,10 +898,11 @@ int orc_set_threads(int nthreads) {
 #endif
 }
 
-/* y = W x for one of the stored operators (0 Dx, 1 Dy, 2 Lap, 3 p' matrix, 4 momentum). */
+/* y = W x for one of the stored operators (0 Dx, 1 Dy, 2 Lap, 3 p' matrix,  */
+/* 4 u-momentum, 5 v-momentum; the two differ only on symmetry lines).      */
 int orc_apply(orc_problem *P, int which, const double *xv, double *yv) {
   csr_t *A = which == 0 ? &P->Dx : which == 1 ? &P->Dy : which == 2 ? &P->Dl
-           : which == 3 ? &P->Pp : which == 4 ? &P->Am : NULL;
+           : which == 3 ? &P->Pp : which == 4 ? &P->Am : which == 5 ? &P->Av : NULL;
   if (!A) return ORC_EINVAL;
   csr_spmv(A, xv, yv);
   return ORC_OK;

@@ -21,6 +21,13 @@ data here, so seeded clouds with the same structure stand in for them):
   points belong to the side walls (u = v = 0); the lid velocity is applied
   on the open top edge only.
 
+* ``channel(n_x, n_y)``: plane Poiseuille flow in [0, L] x [0, H] at
+  Re = U H / nu: parabolic inlet u = 4 U y (H - y) / H^2 at x = 0, no-slip
+  walls, a fixed-pressure outlet (p = 0) at x = L.  With ``symmetry=True``
+  only the lower half [0, L] x [0, H/2] is meshed and y = H/2 is a
+  symmetry line.  Closed form: u as at the inlet, v = 0,
+  p = 8 mu U (L - x) / H^2.  Interior points are jittered by +-0.25 h.
+
 Point numbering is lattice row-major (index = j * n_side + i), which keeps
 stencil neighbours close in memory.  ``pin`` is the boundary point nearest
 the middle of the bottom edge: the pressure correction has only Neumann
@@ -35,6 +42,8 @@ import numpy as np
 
 TAG_INTERIOR = 0
 TAG_DIRICHLET = 1  # wall / inlet: velocity prescribed, p' homogeneous Neumann
+TAG_OUTFLOW = 2    # fixed-pressure outlet: p held, p' = 0, zero normal velocity gradient
+TAG_SYMMETRY = 3   # symmetry line: normal velocity prescribed, tangential d/dn = 0
 
 
 @dataclasses.dataclass
@@ -155,6 +164,65 @@ def cavity(n_side=200, seed=2, degree=4, q=30, re=1000.0, dt=None, lid=1.0):
     return FlowProblem(
         name=f"cavity{n_side}", x=x, y=y, tag=tag, nx=nx, ny=ny, ubc=ubc, vbc=vbc,
         pin=pin, rho=1.0, mu=lid * 1.0 / re, degree=degree, q=q, dt=float(dt))
+
+
+def _rect_cloud(n_x, n_y, x0, x1, y0, y1, seed, jitter=0.25):
+    """Row-major n_x x n_y lattice on [x0, x1] x [y0, y1] with interior
+    jitter; returns x, y, lattice indices."""
+    cx = np.linspace(x0, x1, n_x)
+    cy = np.linspace(y0, y1, n_y)
+    hx, hy = (x1 - x0) / (n_x - 1), (y1 - y0) / (n_y - 1)
+    ii, jj = np.meshgrid(np.arange(n_x), np.arange(n_y), indexing="xy")
+    ii, jj = ii.ravel(), jj.ravel()
+    x, y = cx[ii].astype(np.float64), cy[jj].astype(np.float64)
+    bnd = (ii == 0) | (ii == n_x - 1) | (jj == 0) | (jj == n_y - 1)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    jx = rng.uniform(-jitter, jitter, size=x.shape) * hx
+    jy = rng.uniform(-jitter, jitter, size=y.shape) * hy
+    return np.where(bnd, x, x + jx), np.where(bnd, y, y + jy), ii, jj
+
+
+def poiseuille_exact(x, y, mu, length=3.0, height=1.0, u_max=1.0):
+    """Plane Poiseuille flow with p = 0 at x = length."""
+    u = 4.0 * u_max * y * (height - y) / height**2
+    return u, np.zeros_like(x), 8.0 * mu * u_max * (length - x) / height**2
+
+
+def channel(n_x=31, n_y=11, length=3.0, height=1.0, seed=6, degree=3, q=20, re=10.0, dt=0.1,
+            symmetry=False):
+    """Poiseuille channel with an inlet, walls, an outlet and optionally a
+    symmetry line (see the module docstring).  The outlet and the symmetry
+    line start at rest; the pressure correction needs no pin (the outlet
+    fixes its level)."""
+    top = height / 2.0 if symmetry else height
+    x, y, ii, jj = _rect_cloud(n_x, n_y, 0.0, length, 0.0, top, seed)
+    mu = 1.0 / re
+    ue, ve, pe = poiseuille_exact(x, y, mu, length, height)
+    n = x.shape[0]
+    tag = np.full(n, TAG_INTERIOR, np.int8)
+    nx, ny = np.zeros(n), np.zeros(n)
+    ubc, vbc = np.zeros(n), np.zeros(n)
+    inlet, outlet = ii == 0, ii == n_x - 1
+    bottom, upper = jj == 0, jj == n_y - 1
+    # walls (and wall corners) first; the inlet edge keeps its own normal
+    wall_top = upper & (not symmetry)
+    tag[bottom | wall_top] = TAG_DIRICHLET
+    ny[bottom] = -1.0
+    ny[wall_top] = 1.0
+    if symmetry:
+        sym = upper & ~inlet & ~outlet
+        tag[sym] = TAG_SYMMETRY
+        ny[sym] = 1.0
+    out = outlet & ~bottom & ~wall_top
+    tag[out] = TAG_OUTFLOW
+    nx[out], ny[out] = 1.0, 0.0
+    tag[inlet] = TAG_DIRICHLET
+    nx[inlet], ny[inlet] = -1.0, 0.0
+    ubc[inlet] = ue[inlet]
+    return FlowProblem(
+        name=f"channel{n_x}x{n_y}{'s' if symmetry else ''}", x=x, y=y, tag=tag, nx=nx, ny=ny,
+        ubc=ubc, vbc=vbc, pin=-1, rho=1.0, mu=mu, degree=degree, q=q, dt=dt,
+        exact={"u": ue, "v": ve, "p": pe})
 
 
 def random_cloud(n, seed, lo=0.0, hi=1.0):
