@@ -50,16 +50,21 @@ def workload(name: str):
     elif name == "kovasznay50":
         fp = clouds.kovasznay(50, dt=0.4)
         desc = f"Kovasznay Re=40, 50x50 jittered cloud (N={fp.n}), degree 3, q=20, dt=0.4"
+    elif name == "cylinder150k":
+        fp = clouds.cylinder()
+        desc = (f"flow past a cylinder Re=100 in [-5,15]x[-5,5], graded cloud h 0.02 at the "
+                f"cylinder (N={fp.n}), degree 3, q=20, dt={fp.dt:.3g}, inlet / symmetry / "
+                f"outlet / no-slip rows, uniform start")
     else:
         raise SystemExit(f"unknown workload {name}")
     return fp, desc
 
 
-def krylov_traffic(precision):
+def krylov_traffic(precision, workload_name):
     """DRAM bytes per pressure-correction launch from the committed ncu
     summary, only while the kernel sources still hash to the profiled ones."""
     import hashlib
-    if precision != "fp64":
+    if precision != "fp64" or workload_name != "cavity200":
         return None
     prof = os.path.join(ROOT, "profiles", "k_bicgstab_fp64_cavity200.md")
     csrc = os.path.join(ROOT, "paper_2106_07616_gb300", "csrc")
@@ -293,6 +298,8 @@ def cpu_oracle_step(fp, outer, threads=0):
     cores = oracle.set_threads(threads)
     t0 = time.perf_counter()
     O = oracle.Problem(fp, krylov_tol=1e-12)
+    for k, a in (fp.initial or {}).items():
+        O.set(k, a)
     it, ch, last = O.time_step(fp.dt, 1e-4, max_outer=outer)
     dt = time.perf_counter() - t0
     del O
@@ -350,15 +357,20 @@ def run_native(args):
     ctx = rbffd.Context(local, stream=stream.cuda_stream)
     dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(fp, k))).to(f"cuda:{local}")
            for k in ("x", "y", "tag", "nx", "ny", "ubc", "vbc")}
-    prec = rbffd.PREC_MIXED if args.precision == "mixed" else rbffd.PREC_FP64
+    prec = {"mixed": rbffd.PREC_MIXED, "ff": rbffd.PREC_MIXED_FF,
+            "fp64": rbffd.PREC_FP64}[args.precision]
+    init = {k: torch.from_numpy(np.ascontiguousarray(a)).to(f"cuda:{local}")
+            for k, a in (fp.initial or {}).items()}
     desc_dev = rbffd.desc_from_pointers(fp.n, fp.q, fp.degree, fp.pin, fp.rho, fp.mu, prec,
                                         dev["x"], dev["y"], dev["tag"], dev["nx"], dev["ny"],
                                         dev["ubc"], dev["vbc"])
     P = rbffd.Problem(ctx, desc=desc_dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
 
-    def step(desc):
+    def step(desc, start=None):
         P.reload(desc=desc)
+        for k, a in (init if start is None else start).items():
+            P.set(k, a)
         it, _ = P.time_step(fp.dt, 1e-4, max_outer=args.outer)
         return it
 
@@ -412,14 +424,17 @@ def run_native(args):
                                          host["x"], host["y"], host["tag"], host["nx"],
                                          host["ny"], host["ubc"], host["vbc"])
     outs = [torch.empty(fp.n, dtype=torch.float64).pin_memory() for _ in range(3)]
-    h2d = sum(int(t.numel() * t.element_size()) for t in host.values())
+    init_host = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                 for k, a in (fp.initial or {}).items()}
+    h2d = sum(int(t.numel() * t.element_size())
+              for t in list(host.values()) + list(init_host.values()))
     d2h = sum(int(t.numel() * t.element_size()) for t in outs)
     e2e_s, e2e_it = 0.0, 0
     for k in range(args.steps):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e2e_it += step(desc_host)
+        e2e_it += step(desc_host, init_host)
         for name, o in zip(("u", "v", "p"), outs):
             P.get(name, out=o)
         e2e_s += time.perf_counter() - t0
@@ -427,20 +442,24 @@ def run_native(args):
            "d2h_bytes_per_step": d2h}
 
     peak, peak_src = read_peaks()
+    l2_mb = fp.n * (fp.q * 12 + 8 * 8) / 1e6  # p' operator + indices + Krylov vectors
     achieved = kp["bytes"] / (kp["ms"] / 1e3) / 1e9 if kp["ms"] > 0 else 0.0
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": krylov_traffic(args.precision),
+            "frac": achieved / peak, "traffic": krylov_traffic(args.precision, args.workload),
             "peak_source": peak_src,
-            "kernel": ("k_bicgstab_ir<1> (pressure-correction FP32 BiCGSTAB in FP64 refinement)"
-                       if args.precision == "mixed" else
-                       "k_bicgstab<1> (pressure-correction BiCGSTAB, persistent)"),
+            "kernel": {"mixed": "k_bicgstab_ir<1> (pressure-correction FP32 BiCGSTAB in FP64 "
+                                "refinement)",
+                       "ff": "k_bicgstab_ir<1> (pressure-correction float-float BiCGSTAB in "
+                             "FP64 refinement)"}.get(
+                           args.precision, "k_bicgstab<1> (pressure-correction BiCGSTAB, persistent)"),
             "launches": kp["launches"], "avg_launch_ms": kp["ms"] / max(kp["launches"], 1),
             "bytes_per_unit": (f"2q(4+4)+14*4 = {2 * fp.q * 8 + 56} B per FP32 row-iteration"
                                if args.precision == "mixed" else
                                f"2q(8+4)+14*8 = {2 * fp.q * 12 + 112} B per row-iteration"),
             "units": kp["units"],
-            "note": ("operators and Krylov vectors of this workload (~20 MB) stay resident in "
-                     "the 129 MB L2 during a solve; achieved/peak is against HBM")}
+            "note": (f"operators and Krylov vectors of this workload (~{l2_mb:.0f} MB) "
+                     f"{'stay resident in' if l2_mb < 100 else 'exceed'} the 129 MB L2 during a "
+                     f"solve; achieved/peak is against HBM")}
     kernels = {
         "krylov_p": {"launches": kp["launches"], "ms": kp["ms"],
                      "GBps": achieved},
@@ -464,7 +483,8 @@ def run_native(args):
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None,
-               "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+               "dtype": {"mixed": "f32+f64", "ff": "f32x2+f64"}.get(args.precision, "f64"),
+               "data": "synthetic",
                "config": {"workload": args.workload, "description": desc,
                           "outer_cap": args.outer, "outer_iters_per_step": all_it / args.steps / world,
                           "precision": args.precision, "krylov_tol": 1e-12,
@@ -491,8 +511,9 @@ def main():
     ap.add_argument("--criterion", type=int, default=1,
                     help="serve: 0 = steady residual R, 1 = the paper's steady error change/dt")
     ap.add_argument("--max-steps", type=int, default=3000)
-    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"],
-                    help="Krylov arithmetic: FP32 inside FP64 defect correction, or FP64")
+    ap.add_argument("--precision", default="fp64", choices=["mixed", "ff", "fp64"],
+                    help="Krylov arithmetic: FP32 or float-float inside FP64 defect "
+                         "correction, or FP64")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -41,10 +41,20 @@ enum {
   RBFFD_ENOTIMPL = -8
 };
 
-/* Boundary tags (Sec. 3.1 of the paper). */
+/* Boundary tags (paper Sec. 3.3, "Boundary Conditions").  Every non-interior
+ * point has a one-sided cloud (itself and interior points only). */
 enum {
   RBFFD_TAG_INTERIOR = 0,
-  RBFFD_TAG_DIRICHLET = 1 /* wall / inlet: velocity prescribed, p' homogeneous Neumann */
+  RBFFD_TAG_DIRICHLET = 1, /* wall / inlet: u, v prescribed (ubc, vbc); p from the normal
+                              momentum equation; p' homogeneous Neumann */
+  RBFFD_TAG_OUTFLOW = 2,   /* fixed-pressure outlet: p held at its current value (0 from
+                              create; rbffd_set_field changes it), p' = 0, and zero normal
+                              derivative of u and v; ubc, vbc are initial values only */
+  RBFFD_TAG_SYMMETRY = 3   /* symmetry line: the normal velocity component prescribed
+                              (ubc if the normal is along x, vbc if along y), zero normal
+                              derivative of the tangential one; p from the normal momentum
+                              equation; p' homogeneous Neumann.  The normal must be
+                              axis-aligned (its smaller component |.| <= 1e-12). */
 };
 
 /* Operators of the problem (rbffd_apply, rbffd_get_operators). */
@@ -53,7 +63,8 @@ enum {
   RBFFD_OP_DY = 1,        /* d/dy weights */
   RBFFD_OP_LAP = 2,       /* Laplacian weights */
   RBFFD_OP_PCORR = 3,     /* pressure-correction matrix */
-  RBFFD_OP_MOMENTUM = 4   /* momentum matrix of the last outer iteration */
+  RBFFD_OP_MOMENTUM = 4,  /* u-momentum matrix of the last outer iteration */
+  RBFFD_OP_MOMENTUM_V = 5 /* v-momentum matrix: equal to the u one except on symmetry lines */
 };
 
 /* Fields of a problem (rbffd_get_field / rbffd_set_field). */
@@ -193,8 +204,9 @@ typedef struct {
   int32_t n;       /* points */
   int32_t q;       /* cloud size */
   int32_t degree;  /* appended polynomial degree k */
-  int32_t pin;     /* boundary point whose p' row is the identity (fixes the
-                      free constant of the pure-Neumann p' equation) */
+  int32_t pin;     /* Dirichlet or symmetry point whose p' row is the identity
+                      (fixes the free constant of a pure-Neumann p' equation), or
+                      -1 when an outflow point fixes the level */
   double rho, mu;  /* density, dynamic viscosity */
   int32_t precision; /* RBFFD_PREC_* */
   /* host or device arrays of n entries (copied at create / reload): */
@@ -206,11 +218,12 @@ typedef struct {
 
 /* Allocate a problem and build everything that depends only on the points
  * (S1 clouds, S2 weights, S3 packed operators, the pressure-correction
- * matrix: Laplacian rows inside, n . grad rows at Dirichlet-velocity
- * boundary points, identity at `pin`).  Initial state: u = v = p = 0 in the
- * interior, boundary velocity on the boundary, flat time history.
- * Errors: RBFFD_EINVAL, RBFFD_ENOMEM (allocation or budget), RBFFD_ESINGULAR,
- * RBFFD_ECUDA. */
+ * matrix: Laplacian rows inside, n . grad rows at Dirichlet and symmetry
+ * points, identity at outflow points and at `pin`).  Initial state:
+ * u = v = p = 0 in the interior, ubc / vbc on the boundary, flat time
+ * history.  Errors: RBFFD_EINVAL (also: an unknown tag, an oblique symmetry
+ * normal, pin not a Dirichlet / symmetry point, pin = -1 without an outflow
+ * point), RBFFD_ENOMEM (allocation or budget), RBFFD_ESINGULAR, RBFFD_ECUDA. */
 int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *desc, rbffd_problem **out);
 /* Same as create for a problem of identical n, q, degree and precision,
  * reusing its memory (no allocation): re-copies the inputs, rebuilds the

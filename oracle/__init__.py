@@ -53,6 +53,9 @@ def lib():
         L.orc_knn.argtypes = [C.c_int, _dp, _dp, C.c_void_p, C.c_int, _ip]
         L.orc_weights.argtypes = [C.c_int, _dp, _dp, C.c_int, _ip, C.c_int, _dp, _dp, _dp,
                                   C.POINTER(C.c_int32)]
+        L.orc_knn_rows.argtypes = [C.c_int, _dp, _dp, C.c_void_p, C.c_int, C.c_int, _ip, _ip]
+        L.orc_weights_rows.argtypes = [C.c_int, _dp, _dp, C.c_int, C.c_int, _ip, _ip, C.c_int,
+                                       _dp, _dp, _dp, C.POINTER(C.c_int32)]
         L.orc_lu_solve.argtypes = [C.c_int, C.c_int, _dp, C.c_int, _dp]
         L.orc_bicgstab_csr.argtypes = [C.c_int, _lp, _ip, _dp, _dp, _dp, C.c_double, C.c_int,
                                        C.POINTER(C.c_int32), C.POINTER(C.c_double)]
@@ -110,6 +113,33 @@ def knn(x, y, q, tag=None):
     if rc:
         raise ValueError(f"orc_knn failed: {rc}")
     return idx
+
+
+def knn_rows(x, y, q, rows, tag=None):
+    """Stencils of the points `rows` only: (len(rows), q), as knn()."""
+    x, y = _f64(x), _f64(y)
+    rows = np.ascontiguousarray(rows, np.int32)
+    idx = np.zeros((rows.size, q), np.int32)
+    tg = None if tag is None else np.ascontiguousarray(tag, np.int8)
+    rc = lib().orc_knn_rows(x.size, x, y, None if tg is None else tg.ctypes.data, q, rows.size,
+                            rows, idx)
+    if rc:
+        raise ValueError(f"orc_knn_rows failed: {rc}")
+    return idx
+
+
+def weights_rows(x, y, idx, rows, degree):
+    """Weights of the clouds idx (len(rows), q) centred at the points rows."""
+    x, y = _f64(x), _f64(y)
+    idx = np.ascontiguousarray(idx, np.int32)
+    rows = np.ascontiguousarray(rows, np.int32)
+    k, q = idx.shape
+    wx, wy, wl = np.zeros((k, q)), np.zeros((k, q)), np.zeros((k, q))
+    fs = C.c_int32(-1)
+    rc = lib().orc_weights_rows(x.size, x, y, q, k, rows, idx, degree, wx, wy, wl, C.byref(fs))
+    if rc:
+        raise ValueError(f"orc_weights_rows failed: {rc} (first singular {fs.value})")
+    return wx, wy, wl
 
 
 def weights(x, y, idx, degree):

@@ -93,12 +93,48 @@ static int key_less(double d2a, int ja, double d2b, int jb) {
   return d2a < d2b || (d2a == d2b && ja < jb);
 }
 
-int orc_knn(int n, const double *x, const double *y, const int8_t *tag, int q, int32_t *idx) {
-  if (n <= 0 || q <= 0 || q > n) return ORC_EINVAL;
+/* The cloud of point i into out[0..q-1]; bd, bj: work arrays of q-1.     */
+static void knn_one(int n, const double *x, const double *y, const int8_t *tag, int q, int i,
+                    double *bd, int *bj, int32_t *out) {
+  int boundary = tag && tag[i] != TAG_INTERIOR;
+  int cnt = 0;
+  for (int j = 0; j < n; ++j) {
+    if (j == i) continue;
+    if (boundary && tag[j] != TAG_INTERIOR) continue;
+    double dx = x[j] - x[i];
+    double dy = y[j] - y[i];
+    double d2 = dx * dx + dy * dy;
+    /* keep the q-1 best in a sorted list (insertion) */
+    if (cnt < q - 1) {
+      int s = cnt++;
+      while (s > 0 && key_less(d2, j, bd[s - 1], bj[s - 1])) {
+        bd[s] = bd[s - 1]; bj[s] = bj[s - 1]; --s;
+      }
+      bd[s] = d2; bj[s] = j;
+    } else if (q > 1 && key_less(d2, j, bd[q - 2], bj[q - 2])) {
+      int s = q - 2;
+      while (s > 0 && key_less(d2, j, bd[s - 1], bj[s - 1])) {
+        bd[s] = bd[s - 1]; bj[s] = bj[s - 1]; --s;
+      }
+      bd[s] = d2; bj[s] = j;
+    }
+  }
+  out[0] = i;
+  for (int s = 0; s < q - 1; ++s) out[1 + s] = bj[s];
+}
+
+/* Clouds of the points rows[0..nrows-1] (all points when rows == NULL,     */
+/* nrows = n), written row by row to idx (nrows x q).                       */
+static int knn_rows(int n, const double *x, const double *y, const int8_t *tag, int q,
+                    int nrows, const int32_t *rows, int32_t *idx) {
+  if (n <= 0 || q <= 0 || q > n || nrows < 0) return ORC_EINVAL;
   int n_int = 0;
   for (int j = 0; j < n; ++j) n_int += (!tag || tag[j] == TAG_INTERIOR);
   int any_bnd = n_int < n;
   if (any_bnd && q - 1 > n_int) return ORC_EINVAL;
+  if (rows)
+    for (int k = 0; k < nrows; ++k)
+      if (rows[k] < 0 || rows[k] >= n) return ORC_EINVAL;
   int status = ORC_OK;
 #pragma omp parallel
   {
@@ -109,37 +145,23 @@ int orc_knn(int n, const double *x, const double *y, const int8_t *tag, int q, i
     status = ORC_ENOMEM;
   }
 #pragma omp for schedule(dynamic, 64)
-  for (int i = 0; i < n; ++i) {
+  for (int k = 0; k < nrows; ++k) {
     if (!bd || !bj) continue;
-    int boundary = tag && tag[i] != TAG_INTERIOR;
-    int cnt = 0;
-    for (int j = 0; j < n; ++j) {
-      if (j == i) continue;
-      if (boundary && tag[j] != TAG_INTERIOR) continue;
-      double dx = x[j] - x[i];
-      double dy = y[j] - y[i];
-      double d2 = dx * dx + dy * dy;
-      /* keep the q-1 best in a sorted list (insertion) */
-      if (cnt < q - 1) {
-        int s = cnt++;
-        while (s > 0 && key_less(d2, j, bd[s - 1], bj[s - 1])) {
-          bd[s] = bd[s - 1]; bj[s] = bj[s - 1]; --s;
-        }
-        bd[s] = d2; bj[s] = j;
-      } else if (q > 1 && key_less(d2, j, bd[q - 2], bj[q - 2])) {
-        int s = q - 2;
-        while (s > 0 && key_less(d2, j, bd[s - 1], bj[s - 1])) {
-          bd[s] = bd[s - 1]; bj[s] = bj[s - 1]; --s;
-        }
-        bd[s] = d2; bj[s] = j;
-      }
-    }
-    idx[(int64_t)i * q] = i;
-    for (int s = 0; s < q - 1; ++s) idx[(int64_t)i * q + 1 + s] = bj[s];
+    knn_one(n, x, y, tag, q, rows ? rows[k] : k, bd, bj, idx + (int64_t)k * q);
   }
   free(bd); free(bj);
   }
   return status;
+}
+
+int orc_knn(int n, const double *x, const double *y, const int8_t *tag, int q, int32_t *idx) {
+  return knn_rows(n, x, y, tag, q, n, NULL, idx);
+}
+
+/* Clouds of selected points only (spot checks of large problems). */
+int orc_knn_rows(int n, const double *x, const double *y, const int8_t *tag, int q, int nrows,
+                 const int32_t *rows, int32_t *idx) {
+  return knn_rows(n, x, y, tag, q, nrows, rows, idx);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -254,10 +276,28 @@ static int weights_one(const double *x, const double *y, int q, const int32_t *c
   return 0;
 }
 
+static int weights_rows(int n, const double *x, const double *y, int q, int nrows,
+                        const int32_t *rows, const int32_t *idx, int degree, double *wx,
+                        double *wy, double *wl, int32_t *first_singular);
+
 int orc_weights(int n, const double *x, const double *y, int q, const int32_t *idx,
                 int degree, double *wx, double *wy, double *wl, int32_t *first_singular) {
+  return weights_rows(n, x, y, q, n, NULL, idx, degree, wx, wy, wl, first_singular);
+}
+
+/* Weights of the clouds idx (nrows x q) centred at rows[k] (spot checks of */
+/* large problems); first_singular reports the position k.                 */
+int orc_weights_rows(int n, const double *x, const double *y, int q, int nrows,
+                     const int32_t *rows, const int32_t *idx, int degree, double *wx, double *wy,
+                     double *wl, int32_t *first_singular) {
+  return weights_rows(n, x, y, q, nrows, rows, idx, degree, wx, wy, wl, first_singular);
+}
+
+static int weights_rows(int n, const double *x, const double *y, int q, int nrows,
+                        const int32_t *rows, const int32_t *idx, int degree, double *wx,
+                        double *wy, double *wl, int32_t *first_singular) {
   int m = orc_num_monomials(degree);
-  if (n <= 0 || q <= 0 || q > n || degree < 0 || q < m) return ORC_EINVAL;
+  if (n <= 0 || q <= 0 || q > n || degree < 0 || q < m || nrows < 0) return ORC_EINVAL;
   int N = q + m;
   int32_t ax[64], ay[64];
   if (m > 64) return ORC_EINVAL;
@@ -275,10 +315,10 @@ int orc_weights(int n, const double *x, const double *y, int q, const int32_t *i
     status = ORC_ENOMEM;
   }
 #pragma omp for schedule(dynamic, 16)
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < nrows; ++i) {
     if (!ok) continue;
     int64_t o = (int64_t)i * q;
-    if (weights_one(x, y, q, idx + o, i, m, ax, ay, M, sol, xi, eta, wx ? wx + o : NULL,
+    if (weights_one(x, y, q, idx + o, rows ? rows[i] : i, m, ax, ay, M, sol, xi, eta, wx ? wx + o : NULL,
                     wy ? wy + o : NULL, wl ? wl + o : NULL) != 0) {
 #pragma omp critical(orc_singular)
       {

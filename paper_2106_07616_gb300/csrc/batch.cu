@@ -166,15 +166,18 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
       return RBFFD_EINVAL;
     }
   }
-  RBFFD_TRY(S.reserve(ctx, m));
-  std::vector<int> rows(m);
-  for (int i = 0; i < m; ++i) rows[i] = P[i]->n;
-  // momentum predictor of every member, then one launch for all the solves
-  std::vector<KrylovArgs> a2(m), a1(m);
+  // a member with symmetry lines solves u~ and v~ as two single-RHS systems
+  // (their rows differ there), so a launch may hold up to 2m systems
+  RBFFD_TRY(S.reserve(ctx, 2 * m));
+  // momentum predictor of every member, then one launch for the two-RHS
+  // solves of all members (and one for the single-RHS pairs, if any)
+  std::vector<KrylovArgs> a2, a1s, a1(m);
+  std::vector<int> rows2, rows1s, rows(m);
   for (int i = 0; i < m; ++i) {
     const rbffd_step_params *sp = spv[i];
+    rows[i] = P[i]->n;
     RBFFD_TRY(ops_momentum(P[i], sp));
-    KrylovArgs &a = a2[i];
+    KrylovArgs a;
     memset(&a, 0, sizeof(a));
     a.n = P[i]->n;
     a.q = P[i]->q;
@@ -192,20 +195,43 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
     a.w[0] = P[i]->kv[0];
     a.w[1] = P[i]->kv[1];
     a.out = P[i]->kout;
-    a.nblocks = std::max(P[i]->kblocks1, P[i]->kblocks2);  // partial-sum capacity
+    const int capb = std::max(P[i]->kblocks1, P[i]->kblocks2);  // partial-sum capacity
+    a.nblocks = capb;
+    if (!P[i]->has_sym) {
+      a2.push_back(a);
+      rows2.push_back(P[i]->n);
+    } else {
+      KrylovArgs au = a;
+      au.b[1] = nullptr;
+      au.x[1] = nullptr;
+      KrylovArgs av = au;
+      av.val = P[i]->Am2;
+      av.dinv = P[i]->m_dinv2;
+      av.b[0] = P[i]->bv;
+      av.x[0] = P[i]->vt;
+      av.w[0] = P[i]->kv[1];
+      av.out = P[i]->kout + 1;
+      av.part = P[i]->part + krylov_partials_doubles(1, capb);  // second half
+      a1s.push_back(au);
+      a1s.push_back(av);
+      rows1s.push_back(P[i]->n);
+      rows1s.push_back(P[i]->n);
+    }
+    a1[i] = a;
   }
   prof_begin(ctx, 0);
-  RBFFD_TRY(launch_krylov(S, 2, a2, rows));
+  if (!a2.empty()) RBFFD_TRY(launch_krylov(S, 2, a2, rows2));
+  if (!a1s.empty()) RBFFD_TRY(launch_krylov(S, 1, a1s, rows1s));
   prof_end(ctx, 0);
   for (int i = 0; i < m; ++i) {
     RBFFD_TRY(ops_divergence(P[i], spv[i]));
-    a1[i] = a2[i];
     a1[i].val = P[i]->Pp;
     a1[i].dinv = P[i]->p_dinv;
     a1[i].b[0] = P[i]->bp;
     a1[i].b[1] = nullptr;
     a1[i].x[0] = P[i]->pc;
     a1[i].x[1] = nullptr;
+    a1[i].w[0] = P[i]->kv[0];
     a1[i].out = P[i]->kout + 2;
     a1[i].nblocks = 2 * std::max(P[i]->kblocks1, P[i]->kblocks2);
   }

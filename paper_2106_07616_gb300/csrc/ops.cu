@@ -16,6 +16,20 @@ namespace rbffd {
 
 constexpr int RT = 256;
 
+// Kind of the momentum row of a point for velocity component c (0 = u,
+// 1 = v), paper Sec. 3.3: the equation inside (ROW_EQ); an identity row with
+// the boundary value where the component is prescribed (walls, inlets, the
+// normal component on a symmetry line); a zero normal derivative n . grad
+// at outlets and for the tangential component on a symmetry line.
+enum { ROW_EQ = 0, ROW_ID = 1, ROW_NEU = 2 };
+
+__device__ __forceinline__ int row_kind(int t, double nxi, double nyi, int c) {
+  if (t == RBFFD_TAG_INTERIOR) return ROW_EQ;
+  if (t == RBFFD_TAG_OUTFLOW) return ROW_NEU;
+  if (t == RBFFD_TAG_SYMMETRY) return c == (fabs(nxi) > fabs(nyi) ? 0 : 1) ? ROW_ID : ROW_NEU;
+  return ROW_ID;
+}
+
 __global__ void k_pack(int n, int q, int ldn, int pin, const int32_t *__restrict__ idx_rm,
                        const double *__restrict__ wx_rm, const double *__restrict__ wy_rm,
                        const double *__restrict__ wl_rm, const int8_t *__restrict__ tag,
@@ -46,7 +60,7 @@ __global__ void k_pack(int n, int q, int ldn, int pin, const int32_t *__restrict
     Wy[e] = b;
     Wl[e] = l;
     double pv;
-    if (i == pin)
+    if (i == pin || tag[i] == RBFFD_TAG_OUTFLOW)
       pv = (c == i) ? 1.0 : 0.0;
     else if (interior)
       pv = l;
@@ -61,8 +75,11 @@ __global__ void k_pack(int n, int q, int ldn, int pin, const int32_t *__restrict
 // S4: momentum matrix and right-hand sides, Eqs. (u:tilde), (v:tilde):
 //   rho a1/dt u~ + rho u^r Dx u~ + rho v^r Dy u~ - mu Lap u~
 //       = -rho (a2 u^n + a3 u^{n-1}) / dt - (Dx p^r)
-// at interior rows; identity rows with the boundary value elsewhere.  The
-// initial guesses of the momentum solve are set to the current iterate.
+// at interior rows; boundary rows by row_kind (identity with the boundary
+// value, or n . grad with a zero right-hand side).  Am serves u~ (and v~
+// too when Am2 is null: no symmetry rows); Am2, when given, is the v~
+// matrix, equal to Am except on symmetry lines.  The initial guesses of the
+// momentum solve are set to the current iterate.
 __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ col,
                            const double *__restrict__ Wx, const double *__restrict__ Wy,
                            const double *__restrict__ Wl, const int8_t *__restrict__ tag,
@@ -70,22 +87,37 @@ __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ co
                            const double *__restrict__ p, const double *__restrict__ un,
                            const double *__restrict__ vn, const double *__restrict__ unm1,
                            const double *__restrict__ vnm1, const double *__restrict__ ubc,
-                           const double *__restrict__ vbc, double rho, double mu, double dt,
+                           const double *__restrict__ vbc, const double *__restrict__ nx,
+                           const double *__restrict__ ny, double rho, double mu, double dt,
                            double a1, double a2, double a3, double *__restrict__ Am,
-                           double *__restrict__ mdinv, double *__restrict__ bu,
+                           double *__restrict__ mdinv, double *__restrict__ Am2,
+                           double *__restrict__ mdinv2, double *__restrict__ bu,
                            double *__restrict__ bv, double *__restrict__ ut,
                            double *__restrict__ vt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const bool interior = tag[i] == 0;
+  const int t = tag[i];
   const double ui = u[i], vi = v[i];
   ut[i] = ui;
   vt[i] = vi;
-  if (!interior) {
-    for (int j = 0; j < q; ++j) Am[(int64_t)j * ldn + i] = (j == 0) ? 1.0 : 0.0;
-    mdinv[i] = 1.0;
-    bu[i] = ubc[i];
-    bv[i] = vbc[i];
+  if (t != RBFFD_TAG_INTERIOR) {
+    const double ni = nx[i], mi = ny[i];
+    const int ku = row_kind(t, ni, mi, 0), kv = row_kind(t, ni, mi, 1);
+    const bool neu = ku == ROW_NEU || kv == ROW_NEU;
+    double gd = 0.0;
+    for (int j = 0; j < q; ++j) {
+      const int64_t e = (int64_t)j * ldn + i;
+      const double id = (j == 0) ? 1.0 : 0.0;  // slot 0 is the point itself
+      const double g = neu ? ni * Wx[e] + mi * Wy[e] : 0.0;
+      if (j == 0) gd = g;
+      Am[e] = ku == ROW_ID ? id : g;
+      if (Am2) Am2[e] = kv == ROW_ID ? id : g;
+    }
+    const double gi = 1.0 / (gd == 0.0 ? 1.0 : gd);
+    mdinv[i] = ku == ROW_ID ? 1.0 : gi;
+    if (Am2) mdinv2[i] = kv == ROW_ID ? 1.0 : gi;
+    bu[i] = ku == ROW_ID ? ubc[i] : 0.0;
+    bv[i] = kv == ROW_ID ? vbc[i] : 0.0;
     return;
   }
   const double ru = rho * ui, rv = rho * vi, dd = rho * a1 / dt;
@@ -104,8 +136,10 @@ __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ co
       diag += val;
     }
     Am[e] = val;
+    if (Am2) Am2[e] = val;
   }
   mdinv[i] = 1.0 / (diag == 0.0 ? 1.0 : diag);
+  if (Am2) mdinv2[i] = mdinv[i];
   bu[i] = -rho * (a2 * un[i] + a3 * unm1[i]) / dt - gx;
   bv[i] = -rho * (a2 * vn[i] + a3 * vnm1[i]) / dt - gy;
 }
@@ -135,7 +169,8 @@ __global__ void k_divergence(int n, int q, int ldn, const int32_t *__restrict__ 
   bp[i] = coef * (dx + dy);
 }
 
-// S8 (p += p' inside) fused with S9 (boundary pressure, Eq. normal momentum):
+// S8 (p += p' inside) fused with S9 (boundary pressure, Eq. normal momentum;
+// outlets keep their prescribed pressure):
 // for a boundary point i with G = nx Wx + ny Wy (row i),
 //   sum_j G_ij p_j = N . [ -rho (a1 u~ + a2 u^n + a3 u^{n-1})/dt
 //                          - rho (u~ . grad) u~ + mu Lap u~ ]_i,
@@ -153,8 +188,12 @@ __global__ void k_pressure(int n, int q, int ldn, const int32_t *__restrict__ co
                            double *__restrict__ p_out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if (tag[i] == 0) {
+  if (tag[i] == RBFFD_TAG_INTERIOR) {
     p_out[i] = p[i] + pc[i];
+    return;
+  }
+  if (tag[i] == RBFFD_TAG_OUTFLOW) {
+    p_out[i] = p[i];
     return;
   }
   const double ni = nx[i], mi = ny[i];
@@ -186,11 +225,14 @@ __global__ void k_pressure(int n, int q, int ldn, const int32_t *__restrict__ co
   p_out[i] = (ni * fx + mi * fy - off) / gii;
 }
 
-// S8 velocity correction, Eqs. (u:correction), (v:correction), at interior
-// rows, with the block partials of sum|du| and sum|dv| for Delta (S10).
+// S8 velocity correction, Eqs. (u:correction), (v:correction), of every
+// component that is not prescribed (row_kind != ROW_ID: interior, outlets,
+// the tangential component on symmetry lines), with the block partials of
+// sum|du| and sum|dv| for Delta (S10).
 __global__ void __launch_bounds__(RT) k_correct(
     int n, int q, int ldn, const int32_t *__restrict__ col, const double *__restrict__ Wx,
     const double *__restrict__ Wy, const int8_t *__restrict__ tag,
+    const double *__restrict__ nx, const double *__restrict__ ny,
     const double *__restrict__ pc, const double *__restrict__ ut,
     const double *__restrict__ vt, double c, double *__restrict__ u, double *__restrict__ v,
     double *__restrict__ part) {
@@ -198,7 +240,8 @@ __global__ void __launch_bounds__(RT) k_correct(
   double su = 0.0, sv = 0.0;
   for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
     double unew = ut[i], vnew = vt[i];
-    if (tag[i] == 0) {
+    const int t = tag[i];
+    if (t != RBFFD_TAG_DIRICHLET) {
       double gx = 0.0, gy = 0.0;
 #pragma unroll 4
       for (int j = 0; j < q; ++j) {
@@ -207,8 +250,14 @@ __global__ void __launch_bounds__(RT) k_correct(
         gx += Wx[e] * pj;
         gy += Wy[e] * pj;
       }
-      unew = unew - c * gx;
-      vnew = vnew - c * gy;
+      bool cu = true, cv = true;
+      if (t == RBFFD_TAG_SYMMETRY) {
+        const double ni = nx[i], mi = ny[i];
+        cu = row_kind(t, ni, mi, 0) != ROW_ID;
+        cv = row_kind(t, ni, mi, 1) != ROW_ID;
+      }
+      if (cu) unew = unew - c * gx;
+      if (cv) vnew = vnew - c * gy;
     }
     su += fabs(unew - u[i]);
     sv += fabs(vnew - v[i]);
@@ -369,8 +418,9 @@ int ops_pack(rbffd_problem *P) {
 int ops_momentum(rbffd_problem *P, const rbffd_step_params *sp) {
   k_momentum<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(
       P->n, P->q, P->ldn, P->col, P->Wx, P->Wy, P->Wl, P->tag, P->u, P->v, P->p, P->un, P->vn,
-      P->unm1, P->vnm1, P->ubc, P->vbc, P->rho, P->mu, sp->dt, sp->alpha[0], sp->alpha[1],
-      sp->alpha[2], P->Am, P->m_dinv, P->bu, P->bv, P->ut, P->vt);
+      P->unm1, P->vnm1, P->ubc, P->vbc, P->nx, P->ny, P->rho, P->mu, sp->dt, sp->alpha[0],
+      sp->alpha[1], sp->alpha[2], P->Am, P->m_dinv, P->has_sym ? P->Am2 : nullptr,
+      P->has_sym ? P->m_dinv2 : nullptr, P->bu, P->bv, P->ut, P->vt);
   return after_launch(P->ctx, "k_momentum");
 }
 
@@ -397,8 +447,8 @@ int ops_pressure(rbffd_problem *P, const rbffd_step_params *sp) {
 int ops_correct(rbffd_problem *P, const rbffd_step_params *sp) {
   double c = sp->dt / (P->rho * sp->alpha[0]);
   k_correct<<<P->rblocks, RT, 0, P->ctx->stream>>>(P->n, P->q, P->ldn, P->col, P->Wx, P->Wy,
-                                                   P->tag, P->pc, P->ut, P->vt, c, P->u, P->v,
-                                                   P->rpart);
+                                                   P->tag, P->nx, P->ny, P->pc, P->ut, P->vt, c,
+                                                   P->u, P->v, P->rpart);
   RBFFD_TRY(after_launch(P->ctx, "k_correct"));
   k_finalize<<<1, 32, 0, P->ctx->stream>>>(P->rpart, P->rblocks, P->n, 0, P->rec);
   return after_launch(P->ctx, "k_finalize");

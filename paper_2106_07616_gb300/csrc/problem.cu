@@ -2,6 +2,7 @@
 // steady and unsteady drivers (paper Sec. 3.2), behind the C ABI.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "ops.cuh"
 #include "problem.cuh"
@@ -44,7 +45,7 @@ int check_desc(const rbffd_problem_desc *d) {
     set_error("problem desc: bad n=%d q=%d degree=%d", d->n, d->q, d->degree);
     return RBFFD_EINVAL;
   }
-  if (d->pin < 0 || d->pin >= d->n) {
+  if (d->pin < -1 || d->pin >= d->n) {
     set_error("problem desc: pin %d out of range", d->pin);
     return RBFFD_EINVAL;
   }
@@ -72,19 +73,47 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
   RBFFD_CK(cudaMemcpyAsync(P->ubc, d->ubc, nb, cudaMemcpyDefault, st));
   RBFFD_CK(cudaMemcpyAsync(P->vbc, d->vbc, nb, cudaMemcpyDefault, st));
   RBFFD_CK(cudaMemcpyAsync(P->tag, d->tag, (size_t)d->n, cudaMemcpyDefault, st));
-  // the pinned row must be a boundary row: check on the host copy of its tag
-  int8_t pin_tag = 0;
-  RBFFD_CK(cudaMemcpyAsync(&pin_tag, P->tag + d->pin, 1, cudaMemcpyDeviceToHost, st));
+  // boundary description, checked on host copies of the tags and normals
+  {
+    std::vector<int8_t> ht(d->n);
+    std::vector<double> hnx(d->n), hny(d->n);
+    RBFFD_CK(cudaMemcpyAsync(ht.data(), P->tag, (size_t)d->n, cudaMemcpyDeviceToHost, st));
+    RBFFD_CK(cudaMemcpyAsync(hnx.data(), P->nx, nb, cudaMemcpyDeviceToHost, st));
+    RBFFD_CK(cudaMemcpyAsync(hny.data(), P->ny, nb, cudaMemcpyDeviceToHost, st));
+    RBFFD_CK(cudaStreamSynchronize(st));
+    int n_out = 0;
+    bool sym = false;
+    for (int i = 0; i < d->n; ++i) {
+      const int t = ht[i];
+      if (t < RBFFD_TAG_INTERIOR || t > RBFFD_TAG_SYMMETRY) {
+        set_error("problem desc: unknown tag %d at point %d", t, i);
+        return RBFFD_EINVAL;
+      }
+      n_out += t == RBFFD_TAG_OUTFLOW;
+      if (t == RBFFD_TAG_SYMMETRY) {
+        sym = true;
+        if (std::fabs(hnx[i]) > 1e-12 && std::fabs(hny[i]) > 1e-12) {
+          set_error("problem desc: symmetry point %d needs an axis-aligned normal", i);
+          return RBFFD_EINVAL;
+        }
+      }
+    }
+    if (d->pin < 0 && n_out == 0) {
+      set_error("problem desc: pin = -1 needs an outflow point to fix the pressure level");
+      return RBFFD_EINVAL;
+    }
+    if (d->pin >= 0 && ht[d->pin] != RBFFD_TAG_DIRICHLET && ht[d->pin] != RBFFD_TAG_SYMMETRY) {
+      set_error("problem desc: pin %d is not a Dirichlet or symmetry point", d->pin);
+      return RBFFD_EINVAL;
+    }
+    P->has_sym = sym;
+  }
   P->rho = d->rho;
   P->mu = d->mu;
   P->pin = d->pin;
   prof_begin(ctx, 3);
   RBFFD_TRY(knn_run(ctx, P->knn_ws, P->knn_lay, P->n, P->x, P->y, P->tag, P->q, P->idx_rm));
   prof_end(ctx, 3);
-  if (pin_tag == RBFFD_TAG_INTERIOR) {
-    set_error("problem desc: pin %d is not a boundary point", d->pin);
-    return RBFFD_EINVAL;
-  }
   int big = 0x7fffffff;
   RBFFD_CK(cudaMemcpyAsync(P->d_first_singular, &big, sizeof(int), cudaMemcpyHostToDevice, st));
   prof_begin(ctx, 0);
@@ -173,7 +202,26 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
     m.out = P->kout;
     m.tpr = krylov_threads_per_row(P->n, 2, P->kblocks2);
     prof_begin(ctx, 0);
-    RBFFD_TRY(krylov_ir_launch(ctx, 2, P->kblocks2, m));
+    if (!P->has_sym) {
+      RBFFD_TRY(krylov_ir_launch(ctx, 2, P->kblocks2, m));
+    } else {
+      // u~ and v~ rows differ on symmetry lines: two single-RHS solves
+      RBFFD_TRY(ops_to_inner(P, P->Am2, P->Ain2, (int64_t)P->ldn * P->q));
+      RBFFD_TRY(ops_to_inner(P, P->m_dinv2, P->mdin2, P->ldn));
+      m.b[1] = nullptr;
+      m.x[1] = nullptr;
+      m.tpr = krylov_threads_per_row(P->n, 1, P->kblocks1);
+      RBFFD_TRY(krylov_ir_launch(ctx, 1, P->kblocks1, m));
+      m.val64 = P->Am2;
+      m.valin = P->Ain2;
+      m.dinvin = P->mdin2;
+      m.b[0] = P->bv;
+      m.x[0] = P->vt;
+      m.w[0] = P->mv[1];
+      m.out = P->kout + 1;
+      RBFFD_TRY(krylov_ir_launch(ctx, 1, P->kblocks1, m));
+      m.w[0] = P->mv[0];
+    }
     prof_end(ctx, 0);
     RBFFD_TRY(ops_divergence(P, sp));
     m.val64 = P->Pp;
@@ -205,7 +253,23 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   a.out = P->kout;
   a.tpr = krylov_threads_per_row(P->n, 2, P->kblocks2);
   prof_begin(ctx, 0);
-  RBFFD_TRY(krylov_launch(ctx, 2, P->kblocks2, a));
+  if (!P->has_sym) {
+    RBFFD_TRY(krylov_launch(ctx, 2, P->kblocks2, a));
+  } else {
+    // u~ and v~ rows differ on symmetry lines: two single-RHS solves
+    KrylovArgs b1 = a;
+    b1.b[1] = nullptr;
+    b1.x[1] = nullptr;
+    b1.tpr = krylov_threads_per_row(P->n, 1, P->kblocks1);
+    RBFFD_TRY(krylov_launch(ctx, 1, P->kblocks1, b1));
+    b1.val = P->Am2;
+    b1.dinv = P->m_dinv2;
+    b1.b[0] = P->bv;
+    b1.x[0] = P->vt;
+    b1.w[0] = P->kv[1];
+    b1.out = P->kout + 1;
+    RBFFD_TRY(krylov_launch(ctx, 1, P->kblocks1, b1));
+  }
   prof_end(ctx, 0);
   RBFFD_TRY(ops_divergence(P, sp));
   // pressure correction
@@ -293,9 +357,11 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
     if (P->kblocks2 > c2) P->kblocks2 = c2;
   }
   P->rblocks = ops_reduce_blocks(ctx, n);
-  size_t npart = krylov_partials_doubles(2, P->kblocks2);
-  size_t np1 = krylov_partials_doubles(1, P->kblocks1);
-  if (np1 > npart) npart = np1;
+  // partials: room for two right-hand sides over the larger grid (a batched
+  // launch may give one member two single-RHS systems, or one system twice
+  // the CTAs)
+  const int kbmax = P->kblocks1 > P->kblocks2 ? P->kblocks1 : P->kblocks2;
+  size_t npart = krylov_partials_doubles(2, kbmax);
   Carver c;
   size_t o_x = c.take<double>(n), o_y = c.take<double>(n), o_nx = c.take<double>(n),
          o_ny = c.take<double>(n), o_ubc = c.take<double>(n), o_vbc = c.take<double>(n),
@@ -303,8 +369,10 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   size_t o_idx = c.take<int32_t>(nq), o_wx = c.take<double>(nq), o_wy = c.take<double>(nq),
          o_wl = c.take<double>(nq);
   size_t o_col = c.take<int32_t>(lq), o_Wx = c.take<double>(lq), o_Wy = c.take<double>(lq),
-         o_Wl = c.take<double>(lq), o_Pp = c.take<double>(lq), o_Am = c.take<double>(lq);
-  size_t o_pd = c.take<double>(P->ldn), o_md = c.take<double>(P->ldn);
+         o_Wl = c.take<double>(lq), o_Pp = c.take<double>(lq), o_Am = c.take<double>(lq),
+         o_Am2 = c.take<double>(lq);
+  size_t o_pd = c.take<double>(P->ldn), o_md = c.take<double>(P->ldn),
+         o_md2 = c.take<double>(P->ldn);
   size_t o_f[14];
   for (int k = 0; k < 14; ++k) o_f[k] = c.take<double>(n);
   size_t o_kv[16];
@@ -316,11 +384,14 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   size_t o_fs = c.take<int>(1);
   size_t o_knn = c.take<char>(P->knn_lay.bytes);
   size_t o_p32 = 0, o_a32 = 0, o_pd32 = 0, o_md32 = 0, o_mv[18] = {}, o_part64 = 0, o_part32 = 0;
+  size_t o_a32b = 0, o_md32b = 0;
   if (mixed) {
     o_p32 = c.take<char>(lq * es);
     o_a32 = c.take<char>(lq * es);
+    o_a32b = c.take<char>(lq * es);
     o_pd32 = c.take<char>(P->ldn * es);
     o_md32 = c.take<char>(P->ldn * es);
+    o_md32b = c.take<char>(P->ldn * es);
     for (int k = 0; k < 18; ++k) o_mv[k] = c.take<char>((size_t)n * es);
     int kb = P->kblocks1 > P->kblocks2 ? P->kblocks1 : P->kblocks2;
     o_part64 = c.take<double>(krylov_ir_partials64(2, kb));
@@ -351,8 +422,10 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   P->Wl = (double *)(b + o_Wl);
   P->Pp = (double *)(b + o_Pp);
   P->Am = (double *)(b + o_Am);
+  P->Am2 = (double *)(b + o_Am2);
   P->p_dinv = (double *)(b + o_pd);
   P->m_dinv = (double *)(b + o_md);
+  P->m_dinv2 = (double *)(b + o_md2);
   double **f[14] = {&P->u,  &P->v,  &P->p,  &P->p2, &P->un, &P->vn, &P->unm1,
                     &P->vnm1, &P->ut, &P->vt, &P->pc, &P->bu, &P->bv, &P->bp};
   for (int k = 0; k < 14; ++k) *f[k] = (double *)(b + o_f[k]);
@@ -374,6 +447,8 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
     P->Ain = (void *)(b + o_a32);
     P->pdin = (void *)(b + o_pd32);
     P->mdin = (void *)(b + o_md32);
+    P->Ain2 = (void *)(b + o_a32b);
+    P->mdin2 = (void *)(b + o_md32b);
     for (int r = 0; r < 2; ++r) {
       void **w[9] = {&P->mv[r].r, &P->mv[r].rh, &P->mv[r].p0, &P->mv[r].p1, &P->mv[r].v0,
                      &P->mv[r].v1, &P->mv[r].s, &P->mv[r].t, &P->mv[r].d};
@@ -661,7 +736,9 @@ extern "C" int rbffd_apply(rbffd_problem *P, int32_t which, const double *x, dou
                       : which == RBFFD_OP_DY ? P->Wy
                       : which == RBFFD_OP_LAP ? P->Wl
                       : which == RBFFD_OP_PCORR ? P->Pp
-                      : which == RBFFD_OP_MOMENTUM ? P->Am : nullptr;
+                      : which == RBFFD_OP_MOMENTUM ? P->Am
+                      : which == RBFFD_OP_MOMENTUM_V ? (P->has_sym ? P->Am2 : P->Am)
+                      : nullptr;
   if (!val) return RBFFD_EINVAL;
   RBFFD_CK(cudaSetDevice(P->ctx->device));
   RBFFD_TRY(ops_spmv(P, val, x, y));

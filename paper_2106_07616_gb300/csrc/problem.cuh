@@ -27,10 +27,15 @@ struct rbffd_problem {
   int32_t *col;
   double *Wx, *Wy, *Wl, *Pp, *Am;
   double *p_dinv, *m_dinv;
+  // v~ matrix and its Jacobi diagonal, used only when symmetry lines exist
+  // (the u~ and v~ rows differ there); otherwise Am serves both
+  double *Am2, *m_dinv2;
+  bool has_sym = false;
   // copies in the inner arithmetic of the mixed-precision solves (FP32 or
   // float-float; null in the FP64 path)
   int inner = 0;  // rbffd::INNER_F32 / INNER_FF
   void *Pin = nullptr, *Ain = nullptr, *pdin = nullptr, *mdin = nullptr;
+  void *Ain2 = nullptr, *mdin2 = nullptr;
   rbffd::MixedVecs mv[2] = {};
   double *part64 = nullptr;
   void *partin = nullptr;

@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(_HERE, "librbffd.so")
 
 OK, EINVAL, ENOMEM, ESINGULAR, ENOCONV, EDIVERGED, ETIMEOUT, ECUDA, ENOTIMPL = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
-TAG_INTERIOR, TAG_DIRICHLET = 0, 1
-OP_DX, OP_DY, OP_LAP, OP_PCORR, OP_MOMENTUM = 0, 1, 2, 3, 4
+OP_DX, OP_DY, OP_LAP, OP_PCORR, OP_MOMENTUM, OP_MOMENTUM_V = 0, 1, 2, 3, 4, 5
+TAG_INTERIOR, TAG_DIRICHLET, TAG_OUTFLOW, TAG_SYMMETRY = 0, 1, 2, 3
 FIELDS = {"u": 0, "v": 1, "p": 2, "un": 3, "vn": 4, "unm1": 5, "vnm1": 6, "ut": 7, "vt": 8,
           "pc": 9, "ubc": 10, "vbc": 11}
 PREC_FP64, PREC_MIXED, PREC_MIXED_FF = 0, 1, 2

@@ -70,3 +70,17 @@ def test_knn_rejects_bad_sizes():
     x, y = clouds.random_cloud(5, 0)
     with pytest.raises(ValueError):
         oracle.knn(x, y, 6)
+
+
+def test_row_subset_matches_full_build():
+    """knn_rows / weights_rows (spot checks of large problems) give the rows
+    of the full build exactly."""
+    fp = clouds.kovasznay(20)
+    full = oracle.knn(fp.x, fp.y, 20, fp.tag)
+    rows = np.array([0, 5, 77, 212, 399, 19], np.int32)
+    sub = oracle.knn_rows(fp.x, fp.y, 20, rows, fp.tag)
+    assert np.array_equal(sub, full[rows])
+    wf = oracle.weights(fp.x, fp.y, full, 3)
+    ws = oracle.weights_rows(fp.x, fp.y, sub, rows, 3)
+    for a, b in zip(ws, wf):
+        assert np.array_equal(a, b[rows])
