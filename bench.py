@@ -361,9 +361,10 @@ def run_native(args):
             "fp64": rbffd.PREC_FP64}[args.precision]
     init = {k: torch.from_numpy(np.ascontiguousarray(a)).to(f"cuda:{local}")
             for k, a in (fp.initial or {}).items()}
+    pc = rbffd.PRECOND_AMG if args.precond == "amg" else rbffd.PRECOND_JACOBI
     desc_dev = rbffd.desc_from_pointers(fp.n, fp.q, fp.degree, fp.pin, fp.rho, fp.mu, prec,
                                         dev["x"], dev["y"], dev["tag"], dev["nx"], dev["ny"],
-                                        dev["ubc"], dev["vbc"])
+                                        dev["ubc"], dev["vbc"], pc)
     P = rbffd.Problem(ctx, desc=desc_dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
 
@@ -422,7 +423,7 @@ def run_native(args):
             for k in ("x", "y", "tag", "nx", "ny", "ubc", "vbc")}
     desc_host = rbffd.desc_from_pointers(fp.n, fp.q, fp.degree, fp.pin, fp.rho, fp.mu, prec,
                                          host["x"], host["y"], host["tag"], host["nx"],
-                                         host["ny"], host["ubc"], host["vbc"])
+                                         host["ny"], host["ubc"], host["vbc"], pc)
     outs = [torch.empty(fp.n, dtype=torch.float64).pin_memory() for _ in range(3)]
     init_host = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                  for k, a in (fp.initial or {}).items()}
@@ -453,7 +454,10 @@ def run_native(args):
                              "FP64 refinement)"}.get(
                            args.precision, "k_bicgstab<1> (pressure-correction BiCGSTAB, persistent)"),
             "launches": kp["launches"], "avg_launch_ms": kp["ms"] / max(kp["launches"], 1),
-            "bytes_per_unit": (f"2q(4+4)+14*4 = {2 * fp.q * 8 + 56} B per FP32 row-iteration"
+            "bytes_per_unit": (f"6q(8+4)+32*8 = {6 * fp.q * 12 + 256} B per row-iteration "
+                               f"(2 SpMV + 2 V-cycles) + the coarse levels' operators"
+                               if args.precond == "amg" else
+                               f"2q(4+4)+14*4 = {2 * fp.q * 8 + 56} B per FP32 row-iteration"
                                if args.precision == "mixed" else
                                f"2q(8+4)+14*8 = {2 * fp.q * 12 + 112} B per row-iteration"),
             "units": kp["units"],
@@ -487,7 +491,8 @@ def run_native(args):
                "data": "synthetic",
                "config": {"workload": args.workload, "description": desc,
                           "outer_cap": args.outer, "outer_iters_per_step": all_it / args.steps / world,
-                          "precision": args.precision, "krylov_tol": 1e-12,
+                          "precision": args.precision, "precond": args.precond,
+                          "amg_levels": P.amg_info(), "krylov_tol": 1e-12,
                           "l2": "flushed between steps (256 MB write)",
                           "parallelism": f"replicas x{world}"},
                "e2e": e2e, "gpu_launches": launches, "roofline": roof,
@@ -511,6 +516,8 @@ def main():
     ap.add_argument("--criterion", type=int, default=1,
                     help="serve: 0 = steady residual R, 1 = the paper's steady error change/dt")
     ap.add_argument("--max-steps", type=int, default=3000)
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "amg"],
+                    help="preconditioner of the pressure-correction BiCGSTAB")
     ap.add_argument("--precision", default="fp64", choices=["mixed", "ff", "fp64"],
                     help="Krylov arithmetic: FP32 or float-float inside FP64 defect "
                          "correction, or FP64")

@@ -88,6 +88,17 @@ enum {
                               FP64 defect correction */
 };
 
+/* Preconditioner of the pressure-correction BiCGSTAB.  The paper only says
+ * "preconditioned" (Sec. 3); either choice stops on the same relative
+ * residual, so it changes the iteration count, not the solution. */
+enum {
+  RBFFD_PRECOND_JACOBI = 0, /* diagonal scaling (default) */
+  RBFFD_PRECOND_AMG = 1     /* one V-cycle of a smoothed-aggregation multigrid hierarchy,
+                               built on the host when the problem is built (RBFFD_PREC_FP64
+                               only; batched and served solves use Jacobi) */
+};
+#define RBFFD_AMG_MAX_LEVELS 10
+
 typedef struct rbffd_ctx rbffd_ctx;
 typedef struct rbffd_problem rbffd_problem;
 
@@ -214,6 +225,7 @@ typedef struct {
   const int8_t *tag;     /* RBFFD_TAG_* */
   const double *nx, *ny; /* outward unit normal at boundary points (0 inside) */
   const double *ubc, *vbc; /* prescribed velocity at boundary points */
+  int32_t precond;         /* RBFFD_PRECOND_* of the p' solve */
 } rbffd_problem_desc;
 
 /* Allocate a problem and build everything that depends only on the points
@@ -232,6 +244,10 @@ int rbffd_problem_reload(rbffd_problem *prob, const rbffd_problem_desc *desc);
 void rbffd_problem_destroy(rbffd_problem *prob);
 /* Device bytes held by the problem. */
 size_t rbffd_problem_bytes(const rbffd_problem *prob);
+/* Multigrid hierarchy of the p' preconditioner: *levels (0 with Jacobi),
+ * rows and nonzeros per level (arrays of RBFFD_AMG_MAX_LEVELS, nullable). */
+int rbffd_problem_amg_info(const rbffd_problem *prob, int32_t *levels, int32_t *rows,
+                           int64_t *nnz);
 
 typedef struct {
   double dt;             /* time step */

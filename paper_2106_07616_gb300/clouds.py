@@ -42,6 +42,19 @@ data here, so seeded clouds with the same structure stand in for them):
   Points are numbered along a Morton curve (stencil neighbours stay close
   in memory).
 
+* ``couette(h)``: steady cylindrical Couette flow between r1 = 0.5 (turning
+  at omega = 2) and r2 = 1 (at rest), Re = rho r1 omega (2 r1) / mu = 100.
+  Concentric rings at a radial spacing of about h, each with
+  round(2 pi r / h) points at a seeded phase; interior rings jittered by
+  +-0.25 h.  Closed form v_theta(r) = A (r2 / r - r / r2),
+  A = omega r1^2 r2 / (r2^2 - r1^2), and p(r) from dp/dr = rho v_theta^2 / r.
+* ``decaying(n_side, level)``: the decaying flow in the unit square from
+  the stream function sin^2(pi x) sin^2(pi y) / pi, no-slip walls,
+  Re = 100.  The clouds of levels 0, 1, 2 are nested: the level-l cloud is
+  the points of the finest (n_side^2) jittered lattice whose lattice
+  indices are multiples of 2^(2 - l), so coarser clouds are subsets of
+  finer ones and fields compare at shared points without interpolation.
+
 Point numbering is lattice row-major (index = j * n_side + i), which keeps
 stencil neighbours close in memory.  ``pin`` is the boundary point nearest
 the middle of the bottom edge: the pressure correction has only Neumann
@@ -352,6 +365,83 @@ def cylinder(n_target=150_000, seed=3, degree=3, q=20, re=100.0, dt=0.2, h0=0.02
         name=f"cylinder{x.shape[0]}", x=x, y=y, tag=tag.astype(np.int8), nx=nx, ny=ny,
         ubc=ubc, vbc=vbc, pin=-1, rho=1.0, mu=1.0 / re, degree=degree, q=q, dt=dt,
         initial=init)
+
+
+def couette_exact(x, y, r1=0.5, r2=1.0, omega=2.0, rho=1.0):
+    """Cylindrical Couette flow; pressure zero at r = r2."""
+    r = np.hypot(x, y)
+    a = omega * r1 * r1 * r2 / (r2 * r2 - r1 * r1)
+    vt = a * (r2 / r - r / r2)
+    th = np.arctan2(y, x)
+
+    def prim(rr):  # integral of v_theta^2 / r
+        return a * a * (-r2 * r2 / (2 * rr * rr) - 2.0 * np.log(rr) + rr * rr / (2 * r2 * r2))
+    return -vt * np.sin(th), vt * np.cos(th), rho * (prim(r) - prim(r2))
+
+
+def couette(h=0.036, r1=0.5, r2=1.0, omega=2.0, re=100.0, seed=7, degree=3, q=None, dt=None):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nr = max(2, int(round((r2 - r1) / h)))
+    dr = (r2 - r1) / nr
+    xs, ys, ts, nxs, nys = [], [], [], [], []
+    for k in range(nr + 1):
+        r = r1 + k * dr
+        cnt = max(8, int(round(2.0 * math.pi * r / h)))
+        th = 2.0 * math.pi * (np.arange(cnt) + rng.uniform()) / cnt
+        if 0 < k < nr:
+            rr = r + rng.uniform(-0.25, 0.25, cnt) * dr
+            tt = th + rng.uniform(-0.25, 0.25, cnt) * h / r
+            xs.append(rr * np.cos(tt)); ys.append(rr * np.sin(tt))
+            ts.append(np.full(cnt, TAG_INTERIOR, np.int8))
+            nxs.append(np.zeros(cnt)); nys.append(np.zeros(cnt))
+        else:
+            xs.append(r * np.cos(th)); ys.append(r * np.sin(th))
+            ts.append(np.full(cnt, TAG_DIRICHLET, np.int8))
+            sgn = -1.0 if k == 0 else 1.0  # out of the fluid
+            nxs.append(sgn * np.cos(th)); nys.append(sgn * np.sin(th))
+    x, y = np.concatenate(xs), np.concatenate(ys)
+    tag, nx, ny = np.concatenate(ts), np.concatenate(nxs), np.concatenate(nys)
+    order = _morton_order(x, y)
+    x, y, tag, nx, ny = x[order], y[order], tag[order], nx[order], ny[order]
+    ue, ve, pe = couette_exact(x, y, r1, r2, omega)
+    bnd = tag != TAG_INTERIOR
+    m = num_monomials(degree)
+    if q is None:
+        q = 2 * m
+    if dt is None:
+        dt = 10.0 * h / (omega * r1)  # Courant ~10 at the wall speed
+    pin = _pin_index(x, y, bnd, r2, 0.0)
+    return FlowProblem(
+        name=f"couette{x.shape[0]}", x=x, y=y, tag=tag, nx=nx, ny=ny,
+        ubc=np.where(bnd, ue, 0.0), vbc=np.where(bnd, ve, 0.0), pin=pin, rho=1.0,
+        mu=omega * r1 * 2 * r1 / re, degree=degree, q=q, dt=float(dt),
+        exact={"u": ue, "v": ve, "p": pe})
+
+
+def decaying(n_side=65, level=2, seed=8, degree=3, q=None, re=100.0, dt=0.01):
+    """Nested clouds of the decaying flow (see the module docstring); the
+    initial fields are in ``initial``; ``lattice`` holds each point's
+    finest-lattice (i, j)."""
+    if (n_side - 1) % 4:
+        raise ValueError("n_side - 1 must be a multiple of 4")
+    x, y, bnd, nx, ny, ii, jj = _box_cloud(n_side, 0.0, 1.0, seed)
+    stride = 1 << (2 - level)
+    keep = (ii % stride == 0) & (jj % stride == 0)
+    x, y, bnd, nx, ny, ii, jj = (a[keep] for a in (x, y, bnd, nx, ny, ii, jj))
+    tag = np.where(bnd, TAG_DIRICHLET, TAG_INTERIOR).astype(np.int8)
+    s2 = np.sin(math.pi * x) ** 2, np.sin(math.pi * y) ** 2
+    u0 = s2[0] * np.sin(2 * math.pi * y)
+    v0 = -np.sin(2 * math.pi * x) * s2[1]
+    u0[bnd] = 0.0
+    v0[bnd] = 0.0
+    m = num_monomials(degree)
+    fp = FlowProblem(
+        name=f"decaying{(n_side - 1) // stride + 1}", x=x, y=y, tag=tag, nx=nx, ny=ny,
+        ubc=np.zeros_like(x), vbc=np.zeros_like(x), pin=_pin_index(x, y, bnd, 0.5, 0.0),
+        rho=1.0, mu=1.0 / re, degree=degree, q=2 * m if q is None else q, dt=dt,
+        initial={"u": u0, "un": u0, "unm1": u0, "v": v0, "vn": v0, "vnm1": v0})
+    fp.lattice = (ii, jj)
+    return fp
 
 
 def random_cloud(n, seed, lo=0.0, hi=1.0):

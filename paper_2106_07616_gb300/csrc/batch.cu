@@ -99,7 +99,7 @@ int BatchScratch::reserve(rbffd_ctx *c, int members) {
 // One batched Krylov launch for the systems args[0..m) (args filled except
 // nblocks, tpr, flags and bar, which are set here).
 static int launch_krylov(BatchScratch &S, int nr, std::vector<KrylovArgs> &args,
-                         const std::vector<int> &rows) {
+                         const std::vector<int> &rows, bool amg = false) {
   rbffd_ctx *ctx = S.ctx;
   const int m = (int)args.size();
   const int cmax = krylov_batch_max_ctas(ctx, nr);
@@ -149,7 +149,7 @@ static int launch_krylov(BatchScratch &S, int nr, std::vector<KrylovArgs> &args,
   RBFFD_CK(cudaMemsetAsync(dbars, 0, sizeof(GridBarrier) * m, ctx->stream));
   RBFFD_TRY(krylov_batch_launch(ctx, nr, nctas, (const KrylovArgs *)(db + S.off_sys),
                                 (const int *)(db + S.off_cta_sys),
-                                (const int *)(db + S.off_cta_first)));
+                                (const int *)(db + S.off_cta_first), amg));
   // the pinned tables are reused by the next launch: wait until copied
   RBFFD_CK(cudaStreamSynchronize(ctx->stream));
   return RBFFD_OK;
@@ -172,10 +172,9 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
   // momentum predictor of every member, then one launch for the two-RHS
   // solves of all members (and one for the single-RHS pairs, if any)
   std::vector<KrylovArgs> a2, a1s, a1(m);
-  std::vector<int> rows2, rows1s, rows(m);
+  std::vector<int> rows2, rows1s;
   for (int i = 0; i < m; ++i) {
     const rbffd_step_params *sp = spv[i];
-    rows[i] = P[i]->n;
     RBFFD_TRY(ops_momentum(P[i], sp));
     KrylovArgs a;
     memset(&a, 0, sizeof(a));
@@ -223,6 +222,10 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
   if (!a2.empty()) RBFFD_TRY(launch_krylov(S, 2, a2, rows2));
   if (!a1s.empty()) RBFFD_TRY(launch_krylov(S, 1, a1s, rows1s));
   prof_end(ctx, 0);
+  // p' solves: members with a multigrid hierarchy in one launch, the
+  // Jacobi-preconditioned ones in another
+  std::vector<KrylovArgs> pj, pa;
+  std::vector<int> rj, ra;
   for (int i = 0; i < m; ++i) {
     RBFFD_TRY(ops_divergence(P[i], spv[i]));
     a1[i].val = P[i]->Pp;
@@ -234,9 +237,19 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
     a1[i].w[0] = P[i]->kv[0];
     a1[i].out = P[i]->kout + 2;
     a1[i].nblocks = 2 * std::max(P[i]->kblocks1, P[i]->kblocks2);
+    if (P[i]->amg) {
+      a1[i].amg = P[i]->amg;
+      a1[i].dinv = P[i]->amg_host.lev[0].wdinv;
+      pa.push_back(a1[i]);
+      ra.push_back(P[i]->n);
+    } else {
+      pj.push_back(a1[i]);
+      rj.push_back(P[i]->n);
+    }
   }
   prof_begin(ctx, 1);
-  RBFFD_TRY(launch_krylov(S, 1, a1, rows));
+  if (!pj.empty()) RBFFD_TRY(launch_krylov(S, 1, pj, rj));
+  if (!pa.empty()) RBFFD_TRY(launch_krylov(S, 1, pa, ra, true));
   prof_end(ctx, 1);
   for (int i = 0; i < m; ++i) {
     RBFFD_TRY(ops_pressure(P[i], spv[i]));
@@ -270,7 +283,7 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
       um += n * im;
       up += n * ip;
       bm += n * im * (2 * q * 12.0 + 28 * 8.0);
-      bp += n * ip * (2 * q * 12.0 + 14 * 8.0);
+      bp += pcorr_bytes(P[i], mo[i].iters[2]);
     }
     prof_collect(ctx, 0, RBFFD_KSTAT_KRYLOV_MOM, um, bm);
     prof_collect(ctx, 1, RBFFD_KSTAT_KRYLOV_P, up, bp);

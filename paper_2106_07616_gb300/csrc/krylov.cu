@@ -20,6 +20,7 @@
 // with __ldcg (L2, coherent across SMs); row-local vectors are only ever
 // touched by the thread that owns the row; the matrix never changes during
 // a solve and goes through the read-only path.
+#include "amg_dev.cuh"
 #include "common.cuh"
 #include "krylov.cuh"
 #include "krylov_dev.cuh"
@@ -56,8 +57,13 @@ struct KScalars {
 // solve it is simply unused.  rho' equals (r^, r) in exact arithmetic.
 // The solve of one system by the nb CTAs lb = 0..nb-1 that share it (the
 // whole grid for a single system; a subrange of a batched launch).
-template <int NR, int NT>
+// AMGP: the preconditioner is a V-cycle of the hierarchy A.amg instead of
+// the Jacobi scaling (one right-hand side); A.dinv then holds level 0's
+// smoother weights, and the loops that form p and s write its pre-smoothed
+// start w D^-1 p (or s) instead of p^ (s^).
+template <int NR, int NT, bool AMGP = false>
 __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb, const int nb) {
+  static_assert(!AMGP || NR == 1, "the multigrid preconditioner serves one right-hand side");
   __shared__ double sred[5 * NR * NT];  // block_partials of up to 5 NR values
   __shared__ double stot[16];
   __shared__ KScalars ks[NR];
@@ -71,6 +77,11 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
   auto P = [&](int slot, int k) { return part + (size_t)(slot * NR + k) * nb; };
   const bool leader = threadIdx.x == 0;
   int *err = &A.bar->err;
+  double *amg_x0 = nullptr;
+  amgdev::Ctx actx{&A, lb, nb, tid, stride, wglobal, nwarps, stot};
+  if constexpr (AMGP) amg_x0 = A.amg->lev[0].x;
+  (void)amg_x0;
+  (void)actx;
 
   if (leader) {
 #pragma unroll
@@ -114,7 +125,10 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
                         A.w[k].r[i] = ri;
                         A.w[k].rh[i] = ri;
                         A.w[k].p[i] = ri;
-                        A.w[k].ph[i] = ri * di;
+                        if constexpr (AMGP)
+                          amg_x0[i] = ri * di;
+                        else
+                          A.w[k].ph[i] = ri * di;
                         acc[2 * k] += bi * bi;
                         acc[2 * k + 1] += ri * ri;
                       }
@@ -179,6 +193,12 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
     for (int k = 0; k < NR; ++k) run[k] = ks[k].run != 0;
 
     // ---------------- A: v = A p^, partial (r^, v)
+    if constexpr (AMGP) {
+      if (!amgdev::vcycle(A.amg, actx, A.w[0].p, A.w[0].ph, epoch)) {
+        ok = false;
+        break;
+      }
+    }
     {
       double acc[NR];
 #pragma unroll
@@ -222,11 +242,20 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
           if (!run[k]) continue;
           const double si = A.w[k].r[i] - alp[k] * A.w[k].v[i];
           A.w[k].s[i] = si;
-          A.w[k].sh[i] = si * di;
+          if constexpr (AMGP)
+            amg_x0[i] = si * di;
+          else
+            A.w[k].sh[i] = si * di;
         }
       }
       ok = kdev::exchange<0, double>(A.flags, err, epoch++, nullptr, nullptr, stot, lb, nb);
       if (!ok) break;
+      if constexpr (AMGP) {
+        if (!amgdev::vcycle(A.amg, actx, A.w[0].s, A.w[0].sh, epoch)) {
+          ok = false;
+          break;
+        }
+      }
     }
 
     // ---------------- C: t = A s^, partials (s,s) (t,t) (t,s) (r^,s) (r^,t)
@@ -324,7 +353,10 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
             acc[k] += ri * ri;
             const double pi = ri + bet[k] * (A.w[k].p[i] - omg[k] * A.w[k].v[i]);
             A.w[k].p[i] = pi;
-            A.w[k].ph[i] = pi * di;
+            if constexpr (AMGP)
+              amg_x0[i] = pi * di;
+            else
+              A.w[k].ph[i] = pi * di;
           }
         }
       }
@@ -382,6 +414,12 @@ __global__ void __launch_bounds__(NT) k_bicgstab(KrylovArgs A) {
   bicgstab_body<NR, NT>(A, blockIdx.x, gridDim.x);
 }
 
+// One right-hand side, multigrid-preconditioned (A.amg set).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_bicgstab_amg(KrylovArgs A) {
+  bicgstab_body<1, NT, true>(A, blockIdx.x, gridDim.x);
+}
+
 // Many independent systems in one cooperative launch: CTA b works on system
 // cta_sys[b]; the CTAs of one system are consecutive and synchronise only
 // with each other, so systems progress (and finish) independently.
@@ -396,6 +434,18 @@ __global__ void __launch_bounds__(NT) k_bicgstab_batch(const KrylovArgs *__restr
   bicgstab_body<NR, NT>(A, blockIdx.x - cta_first[s], A.nblocks);
 }
 
+// Batched launch of multigrid-preconditioned single-RHS systems.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_bicgstab_batch_amg(const KrylovArgs *__restrict__ sys,
+                                                           const int *__restrict__ cta_sys,
+                                                           const int *__restrict__ cta_first) {
+  __shared__ KrylovArgs A;
+  const int s = cta_sys[blockIdx.x];
+  if (threadIdx.x == 0) A = sys[s];
+  __syncthreads();
+  bicgstab_body<1, NT, true>(A, blockIdx.x - cta_first[s], A.nblocks);
+}
+
 namespace {
 constexpr int NT1 = 1024;  // threads per block, one right-hand side
 constexpr int NT2 = 512;   // two right-hand sides (more registers per thread)
@@ -406,10 +456,15 @@ inline int nt_for(int nr) { return nr == 1 ? NT1 : NT2; }
 int krylov_max_blocks(rbffd_ctx *ctx, int nr) {
   int per_sm = 0;
   cudaError_t e;
-  if (nr == 1)
+  if (nr == 1) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab<1, NT1>, NT1, 0);
-  else
+    int per_sm_amg = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_amg, k_bicgstab_amg<NT1>, NT1, 0);
+    if (per_sm_amg < per_sm) per_sm = per_sm_amg;
+  } else {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab<2, NT2>, NT2, 0);
+  }
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return 0;
@@ -451,7 +506,10 @@ int krylov_launch(rbffd_ctx *ctx, int nr, int nblocks, const KrylovArgs &args) {
   RBFFD_CK(cudaMemsetAsync(args.flags, 0, sizeof(unsigned int) * nblocks, ctx->stream));
   void *kargs[] = {(void *)&args};
   cudaError_t e;
-  if (nr == 1)
+  if (nr == 1 && args.amg)
+    e = cudaLaunchCooperativeKernel((const void *)k_bicgstab_amg<NT1>, dim3(nblocks), dim3(NT1),
+                                    kargs, 0, ctx->stream);
+  else if (nr == 1)
     e = cudaLaunchCooperativeKernel((const void *)k_bicgstab<1, NT1>, dim3(nblocks), dim3(NT1),
                                     kargs, 0, ctx->stream);
   else
@@ -470,10 +528,15 @@ size_t krylov_partials_doubles(int nr, int nblocks) { return (size_t)S_COUNT * n
 int krylov_batch_max_ctas(rbffd_ctx *ctx, int nr) {
   int per_sm = 0;
   cudaError_t e;
-  if (nr == 1)
+  if (nr == 1) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_batch<1, KB_NT>, KB_NT,
                                                       0);
-  else
+    int per_sm_amg = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_amg,
+                                                        k_bicgstab_batch_amg<KB_NT>, KB_NT, 0);
+    if (per_sm_amg < per_sm) per_sm = per_sm_amg;
+  } else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_batch<2, KB_NT>, KB_NT,
                                                       0);
   if (e != cudaSuccess || per_sm < 1) {
@@ -484,14 +547,15 @@ int krylov_batch_max_ctas(rbffd_ctx *ctx, int nr) {
 }
 
 int krylov_batch_launch(rbffd_ctx *ctx, int nr, int nctas, const KrylovArgs *d_sys,
-                        const int *d_cta_sys, const int *d_cta_first) {
+                        const int *d_cta_sys, const int *d_cta_first, bool amg) {
   if (nctas < 1 || nctas > krylov_batch_max_ctas(ctx, nr)) {
     set_error("krylov_batch_launch: %d CTAs are not co-resident", nctas);
     return RBFFD_EINVAL;
   }
   void *kargs[] = {(void *)&d_sys, (void *)&d_cta_sys, (void *)&d_cta_first};
-  const void *fn = nr == 1 ? (const void *)k_bicgstab_batch<1, KB_NT>
-                           : (const void *)k_bicgstab_batch<2, KB_NT>;
+  const void *fn = amg ? (const void *)k_bicgstab_batch_amg<KB_NT>
+                   : nr == 1 ? (const void *)k_bicgstab_batch<1, KB_NT>
+                             : (const void *)k_bicgstab_batch<2, KB_NT>;
   cudaError_t e =
       cudaLaunchCooperativeKernel(fn, dim3(nctas), dim3(KB_NT), kargs, 0, ctx->stream);
   ctx->launches++;

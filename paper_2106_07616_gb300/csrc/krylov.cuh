@@ -34,6 +34,7 @@ struct KrylovArgs {
   int maxit;
   int tpr;              // threads per row in the SpMV phases (1..8)
   int nblocks;          // CTAs that share the solve (batched launches)
+  const struct AmgDev *amg;  // multigrid preconditioner (one RHS), or null: Jacobi
 };
 
 constexpr int KB_NT = 256;  // threads per CTA of batched Krylov launches
@@ -81,8 +82,9 @@ int krylov_batch_max_ctas(rbffd_ctx *ctx, int nr);
 // d_sys: device array of per-system arguments (nblocks, flags and partials
 // sized for that many CTAs); d_cta_sys / d_cta_first: per CTA, its system
 // and per system, its first CTA.  Flags and barrier words must be zeroed.
+// amg: every system has a multigrid preconditioner (nr = 1).
 int krylov_batch_launch(rbffd_ctx *ctx, int nr, int nctas, const KrylovArgs *d_sys,
-                        const int *d_cta_sys, const int *d_cta_first);
+                        const int *d_cta_sys, const int *d_cta_first, bool amg = false);
 int krylov_launch(rbffd_ctx *ctx, int nr, int nblocks, const KrylovArgs &args);
 size_t krylov_partials_doubles(int nr, int nblocks);
 

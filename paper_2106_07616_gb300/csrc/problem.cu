@@ -58,7 +58,24 @@ int check_desc(const rbffd_problem_desc *d) {
     set_error("problem desc: rho must be > 0 and mu >= 0");
     return RBFFD_EINVAL;
   }
+  if (d->precond != RBFFD_PRECOND_JACOBI && d->precond != RBFFD_PRECOND_AMG) {
+    set_error("problem desc: unknown preconditioner %d", d->precond);
+    return RBFFD_EINVAL;
+  }
+  if (d->precond == RBFFD_PRECOND_AMG && d->precision != RBFFD_PREC_FP64) {
+    set_error("problem desc: the multigrid preconditioner needs RBFFD_PREC_FP64");
+    return RBFFD_ENOTIMPL;
+  }
   return RBFFD_OK;
+}
+
+void free_amg(rbffd_problem *P) {
+  if (P->amg_mem) dev_free(P->ctx, P->amg_mem, P->amg_bytes);
+  P->amg_mem = nullptr;
+  P->amg_bytes = 0;
+  P->amg = nullptr;
+  memset(&P->amg_host, 0, sizeof(P->amg_host));
+  memset(&P->amg_info, 0, sizeof(P->amg_info));
 }
 
 // Copy the inputs, build clouds, weights and operators, reset the state.
@@ -121,6 +138,12 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
                         P->wl_rm, P->d_first_singular));
   prof_end(ctx, 0);
   RBFFD_TRY(ops_pack(P));
+  free_amg(P);
+  P->precond = d->precond;
+  if (P->precond == RBFFD_PRECOND_AMG) {
+    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, &P->amg_mem, &P->amg_bytes,
+                        &P->amg, &P->amg_host, &P->amg_info));
+  }
   if (P->precision != RBFFD_PREC_FP64) {
     RBFFD_TRY(ops_to_inner(P, P->Pp, P->Pin, (int64_t)P->ldn * P->q));
     RBFFD_TRY(ops_to_inner(P, P->p_dinv, P->pdin, P->ldn));
@@ -275,6 +298,10 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   // pressure correction
   a.val = P->Pp;
   a.dinv = P->p_dinv;
+  if (P->amg) {  // V-cycle preconditioner; level 0's smoother weights in dinv
+    a.amg = P->amg;
+    a.dinv = P->amg_host.lev[0].wdinv;
+  }
   a.b[0] = P->bp;
   a.b[1] = nullptr;
   a.x[0] = P->pc;
@@ -487,12 +514,27 @@ extern "C" void rbffd_problem_destroy(rbffd_problem *P) {
   rbffd_ctx *ctx = P->ctx;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  free_amg(P);
   dev_free(ctx, P->mem, P->bytes);
   delete P;
   ctx_unref(ctx);
 }
 
-extern "C" size_t rbffd_problem_bytes(const rbffd_problem *P) { return P ? P->bytes : 0; }
+extern "C" size_t rbffd_problem_bytes(const rbffd_problem *P) {
+  return P ? P->bytes + P->amg_bytes : 0;
+}
+
+extern "C" int rbffd_problem_amg_info(const rbffd_problem *P, int32_t *levels, int32_t *rows,
+                                      int64_t *nnz) {
+  if (!P) return RBFFD_EINVAL;
+  if (levels) *levels = P->amg ? P->amg_info.nlev : 0;
+  for (int l = 0; l < RBFFD_AMG_MAX_LEVELS; ++l) {
+    const bool have = P->amg && l < P->amg_info.nlev;
+    if (rows) rows[l] = have ? P->amg_info.n[l] : 0;
+    if (nnz) nnz[l] = have ? P->amg_info.nnz[l] : 0;
+  }
+  return RBFFD_OK;
+}
 
 extern "C" int simple_iterate(rbffd_problem *P, const rbffd_step_params *sp, double *delta_out,
                               rbffd_iter_stats *stats) {
@@ -509,7 +551,8 @@ extern "C" int simple_iterate(rbffd_problem *P, const rbffd_step_params *sp, dou
     int im = r.kout[0].iters > r.kout[1].iters ? r.kout[0].iters : r.kout[1].iters;
     double um = n * im, upc = n * r.kout[2].iters;
     prof_collect(P->ctx, 0, RBFFD_KSTAT_KRYLOV_MOM, um, um * (2 * q * (sw + si) + 28 * sv));
-    prof_collect(P->ctx, 1, RBFFD_KSTAT_KRYLOV_P, upc, upc * (2 * q * (sw + si) + 14 * sv));
+    prof_collect(P->ctx, 1, RBFFD_KSTAT_KRYLOV_P, upc,
+                 mx ? upc * (2 * q * (sw + si) + 14 * sv) : pcorr_bytes(P, r.kout[2].iters));
     prof_collect(P->ctx, 2, RBFFD_KSTAT_OUTER, 1.0, 0.0);
   }
   if (stats) {
@@ -580,6 +623,22 @@ extern "C" int rbffd_steady_residual(rbffd_problem *P, double *R3) {
 }
 
 namespace rbffd {
+// Algorithmic bytes of an FP64 p' solve of `iters` BiCGSTAB iterations:
+// per row-iteration 2 SpMVs (q (8 + 4) B each) and 14 vector passes; with
+// the multigrid preconditioner two V-cycles more, each 2 level-0 SpMVs and
+// ~9 level-0 vector passes plus the coarser levels' operators, transfers
+// and vectors (and the dense coarsest inverse).
+double pcorr_bytes(const rbffd_problem *P, int iters) {
+  const double n = P->n, q = P->q, it = iters;
+  if (!P->amg) return n * it * (2 * q * 12 + 14 * 8);
+  const AmgInfo &I = P->amg_info;
+  double coarse = 12.0 * I.nnz_p[0];
+  for (int l = 1; l < I.nlev; ++l)
+    coarse += l + 1 < I.nlev ? 24.0 * I.nnz[l] + 12.0 * I.nnz_p[l] + 80.0 * I.n[l]
+                             : 8.0 * I.n[l] * I.n[l];
+  return n * it * (6 * q * 12 + 14 * 8 + 2 * 9 * 8) + 2.0 * it * coarse;
+}
+
 // The steady test: R <= tol, or (criterion 1) the paper's steady error
 // change / dt <= tol.
 bool steady_done(const rbffd_solve_params *s, double R, double change) {

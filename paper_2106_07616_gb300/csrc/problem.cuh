@@ -1,6 +1,7 @@
 // problem.cuh -- device-resident state of one flow problem.
 #pragma once
 #include "common.cuh"
+#include "amg.cuh"
 #include "knn.cuh"
 #include "krylov.cuh"
 
@@ -58,12 +59,22 @@ struct rbffd_problem {
   // one allocation holds everything above
   void *mem = nullptr;
   size_t bytes = 0;
+  // multigrid preconditioner of the p' solve (its own allocation), or none
+  int precond = 0;
+  void *amg_mem = nullptr;
+  size_t amg_bytes = 0;
+  const rbffd::AmgDev *amg = nullptr;  // device copy of the level table
+  rbffd::AmgDev amg_host{};             // host copy (device pointers)
+  rbffd::AmgInfo amg_info{};
 };
 
 namespace rbffd {
 // End of a BDF2 time step (rotation of the time levels); change = mean
 // |u - u^n| + mean |v - v^n| of the step.  Synchronises the stream.
 int problem_step_end(rbffd_problem *P, double *change);
+// Algorithmic bytes of an FP64 pressure-correction solve of `iters`
+// iterations (the roofline numerator of the p' kernel statistics).
+double pcorr_bytes(const rbffd_problem *P, int iters);
 // Steady stopping test of solve_steady and of the request server.
 bool steady_done(const rbffd_solve_params *s, double R, double change);
 }  // namespace rbffd

@@ -24,6 +24,8 @@ TAG_INTERIOR, TAG_DIRICHLET, TAG_OUTFLOW, TAG_SYMMETRY = 0, 1, 2, 3
 FIELDS = {"u": 0, "v": 1, "p": 2, "un": 3, "vn": 4, "unm1": 5, "vnm1": 6, "ut": 7, "vt": 8,
           "pc": 9, "ubc": 10, "vbc": 11}
 PREC_FP64, PREC_MIXED, PREC_MIXED_FF = 0, 1, 2
+PRECOND_JACOBI, PRECOND_AMG = 0, 1
+AMG_MAX_LEVELS = 10
 
 
 class RbffdError(RuntimeError):
@@ -36,7 +38,8 @@ class ProblemDesc(C.Structure):
     _fields_ = [("n", C.c_int32), ("q", C.c_int32), ("degree", C.c_int32), ("pin", C.c_int32),
                 ("rho", C.c_double), ("mu", C.c_double), ("precision", C.c_int32),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("tag", C.c_void_p), ("nx", C.c_void_p),
-                ("ny", C.c_void_p), ("ubc", C.c_void_p), ("vbc", C.c_void_p)]
+                ("ny", C.c_void_p), ("ubc", C.c_void_p), ("vbc", C.c_void_p),
+                ("precond", C.c_int32)]
 
 
 class StepParams(C.Structure):
@@ -109,6 +112,7 @@ def load(path: str = LIB_PATH):
         "rbffd_problem_reload": (C.c_int, [vp, C.POINTER(ProblemDesc)]),
         "rbffd_problem_destroy": (None, [vp]),
         "rbffd_problem_bytes": (sz, [vp]),
+        "rbffd_problem_amg_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
         "simple_iterate": (C.c_int, [vp, C.POINTER(StepParams), C.POINTER(dbl),
                                      C.POINTER(IterStats)]),
         "rbffd_time_step": (C.c_int, [vp, C.POINTER(SolveParams), dbl, C.POINTER(i32),
@@ -219,7 +223,7 @@ def rbffd_weights(ctx, x, y, q, idx, degree, wx, wy, wl):
     return -1
 
 
-def make_desc(fp, precision=PREC_FP64, keep=None):
+def make_desc(fp, precision=PREC_FP64, keep=None, precond=PRECOND_JACOBI):
     """ProblemDesc for a FlowProblem (host numpy arrays, copied by the
     library at create/reload).  `keep` receives the arrays to keep alive."""
     arrs = {
@@ -234,16 +238,19 @@ def make_desc(fp, precision=PREC_FP64, keep=None):
     d = ProblemDesc()
     d.n, d.q, d.degree, d.pin = fp.n, fp.q, fp.degree, int(fp.pin)
     d.rho, d.mu, d.precision = float(fp.rho), float(fp.mu), int(precision)
+    d.precond = int(precond)
     for k, a in arrs.items():
         setattr(d, k, a.ctypes.data)
     return d
 
 
-def desc_from_pointers(n, q, degree, pin, rho, mu, precision, x, y, tag, nx, ny, ubc, vbc):
+def desc_from_pointers(n, q, degree, pin, rho, mu, precision, x, y, tag, nx, ny, ubc, vbc,
+                       precond=PRECOND_JACOBI):
     """ProblemDesc from raw host or device buffers (tensors or arrays)."""
     d = ProblemDesc()
     d.n, d.q, d.degree, d.pin = int(n), int(q), int(degree), int(pin)
     d.rho, d.mu, d.precision = float(rho), float(mu), int(precision)
+    d.precond = int(precond)
     for k, a in (("x", x), ("y", y), ("tag", tag), ("nx", nx), ("ny", ny), ("ubc", ubc),
                  ("vbc", vbc)):
         setattr(d, k, ptr(a))
@@ -253,18 +260,18 @@ def desc_from_pointers(n, q, degree, pin, rho, mu, precision, x, y, tag, nx, ny,
 class Problem:
     """A device-resident flow problem (clouds, weights, operators, fields)."""
 
-    def __init__(self, ctx, fp=None, precision=PREC_FP64, desc=None):
+    def __init__(self, ctx, fp=None, precision=PREC_FP64, desc=None, precond=PRECOND_JACOBI):
         self.ctx = ctx
         keep = {}
-        d = desc if desc is not None else make_desc(fp, precision, keep)
+        d = desc if desc is not None else make_desc(fp, precision, keep, precond)
         h = C.c_void_p()
         _check(load().rbffd_problem_create(ctx.h, C.byref(d), C.byref(h)), "rbffd_problem_create")
         self.h = h
         self.n, self.q = int(d.n), int(d.q)
 
-    def reload(self, fp=None, precision=PREC_FP64, desc=None):
+    def reload(self, fp=None, precision=PREC_FP64, desc=None, precond=PRECOND_JACOBI):
         keep = {}
-        d = desc if desc is not None else make_desc(fp, precision, keep)
+        d = desc if desc is not None else make_desc(fp, precision, keep, precond)
         _check(load().rbffd_problem_reload(self.h, C.byref(d)), "rbffd_problem_reload")
 
     def close(self):
@@ -281,6 +288,15 @@ class Problem:
     @property
     def nbytes(self) -> int:
         return int(load().rbffd_problem_bytes(self.h))
+
+    def amg_info(self):
+        """Rows and nonzeros per level of the p' multigrid hierarchy ([] with Jacobi)."""
+        lv = C.c_int32(0)
+        rows = (C.c_int32 * AMG_MAX_LEVELS)()
+        nnz = (C.c_int64 * AMG_MAX_LEVELS)()
+        _check(load().rbffd_problem_amg_info(self.h, C.byref(lv), rows, nnz),
+               "rbffd_problem_amg_info")
+        return [(int(rows[i]), int(nnz[i])) for i in range(lv.value)]
 
     def get(self, name, out=None):
         out = np.zeros(self.n) if out is None else out
@@ -406,9 +422,9 @@ class Server:
         self.n = {}
 
     def submit(self, fp, dt=None, resid_tol=1e-6, max_steps=2000, max_outer=20,
-               krylov_tol=1e-12, krylov_maxit=10000, criterion=0):
+               krylov_tol=1e-12, krylov_maxit=10000, criterion=0, precond=PRECOND_JACOBI):
         keep = {}
-        d = make_desc(fp, PREC_FP64, keep)
+        d = make_desc(fp, PREC_FP64, keep, precond)
         sp = SolveParams(fp.dt if dt is None else dt, resid_tol, max_steps, max_outer,
                          krylov_tol, krylov_maxit, 0.0, 0, criterion)
         t = C.c_uint64(0)
