@@ -245,9 +245,16 @@ void rbffd_problem_destroy(rbffd_problem *prob);
 /* Device bytes held by the problem. */
 size_t rbffd_problem_bytes(const rbffd_problem *prob);
 /* Multigrid hierarchy of the p' preconditioner: *levels (0 with Jacobi),
- * rows and nonzeros per level (arrays of RBFFD_AMG_MAX_LEVELS, nullable). */
+ * rows and nonzeros per level (arrays of RBFFD_AMG_MAX_LEVELS, nullable)
+ * and the host time its build took (nullable). */
 int rbffd_problem_amg_info(const rbffd_problem *prob, int32_t *levels, int32_t *rows,
-                           int64_t *nnz);
+                           int64_t *nnz, double *setup_ms);
+/* The same hierarchy built on the host only, for a CSR matrix (host arrays:
+ * rowptr[n+1], col and val[rowptr[n]]); no device work.  Errors:
+ * RBFFD_EINVAL, RBFFD_ESINGULAR (singular coarsest matrix), RBFFD_ENOTIMPL
+ * (coarsening stalled above 600 rows). */
+int rbffd_amg_analyze(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                      int32_t *levels, int32_t *rows, int64_t *nnz, double *setup_ms);
 
 typedef struct {
   double dt;             /* time step */

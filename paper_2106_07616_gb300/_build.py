@@ -21,7 +21,8 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
           "--expt-relaxed-constexpr"]
 # per-source extra flags: the weight kernel keeps every product and sum a
 # separate rounding (its arithmetic is spelled with __d*_rn intrinsics too)
-EXTRA = {"weights.cu": ["-fmad=false"], "knn.cu": ["-fmad=false"]}
+EXTRA = {"weights.cu": ["-fmad=false"], "knn.cu": ["-fmad=false"],
+         "amg.cu": ["-Xcompiler", "-fopenmp"]}
 
 
 def nvcc() -> str:
@@ -64,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nv, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+        cmd = [nv, *ARCH, "-shared", "-cudart", "shared", "-lgomp", "-o", tmp, *objs,
                "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-lpthread"]
         run(cmd)
         os.replace(tmp, LIB)

@@ -9,13 +9,20 @@
 //   tentative prolongation T (one 1 per row, in the point's aggregate);
 //   smoothed prolongation P = (I - w_P D^-1 A) T, w_P = 4 / (3 rho(D^-1 A))
 //     (rho by power iteration);
-//   R = P^T, A_{l+1} = R A P (Gustavson sparse products);
+//   R = P^T, A_{l+1} = (R A) P (Gustavson sparse products);
+//   the fused V-cycle operators S, R~, P~ of amg.cuh;
 // until at most AMG_NCOARSE rows remain, whose matrix is inverted densely.
-// Everything is deterministic: fixed start vectors, index-ordered loops.
+// Everything is deterministic: fixed start vectors, index-ordered loops;
+// the sparse products run over rows in parallel (OpenMP) with per-thread
+// accumulators, each row's result independent of the thread count.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include "amg.cuh"
 
@@ -40,93 +47,185 @@ Csr from_ell(int n, int q, int ldn, const std::vector<int32_t> &col,
   Csr A;
   A.n = A.m = n;
   A.ptr.assign(n + 1, 0);
-  A.col.reserve((size_t)n * q);
-  A.val.reserve((size_t)n * q);
+  auto kept = [&](int i, int j) {  // identity rows store zero weights
+    const size_t e = (size_t)j * ldn + i;
+    return val[e] != 0.0 || col[e] == i;
+  };
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
-    for (int j = 0; j < q; ++j) {
-      const size_t e = (size_t)j * ldn + i;
-      const int c = col[e];
-      const double v = val[e];
-      if (v == 0.0 && c != i) continue;  // identity rows store zero weights
-      A.col.push_back(c);
-      A.val.push_back(v);
-    }
-    A.ptr[i + 1] = (int32_t)A.col.size();
+    int c = 0;
+    for (int j = 0; j < q; ++j) c += kept(i, j);
+    A.ptr[i + 1] = c;
+  }
+  for (int i = 0; i < n; ++i) A.ptr[i + 1] += A.ptr[i];
+  A.col.resize(A.ptr[n]);
+  A.val.resize(A.ptr[n]);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; ++i) {
+    int k = A.ptr[i];
+    for (int j = 0; j < q; ++j)
+      if (kept(i, j)) {
+        const size_t e = (size_t)j * ldn + i;
+        A.col[k] = col[e];
+        A.val[k++] = val[e];
+      }
   }
   return A;
 }
 
 std::vector<double> diagonal(const Csr &A) {
   std::vector<double> d(A.n, 0.0);
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < A.n; ++i)
     for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
       if (A.col[k] == i) d[i] += A.val[k];
   return d;
 }
 
-// |lambda|max of D^-1 A by 15 power steps from a fixed non-constant start
+// A CSR matrix whose row i is produced by row(i, mark, emit): `mark` is a
+// per-thread int array of m entries (the row index marks a column as seen),
+// emit(c, v) adds v at column c.  Two parallel passes -- sizes, then values
+// into place -- so no per-row allocation; column order = first emission.
+template <typename RowFn>
+Csr build_rows(int n, int m, RowFn &&row) {
+  Csr C;
+  C.n = n;
+  C.m = m;
+  C.ptr.assign(n + 1, 0);
+#pragma omp parallel
+  {
+    std::vector<int32_t> mark(m, -1);
+#pragma omp for schedule(dynamic, 256)
+    for (int i = 0; i < n; ++i) {
+      int cnt = 0;
+      row(i, mark, [&](int c, double) {
+        if (mark[c] != i) {
+          mark[c] = i;
+          ++cnt;
+        }
+      });
+      C.ptr[i + 1] = cnt;
+    }
+  }
+  for (int i = 0; i < n; ++i) C.ptr[i + 1] += C.ptr[i];
+  C.col.resize(C.ptr[n]);
+  C.val.resize(C.ptr[n]);
+#pragma omp parallel
+  {
+    std::vector<int32_t> mark(m, -1), where(m, 0);
+#pragma omp for schedule(dynamic, 256)
+    for (int i = 0; i < n; ++i) {
+      int o = C.ptr[i];
+      row(i, mark, [&](int c, double v) {
+        if (mark[c] != i) {
+          mark[c] = i;
+          where[c] = o;
+          C.col[o] = c;
+          C.val[o++] = v;
+        } else {
+          C.val[where[c]] += v;
+        }
+      });
+    }
+  }
+  return C;
+}
+
+Csr transpose(const Csr &A) {
+  Csr T;
+  T.n = A.m;
+  T.m = A.n;
+  T.ptr.assign(A.m + 1, 0);
+  for (int32_t c : A.col) T.ptr[c + 1]++;
+  for (int i = 0; i < A.m; ++i) T.ptr[i + 1] += T.ptr[i];
+  T.col.resize(A.col.size());
+  T.val.resize(A.val.size());
+  std::vector<int32_t> fill(T.ptr.begin(), T.ptr.end() - 1);
+  for (int i = 0; i < A.n; ++i)
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      const int f = fill[A.col[k]]++;
+      T.col[f] = i;
+      T.val[f] = A.val[k];
+    }
+  return T;
+}
+
+// |lambda|max of D^-1 A by 12 power steps from a fixed non-constant start.
+// Norms are summed per fixed chunk of rows, then over the chunks in order,
+// so the estimate does not depend on the thread count.
 double rho_estimate(const Csr &A, const std::vector<double> &dinv) {
-  std::vector<double> x(A.n), y(A.n);
+  constexpr int CHUNK = 4096;
+  const int nch = (A.n + CHUNK - 1) / CHUNK;
+  std::vector<double> x(A.n), y(A.n), px(nch), py(nch);
   for (int i = 0; i < A.n; ++i) x[i] = 1.0 + 0.5 * (double)((i * 7919) % 13) / 13.0;
   double lam = 1.0;
-  for (int it = 0; it < 15; ++it) {
+  for (int it = 0; it < 12; ++it) {
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < nch; ++c) {
+      double sx = 0.0, sy = 0.0;
+      const int e = std::min(A.n, (c + 1) * CHUNK);
+      for (int i = c * CHUNK; i < e; ++i) {
+        double s = 0.0;
+        for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) s += A.val[k] * x[A.col[k]];
+        y[i] = dinv[i] * s;
+        sx += x[i] * x[i];
+        sy += y[i] * y[i];
+      }
+      px[c] = sx;
+      py[c] = sy;
+    }
     double nx = 0.0, ny = 0.0;
-    for (int i = 0; i < A.n; ++i) {
-      double s = 0.0;
-      for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) s += A.val[k] * x[A.col[k]];
-      y[i] = dinv[i] * s;
-      nx += x[i] * x[i];
-      ny += y[i] * y[i];
+    for (int c = 0; c < nch; ++c) {
+      nx += px[c];
+      ny += py[c];
     }
     if (!(ny > 0.0)) break;
     lam = std::sqrt(ny / nx);
     const double sc = 1.0 / std::sqrt(ny);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < A.n; ++i) x[i] = y[i] * sc;
   }
   return lam;
 }
 
-// symmetric strength graph as adjacency lists (sorted, unique)
+// symmetric strength graph as adjacency lists: row i's strong columns in
+// stored order, then the rows that hold i as strong and are not yet listed
 void strength(const Csr &A, double theta, std::vector<int32_t> &sp, std::vector<int32_t> &sc) {
   const int n = A.n;
-  std::vector<double> mx(n, 0.0);
-  for (int i = 0; i < n; ++i)
-    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
-      if (A.col[k] != i) mx[i] = std::max(mx[i], std::fabs(A.val[k]));
-  auto strong = [&](int i, int k) {
-    const int j = A.col[k];
-    return j != i && mx[i] > 0.0 && std::fabs(A.val[k]) >= theta * mx[i];
-  };
+  std::vector<char> st(A.nnz(), 0);
   std::vector<int32_t> cnt(n + 1, 0);
-  for (int i = 0; i < n; ++i)
-    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
-      if (strong(i, k)) {
-        cnt[i]++;
-        cnt[A.col[k]]++;
-      }
-  sp.assign(n + 1, 0);
-  for (int i = 0; i < n; ++i) sp[i + 1] = sp[i] + cnt[i];
-  sc.assign(sp[n], 0);
-  std::vector<int32_t> fill(sp.begin(), sp.end() - 1);
-  for (int i = 0; i < n; ++i)
-    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
-      if (strong(i, k)) {
-        const int j = A.col[k];
-        sc[fill[i]++] = j;
-        sc[fill[j]++] = i;
-      }
-  // sort and deduplicate each list, then compact
-  int w = 0;
-  std::vector<int32_t> np(n + 1, 0);
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
-    auto b = sc.begin() + sp[i], e = sc.begin() + sp[i + 1];
-    std::sort(b, e);
-    auto u = std::unique(b, e);
-    for (auto it = b; it != u; ++it) sc[w++] = *it;
-    np[i + 1] = w;
+    double mx = 0.0;
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+      if (A.col[k] != i) mx = std::max(mx, std::fabs(A.val[k]));
+    int c = 0;
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      st[k] = A.col[k] != i && mx > 0.0 && std::fabs(A.val[k]) >= theta * mx;
+      c += st[k];
+    }
+    cnt[i + 1] = c;
   }
-  sc.resize(w);
-  sp.swap(np);
+  // strong matrix S1 and its transpose
+  Csr S1;
+  S1.n = S1.m = n;
+  S1.ptr = cnt;
+  for (int i = 0; i < n; ++i) S1.ptr[i + 1] += S1.ptr[i];
+  S1.col.resize(S1.ptr[n]);
+  S1.val.assign(S1.ptr[n], 1.0);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; ++i) {
+    int w = S1.ptr[i];
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+      if (st[k]) S1.col[w++] = A.col[k];
+  }
+  const Csr S1T = transpose(S1);
+  const Csr U = build_rows(n, n, [&](int i, std::vector<int32_t> &, auto &&emit) {
+    for (int k = S1.ptr[i]; k < S1.ptr[i + 1]; ++k) emit(S1.col[k], 1.0);
+    for (int k = S1T.ptr[i]; k < S1T.ptr[i + 1]; ++k) emit(S1T.col[k], 1.0);
+  });
+  sp = U.ptr;
+  sc = U.col;
 }
 
 // greedy aggregation; returns the number of aggregates
@@ -162,83 +261,142 @@ int aggregate(int n, const std::vector<int32_t> &sp, const std::vector<int32_t> 
 // P = T - w D^-1 A T, T[i, agg[i]] = 1
 Csr smoothed_prolongator(const Csr &A, const std::vector<double> &dinv,
                          const std::vector<int32_t> &agg, int na, double w) {
-  Csr P;
-  P.n = A.n;
-  P.m = na;
-  P.ptr.assign(A.n + 1, 0);
-  std::vector<int32_t> mark(na, -1), cols;
-  std::vector<double> acc(na, 0.0);
-  for (int i = 0; i < A.n; ++i) {
-    cols.clear();
-    auto add = [&](int c, double v) {
-      if (mark[c] != i) {
-        mark[c] = i;
-        acc[c] = 0.0;
-        cols.push_back(c);
+  Csr P = build_rows(A.n, na, [&](int i, std::vector<int32_t> &, auto &&emit) {
+    emit(agg[i], 1.0);
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) emit(agg[A.col[k]], -w * dinv[i] * A.val[k]);
+  });
+  // drop exact zeros (a row whose terms cancel), keeping the order
+  Csr Q;
+  Q.n = P.n;
+  Q.m = P.m;
+  Q.ptr.assign(P.n + 1, 0);
+  for (int i = 0; i < P.n; ++i) {
+    for (int k = P.ptr[i]; k < P.ptr[i + 1]; ++k)
+      if (P.val[k] != 0.0) {
+        Q.col.push_back(P.col[k]);
+        Q.val.push_back(P.val[k]);
       }
-      acc[c] += v;
-    };
-    add(agg[i], 1.0);
-    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) add(agg[A.col[k]], -w * dinv[i] * A.val[k]);
-    for (int c : cols)
-      if (acc[c] != 0.0) {
-        P.col.push_back(c);
-        P.val.push_back(acc[c]);
-      }
-    P.ptr[i + 1] = (int32_t)P.col.size();
+    Q.ptr[i + 1] = (int32_t)Q.col.size();
   }
-  return P;
+  return Q;
 }
 
-Csr transpose(const Csr &A) {
-  Csr T;
-  T.n = A.m;
-  T.m = A.n;
-  T.ptr.assign(A.m + 1, 0);
-  for (int32_t c : A.col) T.ptr[c + 1]++;
-  for (int i = 0; i < A.m; ++i) T.ptr[i + 1] += T.ptr[i];
-  T.col.resize(A.col.size());
-  T.val.resize(A.val.size());
-  std::vector<int32_t> fill(T.ptr.begin(), T.ptr.end() - 1);
-  for (int i = 0; i < A.n; ++i)
-    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
-      const int f = fill[A.col[k]]++;
-      T.col[f] = i;
-      T.val[f] = A.val[k];
-    }
-  return T;
-}
-
-// C = A B (Gustavson, dense accumulator over B's columns)
+// C = A B (Gustavson: row i of C accumulates the rows of B picked by row i
+// of A, columns in order of first appearance)
 Csr spgemm(const Csr &A, const Csr &B) {
-  Csr C;
-  C.n = A.n;
-  C.m = B.m;
-  C.ptr.assign(A.n + 1, 0);
-  std::vector<int32_t> mark(B.m, -1), cols;
-  std::vector<double> acc(B.m, 0.0);
-  for (int i = 0; i < A.n; ++i) {
-    cols.clear();
+  return build_rows(A.n, B.m, [&](int i, std::vector<int32_t> &, auto &&emit) {
     for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
       const int r = A.col[k];
       const double a = A.val[k];
-      for (int t = B.ptr[r]; t < B.ptr[r + 1]; ++t) {
-        const int c = B.col[t];
+      for (int t = B.ptr[r]; t < B.ptr[r + 1]; ++t) emit(B.col[t], a * B.val[t]);
+    }
+  });
+}
+
+// X - s(Y), s scaling Y's columns (cols = true) or rows by w.  Y's pattern
+// must hold X's (true here: Y = R A or A P with A's diagonal nonzero), so
+// the result has Y's pattern.
+Csr minus_scaled(const Csr &X, const Csr &Y, const std::vector<double> &w, bool cols) {
+  Csr C;
+  C.n = Y.n;
+  C.m = Y.m;
+  C.ptr = Y.ptr;
+  C.col = Y.col;
+  C.val.resize(Y.val.size());
+  int bad = 0;
+#pragma omp parallel
+  {
+    std::vector<int32_t> pos(Y.m, -1);
+#pragma omp for schedule(dynamic, 512)
+    for (int i = 0; i < Y.n; ++i) {
+      for (int k = Y.ptr[i]; k < Y.ptr[i + 1]; ++k) {
+        C.val[k] = -(cols ? w[Y.col[k]] : w[i]) * Y.val[k];
+        pos[Y.col[k]] = k;
+      }
+      for (int k = X.ptr[i]; k < X.ptr[i + 1]; ++k) {
+        const int p = pos[X.col[k]];
+        if (p >= Y.ptr[i] && p < Y.ptr[i + 1] && Y.col[p] == X.col[k])
+          C.val[p] += X.val[k];
+        else {
+#pragma omp atomic write
+          bad = 1;
+        }
+      }
+    }
+  }
+  if (bad) {  // a pattern not covered (not expected): build the union serially
+    C = Csr();
+    C.n = X.n;
+    C.m = X.m;
+    C.ptr.assign(X.n + 1, 0);
+    std::vector<int32_t> mark(X.m, -1), list;
+    std::vector<double> acc(X.m, 0.0);
+    for (int i = 0; i < X.n; ++i) {
+      list.clear();
+      auto add = [&](int c, double v) {
         if (mark[c] != i) {
           mark[c] = i;
           acc[c] = 0.0;
-          cols.push_back(c);
+          list.push_back(c);
         }
-        acc[c] += a * B.val[t];
+        acc[c] += v;
+      };
+      for (int k = X.ptr[i]; k < X.ptr[i + 1]; ++k) add(X.col[k], X.val[k]);
+      for (int k = Y.ptr[i]; k < Y.ptr[i + 1]; ++k)
+        add(Y.col[k], -(cols ? w[Y.col[k]] : w[i]) * Y.val[k]);
+      for (int c : list) {
+        C.col.push_back(c);
+        C.val.push_back(acc[c]);
       }
+      C.ptr[i + 1] = (int32_t)C.col.size();
     }
-    for (int c : cols) {
-      C.col.push_back(c);
-      C.val.push_back(acc[c]);
-    }
-    C.ptr[i + 1] = (int32_t)C.col.size();
   }
   return C;
+}
+
+// S = 2 W - W A W on A's pattern (every row of these matrices holds its
+// diagonal; a row without one gets it appended)
+Csr smoother_matrix(const Csr &A, const std::vector<double> &w) {
+  Csr S;
+  S.n = S.m = A.n;
+  S.ptr.assign(A.n + 1, 0);
+  std::vector<char> has(A.n, 0);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < A.n; ++i) {
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) has[i] |= A.col[k] == i;
+    S.ptr[i + 1] = A.ptr[i + 1] - A.ptr[i] + !has[i];
+  }
+  for (int i = 0; i < A.n; ++i) S.ptr[i + 1] += S.ptr[i];
+  S.col.resize(S.ptr[A.n]);
+  S.val.resize(S.ptr[A.n]);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < A.n; ++i) {
+    int o = S.ptr[i];
+    bool diag = false;
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      const int j = A.col[k];
+      double v = -w[i] * A.val[k] * w[j];
+      if (j == i && !diag) {
+        v += 2.0 * w[i];
+        diag = true;
+      }
+      S.col[o] = j;
+      S.val[o++] = v;
+    }
+    if (!diag) {
+      S.col[o] = i;
+      S.val[o] = 2.0 * w[i];
+    }
+  }
+  return S;
+}
+
+// lanes per row for a CSR matrix: about 4 entries per lane, 1..32
+int lanes_for(const Csr &A) {
+  const double avg = A.n > 0 ? (double)A.nnz() / A.n : 0.0;
+  int g = 1;
+  while (g < 32 && g * 4 < avg) g *= 2;
+  return g;
 }
 
 // inverse of a small CSR matrix by Gauss-Jordan with partial pivoting
@@ -277,6 +435,72 @@ bool dense_inverse(const Csr &A, std::vector<double> &inv) {
   return true;
 }
 
+struct Hierarchy {
+  std::vector<Csr> A, S, R, P;         // A_l; S_l (l >= 1); R~_l, P~_l (l < L-1)
+  std::vector<std::vector<double>> W;  // w_l D_l^-1
+  std::vector<double> omega, cinv;
+};
+
+// The levels of A0 (see the top of the file).  RBFFD_OK, or an error with
+// its text set.
+int build_hierarchy(Csr A0, Hierarchy &H) {
+  H.A.push_back(std::move(A0));
+  for (;;) {
+    const Csr &A = H.A.back();
+    std::vector<double> d = diagonal(A), dinv(A.n);
+    for (int i = 0; i < A.n; ++i) dinv[i] = d[i] != 0.0 ? 1.0 / d[i] : 0.0;
+    const double lam = rho_estimate(A, dinv);
+    const double om = std::min(AMG_OMEGA, 4.0 / (3.0 * lam));
+    std::vector<double> wd(A.n);
+    for (int i = 0; i < A.n; ++i) wd[i] = om * dinv[i];
+    H.omega.push_back(om);
+    H.S.push_back(H.A.size() > 1 ? smoother_matrix(A, wd) : Csr());  // level 0: ELL copy
+    H.W.push_back(std::move(wd));
+    if (A.n <= AMG_NCOARSE || (int)H.A.size() == AMG_MAXLEV) break;
+    std::vector<int32_t> sp, sc, agg;
+    strength(A, AMG_THETA, sp, sc);
+    const int na = aggregate(A.n, sp, sc, agg);
+    if (na > 0.8 * A.n || na == 0) break;  // coarsening stalled
+    Csr P = smoothed_prolongator(A, dinv, agg, na, 4.0 / (3.0 * lam));
+    Csr R = transpose(P);
+    Csr RA = spgemm(R, A);
+    Csr Ac = spgemm(RA, P);
+    Csr AP = spgemm(A, P);
+    const std::vector<double> &w = H.W.back();
+    H.R.push_back(minus_scaled(R, RA, w, true));   // R (I - A W)
+    H.P.push_back(minus_scaled(P, AP, w, false));  // (I - W A) P
+    H.A.push_back(std::move(Ac));
+  }
+  if (H.A.back().n > AMG_NCOARSE_MAX) {
+    set_error("amg: coarsening stalled at %d rows", H.A.back().n);
+    return RBFFD_ENOTIMPL;
+  }
+  if (!dense_inverse(H.A.back(), H.cinv)) {
+    set_error("amg: the coarsest matrix (%d rows) is singular", H.A.back().n);
+    return RBFFD_ESINGULAR;
+  }
+  return RBFFD_OK;
+}
+
+void fill_info(const Hierarchy &H, double ms, AmgInfo *info) {
+  if (!info) return;
+  memset(info, 0, sizeof(*info));
+  const int L = (int)H.A.size();
+  info->nlev = L;
+  info->setup_ms = ms;
+  for (int l = 0; l < L; ++l) {
+    info->n[l] = H.A[l].n;
+    info->nnz[l] = H.A[l].nnz();
+    info->nnz_r[l] = l + 1 < L ? H.R[l].nnz() : 0;
+    info->nnz_p[l] = l + 1 < L ? H.P[l].nnz() : 0;
+    info->omega[l] = H.omega[l];
+  }
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 struct Staging {
   std::vector<char> buf;
   size_t take(size_t bytes) {
@@ -294,11 +518,26 @@ struct Staging {
 
 }  // namespace
 
+int amg_analyze(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                AmgInfo *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  Csr A;
+  A.n = A.m = n;
+  A.ptr.assign(rowptr, rowptr + n + 1);
+  A.col.assign(col, col + rowptr[n]);
+  A.val.assign(val, val + rowptr[n]);
+  Hierarchy H;
+  RBFFD_TRY(build_hierarchy(std::move(A), H));
+  fill_info(H, ms_since(t0), info);
+  return RBFFD_OK;
+}
+
 int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
               void **mem, size_t *bytes, const AmgDev **dev, AmgDev *host_view, AmgInfo *info) {
   *mem = nullptr;
   *bytes = 0;
   *dev = nullptr;
+  const auto t0 = std::chrono::steady_clock::now();
   std::vector<int32_t> hcol((size_t)q * ldn);
   std::vector<double> hval((size_t)q * ldn);
   RBFFD_CK(cudaMemcpyAsync(hcol.data(), col, hcol.size() * 4, cudaMemcpyDeviceToHost,
@@ -306,99 +545,84 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
   RBFFD_CK(cudaMemcpyAsync(hval.data(), val, hval.size() * 8, cudaMemcpyDeviceToHost,
                            ctx->stream));
   RBFFD_CK(cudaStreamSynchronize(ctx->stream));
-
-  std::vector<Csr> As, Ps, Rs;
-  std::vector<std::vector<double>> W;  // smoother weight / diagonal per level
-  std::vector<double> omegas;
-  As.push_back(from_ell(n, q, ldn, hcol, hval));
-  for (;;) {
-    const Csr &A = As.back();
-    std::vector<double> d = diagonal(A), dinv(A.n);
-    for (int i = 0; i < A.n; ++i) dinv[i] = d[i] != 0.0 ? 1.0 / d[i] : 0.0;
-    const double lam = rho_estimate(A, dinv);
-    const double om = std::min(AMG_OMEGA, 4.0 / (3.0 * lam));
-    std::vector<double> wd(A.n);
-    for (int i = 0; i < A.n; ++i) wd[i] = om * dinv[i];
-    W.push_back(wd);
-    omegas.push_back(om);
-    if (A.n <= AMG_NCOARSE || (int)As.size() == AMG_MAXLEV) break;
-    std::vector<int32_t> sp, sc, agg;
-    strength(A, AMG_THETA, sp, sc);
-    const int na = aggregate(A.n, sp, sc, agg);
-    if (na > 0.8 * A.n || na == 0) break;  // coarsening stalled
-    Csr P = smoothed_prolongator(A, dinv, agg, na, 4.0 / (3.0 * lam));
-    Csr R = transpose(P);
-    Csr AP = spgemm(A, P);
-    Csr Ac = spgemm(R, AP);
-    Ps.push_back(std::move(P));
-    Rs.push_back(std::move(R));
-    As.push_back(std::move(Ac));
-  }
-  const int L = (int)As.size();
-  if (As.back().n > AMG_NCOARSE_MAX) {
-    set_error("amg: coarsening stalled at %d rows", As.back().n);
-    return RBFFD_ENOTIMPL;
-  }
-  std::vector<double> cinv;
-  if (!dense_inverse(As.back(), cinv)) {
-    set_error("amg: the coarsest matrix (%d rows) is singular", As.back().n);
-    return RBFFD_ESINGULAR;
+  Hierarchy H;
+  RBFFD_TRY(build_hierarchy(from_ell(n, q, ldn, hcol, hval), H));
+  const int L = (int)H.A.size();
+  // level 0's S in the solve's ELL layout: s_e = -w_i a_e w_c (+ 2 w_i on the diagonal)
+  std::vector<double> s0((size_t)q * ldn, 0.0);
+  {
+    const std::vector<double> &w = H.W[0];
+    for (int i = 0; i < n; ++i) {
+      bool diag = false;
+      for (int j = 0; j < q; ++j) {
+        const size_t e = (size_t)j * ldn + i;
+        const int c = hcol[e];
+        double v = -w[i] * hval[e] * w[c];
+        if (c == i && !diag) {
+          v += 2.0 * w[i];
+          diag = true;
+        }
+        s0[e] = v;
+      }
+    }
   }
 
   // ---- pack everything into one staging buffer, then one upload
   Staging S;
   const size_t o_dev = S.take(sizeof(AmgDev));
+  struct CsrOff {
+    size_t ptr = 0, col = 0, val = 0;
+    int grp = 1;
+  };
+  auto put_csr = [&](const Csr &M) {
+    CsrOff o;
+    o.ptr = S.put(M.ptr);
+    o.col = S.put(M.col);
+    o.val = S.put(M.val);
+    o.grp = lanes_for(M);
+    return o;
+  };
   struct Off {
-    size_t a_ptr = 0, a_col = 0, a_val = 0, wd = 0, p_ptr = 0, p_col = 0, p_val = 0, r_ptr = 0,
-           r_col = 0, r_val = 0, x = 0, b = 0, y = 0;
+    CsrOff S, R, P;
+    size_t b = 0, z = 0, y = 0;
   };
   std::vector<Off> off(L);
+  const size_t o_s0 = S.put(s0);
   for (int l = 0; l < L; ++l) {
-    if (l > 0) {
-      off[l].a_ptr = S.put(As[l].ptr);
-      off[l].a_col = S.put(As[l].col);
-      off[l].a_val = S.put(As[l].val);
-    }
-    off[l].wd = S.put(W[l]);
+    if (l > 0) off[l].S = put_csr(H.S[l]);
     if (l + 1 < L) {
-      off[l].p_ptr = S.put(Ps[l].ptr);
-      off[l].p_col = S.put(Ps[l].col);
-      off[l].p_val = S.put(Ps[l].val);
-      off[l].r_ptr = S.put(Rs[l].ptr);
-      off[l].r_col = S.put(Rs[l].col);
-      off[l].r_val = S.put(Rs[l].val);
+      off[l].R = put_csr(H.R[l]);
+      off[l].P = put_csr(H.P[l]);
     }
-    off[l].x = S.take(sizeof(double) * As[l].n);
-    if (l > 0) off[l].b = S.take(sizeof(double) * As[l].n);
-    off[l].y = S.take(sizeof(double) * As[l].n);
+    if (l > 0) off[l].b = S.take(sizeof(double) * H.A[l].n);
+    off[l].z = S.take(sizeof(double) * H.A[l].n);
+    off[l].y = S.take(sizeof(double) * H.A[l].n);
   }
-  const size_t o_cinv = S.put(cinv);
+  const size_t o_cinv = S.put(H.cinv);
   void *dmem = nullptr;
   RBFFD_TRY(dev_alloc(ctx, &dmem, S.buf.size()));
   char *base = (char *)dmem;
+  auto csr_at = [&](const CsrOff &o, bool have) {
+    AmgCsr c;
+    c.ptr = have ? (const int32_t *)(base + o.ptr) : nullptr;
+    c.col = have ? (const int32_t *)(base + o.col) : nullptr;
+    c.val = have ? (const double *)(base + o.val) : nullptr;
+    c.grp = o.grp;
+    return c;
+  };
   AmgDev h;
   memset(&h, 0, sizeof(h));
   h.nlev = L;
   h.cinv = (const double *)(base + o_cinv);
+  h.s0 = (const double *)(base + o_s0);
   for (int l = 0; l < L; ++l) {
     AmgLevel &v = h.lev[l];
-    v.n = As[l].n;
-    if (l > 0) {
-      v.a_ptr = (const int32_t *)(base + off[l].a_ptr);
-      v.a_col = (const int32_t *)(base + off[l].a_col);
-      v.a_val = (const double *)(base + off[l].a_val);
-      v.b = (double *)(base + off[l].b);
-    }
-    v.wdinv = (const double *)(base + off[l].wd);
-    if (l + 1 < L) {
-      v.p_ptr = (const int32_t *)(base + off[l].p_ptr);
-      v.p_col = (const int32_t *)(base + off[l].p_col);
-      v.p_val = (const double *)(base + off[l].p_val);
-      v.r_ptr = (const int32_t *)(base + off[l].r_ptr);
-      v.r_col = (const int32_t *)(base + off[l].r_col);
-      v.r_val = (const double *)(base + off[l].r_val);
-    }
-    v.x = (double *)(base + off[l].x);
+    v.n = H.A[l].n;
+    v.S = csr_at(off[l].S, l > 0);
+    v.R = csr_at(off[l].R, l + 1 < L);
+    v.P = csr_at(off[l].P, l + 1 < L);
+    v.b = l > 0 ? (double *)(base + off[l].b) : nullptr;
+    v.z = (double *)(base + off[l].z);
     v.y = (double *)(base + off[l].y);
   }
   memcpy(S.buf.data() + o_dev, &h, sizeof(h));
@@ -413,16 +637,7 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
   *bytes = S.buf.size();
   *dev = (const AmgDev *)(base + o_dev);
   if (host_view) *host_view = h;
-  if (info) {
-    memset(info, 0, sizeof(*info));
-    info->nlev = L;
-    for (int l = 0; l < L; ++l) {
-      info->n[l] = As[l].n;
-      info->nnz[l] = As[l].nnz();
-      info->nnz_p[l] = l + 1 < L ? Ps[l].nnz() : 0;
-      info->omega[l] = omegas[l];
-    }
-  }
+  fill_info(H, ms_since(t0), info);
   return RBFFD_OK;
 }
 

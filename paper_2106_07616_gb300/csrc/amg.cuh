@@ -11,25 +11,35 @@ namespace rbffd {
 
 constexpr int AMG_MAXLEV = 10;
 
-// One level of the hierarchy (device pointers).  Level 0 is the p' matrix
-// itself, kept in the problem's ELL arrays; its CSR fields are null.
+// A CSR matrix on the device, read with `grp` lanes per row.
+struct AmgCsr {
+  const int32_t *ptr, *col;
+  const double *val;
+  int grp;  // 1, 2, 4, 8, 16 or 32
+};
+
+// One level of the hierarchy, with the V-cycle's smoothing folded into the
+// transfer operators.  With W = w D^-1 (damped Jacobi) and a zero start, one
+// V(1,1) cycle from level l is
+//   z_l = S_l b_l,          S_l = 2 W - W A_l W          (both smoothings' b terms)
+//   b_{l+1} = R~_l b_l,     R~_l = R_l (I - A_l W)       (restricted residual)
+//   y_l = z_l + P~_l y_{l+1},  P~_l = (I - W A_l) P_l    (correction, post-smoothed)
+// which needs one grid exchange per level on the way down and one on the
+// way up.  Level 0's S lives in AmgDev::s0 in the solve's ELL layout.
 struct AmgLevel {
-  int n;  // rows
-  const int32_t *a_ptr, *a_col;  // A_l, CSR (levels >= 1)
-  const double *a_val;
-  const double *wdinv;           // Jacobi smoother weight / diag(A_l)
-  const int32_t *p_ptr, *p_col;  // P_l: n_l x n_{l+1} prolongation (not on the coarsest)
-  const double *p_val;
-  const int32_t *r_ptr, *r_col;  // R_l = P_l^T: n_{l+1} x n_l restriction
-  const double *r_val;
-  double *x;  // level iterate
-  double *b;  // level right-hand side (levels >= 1)
-  double *y;  // residual on the way down, smoothed result on the way up
+  int n;       // rows
+  AmgCsr S;    // levels >= 1
+  AmgCsr R;    // n_{l+1} x n_l (not on the coarsest)
+  AmgCsr P;    // n_l x n_{l+1} (not on the coarsest)
+  double *b;   // right-hand side (levels >= 1)
+  double *z;   // S_l b_l
+  double *y;   // the level's result
 };
 
 struct AmgDev {
   int nlev;            // levels including the coarsest
   const double *cinv;  // inverse of the coarsest matrix, row-major nc x nc
+  const double *s0;    // level 0's S, ELL [q][ldn] on the solve's column array
   AmgLevel lev[AMG_MAXLEV];
 };
 
@@ -37,8 +47,10 @@ struct AmgInfo {
   int nlev;
   int n[AMG_MAXLEV];
   long long nnz[AMG_MAXLEV];    // A_l
-  long long nnz_p[AMG_MAXLEV];  // P_l (= R_l), 0 on the coarsest
+  long long nnz_r[AMG_MAXLEV];  // R~_l
+  long long nnz_p[AMG_MAXLEV];  // P~_l
   double omega[AMG_MAXLEV];
+  double setup_ms;              // host time of the hierarchy build
 };
 
 // Build the hierarchy of the packed p' matrix (ELL, column-major [q][ldn],
@@ -48,5 +60,10 @@ struct AmgInfo {
 // RBFFD_ENOMEM, RBFFD_ECUDA.
 int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
               void **mem, size_t *bytes, const AmgDev **dev, AmgDev *host_view, AmgInfo *info);
+
+// The host part alone, on a CSR matrix (analysis and tests): level sizes
+// and nonzeros in *info.
+int amg_analyze(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                AmgInfo *info);
 
 }  // namespace rbffd

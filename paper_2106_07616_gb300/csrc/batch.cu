@@ -239,7 +239,6 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
     a1[i].nblocks = 2 * std::max(P[i]->kblocks1, P[i]->kblocks2);
     if (P[i]->amg) {
       a1[i].amg = P[i]->amg;
-      a1[i].dinv = P[i]->amg_host.lev[0].wdinv;
       pa.push_back(a1[i]);
       ra.push_back(P[i]->n);
     } else {

@@ -58,9 +58,8 @@ struct KScalars {
 // The solve of one system by the nb CTAs lb = 0..nb-1 that share it (the
 // whole grid for a single system; a subrange of a batched launch).
 // AMGP: the preconditioner is a V-cycle of the hierarchy A.amg instead of
-// the Jacobi scaling (one right-hand side); A.dinv then holds level 0's
-// smoother weights, and the loops that form p and s write its pre-smoothed
-// start w D^-1 p (or s) instead of p^ (s^).
+// the Jacobi scaling (one right-hand side): p^ and s^ come from the cycle
+// after p and s are published, not from the row loops.
 template <int NR, int NT, bool AMGP = false>
 __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb, const int nb) {
   static_assert(!AMGP || NR == 1, "the multigrid preconditioner serves one right-hand side");
@@ -77,10 +76,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
   auto P = [&](int slot, int k) { return part + (size_t)(slot * NR + k) * nb; };
   const bool leader = threadIdx.x == 0;
   int *err = &A.bar->err;
-  double *amg_x0 = nullptr;
   amgdev::Ctx actx{&A, lb, nb, tid, stride, wglobal, nwarps, stot};
-  if constexpr (AMGP) amg_x0 = A.amg->lev[0].x;
-  (void)amg_x0;
   (void)actx;
 
   if (leader) {
@@ -125,10 +121,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
                         A.w[k].r[i] = ri;
                         A.w[k].rh[i] = ri;
                         A.w[k].p[i] = ri;
-                        if constexpr (AMGP)
-                          amg_x0[i] = ri * di;
-                        else
-                          A.w[k].ph[i] = ri * di;
+                        if constexpr (!AMGP) A.w[k].ph[i] = ri * di;
                         acc[2 * k] += bi * bi;
                         acc[2 * k + 1] += ri * ri;
                       }
@@ -242,10 +235,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
           if (!run[k]) continue;
           const double si = A.w[k].r[i] - alp[k] * A.w[k].v[i];
           A.w[k].s[i] = si;
-          if constexpr (AMGP)
-            amg_x0[i] = si * di;
-          else
-            A.w[k].sh[i] = si * di;
+          if constexpr (!AMGP) A.w[k].sh[i] = si * di;
         }
       }
       ok = kdev::exchange<0, double>(A.flags, err, epoch++, nullptr, nullptr, stot, lb, nb);
@@ -353,10 +343,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
             acc[k] += ri * ri;
             const double pi = ri + bet[k] * (A.w[k].p[i] - omg[k] * A.w[k].v[i]);
             A.w[k].p[i] = pi;
-            if constexpr (AMGP)
-              amg_x0[i] = pi * di;
-            else
-              A.w[k].ph[i] = pi * di;
+            if constexpr (!AMGP) A.w[k].ph[i] = pi * di;
           }
         }
       }

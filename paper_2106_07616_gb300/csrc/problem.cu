@@ -298,10 +298,7 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   // pressure correction
   a.val = P->Pp;
   a.dinv = P->p_dinv;
-  if (P->amg) {  // V-cycle preconditioner; level 0's smoother weights in dinv
-    a.amg = P->amg;
-    a.dinv = P->amg_host.lev[0].wdinv;
-  }
+  if (P->amg) a.amg = P->amg;  // V-cycle preconditioner
   a.b[0] = P->bp;
   a.b[1] = nullptr;
   a.x[0] = P->pc;
@@ -524,15 +521,35 @@ extern "C" size_t rbffd_problem_bytes(const rbffd_problem *P) {
   return P ? P->bytes + P->amg_bytes : 0;
 }
 
-extern "C" int rbffd_problem_amg_info(const rbffd_problem *P, int32_t *levels, int32_t *rows,
-                                      int64_t *nnz) {
-  if (!P) return RBFFD_EINVAL;
-  if (levels) *levels = P->amg ? P->amg_info.nlev : 0;
+static void report_levels(const AmgInfo &I, bool have_any, int32_t *levels, int32_t *rows,
+                          int64_t *nnz, double *setup_ms) {
+  if (levels) *levels = have_any ? I.nlev : 0;
   for (int l = 0; l < RBFFD_AMG_MAX_LEVELS; ++l) {
-    const bool have = P->amg && l < P->amg_info.nlev;
-    if (rows) rows[l] = have ? P->amg_info.n[l] : 0;
-    if (nnz) nnz[l] = have ? P->amg_info.nnz[l] : 0;
+    const bool have = have_any && l < I.nlev;
+    if (rows) rows[l] = have ? I.n[l] : 0;
+    if (nnz) nnz[l] = have ? I.nnz[l] : 0;
   }
+  if (setup_ms) *setup_ms = have_any ? I.setup_ms : 0.0;
+}
+
+extern "C" int rbffd_problem_amg_info(const rbffd_problem *P, int32_t *levels, int32_t *rows,
+                                      int64_t *nnz, double *setup_ms) {
+  if (!P) return RBFFD_EINVAL;
+  report_levels(P->amg_info, P->amg != nullptr, levels, rows, nnz, setup_ms);
+  return RBFFD_OK;
+}
+
+extern "C" int rbffd_amg_analyze(int32_t n, const int32_t *rowptr, const int32_t *col,
+                                 const double *val, int32_t *levels, int32_t *rows, int64_t *nnz,
+                                 double *setup_ms) {
+  if (n < 1 || !rowptr || !col || !val || rowptr[0] != 0) return RBFFD_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return RBFFD_EINVAL;
+  for (int k = 0; k < rowptr[n]; ++k)
+    if (col[k] < 0 || col[k] >= n) return RBFFD_EINVAL;
+  AmgInfo I;
+  RBFFD_TRY(amg_analyze(n, rowptr, col, val, &I));
+  report_levels(I, true, levels, rows, nnz, setup_ms);
   return RBFFD_OK;
 }
 
@@ -631,12 +648,16 @@ namespace rbffd {
 double pcorr_bytes(const rbffd_problem *P, int iters) {
   const double n = P->n, q = P->q, it = iters;
   if (!P->amg) return n * it * (2 * q * 12 + 14 * 8);
+  // per V-cycle: S_0 b_0 (ELL, q (8 + 4) + 2 vectors), R~_l and P~_l and
+  // S_l (l >= 1) entries at 12 B, their vectors, the dense coarsest inverse
   const AmgInfo &I = P->amg_info;
-  double coarse = 12.0 * I.nnz_p[0];
-  for (int l = 1; l < I.nlev; ++l)
-    coarse += l + 1 < I.nlev ? 24.0 * I.nnz[l] + 12.0 * I.nnz_p[l] + 80.0 * I.n[l]
-                             : 8.0 * I.n[l] * I.n[l];
-  return n * it * (6 * q * 12 + 14 * 8 + 2 * 9 * 8) + 2.0 * it * coarse;
+  double cyc = n * (q * 12 + 16) + n * 24;  // S_0, then P~_0's z read and out write
+  for (int l = 0; l < I.nlev; ++l) {
+    if (l + 1 < I.nlev) cyc += 12.0 * (I.nnz_r[l] + I.nnz_p[l]);
+    if (l >= 1 && l + 1 < I.nlev) cyc += 12.0 * I.nnz[l] + 40.0 * I.n[l];
+    if (l + 1 == I.nlev) cyc += 8.0 * I.n[l] * I.n[l];
+  }
+  return n * it * (2 * q * 12 + 14 * 8) + 2.0 * it * cyc;
 }
 
 // The steady test: R <= tol, or (criterion 1) the paper's steady error

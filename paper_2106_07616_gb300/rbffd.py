@@ -112,7 +112,10 @@ def load(path: str = LIB_PATH):
         "rbffd_problem_reload": (C.c_int, [vp, C.POINTER(ProblemDesc)]),
         "rbffd_problem_destroy": (None, [vp]),
         "rbffd_problem_bytes": (sz, [vp]),
-        "rbffd_problem_amg_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]),
+        "rbffd_problem_amg_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64),
+                                             C.POINTER(dbl)]),
+        "rbffd_amg_analyze": (C.c_int, [i32, vp, vp, vp, C.POINTER(i32), C.POINTER(i32),
+                                        C.POINTER(i64), C.POINTER(dbl)]),
         "simple_iterate": (C.c_int, [vp, C.POINTER(StepParams), C.POINTER(dbl),
                                      C.POINTER(IterStats)]),
         "rbffd_time_step": (C.c_int, [vp, C.POINTER(SolveParams), dbl, C.POINTER(i32),
@@ -289,14 +292,17 @@ class Problem:
     def nbytes(self) -> int:
         return int(load().rbffd_problem_bytes(self.h))
 
-    def amg_info(self):
-        """Rows and nonzeros per level of the p' multigrid hierarchy ([] with Jacobi)."""
+    def amg_info(self, with_time=False):
+        """Rows and nonzeros per level of the p' multigrid hierarchy ([] with
+        Jacobi); with_time: also the host build time in ms."""
         lv = C.c_int32(0)
         rows = (C.c_int32 * AMG_MAX_LEVELS)()
         nnz = (C.c_int64 * AMG_MAX_LEVELS)()
-        _check(load().rbffd_problem_amg_info(self.h, C.byref(lv), rows, nnz),
+        ms = C.c_double(0)
+        _check(load().rbffd_problem_amg_info(self.h, C.byref(lv), rows, nnz, C.byref(ms)),
                "rbffd_problem_amg_info")
-        return [(int(rows[i]), int(nnz[i])) for i in range(lv.value)]
+        levels = [(int(rows[i]), int(nnz[i])) for i in range(lv.value)]
+        return (levels, ms.value) if with_time else levels
 
     def get(self, name, out=None):
         out = np.zeros(self.n) if out is None else out
@@ -408,6 +414,20 @@ class Batch:
                "rbffd_batch_iterate")
         its = np.array([list(s.iters) for s in st])
         return d, its, status
+
+
+def amg_analyze(rowptr, col, val):
+    """Host-only multigrid hierarchy of a CSR matrix: ([(rows, nnz)], ms)."""
+    rowptr = np.ascontiguousarray(rowptr, np.int32)
+    col = np.ascontiguousarray(col, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    lv = C.c_int32(0)
+    rows = (C.c_int32 * AMG_MAX_LEVELS)()
+    nnz = (C.c_int64 * AMG_MAX_LEVELS)()
+    ms = C.c_double(0)
+    _check(load().rbffd_amg_analyze(rowptr.size - 1, ptr(rowptr), ptr(col), ptr(val),
+                                    C.byref(lv), rows, nnz, C.byref(ms)), "rbffd_amg_analyze")
+    return [(int(rows[i]), int(nnz[i])) for i in range(lv.value)], ms.value
 
 
 class Server:

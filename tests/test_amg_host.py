@@ -1,0 +1,62 @@
+"""Host part of the multigrid preconditioner (rbffd_amg_analyze): the
+hierarchy build runs on the CPU, no GPU needed.  Its operators are checked
+on the GPU by the preconditioned solves (tests/test_gpu_amg.py); here the
+structure: coarsening, determinism, argument checks."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_07616_gb300 import _build, clouds, rbffd
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+
+
+def poisson5(m):
+    """5-point Laplacian on an m x m grid with identity rows on the edge."""
+    n = m * m
+    rows, cols, vals = [], [], []
+    for j in range(m):
+        for i in range(m):
+            r = j * m + i
+            if i in (0, m - 1) or j in (0, m - 1):
+                rows.append(r); cols.append(r); vals.append(1.0)
+                continue
+            for di, dj, v in ((0, 0, -4.0), (1, 0, 1.0), (-1, 0, 1.0), (0, 1, 1.0), (0, -1, 1.0)):
+                rows.append(r); cols.append((j + dj) * m + i + di); vals.append(v)
+    order = np.lexsort((np.arange(len(rows)), rows))
+    rows, cols, vals = np.array(rows)[order], np.array(cols)[order], np.array(vals)[order]
+    rowptr = np.searchsorted(rows, np.arange(n + 1))
+    return rowptr, cols, vals
+
+
+def test_poisson_hierarchy_coarsens_to_a_dense_level():
+    levels, ms = rbffd.amg_analyze(*poisson5(64))
+    sizes = [n for n, _ in levels]
+    assert sizes[0] == 64 * 64
+    assert all(b < a / 3 for a, b in zip(sizes, sizes[1:]))  # aggregates of >3 points
+    assert sizes[-1] <= 200 and len(sizes) >= 3
+    assert ms >= 0.0
+
+
+def test_hierarchy_is_deterministic_on_a_p_prime_matrix():
+    fp = clouds.cavity(60, dt=0.05)
+    O = oracle.Problem(fp)
+    ops = O.operators()
+    pv, idx = ops["pval"], ops["idx"]
+    keep = (pv != 0) | (idx == np.arange(fp.n)[:, None])
+    rowptr = np.concatenate([[0], np.cumsum(keep.sum(1))])
+    a = rbffd.amg_analyze(rowptr, idx[keep], pv[keep])[0]
+    b = rbffd.amg_analyze(rowptr, idx[keep], pv[keep])[0]
+    assert a == b and len(a) >= 2 and a[-1][0] <= 600
+
+
+def test_bad_csr_rejected():
+    rowptr, cols, vals = poisson5(8)
+    bad = cols.copy()
+    bad[3] = 10_000
+    with pytest.raises(rbffd.RbffdError) as e:
+        rbffd.amg_analyze(rowptr, bad, vals)
+    assert e.value.code == rbffd.EINVAL
