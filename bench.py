@@ -1,16 +1,21 @@
 """Benchmark of the semi-implicit PHS-RBF-FD hot path on one GB300.
 
 One STEP is one pass of the whole hot path over one synthetic problem:
-S1 clouds + S2 weights + S3 packed operators (rbffd_problem_reload), then
-the first BDF2 time step from rest (S4-S10 outer iterations, the paper's
-outer tolerance 1e-4, capped at --outer iterations).  The metric is SIMPLE
-outer iterations per second of whole-step time.
+S1 clouds + S2 weights + S3 packed operators and the p' preconditioner
+(rbffd_problem_reload), then the first BDF2 time step from rest (S4-S10
+outer iterations until Delta < 1e-4, the paper's first outer tolerance, at
+most --outer of them).  The metric is SIMPLE outer iterations per second of
+whole-step time.
 
 Workload (default): the lid-driven cavity, Re = 1000, 200 x 200 clustered
 and jittered cloud (N = 40 000), polynomial degree 4, q = 30, dt from a
-Courant number of about 10.  --precision fp64 (default): FP64 Krylov
-throughout; --precision mixed: FP32 BiCGSTAB inside FP64 defect correction
-to the same FP64 tolerance (converges only while cond * eps_fp32 < 1).
+Courant number of about 10.  --precond amg (default): the p' BiCGSTAB is
+preconditioned by a smoothed-aggregation V-cycle (jacobi: diagonal).
+--precision fp64 (default): FP64 Krylov throughout; mixed / ff: FP32 or
+float-float BiCGSTAB inside FP64 defect correction to the same tolerance.
+Other workloads: kovasznay50, cylinder150k (outlet, symmetry and no-slip
+rows, 147 827 graded points), batch (many instances per launch) and serve
+(a Poisson stream of steady-solve requests through the request server).
 
 Printed: one JSON line (rank 0).  `value` is device-resident throughput
 (inputs already in HBM); `e2e` is the same metric through the C ABI from
@@ -108,7 +113,8 @@ def run_batch(args):
     fps = batch_instances(args.count)
     stream = torch.cuda.current_stream()
     ctx = rbffd.Context(0, stream=stream.cuda_stream)
-    probs = [rbffd.Problem(ctx, fp) for fp in fps]
+    pc = rbffd.PRECOND_AMG if args.precond == "amg" else rbffd.PRECOND_JACOBI
+    probs = [rbffd.Problem(ctx, fp, precond=pc) for fp in fps]
     B = rbffd.Batch(ctx, probs)
     rows = sum(fp.n for fp in fps)
     nnz = sum(fp.n * fp.q for fp in fps)
@@ -121,7 +127,7 @@ def run_batch(args):
 
     for _ in range(args.warmup):
         for P, fp in zip(probs, fps):
-            P.reload(fp)
+            P.reload(fp, precond=pc)
         iterate_all()
     torch.cuda.synchronize()
     ctx.profile(True)
@@ -132,7 +138,7 @@ def run_batch(args):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for P, fp in zip(probs, fps):
-                P.reload(fp)
+                P.reload(fp, precond=pc)
             its, ok = iterate_all()
             e1.record(stream)
             e1.synchronize()
@@ -146,6 +152,7 @@ def run_batch(args):
            "unit": "instance_outer_iter/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "dtype": "f64",
            "config": {"workload": f"batch{args.count}", "instances": len(fps), "rows": rows,
+                      "precond": args.precond,
                       "nnz_per_operator": nnz,
                       "description": "Kovasznay/cavity instances, N log-uniform [1k,64k], "
                                      "degree {2..5}, q=2m; step = S1-S3 for all + one outer "
@@ -197,7 +204,9 @@ def run_serve(args):
         if wait > 0:
             time.sleep(wait)
         tickets.append(S.submit(fp, resid_tol=args.resid_tol, max_steps=args.max_steps,
-                                criterion=args.criterion))
+                                criterion=args.criterion,
+                                precond=(rbffd.PRECOND_AMG if args.precond == "amg"
+                                         else rbffd.PRECOND_JACOBI)))
     S.drain()
     wall = time.perf_counter() - t0
     res = [S.poll(t) for t in tickets]
@@ -215,6 +224,8 @@ def run_serve(args):
                       for s in sorted(set(r["status"] for r in res)) if s != 0},
            "resid_tol": args.resid_tol, "wall_s": wall, "failures": fails[:12],
            "steps_ok": [r["steps"] for r in ok], "outer_ok": [r["outer"] for r in ok],
+           "R_ok": [float(r["resid"][2]) for r in ok], "max_steps": args.max_steps,
+           "precond": args.precond,
            "config": {"workload": f"serve{args.count}",
                       "description": "Poisson arrivals 20/s; Kovasznay Re 20-60 / cavity "
                                      "Re 10-100, N log-uniform [1k,4k], degree {3,4}, q=2m; "
@@ -509,14 +520,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="cavity200")
-    ap.add_argument("--outer", type=int, default=3)
+    ap.add_argument("--outer", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--count", type=int, default=256, help="instances / requests (batch, serve)")
     ap.add_argument("--resid-tol", type=float, default=1e-5)
     ap.add_argument("--criterion", type=int, default=1,
                     help="serve: 0 = steady residual R, 1 = the paper's steady error change/dt")
-    ap.add_argument("--max-steps", type=int, default=3000)
-    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "amg"],
+    ap.add_argument("--max-steps", type=int, default=1000)
+    ap.add_argument("--precond", default="amg", choices=["jacobi", "amg"],
                     help="preconditioner of the pressure-correction BiCGSTAB")
     ap.add_argument("--precision", default="fp64", choices=["mixed", "ff", "fp64"],
                     help="Krylov arithmetic: FP32 or float-float inside FP64 defect "

@@ -41,7 +41,7 @@ enum {
   RBFFD_ENOTIMPL = -8
 };
 
-/* Boundary tags (paper Sec. 3.3, "Boundary Conditions").  Every non-interior
+/* Boundary tags (paper Sec. 3.1, "Boundary Conditions").  Every non-interior
  * point has a one-sided cloud (itself and interior points only). */
 enum {
   RBFFD_TAG_INTERIOR = 0,

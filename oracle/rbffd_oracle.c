@@ -647,7 +647,7 @@ void orc_set_krylov(orc_problem *P, double tol, int maxit) {
 
 /* ------------------------------------------------------------------------ */
 /* Kind of the momentum row of point i for velocity component c (0 = u,     */
-/* 1 = v), Sec. 3.3: the equation itself inside; an identity row with the   */
+/* 1 = v), Sec. 3.1: the equation itself inside; an identity row with the   */
 /* boundary value where the component is prescribed (walls, inlets, the     */
 /* normal component on a symmetry line); a zero normal derivative           */
 /* n.grad = 0 at outlets and for the tangential component on a symmetry     */

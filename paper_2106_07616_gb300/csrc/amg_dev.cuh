@@ -20,6 +20,11 @@ namespace amgdev {
 
 // f(i, sum_k M(i,k) x(k)) for the rows of a CSR matrix, M.grp lanes per
 // row (a power of two); all 32 lanes of a warp run the same trip count.
+// Each lane loads CC column indices and values of its strided share first,
+// then the CC gathers, so a long row costs two dependent L2 round trips per
+// CC entries a lane, not per entry.
+constexpr int CC = 8;
+
 template <typename F>
 __device__ __forceinline__ void csr_rows(const AmgCsr &M, int nrows, const double *x, int wglobal,
                                          int nwarps, F &&f) {
@@ -30,7 +35,19 @@ __device__ __forceinline__ void csr_rows(const AmgCsr &M, int nrows, const doubl
     double t = 0.0;
     if (i < nrows) {
       const int s = __ldg(M.ptr + i), e = __ldg(M.ptr + i + 1);
-      for (int k = s + lg; k < e; k += G) t += __ldg(M.val + k) * __ldcg(x + __ldg(M.col + k));
+      for (int k0 = s + lg; k0 < e; k0 += CC * G) {
+        int c[CC];
+        double a[CC];
+#pragma unroll
+        for (int u = 0; u < CC; ++u) {
+          const int k = k0 + u * G;
+          c[u] = k < e ? __ldg(M.col + k) : -1;
+          a[u] = k < e ? __ldg(M.val + k) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < CC; ++u)
+          if (c[u] >= 0) t += a[u] * __ldcg(x + c[u]);
+      }
     }
     for (int o = G >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (i < nrows && lg == 0) f(i, t);

@@ -17,7 +17,7 @@ namespace rbffd {
 constexpr int RT = 256;
 
 // Kind of the momentum row of a point for velocity component c (0 = u,
-// 1 = v), paper Sec. 3.3: the equation inside (ROW_EQ); an identity row with
+// 1 = v), paper Sec. 3.1: the equation inside (ROW_EQ); an identity row with
 // the boundary value where the component is prescribed (walls, inlets, the
 // normal component on a symmetry line); a zero normal derivative n . grad
 // at outlets and for the tangential component on a symmetry line.

@@ -1,4 +1,4 @@
-"""Outlet and symmetry-line boundary rows on the GPU (paper Sec. 3.3)
+"""Outlet and symmetry-line boundary rows on the GPU (paper Sec. 3.1)
 against the oracle, on the Poiseuille channel."""
 import dataclasses
 

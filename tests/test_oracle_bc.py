@@ -1,4 +1,4 @@
-"""Oracle pins for the outlet and symmetry boundary rows (paper Sec. 3.3).
+"""Oracle pins for the outlet and symmetry boundary rows (paper Sec. 3.1).
 
 Plane Poiseuille flow is reproduced exactly by weights of degree >= 2
 (quadratic velocity, linear pressure), so it is a discrete fixed point of
