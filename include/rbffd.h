@@ -226,6 +226,14 @@ typedef struct {
   const double *nx, *ny; /* outward unit normal at boundary points (0 inside) */
   const double *ubc, *vbc; /* prescribed velocity at boundary points */
   int32_t precond;         /* RBFFD_PRECOND_* of the p' solve */
+  double period[2];        /* periods of x and y, 0 for a bounded axis (Sec. 3.1,
+                              periodic boundaries): clouds near one side take points
+                              from the other, at their nearest periodic image.  Put
+                              no boundary points on a periodic side; a period must
+                              exceed twice any cloud's radius */
+  double force[2];         /* body force per unit volume added to the momentum
+                              equations (the paper's mean pressure gradient that
+                              drives a periodic flow); 0 for none */
 } rbffd_problem_desc;
 
 /* Allocate a problem and build everything that depends only on the points
@@ -342,6 +350,17 @@ int solve_unsteady(rbffd_problem *prob, const rbffd_solve_params *params, int32_
  *   R_c = |Dx u + Dy v| / |grad u|
  * R3 (host, 3 doubles) = R_m, R_c, max of the two. */
 int rbffd_steady_residual(rbffd_problem *prob, double *R3);
+
+/* Courant number of the explicit-Euler stability bound quoted in the paper
+ * (Sec. 3.2, after the solution steps): lambda * dt / 2, with lambda the
+ * spectral radius of the discrete convection-diffusion operator
+ * rho (u Dx + v Dy) - mu Lap (interior rows) at the current velocity.
+ * lambda: power iteration from a fixed start vector, `iters` steps (>= 2;
+ * 200 is typical), geometric mean of the growth over the second half.
+ * Outputs nullable.  The time step for a target Courant number Co is
+ * 2 Co / lambda. */
+int rbffd_courant(rbffd_problem *prob, double dt, int32_t iters, double *lambda_out,
+                  double *courant_out);
 
 /* Copy a field (RBFFD_FIELD_*) out of / into the problem; n doubles, host
  * or device.  Setting U, V or P leaves the time history untouched. */

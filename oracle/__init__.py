@@ -62,7 +62,11 @@ def lib():
         L.orc_problem_create.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _bp, _dp, _dp, _dp,
                                          _dp, C.c_int, C.c_double, C.c_double,
                                          C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]
+        L.orc_problem_create2.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _bp, _dp, _dp,
+                                          _dp, _dp, C.c_int, C.c_double, C.c_double, _dp, _dp,
+                                          C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]
         L.orc_problem_destroy.argtypes = [C.c_void_p]
+        L.orc_courant.argtypes = [C.c_void_p, C.c_double, C.c_int, _dp]
         L.orc_get_field.argtypes = [C.c_void_p, C.c_int, _dp]
         L.orc_set_field.argtypes = [C.c_void_p, C.c_int, _dp]
         L.orc_get_operators.argtypes = [C.c_void_p, _ip, _dp, _dp, _dp, _dp]
@@ -189,10 +193,13 @@ class Problem:
         self.fp = fp
         h = C.c_void_p()
         fs = C.c_int32(-1)
-        rc = lib().orc_problem_create(
+        per = np.array(getattr(fp, "period", (0.0, 0.0)), np.float64)
+        force = np.array(getattr(fp, "force", (0.0, 0.0)), np.float64)
+        rc = lib().orc_problem_create2(
             fp.n, fp.q, fp.degree, _f64(fp.x), _f64(fp.y),
             np.ascontiguousarray(fp.tag, np.int8), _f64(fp.nx), _f64(fp.ny), _f64(fp.ubc),
-            _f64(fp.vbc), int(fp.pin), float(fp.rho), float(fp.mu), C.byref(h), C.byref(fs))
+            _f64(fp.vbc), int(fp.pin), float(fp.rho), float(fp.mu), per, force, C.byref(h),
+            C.byref(fs))
         if rc:
             raise ValueError(f"orc_problem_create failed: {rc} (first singular {fs.value})")
         self.h = h
@@ -240,6 +247,14 @@ class Problem:
         if rc:
             raise RuntimeError(f"orc_time_step failed: {rc}")
         return it.value, ch.value, last.value
+
+    def courant(self, dt, iters=200):
+        """(lambda, lambda dt / 2) of the convection-diffusion operator."""
+        out = np.zeros(2)
+        rc = lib().orc_courant(self.h, dt, iters, out)
+        if rc:
+            raise RuntimeError(f"orc_courant failed: {rc}")
+        return out[0], out[1]
 
     def steady_residual(self):
         r = np.zeros(3)

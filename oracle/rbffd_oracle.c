@@ -93,16 +93,29 @@ static int key_less(double d2a, int ja, double d2b, int jb) {
   return d2a < d2b || (d2a == d2b && ja < jb);
 }
 
+/* a - b along an axis that is periodic with length L (L = 0: not          */
+/* periodic): the difference moved by one period when it exceeds half of   */
+/* one, i.e. the nearest image (Sec. 3.1: clouds wrap around a periodic    */
+/* boundary).                                                              */
+static double pdiff(double a, double b, double L) {
+  double d = a - b;
+  if (L > 0.0) {
+    if (d > 0.5 * L) d = d - L;
+    else if (d < -0.5 * L) d = d + L;
+  }
+  return d;
+}
+
 /* The cloud of point i into out[0..q-1]; bd, bj: work arrays of q-1.     */
 static void knn_one(int n, const double *x, const double *y, const int8_t *tag, int q, int i,
-                    double *bd, int *bj, int32_t *out) {
+                    const double *per, double *bd, int *bj, int32_t *out) {
   int boundary = tag && tag[i] != TAG_INTERIOR;
   int cnt = 0;
   for (int j = 0; j < n; ++j) {
     if (j == i) continue;
     if (boundary && tag[j] != TAG_INTERIOR) continue;
-    double dx = x[j] - x[i];
-    double dy = y[j] - y[i];
+    double dx = pdiff(x[j], x[i], per ? per[0] : 0.0);
+    double dy = pdiff(y[j], y[i], per ? per[1] : 0.0);
     double d2 = dx * dx + dy * dy;
     /* keep the q-1 best in a sorted list (insertion) */
     if (cnt < q - 1) {
@@ -126,7 +139,7 @@ static void knn_one(int n, const double *x, const double *y, const int8_t *tag, 
 /* Clouds of the points rows[0..nrows-1] (all points when rows == NULL,     */
 /* nrows = n), written row by row to idx (nrows x q).                       */
 static int knn_rows(int n, const double *x, const double *y, const int8_t *tag, int q,
-                    int nrows, const int32_t *rows, int32_t *idx) {
+                    int nrows, const int32_t *rows, const double *per, int32_t *idx) {
   if (n <= 0 || q <= 0 || q > n || nrows < 0) return ORC_EINVAL;
   int n_int = 0;
   for (int j = 0; j < n; ++j) n_int += (!tag || tag[j] == TAG_INTERIOR);
@@ -147,7 +160,7 @@ static int knn_rows(int n, const double *x, const double *y, const int8_t *tag, 
 #pragma omp for schedule(dynamic, 64)
   for (int k = 0; k < nrows; ++k) {
     if (!bd || !bj) continue;
-    knn_one(n, x, y, tag, q, rows ? rows[k] : k, bd, bj, idx + (int64_t)k * q);
+    knn_one(n, x, y, tag, q, rows ? rows[k] : k, per, bd, bj, idx + (int64_t)k * q);
   }
   free(bd); free(bj);
   }
@@ -155,13 +168,13 @@ static int knn_rows(int n, const double *x, const double *y, const int8_t *tag, 
 }
 
 int orc_knn(int n, const double *x, const double *y, const int8_t *tag, int q, int32_t *idx) {
-  return knn_rows(n, x, y, tag, q, n, NULL, idx);
+  return knn_rows(n, x, y, tag, q, n, NULL, NULL, idx);
 }
 
 /* Clouds of selected points only (spot checks of large problems). */
 int orc_knn_rows(int n, const double *x, const double *y, const int8_t *tag, int q, int nrows,
                  const int32_t *rows, int32_t *idx) {
-  return knn_rows(n, x, y, tag, q, nrows, rows, idx);
+  return knn_rows(n, x, y, tag, q, nrows, rows, NULL, idx);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -218,22 +231,23 @@ int orc_lu_solve(int n, int nr, double *M, int ld, double *sol /* n*nr, col-majo
 /* One cloud: centre i, members cl[0..q-1].  Work arrays M (N*(N+3)),       */
 /* sol (3N), xi, eta (q).  Returns 0, or -1 on an exactly zero pivot.        */
 static int weights_one(const double *x, const double *y, int q, const int32_t *cl, int i, int m,
-                       const int32_t *ax, const int32_t *ay, double *M, double *sol, double *xi,
-                       double *eta, double *wx, double *wy, double *wl) {
+                       const int32_t *ax, const int32_t *ay, const double *per, double *M,
+                       double *sol, double *xi, double *eta, double *wx, double *wy, double *wl) {
   int N = q + m, ld = N + 3;
   double xc = x[i], yc = y[i];
-  /* stencil radius */
+  double Lx = per ? per[0] : 0.0, Ly = per ? per[1] : 0.0;
+  /* stencil radius (members at their nearest periodic image) */
   double d2max = 0.0;
   for (int a = 0; a < q; ++a) {
-    double dx = x[cl[a]] - xc, dy = y[cl[a]] - yc;
+    double dx = pdiff(x[cl[a]], xc, Lx), dy = pdiff(y[cl[a]], yc, Ly);
     double d2 = dx * dx + dy * dy;
     if (d2 > d2max) d2max = d2;
   }
   double h = sqrt(d2max);
   if (h == 0.0) h = 1.0; /* a one-point cloud: nothing to scale */
   for (int a = 0; a < q; ++a) {
-    xi[a] = (x[cl[a]] - xc) / h;
-    eta[a] = (y[cl[a]] - yc) / h;
+    xi[a] = pdiff(x[cl[a]], xc, Lx) / h;
+    eta[a] = pdiff(y[cl[a]], yc, Ly) / h;
   }
   /* A = [Phi P; P^T 0] with the three right-hand sides appended */
   for (int a = 0; a < q; ++a) {
@@ -277,12 +291,12 @@ static int weights_one(const double *x, const double *y, int q, const int32_t *c
 }
 
 static int weights_rows(int n, const double *x, const double *y, int q, int nrows,
-                        const int32_t *rows, const int32_t *idx, int degree, double *wx,
-                        double *wy, double *wl, int32_t *first_singular);
+                        const int32_t *rows, const int32_t *idx, int degree, const double *per,
+                        double *wx, double *wy, double *wl, int32_t *first_singular);
 
 int orc_weights(int n, const double *x, const double *y, int q, const int32_t *idx,
                 int degree, double *wx, double *wy, double *wl, int32_t *first_singular) {
-  return weights_rows(n, x, y, q, n, NULL, idx, degree, wx, wy, wl, first_singular);
+  return weights_rows(n, x, y, q, n, NULL, idx, degree, NULL, wx, wy, wl, first_singular);
 }
 
 /* Weights of the clouds idx (nrows x q) centred at rows[k] (spot checks of */
@@ -290,12 +304,12 @@ int orc_weights(int n, const double *x, const double *y, int q, const int32_t *i
 int orc_weights_rows(int n, const double *x, const double *y, int q, int nrows,
                      const int32_t *rows, const int32_t *idx, int degree, double *wx, double *wy,
                      double *wl, int32_t *first_singular) {
-  return weights_rows(n, x, y, q, nrows, rows, idx, degree, wx, wy, wl, first_singular);
+  return weights_rows(n, x, y, q, nrows, rows, idx, degree, NULL, wx, wy, wl, first_singular);
 }
 
 static int weights_rows(int n, const double *x, const double *y, int q, int nrows,
-                        const int32_t *rows, const int32_t *idx, int degree, double *wx,
-                        double *wy, double *wl, int32_t *first_singular) {
+                        const int32_t *rows, const int32_t *idx, int degree, const double *per,
+                        double *wx, double *wy, double *wl, int32_t *first_singular) {
   int m = orc_num_monomials(degree);
   if (n <= 0 || q <= 0 || q > n || degree < 0 || q < m || nrows < 0) return ORC_EINVAL;
   int N = q + m;
@@ -318,7 +332,7 @@ static int weights_rows(int n, const double *x, const double *y, int q, int nrow
   for (int i = 0; i < nrows; ++i) {
     if (!ok) continue;
     int64_t o = (int64_t)i * q;
-    if (weights_one(x, y, q, idx + o, rows ? rows[i] : i, m, ax, ay, M, sol, xi, eta, wx ? wx + o : NULL,
+    if (weights_one(x, y, q, idx + o, rows ? rows[i] : i, m, ax, ay, per, M, sol, xi, eta, wx ? wx + o : NULL,
                     wy ? wy + o : NULL, wl ? wl + o : NULL) != 0) {
 #pragma omp critical(orc_singular)
       {
@@ -468,6 +482,8 @@ int orc_bicgstab_csr(int n, const int64_t *rowptr, const int32_t *col, const dou
 typedef struct {
   int n, q, degree, pin;
   double rho, mu;
+  double per[2];   /* periods of x and y (0: not periodic), Sec. 3.1 */
+  double force[2]; /* body force per unit volume, e.g. a mean pressure gradient */
   double *x, *y, *nx, *ny, *ubc, *vbc;
   int8_t *tag;
   int32_t *idx;
@@ -517,12 +533,32 @@ void orc_problem_destroy(orc_problem *P) {
 /* of one boundary point (pin) is then replaced by the identity with a zero */
 /* right-hand side, which fixes that constant.  pin = -1 is allowed when an */
 /* outlet point exists.  Symmetry points need an axis-aligned normal (the   */
-/* normal velocity component is then u or v).                               */
+/* normal velocity component is then u or v).  per[2] (nullable): periods  */
+/* of x and y, 0 for a bounded axis -- clouds and weights then use nearest */
+/* periodic images (Sec. 3.1, periodic boundaries).  force[2] (nullable):   */
+/* a body force added to the momentum equations, the paper's mean pressure */
+/* gradient of periodic flows.                                              */
+int orc_problem_create2(int n, int q, int degree, const double *x, const double *y,
+                        const int8_t *tag, const double *nx, const double *ny,
+                        const double *ubc, const double *vbc, int pin, double rho, double mu,
+                        const double *per, const double *force, orc_problem **out,
+                        int32_t *first_singular);
+
 int orc_problem_create(int n, int q, int degree, const double *x, const double *y,
                        const int8_t *tag, const double *nx, const double *ny, const double *ubc,
                        const double *vbc, int pin, double rho, double mu, orc_problem **out,
                        int32_t *first_singular) {
+  return orc_problem_create2(n, q, degree, x, y, tag, nx, ny, ubc, vbc, pin, rho, mu, NULL, NULL,
+                             out, first_singular);
+}
+
+int orc_problem_create2(int n, int q, int degree, const double *x, const double *y,
+                        const int8_t *tag, const double *nx, const double *ny,
+                        const double *ubc, const double *vbc, int pin, double rho, double mu,
+                        const double *per, const double *force, orc_problem **out,
+                        int32_t *first_singular) {
   *out = NULL;
+  if (per && (per[0] < 0.0 || per[1] < 0.0)) return ORC_EINVAL;
   int m = orc_num_monomials(degree);
   if (n <= 0 || q <= 0 || q > n || q < m || pin < -1 || pin >= n) return ORC_EINVAL;
   int n_out = 0;
@@ -536,6 +572,8 @@ int orc_problem_create(int n, int q, int degree, const double *x, const double *
   orc_problem *P = (orc_problem *)calloc(1, sizeof(orc_problem));
   if (!P) return ORC_ENOMEM;
   P->n = n; P->q = q; P->degree = degree; P->pin = pin; P->rho = rho; P->mu = mu;
+  P->per[0] = per ? per[0] : 0.0; P->per[1] = per ? per[1] : 0.0;
+  P->force[0] = force ? force[0] : 0.0; P->force[1] = force ? force[1] : 0.0;
   P->ktol = 1e-12; P->kmaxit = 10000;
   size_t nq = (size_t)n * q;
   P->x = dvec(n); P->y = dvec(n); P->nx = dvec(n); P->ny = dvec(n);
@@ -562,9 +600,10 @@ int orc_problem_create(int n, int q, int degree, const double *x, const double *
   memcpy(P->nx, nx, sizeof(double) * n); memcpy(P->ny, ny, sizeof(double) * n);
   memcpy(P->ubc, ubc, sizeof(double) * n); memcpy(P->vbc, vbc, sizeof(double) * n);
   memcpy(P->tag, tag, (size_t)n);
-  int rc = orc_knn(n, P->x, P->y, P->tag, q, P->idx);
+  int rc = knn_rows(n, P->x, P->y, P->tag, q, n, NULL, P->per, P->idx);
   if (rc) { orc_problem_destroy(P); return rc; }
-  rc = orc_weights(n, P->x, P->y, q, P->idx, degree, P->wx, P->wy, P->wl, first_singular);
+  rc = weights_rows(n, P->x, P->y, q, n, NULL, P->idx, degree, P->per, P->wx, P->wy, P->wl,
+                    first_singular);
   if (rc) { orc_problem_destroy(P); return rc; }
   for (int i = 0; i <= n; ++i) P->rowptr[i] = (int64_t)i * q;
   csr_t base = {n, P->rowptr, P->idx, NULL};
@@ -700,8 +739,8 @@ int orc_simple_iterate(orc_problem *P, double dt, double a1, double a2, double a
       }
       double b;
       if (kind == ROW_EQ)
-        b = c == 0 ? -rho * (a2 * P->un[i] + a3 * P->unm1[i]) / dt - P->w1[i]
-                   : -rho * (a2 * P->vn[i] + a3 * P->vnm1[i]) / dt - P->w2[i];
+        b = c == 0 ? -rho * (a2 * P->un[i] + a3 * P->unm1[i]) / dt - P->w1[i] + P->force[0]
+                   : -rho * (a2 * P->vn[i] + a3 * P->vnm1[i]) / dt - P->w2[i] + P->force[1];
       else if (kind == ROW_NEU)
         b = 0.0;
       else
@@ -750,9 +789,9 @@ int orc_simple_iterate(orc_problem *P, double dt, double a1, double a2, double a
     pnew[i] = P->p[i];
     if (P->tag[i] == TAG_INTERIOR || P->tag[i] == TAG_OUTFLOW) continue;
     double fx = -rho * (a1 * P->ut[i] + a2 * P->un[i] + a3 * P->unm1[i]) / dt -
-                rho * (P->ut[i] * gxu[i] + P->vt[i] * gyu[i]) + mu * lu[i];
+                rho * (P->ut[i] * gxu[i] + P->vt[i] * gyu[i]) + mu * lu[i] + P->force[0];
     double fy = -rho * (a1 * P->vt[i] + a2 * P->vn[i] + a3 * P->vnm1[i]) / dt -
-                rho * (P->ut[i] * gxv[i] + P->vt[i] * gyv[i]) + mu * lv[i];
+                rho * (P->ut[i] * gxv[i] + P->vt[i] * gyv[i]) + mu * lv[i] + P->force[1];
     double rhs = P->nx[i] * fx + P->ny[i] * fy;
     double gii = 0.0, off = 0.0;
     for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
@@ -825,10 +864,60 @@ int orc_time_step(orc_problem *P, double dt, double tol_outer, int max_outer, in
 }
 
 /* ------------------------------------------------------------------------ */
+/* Courant number of the explicit-Euler stability bound the paper quotes    */
+/* (Sec. 3.2, the paragraph after the solution steps): lambda dt / 2, lambda */
+/* the spectral radius of the discrete convection-diffusion operator        */
+/*   C = rho (u Dx + v Dy) - mu Lap   at interior rows (other rows zero)    */
+/* at the current velocity.  lambda by power iteration from a fixed start:   */
+/* x_{k+1} = C x_k / |C x_k|_2, lambda = geometric mean of |C x_k|_2 / |x_k| */
+/* over the second half of `iters` steps (robust to complex pairs, unlike    */
+/* a Rayleigh quotient).  out: lambda, courant.                              */
+int orc_courant(orc_problem *P, double dt, int iters, double *out) {
+  int n = P->n;
+  if (iters < 2) return ORC_EINVAL;
+  double *x = dvec(n), *y = dvec(n), *gx = dvec(n), *gy = dvec(n), *gl = dvec(n);
+  if (!x || !y || !gx || !gy || !gl) {
+    free(x); free(y); free(gx); free(gy); free(gl);
+    return ORC_ENOMEM;
+  }
+  for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.5 * (double)((i * 7919) % 13) / 13.0;
+  double nx = 0.0;
+  for (int i = 0; i < n; ++i) nx = nx + x[i] * x[i];
+  nx = sqrt(nx);
+  for (int i = 0; i < n; ++i) x[i] = x[i] / nx;
+  double logsum = 0.0;
+  int counted = 0;
+  for (int k = 0; k < iters; ++k) {
+    csr_spmv(&P->Dx, x, gx);
+    csr_spmv(&P->Dy, x, gy);
+    csr_spmv(&P->Dl, x, gl);
+    double ny = 0.0;
+    for (int i = 0; i < n; ++i) {
+      y[i] = P->tag[i] == TAG_INTERIOR
+                 ? P->rho * (P->u[i] * gx[i] + P->v[i] * gy[i]) - P->mu * gl[i]
+                 : 0.0;
+      ny = ny + y[i] * y[i];
+    }
+    ny = sqrt(ny);
+    if (!(ny > 0.0)) break;
+    if (k >= iters / 2) {
+      logsum = logsum + log(ny);
+      counted++;
+    }
+    for (int i = 0; i < n; ++i) x[i] = y[i] / ny;
+  }
+  double lam = counted > 0 ? exp(logsum / counted) : 0.0;
+  out[0] = lam;
+  out[1] = lam * dt / 2.0;
+  free(x); free(y); free(gx); free(gy); free(gl);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Steady relative residual of the discrete steady equations over the       */
 /* interior rows (vector norms over both velocity components):              */
-/*   r = rho (u.grad) u - mu lap u + grad p                                  */
-/*   R_m = |r|_2 / (|rho (u.grad) u|_2 + |mu lap u|_2 + |grad p|_2)          */
+/*   r = rho (u.grad) u - mu lap u + grad p - f   (f: the body force)       */
+/*   R_m = |r|_2 / (|rho (u.grad) u|_2 + |mu lap u|_2 + |grad p|_2 + |f|_2)  */
 /*   R_c = |Dx u + Dy v|_2 / |grad u|_2,  |grad u|^2 = sum of the squares of */
 /*         Dx u, Dy u, Dx v, Dy v                                           */
 /* out: R_m, R_c, R = max(R_m, R_c).                                         */
@@ -843,22 +932,24 @@ int orc_steady_residual(orc_problem *P, double *R3) {
   csr_spmv(&P->Dx, P->u, gxu); csr_spmv(&P->Dy, P->u, gyu); csr_spmv(&P->Dl, P->u, lu);
   csr_spmv(&P->Dx, P->v, gxv); csr_spmv(&P->Dy, P->v, gyv); csr_spmv(&P->Dl, P->v, lv);
   csr_spmv(&P->Dx, P->p, gpx); csr_spmv(&P->Dy, P->p, gpy);
-  double nr = 0, sa = 0, sd = 0, sp = 0, nc = 0, sg = 0;
+  double nr = 0, sa = 0, sd = 0, sp = 0, nc = 0, sg = 0, sf = 0;
+  const double fx = P->force[0], fy = P->force[1];
   for (int i = 0; i < n; ++i) {
     if (P->tag[i] != TAG_INTERIOR) continue;
     double au = P->rho * (P->u[i] * gxu[i] + P->v[i] * gyu[i]);
     double av = P->rho * (P->u[i] * gxv[i] + P->v[i] * gyv[i]);
     double du = P->mu * lu[i], dv = P->mu * lv[i];
-    double ru = au - du + gpx[i], rv = av - dv + gpy[i];
+    double ru = au - du + gpx[i] - fx, rv = av - dv + gpy[i] - fy;
     nr += ru * ru + rv * rv;
     sa += au * au + av * av;
     sd += du * du + dv * dv;
     sp += gpx[i] * gpx[i] + gpy[i] * gpy[i];
+    sf += fx * fx + fy * fy;
     double rc = gxu[i] + gyv[i];
     nc += rc * rc;
     sg += gxu[i] * gxu[i] + gyu[i] * gyu[i] + gxv[i] * gxv[i] + gyv[i] * gyv[i];
   }
-  double den_m = sqrt(sa) + sqrt(sd) + sqrt(sp);
+  double den_m = sqrt(sa) + sqrt(sd) + sqrt(sp) + sqrt(sf);
   double den_c = sqrt(sg);
   R3[0] = den_m > 0 ? sqrt(nr) / den_m : sqrt(nr);
   R3[1] = den_c > 0 ? sqrt(nc) / den_c : sqrt(nc);

@@ -34,6 +34,27 @@ struct rbffd_ctx {
 
 namespace rbffd {
 
+// a - b along an axis that is periodic with length L (L = 0: bounded): the
+// difference moved by one period when it exceeds half of one, i.e. the
+// nearest periodic image (paper Sec. 3.1: clouds wrap around a periodic
+// boundary).  Round-to-nearest steps, no fusion.
+__host__ __device__ __forceinline__ double pdiff(double a, double b, double L) {
+#ifdef __CUDA_ARCH__
+  double d = __dsub_rn(a, b);
+  if (L > 0.0) {
+    if (d > 0.5 * L) d = __dsub_rn(d, L);
+    else if (d < -0.5 * L) d = __dadd_rn(d, L);
+  }
+#else
+  double d = a - b;
+  if (L > 0.0) {
+    if (d > 0.5 * L) d = d - L;
+    else if (d < -0.5 * L) d = d + L;
+  }
+#endif
+  return d;
+}
+
 void set_error(const char *fmt, ...);
 void clear_error();
 

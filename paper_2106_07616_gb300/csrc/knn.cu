@@ -7,7 +7,10 @@
 // those of a brute-force search that evaluates dx*dx + dy*dy the same way.
 // The ring search stops only when the current (q-1)-th distance is strictly
 // below the clearance of the searched block of cells, so no unvisited point
-// can enter or tie.
+// can enter or tie.  A periodic axis (period L > 0) measures differences to
+// the nearest image and wraps the ring around the grid, each column (row)
+// visited once at its smallest offset; a cell at wrapped offset r + 1 is
+// still at least r cells away, so the clearance bound holds.
 #include "common.cuh"
 #include "knn.cuh"
 
@@ -115,12 +118,25 @@ __device__ __forceinline__ bool key_less(double da, int ja, double db, int jb) {
   return da < db || (da == db && ja < jb);
 }
 
+// Column (row) of the ring at offset d from c, or -1 to skip it: out of a
+// bounded grid, or on a periodic axis not the smallest offset of its column.
+__device__ __forceinline__ int ring_index(int c, int d, int G, bool periodic) {
+  if (!periodic) {
+    const int k = c + d;
+    return (k < 0 || k >= G) ? -1 : k;
+  }
+  int canon = ((d % G) + G) % G;
+  if (canon > G / 2) canon -= G;
+  if (canon != d) return -1;
+  return ((c + d) % G + G) % G;
+}
+
 template <int KMAX>
 __global__ void __launch_bounds__(128) k_knn_query(
     int n, const double *__restrict__ x, const double *__restrict__ y,
     const int8_t *__restrict__ tag, int q, const double *bbox, int G,
     const int *__restrict__ start, const int *__restrict__ pts, int32_t *__restrict__ idx,
-    int *err) {
+    int *err, double Lx, double Ly) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int K = q - 1;
@@ -137,20 +153,20 @@ __global__ void __launch_bounds__(128) k_knn_query(
   int cnt = 0;
   for (int r = 0;; ++r) {
     for (int dy = -r; dy <= r; ++dy) {
-      int yy = cj + dy;
-      if (yy < 0 || yy >= G) continue;
+      const int yy = ring_index(cj, dy, G, Ly > 0.0);
+      if (yy < 0) continue;
       const bool edge = (dy == -r || dy == r);
       const int stp = edge ? 1 : 2 * r;
       for (int dx = -r; dx <= r; dx += stp) {
-        int xx = ci + dx;
-        if (xx < 0 || xx >= G) continue;
+        const int xx = ring_index(ci, dx, G, Lx > 0.0);
+        if (xx < 0) continue;
         int c = yy * G + xx;
         for (int s = start[c], se = start[c + 1]; s < se; ++s) {
           int j = pts[s];
           if (j == i) continue;
           if (bnd && tag[j] != 0) continue;
-          double ddx = __dsub_rn(x[j], xi);
-          double ddy = __dsub_rn(y[j], yi);
+          double ddx = pdiff(x[j], xi, Lx);
+          double ddy = pdiff(y[j], yi, Ly);
           double d2 = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy));
           int p;
           if (cnt < K) {
@@ -208,7 +224,7 @@ int knn_workspace_bytes(int n, KnnLayout *lay) {
 }
 
 int knn_run(rbffd_ctx *ctx, void *ws, const KnnLayout &lay, int n, const double *x,
-            const double *y, const int8_t *tag, int q, int32_t *idx) {
+            const double *y, const int8_t *tag, int q, int32_t *idx, double Lx, double Ly) {
   char *b = (char *)ws;
   double *bbox = (double *)(b + lay.off_bbox);
   int *err = (int *)(b + lay.off_err);
@@ -232,11 +248,14 @@ int knn_run(rbffd_ctx *ctx, void *ws, const KnnLayout &lay, int n, const double 
   RBFFD_TRY(after_launch(ctx, "k_cell_fill"));
   int qb = (n + 127) / 128;
   if (q - 1 <= 32) {
-    k_knn_query<32><<<qb, 128, 0, st>>>(n, x, y, tag, q, bbox, lay.G, start, pts, idx, err);
+    k_knn_query<32><<<qb, 128, 0, st>>>(n, x, y, tag, q, bbox, lay.G, start, pts, idx, err, Lx,
+                                                     Ly);
   } else if (q - 1 <= 64) {
-    k_knn_query<64><<<qb, 128, 0, st>>>(n, x, y, tag, q, bbox, lay.G, start, pts, idx, err);
+    k_knn_query<64><<<qb, 128, 0, st>>>(n, x, y, tag, q, bbox, lay.G, start, pts, idx, err, Lx,
+                                                     Ly);
   } else {
-    k_knn_query<128><<<qb, 128, 0, st>>>(n, x, y, tag, q, bbox, lay.G, start, pts, idx, err);
+    k_knn_query<128><<<qb, 128, 0, st>>>(n, x, y, tag, q, bbox, lay.G, start, pts, idx, err, Lx,
+                                                     Ly);
   }
   RBFFD_TRY(after_launch(ctx, "k_knn_query"));
   int herr = 0;
@@ -264,7 +283,7 @@ extern "C" int rbffd_build_stencils(rbffd_ctx *ctx, int32_t n, const double *x, 
   knn_workspace_bytes(n, &lay);
   void *ws = nullptr;
   RBFFD_TRY(dev_alloc(ctx, &ws, lay.bytes));
-  int rc = knn_run(ctx, ws, lay, n, x, y, tag, q, idx);
+  int rc = knn_run(ctx, ws, lay, n, x, y, tag, q, idx, 0.0, 0.0);
   cudaStreamSynchronize(ctx->stream);
   dev_free(ctx, ws, lay.bytes);
   return rc;
@@ -336,5 +355,5 @@ extern "C" int rbffd_build_stencils_static(rbffd_ctx *ctx, int32_t n, const doub
   RBFFD_TRY(static_scratch(ctx->device, &ws));
   // knn_run clears the counters, cursors and error word it reads before
   // writing them, so the contents left by an earlier call do not matter.
-  return knn_run(ctx, ws, lay, n, x, y, tag, q, idx);
+  return knn_run(ctx, ws, lay, n, x, y, tag, q, idx, 0.0, 0.0);
 }

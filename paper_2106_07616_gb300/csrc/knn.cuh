@@ -13,7 +13,8 @@ struct KnnLayout {
 };
 
 int knn_workspace_bytes(int n, KnnLayout *lay);
+// Lx, Ly: periods of the axes (0: bounded).
 int knn_run(rbffd_ctx *ctx, void *ws, const KnnLayout &lay, int n, const double *x,
-            const double *y, const int8_t *tag, int q, int32_t *idx);
+            const double *y, const int8_t *tag, int q, int32_t *idx, double Lx, double Ly);
 
 }  // namespace rbffd

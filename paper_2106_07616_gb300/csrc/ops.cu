@@ -74,8 +74,9 @@ __global__ void k_pack(int n, int q, int ldn, int pin, const int32_t *__restrict
 
 // S4: momentum matrix and right-hand sides, Eqs. (u:tilde), (v:tilde):
 //   rho a1/dt u~ + rho u^r Dx u~ + rho v^r Dy u~ - mu Lap u~
-//       = -rho (a2 u^n + a3 u^{n-1}) / dt - (Dx p^r)
-// at interior rows; boundary rows by row_kind (identity with the boundary
+//       = -rho (a2 u^n + a3 u^{n-1}) / dt - (Dx p^r) + f_x
+// at interior rows (f: the body force, e.g. the mean pressure gradient of
+// a periodic flow); boundary rows by row_kind (identity with the boundary
 // value, or n . grad with a zero right-hand side).  Am serves u~ (and v~
 // too when Am2 is null: no symmetry rows); Am2, when given, is the v~
 // matrix, equal to Am except on symmetry lines.  The initial guesses of the
@@ -89,7 +90,8 @@ __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ co
                            const double *__restrict__ vnm1, const double *__restrict__ ubc,
                            const double *__restrict__ vbc, const double *__restrict__ nx,
                            const double *__restrict__ ny, double rho, double mu, double dt,
-                           double a1, double a2, double a3, double *__restrict__ Am,
+                           double a1, double a2, double a3, double fx, double fy,
+                           double *__restrict__ Am,
                            double *__restrict__ mdinv, double *__restrict__ Am2,
                            double *__restrict__ mdinv2, double *__restrict__ bu,
                            double *__restrict__ bv, double *__restrict__ ut,
@@ -140,8 +142,8 @@ __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ co
   }
   mdinv[i] = 1.0 / (diag == 0.0 ? 1.0 : diag);
   if (Am2) mdinv2[i] = mdinv[i];
-  bu[i] = -rho * (a2 * un[i] + a3 * unm1[i]) / dt - gx;
-  bv[i] = -rho * (a2 * vn[i] + a3 * vnm1[i]) / dt - gy;
+  bu[i] = -rho * (a2 * un[i] + a3 * unm1[i]) / dt - gx + fx;
+  bv[i] = -rho * (a2 * vn[i] + a3 * vnm1[i]) / dt - gy + fy;
 }
 
 // S6: right-hand side of Eq. (pressure poisson) at interior rows, zero at
@@ -185,7 +187,7 @@ __global__ void k_pressure(int n, int q, int ldn, const int32_t *__restrict__ co
                            const double *__restrict__ un, const double *__restrict__ vn,
                            const double *__restrict__ unm1, const double *__restrict__ vnm1,
                            double rho, double mu, double dt, double a1, double a2, double a3,
-                           double *__restrict__ p_out) {
+                           double fx, double fy, double *__restrict__ p_out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (tag[i] == RBFFD_TAG_INTERIOR) {
@@ -218,11 +220,11 @@ __global__ void k_pressure(int n, int q, int ldn, const int32_t *__restrict__ co
     }
   }
   const double uti = ut[i], vti = vt[i];
-  const double fx = -rho * (a1 * uti + a2 * un[i] + a3 * unm1[i]) / dt -
-                    rho * (uti * gxu + vti * gyu) + mu * lu;
-  const double fy = -rho * (a1 * vti + a2 * vn[i] + a3 * vnm1[i]) / dt -
-                    rho * (uti * gxv + vti * gyv) + mu * lv;
-  p_out[i] = (ni * fx + mi * fy - off) / gii;
+  const double mx = -rho * (a1 * uti + a2 * un[i] + a3 * unm1[i]) / dt -
+                    rho * (uti * gxu + vti * gyu) + mu * lu + fx;
+  const double my = -rho * (a1 * vti + a2 * vn[i] + a3 * vnm1[i]) / dt -
+                    rho * (uti * gxv + vti * gyv) + mu * lv + fy;
+  p_out[i] = (ni * mx + mi * my - off) / gii;
 }
 
 // S8 velocity correction, Eqs. (u:correction), (v:correction), of every
@@ -311,9 +313,10 @@ __global__ void __launch_bounds__(RT) k_resid(int n, int q, int ldn,
                                               const double *__restrict__ u,
                                               const double *__restrict__ v,
                                               const double *__restrict__ p, double rho,
-                                              double mu, double *__restrict__ part) {
+                                              double mu, double fx, double fy,
+                                              double *__restrict__ part) {
   __shared__ double sred[RT / 32];
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
     if (tag[i] != 0) continue;
     double gxu = 0, gyu = 0, lu = 0, gxv = 0, gyv = 0, lv = 0, gpx = 0, gpy = 0;
@@ -329,8 +332,9 @@ __global__ void __launch_bounds__(RT) k_resid(int n, int q, int ldn,
     const double ui = u[i], vi = v[i];
     const double au = rho * (ui * gxu + vi * gyu), av = rho * (ui * gxv + vi * gyv);
     const double du = mu * lu, dv = mu * lv;
-    const double ru = au - du + gpx, rv = av - dv + gpy;
+    const double ru = au - du + gpx - fx, rv = av - dv + gpy - fy;
     acc[0] += ru * ru + rv * rv;
+    acc[6] += fx * fx + fy * fy;
     acc[1] += au * au + av * av;
     acc[2] += du * du + dv * dv;
     acc[3] += gpx * gpx + gpy * gpy;
@@ -339,7 +343,7 @@ __global__ void __launch_bounds__(RT) k_resid(int n, int q, int ldn,
     acc[5] += gxu * gxu + gyu * gyu + gxv * gxv + gyv * gyv;
   }
 #pragma unroll
-  for (int s = 0; s < 6; ++s) {
+  for (int s = 0; s < 7; ++s) {
     double t = block_sum<RT>(acc[s], sred);
     if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
   }
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(RT) k_resid(int n, int q, int ldn,
 
 // Fixed-order sums of the partials into the iteration record.
 // mode 0: delta = (S0 + S1) / n   mode 1: change = (S0 + S1) / n
-// mode 2: steady residual from the six sums of k_resid.
+// mode 2: steady residual from the seven sums of k_resid.
 __global__ void k_finalize(const double *__restrict__ part, int nb, int n, int mode,
                            IterRecord *rec) {
   if (threadIdx.x >= 32) return;
@@ -362,10 +366,10 @@ __global__ void k_finalize(const double *__restrict__ part, int nb, int n, int m
         rec->change = d;
     }
   } else {
-    double s[6];
-    for (int k = 0; k < 6; ++k) s[k] = warp_sum_array(part + k * nb, nb);
+    double s[7];
+    for (int k = 0; k < 7; ++k) s[k] = warp_sum_array(part + k * nb, nb);
     if (threadIdx.x == 0) {
-      double dm = sqrt(s[1]) + sqrt(s[2]) + sqrt(s[3]);
+      double dm = sqrt(s[1]) + sqrt(s[2]) + sqrt(s[3]) + sqrt(s[6]);
       double dc = sqrt(s[5]);
       double rm = dm > 0 ? sqrt(s[0]) / dm : sqrt(s[0]);
       double rc = dc > 0 ? sqrt(s[4]) / dc : sqrt(s[4]);
@@ -404,6 +408,59 @@ __global__ void k_spmv(int n, int q, int ldn, const int32_t *__restrict__ col,
   y[i] = s;
 }
 
+// Courant helper: y = C x with C = rho (u Dx + v Dy) - mu Lap at interior
+// rows (zero elsewhere), plus the block partials of sum y^2.
+__global__ void __launch_bounds__(RT) k_cd_apply(
+    int n, int q, int ldn, const int32_t *__restrict__ col, const double *__restrict__ Wx,
+    const double *__restrict__ Wy, const double *__restrict__ Wl, const int8_t *__restrict__ tag,
+    const double *__restrict__ u, const double *__restrict__ v, double rho, double mu,
+    const double *__restrict__ x, double *__restrict__ y, double *__restrict__ part) {
+  __shared__ double sred[RT / 32];
+  double acc = 0.0;
+  for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
+    double yi = 0.0;
+    if (tag[i] == 0) {
+      double gx = 0.0, gy = 0.0, gl = 0.0;
+      for (int j = 0; j < q; ++j) {
+        const int64_t e = (int64_t)j * ldn + i;
+        const double xc = x[col[e]];
+        gx += Wx[e] * xc;
+        gy += Wy[e] * xc;
+        gl += Wl[e] * xc;
+      }
+      yi = rho * (u[i] * gx + v[i] * gy) - mu * gl;
+    }
+    y[i] = yi;
+    acc += yi * yi;
+  }
+  acc = block_sum<RT>(acc, sred);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// x = y / |y| (every block sums the partials in the same order); block 0
+// adds log|y| to *logacc when `count` is set.
+__global__ void __launch_bounds__(RT) k_cd_scale(int n, const double *__restrict__ y,
+                                                 const double *__restrict__ part, int nb,
+                                                 double *__restrict__ x, double *logacc,
+                                                 int count) {
+  __shared__ double s_norm;
+  if (threadIdx.x < 32) {
+    const double t = warp_sum_array(part, nb);
+    if (threadIdx.x == 0) s_norm = sqrt(t);
+  }
+  __syncthreads();
+  const double nrm = s_norm;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && count && nrm > 0.0) *logacc += log(nrm);
+  const double r = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) x[i] = y[i] * r;
+}
+
+__global__ void k_cd_start(int n, double *__restrict__ x, double *logacc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *logacc = 0.0;
+  if (i < n) x[i] = 1.0 + 0.5 * (double)((i * 7919) % 13) / 13.0;
+}
+
 // ------------------------------------------------------------------ host
 
 static inline int grid_of(int n) { return (n + RT - 1) / RT; }
@@ -419,7 +476,8 @@ int ops_momentum(rbffd_problem *P, const rbffd_step_params *sp) {
   k_momentum<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(
       P->n, P->q, P->ldn, P->col, P->Wx, P->Wy, P->Wl, P->tag, P->u, P->v, P->p, P->un, P->vn,
       P->unm1, P->vnm1, P->ubc, P->vbc, P->nx, P->ny, P->rho, P->mu, sp->dt, sp->alpha[0],
-      sp->alpha[1], sp->alpha[2], P->Am, P->m_dinv, P->has_sym ? P->Am2 : nullptr,
+      sp->alpha[1], sp->alpha[2], P->force[0], P->force[1], P->Am, P->m_dinv,
+      P->has_sym ? P->Am2 : nullptr,
       P->has_sym ? P->m_dinv2 : nullptr, P->bu, P->bv, P->ut, P->vt);
   return after_launch(P->ctx, "k_momentum");
 }
@@ -436,7 +494,7 @@ int ops_pressure(rbffd_problem *P, const rbffd_step_params *sp) {
   k_pressure<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(
       P->n, P->q, P->ldn, P->col, P->Wx, P->Wy, P->Wl, P->tag, P->nx, P->ny, P->p, P->pc,
       P->ut, P->vt, P->un, P->vn, P->unm1, P->vnm1, P->rho, P->mu, sp->dt, sp->alpha[0],
-      sp->alpha[1], sp->alpha[2], P->p2);
+      sp->alpha[1], sp->alpha[2], P->force[0], P->force[1], P->p2);
   RBFFD_TRY(after_launch(P->ctx, "k_pressure"));
   double *t = P->p;
   P->p = P->p2;
@@ -471,10 +529,29 @@ int ops_rotate(rbffd_problem *P) {
 int ops_resid(rbffd_problem *P) {
   k_resid<<<P->rblocks, RT, 0, P->ctx->stream>>>(P->n, P->q, P->ldn, P->col, P->Wx, P->Wy,
                                                  P->Wl, P->tag, P->u, P->v, P->p, P->rho, P->mu,
-                                                 P->rpart);
+                                                 P->force[0], P->force[1], P->rpart);
   RBFFD_TRY(after_launch(P->ctx, "k_resid"));
   k_finalize<<<1, 32, 0, P->ctx->stream>>>(P->rpart, P->rblocks, P->n, 2, P->rec);
   return after_launch(P->ctx, "k_finalize");
+}
+
+// Power iteration of the Courant helper (see k_cd_apply): iters steps from
+// the fixed start, log|C x_k| summed over the second half into *logacc.
+int ops_courant(rbffd_problem *P, int iters, double *logacc) {
+  cudaStream_t st = P->ctx->stream;
+  double *x = P->kv[0].r, *y = P->kv[0].p;  // Krylov workspace, free between solves
+  double *part = P->rpart;
+  k_cd_start<<<grid_of(P->n), RT, 0, st>>>(P->n, x, logacc);
+  RBFFD_TRY(after_launch(P->ctx, "k_cd_start"));
+  for (int k = 0; k < iters; ++k) {
+    k_cd_apply<<<P->rblocks, RT, 0, st>>>(P->n, P->q, P->ldn, P->col, P->Wx, P->Wy, P->Wl,
+                                          P->tag, P->u, P->v, P->rho, P->mu, x, y, part);
+    RBFFD_TRY(after_launch(P->ctx, "k_cd_apply"));
+    k_cd_scale<<<P->rblocks, RT, 0, st>>>(P->n, y, part, P->rblocks, x, logacc,
+                                          k >= iters / 2);
+    RBFFD_TRY(after_launch(P->ctx, "k_cd_scale"));
+  }
+  return RBFFD_OK;
 }
 
 int ops_spmv(rbffd_problem *P, const double *val, const double *x, double *y) {

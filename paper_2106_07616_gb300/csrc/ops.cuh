@@ -10,6 +10,7 @@ int ops_pressure(rbffd_problem *P, const rbffd_step_params *sp);
 int ops_correct(rbffd_problem *P, const rbffd_step_params *sp);
 int ops_rotate(rbffd_problem *P);
 int ops_resid(rbffd_problem *P);
+int ops_courant(rbffd_problem *P, int iters, double *logacc);
 int ops_spmv(rbffd_problem *P, const double *val, const double *x, double *y);
 int ops_reduce_blocks(rbffd_ctx *ctx, int n);
 int ops_to_inner(rbffd_problem *P, const double *src, void *dst, int64_t m);

@@ -58,6 +58,11 @@ int check_desc(const rbffd_problem_desc *d) {
     set_error("problem desc: rho must be > 0 and mu >= 0");
     return RBFFD_EINVAL;
   }
+  if (!(d->period[0] >= 0.0) || !(d->period[1] >= 0.0) || !std::isfinite(d->force[0]) ||
+      !std::isfinite(d->force[1])) {
+    set_error("problem desc: periods must be >= 0 and forces finite");
+    return RBFFD_EINVAL;
+  }
   if (d->precond != RBFFD_PRECOND_JACOBI && d->precond != RBFFD_PRECOND_AMG) {
     set_error("problem desc: unknown preconditioner %d", d->precond);
     return RBFFD_EINVAL;
@@ -128,14 +133,19 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
   P->rho = d->rho;
   P->mu = d->mu;
   P->pin = d->pin;
+  P->per[0] = d->period[0];
+  P->per[1] = d->period[1];
+  P->force[0] = d->force[0];
+  P->force[1] = d->force[1];
   prof_begin(ctx, 3);
-  RBFFD_TRY(knn_run(ctx, P->knn_ws, P->knn_lay, P->n, P->x, P->y, P->tag, P->q, P->idx_rm));
+  RBFFD_TRY(knn_run(ctx, P->knn_ws, P->knn_lay, P->n, P->x, P->y, P->tag, P->q, P->idx_rm,
+                    P->per[0], P->per[1]));
   prof_end(ctx, 3);
   int big = 0x7fffffff;
   RBFFD_CK(cudaMemcpyAsync(P->d_first_singular, &big, sizeof(int), cudaMemcpyHostToDevice, st));
   prof_begin(ctx, 0);
   RBFFD_TRY(weights_run(ctx, P->n, P->x, P->y, P->q, P->idx_rm, P->degree, P->wx_rm, P->wy_rm,
-                        P->wl_rm, P->d_first_singular));
+                        P->wl_rm, P->d_first_singular, P->per[0], P->per[1]));
   prof_end(ctx, 0);
   RBFFD_TRY(ops_pack(P));
   free_amg(P);
@@ -401,7 +411,7 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
   for (int k = 0; k < 14; ++k) o_f[k] = c.take<double>(n);
   size_t o_kv[16];
   for (int k = 0; k < 16; ++k) o_kv[k] = c.take<double>(n);
-  size_t o_part = c.take<double>(npart), o_rpart = c.take<double>(6 * (size_t)P->rblocks);
+  size_t o_part = c.take<double>(npart), o_rpart = c.take<double>(7 * (size_t)P->rblocks);
   size_t o_bar = c.take<GridBarrier>(1);
   size_t o_flags = c.take<unsigned int>(256);
   size_t o_rec = c.take<Readback>(1);
@@ -628,6 +638,20 @@ int problem_step_end(rbffd_problem *P, double *change) {
   return RBFFD_OK;
 }
 }  // namespace rbffd
+
+extern "C" int rbffd_courant(rbffd_problem *P, double dt, int32_t iters, double *lambda_out,
+                             double *courant_out) {
+  if (!P || iters < 2 || !(dt > 0)) return RBFFD_EINVAL;
+  RBFFD_CK(cudaSetDevice(P->ctx->device));
+  RBFFD_TRY(ops_courant(P, iters, &P->rec->pad[0]));
+  Readback r;
+  RBFFD_TRY(read_back(P, &r));
+  const int counted = iters - iters / 2;
+  const double lam = std::exp(r.rec.pad[0] / counted);
+  if (lambda_out) *lambda_out = lam;
+  if (courant_out) *courant_out = lam * dt / 2.0;
+  return RBFFD_OK;
+}
 
 extern "C" int rbffd_steady_residual(rbffd_problem *P, double *R3) {
   if (!P || !R3) return RBFFD_EINVAL;

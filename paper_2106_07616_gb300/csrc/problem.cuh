@@ -18,6 +18,8 @@ struct rbffd_problem {
   int n = 0, q = 0, degree = 0, pin = 0, precision = 0;
   int ldn = 0;  // padded row count of the column-major ELL arrays
   double rho = 1.0, mu = 1.0;
+  double per[2] = {0.0, 0.0};    // periods of x and y (0: bounded)
+  double force[2] = {0.0, 0.0};  // body force per unit volume
   // inputs
   double *x, *y, *nx, *ny, *ubc, *vbc;
   int8_t *tag;

@@ -45,7 +45,7 @@ __device__ __forceinline__ double ipow_rn(double b, int e) {
 __global__ void k_weights(int n, const double *__restrict__ x, const double *__restrict__ y,
                           int q, const int32_t *__restrict__ idx, int m, int wpb,
                           double *__restrict__ wx, double *__restrict__ wy,
-                          double *__restrict__ wl, int *first_singular) {
+                          double *__restrict__ wl, int *first_singular, double Lx, double Ly) {
   extern __shared__ double smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = q + m, LD = (N + 3) | 1, W = N + 3;
@@ -59,7 +59,7 @@ __global__ void k_weights(int n, const double *__restrict__ x, const double *__r
     double d2m = 0.0;
     for (int a = lane; a < q; a += 32) {
       int j = cl[a];
-      double dx = __dsub_rn(x[j], xc), dy = __dsub_rn(y[j], yc);
+      double dx = pdiff(x[j], xc, Lx), dy = pdiff(y[j], yc, Ly);
       double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
       d2m = fmax(d2m, d2);
     }
@@ -69,8 +69,8 @@ __global__ void k_weights(int n, const double *__restrict__ x, const double *__r
     if (h == 0.0) h = 1.0;
     for (int a = lane; a < q; a += 32) {
       int j = cl[a];
-      xi[a] = __ddiv_rn(__dsub_rn(x[j], xc), h);
-      eta[a] = __ddiv_rn(__dsub_rn(y[j], yc), h);
+      xi[a] = __ddiv_rn(pdiff(x[j], xc, Lx), h);
+      eta[a] = __ddiv_rn(pdiff(y[j], yc, Ly), h);
     }
     __syncwarp();
     // Phi block: r^3
@@ -188,7 +188,7 @@ int weights_config(int q, int degree, int *wpb, size_t *smem) {
 
 int weights_run(rbffd_ctx *ctx, int n, const double *x, const double *y, int q,
                 const int32_t *idx, int degree, double *wx, double *wy, double *wl,
-                int *d_first_singular) {
+                int *d_first_singular, double Lx, double Ly) {
   int m = (degree + 1) * (degree + 2) / 2;
   RBFFD_TRY(ensure_tables(ctx->device));
   int wpb;
@@ -200,7 +200,7 @@ int weights_run(rbffd_ctx *ctx, int n, const double *x, const double *y, int q,
   int cap = ctx->num_sms * 16;
   if (blocks > cap) blocks = cap;
   k_weights<<<blocks, 32 * wpb, smem, ctx->stream>>>(n, x, y, q, idx, m, wpb, wx, wy, wl,
-                                                     d_first_singular);
+                                                     d_first_singular, Lx, Ly);
   return after_launch(ctx, "k_weights");
 }
 
@@ -231,7 +231,7 @@ extern "C" int rbffd_weights(rbffd_ctx *ctx, int32_t n, const double *x, const d
       cudaSuccess) {
     rc = RBFFD_ECUDA;
   } else {
-    rc = weights_run(ctx, n, x, y, q, idx, degree, wx, wy, wl, dfs);
+    rc = weights_run(ctx, n, x, y, q, idx, degree, wx, wy, wl, dfs, 0.0, 0.0);
   }
   int hfs = big;
   if (rc == RBFFD_OK) {

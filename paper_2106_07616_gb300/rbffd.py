@@ -39,7 +39,7 @@ class ProblemDesc(C.Structure):
                 ("rho", C.c_double), ("mu", C.c_double), ("precision", C.c_int32),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("tag", C.c_void_p), ("nx", C.c_void_p),
                 ("ny", C.c_void_p), ("ubc", C.c_void_p), ("vbc", C.c_void_p),
-                ("precond", C.c_int32)]
+                ("precond", C.c_int32), ("period", C.c_double * 2), ("force", C.c_double * 2)]
 
 
 class StepParams(C.Structure):
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
         "rbffd_problem_reload": (C.c_int, [vp, C.POINTER(ProblemDesc)]),
         "rbffd_problem_destroy": (None, [vp]),
         "rbffd_problem_bytes": (sz, [vp]),
+        "rbffd_courant": (C.c_int, [vp, dbl, i32, C.POINTER(dbl), C.POINTER(dbl)]),
         "rbffd_problem_amg_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64),
                                              C.POINTER(dbl)]),
         "rbffd_amg_analyze": (C.c_int, [i32, vp, vp, vp, C.POINTER(i32), C.POINTER(i32),
@@ -242,18 +243,22 @@ def make_desc(fp, precision=PREC_FP64, keep=None, precond=PRECOND_JACOBI):
     d.n, d.q, d.degree, d.pin = fp.n, fp.q, fp.degree, int(fp.pin)
     d.rho, d.mu, d.precision = float(fp.rho), float(fp.mu), int(precision)
     d.precond = int(precond)
+    d.period[0], d.period[1] = (float(v) for v in getattr(fp, "period", (0.0, 0.0)))
+    d.force[0], d.force[1] = (float(v) for v in getattr(fp, "force", (0.0, 0.0)))
     for k, a in arrs.items():
         setattr(d, k, a.ctypes.data)
     return d
 
 
 def desc_from_pointers(n, q, degree, pin, rho, mu, precision, x, y, tag, nx, ny, ubc, vbc,
-                       precond=PRECOND_JACOBI):
+                       precond=PRECOND_JACOBI, period=(0.0, 0.0), force=(0.0, 0.0)):
     """ProblemDesc from raw host or device buffers (tensors or arrays)."""
     d = ProblemDesc()
     d.n, d.q, d.degree, d.pin = int(n), int(q), int(degree), int(pin)
     d.rho, d.mu, d.precision = float(rho), float(mu), int(precision)
     d.precond = int(precond)
+    d.period[0], d.period[1] = float(period[0]), float(period[1])
+    d.force[0], d.force[1] = float(force[0]), float(force[1])
     for k, a in (("x", x), ("y", y), ("tag", tag), ("nx", nx), ("ny", ny), ("ubc", ubc),
                  ("vbc", vbc)):
         setattr(d, k, ptr(a))
@@ -291,6 +296,14 @@ class Problem:
     @property
     def nbytes(self) -> int:
         return int(load().rbffd_problem_bytes(self.h))
+
+    def courant(self, dt, iters=200):
+        """(lambda, lambda dt / 2) of the convection-diffusion operator."""
+        lam = C.c_double(0)
+        co = C.c_double(0)
+        _check(load().rbffd_courant(self.h, float(dt), int(iters), C.byref(lam), C.byref(co)),
+               "rbffd_courant")
+        return lam.value, co.value
 
     def amg_info(self, with_time=False):
         """Rows and nonzeros per level of the p' multigrid hierarchy ([] with
