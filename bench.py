@@ -65,17 +65,26 @@ def workload(name: str):
     return fp, desc
 
 
-def krylov_traffic(precision, workload_name):
+KRYLOV_PROFILES = {
+    # preconditioner: (committed ncu summary, kernel sources it was taken from)
+    "jacobi": ("k_bicgstab_fp64_cavity200.md", ("krylov.cu", "krylov_dev.cuh", "common.cuh")),
+    "amg": ("k_bicgstab_amg_fp64_cavity200.md",
+            ("krylov.cu", "krylov_dev.cuh", "common.cuh", "amg_dev.cuh", "amg.cuh")),
+}
+
+
+def krylov_traffic(precision, workload_name, precond="jacobi"):
     """DRAM bytes per pressure-correction launch from the committed ncu
     summary, only while the kernel sources still hash to the profiled ones."""
     import hashlib
-    if precision != "fp64" or workload_name != "cavity200":
+    if precision != "fp64" or workload_name != "cavity200" or precond not in KRYLOV_PROFILES:
         return None
-    prof = os.path.join(ROOT, "profiles", "k_bicgstab_fp64_cavity200.md")
+    name, files = KRYLOV_PROFILES[precond]
+    prof = os.path.join(ROOT, "profiles", name)
     csrc = os.path.join(ROOT, "paper_2106_07616_gb300", "csrc")
     try:
         h = hashlib.sha256()
-        for f in ("krylov.cu", "krylov_dev.cuh", "common.cuh"):
+        for f in files:
             h.update(open(os.path.join(csrc, f), "rb").read())
         fields = dict(l.split(":", 1) for l in open(prof) if l.startswith(("source_hash", "traffic_")))
         if fields["source_hash"].split()[0] != h.hexdigest()[:16]:
@@ -457,16 +466,20 @@ def run_native(args):
     l2_mb = fp.n * (fp.q * 12 + 8 * 8) / 1e6  # p' operator + indices + Krylov vectors
     achieved = kp["bytes"] / (kp["ms"] / 1e3) / 1e9 if kp["ms"] > 0 else 0.0
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": krylov_traffic(args.precision, args.workload),
+            "frac": achieved / peak, "traffic": krylov_traffic(args.precision, args.workload, args.precond),
             "peak_source": peak_src,
-            "kernel": {"mixed": "k_bicgstab_ir<1> (pressure-correction FP32 BiCGSTAB in FP64 "
+            "kernel": ("k_bicgstab_amg<1024> (pressure-correction BiCGSTAB, FP32 multigrid "
+                       "V-cycle preconditioner, persistent)" if args.precond == "amg" and
+                       args.precision == "fp64" else
+                       {"mixed": "k_bicgstab_ir<1> (pressure-correction FP32 BiCGSTAB in FP64 "
                                 "refinement)",
                        "ff": "k_bicgstab_ir<1> (pressure-correction float-float BiCGSTAB in "
                              "FP64 refinement)"}.get(
-                           args.precision, "k_bicgstab<1> (pressure-correction BiCGSTAB, persistent)"),
+                           args.precision, "k_bicgstab<1> (pressure-correction BiCGSTAB, persistent)")),
             "launches": kp["launches"], "avg_launch_ms": kp["ms"] / max(kp["launches"], 1),
-            "bytes_per_unit": (f"6q(8+4)+32*8 = {6 * fp.q * 12 + 256} B per row-iteration "
-                               f"(2 SpMV + 2 V-cycles) + the coarse levels' operators"
+            "bytes_per_unit": (f"2q(8+4)+14*8 + 2 FP32 V-cycles (~2q(4+4)+48) = "
+                               f"{2 * fp.q * 12 + 112 + 2 * (fp.q * 8 + 48)} B per row-iteration "
+                               f"+ the coarse levels' operators"
                                if args.precond == "amg" else
                                f"2q(4+4)+14*4 = {2 * fp.q * 8 + 56} B per FP32 row-iteration"
                                if args.precision == "mixed" else

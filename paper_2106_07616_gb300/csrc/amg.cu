@@ -514,6 +514,13 @@ struct Staging {
     if (!v.empty()) memcpy(buf.data() + at, v.data(), v.size() * sizeof(T));
     return at;
   }
+  // FP64 values stored in the cycle's arithmetic (round to nearest)
+  size_t put_amg(const std::vector<double> &v) {
+    size_t at = take(v.size() * sizeof(amg_t));
+    amg_t *d = reinterpret_cast<amg_t *>(buf.data() + at);
+    for (size_t k = 0; k < v.size(); ++k) d[k] = (amg_t)v[k];
+    return at;
+  }
 };
 
 }  // namespace
@@ -578,7 +585,7 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
     CsrOff o;
     o.ptr = S.put(M.ptr);
     o.col = S.put(M.col);
-    o.val = S.put(M.val);
+    o.val = S.put_amg(M.val);
     o.grp = lanes_for(M);
     return o;
   };
@@ -587,18 +594,18 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
     size_t b = 0, z = 0, y = 0;
   };
   std::vector<Off> off(L);
-  const size_t o_s0 = S.put(s0);
+  const size_t o_s0 = S.put_amg(s0);
   for (int l = 0; l < L; ++l) {
     if (l > 0) off[l].S = put_csr(H.S[l]);
     if (l + 1 < L) {
       off[l].R = put_csr(H.R[l]);
       off[l].P = put_csr(H.P[l]);
     }
-    if (l > 0) off[l].b = S.take(sizeof(double) * H.A[l].n);
-    off[l].z = S.take(sizeof(double) * H.A[l].n);
-    off[l].y = S.take(sizeof(double) * H.A[l].n);
+    if (l > 0) off[l].b = S.take(sizeof(amg_t) * H.A[l].n);
+    off[l].z = S.take(sizeof(amg_t) * H.A[l].n);
+    off[l].y = S.take(sizeof(amg_t) * H.A[l].n);
   }
-  const size_t o_cinv = S.put(H.cinv);
+  const size_t o_cinv = S.put_amg(H.cinv);
   void *dmem = nullptr;
   RBFFD_TRY(dev_alloc(ctx, &dmem, S.buf.size()));
   char *base = (char *)dmem;
@@ -606,24 +613,24 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
     AmgCsr c;
     c.ptr = have ? (const int32_t *)(base + o.ptr) : nullptr;
     c.col = have ? (const int32_t *)(base + o.col) : nullptr;
-    c.val = have ? (const double *)(base + o.val) : nullptr;
+    c.val = have ? (const amg_t *)(base + o.val) : nullptr;
     c.grp = o.grp;
     return c;
   };
   AmgDev h;
   memset(&h, 0, sizeof(h));
   h.nlev = L;
-  h.cinv = (const double *)(base + o_cinv);
-  h.s0 = (const double *)(base + o_s0);
+  h.cinv = (const amg_t *)(base + o_cinv);
+  h.s0 = (const amg_t *)(base + o_s0);
   for (int l = 0; l < L; ++l) {
     AmgLevel &v = h.lev[l];
     v.n = H.A[l].n;
     v.S = csr_at(off[l].S, l > 0);
     v.R = csr_at(off[l].R, l + 1 < L);
     v.P = csr_at(off[l].P, l + 1 < L);
-    v.b = l > 0 ? (double *)(base + off[l].b) : nullptr;
-    v.z = (double *)(base + off[l].z);
-    v.y = (double *)(base + off[l].y);
+    v.b = l > 0 ? (amg_t *)(base + off[l].b) : nullptr;
+    v.z = (amg_t *)(base + off[l].z);
+    v.y = (amg_t *)(base + off[l].y);
   }
   memcpy(S.buf.data() + o_dev, &h, sizeof(h));
   if (cudaMemcpyAsync(dmem, S.buf.data(), S.buf.size(), cudaMemcpyHostToDevice, ctx->stream) !=

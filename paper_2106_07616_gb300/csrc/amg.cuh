@@ -11,10 +11,17 @@ namespace rbffd {
 
 constexpr int AMG_MAXLEV = 10;
 
+// The V-cycle runs in FP32: the preconditioner only has to approximate
+// A^-1, the BiCGSTAB around it keeps FP64 vectors, SpMVs and dot products
+// and stops on the FP64 residual.  On GB300, where FP64 issues at a small
+// fraction of the FP32 rate, this takes the cycle's arithmetic off the
+// FP64 pipe and halves its bytes.
+using amg_t = float;
+
 // A CSR matrix on the device, read with `grp` lanes per row.
 struct AmgCsr {
   const int32_t *ptr, *col;
-  const double *val;
+  const amg_t *val;
   int grp;  // 1, 2, 4, 8, 16 or 32
 };
 
@@ -31,15 +38,15 @@ struct AmgLevel {
   AmgCsr S;    // levels >= 1
   AmgCsr R;    // n_{l+1} x n_l (not on the coarsest)
   AmgCsr P;    // n_l x n_{l+1} (not on the coarsest)
-  double *b;   // right-hand side (levels >= 1)
-  double *z;   // S_l b_l
-  double *y;   // the level's result
+  amg_t *b;    // right-hand side (levels >= 1)
+  amg_t *z;    // S_l b_l
+  amg_t *y;    // the level's result
 };
 
 struct AmgDev {
   int nlev;            // levels including the coarsest
-  const double *cinv;  // inverse of the coarsest matrix, row-major nc x nc
-  const double *s0;    // level 0's S, ELL [q][ldn] on the solve's column array
+  const amg_t *cinv;   // inverse of the coarsest matrix, row-major nc x nc
+  const amg_t *s0;     // level 0's S, ELL [q][ldn] on the solve's column array
   AmgLevel lev[AMG_MAXLEV];
 };
 

@@ -8,8 +8,9 @@
 // (an exchange since it was written) before the call.
 //
 // Level 0's S uses the solve's ELL columns (T threads per row); the CSR
-// operators use grp lanes per row.  Vectors written in this launch are read
-// with __ldcg (coherent L2).
+// operators use grp lanes per row.  The cycle computes in amg_t (FP32): it
+// reads b_0 in FP64 and rounds, and writes the FP64 result.  Vectors written
+// in this launch are read with __ldcg (coherent L2).
 #pragma once
 #include "amg.cuh"
 #include "krylov.cuh"
@@ -25,28 +26,28 @@ namespace amgdev {
 // CC entries a lane, not per entry.
 constexpr int CC = 8;
 
-template <typename F>
-__device__ __forceinline__ void csr_rows(const AmgCsr &M, int nrows, const double *x, int wglobal,
+template <typename XT, typename F>
+__device__ __forceinline__ void csr_rows(const AmgCsr &M, int nrows, const XT *x, int wglobal,
                                          int nwarps, F &&f) {
   const int lane = threadIdx.x & 31;
   const int G = M.grp, rpw = 32 / G, g = lane / G, lg = lane - g * G;
   for (int base = wglobal * rpw; base < nrows; base += nwarps * rpw) {
     const int i = base + g;
-    double t = 0.0;
+    amg_t t = 0;
     if (i < nrows) {
       const int s = __ldg(M.ptr + i), e = __ldg(M.ptr + i + 1);
       for (int k0 = s + lg; k0 < e; k0 += CC * G) {
         int c[CC];
-        double a[CC];
+        amg_t a[CC];
 #pragma unroll
         for (int u = 0; u < CC; ++u) {
           const int k = k0 + u * G;
           c[u] = k < e ? __ldg(M.col + k) : -1;
-          a[u] = k < e ? __ldg(M.val + k) : 0.0;
+          a[u] = k < e ? __ldg(M.val + k) : amg_t(0);
         }
 #pragma unroll
         for (int u = 0; u < CC; ++u)
-          if (c[u] >= 0) t += a[u] * __ldcg(x + c[u]);
+          if (c[u] >= 0) t += a[u] * amg_t(__ldcg(x + c[u]));
       }
     }
     for (int o = G >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
@@ -66,14 +67,16 @@ __device__ __forceinline__ bool sync(const Ctx &c, unsigned int &epoch) {
 }
 
 // y = A_L^-1 b on the coarsest level, one warp per row
-__device__ __forceinline__ void coarse_solve(const AmgDev *__restrict__ G, int nc, const double *b,
-                                             double *y, const Ctx &c) {
+template <typename XT, typename YT>
+__device__ __forceinline__ void coarse_solve(const AmgDev *__restrict__ G, int nc, const XT *b,
+                                             YT *y, const Ctx &c) {
   const int lane = threadIdx.x & 31;
   for (int i = c.wglobal; i < nc; i += c.nwarps) {
-    double t = 0.0;
-    for (int j = lane; j < nc; j += 32) t += __ldg(G->cinv + (size_t)i * nc + j) * __ldcg(b + j);
+    amg_t t = 0;
+    for (int j = lane; j < nc; j += 32)
+      t += __ldg(G->cinv + (size_t)i * nc + j) * amg_t(__ldcg(b + j));
     t = kdev::wsum(t);
-    if (lane == 0) y[i] = t;
+    if (lane == 0) y[i] = YT(t);
   }
 }
 
@@ -90,17 +93,18 @@ __device__ __noinline__ bool vcycle(const AmgDev *__restrict__ G, const Ctx &c,
   for (int l = 0; l + 1 < L; ++l) {
     const AmgLevel &Lv = G->lev[l];
     const AmgLevel &Nx = G->lev[l + 1];
-    const double *bl = l == 0 ? b0 : Lv.b;
-    double *z = Lv.z;
+    amg_t *z = Lv.z;
+    amg_t *bn = Nx.b;
     if (l == 0) {
-      const double *xs[1] = {bl};
-      kdev::spmv_rows<1, double>(A.n, A.q, A.ldn, A.tpr, A.col, G->s0, xs, c.wglobal, c.nwarps,
-                                 [&](int i, const double *sb) { z[i] = sb[0]; });
+      const double *xs[1] = {b0};
+      kdev::spmv_rows<1, amg_t>(A.n, A.q, A.ldn, A.tpr, A.col, G->s0, xs, c.wglobal, c.nwarps,
+                                [&](int i, const amg_t *sb) { z[i] = sb[0]; });
+      csr_rows(Lv.R, Nx.n, b0, c.wglobal, c.nwarps, [&](int k, amg_t t) { bn[k] = t; });
     } else {
-      csr_rows(Lv.S, Lv.n, bl, c.wglobal, c.nwarps, [&](int i, double t) { z[i] = t; });
+      const amg_t *bl = Lv.b;
+      csr_rows(Lv.S, Lv.n, bl, c.wglobal, c.nwarps, [&](int i, amg_t t) { z[i] = t; });
+      csr_rows(Lv.R, Nx.n, bl, c.wglobal, c.nwarps, [&](int k, amg_t t) { bn[k] = t; });
     }
-    double *bn = Nx.b;
-    csr_rows(Lv.R, Nx.n, bl, c.wglobal, c.nwarps, [&](int k, double t) { bn[k] = t; });
     if (!sync(c, epoch)) return false;
   }
   // ---- coarsest
@@ -112,10 +116,15 @@ __device__ __noinline__ bool vcycle(const AmgDev *__restrict__ G, const Ctx &c,
   // ---- up
   for (int l = L - 2; l >= 0; --l) {
     const AmgLevel &Lv = G->lev[l];
-    double *res = l == 0 ? out : Lv.y;
-    const double *z = Lv.z;
-    csr_rows(Lv.P, Lv.n, G->lev[l + 1].y, c.wglobal, c.nwarps,
-             [&](int i, double t) { res[i] = __ldcg(z + i) + t; });
+    const amg_t *z = Lv.z;
+    if (l == 0) {
+      csr_rows(Lv.P, Lv.n, G->lev[1].y, c.wglobal, c.nwarps,
+               [&](int i, amg_t t) { out[i] = double(__ldcg(z + i) + t); });
+    } else {
+      amg_t *res = Lv.y;
+      csr_rows(Lv.P, Lv.n, G->lev[l + 1].y, c.wglobal, c.nwarps,
+               [&](int i, amg_t t) { res[i] = __ldcg(z + i) + t; });
+    }
     if (!sync(c, epoch)) return false;
   }
   return true;

@@ -672,14 +672,16 @@ namespace rbffd {
 double pcorr_bytes(const rbffd_problem *P, int iters) {
   const double n = P->n, q = P->q, it = iters;
   if (!P->amg) return n * it * (2 * q * 12 + 14 * 8);
-  // per V-cycle: S_0 b_0 (ELL, q (8 + 4) + 2 vectors), R~_l and P~_l and
-  // S_l (l >= 1) entries at 12 B, their vectors, the dense coarsest inverse
+  // per V-cycle (FP32 operators and level vectors, FP64 in and out): S_0 b_0
+  // (ELL, q (4 + 4) + b_0 read + z written), R~_l, P~_l and S_l (l >= 1)
+  // entries at 8 B, their vectors, the dense coarsest inverse
   const AmgInfo &I = P->amg_info;
-  double cyc = n * (q * 12 + 16) + n * 24;  // S_0, then P~_0's z read and out write
+  const double e = sizeof(amg_t) + 4.0, v = sizeof(amg_t);
+  double cyc = n * (q * e + 8 + v) + n * (v + 8);  // S_0, then P~_0's z read and out write
   for (int l = 0; l < I.nlev; ++l) {
-    if (l + 1 < I.nlev) cyc += 12.0 * (I.nnz_r[l] + I.nnz_p[l]);
-    if (l >= 1 && l + 1 < I.nlev) cyc += 12.0 * I.nnz[l] + 40.0 * I.n[l];
-    if (l + 1 == I.nlev) cyc += 8.0 * I.n[l] * I.n[l];
+    if (l + 1 < I.nlev) cyc += e * (I.nnz_r[l] + I.nnz_p[l]);
+    if (l >= 1 && l + 1 < I.nlev) cyc += e * I.nnz[l] + 5.0 * v * I.n[l];
+    if (l + 1 == I.nlev) cyc += v * I.n[l] * I.n[l];
   }
   return n * it * (2 * q * 12 + 14 * 8) + 2.0 * it * cyc;
 }
