@@ -119,7 +119,7 @@ def run_batch(args):
 
     from paper_2106_07616_gb300 import _build, rbffd
     _build.build()
-    fps = batch_instances(args.count)
+    fps = batch_instances(args.count or 256)
     stream = torch.cuda.current_stream()
     ctx = rbffd.Context(0, stream=stream.cuda_stream)
     pc = rbffd.PRECOND_AMG if args.precond == "amg" else rbffd.PRECOND_JACOBI
@@ -160,7 +160,7 @@ def run_batch(args):
     out = {"metric": "SIMPLE outer iters/s (batched instances)", "value": outer / (total_ms / 1e3),
            "unit": "instance_outer_iter/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "dtype": "f64",
-           "config": {"workload": f"batch{args.count}", "instances": len(fps), "rows": rows,
+           "config": {"workload": f"batch{args.count or 256}", "instances": len(fps), "rows": rows,
                       "precond": args.precond,
                       "nnz_per_operator": nnz,
                       "description": "Kovasznay/cavity instances, N log-uniform [1k,64k], "
@@ -175,25 +175,33 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
-def serve_requests(count, seed=5):
-    """Serving workload: Kovasznay (Re 20-60) and cavity (Re 10-100) steady
-    solves, N log-uniform on [1k, 4k], degree {3, 4}, q = 2m, Poisson
-    arrivals at a mean of 20 per second."""
+def serve_requests(count, seed=5, n_lo=5000.0, n_hi=50000.0):
+    """Serving workload: steady solves of three geometries drawn uniformly --
+    Kovasznay (Re 20-60), lid-driven cavity (Re 10-400) and flow past a
+    cylinder (Re 10-40, the paper's steady range) -- N log-uniform on
+    [n_lo, n_hi], degree {3, 4}, q = 2m, dt at a Courant number of about 10,
+    Poisson arrivals at a mean of 20 per second."""
     rng = np.random.Generator(np.random.PCG64(seed))
     reqs, t = [], 0.0
     for i in range(count):
         t += rng.exponential(1.0 / 20.0)
-        n = float(np.exp(rng.uniform(np.log(1000.0), np.log(4000.0))))
+        n = float(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
         side = int(np.ceil(np.sqrt(n)))
         k = int(rng.integers(3, 5))
         q = (k + 1) * (k + 2)
-        if rng.uniform() < 0.5:
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
             re = float(rng.uniform(20.0, 60.0))
             fp = clouds.kovasznay(side, seed=5000 + i, degree=k, q=q, re=re,
                                   dt=20.0 / (side - 1))
-        else:
-            re = float(rng.uniform(10.0, 100.0))
+        elif kind == 1:
+            re = float(rng.uniform(10.0, 400.0))
             fp = clouds.cavity(side, seed=5000 + i, degree=k, q=q, re=re, dt=10.0 / (side - 1))
+        else:
+            re = float(rng.uniform(10.0, 40.0))
+            h0 = 0.1 * float(np.sqrt(5000.0 / n))
+            fp = clouds.cylinder(int(n), seed=5000 + i, degree=k, q=q, re=re, dt=10.0 * h0,
+                                 h0=h0, hmax=0.5)
         reqs.append((t, fp))
     return reqs
 
@@ -203,7 +211,7 @@ def run_serve(args):
 
     from paper_2106_07616_gb300 import _build, rbffd
     _build.build()
-    reqs = serve_requests(args.count)
+    reqs = serve_requests(args.count or 48)
     ctx = rbffd.Context(0)
     S = rbffd.Server(ctx)
     t0 = time.perf_counter()
@@ -235,10 +243,10 @@ def run_serve(args):
            "steps_ok": [r["steps"] for r in ok], "outer_ok": [r["outer"] for r in ok],
            "R_ok": [float(r["resid"][2]) for r in ok], "max_steps": args.max_steps,
            "precond": args.precond,
-           "config": {"workload": f"serve{args.count}",
+           "config": {"workload": f"serve{args.count or 48}",
                       "description": "Poisson arrivals 20/s; Kovasznay Re 20-60 / cavity "
-                                     "Re 10-100, N log-uniform [1k,4k], degree {3,4}, q=2m; "
-                                     "continuous batching in one server"}}
+                                     "Re 10-400 / cylinder Re 10-40, N log-uniform [5k,50k], "
+                                     "degree {3,4}, q=2m; continuous batching in one server"}}
     print(json.dumps(out), flush=True)
 
 
@@ -535,7 +543,8 @@ def main():
     ap.add_argument("--workload", default="cavity200")
     ap.add_argument("--outer", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--count", type=int, default=256, help="instances / requests (batch, serve)")
+    ap.add_argument("--count", type=int, default=None,
+                    help="instances (batch, default 256) / requests (serve, default 48)")
     ap.add_argument("--resid-tol", type=float, default=1e-5)
     ap.add_argument("--criterion", type=int, default=1,
                     help="serve: 0 = steady residual R, 1 = the paper's steady error change/dt")
