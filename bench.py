@@ -476,7 +476,7 @@ def run_native(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": krylov_traffic(args.precision, args.workload, args.precond),
             "peak_source": peak_src,
-            "kernel": ("k_bicgstab_amg<1024> (pressure-correction BiCGSTAB, FP32 multigrid "
+            "kernel": ("k_bicgstab_amg<1024> (pressure-correction BiCGSTAB, multigrid "
                        "V-cycle preconditioner, persistent)" if args.precond == "amg" and
                        args.precision == "fp64" else
                        {"mixed": "k_bicgstab_ir<1> (pressure-correction FP32 BiCGSTAB in FP64 "
@@ -485,8 +485,8 @@ def run_native(args):
                              "FP64 refinement)"}.get(
                            args.precision, "k_bicgstab<1> (pressure-correction BiCGSTAB, persistent)")),
             "launches": kp["launches"], "avg_launch_ms": kp["ms"] / max(kp["launches"], 1),
-            "bytes_per_unit": (f"2q(8+4)+14*8 + 2 FP32 V-cycles (~2q(4+4)+48) = "
-                               f"{2 * fp.q * 12 + 112 + 2 * (fp.q * 8 + 48)} B per row-iteration "
+            "bytes_per_unit": (f"2q(8+4)+14*8 + 2 V-cycles (~2q(8+4)+64) = "
+                               f"{2 * fp.q * 12 + 112 + 2 * (fp.q * 12 + 64)} B per row-iteration "
                                f"+ the coarse levels' operators"
                                if args.precond == "amg" else
                                f"2q(4+4)+14*4 = {2 * fp.q * 8 + 56} B per FP32 row-iteration"

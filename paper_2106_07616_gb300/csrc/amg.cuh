@@ -11,12 +11,13 @@ namespace rbffd {
 
 constexpr int AMG_MAXLEV = 10;
 
-// The V-cycle runs in FP32: the preconditioner only has to approximate
-// A^-1, the BiCGSTAB around it keeps FP64 vectors, SpMVs and dot products
-// and stops on the FP64 residual.  On GB300, where FP64 issues at a small
-// fraction of the FP32 rate, this takes the cycle's arithmetic off the
-// FP64 pipe and halves its bytes.
-using amg_t = float;
+// Arithmetic of the V-cycle (operators, dense inverse, level vectors).
+// FP64: with amg_t = float the cycle's rounding (~1e-7 relative on every
+// application, different for every input) breaks the short recurrences of
+// the BiCGSTAB around it -- measured on the 200 x 200 cavity p' system:
+// 1996 iterations to 1e-12 instead of 76 -- so the cycle stays in FP64
+// although GB300 issues FP32 far faster.
+using amg_t = double;
 
 // A CSR matrix on the device, read with `grp` lanes per row.
 struct AmgCsr {
