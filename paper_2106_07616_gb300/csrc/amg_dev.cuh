@@ -8,9 +8,9 @@
 // (an exchange since it was written) before the call.
 //
 // Level 0's S uses the solve's ELL columns (T threads per row); the CSR
-// operators use grp lanes per row.  The cycle computes in amg_t (FP32): it
-// reads b_0 in FP64 and rounds, and writes the FP64 result.  Vectors written
-// in this launch are read with __ldcg (coherent L2).
+// operators use grp lanes per row.  The cycle computes in amg_t (see
+// amg.cuh); it reads b_0 and writes its result in FP64.  Vectors written in
+// this launch are read with __ldcg (coherent L2).
 #pragma once
 #include "amg.cuh"
 #include "krylov.cuh"
