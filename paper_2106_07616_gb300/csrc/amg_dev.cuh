@@ -81,7 +81,7 @@ __device__ __forceinline__ void coarse_solve(const AmgDev *__restrict__ G, int n
 }
 
 // out = V-cycle(b0)
-__device__ __noinline__ bool vcycle(const AmgDev *__restrict__ G, const Ctx &c,
+__device__ __forceinline__ bool vcycle(const AmgDev *__restrict__ G, const Ctx &c,
                                     const double *b0, double *out, unsigned int &epoch) {
   const KrylovArgs &A = *c.A;
   const int L = G->nlev;
