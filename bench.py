@@ -389,7 +389,8 @@ def run_native(args):
             "fp64": rbffd.PREC_FP64}[args.precision]
     init = {k: torch.from_numpy(np.ascontiguousarray(a)).to(f"cuda:{local}")
             for k, a in (fp.initial or {}).items()}
-    pc = rbffd.PRECOND_AMG if args.precond == "amg" else rbffd.PRECOND_JACOBI
+    pc = {"amg": rbffd.PRECOND_AMG, "fgmres": rbffd.PRECOND_AMG_FGMRES}.get(
+        args.precond, rbffd.PRECOND_JACOBI)
     desc_dev = rbffd.desc_from_pointers(fp.n, fp.q, fp.degree, fp.pin, fp.rho, fp.mu, prec,
                                         dev["x"], dev["y"], dev["tag"], dev["nx"], dev["ny"],
                                         dev["ubc"], dev["vbc"], pc)
@@ -476,7 +477,9 @@ def run_native(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": krylov_traffic(args.precision, args.workload, args.precond),
             "peak_source": peak_src,
-            "kernel": ("k_bicgstab_amg<1024> (pressure-correction BiCGSTAB, multigrid "
+            "kernel": ("k_fgmres<1024> (pressure-correction flexible GMRES(30), FP32 multigrid "
+                       "V-cycle preconditioner, persistent)" if args.precond == "fgmres" else
+                       "k_bicgstab_amg<1024> (pressure-correction BiCGSTAB, multigrid "
                        "V-cycle preconditioner, persistent)" if args.precond == "amg" and
                        args.precision == "fp64" else
                        {"mixed": "k_bicgstab_ir<1> (pressure-correction FP32 BiCGSTAB in FP64 "
@@ -485,7 +488,9 @@ def run_native(args):
                              "FP64 refinement)"}.get(
                            args.precision, "k_bicgstab<1> (pressure-correction BiCGSTAB, persistent)")),
             "launches": kp["launches"], "avg_launch_ms": kp["ms"] / max(kp["launches"], 1),
-            "bytes_per_unit": (f"2q(8+4)+14*8 + 2 V-cycles (~2q(8+4)+64) = "
+            "bytes_per_unit": (f"q(8+4)+16 + one FP32 V-cycle + Gram-Schmidt over the basis "
+                               f"per row-iteration (pcorr_bytes)" if args.precond == "fgmres" else
+                               f"2q(8+4)+14*8 + 2 V-cycles (~2q(8+4)+64) = "
                                f"{2 * fp.q * 12 + 112 + 2 * (fp.q * 12 + 64)} B per row-iteration "
                                f"+ the coarse levels' operators"
                                if args.precond == "amg" else
@@ -549,7 +554,7 @@ def main():
     ap.add_argument("--criterion", type=int, default=1,
                     help="serve: 0 = steady residual R, 1 = the paper's steady error change/dt")
     ap.add_argument("--max-steps", type=int, default=1000)
-    ap.add_argument("--precond", default="amg", choices=["jacobi", "amg"],
+    ap.add_argument("--precond", default="amg", choices=["jacobi", "amg", "fgmres"],
                     help="preconditioner of the pressure-correction BiCGSTAB")
     ap.add_argument("--precision", default="fp64", choices=["mixed", "ff", "fp64"],
                     help="Krylov arithmetic: FP32 or float-float inside FP64 defect "

@@ -93,9 +93,12 @@ enum {
  * residual, so it changes the iteration count, not the solution. */
 enum {
   RBFFD_PRECOND_JACOBI = 0, /* diagonal scaling (default) */
-  RBFFD_PRECOND_AMG = 1     /* one V-cycle of a smoothed-aggregation multigrid hierarchy,
+  RBFFD_PRECOND_AMG = 1,    /* one V-cycle of a smoothed-aggregation multigrid hierarchy,
                                built on the host when the problem is built (RBFFD_PREC_FP64
-                               only; batched and served solves use Jacobi) */
+                               only); two cycles per BiCGSTAB iteration, FP64 */
+  RBFFD_PRECOND_AMG_FGMRES = 2 /* the same hierarchy stored in FP32, one cycle per step of
+                               a flexible GMRES(30) instead of BiCGSTAB (RBFFD_PREC_FP64
+                               only; not in batches or the request server) */
 };
 #define RBFFD_AMG_MAX_LEVELS 10
 

@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "librbffd.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 
-SOURCES = ["context.cu", "knn.cu", "weights.cu", "krylov.cu", "krylov_mixed.cu", "ops.cu", "amg.cu",
+SOURCES = ["context.cu", "knn.cu", "weights.cu", "krylov.cu", "krylov_mixed.cu", "ops.cu", "amg.cu", "fgmres.cu",
            "problem.cu", "batch.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,

@@ -514,11 +514,12 @@ struct Staging {
     if (!v.empty()) memcpy(buf.data() + at, v.data(), v.size() * sizeof(T));
     return at;
   }
-  // FP64 values stored in the cycle's arithmetic (round to nearest)
-  size_t put_amg(const std::vector<double> &v) {
-    size_t at = take(v.size() * sizeof(amg_t));
-    amg_t *d = reinterpret_cast<amg_t *>(buf.data() + at);
-    for (size_t k = 0; k < v.size(); ++k) d[k] = (amg_t)v[k];
+  // FP64 values stored in the cycle's arithmetic T (round to nearest)
+  template <typename T>
+  size_t put_as(const std::vector<double> &v) {
+    size_t at = take(v.size() * sizeof(T));
+    T *d = reinterpret_cast<T *>(buf.data() + at);
+    for (size_t k = 0; k < v.size(); ++k) d[k] = (T)v[k];
     return at;
   }
 };
@@ -539,8 +540,10 @@ int amg_analyze(int n, const int32_t *rowptr, const int32_t *col, const double *
   return RBFFD_OK;
 }
 
+template <typename T>
 int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
-              void **mem, size_t *bytes, const AmgDev **dev, AmgDev *host_view, AmgInfo *info) {
+              void **mem, size_t *bytes, const AmgDevT<T> **dev, AmgDevT<T> *host_view,
+              AmgInfo *info) {
   *mem = nullptr;
   *bytes = 0;
   *dev = nullptr;
@@ -576,7 +579,7 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
 
   // ---- pack everything into one staging buffer, then one upload
   Staging S;
-  const size_t o_dev = S.take(sizeof(AmgDev));
+  const size_t o_dev = S.take(sizeof(AmgDevT<T>));
   struct CsrOff {
     size_t ptr = 0, col = 0, val = 0;
     int grp = 1;
@@ -585,7 +588,7 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
     CsrOff o;
     o.ptr = S.put(M.ptr);
     o.col = S.put(M.col);
-    o.val = S.put_amg(M.val);
+    o.val = S.put_as<T>(M.val);
     o.grp = lanes_for(M);
     return o;
   };
@@ -594,43 +597,43 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
     size_t b = 0, z = 0, y = 0;
   };
   std::vector<Off> off(L);
-  const size_t o_s0 = S.put_amg(s0);
+  const size_t o_s0 = S.put_as<T>(s0);
   for (int l = 0; l < L; ++l) {
     if (l > 0) off[l].S = put_csr(H.S[l]);
     if (l + 1 < L) {
       off[l].R = put_csr(H.R[l]);
       off[l].P = put_csr(H.P[l]);
     }
-    if (l > 0) off[l].b = S.take(sizeof(amg_t) * H.A[l].n);
-    off[l].z = S.take(sizeof(amg_t) * H.A[l].n);
-    off[l].y = S.take(sizeof(amg_t) * H.A[l].n);
+    if (l > 0) off[l].b = S.take(sizeof(T) * H.A[l].n);
+    off[l].z = S.take(sizeof(T) * H.A[l].n);
+    off[l].y = S.take(sizeof(T) * H.A[l].n);
   }
-  const size_t o_cinv = S.put_amg(H.cinv);
+  const size_t o_cinv = S.put_as<T>(H.cinv);
   void *dmem = nullptr;
   RBFFD_TRY(dev_alloc(ctx, &dmem, S.buf.size()));
   char *base = (char *)dmem;
   auto csr_at = [&](const CsrOff &o, bool have) {
-    AmgCsr c;
+    AmgCsrT<T> c;
     c.ptr = have ? (const int32_t *)(base + o.ptr) : nullptr;
     c.col = have ? (const int32_t *)(base + o.col) : nullptr;
-    c.val = have ? (const amg_t *)(base + o.val) : nullptr;
+    c.val = have ? (const T *)(base + o.val) : nullptr;
     c.grp = o.grp;
     return c;
   };
-  AmgDev h;
+  AmgDevT<T> h;
   memset(&h, 0, sizeof(h));
   h.nlev = L;
-  h.cinv = (const amg_t *)(base + o_cinv);
-  h.s0 = (const amg_t *)(base + o_s0);
+  h.cinv = (const T *)(base + o_cinv);
+  h.s0 = (const T *)(base + o_s0);
   for (int l = 0; l < L; ++l) {
-    AmgLevel &v = h.lev[l];
+    AmgLevelT<T> &v = h.lev[l];
     v.n = H.A[l].n;
     v.S = csr_at(off[l].S, l > 0);
     v.R = csr_at(off[l].R, l + 1 < L);
     v.P = csr_at(off[l].P, l + 1 < L);
-    v.b = l > 0 ? (amg_t *)(base + off[l].b) : nullptr;
-    v.z = (amg_t *)(base + off[l].z);
-    v.y = (amg_t *)(base + off[l].y);
+    v.b = l > 0 ? (T *)(base + off[l].b) : nullptr;
+    v.z = (T *)(base + off[l].z);
+    v.y = (T *)(base + off[l].y);
   }
   memcpy(S.buf.data() + o_dev, &h, sizeof(h));
   if (cudaMemcpyAsync(dmem, S.buf.data(), S.buf.size(), cudaMemcpyHostToDevice, ctx->stream) !=
@@ -642,10 +645,17 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
   }
   *mem = dmem;
   *bytes = S.buf.size();
-  *dev = (const AmgDev *)(base + o_dev);
+  *dev = (const AmgDevT<T> *)(base + o_dev);
   if (host_view) *host_view = h;
   fill_info(H, ms_since(t0), info);
   return RBFFD_OK;
 }
+
+template int amg_build<double>(rbffd_ctx *, int, int, int, const int32_t *, const double *,
+                               void **, size_t *, const AmgDevT<double> **, AmgDevT<double> *,
+                               AmgInfo *);
+template int amg_build<float>(rbffd_ctx *, int, int, int, const int32_t *, const double *,
+                              void **, size_t *, const AmgDevT<float> **, AmgDevT<float> *,
+                              AmgInfo *);
 
 }  // namespace rbffd

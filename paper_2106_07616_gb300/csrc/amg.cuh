@@ -11,18 +11,19 @@ namespace rbffd {
 
 constexpr int AMG_MAXLEV = 10;
 
-// Arithmetic of the V-cycle (operators, dense inverse, level vectors).
-// FP64: with amg_t = float the cycle's rounding (~1e-7 relative on every
-// application, different for every input) breaks the short recurrences of
-// the BiCGSTAB around it -- measured on the 200 x 200 cavity p' system:
-// 1996 iterations to 1e-12 instead of 76 -- so the cycle stays in FP64
-// although GB300 issues FP32 far faster.
-using amg_t = double;
+// Arithmetic of the V-cycle (operators, dense inverse, level vectors): a
+// type parameter T.  Inside BiCGSTAB the cycle is FP64: an FP32 cycle's
+// rounding (~1e-7 relative on every application, different for every
+// input) breaks BiCGSTAB's short recurrences, which assume one fixed linear
+// preconditioner -- measured on the 200 x 200 cavity p' system: 1996
+// iterations to 1e-12 instead of 76.  FGMRES keeps every preconditioned
+// vector and minimises over them, so it takes an FP32 cycle (fgmres.cu).
 
 // A CSR matrix on the device, read with `grp` lanes per row.
-struct AmgCsr {
+template <typename T>
+struct AmgCsrT {
   const int32_t *ptr, *col;
-  const amg_t *val;
+  const T *val;
   int grp;  // 1, 2, 4, 8, 16 or 32
 };
 
@@ -33,23 +34,32 @@ struct AmgCsr {
 //   b_{l+1} = R~_l b_l,     R~_l = R_l (I - A_l W)       (restricted residual)
 //   y_l = z_l + P~_l y_{l+1},  P~_l = (I - W A_l) P_l    (correction, post-smoothed)
 // which needs one grid exchange per level on the way down and one on the
-// way up.  Level 0's S lives in AmgDev::s0 in the solve's ELL layout.
-struct AmgLevel {
-  int n;       // rows
-  AmgCsr S;    // levels >= 1
-  AmgCsr R;    // n_{l+1} x n_l (not on the coarsest)
-  AmgCsr P;    // n_l x n_{l+1} (not on the coarsest)
-  amg_t *b;    // right-hand side (levels >= 1)
-  amg_t *z;    // S_l b_l
-  amg_t *y;    // the level's result
+// way up.  Level 0's S lives in AmgDevT::s0 in the solve's ELL layout.
+template <typename T>
+struct AmgLevelT {
+  int n;            // rows
+  AmgCsrT<T> S;     // levels >= 1
+  AmgCsrT<T> R;     // n_{l+1} x n_l (not on the coarsest)
+  AmgCsrT<T> P;     // n_l x n_{l+1} (not on the coarsest)
+  T *b;             // right-hand side (levels >= 1)
+  T *z;             // S_l b_l
+  T *y;             // the level's result
 };
 
-struct AmgDev {
-  int nlev;            // levels including the coarsest
-  const amg_t *cinv;   // inverse of the coarsest matrix, row-major nc x nc
-  const amg_t *s0;     // level 0's S, ELL [q][ldn] on the solve's column array
-  AmgLevel lev[AMG_MAXLEV];
+template <typename T>
+struct AmgDevT {
+  using value_type = T;
+  int nlev;         // levels including the coarsest
+  const T *cinv;    // inverse of the coarsest matrix, row-major nc x nc
+  const T *s0;      // level 0's S, ELL [q][ldn] on the solve's column array
+  AmgLevelT<T> lev[AMG_MAXLEV];
 };
+
+using amg_t = double;  // the cycle inside BiCGSTAB
+using AmgCsr = AmgCsrT<double>;
+using AmgLevel = AmgLevelT<double>;
+using AmgDev = AmgDevT<double>;
+using AmgDevF = AmgDevT<float>;  // the cycle inside FGMRES
 
 struct AmgInfo {
   int nlev;
@@ -66,8 +76,11 @@ struct AmgInfo {
 // *bytes; freed with dev_free).  *dev receives the device copy of the
 // level table.  Errors: RBFFD_ESINGULAR if the coarsest matrix is singular,
 // RBFFD_ENOMEM, RBFFD_ECUDA.
+// T = double or float: the stored arithmetic of the cycle.
+template <typename T>
 int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
-              void **mem, size_t *bytes, const AmgDev **dev, AmgDev *host_view, AmgInfo *info);
+              void **mem, size_t *bytes, const AmgDevT<T> **dev, AmgDevT<T> *host_view,
+              AmgInfo *info);
 
 // The host part alone, on a CSR matrix (analysis and tests): level sizes
 // and nonzeros in *info.

@@ -8,9 +8,11 @@
 // (an exchange since it was written) before the call.
 //
 // Level 0's S uses the solve's ELL columns (T threads per row); the CSR
-// operators use grp lanes per row.  The cycle computes in amg_t (see
-// amg.cuh); it reads b_0 and writes its result in FP64.  Vectors written in
-// this launch are read with __ldcg (coherent L2).
+// operators use grp lanes per row.  The cycle computes in the hierarchy's
+// value type T (FP64 or FP32, see amg.cuh); it reads b_0 and writes its
+// result in FP64.  Vectors written in this launch are read with __ldcg
+// (coherent L2).  Ctx carries the grid-exchange state; it is independent of
+// the Krylov method around the cycle.
 #pragma once
 #include "amg.cuh"
 #include "krylov.cuh"
@@ -26,28 +28,28 @@ namespace amgdev {
 // CC entries a lane, not per entry.
 constexpr int CC = 8;
 
-template <typename XT, typename F>
-__device__ __forceinline__ void csr_rows(const AmgCsr &M, int nrows, const XT *x, int wglobal,
+template <typename T, typename XT, typename F>
+__device__ __forceinline__ void csr_rows(const AmgCsrT<T> &M, int nrows, const XT *x, int wglobal,
                                          int nwarps, F &&f) {
   const int lane = threadIdx.x & 31;
   const int G = M.grp, rpw = 32 / G, g = lane / G, lg = lane - g * G;
   for (int base = wglobal * rpw; base < nrows; base += nwarps * rpw) {
     const int i = base + g;
-    amg_t t = 0;
+    T t = 0;
     if (i < nrows) {
       const int s = __ldg(M.ptr + i), e = __ldg(M.ptr + i + 1);
       for (int k0 = s + lg; k0 < e; k0 += CC * G) {
         int c[CC];
-        amg_t a[CC];
+        T a[CC];
 #pragma unroll
         for (int u = 0; u < CC; ++u) {
           const int k = k0 + u * G;
           c[u] = k < e ? __ldg(M.col + k) : -1;
-          a[u] = k < e ? __ldg(M.val + k) : amg_t(0);
+          a[u] = k < e ? __ldg(M.val + k) : T(0);
         }
 #pragma unroll
         for (int u = 0; u < CC; ++u)
-          if (c[u] >= 0) t += a[u] * amg_t(__ldcg(x + c[u]));
+          if (c[u] >= 0) t += a[u] * T(__ldcg(x + c[u]));
       }
     }
     for (int o = G >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
@@ -55,35 +57,40 @@ __device__ __forceinline__ void csr_rows(const AmgCsr &M, int nrows, const XT *x
   }
 }
 
+// What a cycle needs from the solve around it: level 0's ELL structure,
+// the grid-exchange flags and this thread's place in the grid.
 struct Ctx {
-  const KrylovArgs *A;
+  int n, q, ldn, tpr;
+  const int32_t *col;
+  unsigned int *flags;
+  int *err;
   int lb, nb, tid, stride, wglobal, nwarps;
   double *stot;
 };
 
 __device__ __forceinline__ bool sync(const Ctx &c, unsigned int &epoch) {
-  return kdev::exchange<0, double>(c.A->flags, &c.A->bar->err, epoch++, nullptr, nullptr,
-                                   c.stot, c.lb, c.nb);
+  return kdev::exchange<0, double>(c.flags, c.err, epoch++, nullptr, nullptr, c.stot, c.lb,
+                                   c.nb);
 }
 
 // y = A_L^-1 b on the coarsest level, one warp per row
-template <typename XT, typename YT>
-__device__ __forceinline__ void coarse_solve(const AmgDev *__restrict__ G, int nc, const XT *b,
-                                             YT *y, const Ctx &c) {
+template <typename T, typename XT, typename YT>
+__device__ __forceinline__ void coarse_solve(const AmgDevT<T> *__restrict__ G, int nc,
+                                             const XT *b, YT *y, const Ctx &c) {
   const int lane = threadIdx.x & 31;
   for (int i = c.wglobal; i < nc; i += c.nwarps) {
-    amg_t t = 0;
+    T t = 0;
     for (int j = lane; j < nc; j += 32)
-      t += __ldg(G->cinv + (size_t)i * nc + j) * amg_t(__ldcg(b + j));
+      t += __ldg(G->cinv + (size_t)i * nc + j) * T(__ldcg(b + j));
     t = kdev::wsum(t);
     if (lane == 0) y[i] = YT(t);
   }
 }
 
 // out = V-cycle(b0)
-__device__ __forceinline__ bool vcycle(const AmgDev *__restrict__ G, const Ctx &c,
-                                    const double *b0, double *out, unsigned int &epoch) {
-  const KrylovArgs &A = *c.A;
+template <typename T>
+__device__ __forceinline__ bool vcycle(const AmgDevT<T> *__restrict__ G, const Ctx &c,
+                                       const double *b0, double *out, unsigned int &epoch) {
   const int L = G->nlev;
   if (L == 1) {
     coarse_solve(G, G->lev[0].n, b0, out, c);
@@ -91,39 +98,39 @@ __device__ __forceinline__ bool vcycle(const AmgDev *__restrict__ G, const Ctx &
   }
   // ---- down
   for (int l = 0; l + 1 < L; ++l) {
-    const AmgLevel &Lv = G->lev[l];
-    const AmgLevel &Nx = G->lev[l + 1];
-    amg_t *z = Lv.z;
-    amg_t *bn = Nx.b;
+    const AmgLevelT<T> &Lv = G->lev[l];
+    const AmgLevelT<T> &Nx = G->lev[l + 1];
+    T *z = Lv.z;
+    T *bn = Nx.b;
     if (l == 0) {
       const double *xs[1] = {b0};
-      kdev::spmv_rows<1, amg_t>(A.n, A.q, A.ldn, A.tpr, A.col, G->s0, xs, c.wglobal, c.nwarps,
-                                [&](int i, const amg_t *sb) { z[i] = sb[0]; });
-      csr_rows(Lv.R, Nx.n, b0, c.wglobal, c.nwarps, [&](int k, amg_t t) { bn[k] = t; });
+      kdev::spmv_rows<1, T>(c.n, c.q, c.ldn, c.tpr, c.col, G->s0, xs, c.wglobal, c.nwarps,
+                            [&](int i, const T *sb) { z[i] = sb[0]; });
+      csr_rows(Lv.R, Nx.n, b0, c.wglobal, c.nwarps, [&](int k, T t) { bn[k] = t; });
     } else {
-      const amg_t *bl = Lv.b;
-      csr_rows(Lv.S, Lv.n, bl, c.wglobal, c.nwarps, [&](int i, amg_t t) { z[i] = t; });
-      csr_rows(Lv.R, Nx.n, bl, c.wglobal, c.nwarps, [&](int k, amg_t t) { bn[k] = t; });
+      const T *bl = Lv.b;
+      csr_rows(Lv.S, Lv.n, bl, c.wglobal, c.nwarps, [&](int i, T t) { z[i] = t; });
+      csr_rows(Lv.R, Nx.n, bl, c.wglobal, c.nwarps, [&](int k, T t) { bn[k] = t; });
     }
     if (!sync(c, epoch)) return false;
   }
   // ---- coarsest
   {
-    const AmgLevel &Cl = G->lev[L - 1];
+    const AmgLevelT<T> &Cl = G->lev[L - 1];
     coarse_solve(G, Cl.n, Cl.b, Cl.y, c);
     if (!sync(c, epoch)) return false;
   }
   // ---- up
   for (int l = L - 2; l >= 0; --l) {
-    const AmgLevel &Lv = G->lev[l];
-    const amg_t *z = Lv.z;
+    const AmgLevelT<T> &Lv = G->lev[l];
+    const T *z = Lv.z;
     if (l == 0) {
       csr_rows(Lv.P, Lv.n, G->lev[1].y, c.wglobal, c.nwarps,
-               [&](int i, amg_t t) { out[i] = double(__ldcg(z + i) + t); });
+               [&](int i, T t) { out[i] = double(__ldcg(z + i) + t); });
     } else {
-      amg_t *res = Lv.y;
+      T *res = Lv.y;
       csr_rows(Lv.P, Lv.n, G->lev[l + 1].y, c.wglobal, c.nwarps,
-               [&](int i, amg_t t) { res[i] = __ldcg(z + i) + t; });
+               [&](int i, T t) { res[i] = __ldcg(z + i) + t; });
     }
     if (!sync(c, epoch)) return false;
   }

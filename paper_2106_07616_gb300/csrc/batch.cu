@@ -161,8 +161,9 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
   if (m <= 0) return RBFFD_OK;
   rbffd_ctx *ctx = P[0]->ctx;
   for (int i = 0; i < m; ++i) {
-    if (P[i]->ctx != ctx || P[i]->precision != RBFFD_PREC_FP64) {
-      set_error("batch: members must share one context and use RBFFD_PREC_FP64");
+    if (P[i]->ctx != ctx || P[i]->precision != RBFFD_PREC_FP64 || P[i]->amgf) {
+      set_error("batch: members must share one context, use RBFFD_PREC_FP64 and a Jacobi or "
+                "BiCGSTAB multigrid p' preconditioner");
       return RBFFD_EINVAL;
     }
   }
@@ -321,8 +322,10 @@ extern "C" int rbffd_batch_create(rbffd_ctx *ctx, int32_t count, rbffd_problem *
   if (!ctx || !out || count < 1 || !members) return RBFFD_EINVAL;
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
-    if (!members[i] || members[i]->ctx != ctx || members[i]->precision != RBFFD_PREC_FP64) {
-      set_error("rbffd_batch_create: member %d is null, on another context or not FP64", i);
+    if (!members[i] || members[i]->ctx != ctx || members[i]->precision != RBFFD_PREC_FP64 ||
+        members[i]->amgf) {
+      set_error("rbffd_batch_create: member %d is null, on another context, not FP64 or on "
+                "flexible GMRES", i);
       return RBFFD_EINVAL;
     }
   }

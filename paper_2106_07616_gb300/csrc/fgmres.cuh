@@ -1,0 +1,35 @@
+// fgmres.cuh -- interface of the persistent flexible GMRES solver of the
+// pressure-correction system with an FP32 multigrid V-cycle preconditioner.
+#pragma once
+#include "amg.cuh"
+#include "common.cuh"
+#include "krylov.cuh"
+
+namespace rbffd {
+
+constexpr int FG_MAXM = 30;  // largest restart length
+
+struct FgmresArgs {
+  int n, q, ldn, tpr;   // rows, ELL width, leading dimension, threads per row
+  int m;                // restart length, 1..FG_MAXM
+  const int32_t *col;   // ELL [q][ldn]
+  const double *val;    // ELL [q][ldn]
+  const double *b;
+  double *x;            // initial guess in, solution out
+  double *V;            // (m + 1) x n Arnoldi basis
+  double *Z;            // m x n preconditioned directions
+  double *part;         // fgmres_partials_doubles(nblocks)
+  GridBarrier *bar;     // err word (bounded waits that gave up)
+  unsigned int *flags;  // one publish flag per block, zeroed per launch
+  KrylovOut *out;       // iters, restarts, status (KRY_*), relres (true residual)
+  double tol;           // relative residual to reach
+  int maxit;            // cap on Arnoldi steps over all restarts
+  const AmgDevF *amg;   // the FP32 hierarchy
+};
+
+size_t fgmres_partials_doubles(int nblocks);
+int fgmres_max_blocks(rbffd_ctx *ctx);
+// rows per block fixed by nblocks; threads per row chosen inside
+int fgmres_launch(rbffd_ctx *ctx, int nblocks, const FgmresArgs &args);
+
+}  // namespace rbffd

@@ -76,7 +76,8 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
   auto P = [&](int slot, int k) { return part + (size_t)(slot * NR + k) * nb; };
   const bool leader = threadIdx.x == 0;
   int *err = &A.bar->err;
-  amgdev::Ctx actx{&A, lb, nb, tid, stride, wglobal, nwarps, stot};
+  amgdev::Ctx actx{n,  q,  ldn,    T,      A.col,   A.flags, &A.bar->err,
+                   lb, nb, tid, stride, wglobal, nwarps, stot};
   (void)actx;
 
   if (leader) {

@@ -1,5 +1,6 @@
 // krylov.cuh -- internal interface of the persistent BiCGSTAB solver.
 #pragma once
+#include "amg.cuh"
 #include "common.cuh"
 
 namespace rbffd {
@@ -34,7 +35,7 @@ struct KrylovArgs {
   int maxit;
   int tpr;              // threads per row in the SpMV phases (1..8)
   int nblocks;          // CTAs that share the solve (batched launches)
-  const struct AmgDev *amg;  // multigrid preconditioner (one RHS), or null: Jacobi
+  const AmgDev *amg;    // multigrid preconditioner (one RHS), or null: Jacobi
 };
 
 constexpr int KB_NT = 256;  // threads per CTA of batched Krylov launches

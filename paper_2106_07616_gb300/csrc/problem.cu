@@ -4,6 +4,7 @@
 #include <cstring>
 #include <vector>
 
+#include "fgmres.cuh"
 #include "ops.cuh"
 #include "problem.cuh"
 #include "weights.cuh"
@@ -63,11 +64,12 @@ int check_desc(const rbffd_problem_desc *d) {
     set_error("problem desc: periods must be >= 0 and forces finite");
     return RBFFD_EINVAL;
   }
-  if (d->precond != RBFFD_PRECOND_JACOBI && d->precond != RBFFD_PRECOND_AMG) {
+  if (d->precond != RBFFD_PRECOND_JACOBI && d->precond != RBFFD_PRECOND_AMG &&
+      d->precond != RBFFD_PRECOND_AMG_FGMRES) {
     set_error("problem desc: unknown preconditioner %d", d->precond);
     return RBFFD_EINVAL;
   }
-  if (d->precond == RBFFD_PRECOND_AMG && d->precision != RBFFD_PREC_FP64) {
+  if (d->precond != RBFFD_PRECOND_JACOBI && d->precision != RBFFD_PREC_FP64) {
     set_error("problem desc: the multigrid preconditioner needs RBFFD_PREC_FP64");
     return RBFFD_ENOTIMPL;
   }
@@ -76,6 +78,12 @@ int check_desc(const rbffd_problem_desc *d) {
 
 void free_amg(rbffd_problem *P) {
   if (P->amg_mem) dev_free(P->ctx, P->amg_mem, P->amg_bytes);
+  if (P->fg_mem) dev_free(P->ctx, P->fg_mem, P->fg_bytes);
+  P->fg_mem = nullptr;
+  P->fg_bytes = 0;
+  P->fgV = P->fgZ = P->fgpart = nullptr;
+  P->amgf = nullptr;
+  memset(&P->amgf_host, 0, sizeof(P->amgf_host));
   P->amg_mem = nullptr;
   P->amg_bytes = 0;
   P->amg = nullptr;
@@ -153,6 +161,19 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
   if (P->precond == RBFFD_PRECOND_AMG) {
     RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, &P->amg_mem, &P->amg_bytes,
                         &P->amg, &P->amg_host, &P->amg_info));
+  } else if (P->precond == RBFFD_PRECOND_AMG_FGMRES) {
+    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, &P->amg_mem, &P->amg_bytes,
+                        &P->amgf, &P->amgf_host, &P->amg_info));
+    // Arnoldi basis (m + 1 vectors), directions (m) and partial sums
+    P->fg_m = FG_MAXM;
+    P->fg_blocks = fgmres_max_blocks(ctx);
+    if (P->fg_blocks > P->kblocks1) P->fg_blocks = P->kblocks1;
+    const size_t nv = (size_t)(2 * P->fg_m + 1) * P->n;
+    P->fg_bytes = sizeof(double) * (nv + fgmres_partials_doubles(P->fg_blocks));
+    RBFFD_TRY(dev_alloc(ctx, &P->fg_mem, P->fg_bytes));
+    P->fgV = (double *)P->fg_mem;
+    P->fgZ = P->fgV + (size_t)(P->fg_m + 1) * P->n;
+    P->fgpart = P->fgZ + (size_t)P->fg_m * P->n;
   }
   if (P->precision != RBFFD_PREC_FP64) {
     RBFFD_TRY(ops_to_inner(P, P->Pp, P->Pin, (int64_t)P->ldn * P->q));
@@ -316,7 +337,31 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   a.out = P->kout + 2;
   a.tpr = krylov_threads_per_row(P->n, 1, P->kblocks1);
   prof_begin(ctx, 1);
-  RBFFD_TRY(krylov_launch(ctx, 1, P->kblocks1, a));
+  if (P->amgf) {
+    FgmresArgs f;
+    memset(&f, 0, sizeof(f));
+    f.n = P->n;
+    f.q = P->q;
+    f.ldn = P->ldn;
+    f.tpr = krylov_threads_per_row(P->n, 1, P->fg_blocks);
+    f.m = P->fg_m;
+    f.col = P->col;
+    f.val = P->Pp;
+    f.b = P->bp;
+    f.x = P->pc;
+    f.V = P->fgV;
+    f.Z = P->fgZ;
+    f.part = P->fgpart;
+    f.bar = P->bar;
+    f.flags = P->flags;
+    f.out = P->kout + 2;
+    f.tol = sp->krylov_tol;
+    f.maxit = sp->krylov_maxit;
+    f.amg = P->amgf;
+    RBFFD_TRY(fgmres_launch(ctx, P->fg_blocks, f));
+  } else {
+    RBFFD_TRY(krylov_launch(ctx, 1, P->kblocks1, a));
+  }
   prof_end(ctx, 1);
   RBFFD_TRY(ops_pressure(P, sp));
   RBFFD_TRY(ops_correct(P, sp));
@@ -528,7 +573,7 @@ extern "C" void rbffd_problem_destroy(rbffd_problem *P) {
 }
 
 extern "C" size_t rbffd_problem_bytes(const rbffd_problem *P) {
-  return P ? P->bytes + P->amg_bytes : 0;
+  return P ? P->bytes + P->amg_bytes + P->fg_bytes : 0;
 }
 
 static void report_levels(const AmgInfo &I, bool have_any, int32_t *levels, int32_t *rows,
@@ -545,7 +590,8 @@ static void report_levels(const AmgInfo &I, bool have_any, int32_t *levels, int3
 extern "C" int rbffd_problem_amg_info(const rbffd_problem *P, int32_t *levels, int32_t *rows,
                                       int64_t *nnz, double *setup_ms) {
   if (!P) return RBFFD_EINVAL;
-  report_levels(P->amg_info, P->amg != nullptr, levels, rows, nnz, setup_ms);
+  report_levels(P->amg_info, P->amg != nullptr || P->amgf != nullptr, levels, rows, nnz,
+                setup_ms);
   return RBFFD_OK;
 }
 
@@ -671,17 +717,25 @@ namespace rbffd {
 // and vectors (and the dense coarsest inverse).
 double pcorr_bytes(const rbffd_problem *P, int iters) {
   const double n = P->n, q = P->q, it = iters;
-  if (!P->amg) return n * it * (2 * q * 12 + 14 * 8);
-  // per V-cycle (FP32 operators and level vectors, FP64 in and out): S_0 b_0
-  // (ELL, q (4 + 4) + b_0 read + z written), R~_l, P~_l and S_l (l >= 1)
-  // entries at 8 B, their vectors, the dense coarsest inverse
+  if (!P->amg && !P->amgf) return n * it * (2 * q * 12 + 14 * 8);
+  // per V-cycle (operators and level vectors in the cycle's type, FP64 in
+  // and out): S_0 b_0 (ELL, q (s + 4) + b_0 read + z written), R~_l, P~_l
+  // and S_l (l >= 1) entries at s + 4 B, their vectors, the dense inverse
   const AmgInfo &I = P->amg_info;
-  const double e = sizeof(amg_t) + 4.0, v = sizeof(amg_t);
+  const double s = P->amgf ? 4.0 : 8.0;
+  const double e = s + 4.0, v = s;
   double cyc = n * (q * e + 8 + v) + n * (v + 8);  // S_0, then P~_0's z read and out write
   for (int l = 0; l < I.nlev; ++l) {
     if (l + 1 < I.nlev) cyc += e * (I.nnz_r[l] + I.nnz_p[l]);
     if (l >= 1 && l + 1 < I.nlev) cyc += e * I.nnz[l] + 5.0 * v * I.n[l];
     if (l + 1 == I.nlev) cyc += v * I.n[l] * I.n[l];
+  }
+  if (P->amgf) {
+    // one SpMV and one cycle per Arnoldi step, classical Gram-Schmidt with
+    // one reorthogonalisation over on average min(it, m) / 2 + 1 basis
+    // vectors (two dot passes and two update passes), normalisation
+    const double jv = (it < P->fg_m ? it : P->fg_m) / 2.0 + 1.0;
+    return n * it * (q * 12 + 16 + 8.0 * (4 * jv + 4)) + it * cyc;
   }
   return n * it * (2 * q * 12 + 14 * 8) + 2.0 * it * cyc;
 }

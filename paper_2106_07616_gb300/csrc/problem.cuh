@@ -68,6 +68,14 @@ struct rbffd_problem {
   const rbffd::AmgDev *amg = nullptr;  // device copy of the level table
   rbffd::AmgDev amg_host{};             // host copy (device pointers)
   rbffd::AmgInfo amg_info{};
+  // flexible GMRES with an FP32 hierarchy (RBFFD_PRECOND_AMG_FGMRES): the
+  // FP32 level table and the basis / direction vectors and partials
+  const rbffd::AmgDevF *amgf = nullptr;
+  rbffd::AmgDevF amgf_host{};
+  void *fg_mem = nullptr;
+  size_t fg_bytes = 0;
+  double *fgV = nullptr, *fgZ = nullptr, *fgpart = nullptr;
+  int fg_m = 0, fg_blocks = 0;
 };
 
 namespace rbffd {

@@ -24,7 +24,7 @@ TAG_INTERIOR, TAG_DIRICHLET, TAG_OUTFLOW, TAG_SYMMETRY = 0, 1, 2, 3
 FIELDS = {"u": 0, "v": 1, "p": 2, "un": 3, "vn": 4, "unm1": 5, "vnm1": 6, "ut": 7, "vt": 8,
           "pc": 9, "ubc": 10, "vbc": 11}
 PREC_FP64, PREC_MIXED, PREC_MIXED_FF = 0, 1, 2
-PRECOND_JACOBI, PRECOND_AMG = 0, 1
+PRECOND_JACOBI, PRECOND_AMG, PRECOND_AMG_FGMRES = 0, 1, 2
 AMG_MAX_LEVELS = 10
 
 

@@ -18,10 +18,13 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("pc", [rbffd.PRECOND_AMG, rbffd.PRECOND_AMG_FGMRES])
 @pytest.mark.parametrize("case", list(CASES))
-def test_amg_outer_iterations_match_oracle(case):
+def test_amg_outer_iterations_match_oracle(case, pc):
+    """BiCGSTAB with an FP64 cycle and flexible GMRES with an FP32 cycle both
+    stop on the FP64 relative residual and give the oracle's iterates."""
     fp = CASES[case]()
-    P = rbffd.Problem(ctx(), fp, precond=rbffd.PRECOND_AMG)
+    P = rbffd.Problem(ctx(), fp, precond=pc)
     J = rbffd.Problem(ctx(), fp)
     O = oracle.Problem(fp, krylov_tol=1e-12)
     for X in (P, J, O):
@@ -34,7 +37,8 @@ def test_amg_outer_iterations_match_oracle(case):
         dj, sj = J.simple_iterate(fp.dt, krylov_tol=1e-12)
         do, _ = O.simple_iterate(fp.dt)
         assert sg["relres"][2] <= 1e-12
-        assert sg["iters"][2] * 2 < sj["iters"][2], (sg["iters"], sj["iters"])
+        assert sg["iters"][2] * (2 if pc == rbffd.PRECOND_AMG else 4) < sj["iters"][2], (
+            sg["iters"], sj["iters"])
         assert abs(dg - do) <= 1e-8 * abs(do), (r, dg, do)
         vel = lambda X: np.concatenate([X.get("u"), X.get("v")])
         assert rel_l2(vel(P), vel(O)) <= 1e-8
@@ -90,3 +94,28 @@ def test_batch_with_amg_members_matches_alone():
             e = rel_l2(B.problems[i].get(k), alone[i].get(k))
             assert e <= 1e-8, (i, k, e)
     B.close()
+
+
+def test_fgmres_on_full_cavity_matches_jacobi_path():
+    """200 x 200 cavity: flexible GMRES with the FP32 cycle reaches the FP64
+    tolerance in a small fraction of the Jacobi iterations and lands on the
+    same outer iterate."""
+    fp = clouds.cavity(200)
+    A = rbffd.Problem(ctx(), fp)
+    B = rbffd.Problem(ctx(), fp, precond=rbffd.PRECOND_AMG_FGMRES)
+    for _ in range(2):
+        da, sa = A.simple_iterate(fp.dt, krylov_tol=1e-12, krylov_maxit=100000)
+        db, sb = B.simple_iterate(fp.dt, krylov_tol=1e-12, krylov_maxit=100000)
+        assert sb["relres"][2] <= 1e-12
+        assert sb["iters"][2] * 20 < sa["iters"][2], (sb["iters"], sa["iters"])
+        assert abs(da - db) <= 1e-8 * abs(da)
+    for k in ("u", "v", "p"):
+        assert rel_l2(B.get(k), A.get(k)) <= 1e-8, k
+
+
+def test_fgmres_members_rejected_by_batches():
+    fp = clouds.kovasznay(30, dt=0.4)
+    P = rbffd.Problem(ctx(), fp, precond=rbffd.PRECOND_AMG_FGMRES)
+    with pytest.raises(rbffd.RbffdError) as e:
+        rbffd.Batch(ctx(), [P])
+    assert e.value.code == rbffd.EINVAL
