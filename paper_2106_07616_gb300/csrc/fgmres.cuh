@@ -20,7 +20,7 @@ struct FgmresArgs {
   double *Z;            // m x n preconditioned directions
   double *part;         // fgmres_partials_doubles(nblocks)
   GridBarrier *bar;     // err word (bounded waits that gave up)
-  unsigned int *flags;  // one publish flag per block, zeroed per launch
+  unsigned int *flags;  // word 0: the arrival counter, zeroed per launch
   KrylovOut *out;       // iters, restarts, status (KRY_*), relres (true residual)
   double tol;           // relative residual to reach
   int maxit;            // cap on Arnoldi steps over all restarts

@@ -29,7 +29,7 @@ struct KrylovArgs {
   KrylovVecs w[2];
   double *part;         // krylov_partials_doubles(nr, nblocks)
   GridBarrier *bar;     // err word (bounded waits that gave up)
-  unsigned int *flags;  // one publish flag per block, zeroed per launch
+  unsigned int *flags;  // word 0: the arrival counter, zeroed per launch
   KrylovOut *out;       // nr entries
   double tol;
   int maxit;

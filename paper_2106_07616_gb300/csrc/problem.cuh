@@ -49,7 +49,7 @@ struct rbffd_problem {
   double *part;       // Krylov partials
   double *rpart;      // partials of the outer-loop reductions
   rbffd::GridBarrier *bar;
-  unsigned int *flags;     // Krylov publish flags (one per block)
+  unsigned int *flags;     // Krylov arrival counter (word 0)
   rbffd::KrylovOut *kout;  // [0..1] momentum, [2] pressure correction
   IterRecord *rec;         // device copy of the iteration record
   int *d_first_singular;
