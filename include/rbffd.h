@@ -403,6 +403,14 @@ void rbffd_batch_destroy(rbffd_batch *batch);
 int rbffd_batch_iterate(rbffd_batch *batch, const rbffd_step_params *params, const double *dt,
                         const int32_t *active, double *deltas, rbffd_iter_stats *stats,
                         int32_t *status);
+/* The batched outer iteration is captured as a CUDA graph the first time it
+ * runs for a set of active members, their builds and step parameters, and
+ * replayed while those stay the same (live kernel timing, rbffd_ctx_profile,
+ * launches it directly).  captures / replays / kernels (nullable host
+ * outputs): graphs captured and replayed so far, and the kernels one replay
+ * launches (0 when capture is off).  Errors: RBFFD_EINVAL (null batch). */
+int rbffd_batch_graph_stats(const rbffd_batch *batch, int64_t *captures, int64_t *replays,
+                            int64_t *kernels);
 
 /* -------------------------------------------------------------- serving */
 

@@ -19,12 +19,14 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
 
 #include "amg.cuh"
+#include "krylov_dev.cuh"
 
 namespace rbffd {
 
@@ -131,22 +133,53 @@ Csr build_rows(int n, int m, RowFn &&row) {
   return C;
 }
 
+// A^T with the rows of each column in increasing order.  Threads take
+// contiguous row ranges in order, count their columns, and place their
+// entries after those of the ranges before them: the same result as one
+// pass over the rows.
 Csr transpose(const Csr &A) {
   Csr T;
   T.n = A.m;
   T.m = A.n;
   T.ptr.assign(A.m + 1, 0);
-  for (int32_t c : A.col) T.ptr[c + 1]++;
-  for (int i = 0; i < A.m; ++i) T.ptr[i + 1] += T.ptr[i];
   T.col.resize(A.col.size());
   T.val.resize(A.val.size());
-  std::vector<int32_t> fill(T.ptr.begin(), T.ptr.end() - 1);
-  for (int i = 0; i < A.n; ++i)
-    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
-      const int f = fill[A.col[k]]++;
-      T.col[f] = i;
-      T.val[f] = A.val[k];
+  const int nt = A.nnz() < (1 << 16) ? 1 : std::max(1, omp_get_max_threads());
+  const size_t m1 = (size_t)A.m + 1;
+  std::vector<int32_t> at((size_t)nt * m1, 0);  // per range: count, then start, per column
+  auto range = [&](int t, int &lo, int &hi) {
+    lo = (int)((long long)A.n * t / nt);
+    hi = (int)((long long)A.n * (t + 1) / nt);
+  };
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+  for (int t = 0; t < nt; ++t) {
+    int lo, hi;
+    range(t, lo, hi);
+    int32_t *cnt = at.data() + (size_t)t * m1;
+    for (int k = A.ptr[lo]; k < A.ptr[hi]; ++k) cnt[A.col[k]]++;
+  }
+  for (int c = 0; c < A.m; ++c) {
+    int32_t s = T.ptr[c];
+    for (int t = 0; t < nt; ++t) {
+      int32_t &x = at[(size_t)t * m1 + c];
+      const int32_t k = x;
+      x = s;
+      s += k;
     }
+    T.ptr[c + 1] = s;
+  }
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+  for (int t = 0; t < nt; ++t) {
+    int lo, hi;
+    range(t, lo, hi);
+    int32_t *fill = at.data() + (size_t)t * m1;
+    for (int i = lo; i < hi; ++i)
+      for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+        const int f = fill[A.col[k]]++;
+        T.col[f] = i;
+        T.val[f] = A.val[k];
+      }
+  }
   return T;
 }
 
@@ -220,12 +253,12 @@ void strength(const Csr &A, double theta, std::vector<int32_t> &sp, std::vector<
       if (st[k]) S1.col[w++] = A.col[k];
   }
   const Csr S1T = transpose(S1);
-  const Csr U = build_rows(n, n, [&](int i, std::vector<int32_t> &, auto &&emit) {
+  Csr U = build_rows(n, n, [&](int i, std::vector<int32_t> &, auto &&emit) {
     for (int k = S1.ptr[i]; k < S1.ptr[i + 1]; ++k) emit(S1.col[k], 1.0);
     for (int k = S1T.ptr[i]; k < S1T.ptr[i + 1]; ++k) emit(S1T.col[k], 1.0);
   });
-  sp = U.ptr;
-  sc = U.col;
+  sp = std::move(U.ptr);
+  sc = std::move(U.col);
 }
 
 // greedy aggregation; returns the number of aggregates
@@ -391,12 +424,73 @@ Csr smoother_matrix(const Csr &A, const std::vector<double> &w) {
   return S;
 }
 
-// lanes per row for a CSR matrix: about 4 entries per lane, 1..32
-int lanes_for(const Csr &A) {
-  const double avg = A.n > 0 ? (double)A.nnz() / A.n : 0.0;
-  int g = 1;
-  while (g < 32 && g * 4 < avg) g *= 2;
-  return g;
+// ---- how the cycle spreads an operator's rows over the launch's warps
+// A phase of the cycle costs the dependent L2 round trips of its slowest
+// warp.  A CSR row with g lanes costs one trip for its row pointers and two
+// (indices and values, then the gathers) per AMG_CSR_CHUNK entries a lane;
+// an ELL row with T threads two per kdev::CH entries a thread; a warp that
+// takes more than one pass over its rows pays each pass.  The down phase
+// runs S_l and R~_l side by side (R~_l dealt from the last warp), so their
+// lanes per row are chosen together: side by side when their warps fit in
+// the launch, one after the other otherwise.
+struct Shape {
+  int rows = 0, maxlen = 0;
+};
+Shape shape(const Csr &M) {
+  Shape s;
+  s.rows = M.n;
+  for (int i = 0; i < M.n; ++i) s.maxlen = std::max(s.maxlen, M.ptr[i + 1] - M.ptr[i]);
+  return s;
+}
+long long csr_warps(const Shape &s, int g) { return (s.rows + 32 / g - 1) / (32 / g); }
+int csr_trips(const Shape &s, int g, long long warps) {
+  const long long per_pass = warps * (32 / g);
+  const int passes = (int)((s.rows + per_pass - 1) / per_pass);
+  const int chunks = std::max(1, (s.maxlen + g * AMG_CSR_CHUNK - 1) / (g * AMG_CSR_CHUNK));
+  return passes * (1 + 2 * chunks);
+}
+long long ell_warps(int n, int T) { return (n + 32 / T - 1) / (32 / T); }
+int ell_trips(int n, int q, int T, long long warps) {
+  const long long per_pass = warps * (32 / T);
+  const int passes = (int)((n + per_pass - 1) / per_pass);
+  const int chunks = std::max(1, (q + T * kdev::CH - 1) / (T * kdev::CH));
+  return passes * 2 * chunks;
+}
+int pair_trips(int ta, long long wa, int tb, long long wb, long long warps) {
+  return wa + wb <= warps ? std::max(ta, tb) : ta + tb;
+}
+// lanes per row of one CSR operator run alone
+int lanes_alone(const Shape &s, long long warps) {
+  int best = 1, bt = 1 << 30;
+  for (int g = 1; g <= 32; g *= 2) {
+    const int t = csr_trips(s, g, warps);
+    if (t < bt) bt = t, best = g;
+  }
+  return best;
+}
+// lanes per row of S_l and R~_l run side by side
+void lanes_pair(const Shape &a, const Shape &b, long long warps, int &ga, int &gb) {
+  int bt = 1 << 30;
+  long long bw = 0;
+  for (int x = 1; x <= 32; x *= 2)
+    for (int y = 1; y <= 32; y *= 2) {
+      const long long w = csr_warps(a, x) + csr_warps(b, y);
+      const int t = pair_trips(csr_trips(a, x, warps), csr_warps(a, x), csr_trips(b, y, warps),
+                               csr_warps(b, y), warps);
+      if (t < bt || (t == bt && w < bw)) bt = t, bw = w, ga = x, gb = y;
+    }
+}
+// threads per row of level 0's S (ELL, q wide) and lanes of R~_0
+void lanes_level0(int n, int q, const Shape &r, long long warps, int &ts, int &gr) {
+  int bt = 1 << 30;
+  long long bw = 0;
+  for (int T = 1; T <= 8; ++T)
+    for (int y = 1; y <= 32; y *= 2) {
+      const long long w = ell_warps(n, T) + csr_warps(r, y);
+      const int t = pair_trips(ell_trips(n, q, T, warps), ell_warps(n, T), csr_trips(r, y, warps),
+                               csr_warps(r, y), warps);
+      if (t < bt || (t == bt && w < bw)) bt = t, bw = w, ts = T, gr = y;
+    }
 }
 
 // inverse of a small CSR matrix by Gauss-Jordan with partial pivoting
@@ -501,25 +595,41 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// One host buffer for the whole upload, packed in two passes over the same
+// sequence of take / put calls: the first (buf null) only measures, the
+// second fills one allocation of that size.  Regions that are only taken
+// (level vectors, alignment gaps) are left as they are: the cycle writes
+// its vectors before it reads them.
 struct Staging {
-  std::vector<char> buf;
+  size_t size = 0;
+  char *buf = nullptr;
+  std::unique_ptr<char[]> own;
+  void fill_pass() {
+    own.reset(new char[size]);
+    buf = own.get();
+    size = 0;
+  }
   size_t take(size_t bytes) {
-    size_t at = buf.size();
-    buf.resize(at + (bytes + 255) / 256 * 256, 0);
+    const size_t at = size;
+    size += (bytes + 255) / 256 * 256;
     return at;
   }
   template <typename T>
   size_t put(const std::vector<T> &v) {
-    size_t at = take(v.size() * sizeof(T));
-    if (!v.empty()) memcpy(buf.data() + at, v.data(), v.size() * sizeof(T));
+    const size_t at = take(v.size() * sizeof(T));
+    if (buf && !v.empty()) memcpy(buf + at, v.data(), v.size() * sizeof(T));
     return at;
   }
   // FP64 values stored in the cycle's arithmetic T (round to nearest)
   template <typename T>
   size_t put_as(const std::vector<double> &v) {
-    size_t at = take(v.size() * sizeof(T));
-    T *d = reinterpret_cast<T *>(buf.data() + at);
-    for (size_t k = 0; k < v.size(); ++k) d[k] = (T)v[k];
+    const size_t at = take(v.size() * sizeof(T));
+    if (buf) {
+      T *d = reinterpret_cast<T *>(buf + at);
+      const long long m = (long long)v.size();
+#pragma omp parallel for schedule(static)
+      for (long long k = 0; k < m; ++k) d[k] = (T)v[k];
+    }
     return at;
   }
 };
@@ -542,8 +652,8 @@ int amg_analyze(int n, const int32_t *rowptr, const int32_t *col, const double *
 
 template <typename T>
 int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
-              void **mem, size_t *bytes, const AmgDevT<T> **dev, AmgDevT<T> *host_view,
-              AmgInfo *info) {
+              int nwarps, void **mem, size_t *bytes, const AmgDevT<T> **dev,
+              AmgDevT<T> *host_view, AmgInfo *info) {
   *mem = nullptr;
   *bytes = 0;
   *dev = nullptr;
@@ -562,6 +672,7 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
   std::vector<double> s0((size_t)q * ldn, 0.0);
   {
     const std::vector<double> &w = H.W[0];
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
       bool diag = false;
       for (int j = 0; j < q; ++j) {
@@ -579,38 +690,58 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
 
   // ---- pack everything into one staging buffer, then one upload
   Staging S;
-  const size_t o_dev = S.take(sizeof(AmgDevT<T>));
   struct CsrOff {
     size_t ptr = 0, col = 0, val = 0;
     int grp = 1;
   };
-  auto put_csr = [&](const Csr &M) {
+  auto put_csr = [&](const Csr &M, int grp) {
     CsrOff o;
     o.ptr = S.put(M.ptr);
     o.col = S.put(M.col);
     o.val = S.put_as<T>(M.val);
-    o.grp = lanes_for(M);
+    o.grp = grp;
     return o;
   };
+  // lanes per row for the launch's warps (see Shape)
+  const long long W = nwarps > 0 ? nwarps : 4096;
+  std::vector<int> gS(L, 1), gR(L, 1), gP(L, 1);
+  int ts0 = 1;
+  for (int l = 0; l + 1 < L; ++l) {
+    const Shape r = shape(H.R[l]);
+    if (l == 0)
+      lanes_level0(n, q, r, W, ts0, gR[0]);
+    else
+      lanes_pair(shape(H.S[l]), r, W, gS[l], gR[l]);
+    gP[l] = lanes_alone(shape(H.P[l]), W);
+  }
   struct Off {
     CsrOff S, R, P;
     size_t b = 0, z = 0, y = 0;
   };
   std::vector<Off> off(L);
-  const size_t o_s0 = S.put_as<T>(s0);
-  for (int l = 0; l < L; ++l) {
-    if (l > 0) off[l].S = put_csr(H.S[l]);
-    if (l + 1 < L) {
-      off[l].R = put_csr(H.R[l]);
-      off[l].P = put_csr(H.P[l]);
+  // an FP32 cycle's solve (flexible GMRES) runs its inner SpMVs on level
+  // 0's matrix in FP32 too: a rounded copy of the ELL values
+  const bool low = sizeof(T) < sizeof(double);
+  size_t o_dev = 0, o_s0 = 0, o_a0 = 0, o_cinv = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) S.fill_pass();
+    o_dev = S.take(sizeof(AmgDevT<T>));
+    o_s0 = S.put_as<T>(s0);
+    o_a0 = low ? S.put_as<T>(hval) : 0;
+    for (int l = 0; l < L; ++l) {
+      if (l > 0) off[l].S = put_csr(H.S[l], l + 1 < L ? gS[l] : 1);
+      if (l + 1 < L) {
+        off[l].R = put_csr(H.R[l], gR[l]);
+        off[l].P = put_csr(H.P[l], gP[l]);
+      }
+      if (l > 0) off[l].b = S.take(sizeof(T) * H.A[l].n);
+      off[l].z = S.take(sizeof(T) * H.A[l].n);
+      off[l].y = S.take(sizeof(T) * H.A[l].n);
     }
-    if (l > 0) off[l].b = S.take(sizeof(T) * H.A[l].n);
-    off[l].z = S.take(sizeof(T) * H.A[l].n);
-    off[l].y = S.take(sizeof(T) * H.A[l].n);
+    o_cinv = S.put_as<T>(H.cinv);
   }
-  const size_t o_cinv = S.put_as<T>(H.cinv);
   void *dmem = nullptr;
-  RBFFD_TRY(dev_alloc(ctx, &dmem, S.buf.size()));
+  RBFFD_TRY(dev_alloc(ctx, &dmem, S.size));
   char *base = (char *)dmem;
   auto csr_at = [&](const CsrOff &o, bool have) {
     AmgCsrT<T> c;
@@ -625,6 +756,8 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
   h.nlev = L;
   h.cinv = (const T *)(base + o_cinv);
   h.s0 = (const T *)(base + o_s0);
+  h.ts0 = ts0;
+  h.a0 = low ? (const T *)(base + o_a0) : nullptr;
   for (int l = 0; l < L; ++l) {
     AmgLevelT<T> &v = h.lev[l];
     v.n = H.A[l].n;
@@ -635,26 +768,26 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
     v.z = (T *)(base + off[l].z);
     v.y = (T *)(base + off[l].y);
   }
-  memcpy(S.buf.data() + o_dev, &h, sizeof(h));
-  if (cudaMemcpyAsync(dmem, S.buf.data(), S.buf.size(), cudaMemcpyHostToDevice, ctx->stream) !=
+  memcpy(S.buf + o_dev, &h, sizeof(h));
+  if (cudaMemcpyAsync(dmem, S.buf, S.size, cudaMemcpyHostToDevice, ctx->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-    dev_free(ctx, dmem, S.buf.size());
+    dev_free(ctx, dmem, S.size);
     set_error("amg: upload failed");
     return RBFFD_ECUDA;
   }
   *mem = dmem;
-  *bytes = S.buf.size();
+  *bytes = S.size;
   *dev = (const AmgDevT<T> *)(base + o_dev);
   if (host_view) *host_view = h;
   fill_info(H, ms_since(t0), info);
   return RBFFD_OK;
 }
 
-template int amg_build<double>(rbffd_ctx *, int, int, int, const int32_t *, const double *,
+template int amg_build<double>(rbffd_ctx *, int, int, int, const int32_t *, const double *, int,
                                void **, size_t *, const AmgDevT<double> **, AmgDevT<double> *,
                                AmgInfo *);
-template int amg_build<float>(rbffd_ctx *, int, int, int, const int32_t *, const double *,
+template int amg_build<float>(rbffd_ctx *, int, int, int, const int32_t *, const double *, int,
                               void **, size_t *, const AmgDevT<float> **, AmgDevT<float> *,
                               AmgInfo *);
 

@@ -10,9 +10,11 @@
 namespace rbffd {
 
 constexpr int AMG_MAXLEV = 10;
+constexpr int AMG_CSR_CHUNK = 8;  // entries a lane loads before its gathers (CSR rows)
 
 // Arithmetic of the V-cycle (operators, dense inverse, level vectors): a
-// type parameter T.  Inside BiCGSTAB the cycle is FP64: an FP32 cycle's
+// type parameter T; the vectors it reads and writes on level 0 may be FP64
+// or T.  Inside BiCGSTAB the cycle is FP64: an FP32 cycle's
 // rounding (~1e-7 relative on every application, different for every
 // input) breaks BiCGSTAB's short recurrences, which assume one fixed linear
 // preconditioner -- measured on the 200 x 200 cavity p' system: 1996
@@ -52,6 +54,8 @@ struct AmgDevT {
   int nlev;         // levels including the coarsest
   const T *cinv;    // inverse of the coarsest matrix, row-major nc x nc
   const T *s0;      // level 0's S, ELL [q][ldn] on the solve's column array
+  int ts0;          // threads per row of level 0's S in the cycle (1..8)
+  const T *a0;      // level 0's A rounded to T, same layout (FP32 only, else null)
   AmgLevelT<T> lev[AMG_MAXLEV];
 };
 
@@ -73,14 +77,16 @@ struct AmgInfo {
 
 // Build the hierarchy of the packed p' matrix (ELL, column-major [q][ldn],
 // device) on the host and upload it into one device allocation (*mem,
-// *bytes; freed with dev_free).  *dev receives the device copy of the
+// *bytes; freed with dev_free).  nwarps: the warps of the launch that will
+// run the cycle (lanes per row are chosen for it; any launch runs it
+// correctly).  *dev receives the device copy of the
 // level table.  Errors: RBFFD_ESINGULAR if the coarsest matrix is singular,
 // RBFFD_ENOMEM, RBFFD_ECUDA.
 // T = double or float: the stored arithmetic of the cycle.
 template <typename T>
 int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
-              void **mem, size_t *bytes, const AmgDevT<T> **dev, AmgDevT<T> *host_view,
-              AmgInfo *info);
+              int nwarps, void **mem, size_t *bytes, const AmgDevT<T> **dev,
+              AmgDevT<T> *host_view, AmgInfo *info);
 
 // The host part alone, on a CSR matrix (analysis and tests): level sizes
 // and nonzeros in *info.

@@ -10,7 +10,8 @@
 // Level 0's S uses the solve's ELL columns (T threads per row); the CSR
 // operators use grp lanes per row.  The cycle computes in the hierarchy's
 // value type T (FP64 or FP32, see amg.cuh); it reads b_0 and writes its
-// result in FP64.  Vectors written in this launch are read with __ldcg
+// result in the solve's vector types XT and OT (FP64 inside BiCGSTAB, FP32
+// inside flexible GMRES).  Vectors written in this launch are read with __ldcg
 // (coherent L2).  Ctx carries the grid-exchange state; it is independent of
 // the Krylov method around the cycle.
 #pragma once
@@ -26,16 +27,19 @@ namespace amgdev {
 // Each lane loads CC column indices and values of its strided share first,
 // then the CC gathers, so a long row costs two dependent L2 round trips per
 // CC entries a lane, not per entry.
-constexpr int CC = 8;
+constexpr int CC = AMG_CSR_CHUNK;
 
+// zadd (may be null): z(i) is added to the row's sum, loaded with the row
+// pointers instead of after the sum.
 template <typename T, typename XT, typename F>
 __device__ __forceinline__ void csr_rows(const AmgCsrT<T> &M, int nrows, const XT *x, int wglobal,
-                                         int nwarps, F &&f) {
+                                         int nwarps, F &&f, const T *zadd = nullptr) {
   const int lane = threadIdx.x & 31;
   const int G = M.grp, rpw = 32 / G, g = lane / G, lg = lane - g * G;
   for (int base = wglobal * rpw; base < nrows; base += nwarps * rpw) {
     const int i = base + g;
     T t = 0;
+    const T zi = (zadd != nullptr && i < nrows && lg == 0) ? __ldcg(zadd + i) : T(0);
     if (i < nrows) {
       const int s = __ldg(M.ptr + i), e = __ldg(M.ptr + i + 1);
       for (int k0 = s + lg; k0 < e; k0 += CC * G) {
@@ -53,7 +57,7 @@ __device__ __forceinline__ void csr_rows(const AmgCsrT<T> &M, int nrows, const X
       }
     }
     for (int o = G >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (i < nrows && lg == 0) f(i, t);
+    if (i < nrows && lg == 0) f(i, t + zi);
   }
 }
 
@@ -88,29 +92,32 @@ __device__ __forceinline__ void coarse_solve(const AmgDevT<T> *__restrict__ G, i
 }
 
 // out = V-cycle(b0)
-template <typename T>
+template <typename T, typename XT, typename OT>
 __device__ __forceinline__ bool vcycle(const AmgDevT<T> *__restrict__ G, const Ctx &c,
-                                       const double *b0, double *out, unsigned int &epoch) {
+                                       const XT *b0, OT *out, unsigned int &epoch) {
   const int L = G->nlev;
   if (L == 1) {
     coarse_solve(G, G->lev[0].n, b0, out, c);
     return sync(c, epoch);
   }
-  // ---- down
+  // ---- down: the rows of R~_l are dealt from the last warp backwards, so
+  // that they run beside the rows of S_l (dealt from warp 0) instead of
+  // after them whenever the two fit in one pass over the grid's warps
+  const int wrev = c.nwarps - 1 - c.wglobal;
   for (int l = 0; l + 1 < L; ++l) {
     const AmgLevelT<T> &Lv = G->lev[l];
     const AmgLevelT<T> &Nx = G->lev[l + 1];
     T *z = Lv.z;
     T *bn = Nx.b;
     if (l == 0) {
-      const double *xs[1] = {b0};
-      kdev::spmv_rows<1, T>(c.n, c.q, c.ldn, c.tpr, c.col, G->s0, xs, c.wglobal, c.nwarps,
+      const XT *xs[1] = {b0};
+      kdev::spmv_rows<1, T>(c.n, c.q, c.ldn, G->ts0, c.col, G->s0, xs, c.wglobal, c.nwarps,
                             [&](int i, const T *sb) { z[i] = sb[0]; });
-      csr_rows(Lv.R, Nx.n, b0, c.wglobal, c.nwarps, [&](int k, T t) { bn[k] = t; });
+      csr_rows(Lv.R, Nx.n, b0, wrev, c.nwarps, [&](int k, T t) { bn[k] = t; });
     } else {
       const T *bl = Lv.b;
       csr_rows(Lv.S, Lv.n, bl, c.wglobal, c.nwarps, [&](int i, T t) { z[i] = t; });
-      csr_rows(Lv.R, Nx.n, bl, c.wglobal, c.nwarps, [&](int k, T t) { bn[k] = t; });
+      csr_rows(Lv.R, Nx.n, bl, wrev, c.nwarps, [&](int k, T t) { bn[k] = t; });
     }
     if (!sync(c, epoch)) return false;
   }
@@ -125,12 +132,12 @@ __device__ __forceinline__ bool vcycle(const AmgDevT<T> *__restrict__ G, const C
     const AmgLevelT<T> &Lv = G->lev[l];
     const T *z = Lv.z;
     if (l == 0) {
-      csr_rows(Lv.P, Lv.n, G->lev[1].y, c.wglobal, c.nwarps,
-               [&](int i, T t) { out[i] = double(__ldcg(z + i) + t); });
+      csr_rows(
+          Lv.P, Lv.n, G->lev[1].y, c.wglobal, c.nwarps, [&](int i, T t) { out[i] = OT(t); }, z);
     } else {
       T *res = Lv.y;
-      csr_rows(Lv.P, Lv.n, G->lev[l + 1].y, c.wglobal, c.nwarps,
-               [&](int i, T t) { res[i] = __ldcg(z + i) + t; });
+      csr_rows(
+          Lv.P, Lv.n, G->lev[l + 1].y, c.wglobal, c.nwarps, [&](int i, T t) { res[i] = t; }, z);
     }
     if (!sync(c, epoch)) return false;
   }

@@ -53,8 +53,16 @@ int status_of(int s) {
 
 namespace rbffd {
 
+void BatchScratch::drop_graph() {
+  if (exec) cudaGraphExecDestroy(exec);
+  exec = nullptr;
+  key.clear();
+  graph_launches = 0;
+}
+
 BatchScratch::~BatchScratch() {
   if (ctx) {
+    drop_graph();
     dev_free(ctx, dmem, dbytes);
     if (hmem) cudaFreeHost(hmem);
   }
@@ -63,6 +71,7 @@ BatchScratch::~BatchScratch() {
 int BatchScratch::reserve(rbffd_ctx *c, int members) {
   ctx = c;
   if (members <= cap) return RBFFD_OK;
+  drop_graph();  // it refers to the buffers replaced here
   if (dmem) {
     cudaStreamSynchronize(ctx->stream);
     dev_free(ctx, dmem, dbytes);
@@ -74,18 +83,21 @@ int BatchScratch::reserve(rbffd_ctx *c, int members) {
   }
   cap = std::max(members, 16);
   maxc = std::max(krylov_batch_max_ctas(ctx, 1), krylov_batch_max_ctas(ctx, 2));
-  // device: sys args, cta tables, flags, barriers, record pointers, outputs
+  // device: per slot sys args, cta tables, flags, barriers; record
+  // pointers, outputs.  The pinned host copy has the same layout.
   size_t o = 0;
   auto take = [&](size_t b) {
     size_t a = o;
     o += (b + 255) / 256 * 256;
     return a;
   };
-  off_sys = take(sizeof(KrylovArgs) * cap);
-  off_cta_sys = take(sizeof(int) * maxc);
-  off_cta_first = take(sizeof(int) * cap);
-  off_flags = take(sizeof(unsigned int) * maxc);
-  off_bars = take(sizeof(GridBarrier) * cap);
+  for (int k = 0; k < NSLOT; ++k) {
+    off_sys[k] = take(sizeof(KrylovArgs) * cap);
+    off_cta_sys[k] = take(sizeof(int) * maxc);
+    off_cta_first[k] = take(sizeof(int) * cap);
+    off_flags[k] = take(sizeof(unsigned int) * maxc);
+    off_bars[k] = take(sizeof(GridBarrier) * cap);
+  }
   off_recs = take(sizeof(void *) * cap);
   off_kouts = take(sizeof(void *) * cap);
   off_out = take(sizeof(MemberOut) * cap);
@@ -97,8 +109,8 @@ int BatchScratch::reserve(rbffd_ctx *c, int members) {
 }
 
 // One batched Krylov launch for the systems args[0..m) (args filled except
-// nblocks, tpr, flags and bar, which are set here).
-static int launch_krylov(BatchScratch &S, int nr, std::vector<KrylovArgs> &args,
+// nblocks, tpr, flags and bar, which are set here), with table slot `slot`.
+static int launch_krylov(BatchScratch &S, int slot, int nr, std::vector<KrylovArgs> &args,
                          const std::vector<int> &rows, bool amg = false) {
   rbffd_ctx *ctx = S.ctx;
   const int m = (int)args.size();
@@ -121,11 +133,11 @@ static int launch_krylov(BatchScratch &S, int nr, std::vector<KrylovArgs> &args,
   int nctas = std::accumulate(nb.begin(), nb.end(), 0);
   char *hb = (char *)S.hmem;
   char *db = (char *)S.dmem;
-  KrylovArgs *hsys = (KrylovArgs *)(hb + S.off_sys);
-  int *hcs = (int *)(hb + S.off_cta_sys);
-  int *hcf = (int *)(hb + S.off_cta_first);
-  unsigned int *dflags = (unsigned int *)(db + S.off_flags);
-  GridBarrier *dbars = (GridBarrier *)(db + S.off_bars);
+  KrylovArgs *hsys = (KrylovArgs *)(hb + S.off_sys[slot]);
+  int *hcs = (int *)(hb + S.off_cta_sys[slot]);
+  int *hcf = (int *)(hb + S.off_cta_first[slot]);
+  unsigned int *dflags = (unsigned int *)(db + S.off_flags[slot]);
+  GridBarrier *dbars = (GridBarrier *)(db + S.off_bars[slot]);
   int c = 0;
   for (int i = 0; i < m; ++i) {
     KrylovArgs a = args[i];
@@ -142,34 +154,24 @@ static int launch_krylov(BatchScratch &S, int nr, std::vector<KrylovArgs> &args,
     for (int k = 0; k < nb[i]; ++k) hcs[c + k] = i;
     c += nb[i];
   }
-  // the host tables are contiguous from off_sys to off_flags
-  RBFFD_CK(cudaMemcpyAsync(db + S.off_sys, hb + S.off_sys, S.off_flags - S.off_sys,
-                           cudaMemcpyHostToDevice, ctx->stream));
+  // the slot's host tables are contiguous from off_sys to off_flags
+  RBFFD_CK(cudaMemcpyAsync(db + S.off_sys[slot], hb + S.off_sys[slot],
+                           S.off_flags[slot] - S.off_sys[slot], cudaMemcpyHostToDevice,
+                           ctx->stream));
   RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * nctas, ctx->stream));
   RBFFD_CK(cudaMemsetAsync(dbars, 0, sizeof(GridBarrier) * m, ctx->stream));
-  RBFFD_TRY(krylov_batch_launch(ctx, nr, nctas, (const KrylovArgs *)(db + S.off_sys),
-                                (const int *)(db + S.off_cta_sys),
-                                (const int *)(db + S.off_cta_first), amg));
-  // the pinned tables are reused by the next launch: wait until copied
-  RBFFD_CK(cudaStreamSynchronize(ctx->stream));
+  RBFFD_TRY(krylov_batch_launch(ctx, nr, nctas, (const KrylovArgs *)(db + S.off_sys[slot]),
+                                (const int *)(db + S.off_cta_sys[slot]),
+                                (const int *)(db + S.off_cta_first[slot]), amg));
   return RBFFD_OK;
 }
 
-int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
-                  const rbffd_step_params *const *spv, double *deltas, rbffd_iter_stats *stats,
-                  int *status) {
-  if (m <= 0) return RBFFD_OK;
+// Issue one batched outer iteration on the context's stream, ending with
+// the members' results copied to the pinned host table: no host
+// synchronisation, so it can be captured.
+static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
+                       const rbffd_step_params *const *spv) {
   rbffd_ctx *ctx = P[0]->ctx;
-  for (int i = 0; i < m; ++i) {
-    if (P[i]->ctx != ctx || P[i]->precision != RBFFD_PREC_FP64 || P[i]->amgf) {
-      set_error("batch: members must share one context, use RBFFD_PREC_FP64 and a Jacobi or "
-                "BiCGSTAB multigrid p' preconditioner");
-      return RBFFD_EINVAL;
-    }
-  }
-  // a member with symmetry lines solves u~ and v~ as two single-RHS systems
-  // (their rows differ there), so a launch may hold up to 2m systems
-  RBFFD_TRY(S.reserve(ctx, 2 * m));
   // momentum predictor of every member, then one launch for the two-RHS
   // solves of all members (and one for the single-RHS pairs, if any)
   std::vector<KrylovArgs> a2, a1s, a1(m);
@@ -220,8 +222,8 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
     a1[i] = a;
   }
   prof_begin(ctx, 0);
-  if (!a2.empty()) RBFFD_TRY(launch_krylov(S, 2, a2, rows2));
-  if (!a1s.empty()) RBFFD_TRY(launch_krylov(S, 1, a1s, rows1s));
+  if (!a2.empty()) RBFFD_TRY(launch_krylov(S, 0, 2, a2, rows2));
+  if (!a1s.empty()) RBFFD_TRY(launch_krylov(S, 1, 1, a1s, rows1s));
   prof_end(ctx, 0);
   // p' solves: members with a multigrid hierarchy in one launch, the
   // Jacobi-preconditioned ones in another
@@ -248,8 +250,8 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
     }
   }
   prof_begin(ctx, 1);
-  if (!pj.empty()) RBFFD_TRY(launch_krylov(S, 1, pj, rj));
-  if (!pa.empty()) RBFFD_TRY(launch_krylov(S, 1, pa, ra, true));
+  if (!pj.empty()) RBFFD_TRY(launch_krylov(S, 2, 1, pj, rj));
+  if (!pa.empty()) RBFFD_TRY(launch_krylov(S, 3, 1, pa, ra, true));
   prof_end(ctx, 1);
   for (int i = 0; i < m; ++i) {
     RBFFD_TRY(ops_pressure(P[i], spv[i]));
@@ -272,7 +274,104 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
   RBFFD_TRY(after_launch(ctx, "k_gather_out"));
   RBFFD_CK(cudaMemcpyAsync(hb + S.off_out, db + S.off_out, sizeof(MemberOut) * m,
                            cudaMemcpyDeviceToHost, ctx->stream));
+  return RBFFD_OK;
+}
+
+// what a captured iteration depends on beyond device memory: the members,
+// their builds, and the step parameters baked into kernel arguments and
+// Krylov tables
+static std::vector<uint64_t> graph_key(rbffd_problem *const *P, int m,
+                                       const rbffd_step_params *const *spv) {
+  std::vector<uint64_t> k;
+  k.reserve(1 + 8 * (size_t)m);
+  k.push_back((uint64_t)m);
+  auto bits = [](double v) {
+    uint64_t u;
+    memcpy(&u, &v, sizeof(u));
+    return u;
+  };
+  for (int i = 0; i < m; ++i) {
+    const rbffd_step_params *sp = spv[i];
+    k.push_back((uint64_t)(uintptr_t)P[i]);
+    k.push_back(P[i]->gen);
+    k.push_back(bits(sp->dt));
+    for (int a = 0; a < 3; ++a) k.push_back(bits(sp->alpha[a]));
+    k.push_back(bits(sp->krylov_tol));
+    k.push_back((uint64_t)(uint32_t)sp->krylov_maxit);
+  }
+  return k;
+}
+
+int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
+                  const rbffd_step_params *const *spv, double *deltas, rbffd_iter_stats *stats,
+                  int *status) {
+  if (m <= 0) return RBFFD_OK;
+  rbffd_ctx *ctx = P[0]->ctx;
+  for (int i = 0; i < m; ++i) {
+    if (P[i]->ctx != ctx || P[i]->precision != RBFFD_PREC_FP64 || P[i]->amgf) {
+      set_error("batch: members must share one context, use RBFFD_PREC_FP64 and a Jacobi or "
+                "BiCGSTAB multigrid p' preconditioner");
+      return RBFFD_EINVAL;
+    }
+  }
+  // a member with symmetry lines solves u~ and v~ as two single-RHS systems
+  // (their rows differ there), so a launch may hold up to 2m systems
+  RBFFD_TRY(S.reserve(ctx, 2 * m));
+  // replay the captured iteration when it was captured for exactly these
+  // members, builds and step parameters; otherwise capture it again (live
+  // kernel timing records events per phase: launched directly)
+  const bool want = !ctx->prof && !S.graph_off;
+  std::vector<uint64_t> key;
+  if (want) key = graph_key(P, m, spv);
+  if (want && S.exec && key == S.key) {
+    RBFFD_CK(cudaGraphLaunch(S.exec, ctx->stream));
+    ctx->launches += S.graph_launches;
+    S.replays++;
+  } else {
+    S.drop_graph();
+    bool done = false;
+    if (want && cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      const int64_t l0 = ctx->launches;
+      const int rc = issue_batch(S, P, m, spv);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+      ctx->launches = l0;
+      if (rc != RBFFD_OK) {  // an error of the iteration itself, not of the capture
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc;
+      }
+      if (e == cudaSuccess && g && cudaGraphInstantiate(&S.exec, g, 0) == cudaSuccess) {
+        S.graph_launches = 0;
+        size_t nn = 0;
+        if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+          std::vector<cudaGraphNode_t> nodes(nn);
+          cudaGraphGetNodes(g, nodes.data(), &nn);
+          for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+              S.graph_launches++;
+          }
+        }
+        S.key = std::move(key);
+        S.captures++;
+        done = true;
+      } else {
+        // the capture did not hold: launch directly from now on
+        S.exec = nullptr;
+        S.graph_off = true;
+        cudaGetLastError();
+      }
+      if (g) cudaGraphDestroy(g);
+      if (done) {
+        RBFFD_CK(cudaGraphLaunch(S.exec, ctx->stream));
+        ctx->launches += S.graph_launches;
+      }
+    }
+    if (!done) RBFFD_TRY(issue_batch(S, P, m, spv));
+  }
   RBFFD_CK(cudaStreamSynchronize(ctx->stream));
+  char *hb = (char *)S.hmem;
   const MemberOut *mo = (const MemberOut *)(hb + S.off_out);
   if (ctx->prof) {
     // units: rows x iterations of every member (the launch's work)
@@ -349,6 +448,15 @@ extern "C" void rbffd_batch_destroy(rbffd_batch *b) {
   cudaStreamSynchronize(ctx->stream);
   delete b;  // frees the scratch through ctx, which is still alive here
   ctx_unref(ctx);
+}
+
+extern "C" int rbffd_batch_graph_stats(const rbffd_batch *b, int64_t *captures,
+                                       int64_t *replays, int64_t *kernels) {
+  if (!b) return RBFFD_EINVAL;
+  if (captures) *captures = b->scratch.captures;
+  if (replays) *replays = b->scratch.replays;
+  if (kernels) *kernels = b->scratch.graph_off ? 0 : b->scratch.graph_launches;
+  return RBFFD_OK;
 }
 
 extern "C" int rbffd_batch_iterate(rbffd_batch *b, const rbffd_step_params *sp,

@@ -4,17 +4,36 @@
 #include "common.cuh"
 #include "krylov.cuh"
 
+#include <vector>
+
 namespace rbffd {
 
-// Device + pinned host scratch of batched outer iterations, grown on demand.
+// Device + pinned host scratch of batched outer iterations, grown on demand,
+// and the outer iteration captured as a CUDA graph.  Each of the (up to)
+// four Krylov launches of an outer iteration has its own table slot, so
+// nothing is reused within an iteration and the whole iteration -- row
+// kernels, table copies, barrier resets, the cooperative Krylov launches,
+// the gather of the members' results -- is one stream-ordered sequence that
+// a graph can hold.  The graph is replayed while the members, their builds
+// and their step parameters stay the same, and captured again otherwise.
 struct BatchScratch {
+  static constexpr int NSLOT = 4;
   rbffd_ctx *ctx = nullptr;
   int cap = 0, maxc = 0;
   void *dmem = nullptr, *hmem = nullptr;
   size_t dbytes = 0, hbytes = 0;
-  size_t off_sys = 0, off_cta_sys = 0, off_cta_first = 0, off_flags = 0, off_bars = 0,
-         off_recs = 0, off_kouts = 0, off_out = 0;
+  // per slot: sys args, CTA -> system, first CTA of each system (one
+  // contiguous host -> device copy), flags, barriers
+  size_t off_sys[NSLOT] = {}, off_cta_sys[NSLOT] = {}, off_cta_first[NSLOT] = {},
+         off_flags[NSLOT] = {}, off_bars[NSLOT] = {};
+  size_t off_recs = 0, off_kouts = 0, off_out = 0;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uint64_t> key;     // what the graph was captured for
+  int64_t graph_launches = 0;    // kernels one replay launches
+  bool graph_off = false;        // capture failed once: launch directly
+  int64_t replays = 0, captures = 0;
   int reserve(rbffd_ctx *c, int members);
+  void drop_graph();
   ~BatchScratch();
 };
 

@@ -1,26 +1,37 @@
-// fgmres.cu -- flexible GMRES(m) for the pressure-correction system, right-
-// preconditioned by one FP32 multigrid V-cycle per Arnoldi step, as ONE
-// persistent cooperative kernel per solve.
+// fgmres.cu -- restarted flexible GMRES(m) for the pressure-correction
+// system, right-preconditioned by one FP32 multigrid V-cycle per Arnoldi
+// step, as ONE persistent cooperative kernel per solve.
 //
 // The paper solves the p' equation with a preconditioned BiCGSTAB and does
-// not fix the preconditioner (Sec. 3).  On GB300 the multigrid cycle is the
-// cost of a preconditioned iteration, and FP64 issues at a small fraction
-// of the FP32 rate; BiCGSTAB needs two cycles per iteration and cannot take
-// an FP32 cycle (its short recurrences assume one fixed linear
-// preconditioner).  Flexible GMRES keeps every preconditioned direction
-// z_j = M_j^-1 v_j and minimises the residual over x0 + span{z_j}, so one
-// FP32 cycle per step serves and rounding in the cycle only slows it
-// (Saad 1993).  Everything outside the cycle is FP64: the basis V, the
-// directions Z, the SpMVs, the orthogonalisation and the stopping test on
-// the true residual b - A x at every restart.
+// not fix the preconditioner (Sec. 3).  On GB300 an FP64 warp instruction
+// occupies the FP64 pipe for ~32 cycles, against one for FP32, so the solve
+// keeps FP64 only where the answer's accuracy lives:
 //
-// Per Arnoldi step: the cycle (2L - 1 grid exchanges), w = A z_j and the
-// dot products of classical Gram-Schmidt with one reorthogonalisation
-// (two exchanges), and the normalised v_{j+1} published (one exchange).
-// The SpMV and the dot products of a step use block-contiguous row ranges,
-// so they need no exchange between them.  Dot products are reduced in a
-// fixed order; every block holds bit-identical scalars and runs the Givens
-// rotations and the small triangular solve redundantly.
+//   * each restart computes the true residual r = b - A x in FP64 and ends
+//     by x += Z y in FP64: the restarts are an FP64 iterative refinement
+//     (GMRES-based refinement, Carson & Higham 2018), and the solve stops
+//     only when the FP64 relative residual is at the tolerance;
+//   * inside a restart the Arnoldi process runs in FP32 -- basis V,
+//     directions Z, w = A z_j with the FP32 copy of A, classical
+//     Gram-Schmidt with one reorthogonalisation, the cycle -- which only has
+//     to reduce the residual by the restart's factor (~1e-3), far above
+//     FP32 rounding;
+//   * the small Hessenberg least-squares problem (Givens rotations, the
+//     triangular solve) runs on one thread in FP32 like the Arnoldi
+//     entries it holds, on the system scaled by 1 / beta (g_0 = 1), so its
+//     range does not depend on the residual's size; beta multiplies back
+//     in the FP64 update of x.
+//
+// Flexible GMRES (Saad 1993) keeps every preconditioned direction
+// z_j = M_j^-1 v_j, so a cycle whose rounding differs per input only slows
+// it (BiCGSTAB cannot take that cycle, see amg.cuh).
+//
+// Per Arnoldi step: the cycle (2L - 1 grid exchanges), w = A z_j with the
+// dot products (w, v_i) (one exchange: SpMV and dots use this block's
+// contiguous rows), the reorthogonalised w' with its dots (one exchange),
+// and v_{j+1} = w'' / h_{j+1,j} published (one exchange) while thread 0
+// applies the Givens rotations.  Reductions run in a fixed order, so every
+// block holds bit-identical scalars and takes the same branches.
 #include "amg_dev.cuh"
 #include "fgmres.cuh"
 #include "krylov_dev.cuh"
@@ -32,67 +43,89 @@ namespace {
 constexpr int FNT = 1024;
 constexpr int FG_D = FG_MAXM + 2;  // most dot products one exchange reduces
 constexpr int LDH = FG_MAXM + 1;   // leading dimension of the Hessenberg matrix
+constexpr int GB = 8;              // loads a lane keeps in flight in the loops below
 using kdev::MAXB;
 
-// (A x)_i for the rows [r0, r1) of this block, T threads per row: f(i, Ax_i)
-// on the row's first lane.  Gathers of x go through L2 (written in launch).
-template <typename F>
+// barrier `id` among the first `nthreads` threads that reach it (a multiple
+// of 32); id 0 with the whole block is __syncthreads
+__device__ __forceinline__ void bar_sync(int id, int nthreads) {
+  if (id == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// (A x)_i for the rows [r0, r1) of this block, T threads per row, summed in
+// AT: f(i, Ax_i) on the row's first lane.  Gathers of x go through L2
+// (written in this launch).
+template <typename AT, typename VT, typename XT, typename F>
 __device__ __forceinline__ void block_spmv(int r0, int r1, int q, int ldn, int T,
                                            const int32_t *__restrict__ col,
-                                           const double *__restrict__ val, const double *x,
-                                           F &&f) {
+                                           const VT *__restrict__ val, const XT *x, F &&f) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gpw = 32 / T, g = lane / T, lg = lane - g * T;
   const bool active = g < gpw;
   for (int base = r0 + warp * gpw; base < r1; base += nw * gpw) {
     const int i = base + g;
     const bool valid = active && i < r1;
-    double s = 0.0;
+    AT s = AT(0);
     if (valid) {
       for (int j0 = lg; j0 < q; j0 += kdev::CH * T) {
         int c[kdev::CH];
-        double a[kdev::CH];
+        VT a[kdev::CH];
 #pragma unroll
         for (int u = 0; u < kdev::CH; ++u) {
           const int j = j0 + u * T;
           const int64_t e = (int64_t)j * ldn + i;
           c[u] = j < q ? __ldg(col + e) : -1;
-          a[u] = j < q ? __ldg(val + e) : 0.0;
+          a[u] = j < q ? __ldg(val + e) : VT(0);
         }
 #pragma unroll
         for (int u = 0; u < kdev::CH; ++u)
-          if (c[u] >= 0) s += a[u] * __ldcg(x + c[u]);
+          if (c[u] >= 0) s += AT(a[u]) * AT(__ldcg(x + c[u]));
       }
     }
-    double tot = s;
+    AT tot = s;
     for (int u = 1; u < T; ++u) tot += __shfl_sync(0xffffffffu, s, (lane + u) & 31);
     if (valid && lg == 0) f(i, tot);
   }
 }
 
-// Block partials of the dot products (w, u_d), d < D, over rows [r0, r1):
-// warp d takes product d (u_d = V_d for d < nv, u_d = w for d = nv).
-// Partial d of block lb goes to part[d * MAXB + lb].
-__device__ __forceinline__ void block_dots(int r0, int r1, int n, const double *w,
-                                           const double *V, int nv, double *part, int lb) {
+// Block partials of the FP32 dot products (w, u_d), d <= nv, over rows
+// [r0, r1): warp d takes product d (u_d = V_d for d < nv, u_d = w for
+// d = nv), each lane GB rows per round.  Partial d of block lb goes to
+// part[d * MAXB + lb].
+__device__ __forceinline__ void block_dots(int r0, int r1, int n, const float *w,
+                                           const float *V, int nv, float *part, int lb) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int d = warp; d <= nv; d += nw) {
-    const double *u = d < nv ? V + (size_t)d * n : w;
-    double t = 0.0;
-    for (int r = r0 + lane; r < r1; r += 32) t += __ldcg(w + r) * __ldcg(u + r);
+    const float *u = d < nv ? V + (size_t)d * n : w;
+    float t = 0.0f;
+    for (int r = r0 + lane; r < r1; r += 32 * GB) {
+      float a[GB], b[GB];
+#pragma unroll
+      for (int k = 0; k < GB; ++k) {
+        const int rr = r + 32 * k;
+        a[k] = rr < r1 ? __ldcg(w + rr) : 0.0f;
+        b[k] = rr < r1 ? __ldcg(u + rr) : 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < GB; ++k) t += a[k] * b[k];
+    }
     t = kdev::wsum(t);
     if (lane == 0) part[d * MAXB + lb] = t;
   }
 }
 
-// After every block has published its partials: barrier, then the D totals
+// After every block has published its partials: exchange, then the D totals
 // in a fixed order into tot[0..D).  False if a wait gave up.
-__device__ __forceinline__ bool reduce_all(const amgdev::Ctx &c, const double *part, int D,
-                                           double *tot, unsigned int &epoch) {
+template <typename T>
+__device__ __forceinline__ bool reduce_all(const amgdev::Ctx &c, const T *part, int D, T *tot,
+                                           unsigned int &epoch) {
   if (!amgdev::sync(c, epoch)) return false;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int d = warp; d < D; d += nw) {
-    double t = 0.0;
+    T t = T(0);
     for (int b = lane; b < c.nb; b += 32) t += __ldcg(part + d * MAXB + b);
     t = kdev::wsum(t);
     if (lane == 0) tot[d] = t;
@@ -101,8 +134,60 @@ __device__ __forceinline__ bool reduce_all(const amgdev::Ctx &c, const double *p
   return true;
 }
 
+// out_r = (base_r + sgn * sum_{i<k} coef_i U_i[r]) * scale, summed in AT,
+// for the rows [r0, r1) of this block (U_i = U + i n), run by the nthr
+// threads t0 .. t0 + nthr - 1, which meet at barrier bid.  With R = r1 - r0
+// rows and g = nthr / R > 1, g threads share a row, each taking every g-th
+// vector, and their partial sums meet in red[] (nthr entries) in a fixed
+// order; every thread keeps GB loads in flight.  out may alias base.
+template <typename AT, typename UT, typename CT, typename BT, typename OT>
+__device__ __forceinline__ void block_combine(int r0, int r1, int n, const UT *U, int k,
+                                              const CT *coef, const BT *base, OT *out, AT sgn,
+                                              AT scale, AT *red, int t0, int nthr, int bid) {
+  const int R = r1 - r0;
+  const int tid = (int)threadIdx.x - t0;
+  int g = R > 0 ? nthr / R : 1;
+  g = g < 1 ? 1 : (g > GB ? GB : g);
+  const int sub = g > 1 ? tid / R : 0;
+  const int rl0 = g > 1 ? tid - sub * R : tid;
+  // the combining thread of a row loads its base value with the vectors
+  const AT bv = (g > 1 && tid < R) ? AT(__ldcg(base + r0 + tid)) : AT(0);
+  for (int rl = rl0; rl < R && sub < g; rl += (g > 1 ? R : nthr)) {
+    const int r = r0 + rl;
+    const AT b1 = g == 1 ? AT(__ldcg(base + r)) : AT(0);
+    AT t = AT(0);
+    for (int i0 = sub; i0 < k; i0 += GB * g) {
+      UT a[GB];
+#pragma unroll
+      for (int u = 0; u < GB; ++u) {
+        const int i = i0 + u * g;
+        a[u] = i < k ? __ldcg(U + (size_t)i * n + r) : UT(0);
+      }
+#pragma unroll
+      for (int u = 0; u < GB; ++u) {
+        const int i = i0 + u * g;
+        if (i < k) t += AT(coef[i]) * AT(a[u]);
+      }
+    }
+    if (g == 1) {
+      out[r] = OT((b1 + sgn * t) * scale);
+    } else {
+      red[tid] = t;
+      break;  // g > 1: one row per thread
+    }
+  }
+  bar_sync(bid, nthr);
+  if (g > 1 && tid < R) {
+    AT t = red[tid];
+    for (int q = 1; q < g; ++q) t += red[q * R + tid];
+    out[r0 + tid] = OT((bv + sgn * t) * scale);
+  }
+  bar_sync(bid, nthr);
+}
+
 struct FgState {
-  double bnorm, beta, relres;
+  double bnorm, beta, scale, relres;
+  float hn, hinv;
   int it, restarts, state, k, stop;
 };
 
@@ -110,9 +195,10 @@ struct FgState {
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_fgmres(FgmresArgs A) {
-  __shared__ double H[LDH * FG_MAXM];
-  __shared__ double cs[FG_MAXM], sn[FG_MAXM], g[FG_MAXM + 1], y[FG_MAXM];
-  __shared__ double tot[FG_D];
+  __shared__ float H[LDH * FG_MAXM];
+  __shared__ float cs[FG_MAXM], sn[FG_MAXM], g[FG_MAXM + 1], y[FG_MAXM];
+  __shared__ float tot[FG_D];
+  __shared__ double tot64[2];
   __shared__ double stot[16];
   __shared__ double sred[2 * NT];
   __shared__ FgState st;
@@ -129,8 +215,10 @@ __global__ void __launch_bounds__(NT) k_fgmres(FgmresArgs A) {
   int Tb = 1;
   for (int t = 2; t <= 8; ++t)
     if ((32 / t) * (NT / 32) >= R) Tb = t;
-  double *part0 = A.part, *part1 = A.part + FG_D * MAXB;
-  double *V = A.V, *Z = A.Z;
+  double *p64 = (double *)A.part;  // 2 x MAXB
+  float *part0 = (float *)(p64 + 2 * MAXB), *part1 = part0 + FG_D * MAXB;
+  float *fred = reinterpret_cast<float *>(sred);
+  float *V = A.V, *Z = A.Z;
   bool ok = true;
 
   if (leader) {
@@ -142,22 +230,23 @@ __global__ void __launch_bounds__(NT) k_fgmres(FgmresArgs A) {
   }
   __syncthreads();
 
-  // ---- r = b - A x into V_0, with (b, b) and (r, r)
+  // ---- r = b - A x (FP64) with (b, b) and (r, r)
   auto residual = [&](bool first) -> bool {
     double bb = 0.0, rr = 0.0;
-    block_spmv(r0, r1, A.q, A.ldn, Tb, A.col, A.val, A.x, [&](int i, double ax) {
+    block_spmv<double>(r0, r1, A.q, A.ldn, Tb, A.col, A.val, A.x, [&](int i, double ax) {
       const double bi = A.b[i], ri = bi - ax;
-      V[i] = ri;
+      A.r[i] = ri;
       bb += bi * bi;
       rr += ri * ri;
     });
     double v2[2] = {bb, rr};
-    double *outs[2] = {part0, part0 + MAXB};
+    double *outs[2] = {p64, p64 + MAXB};
     kdev::block_partials<NT, 2>(v2, sred, outs, lb);
-    if (!reduce_all(c, part0, 2, tot, epoch)) return false;
+    if (!reduce_all(c, p64, 2, tot64, epoch)) return false;
     if (leader) {
-      if (first) st.bnorm = sqrt(tot[0]);
-      st.beta = sqrt(tot[1]);
+      if (first) st.bnorm = sqrt(tot64[0]);
+      st.beta = sqrt(tot64[1]);
+      st.scale = st.beta > 0.0 ? 1.0 / st.beta : 0.0;
       st.relres = st.bnorm > 0.0 ? st.beta / st.bnorm : 0.0;
       if (st.bnorm == 0.0) st.state = KRY_OK;
       else if (!(st.relres == st.relres)) st.state = KRY_DIVERGED;
@@ -174,67 +263,78 @@ __global__ void __launch_bounds__(NT) k_fgmres(FgmresArgs A) {
   }
 
   while (ok && st.state == KRY_RUNNING) {
-    // ---- start of a cycle: v_0 = r / beta, published
+    // ---- start of a restart: v_0 = r / beta in FP32, published
     {
-      const double inv = 1.0 / st.beta;
-      for (int i = r0 + (int)threadIdx.x; i < r1; i += NT) V[i] = __ldcg(V + i) * inv;
+      const double sc = st.scale;
+      for (int i = r0 + (int)threadIdx.x; i < r1; i += NT) V[i] = float(__ldcg(A.r + i) * sc);
       if (leader) {
-        g[0] = st.beta;
-        for (int k = 1; k <= FG_MAXM; ++k) g[k] = 0.0;
+        g[0] = 1.0f;
+        for (int k = 1; k <= FG_MAXM; ++k) g[k] = 0.0f;
         st.k = 0;
       }
       if (!amgdev::sync(c, epoch)) { ok = false; break; }
     }
     int j = 0;
     for (; j < m; ++j) {
-      double *vj = V + (size_t)j * n, *w = V + (size_t)(j + 1) * n, *zj = Z + (size_t)j * n;
+      float *vj = V + (size_t)j * n, *w = V + (size_t)(j + 1) * n, *zj = Z + (size_t)j * n;
       // z_j = M^-1 v_j (FP32 cycle), published by its last exchange
       if (!amgdev::vcycle(A.amg, c, vj, zj, epoch)) { ok = false; break; }
       // w = A z_j on this block's rows; dots (w, v_i), i <= j, and (w, w)
-      block_spmv(r0, r1, A.q, A.ldn, Tb, A.col, A.val, zj, [&](int i, double az) { w[i] = az; });
+      block_spmv<float>(r0, r1, A.q, A.ldn, Tb, A.col, A.val32, zj,
+                        [&](int i, float az) { w[i] = az; });
       __syncthreads();
       block_dots(r0, r1, n, w, V, j + 1, part0, lb);
       if (!reduce_all(c, part0, j + 2, tot, epoch)) { ok = false; break; }
-      if (leader)
-        for (int i = 0; i <= j; ++i) H[i + LDH * j] = tot[i];
-      __syncthreads();
+      if ((int)threadIdx.x <= j) H[threadIdx.x + LDH * j] = tot[threadIdx.x];
       // w' = w - sum h_i v_i; reorthogonalisation dots (w', v_i), (w', w')
-      for (int r = r0 + (int)threadIdx.x; r < r1; r += NT) {
-        double t = __ldcg(w + r);
-        for (int i = 0; i <= j; ++i) t -= H[i + LDH * j] * __ldcg(V + (size_t)i * n + r);
-        w[r] = t;
-      }
-      __syncthreads();
+      block_combine<float>(r0, r1, n, V, j + 1, tot, w, w, -1.0f, 1.0f, fred, 0, NT, 0);
       block_dots(r0, r1, n, w, V, j + 1, part1, lb);
       if (!reduce_all(c, part1, j + 2, tot, epoch)) { ok = false; break; }
-      if (leader) {
-        double s2 = 0.0;
-        for (int i = 0; i <= j; ++i) {
-          H[i + LDH * j] += tot[i];
-          s2 += tot[i] * tot[i];
+      // column j += the reorthogonalisation coefficients c_i;
+      // h_{j+1,j} = sqrt((w', w') - sum c_i^2) by warp 0 in a fixed order
+      if ((int)threadIdx.x <= j) H[threadIdx.x + LDH * j] += tot[threadIdx.x];
+      if (threadIdx.x < 32) {
+        float q2 = 0.0f;
+        for (int i = threadIdx.x; i <= j; i += 32) q2 += tot[i] * tot[i];
+        q2 = kdev::wsum(q2);
+        if (leader) {
+          const float hn2 = tot[j + 1] - q2;
+          st.hn = hn2 > 0.0f ? sqrtf(hn2) : 0.0f;
+          st.hinv = st.hn > 0.0f ? 1.0f / st.hn : 0.0f;
         }
-        const double hn2 = tot[j + 1] - s2;
-        const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
-        H[j + 1 + LDH * j] = hn;
-        // previous rotations on column j, then a new one
-        for (int i = 0; i < j; ++i) {
-          const double a = H[i + LDH * j], b = H[i + 1 + LDH * j];
-          H[i + LDH * j] = cs[i] * a + sn[i] * b;
-          H[i + 1 + LDH * j] = -sn[i] * a + cs[i] * b;
+      }
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        // thread 0: the previous rotations on column j (the rotated entry
+        // i + 1 carried in a register), a new one, the residual estimate
+        if (leader) {
+          const float hn = st.hn;
+          float hc = H[LDH * j];
+          for (int i = 0; i < j; ++i) {
+            const float b = H[i + 1 + LDH * j];
+            H[i + LDH * j] = cs[i] * hc + sn[i] * b;
+            hc = -sn[i] * hc + cs[i] * b;
+          }
+          const float a = hc, b = hn;
+          const float rr = sqrtf(a * a + b * b);
+          const float ri = rr > 0.0f ? 1.0f / rr : 0.0f;
+          cs[j] = rr > 0.0f ? a * ri : 1.0f;
+          sn[j] = rr > 0.0f ? b * ri : 0.0f;
+          H[j + LDH * j] = rr;
+          H[j + 1 + LDH * j] = 0.0f;
+          g[j + 1] = -sn[j] * g[j];
+          g[j] = cs[j] * g[j];
+          st.it++;
+          st.k = j + 1;
+          // estimated relative residual: |g_{j+1}| beta / |b|
+          const double est = fabs((double)g[j + 1]) * st.beta / st.bnorm;
+          st.stop = !(est == est) ? 2 : (est <= A.tol || hn == 0.0f || st.it >= A.maxit) ? 1 : 0;
         }
-        const double a = H[j + LDH * j], b = H[j + 1 + LDH * j];
-        const double rr = sqrt(a * a + b * b);
-        cs[j] = rr > 0.0 ? a / rr : 1.0;
-        sn[j] = rr > 0.0 ? b / rr : 0.0;
-        H[j + LDH * j] = rr;
-        H[j + 1 + LDH * j] = 0.0;
-        g[j + 1] = -sn[j] * g[j];
-        g[j] = cs[j] * g[j];
-        st.it++;
-        st.k = j + 1;
-        const double est = fabs(g[j + 1]) / st.bnorm;
-        st.stop = !(est == est) ? 2 : (est <= A.tol || hn == 0.0 || st.it >= A.maxit) ? 1 : 0;
-        y[0] = hn;  // the norm for the normalisation below
+      } else {
+        // warps 1..: v_{j+1} = (w' - sum c_i v_i) / h_{j+1,j} meanwhile (not
+        // used when the restart ends at this step)
+        block_combine<float>(r0, r1, n, V, j + 1, tot, w, w, -1.0f, st.hinv, fred, 32, NT - 32,
+                             1);
       }
       __syncthreads();
       if (st.stop == 2) {
@@ -242,36 +342,21 @@ __global__ void __launch_bounds__(NT) k_fgmres(FgmresArgs A) {
         __syncthreads();
         break;
       }
-      // v_{j+1} = (w' - sum c_i v_i) / h_{j+1,j}, published (skipped when the
-      // cycle ends here: the basis vector is not used)
       if (st.stop || j + 1 == m) break;
-      {
-        const double hn = y[0];
-        const double inv = 1.0 / hn;
-        for (int r = r0 + (int)threadIdx.x; r < r1; r += NT) {
-          double t = __ldcg(w + r);
-          for (int i = 0; i <= j; ++i) t -= tot[i] * __ldcg(V + (size_t)i * n + r);
-          w[r] = t * inv;
-        }
-      }
       if (!amgdev::sync(c, epoch)) { ok = false; break; }
     }
     if (!ok || st.state != KRY_RUNNING) break;
-    // ---- y = H^-1 g on the k columns (upper triangular), x += Z y
+    // ---- y = H^-1 g on the k columns (upper triangular), x += beta Z y in FP64
     if (leader) {
       const int k = st.k;
       for (int i = k - 1; i >= 0; --i) {
-        double t = g[i];
+        float t = g[i];
         for (int l = i + 1; l < k; ++l) t -= H[i + LDH * l] * y[l];
         y[i] = t / H[i + LDH * i];
       }
     }
     __syncthreads();
-    for (int r = r0 + (int)threadIdx.x; r < r1; r += NT) {
-      double t = A.x[r];
-      for (int i = 0; i < st.k; ++i) t += y[i] * __ldcg(Z + (size_t)i * n + r);
-      A.x[r] = t;
-    }
+    block_combine<double>(r0, r1, n, Z, st.k, y, A.x, A.x, st.beta, 1.0, sred, 0, NT, 0);
     if (!amgdev::sync(c, epoch)) { ok = false; break; }
     if (leader) st.restarts++;
     __syncthreads();
@@ -287,9 +372,9 @@ __global__ void __launch_bounds__(NT) k_fgmres(FgmresArgs A) {
   }
 }
 
-size_t fgmres_partials_doubles(int nblocks) {
+size_t fgmres_partials_bytes(int nblocks) {
   (void)nblocks;
-  return (size_t)2 * FG_D * MAXB;
+  return sizeof(double) * 2 * MAXB + sizeof(float) * 2 * FG_D * MAXB;
 }
 
 int fgmres_max_blocks(rbffd_ctx *ctx) {
@@ -307,7 +392,8 @@ int fgmres_max_blocks(rbffd_ctx *ctx) {
 }
 
 int fgmres_launch(rbffd_ctx *ctx, int nblocks, const FgmresArgs &args) {
-  if (nblocks < 1 || nblocks > MAXB || args.m < 1 || args.m > FG_MAXM || !args.amg) {
+  if (nblocks < 1 || nblocks > MAXB || args.m < 1 || args.m > FG_MAXM || !args.amg ||
+      !args.val32 || ((uintptr_t)args.part & 7) != 0) {
     set_error("fgmres_launch: bad arguments (blocks %d, m %d)", nblocks, args.m);
     return RBFFD_EINVAL;
   }

@@ -13,12 +13,14 @@ struct FgmresArgs {
   int n, q, ldn, tpr;   // rows, ELL width, leading dimension, threads per row
   int m;                // restart length, 1..FG_MAXM
   const int32_t *col;   // ELL [q][ldn]
-  const double *val;    // ELL [q][ldn]
+  const double *val;    // ELL [q][ldn], FP64: the true residual at each restart
+  const float *val32;   // the same values rounded to FP32: the Arnoldi SpMVs
   const double *b;
   double *x;            // initial guess in, solution out
-  double *V;            // (m + 1) x n Arnoldi basis
-  double *Z;            // m x n preconditioned directions
-  double *part;         // fgmres_partials_doubles(nblocks)
+  double *r;            // n: b - A x at a restart
+  float *V;             // (m + 1) x n Arnoldi basis
+  float *Z;             // m x n preconditioned directions
+  void *part;           // fgmres_partials_bytes(nblocks), 8-byte aligned
   GridBarrier *bar;     // err word (bounded waits that gave up)
   unsigned int *flags;  // word 0: the arrival counter, zeroed per launch
   KrylovOut *out;       // iters, restarts, status (KRY_*), relres (true residual)
@@ -27,7 +29,7 @@ struct FgmresArgs {
   const AmgDevF *amg;   // the FP32 hierarchy
 };
 
-size_t fgmres_partials_doubles(int nblocks);
+size_t fgmres_partials_bytes(int nblocks);
 int fgmres_max_blocks(rbffd_ctx *ctx);
 // rows per block fixed by nblocks; threads per row chosen inside
 int fgmres_launch(rbffd_ctx *ctx, int nblocks, const FgmresArgs &args);

@@ -1,5 +1,6 @@
 // problem.cu -- problem lifetime and the outer-iteration / time-step /
 // steady and unsteady drivers (paper Sec. 3.2), behind the C ABI.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -69,10 +70,6 @@ int check_desc(const rbffd_problem_desc *d) {
     set_error("problem desc: unknown preconditioner %d", d->precond);
     return RBFFD_EINVAL;
   }
-  if (d->precond != RBFFD_PRECOND_JACOBI && d->precision != RBFFD_PREC_FP64) {
-    set_error("problem desc: the multigrid preconditioner needs RBFFD_PREC_FP64");
-    return RBFFD_ENOTIMPL;
-  }
   return RBFFD_OK;
 }
 
@@ -81,7 +78,9 @@ void free_amg(rbffd_problem *P) {
   if (P->fg_mem) dev_free(P->ctx, P->fg_mem, P->fg_bytes);
   P->fg_mem = nullptr;
   P->fg_bytes = 0;
-  P->fgV = P->fgZ = P->fgpart = nullptr;
+  P->fgV = P->fgZ = nullptr;
+  P->fgR = nullptr;
+  P->fgpart = nullptr;
   P->amgf = nullptr;
   memset(&P->amgf_host, 0, sizeof(P->amgf_host));
   P->amg_mem = nullptr;
@@ -93,6 +92,8 @@ void free_amg(rbffd_problem *P) {
 
 // Copy the inputs, build clouds, weights and operators, reset the state.
 int build(rbffd_problem *P, const rbffd_problem_desc *d) {
+  static std::atomic<uint64_t> generation{0};
+  P->gen = ++generation;
   rbffd_ctx *ctx = P->ctx;
   cudaStream_t st = ctx->stream;
   const size_t nb = (size_t)d->n * sizeof(double);
@@ -159,21 +160,25 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
   free_amg(P);
   P->precond = d->precond;
   if (P->precond == RBFFD_PRECOND_AMG) {
-    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, &P->amg_mem, &P->amg_bytes,
-                        &P->amg, &P->amg_host, &P->amg_info));
+    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, P->kblocks1 * 32, &P->amg_mem,
+                        &P->amg_bytes, &P->amg, &P->amg_host, &P->amg_info));
   } else if (P->precond == RBFFD_PRECOND_AMG_FGMRES) {
-    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, &P->amg_mem, &P->amg_bytes,
-                        &P->amgf, &P->amgf_host, &P->amg_info));
-    // Arnoldi basis (m + 1 vectors), directions (m) and partial sums
-    P->fg_m = FG_MAXM;
     P->fg_blocks = fgmres_max_blocks(ctx);
     if (P->fg_blocks > P->kblocks1) P->fg_blocks = P->kblocks1;
+    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, P->fg_blocks * 32, &P->amg_mem,
+                        &P->amg_bytes, &P->amgf, &P->amgf_host, &P->amg_info));
+    // FP64 restart residual and partial sums, then the FP32 Arnoldi basis
+    // (m + 1 vectors) and directions (m)
+    P->fg_m = FG_MAXM;
+    const size_t rb = (sizeof(double) * P->n + 255) / 256 * 256;
+    const size_t pb = (fgmres_partials_bytes(P->fg_blocks) + 255) / 256 * 256;
     const size_t nv = (size_t)(2 * P->fg_m + 1) * P->n;
-    P->fg_bytes = sizeof(double) * (nv + fgmres_partials_doubles(P->fg_blocks));
+    P->fg_bytes = rb + pb + sizeof(float) * nv;
     RBFFD_TRY(dev_alloc(ctx, &P->fg_mem, P->fg_bytes));
-    P->fgV = (double *)P->fg_mem;
+    P->fgR = (double *)P->fg_mem;
+    P->fgpart = (char *)P->fg_mem + rb;
+    P->fgV = (float *)((char *)P->fg_mem + rb + pb);
     P->fgZ = P->fgV + (size_t)(P->fg_m + 1) * P->n;
-    P->fgpart = P->fgZ + (size_t)P->fg_m * P->n;
   }
   if (P->precision != RBFFD_PREC_FP64) {
     RBFFD_TRY(ops_to_inner(P, P->Pp, P->Pin, (int64_t)P->ldn * P->q));
@@ -210,10 +215,17 @@ int krylov_status_code(int s) {
 }
 
 // Issue one outer iteration (no host synchronisation).
+// The momentum solves run in the problem's precision: FP64 BiCGSTAB, or
+// (mixed) FP32 / float-float BiCGSTAB inside FP64 refinement.  The p'
+// solve follows its preconditioner: with Jacobi it takes the same
+// precision; multigrid BiCGSTAB is FP64 throughout; flexible GMRES runs its
+// Arnoldi process in FP32 inside FP64 restarts (fgmres.cu).  Every solve
+// stops on the same FP64 relative residual.
 int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   rbffd_ctx *ctx = P->ctx;
   prof_begin(ctx, 2);
   RBFFD_TRY(ops_momentum(P, sp));
+  const bool mixed = P->precision != RBFFD_PREC_FP64;
   KrylovArgs a;
   memset(&a, 0, sizeof(a));
   a.n = P->n;
@@ -225,11 +237,9 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   a.flags = P->flags;
   a.tol = sp->krylov_tol;
   a.maxit = sp->krylov_maxit;
-  if (P->precision != RBFFD_PREC_FP64) {
-    RBFFD_TRY(ops_to_inner(P, P->Am, P->Ain, (int64_t)P->ldn * P->q));
-    RBFFD_TRY(ops_to_inner(P, P->m_dinv, P->mdin, P->ldn));
-    MixedArgs m;
-    memset(&m, 0, sizeof(m));
+  MixedArgs m;
+  memset(&m, 0, sizeof(m));
+  if (mixed) {
     m.inner = P->inner;
     m.n = P->n;
     m.q = P->q;
@@ -244,6 +254,14 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
     m.inner_tol = sp->inner_tol > 0 ? sp->inner_tol : 1e-3;
     m.inner_maxit = sp->inner_maxit > 0 ? sp->inner_maxit : 4000;
     m.max_sweeps = 60;
+  }
+
+  // ---- momentum predictor: one matrix, two right-hand sides (two
+  // single-RHS solves when symmetry lines make the u~ and v~ rows differ)
+  prof_begin(ctx, 0);
+  if (mixed) {
+    RBFFD_TRY(ops_to_inner(P, P->Am, P->Ain, (int64_t)P->ldn * P->q));
+    RBFFD_TRY(ops_to_inner(P, P->m_dinv, P->mdin, P->ldn));
     m.val64 = P->Am;
     m.valin = P->Ain;
     m.dinvin = P->mdin;
@@ -255,11 +273,9 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
     m.w[1] = P->mv[1];
     m.out = P->kout;
     m.tpr = krylov_threads_per_row(P->n, 2, P->kblocks2);
-    prof_begin(ctx, 0);
     if (!P->has_sym) {
       RBFFD_TRY(krylov_ir_launch(ctx, 2, P->kblocks2, m));
     } else {
-      // u~ and v~ rows differ on symmetry lines: two single-RHS solves
       RBFFD_TRY(ops_to_inner(P, P->Am2, P->Ain2, (int64_t)P->ldn * P->q));
       RBFFD_TRY(ops_to_inner(P, P->m_dinv2, P->mdin2, P->ldn));
       m.b[1] = nullptr;
@@ -276,66 +292,38 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
       RBFFD_TRY(krylov_ir_launch(ctx, 1, P->kblocks1, m));
       m.w[0] = P->mv[0];
     }
-    prof_end(ctx, 0);
-    RBFFD_TRY(ops_divergence(P, sp));
-    m.val64 = P->Pp;
-    m.valin = P->Pin;
-    m.dinvin = P->pdin;
-    m.b[0] = P->bp;
-    m.b[1] = nullptr;
-    m.x[0] = P->pc;
-    m.x[1] = nullptr;
-    m.out = P->kout + 2;
-    m.tpr = krylov_threads_per_row(P->n, 1, P->kblocks1);
-    prof_begin(ctx, 1);
-    RBFFD_TRY(krylov_ir_launch(ctx, 1, P->kblocks1, m));
-    prof_end(ctx, 1);
-    RBFFD_TRY(ops_pressure(P, sp));
-    RBFFD_TRY(ops_correct(P, sp));
-    prof_end(ctx, 2);
-    return RBFFD_OK;
-  }
-  // momentum predictor: one matrix, two right-hand sides
-  a.val = P->Am;
-  a.dinv = P->m_dinv;
-  a.b[0] = P->bu;
-  a.b[1] = P->bv;
-  a.x[0] = P->ut;
-  a.x[1] = P->vt;
-  a.w[0] = P->kv[0];
-  a.w[1] = P->kv[1];
-  a.out = P->kout;
-  a.tpr = krylov_threads_per_row(P->n, 2, P->kblocks2);
-  prof_begin(ctx, 0);
-  if (!P->has_sym) {
-    RBFFD_TRY(krylov_launch(ctx, 2, P->kblocks2, a));
   } else {
-    // u~ and v~ rows differ on symmetry lines: two single-RHS solves
-    KrylovArgs b1 = a;
-    b1.b[1] = nullptr;
-    b1.x[1] = nullptr;
-    b1.tpr = krylov_threads_per_row(P->n, 1, P->kblocks1);
-    RBFFD_TRY(krylov_launch(ctx, 1, P->kblocks1, b1));
-    b1.val = P->Am2;
-    b1.dinv = P->m_dinv2;
-    b1.b[0] = P->bv;
-    b1.x[0] = P->vt;
-    b1.w[0] = P->kv[1];
-    b1.out = P->kout + 1;
-    RBFFD_TRY(krylov_launch(ctx, 1, P->kblocks1, b1));
+    a.val = P->Am;
+    a.dinv = P->m_dinv;
+    a.b[0] = P->bu;
+    a.b[1] = P->bv;
+    a.x[0] = P->ut;
+    a.x[1] = P->vt;
+    a.w[0] = P->kv[0];
+    a.w[1] = P->kv[1];
+    a.out = P->kout;
+    a.tpr = krylov_threads_per_row(P->n, 2, P->kblocks2);
+    if (!P->has_sym) {
+      RBFFD_TRY(krylov_launch(ctx, 2, P->kblocks2, a));
+    } else {
+      KrylovArgs b1 = a;
+      b1.b[1] = nullptr;
+      b1.x[1] = nullptr;
+      b1.tpr = krylov_threads_per_row(P->n, 1, P->kblocks1);
+      RBFFD_TRY(krylov_launch(ctx, 1, P->kblocks1, b1));
+      b1.val = P->Am2;
+      b1.dinv = P->m_dinv2;
+      b1.b[0] = P->bv;
+      b1.x[0] = P->vt;
+      b1.w[0] = P->kv[1];
+      b1.out = P->kout + 1;
+      RBFFD_TRY(krylov_launch(ctx, 1, P->kblocks1, b1));
+    }
   }
   prof_end(ctx, 0);
   RBFFD_TRY(ops_divergence(P, sp));
-  // pressure correction
-  a.val = P->Pp;
-  a.dinv = P->p_dinv;
-  if (P->amg) a.amg = P->amg;  // V-cycle preconditioner
-  a.b[0] = P->bp;
-  a.b[1] = nullptr;
-  a.x[0] = P->pc;
-  a.x[1] = nullptr;
-  a.out = P->kout + 2;
-  a.tpr = krylov_threads_per_row(P->n, 1, P->kblocks1);
+
+  // ---- pressure correction
   prof_begin(ctx, 1);
   if (P->amgf) {
     FgmresArgs f;
@@ -347,8 +335,10 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
     f.m = P->fg_m;
     f.col = P->col;
     f.val = P->Pp;
+    f.val32 = P->amgf_host.a0;
     f.b = P->bp;
     f.x = P->pc;
+    f.r = P->fgR;
     f.V = P->fgV;
     f.Z = P->fgZ;
     f.part = P->fgpart;
@@ -359,7 +349,30 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
     f.maxit = sp->krylov_maxit;
     f.amg = P->amgf;
     RBFFD_TRY(fgmres_launch(ctx, P->fg_blocks, f));
+  } else if (mixed && !P->amg) {
+    m.val64 = P->Pp;
+    m.valin = P->Pin;
+    m.dinvin = P->pdin;
+    m.b[0] = P->bp;
+    m.b[1] = nullptr;
+    m.x[0] = P->pc;
+    m.x[1] = nullptr;
+    m.w[0] = P->mv[0];
+    m.out = P->kout + 2;
+    m.tpr = krylov_threads_per_row(P->n, 1, P->kblocks1);
+    RBFFD_TRY(krylov_ir_launch(ctx, 1, P->kblocks1, m));
   } else {
+    a.val = P->Pp;
+    a.dinv = P->p_dinv;
+    a.amg = P->amg;  // V-cycle preconditioner, or null (Jacobi)
+    a.b[0] = P->bp;
+    a.b[1] = nullptr;
+    a.x[0] = P->pc;
+    a.x[1] = nullptr;
+    a.w[0] = P->kv[0];
+    a.w[1] = P->kv[1];
+    a.out = P->kout + 2;
+    a.tpr = krylov_threads_per_row(P->n, 1, P->kblocks1);
     RBFFD_TRY(krylov_launch(ctx, 1, P->kblocks1, a));
   }
   prof_end(ctx, 1);
@@ -718,24 +731,26 @@ namespace rbffd {
 double pcorr_bytes(const rbffd_problem *P, int iters) {
   const double n = P->n, q = P->q, it = iters;
   if (!P->amg && !P->amgf) return n * it * (2 * q * 12 + 14 * 8);
-  // per V-cycle (operators and level vectors in the cycle's type, FP64 in
-  // and out): S_0 b_0 (ELL, q (s + 4) + b_0 read + z written), R~_l, P~_l
-  // and S_l (l >= 1) entries at s + 4 B, their vectors, the dense inverse
+  // per V-cycle (operators and level vectors in the cycle's type, in and
+  // out in the solve's vector type): S_0 b_0 (ELL, q (s + 4) + b_0 read + z
+  // written), R~_l, P~_l and S_l (l >= 1) entries at s + 4 B, their
+  // vectors, the dense inverse
   const AmgInfo &I = P->amg_info;
   const double s = P->amgf ? 4.0 : 8.0;
-  const double e = s + 4.0, v = s;
-  double cyc = n * (q * e + 8 + v) + n * (v + 8);  // S_0, then P~_0's z read and out write
+  const double e = s + 4.0, v = s, io = s;
+  double cyc = n * (q * e + io + v) + n * (v + io);  // S_0, then P~_0's z read and out write
   for (int l = 0; l < I.nlev; ++l) {
     if (l + 1 < I.nlev) cyc += e * (I.nnz_r[l] + I.nnz_p[l]);
     if (l >= 1 && l + 1 < I.nlev) cyc += e * I.nnz[l] + 5.0 * v * I.n[l];
     if (l + 1 == I.nlev) cyc += v * I.n[l] * I.n[l];
   }
   if (P->amgf) {
-    // one SpMV and one cycle per Arnoldi step, classical Gram-Schmidt with
-    // one reorthogonalisation over on average min(it, m) / 2 + 1 basis
-    // vectors (two dot passes and two update passes), normalisation
+    // one FP32 SpMV (q (4 + 4) B, z read, w written) and one cycle per
+    // Arnoldi step, classical Gram-Schmidt with one reorthogonalisation
+    // over on average min(it, m) / 2 + 1 FP32 basis vectors (two dot
+    // passes and two update passes), normalisation
     const double jv = (it < P->fg_m ? it : P->fg_m) / 2.0 + 1.0;
-    return n * it * (q * 12 + 16 + 8.0 * (4 * jv + 4)) + it * cyc;
+    return n * it * (q * 8 + 8 + 4.0 * (4 * jv + 4)) + it * cyc;
   }
   return n * it * (2 * q * 12 + 14 * 8) + 2.0 * it * cyc;
 }

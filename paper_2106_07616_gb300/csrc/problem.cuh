@@ -63,6 +63,9 @@ struct rbffd_problem {
   size_t bytes = 0;
   // multigrid preconditioner of the p' solve (its own allocation), or none
   int precond = 0;
+  // changes with every build (create or reload): what a captured batch
+  // graph of this problem refers to (buffers, hierarchy) may have changed
+  uint64_t gen = 0;
   void *amg_mem = nullptr;
   size_t amg_bytes = 0;
   const rbffd::AmgDev *amg = nullptr;  // device copy of the level table
@@ -74,7 +77,9 @@ struct rbffd_problem {
   rbffd::AmgDevF amgf_host{};
   void *fg_mem = nullptr;
   size_t fg_bytes = 0;
-  double *fgV = nullptr, *fgZ = nullptr, *fgpart = nullptr;
+  double *fgR = nullptr;                     // FP64 restart residual
+  float *fgV = nullptr, *fgZ = nullptr;       // FP32 basis and directions
+  void *fgpart = nullptr;
   int fg_m = 0, fg_blocks = 0;
 };
 

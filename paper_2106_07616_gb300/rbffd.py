@@ -132,6 +132,7 @@ def load(path: str = LIB_PATH):
         "rbffd_batch_create": (C.c_int, [vp, i32, C.POINTER(vp), C.POINTER(vp)]),
         "rbffd_batch_destroy": (None, [vp]),
         "rbffd_batch_iterate": (C.c_int, [vp, C.POINTER(StepParams), vp, vp, vp, vp, vp]),
+        "rbffd_batch_graph_stats": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
         "rbffd_server_create": (C.c_int, [vp, C.POINTER(ServerParams), C.POINTER(vp)]),
         "rbffd_server_submit": (C.c_int, [vp, C.POINTER(ProblemDesc), C.POINTER(SolveParams),
                                           C.POINTER(C.c_uint64)]),
@@ -427,6 +428,14 @@ class Batch:
                "rbffd_batch_iterate")
         its = np.array([list(s.iters) for s in st])
         return d, its, status
+
+    def graph_stats(self):
+        """(graphs captured, replays, kernels per replay) of the batched
+        outer iteration."""
+        c, r, k = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        _check(load().rbffd_batch_graph_stats(self.h, C.byref(c), C.byref(r), C.byref(k)),
+               "rbffd_batch_graph_stats")
+        return c.value, r.value, k.value
 
 
 def amg_analyze(rowptr, col, val):

@@ -31,6 +31,36 @@ def test_batch_matches_members_solved_alone():
         for k in ("u", "v", "p"):
             e = rel_l2(B.problems[i].get(k), alone[i].get(k))
             assert e <= 1e-8, (i, k, e)
+    # the first iteration was captured as a graph, the next two replayed it
+    captures, replays, kernels = B.graph_stats()
+    assert (captures, replays) == (1, 2), (captures, replays)
+    assert kernels >= 4 * len(fps) + 2
+    B.close()
+
+
+def test_batch_graph_captured_again_after_a_reload():
+    """A reload rebuilds a member (new weights, hierarchy, fields): the next
+    batched iteration must not replay the old graph."""
+    fps = [clouds.kovasznay(30, dt=0.4), clouds.cavity(24, seed=3, dt=0.05)]
+    alone = [rbffd.Problem(ctx(), fp, precond=rbffd.PRECOND_AMG) for fp in fps]
+    B = rbffd.Batch(ctx(), [rbffd.Problem(ctx(), fp, precond=rbffd.PRECOND_AMG) for fp in fps])
+    dts = [fp.dt for fp in fps]
+    for _ in range(2):
+        B.iterate(dts)
+    for fp, P in zip(fps, alone):
+        for _ in range(2):
+            P.simple_iterate(fp.dt)
+    B.problems[0].reload(fps[0], precond=rbffd.PRECOND_AMG)
+    alone[0].reload(fps[0], precond=rbffd.PRECOND_AMG)
+    d, its, status = B.iterate(dts)
+    assert np.all(status == 0)
+    for fp, P in zip(fps, alone):
+        P.simple_iterate(fp.dt)
+    assert B.graph_stats()[:2] == (2, 1)
+    for i in range(len(fps)):
+        for k in ("u", "v", "p"):
+            e = rel_l2(B.problems[i].get(k), alone[i].get(k))
+            assert e <= 1e-8, (i, k, e)
     B.close()
 
 
