@@ -9,10 +9,14 @@ whole-step time.
 
 Workload (default): the lid-driven cavity, Re = 1000, 200 x 200 clustered
 and jittered cloud (N = 40 000), polynomial degree 4, q = 30, dt from a
-Courant number of about 10.  --precond amg (default): the p' BiCGSTAB is
-preconditioned by a smoothed-aggregation V-cycle (jacobi: diagonal).
---precision fp64 (default): FP64 Krylov throughout; mixed / ff: FP32 or
-float-float BiCGSTAB inside FP64 defect correction to the same tolerance.
+Courant number of about 10.  The p' solver (--precond): fgmres (default for
+single problems): flexible GMRES(30) whose Arnoldi process runs in FP32
+with one FP32 smoothed-aggregation V-cycle per step, inside FP64 restarts;
+amg (default for batch and serve): FP64 BiCGSTAB with an FP64 V-cycle;
+jacobi: FP64 BiCGSTAB with the diagonal.  The momentum solves (--precision):
+mixed (default for single problems): FP32 BiCGSTAB inside FP64 defect
+correction; ff: float-float; fp64 (batch and serve).  Every solve stops on
+the same FP64 relative residual (1e-12).
 Other workloads: kovasznay50, cylinder150k (outlet, symmetry and no-slip
 rows, 147 827 graded points), batch (many instances per launch) and serve
 (a Poisson stream of steady-solve requests through the request server).
@@ -70,6 +74,9 @@ KRYLOV_PROFILES = {
     "jacobi": ("k_bicgstab_fp64_cavity200.md", ("krylov.cu", "krylov_dev.cuh", "common.cuh")),
     "amg": ("k_bicgstab_amg_fp64_cavity200.md",
             ("krylov.cu", "krylov_dev.cuh", "common.cuh", "amg_dev.cuh", "amg.cuh")),
+    "fgmres": ("k_fgmres_cavity200.md",
+               ("fgmres.cu", "fgmres.cuh", "krylov_dev.cuh", "common.cuh", "amg_dev.cuh",
+                "amg.cuh")),
 }
 
 
@@ -77,7 +84,9 @@ def krylov_traffic(precision, workload_name, precond="jacobi"):
     """DRAM bytes per pressure-correction launch from the committed ncu
     summary, only while the kernel sources still hash to the profiled ones."""
     import hashlib
-    if precision != "fp64" or workload_name != "cavity200" or precond not in KRYLOV_PROFILES:
+    # the flexible GMRES kernel is the same whatever the momentum precision
+    if workload_name != "cavity200" or precond not in KRYLOV_PROFILES or (
+            precision != "fp64" and precond != "fgmres"):
         return None
     name, files = KRYLOV_PROFILES[precond]
     prof = os.path.join(ROOT, "profiles", name)
@@ -524,7 +533,9 @@ def run_native(args):
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None,
-               "dtype": {"mixed": "f32+f64", "ff": "f32x2+f64"}.get(args.precision, "f64"),
+               "dtype": ("f32x2+f64" if args.precision == "ff" else
+                         "f32+f64" if args.precision == "mixed" or args.precond == "fgmres"
+                         else "f64"),
                "data": "synthetic",
                "config": {"workload": args.workload, "description": desc,
                           "outer_cap": args.outer, "outer_iters_per_step": all_it / args.steps / world,
@@ -554,12 +565,19 @@ def main():
     ap.add_argument("--criterion", type=int, default=1,
                     help="serve: 0 = steady residual R, 1 = the paper's steady error change/dt")
     ap.add_argument("--max-steps", type=int, default=1000)
-    ap.add_argument("--precond", default="amg", choices=["jacobi", "amg", "fgmres"],
+    ap.add_argument("--precond", default=None, choices=["jacobi", "amg", "fgmres"],
                     help="preconditioner of the pressure-correction BiCGSTAB")
-    ap.add_argument("--precision", default="fp64", choices=["mixed", "ff", "fp64"],
+    ap.add_argument("--precision", default=None, choices=["mixed", "ff", "fp64"],
                     help="Krylov arithmetic: FP32 or float-float inside FP64 defect "
                          "correction, or FP64")
     args = ap.parse_args()
+    # batches and the request server take FP64 members with a BiCGSTAB p'
+    # solver; single problems run the mixed-precision path
+    many = args.workload in ("batch", "serve")
+    if args.precond is None:
+        args.precond = "amg" if many else "fgmres"
+    if args.precision is None:
+        args.precision = "fp64" if many else "mixed"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

@@ -237,10 +237,14 @@ __global__ void __launch_bounds__(RT) k_correct(
     const double *__restrict__ nx, const double *__restrict__ ny,
     const double *__restrict__ pc, const double *__restrict__ ut,
     const double *__restrict__ vt, double c, double *__restrict__ u, double *__restrict__ v,
-    double *__restrict__ part) {
+    const double *__restrict__ pnew, double *__restrict__ p, double *__restrict__ part) {
   __shared__ double sred[RT / 32];
   double su = 0.0, sv = 0.0;
   for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
+    // the pressure k_pressure wrote beside p becomes p (no pointer swap:
+    // the buffers an outer iteration uses stay the same, so it can be
+    // captured and replayed)
+    p[i] = pnew[i];
     double unew = ut[i], vnew = vt[i];
     const int t = tag[i];
     if (t != RBFFD_TAG_DIRICHLET) {
@@ -275,23 +279,24 @@ __global__ void __launch_bounds__(RT) k_correct(
 }
 
 // End of a time step: change partials (sum|u - u^n|, sum|v - v^n|), then
-// u^{n-1} <- u^n, u^n <- u (the caller swaps the n / n-1 pointers first, so
-// `old_n` is the previous level n and `dst_n` receives the new one).
+// u^{n-1} <- u^n, u^n <- u, row by row in place (the buffers keep their
+// roles, so captured outer iterations stay valid across time steps).
 __global__ void __launch_bounds__(RT) k_rotate(int n, const double *__restrict__ u,
                                                const double *__restrict__ v,
-                                               const double *__restrict__ old_un,
-                                               const double *__restrict__ old_vn,
-                                               double *__restrict__ dst_un,
-                                               double *__restrict__ dst_vn,
+                                               double *__restrict__ un, double *__restrict__ vn,
+                                               double *__restrict__ unm1,
+                                               double *__restrict__ vnm1,
                                                double *__restrict__ part) {
   __shared__ double sred[RT / 32];
   double su = 0.0, sv = 0.0;
   for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
-    const double a = u[i], b = v[i];
-    su += fabs(a - old_un[i]);
-    sv += fabs(b - old_vn[i]);
-    dst_un[i] = a;
-    dst_vn[i] = b;
+    const double a = u[i], b = v[i], on = un[i], ovn = vn[i];
+    su += fabs(a - on);
+    sv += fabs(b - ovn);
+    unm1[i] = on;
+    vnm1[i] = ovn;
+    un[i] = a;
+    vn[i] = b;
   }
   su = block_sum<RT>(su, sred);
   sv = block_sum<RT>(sv, sred);
@@ -495,32 +500,22 @@ int ops_pressure(rbffd_problem *P, const rbffd_step_params *sp) {
       P->n, P->q, P->ldn, P->col, P->Wx, P->Wy, P->Wl, P->tag, P->nx, P->ny, P->p, P->pc,
       P->ut, P->vt, P->un, P->vn, P->unm1, P->vnm1, P->rho, P->mu, sp->dt, sp->alpha[0],
       sp->alpha[1], sp->alpha[2], P->force[0], P->force[1], P->p2);
-  RBFFD_TRY(after_launch(P->ctx, "k_pressure"));
-  double *t = P->p;
-  P->p = P->p2;
-  P->p2 = t;
-  return RBFFD_OK;
+  return after_launch(P->ctx, "k_pressure");
 }
 
 int ops_correct(rbffd_problem *P, const rbffd_step_params *sp) {
   double c = sp->dt / (P->rho * sp->alpha[0]);
   k_correct<<<P->rblocks, RT, 0, P->ctx->stream>>>(P->n, P->q, P->ldn, P->col, P->Wx, P->Wy,
                                                    P->tag, P->nx, P->ny, P->pc, P->ut, P->vt, c,
-                                                   P->u, P->v, P->rpart);
+                                                   P->u, P->v, P->p2, P->p, P->rpart);
   RBFFD_TRY(after_launch(P->ctx, "k_correct"));
   k_finalize<<<1, 32, 0, P->ctx->stream>>>(P->rpart, P->rblocks, P->n, 0, P->rec);
   return after_launch(P->ctx, "k_finalize");
 }
 
 int ops_rotate(rbffd_problem *P) {
-  double *t = P->unm1;
-  P->unm1 = P->un;
-  P->un = t;
-  t = P->vnm1;
-  P->vnm1 = P->vn;
-  P->vn = t;
-  k_rotate<<<P->rblocks, RT, 0, P->ctx->stream>>>(P->n, P->u, P->v, P->unm1, P->vnm1, P->un,
-                                                  P->vn, P->rpart);
+  k_rotate<<<P->rblocks, RT, 0, P->ctx->stream>>>(P->n, P->u, P->v, P->un, P->vn, P->unm1,
+                                                  P->vnm1, P->rpart);
   RBFFD_TRY(after_launch(P->ctx, "k_rotate"));
   k_finalize<<<1, 32, 0, P->ctx->stream>>>(P->rpart, P->rblocks, P->n, 1, P->rec);
   return after_launch(P->ctx, "k_finalize");
