@@ -384,8 +384,10 @@ int rbffd_apply(rbffd_problem *prob, int32_t which, const double *x, double *y);
  * (the same steps as simple_iterate) for each active member: the row kernels
  * per member, and the two Krylov solves of all members in one cooperative
  * launch each, in which every member owns consecutive CTAs and synchronises
- * only with them.  Members must be RBFFD_PREC_FP64 problems of the batch's
- * context and stay owned by the caller (destroy the batch first).  A member
+ * only with them (one launch per p' solver: Jacobi BiCGSTAB, multigrid
+ * BiCGSTAB, flexible GMRES).  Members must be problems of the batch's
+ * context with RBFFD_PREC_FP64 momentum solves (any p' solver) and stay
+ * owned by the caller (destroy the batch first).  A member
  * solved in a batch matches the same member solved alone to the Krylov
  * tolerance (the sums are ordered differently, the fixed point is not). */
 typedef struct rbffd_batch rbffd_batch;
@@ -416,7 +418,8 @@ int rbffd_batch_graph_stats(const rbffd_batch *batch, int64_t *captures, int64_t
 
 /* A request server with continuous batching (the serving workload; the
  * paper solves one problem at a time).  Requests are steady solves
- * (solve_steady semantics, RBFFD_PREC_FP64), submitted from any thread.  A
+ * (solve_steady semantics, RBFFD_PREC_FP64 momentum, any p' solver),
+ * submitted from any thread.  A
  * worker thread owns the context's stream (give the server a context of its
  * own) and loops: admit queued requests while the context's HBM budget
  * allows (a request is admitted by building its problem; one that does not

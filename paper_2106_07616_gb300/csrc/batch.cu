@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "fgmres.cuh"
 #include "ops.cuh"
 #include "problem.cuh"
 
@@ -82,7 +83,8 @@ int BatchScratch::reserve(rbffd_ctx *c, int members) {
     hmem = nullptr;
   }
   cap = std::max(members, 16);
-  maxc = std::max(krylov_batch_max_ctas(ctx, 1), krylov_batch_max_ctas(ctx, 2));
+  maxc = std::max({krylov_batch_max_ctas(ctx, 1), krylov_batch_max_ctas(ctx, 2),
+                   fgmres_batch_max_ctas(ctx)});
   // device: per slot sys args, cta tables, flags, barriers; record
   // pointers, outputs.  The pinned host copy has the same layout.
   size_t o = 0;
@@ -92,7 +94,7 @@ int BatchScratch::reserve(rbffd_ctx *c, int members) {
     return a;
   };
   for (int k = 0; k < NSLOT; ++k) {
-    off_sys[k] = take(sizeof(KrylovArgs) * cap);
+    off_sys[k] = take(std::max(sizeof(KrylovArgs), sizeof(FgmresArgs)) * cap);
     off_cta_sys[k] = take(sizeof(int) * maxc);
     off_cta_first[k] = take(sizeof(int) * cap);
     off_flags[k] = take(sizeof(unsigned int) * maxc);
@@ -166,6 +168,56 @@ static int launch_krylov(BatchScratch &S, int slot, int nr, std::vector<KrylovAr
   return RBFFD_OK;
 }
 
+// One batched flexible-GMRES launch for the pressure-correction systems
+// args[0..m) (filled except nblocks, flags and bar), with table slot `slot`:
+// CTAs split as in launch_krylov.
+static int launch_fgmres(BatchScratch &S, int slot, std::vector<FgmresArgs> &args,
+                         const std::vector<int> &rows) {
+  rbffd_ctx *ctx = S.ctx;
+  const int m = (int)args.size();
+  const int cmax = fgmres_batch_max_ctas(ctx);
+  if (m > cmax) {
+    set_error("batch: %d members exceed the %d co-resident CTAs of one launch", m, cmax);
+    return RBFFD_EINVAL;
+  }
+  std::vector<int> nb(m, 1);
+  long long total = std::accumulate(rows.begin(), rows.end(), 0LL);
+  int left = cmax - m;
+  for (int i = 0; i < m && total > 0; ++i) {
+    int extra = (int)((double)left * rows[i] / (double)total);
+    int cap = (int)((rows[i] * 8LL + KB_NT - 1) / KB_NT);
+    cap = std::min(cap, 160);  // partial sums are laid out for at most 160 CTAs
+    nb[i] = std::max(1, std::min(1 + extra, cap));
+  }
+  int nctas = std::accumulate(nb.begin(), nb.end(), 0);
+  char *hb = (char *)S.hmem;
+  char *db = (char *)S.dmem;
+  FgmresArgs *hsys = (FgmresArgs *)(hb + S.off_sys[slot]);
+  int *hcs = (int *)(hb + S.off_cta_sys[slot]);
+  int *hcf = (int *)(hb + S.off_cta_first[slot]);
+  unsigned int *dflags = (unsigned int *)(db + S.off_flags[slot]);
+  GridBarrier *dbars = (GridBarrier *)(db + S.off_bars[slot]);
+  int c = 0;
+  for (int i = 0; i < m; ++i) {
+    FgmresArgs a = args[i];
+    a.nblocks = nb[i];
+    a.flags = dflags + c;
+    a.bar = dbars + i;
+    hsys[i] = a;
+    hcf[i] = c;
+    for (int k = 0; k < nb[i]; ++k) hcs[c + k] = i;
+    c += nb[i];
+  }
+  RBFFD_CK(cudaMemcpyAsync(db + S.off_sys[slot], hb + S.off_sys[slot],
+                           S.off_flags[slot] - S.off_sys[slot], cudaMemcpyHostToDevice,
+                           ctx->stream));
+  RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * nctas, ctx->stream));
+  RBFFD_CK(cudaMemsetAsync(dbars, 0, sizeof(GridBarrier) * m, ctx->stream));
+  return fgmres_batch_launch(ctx, nctas, (const FgmresArgs *)(db + S.off_sys[slot]),
+                             (const int *)(db + S.off_cta_sys[slot]),
+                             (const int *)(db + S.off_cta_first[slot]));
+}
+
 // Issue one batched outer iteration on the context's stream, ending with
 // the members' results copied to the pinned host table: no host
 // synchronisation, so it can be captured.
@@ -225,12 +277,38 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
   if (!a2.empty()) RBFFD_TRY(launch_krylov(S, 0, 2, a2, rows2));
   if (!a1s.empty()) RBFFD_TRY(launch_krylov(S, 1, 1, a1s, rows1s));
   prof_end(ctx, 0);
-  // p' solves: members with a multigrid hierarchy in one launch, the
-  // Jacobi-preconditioned ones in another
+  // p' solves: one launch per solver -- Jacobi BiCGSTAB, multigrid
+  // BiCGSTAB, flexible GMRES
   std::vector<KrylovArgs> pj, pa;
-  std::vector<int> rj, ra;
+  std::vector<FgmresArgs> pf;
+  std::vector<int> rj, ra, rf;
   for (int i = 0; i < m; ++i) {
     RBFFD_TRY(ops_divergence(P[i], spv[i]));
+    if (P[i]->amgf) {
+      FgmresArgs f;
+      memset(&f, 0, sizeof(f));
+      f.n = P[i]->n;
+      f.q = P[i]->q;
+      f.ldn = P[i]->ldn;
+      f.tpr = 1;
+      f.m = P[i]->fg_m;
+      f.col = P[i]->col;
+      f.val = P[i]->Pp;
+      f.val32 = P[i]->amgf_host.a0;
+      f.b = P[i]->bp;
+      f.x = P[i]->pc;
+      f.r = P[i]->fgR;
+      f.V = P[i]->fgV;
+      f.Z = P[i]->fgZ;
+      f.part = P[i]->fgpart;
+      f.out = P[i]->kout + 2;
+      f.tol = spv[i]->krylov_tol;
+      f.maxit = spv[i]->krylov_maxit;
+      f.amg = P[i]->amgf;
+      pf.push_back(f);
+      rf.push_back(P[i]->n);
+      continue;
+    }
     a1[i].val = P[i]->Pp;
     a1[i].dinv = P[i]->p_dinv;
     a1[i].b[0] = P[i]->bp;
@@ -252,6 +330,7 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
   prof_begin(ctx, 1);
   if (!pj.empty()) RBFFD_TRY(launch_krylov(S, 2, 1, pj, rj));
   if (!pa.empty()) RBFFD_TRY(launch_krylov(S, 3, 1, pa, ra, true));
+  if (!pf.empty()) RBFFD_TRY(launch_fgmres(S, 4, pf, rf));
   prof_end(ctx, 1);
   for (int i = 0; i < m; ++i) {
     RBFFD_TRY(ops_pressure(P[i], spv[i]));
@@ -308,9 +387,8 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
   if (m <= 0) return RBFFD_OK;
   rbffd_ctx *ctx = P[0]->ctx;
   for (int i = 0; i < m; ++i) {
-    if (P[i]->ctx != ctx || P[i]->precision != RBFFD_PREC_FP64 || P[i]->amgf) {
-      set_error("batch: members must share one context, use RBFFD_PREC_FP64 and a Jacobi or "
-                "BiCGSTAB multigrid p' preconditioner");
+    if (P[i]->ctx != ctx || P[i]->precision != RBFFD_PREC_FP64) {
+      set_error("batch: members must share one context and use RBFFD_PREC_FP64 momentum");
       return RBFFD_EINVAL;
     }
   }
@@ -421,10 +499,8 @@ extern "C" int rbffd_batch_create(rbffd_ctx *ctx, int32_t count, rbffd_problem *
   if (!ctx || !out || count < 1 || !members) return RBFFD_EINVAL;
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
-    if (!members[i] || members[i]->ctx != ctx || members[i]->precision != RBFFD_PREC_FP64 ||
-        members[i]->amgf) {
-      set_error("rbffd_batch_create: member %d is null, on another context, not FP64 or on "
-                "flexible GMRES", i);
+    if (!members[i] || members[i]->ctx != ctx || members[i]->precision != RBFFD_PREC_FP64) {
+      set_error("rbffd_batch_create: member %d is null, on another context or not FP64", i);
       return RBFFD_EINVAL;
     }
   }

@@ -10,14 +10,14 @@ namespace rbffd {
 
 // Device + pinned host scratch of batched outer iterations, grown on demand,
 // and the outer iteration captured as a CUDA graph.  Each of the (up to)
-// four Krylov launches of an outer iteration has its own table slot, so
+// five Krylov launches of an outer iteration has its own table slot, so
 // nothing is reused within an iteration and the whole iteration -- row
 // kernels, table copies, barrier resets, the cooperative Krylov launches,
 // the gather of the members' results -- is one stream-ordered sequence that
 // a graph can hold.  The graph is replayed while the members, their builds
 // and their step parameters stay the same, and captured again otherwise.
 struct BatchScratch {
-  static constexpr int NSLOT = 4;
+  static constexpr int NSLOT = 5;
   rbffd_ctx *ctx = nullptr;
   int cap = 0, maxc = 0;
   void *dmem = nullptr, *hmem = nullptr;

@@ -193,8 +193,10 @@ struct FgState {
 
 }  // namespace
 
+// The solve of one system by the nb CTAs that share it; this CTA is number
+// lb among them.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_fgmres(FgmresArgs A) {
+__device__ __forceinline__ void fgmres_body(const FgmresArgs &A, const int lb, const int nb) {
   __shared__ float H[LDH * FG_MAXM];
   __shared__ float cs[FG_MAXM], sn[FG_MAXM], g[FG_MAXM + 1], y[FG_MAXM];
   __shared__ float tot[FG_D];
@@ -202,7 +204,6 @@ __global__ void __launch_bounds__(NT) k_fgmres(FgmresArgs A) {
   __shared__ double stot[16];
   __shared__ double sred[2 * NT];
   __shared__ FgState st;
-  const int lb = blockIdx.x, nb = gridDim.x;
   const int tid = lb * NT + threadIdx.x, stride = nb * NT;
   const int n = A.n, m = A.m;
   const bool leader = threadIdx.x == 0;
@@ -372,6 +373,24 @@ __global__ void __launch_bounds__(NT) k_fgmres(FgmresArgs A) {
   }
 }
 
+template <int NT>
+__global__ void __launch_bounds__(NT) k_fgmres(FgmresArgs A) {
+  fgmres_body<NT>(A, blockIdx.x, gridDim.x);
+}
+
+// Batched launch: system cta_sys[b] owns the consecutive CTAs from
+// cta_first[s]; each synchronises only with its system's CTAs.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_fgmres_batch(const FgmresArgs *__restrict__ sys,
+                                                     const int *__restrict__ cta_sys,
+                                                     const int *__restrict__ cta_first) {
+  __shared__ FgmresArgs A;
+  const int s = cta_sys[blockIdx.x];
+  if (threadIdx.x == 0) A = sys[s];
+  __syncthreads();
+  fgmres_body<NT>(A, blockIdx.x - cta_first[s], A.nblocks);
+}
+
 size_t fgmres_partials_bytes(int nblocks) {
   (void)nblocks;
   return sizeof(double) * 2 * MAXB + sizeof(float) * 2 * FG_D * MAXB;
@@ -389,6 +408,34 @@ int fgmres_max_blocks(rbffd_ctx *ctx) {
   if (cap > ctx->num_sms) cap = ctx->num_sms;
   if (cap > MAXB) cap = MAXB;
   return cap;
+}
+
+int fgmres_batch_max_ctas(rbffd_ctx *ctx) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fgmres_batch<KB_NT>, KB_NT, 0) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * ctx->num_sms;
+}
+
+int fgmres_batch_launch(rbffd_ctx *ctx, int nctas, const FgmresArgs *d_sys,
+                        const int *d_cta_sys, const int *d_cta_first) {
+  if (nctas < 1 || nctas > fgmres_batch_max_ctas(ctx)) {
+    set_error("fgmres_batch_launch: %d CTAs are not co-resident", nctas);
+    return RBFFD_EINVAL;
+  }
+  void *kargs[] = {(void *)&d_sys, (void *)&d_cta_sys, (void *)&d_cta_first};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_fgmres_batch<KB_NT>, dim3(nctas),
+                                              dim3(KB_NT), kargs, 0, ctx->stream);
+  ctx->launches++;
+  if (e != cudaSuccess) {
+    set_error("cooperative launch of k_fgmres_batch failed: %s", cudaGetErrorString(e));
+    return RBFFD_ECUDA;
+  }
+  return RBFFD_OK;
 }
 
 int fgmres_launch(rbffd_ctx *ctx, int nblocks, const FgmresArgs &args) {

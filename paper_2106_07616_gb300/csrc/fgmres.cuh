@@ -12,6 +12,7 @@ constexpr int FG_MAXM = 30;  // largest restart length
 struct FgmresArgs {
   int n, q, ldn, tpr;   // rows, ELL width, leading dimension, threads per row
   int m;                // restart length, 1..FG_MAXM
+  int nblocks;          // CTAs of the system in a batched launch
   const int32_t *col;   // ELL [q][ldn]
   const double *val;    // ELL [q][ldn], FP64: the true residual at each restart
   const float *val32;   // the same values rounded to FP32: the Arnoldi SpMVs
@@ -33,5 +34,10 @@ size_t fgmres_partials_bytes(int nblocks);
 int fgmres_max_blocks(rbffd_ctx *ctx);
 // rows per block fixed by nblocks; threads per row chosen inside
 int fgmres_launch(rbffd_ctx *ctx, int nblocks, const FgmresArgs &args);
+// Batched: d_sys[s] (with nblocks set) owns CTAs d_cta_first[s] ..; KB_NT
+// threads per CTA; at most fgmres_batch_max_ctas CTAs in one launch.
+int fgmres_batch_max_ctas(rbffd_ctx *ctx);
+int fgmres_batch_launch(rbffd_ctx *ctx, int nctas, const FgmresArgs *d_sys,
+                        const int *d_cta_sys, const int *d_cta_first);
 
 }  // namespace rbffd

@@ -45,6 +45,33 @@ def test_server_results_match_solves_alone():
     S.close()
 
 
+def test_server_mixes_pressure_solvers():
+    """Requests with flexible GMRES, multigrid BiCGSTAB and Jacobi p' solvers
+    run in the same batched iterations; each result matches the request
+    solved alone with its own solver."""
+    ctx = rbffd.Context(0)
+    S = rbffd.Server(ctx)
+    fps = requests()
+    pcs = [rbffd.PRECOND_AMG_FGMRES, rbffd.PRECOND_AMG, rbffd.PRECOND_AMG_FGMRES,
+           rbffd.PRECOND_JACOBI]
+    tickets = [S.submit(fp, resid_tol=TOL, max_steps=3000, precond=pc)
+               for fp, pc in zip(fps, pcs)]
+    S.drain()
+    solo_ctx = rbffd.Context(0)
+    for fp, pc, t in zip(fps, pcs, tickets):
+        r = S.poll(t, fields=True)
+        assert r["state"] == 2
+        P = rbffd.Problem(solo_ctx, fp, precond=pc)
+        rc, st = P.solve_steady(fp.dt, resid_tol=TOL, max_steps=3000, check=False)
+        assert r["status"] == rc
+        if rc == 0:
+            assert r["resid"][2] <= TOL and st["resid"][2] <= TOL
+            for k in ("u", "v"):
+                assert rel_l2(r[k], P.get(k)) <= 20 * TOL, (fp.name, pc, k)
+        P.close()
+    S.close()
+
+
 def test_server_admits_by_budget_and_reports_bad_requests():
     ctx = rbffd.Context(0)
     fp = clouds.kovasznay(30, dt=0.4)
