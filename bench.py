@@ -69,6 +69,15 @@ def workload(name: str):
     return fp, desc
 
 
+def solver_codes(args, rbffd):
+    """(precision, p' preconditioner) library codes of the command line."""
+    prec = {"mixed": rbffd.PREC_MIXED, "ff": rbffd.PREC_MIXED_FF,
+            "fp64": rbffd.PREC_FP64}[args.precision]
+    pc = {"jacobi": rbffd.PRECOND_JACOBI, "amg": rbffd.PRECOND_AMG,
+          "fgmres": rbffd.PRECOND_AMG_FGMRES}[args.precond]
+    return prec, pc
+
+
 KRYLOV_PROFILES = {
     # preconditioner: (committed ncu summary, kernel sources it was taken from)
     "jacobi": ("k_bicgstab_fp64_cavity200.md", ("krylov.cu", "krylov_dev.cuh", "common.cuh")),
@@ -131,8 +140,8 @@ def run_batch(args):
     fps = batch_instances(args.count or 256)
     stream = torch.cuda.current_stream()
     ctx = rbffd.Context(0, stream=stream.cuda_stream)
-    pc = rbffd.PRECOND_AMG if args.precond == "amg" else rbffd.PRECOND_JACOBI
-    probs = [rbffd.Problem(ctx, fp, precond=pc) for fp in fps]
+    prec, pc = solver_codes(args, rbffd)
+    probs = [rbffd.Problem(ctx, fp, prec, precond=pc) for fp in fps]
     B = rbffd.Batch(ctx, probs)
     rows = sum(fp.n for fp in fps)
     nnz = sum(fp.n * fp.q for fp in fps)
@@ -143,34 +152,71 @@ def run_batch(args):
         d, its, st = B.iterate(dts)  # every member with its own dt, one launch per solve
         return its, int(np.sum(st == 0))
 
-    for _ in range(args.warmup):
+    def reload_all():
         for P, fp in zip(probs, fps):
-            P.reload(fp, precond=pc)
+            P.reload(fp, prec, precond=pc)
+
+    for _ in range(args.warmup):
+        reload_all()
         iterate_all()
     torch.cuda.synchronize()
-    ctx.profile(True)
+    l0 = ctx.launches
     total_ms, outer = 0.0, 0
     with ClockSampler(0) as clk:
         for k in range(args.steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for P, fp in zip(probs, fps):
-                P.reload(fp, precond=pc)
+            reload_all()
             its, ok = iterate_all()
             e1.record(stream)
             e1.synchronize()
             total_ms += e0.elapsed_time(e1)
             outer += ok
+    launches = (ctx.launches - l0) // max(args.steps, 1)
+    # end to end: the same step from host arrays (the reload copies the
+    # points in) with every member's u, v, p read back
+    e2e_t, e2e_it, d2h = 0.0, 0, 0
+    for k in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reload_all()
+        its, ok = iterate_all()
+        for P in probs:
+            for f in ("u", "v", "p"):
+                d2h += P.get(f).nbytes
+        e2e_t += time.perf_counter() - t0
+        e2e_it += ok
+    h2d = sum(sum(np.asarray(getattr(fp, a)).nbytes for a in ("x", "y", "tag", "nx", "ny",
+                                                                 "ubc", "vbc")) for fp in fps)
+    # the kernel split, from one more step with live kernel timing
+    ctx.profile(True)
+    reload_all()
+    iterate_all()
+    torch.cuda.synchronize()
     kp = ctx.kernel_stat("krylov_p")
     km = ctx.kernel_stat("krylov_mom")
     ctx.profile(False)
     peak, src = read_peaks()
+    kp_gbps = kp["bytes"] / (kp["ms"] / 1e3) / 1e9 if kp["ms"] else None
     out = {"metric": "SIMPLE outer iters/s (batched instances)", "value": outer / (total_ms / 1e3),
            "unit": "instance_outer_iter/s", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "dtype": "f64",
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": ("f32x2+f64" if args.precision == "ff" else
+                     "f32+f64" if args.precision == "mixed" or args.precond == "fgmres"
+                     else "f64"),
+           "data": "synthetic",
+           "e2e": {"value": e2e_it / e2e_t, "unit": "instance_outer_iter/s",
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // 2},
+           "gpu_launches": launches,
+           "roofline": {"bound": "hbm", "achieved": kp_gbps, "peak": peak, "unit": "GB/s",
+                        "frac": kp_gbps / peak if kp_gbps else None, "traffic": None,
+                        "kernel": f"batched pressure-correction launch ({args.precond})"},
+           "cpu_baseline": None,
            "config": {"workload": f"batch{args.count or 256}", "instances": len(fps), "rows": rows,
-                      "precond": args.precond,
+                      "precond": args.precond, "precision": args.precision,
+                      "l2": "inputs (~GBs of operators) exceed the 129 MB L2",
                       "nnz_per_operator": nnz,
                       "description": "Kovasznay/cavity instances, N log-uniform [1k,64k], "
                                      "degree {2..5}, q=2m; step = S1-S3 for all + one outer "
@@ -231,8 +277,8 @@ def run_serve(args):
             time.sleep(wait)
         tickets.append(S.submit(fp, resid_tol=args.resid_tol, max_steps=args.max_steps,
                                 criterion=args.criterion,
-                                precond=(rbffd.PRECOND_AMG if args.precond == "amg"
-                                         else rbffd.PRECOND_JACOBI)))
+                                precond=solver_codes(args, rbffd)[1],
+                                precision=solver_codes(args, rbffd)[0]))
     S.drain()
     wall = time.perf_counter() - t0
     res = [S.poll(t) for t in tickets]

@@ -384,10 +384,11 @@ int rbffd_apply(rbffd_problem *prob, int32_t which, const double *x, double *y);
  * (the same steps as simple_iterate) for each active member: the row kernels
  * per member, and the two Krylov solves of all members in one cooperative
  * launch each, in which every member owns consecutive CTAs and synchronises
- * only with them (one launch per p' solver: Jacobi BiCGSTAB, multigrid
- * BiCGSTAB, flexible GMRES).  Members must be problems of the batch's
- * context with RBFFD_PREC_FP64 momentum solves (any p' solver) and stay
- * owned by the caller (destroy the batch first).  A member
+ * only with them (one launch per solver: FP64, FP32-in-FP64 and
+ * float-float-in-FP64 momentum BiCGSTAB; Jacobi BiCGSTAB, multigrid
+ * BiCGSTAB and flexible GMRES for p').  Members must be problems of the
+ * batch's context -- mixed-precision ones with a multigrid p' solver -- and
+ * stay owned by the caller (destroy the batch first).  A member
  * solved in a batch matches the same member solved alone to the Krylov
  * tolerance (the sums are ordered differently, the fixed point is not). */
 typedef struct rbffd_batch rbffd_batch;
@@ -405,10 +406,10 @@ void rbffd_batch_destroy(rbffd_batch *batch);
 int rbffd_batch_iterate(rbffd_batch *batch, const rbffd_step_params *params, const double *dt,
                         const int32_t *active, double *deltas, rbffd_iter_stats *stats,
                         int32_t *status);
-/* The batched outer iteration is captured as a CUDA graph the first time it
- * runs for a set of active members, their builds and step parameters, and
- * replayed while those stay the same (live kernel timing, rbffd_ctx_profile,
- * launches it directly).  captures / replays / kernels (nullable host
+/* The batched outer iteration is captured as a CUDA graph the second time it
+ * runs in a row for the same active members, builds and step parameters
+ * (the first runs directly), and replayed while those stay the same (live
+ * kernel timing, rbffd_ctx_profile, launches it directly).  captures / replays / kernels (nullable host
  * outputs): graphs captured and replayed so far, and the kernels one replay
  * launches (0 when capture is off).  Errors: RBFFD_EINVAL (null batch). */
 int rbffd_batch_graph_stats(const rbffd_batch *batch, int64_t *captures, int64_t *replays,
@@ -418,8 +419,8 @@ int rbffd_batch_graph_stats(const rbffd_batch *batch, int64_t *captures, int64_t
 
 /* A request server with continuous batching (the serving workload; the
  * paper solves one problem at a time).  Requests are steady solves
- * (solve_steady semantics, RBFFD_PREC_FP64 momentum, any p' solver),
- * submitted from any thread.  A
+ * (solve_steady semantics; FP64 or, with a multigrid p' solver,
+ * mixed-precision momentum), submitted from any thread.  A
  * worker thread owns the context's stream (give the server a context of its
  * own) and loops: admit queued requests while the context's HBM budget
  * allows (a request is admitted by building its problem; one that does not

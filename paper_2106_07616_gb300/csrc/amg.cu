@@ -429,10 +429,15 @@ Csr smoother_matrix(const Csr &A, const std::vector<double> &w) {
 // warp.  A CSR row with g lanes costs one trip for its row pointers and two
 // (indices and values, then the gathers) per AMG_CSR_CHUNK entries a lane;
 // an ELL row with T threads two per kdev::CH entries a thread; a warp that
-// takes more than one pass over its rows pays each pass.  The down phase
-// runs S_l and R~_l side by side (R~_l dealt from the last warp), so their
-// lanes per row are chosen together: side by side when their warps fit in
-// the launch, one after the other otherwise.
+// takes more than one pass over its rows pays each pass.  CSR row groups
+// are spread over the CTAs (warp w of every CTA before warp w + 1), level
+// 0's S runs on each CTA's own ceil(n / nb) rows; the down phase runs S_l
+// and R~_l side by side (R~_l from the last warp of every CTA), so their
+// lanes per row are chosen together: side by side when their warps per CTA
+// fit in one CTA, one after the other otherwise.
+struct Grid {
+  long long nb, wpb;  // CTAs, warps per CTA
+};
 struct Shape {
   int rows = 0, maxlen = 0;
 };
@@ -442,54 +447,56 @@ Shape shape(const Csr &M) {
   for (int i = 0; i < M.n; ++i) s.maxlen = std::max(s.maxlen, M.ptr[i + 1] - M.ptr[i]);
   return s;
 }
-long long csr_warps(const Shape &s, int g) { return (s.rows + 32 / g - 1) / (32 / g); }
-int csr_trips(const Shape &s, int g, long long warps) {
-  const long long per_pass = warps * (32 / g);
-  const int passes = (int)((s.rows + per_pass - 1) / per_pass);
+long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+// warps per CTA a CSR operator keeps busy (spread over the CTAs)
+long long csr_warps(const Shape &s, int g, const Grid &G) {
+  return std::min(G.wpb, ceil_div(ceil_div(s.rows, 32 / g), G.nb));
+}
+int csr_trips(const Shape &s, int g, const Grid &G) {
+  const int passes = (int)ceil_div(s.rows, G.nb * G.wpb * (32 / g));
   const int chunks = std::max(1, (s.maxlen + g * AMG_CSR_CHUNK - 1) / (g * AMG_CSR_CHUNK));
   return passes * (1 + 2 * chunks);
 }
-long long ell_warps(int n, int T) { return (n + 32 / T - 1) / (32 / T); }
-int ell_trips(int n, int q, int T, long long warps) {
-  const long long per_pass = warps * (32 / T);
-  const int passes = (int)((n + per_pass - 1) / per_pass);
+long long ell_warps(int n, int T, const Grid &G) {
+  return std::min(G.wpb, ceil_div(ceil_div(n, G.nb), 32 / T));
+}
+int ell_trips(int n, int q, int T, const Grid &G) {
+  const int passes = (int)ceil_div(ceil_div(n, G.nb), G.wpb * (32 / T));
   const int chunks = std::max(1, (q + T * kdev::CH - 1) / (T * kdev::CH));
   return passes * 2 * chunks;
 }
-int pair_trips(int ta, long long wa, int tb, long long wb, long long warps) {
-  return wa + wb <= warps ? std::max(ta, tb) : ta + tb;
+int pair_trips(int ta, long long wa, int tb, long long wb, const Grid &G) {
+  return wa + wb <= G.wpb ? std::max(ta, tb) : ta + tb;
 }
 // lanes per row of one CSR operator run alone
-int lanes_alone(const Shape &s, long long warps) {
+int lanes_alone(const Shape &s, const Grid &G) {
   int best = 1, bt = 1 << 30;
   for (int g = 1; g <= 32; g *= 2) {
-    const int t = csr_trips(s, g, warps);
+    const int t = csr_trips(s, g, G);
     if (t < bt) bt = t, best = g;
   }
   return best;
 }
 // lanes per row of S_l and R~_l run side by side
-void lanes_pair(const Shape &a, const Shape &b, long long warps, int &ga, int &gb) {
+void lanes_pair(const Shape &a, const Shape &b, const Grid &G, int &ga, int &gb) {
   int bt = 1 << 30;
   long long bw = 0;
   for (int x = 1; x <= 32; x *= 2)
     for (int y = 1; y <= 32; y *= 2) {
-      const long long w = csr_warps(a, x) + csr_warps(b, y);
-      const int t = pair_trips(csr_trips(a, x, warps), csr_warps(a, x), csr_trips(b, y, warps),
-                               csr_warps(b, y), warps);
-      if (t < bt || (t == bt && w < bw)) bt = t, bw = w, ga = x, gb = y;
+      const long long wa = csr_warps(a, x, G), wb = csr_warps(b, y, G);
+      const int t = pair_trips(csr_trips(a, x, G), wa, csr_trips(b, y, G), wb, G);
+      if (t < bt || (t == bt && wa + wb < bw)) bt = t, bw = wa + wb, ga = x, gb = y;
     }
 }
 // threads per row of level 0's S (ELL, q wide) and lanes of R~_0
-void lanes_level0(int n, int q, const Shape &r, long long warps, int &ts, int &gr) {
+void lanes_level0(int n, int q, const Shape &r, const Grid &G, int &ts, int &gr) {
   int bt = 1 << 30;
   long long bw = 0;
   for (int T = 1; T <= 8; ++T)
     for (int y = 1; y <= 32; y *= 2) {
-      const long long w = ell_warps(n, T) + csr_warps(r, y);
-      const int t = pair_trips(ell_trips(n, q, T, warps), ell_warps(n, T), csr_trips(r, y, warps),
-                               csr_warps(r, y), warps);
-      if (t < bt || (t == bt && w < bw)) bt = t, bw = w, ts = T, gr = y;
+      const long long wa = ell_warps(n, T, G), wb = csr_warps(r, y, G);
+      const int t = pair_trips(ell_trips(n, q, T, G), wa, csr_trips(r, y, G), wb, G);
+      if (t < bt || (t == bt && wa + wb < bw)) bt = t, bw = wa + wb, ts = T, gr = y;
     }
 }
 
@@ -652,7 +659,7 @@ int amg_analyze(int n, const int32_t *rowptr, const int32_t *col, const double *
 
 template <typename T>
 int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
-              int nwarps, void **mem, size_t *bytes, const AmgDevT<T> **dev,
+              int nblocks, int wpb, void **mem, size_t *bytes, const AmgDevT<T> **dev,
               AmgDevT<T> *host_view, AmgInfo *info) {
   *mem = nullptr;
   *bytes = 0;
@@ -702,8 +709,8 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
     o.grp = grp;
     return o;
   };
-  // lanes per row for the launch's warps (see Shape)
-  const long long W = nwarps > 0 ? nwarps : 4096;
+  // lanes per row for the launch's CTAs (see Shape)
+  const Grid W{nblocks > 0 ? nblocks : 128, wpb > 0 ? wpb : 32};
   std::vector<int> gS(L, 1), gR(L, 1), gP(L, 1);
   int ts0 = 1;
   for (int l = 0; l + 1 < L; ++l) {
@@ -784,10 +791,10 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
   return RBFFD_OK;
 }
 
-template int amg_build<double>(rbffd_ctx *, int, int, int, const int32_t *, const double *, int,
+template int amg_build<double>(rbffd_ctx *, int, int, int, const int32_t *, const double *, int, int,
                                void **, size_t *, const AmgDevT<double> **, AmgDevT<double> *,
                                AmgInfo *);
-template int amg_build<float>(rbffd_ctx *, int, int, int, const int32_t *, const double *, int,
+template int amg_build<float>(rbffd_ctx *, int, int, int, const int32_t *, const double *, int, int,
                               void **, size_t *, const AmgDevT<float> **, AmgDevT<float> *,
                               AmgInfo *);
 

@@ -77,15 +77,15 @@ struct AmgInfo {
 
 // Build the hierarchy of the packed p' matrix (ELL, column-major [q][ldn],
 // device) on the host and upload it into one device allocation (*mem,
-// *bytes; freed with dev_free).  nwarps: the warps of the launch that will
-// run the cycle (lanes per row are chosen for it; any launch runs it
-// correctly).  *dev receives the device copy of the
+// *bytes; freed with dev_free).  nblocks x wpb: the CTAs and warps per CTA
+// of the launch that will run the cycle (lanes per row are chosen for it;
+// any launch runs it correctly).  *dev receives the device copy of the
 // level table.  Errors: RBFFD_ESINGULAR if the coarsest matrix is singular,
 // RBFFD_ENOMEM, RBFFD_ECUDA.
 // T = double or float: the stored arithmetic of the cycle.
 template <typename T>
 int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
-              int nwarps, void **mem, size_t *bytes, const AmgDevT<T> **dev,
+              int nblocks, int wpb, void **mem, size_t *bytes, const AmgDevT<T> **dev,
               AmgDevT<T> *host_view, AmgInfo *info);
 
 // The host part alone, on a CSR matrix (analysis and tests): level sizes

@@ -100,10 +100,15 @@ __device__ __forceinline__ bool vcycle(const AmgDevT<T> *__restrict__ G, const C
     coarse_solve(G, G->lev[0].n, b0, out, c);
     return sync(c, epoch);
   }
-  // ---- down: the rows of R~_l are dealt from the last warp backwards, so
-  // that they run beside the rows of S_l (dealt from warp 0) instead of
-  // after them whenever the two fit in one pass over the grid's warps
-  const int wrev = c.nwarps - 1 - c.wglobal;
+  // warp orders of the CSR phases: row groups go to warp 0 of every CTA,
+  // then warp 1, ... (wfw: S_l, P~_l, the coarsest rows), or to the last
+  // warp of every CTA first (wbw: R~_l), so the two products of a down
+  // phase run side by side on disjoint warps of every CTA when they fit
+  // (level 0's S runs on each CTA's own rows from warp 0, kdev::cta_rows),
+  // and every phase spreads over all SMs
+  const int wpb = blockDim.x >> 5, nbk = c.nwarps / wpb;
+  const int cta = c.wglobal / wpb, wl = c.wglobal - cta * wpb;
+  const int wfw = wl * nbk + cta, wbw = (wpb - 1 - wl) * nbk + cta;
   for (int l = 0; l + 1 < L; ++l) {
     const AmgLevelT<T> &Lv = G->lev[l];
     const AmgLevelT<T> &Nx = G->lev[l + 1];
@@ -113,11 +118,11 @@ __device__ __forceinline__ bool vcycle(const AmgDevT<T> *__restrict__ G, const C
       const XT *xs[1] = {b0};
       kdev::spmv_rows<1, T>(c.n, c.q, c.ldn, G->ts0, c.col, G->s0, xs, c.wglobal, c.nwarps,
                             [&](int i, const T *sb) { z[i] = sb[0]; });
-      csr_rows(Lv.R, Nx.n, b0, wrev, c.nwarps, [&](int k, T t) { bn[k] = t; });
+      csr_rows(Lv.R, Nx.n, b0, wbw, c.nwarps, [&](int k, T t) { bn[k] = t; });
     } else {
       const T *bl = Lv.b;
-      csr_rows(Lv.S, Lv.n, bl, c.wglobal, c.nwarps, [&](int i, T t) { z[i] = t; });
-      csr_rows(Lv.R, Nx.n, bl, wrev, c.nwarps, [&](int k, T t) { bn[k] = t; });
+      csr_rows(Lv.S, Lv.n, bl, wfw, c.nwarps, [&](int i, T t) { z[i] = t; });
+      csr_rows(Lv.R, Nx.n, bl, wbw, c.nwarps, [&](int k, T t) { bn[k] = t; });
     }
     if (!sync(c, epoch)) return false;
   }
@@ -133,11 +138,11 @@ __device__ __forceinline__ bool vcycle(const AmgDevT<T> *__restrict__ G, const C
     const T *z = Lv.z;
     if (l == 0) {
       csr_rows(
-          Lv.P, Lv.n, G->lev[1].y, c.wglobal, c.nwarps, [&](int i, T t) { out[i] = OT(t); }, z);
+          Lv.P, Lv.n, G->lev[1].y, wfw, c.nwarps, [&](int i, T t) { out[i] = OT(t); }, z);
     } else {
       T *res = Lv.y;
       csr_rows(
-          Lv.P, Lv.n, G->lev[l + 1].y, c.wglobal, c.nwarps, [&](int i, T t) { res[i] = t; }, z);
+          Lv.P, Lv.n, G->lev[l + 1].y, wfw, c.nwarps, [&](int i, T t) { res[i] = t; }, z);
     }
     if (!sync(c, epoch)) return false;
   }

@@ -84,7 +84,10 @@ int BatchScratch::reserve(rbffd_ctx *c, int members) {
   }
   cap = std::max(members, 16);
   maxc = std::max({krylov_batch_max_ctas(ctx, 1), krylov_batch_max_ctas(ctx, 2),
-                   fgmres_batch_max_ctas(ctx)});
+                   fgmres_batch_max_ctas(ctx), krylov_ir_batch_max_ctas(ctx, 1, INNER_F32),
+                   krylov_ir_batch_max_ctas(ctx, 2, INNER_F32),
+                   krylov_ir_batch_max_ctas(ctx, 1, INNER_FF),
+                   krylov_ir_batch_max_ctas(ctx, 2, INNER_FF)});
   // device: per slot sys args, cta tables, flags, barriers; record
   // pointers, outputs.  The pinned host copy has the same layout.
   size_t o = 0;
@@ -94,7 +97,7 @@ int BatchScratch::reserve(rbffd_ctx *c, int members) {
     return a;
   };
   for (int k = 0; k < NSLOT; ++k) {
-    off_sys[k] = take(std::max(sizeof(KrylovArgs), sizeof(FgmresArgs)) * cap);
+    off_sys[k] = take(std::max({sizeof(KrylovArgs), sizeof(FgmresArgs), sizeof(MixedArgs)}) * cap);
     off_cta_sys[k] = take(sizeof(int) * maxc);
     off_cta_first[k] = take(sizeof(int) * cap);
     off_flags[k] = take(sizeof(unsigned int) * maxc);
@@ -144,10 +147,11 @@ static int launch_krylov(BatchScratch &S, int slot, int nr, std::vector<KrylovAr
   for (int i = 0; i < m; ++i) {
     KrylovArgs a = args[i];
     a.nblocks = nb[i];
-    const long long warps = (long long)nb[i] * (KB_NT / 32);
+    // threads per row: cover a CTA's rows (kdev::cta_rows) in one pass
+    const long long R = (a.n + (long long)nb[i] - 1) / nb[i];
     int T = 1;
     for (int t = 2; t <= 8; ++t)
-      if ((long long)(32 / t) * warps >= a.n) T = t;
+      if ((long long)(32 / t) * (KB_NT / 32) >= R) T = t;
     a.tpr = T;
     a.flags = dflags + c;
     a.bar = dbars + i;
@@ -166,6 +170,62 @@ static int launch_krylov(BatchScratch &S, int slot, int nr, std::vector<KrylovAr
                                 (const int *)(db + S.off_cta_sys[slot]),
                                 (const int *)(db + S.off_cta_first[slot]), amg));
   return RBFFD_OK;
+}
+
+// One batched mixed-precision launch (FP32 or float-float BiCGSTAB inside
+// FP64 refinement) for the momentum systems args[0..m) of one inner
+// arithmetic, with table slot `slot`: CTAs split as in launch_krylov.
+static int launch_mixed(BatchScratch &S, int slot, int nr, int inner,
+                        std::vector<MixedArgs> &args, const std::vector<int> &rows) {
+  rbffd_ctx *ctx = S.ctx;
+  const int m = (int)args.size();
+  const int cmax = krylov_ir_batch_max_ctas(ctx, nr, inner);
+  if (m > cmax) {
+    set_error("batch: %d members exceed the %d co-resident CTAs of one launch", m, cmax);
+    return RBFFD_EINVAL;
+  }
+  std::vector<int> nb(m, 1);
+  long long total = std::accumulate(rows.begin(), rows.end(), 0LL);
+  int left = cmax - m;
+  for (int i = 0; i < m && total > 0; ++i) {
+    int extra = (int)((double)left * rows[i] / (double)total);
+    int cap = std::min(args[i].nblocks, (int)((rows[i] * 8LL + KB_NT - 1) / KB_NT));
+    cap = std::min(cap, 160);
+    nb[i] = std::max(1, std::min(1 + extra, cap));
+  }
+  int nctas = std::accumulate(nb.begin(), nb.end(), 0);
+  char *hb = (char *)S.hmem;
+  char *db = (char *)S.dmem;
+  MixedArgs *hsys = (MixedArgs *)(hb + S.off_sys[slot]);
+  int *hcs = (int *)(hb + S.off_cta_sys[slot]);
+  int *hcf = (int *)(hb + S.off_cta_first[slot]);
+  unsigned int *dflags = (unsigned int *)(db + S.off_flags[slot]);
+  GridBarrier *dbars = (GridBarrier *)(db + S.off_bars[slot]);
+  int c = 0;
+  for (int i = 0; i < m; ++i) {
+    MixedArgs a = args[i];
+    a.nblocks = nb[i];
+    // threads per row: cover a CTA's rows (kdev::cta_rows) in one pass
+    const long long R = (a.n + (long long)nb[i] - 1) / nb[i];
+    int T = 1;
+    for (int t = 2; t <= 8; ++t)
+      if ((long long)(32 / t) * (KB_NT / 32) >= R) T = t;
+    a.tpr = T;
+    a.flags = dflags + c;
+    a.bar = dbars + i;
+    hsys[i] = a;
+    hcf[i] = c;
+    for (int k = 0; k < nb[i]; ++k) hcs[c + k] = i;
+    c += nb[i];
+  }
+  RBFFD_CK(cudaMemcpyAsync(db + S.off_sys[slot], hb + S.off_sys[slot],
+                           S.off_flags[slot] - S.off_sys[slot], cudaMemcpyHostToDevice,
+                           ctx->stream));
+  RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * nctas, ctx->stream));
+  RBFFD_CK(cudaMemsetAsync(dbars, 0, sizeof(GridBarrier) * m, ctx->stream));
+  return krylov_ir_batch_launch(ctx, nr, inner, nctas, (const MixedArgs *)(db + S.off_sys[slot]),
+                                (const int *)(db + S.off_cta_sys[slot]),
+                                (const int *)(db + S.off_cta_first[slot]));
 }
 
 // One batched flexible-GMRES launch for the pressure-correction systems
@@ -228,9 +288,81 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
   // solves of all members (and one for the single-RHS pairs, if any)
   std::vector<KrylovArgs> a2, a1s, a1(m);
   std::vector<int> rows2, rows1s;
+  // mixed-precision members by inner arithmetic (0 FP32, 1 float-float)
+  std::vector<MixedArgs> x2[2], x1s[2];
+  std::vector<int> xr2[2], xr1s[2];
   for (int i = 0; i < m; ++i) {
     const rbffd_step_params *sp = spv[i];
     RBFFD_TRY(ops_momentum(P[i], sp));
+    if (P[i]->precision != RBFFD_PREC_FP64) {
+      rbffd_problem *Q = P[i];
+      const int ia = Q->inner == INNER_FF ? 1 : 0;
+      RBFFD_TRY(ops_to_inner(Q, Q->Am, Q->Ain, (int64_t)Q->ldn * Q->q));
+      RBFFD_TRY(ops_to_inner(Q, Q->m_dinv, Q->mdin, Q->ldn));
+      MixedArgs x;
+      memset(&x, 0, sizeof(x));
+      x.inner = Q->inner;
+      x.n = Q->n;
+      x.q = Q->q;
+      x.ldn = Q->ldn;
+      x.col = Q->col;
+      x.part64 = Q->part64;
+      x.partin = Q->partin;
+      x.tol = sp->krylov_tol;
+      x.maxit = sp->krylov_maxit;
+      x.inner_tol = sp->inner_tol > 0 ? sp->inner_tol : 1e-3;
+      x.inner_maxit = sp->inner_maxit > 0 ? sp->inner_maxit : 4000;
+      x.max_sweeps = 60;
+      x.val64 = Q->Am;
+      x.valin = Q->Ain;
+      x.dinvin = Q->mdin;
+      x.b[0] = Q->bu;
+      x.b[1] = Q->bv;
+      x.x[0] = Q->ut;
+      x.x[1] = Q->vt;
+      x.w[0] = Q->mv[0];
+      x.w[1] = Q->mv[1];
+      x.out = Q->kout;
+      x.nblocks = std::max(Q->kblocks1, Q->kblocks2);  // partial-sum capacity
+      if (!Q->has_sym) {
+        x2[ia].push_back(x);
+        xr2[ia].push_back(Q->n);
+      } else {
+        // the u~ and v~ systems differ on symmetry lines: two single-RHS
+        // systems, the second on its own partial sums (second half)
+        RBFFD_TRY(ops_to_inner(Q, Q->Am2, Q->Ain2, (int64_t)Q->ldn * Q->q));
+        RBFFD_TRY(ops_to_inner(Q, Q->m_dinv2, Q->mdin2, Q->ldn));
+        MixedArgs xu = x;
+        xu.b[1] = nullptr;
+        xu.x[1] = nullptr;
+        MixedArgs xv = xu;
+        xv.val64 = Q->Am2;
+        xv.valin = Q->Ain2;
+        xv.dinvin = Q->mdin2;
+        xv.b[0] = Q->bv;
+        xv.x[0] = Q->vt;
+        xv.w[0] = Q->mv[1];
+        xv.out = Q->kout + 1;
+        xv.part64 = Q->part64 + krylov_ir_partials64(1, x.nblocks);
+        xv.partin = (char *)Q->partin + krylov_ir_partials_inner_bytes(1, x.nblocks, Q->inner);
+        x1s[ia].push_back(xu);
+        x1s[ia].push_back(xv);
+        xr1s[ia].push_back(Q->n);
+        xr1s[ia].push_back(Q->n);
+      }
+      // the fields a multigrid-BiCGSTAB p' launch takes from a1[i]
+      KrylovArgs a;
+      memset(&a, 0, sizeof(a));
+      a.n = Q->n;
+      a.q = Q->q;
+      a.ldn = Q->ldn;
+      a.col = Q->col;
+      a.part = Q->part;
+      a.tol = sp->krylov_tol;
+      a.maxit = sp->krylov_maxit;
+      a1[i] = a;
+      continue;
+    }
     KrylovArgs a;
     memset(&a, 0, sizeof(a));
     a.n = P[i]->n;
@@ -276,6 +408,11 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
   prof_begin(ctx, 0);
   if (!a2.empty()) RBFFD_TRY(launch_krylov(S, 0, 2, a2, rows2));
   if (!a1s.empty()) RBFFD_TRY(launch_krylov(S, 1, 1, a1s, rows1s));
+  for (int ia = 0; ia < 2; ++ia) {
+    const int inner = ia ? INNER_FF : INNER_F32;
+    if (!x2[ia].empty()) RBFFD_TRY(launch_mixed(S, 5 + 2 * ia, 2, inner, x2[ia], xr2[ia]));
+    if (!x1s[ia].empty()) RBFFD_TRY(launch_mixed(S, 6 + 2 * ia, 1, inner, x1s[ia], xr1s[ia]));
+  }
   prof_end(ctx, 0);
   // p' solves: one launch per solver -- Jacobi BiCGSTAB, multigrid
   // BiCGSTAB, flexible GMRES
@@ -387,8 +524,10 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
   if (m <= 0) return RBFFD_OK;
   rbffd_ctx *ctx = P[0]->ctx;
   for (int i = 0; i < m; ++i) {
-    if (P[i]->ctx != ctx || P[i]->precision != RBFFD_PREC_FP64) {
-      set_error("batch: members must share one context and use RBFFD_PREC_FP64 momentum");
+    if (P[i]->ctx != ctx ||
+        (P[i]->precision != RBFFD_PREC_FP64 && !P[i]->amg && !P[i]->amgf)) {
+      set_error("batch: members must share one context; mixed-precision members need a "
+                "multigrid p' solver");
       return RBFFD_EINVAL;
     }
   }
@@ -396,8 +535,10 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
   // (their rows differ there), so a launch may hold up to 2m systems
   RBFFD_TRY(S.reserve(ctx, 2 * m));
   // replay the captured iteration when it was captured for exactly these
-  // members, builds and step parameters; otherwise capture it again (live
-  // kernel timing records events per phase: launched directly)
+  // members, builds and step parameters.  A new set runs directly once and
+  // is captured when it comes back, so one-off iterations (a rebuild before
+  // every call) pay no capture.  Live kernel timing records events per
+  // phase: launched directly.
   const bool want = !ctx->prof && !S.graph_off;
   std::vector<uint64_t> key;
   if (want) key = graph_key(P, m, spv);
@@ -407,8 +548,10 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
     S.replays++;
   } else {
     S.drop_graph();
+    const bool again = want && key == S.seen;
+    if (want && !again) S.seen = key;
     bool done = false;
-    if (want && cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+    if (again && cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
       const int64_t l0 = ctx->launches;
       const int rc = issue_batch(S, P, m, spv);
       cudaGraph_t g = nullptr;
@@ -499,8 +642,10 @@ extern "C" int rbffd_batch_create(rbffd_ctx *ctx, int32_t count, rbffd_problem *
   if (!ctx || !out || count < 1 || !members) return RBFFD_EINVAL;
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
-    if (!members[i] || members[i]->ctx != ctx || members[i]->precision != RBFFD_PREC_FP64) {
-      set_error("rbffd_batch_create: member %d is null, on another context or not FP64", i);
+    if (!members[i] || members[i]->ctx != ctx ||
+        (members[i]->precision != RBFFD_PREC_FP64 && !members[i]->amg && !members[i]->amgf)) {
+      set_error("rbffd_batch_create: member %d is null, on another context, or mixed-precision "
+                "with a Jacobi p' solver", i);
       return RBFFD_EINVAL;
     }
   }

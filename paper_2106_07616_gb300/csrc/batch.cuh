@@ -10,14 +10,15 @@ namespace rbffd {
 
 // Device + pinned host scratch of batched outer iterations, grown on demand,
 // and the outer iteration captured as a CUDA graph.  Each of the (up to)
-// five Krylov launches of an outer iteration has its own table slot, so
+// nine Krylov launches of an outer iteration has its own table slot, so
 // nothing is reused within an iteration and the whole iteration -- row
 // kernels, table copies, barrier resets, the cooperative Krylov launches,
 // the gather of the members' results -- is one stream-ordered sequence that
-// a graph can hold.  The graph is replayed while the members, their builds
-// and their step parameters stay the same, and captured again otherwise.
+// a graph can hold.  A set of members, builds and step parameters runs
+// directly the first time, is captured the second time, and is replayed
+// from then on while it stays the same.
 struct BatchScratch {
-  static constexpr int NSLOT = 5;
+  static constexpr int NSLOT = 9;
   rbffd_ctx *ctx = nullptr;
   int cap = 0, maxc = 0;
   void *dmem = nullptr, *hmem = nullptr;
@@ -29,6 +30,7 @@ struct BatchScratch {
   size_t off_recs = 0, off_kouts = 0, off_out = 0;
   cudaGraphExec_t exec = nullptr;
   std::vector<uint64_t> key;     // what the graph was captured for
+  std::vector<uint64_t> seen;    // the last set run directly (captured when it returns)
   int64_t graph_launches = 0;    // kernels one replay launches
   bool graph_off = false;        // capture failed once: launch directly
   int64_t replays = 0, captures = 0;

@@ -473,11 +473,14 @@ int krylov_blocks_for(rbffd_ctx *ctx, int n, int nr) {
 
 // Largest T <= 8 whose groups (32 / T per warp) still cover every row in
 // one pass; 1 when the rows outnumber the threads.
+// threads per row: the most that still cover a CTA's ceil(n / nblocks)
+// rows (kdev::cta_rows) in one pass of its warps
 int krylov_threads_per_row(int n, int nr, int nblocks) {
-  const long long warps = (long long)nblocks * nt_for(nr) / 32;
+  const long long wpb = nt_for(nr) / 32;
+  const long long R = (n + (long long)nblocks - 1) / nblocks;
   int best = 1;
   for (int T = 2; T <= 8; ++T)
-    if ((long long)(32 / T) * warps >= n) best = T;
+    if ((32 / T) * wpb >= R) best = T;
   return best;
 }
 

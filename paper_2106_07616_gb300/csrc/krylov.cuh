@@ -53,6 +53,7 @@ struct MixedVecs {
 struct MixedArgs {
   int n, q, ldn, tpr;
   int inner;             // INNER_F32 or INNER_FF
+  int nblocks;           // CTAs of the system in a batched launch
   const int32_t *col;
   const double *val64;   // FP64 operator (residuals)
   const void *valin;     // operator in the inner arithmetic
@@ -75,6 +76,12 @@ struct MixedArgs {
 int krylov_max_blocks(rbffd_ctx *ctx, int nr);
 int krylov_ir_max_blocks(rbffd_ctx *ctx, int nr, int inner);
 int krylov_ir_launch(rbffd_ctx *ctx, int nr, int nblocks, const MixedArgs &args);
+// Batched: d_sys[s] (nblocks, flags, bar set) owns CTAs d_cta_first[s] ..;
+// KB_NT threads per CTA; every system of one launch has the same inner
+// arithmetic.
+int krylov_ir_batch_max_ctas(rbffd_ctx *ctx, int nr, int inner);
+int krylov_ir_batch_launch(rbffd_ctx *ctx, int nr, int inner, int nctas, const MixedArgs *d_sys,
+                           const int *d_cta_sys, const int *d_cta_first);
 size_t krylov_ir_partials64(int nr, int nblocks);
 size_t krylov_ir_partials_inner_bytes(int nr, int nblocks, int inner);
 int krylov_blocks_for(rbffd_ctx *ctx, int n, int nr);

@@ -34,13 +34,28 @@ __device__ __forceinline__ ff ld_cg(const ff *p) {
   return ff(t.x, t.y);
 }
 
+// The contiguous rows [r0, r1) of the CTA that warp `wglobal` belongs to
+// (warps are numbered CTA-major: wglobal = cta * wpb + warp), n rows shared
+// evenly by the nwarps / wpb CTAs.  Spreading rows evenly over the CTAs
+// keeps every SM busy: dealing them from warp 0 onwards left whole SMs idle
+// and doubled the FP64 work of the busy ones.
+__device__ __forceinline__ void cta_rows(int n, int wglobal, int nwarps, int wpb, int &r0,
+                                         int &r1, int &w) {
+  const int cta = wglobal / wpb, nc = nwarps / wpb;
+  const int R = (n + nc - 1) / nc;
+  w = wglobal - cta * wpb;
+  r0 = min(n, cta * R);
+  r1 = min(n, r0 + R);
+}
+
 // y_k(i) = sum_j A(i,j) x_k(j), accumulated in AT, T threads per row
-// (T = 1..8, any value; the last 32 mod T lanes of a warp idle).  The
-// column indices and values of a chunk of CH entries are loaded first, then
-// the CH gathers, so a row costs two dependent memory round trips per
-// chunk.  f(i, y) runs on the group leader; all 32 lanes execute the same
-// trip count and shuffles.  Gathered vectors go through __ldcg (coherent
-// L2) because other blocks of the same launch write them.
+// (T = 1..8, any value; the last 32 mod T lanes of a warp idle), over each
+// CTA's own rows (cta_rows).  The column indices and values of a chunk of
+// CH entries are loaded first, then the CH gathers, so a row costs two
+// dependent memory round trips per chunk.  f(i, y) runs on the group
+// leader; all 32 lanes execute the same trip count and shuffles.  Gathered
+// vectors go through __ldcg (coherent L2) because other blocks of the same
+// launch write them.
 template <int NR, typename AT, typename VT, typename XT, typename F>
 __device__ __forceinline__ void spmv_rows(int n, int q, int ldn, int T,
                                           const int32_t *__restrict__ col,
@@ -51,9 +66,12 @@ __device__ __forceinline__ void spmv_rows(int n, int q, int ldn, int T,
   const int g = lane / T;
   const int lg = lane - g * T;
   const bool active = g < gpw;
-  for (int base = wglobal * gpw; base < n; base += nwarps * gpw) {
+  const int wpb = blockDim.x >> 5;
+  int r0, r1, w;
+  cta_rows(n, wglobal, nwarps, wpb, r0, r1, w);
+  for (int base = r0 + w * gpw; base < r1; base += wpb * gpw) {
     const int i = base + g;
-    const bool valid = active && i < n;
+    const bool valid = active && i < r1;
     AT s[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) s[k] = AT(0);

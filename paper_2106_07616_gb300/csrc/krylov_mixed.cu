@@ -52,9 +52,12 @@ __device__ __forceinline__ void spmv_rows_ia(int n, int q, int ldn, int T,
   const int g = lane / T;
   const int lg = lane - g * T;
   const bool active = g < gpw;
-  for (int base = wglobal * gpw; base < n; base += nwarps * gpw) {
+  const int wpb = blockDim.x >> 5;
+  int r0, r1, w;
+  kdev::cta_rows(n, wglobal, nwarps, wpb, r0, r1, w);
+  for (int base = r0 + w * gpw; base < r1; base += wpb * gpw) {
     const int i = base + g;
-    const bool valid = active && i < n;
+    const bool valid = active && i < r1;
     AC s[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) s[k] = IA::zero();
@@ -105,9 +108,12 @@ __device__ __forceinline__ void spmv_rows_gen(int n, int q, int ldn, int T,
   const int gi = lane / T;
   const int lg = lane - gi * T;
   const bool active = gi < gpw;
-  for (int base = wglobal * gpw; base < n; base += nwarps * gpw) {
+  const int wpb = blockDim.x >> 5;
+  int r0, r1, w;
+  kdev::cta_rows(n, wglobal, nwarps, wpb, r0, r1, w);
+  for (int base = r0 + w * gpw; base < r1; base += wpb * gpw) {
     const int i = base + gi;
-    const bool valid = active && i < n;
+    const bool valid = active && i < r1;
     AC s[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) s[k] = IA::zero();
@@ -142,8 +148,10 @@ __device__ __forceinline__ void spmv_rows_gen(int n, int q, int ldn, int T,
   }
 }
 
+// The solve of one system (NR right-hand sides) by the nb CTAs that share
+// it; this CTA is number lb among them.
 template <int NR, int NT, class IA>
-__global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
+__device__ __forceinline__ void bicgstab_ir_body(const MixedArgs &A, const int lb, const int nb) {
   using S = typename IA::S;
   using AC = typename IA::A;
   using PT = typename IA::P;
@@ -160,11 +168,10 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
   __shared__ double st64[16];
   __shared__ IRS ks[NR];
   __shared__ int s_any;
-  const int tid = blockIdx.x * NT + threadIdx.x;
-  const int stride = gridDim.x * NT;
+  const int tid = lb * NT + threadIdx.x;
+  const int stride = nb * NT;
   const int wglobal = tid >> 5, nwarps = stride >> 5;
   const int n = A.n, q = A.q, ldn = A.ldn, T = A.tpr;
-  const int nb = gridDim.x;
   unsigned int epoch = 1;
   const bool leader = threadIdx.x == 0;
   int *err = &A.bar->err;
@@ -241,9 +248,9 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
         outs[2 * k] = part[k] ? P64(M_BB, k) : nullptr;
         outs[2 * k + 1] = part[k] ? P64(M_RR, k) : nullptr;
       }
-      kdev::block_partials<NT, 2 * NR>(acc, sr64, outs);
+      kdev::block_partials<NT, 2 * NR>(acc, sr64, outs, lb);
       double tot[2 * NR];
-      ok = kdev::exchange<2 * NR>(A.flags, err, epoch++, outs, tot, st64);
+      ok = kdev::exchange<2 * NR>(A.flags, err, epoch++, outs, tot, st64, lb, nb);
       if (!ok) break;
       if (leader) {
         int any = 0;
@@ -355,9 +362,9 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
           outs[2 * k] = run[k] ? P32(F_RHV, k) : nullptr;
           outs[2 * k + 1] = run[k] ? P32(F_RR, k) : nullptr;
         }
-        kdev::block_partials<NT, 2 * NR>(pa, sr32, outs);
+        kdev::block_partials<NT, 2 * NR>(pa, sr32, outs, lb);
         PT tot[2 * NR];
-        ok = kdev::exchange<2 * NR>(A.flags, err, epoch++, outs, tot, st32);
+        ok = kdev::exchange<2 * NR>(A.flags, err, epoch++, outs, tot, st32, lb, nb);
         if (!ok) break;
         if (leader) {
 #pragma unroll
@@ -430,9 +437,9 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
           outs[5 * k + 3] = run[k] ? P32(F_RHS, k) : nullptr;
           outs[5 * k + 4] = run[k] ? P32(F_RHT, k) : nullptr;
         }
-        kdev::block_partials<NT, 5 * NR>(pa, sr32, outs);
+        kdev::block_partials<NT, 5 * NR>(pa, sr32, outs, lb);
         PT tot[5 * NR];
-        ok = kdev::exchange<5 * NR>(A.flags, err, epoch++, outs, tot, st32);
+        ok = kdev::exchange<5 * NR>(A.flags, err, epoch++, outs, tot, st32, lb, nb);
         if (!ok) break;
         if (leader) {
 #pragma unroll
@@ -475,12 +482,13 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
           CF alp[NR];
 #pragma unroll
           for (int k = 0; k < NR; ++k) alp[k] = IA::coef(ks[k].alpha);
-          const int stride_g = (32 / T) * nwarps;
           const int lane = threadIdx.x & 31, gi = lane / T, lg = lane - gi * T;
           // the rows this thread owns are the ones its SpMV leader lane wrote
-          for (int base = wglobal * (32 / T); base < n; base += stride_g) {
+          int r0, r1, wb;
+          kdev::cta_rows(n, wglobal, nwarps, NT >> 5, r0, r1, wb);
+          for (int base = r0 + wb * (32 / T); base < r1; base += (32 / T) * (NT >> 5)) {
             const int i = base + gi;
-            if (gi < 32 / T && lg == 0 && i < n) {
+            if (gi < 32 / T && lg == 0 && i < r1) {
               const S di = IA::ldg(dinv + i);
 #pragma unroll
               for (int k = 0; k < NR; ++k)
@@ -500,9 +508,11 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
       {
         // d of a row was written by its SpMV leader lane: update x there too
         const int lane = threadIdx.x & 31, gi = lane / T, lg = lane - gi * T;
-        for (int base = wglobal * (32 / T); base < n; base += (32 / T) * nwarps) {
+        int r0, r1, wb;
+        kdev::cta_rows(n, wglobal, nwarps, NT >> 5, r0, r1, wb);
+        for (int base = r0 + wb * (32 / T); base < r1; base += (32 / T) * (NT >> 5)) {
           const int i = base + gi;
-          if (gi < 32 / T && lg == 0 && i < n) {
+          if (gi < 32 / T && lg == 0 && i < r1) {
 #pragma unroll
             for (int k = 0; k < NR; ++k)
               if (upd[k]) A.x[k][i] = A.x[k][i] + IA::to_double(d[k][i]);
@@ -514,12 +524,12 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
         for (int k = 0; k < NR; ++k)
           if (upd[k]) ks[k].sweeps++;
       }
-      ok = kdev::exchange<0, double>(A.flags, err, epoch++, nullptr, nullptr, st64);
+      ok = kdev::exchange<0, double>(A.flags, err, epoch++, nullptr, nullptr, st64, lb, nb);
       if (!ok) break;
     }
   }
 
-  if (blockIdx.x == 0 && leader) {
+  if (lb == 0 && leader) {
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
       A.out[k].iters = ks[k].it;
@@ -528,6 +538,24 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
       A.out[k].relres = ks[k].relres;
     }
   }
+}
+
+template <int NR, int NT, class IA>
+__global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
+  bicgstab_ir_body<NR, NT, IA>(A, blockIdx.x, gridDim.x);
+}
+
+// Batched launch: system cta_sys[b] owns the consecutive CTAs from
+// cta_first[s] and synchronises only with them.
+template <int NR, int NT, class IA>
+__global__ void __launch_bounds__(NT) k_bicgstab_ir_batch(const MixedArgs *__restrict__ sys,
+                                                          const int *__restrict__ cta_sys,
+                                                          const int *__restrict__ cta_first) {
+  __shared__ MixedArgs A;
+  const int s = cta_sys[blockIdx.x];
+  if (threadIdx.x == 0) A = sys[s];
+  __syncthreads();
+  bicgstab_ir_body<NR, NT, IA>(A, blockIdx.x - cta_first[s], A.nblocks);
 }
 
 namespace {
@@ -574,6 +602,45 @@ int krylov_ir_launch(rbffd_ctx *ctx, int nr, int nblocks, const MixedArgs &args)
   ctx->launches++;
   if (e != cudaSuccess) {
     set_error("cooperative launch of k_bicgstab_ir failed: %s", cudaGetErrorString(e));
+    return RBFFD_ECUDA;
+  }
+  return RBFFD_OK;
+}
+
+namespace {
+template <int NR, class IA>
+const void *ir_batch_fn() {
+  return (const void *)k_bicgstab_ir_batch<NR, KB_NT, IA>;
+}
+const void *ir_batch_kernel(int nr, int inner) {
+  if (inner == INNER_FF) return nr == 1 ? ir_batch_fn<1, ArithFF>() : ir_batch_fn<2, ArithFF>();
+  return nr == 1 ? ir_batch_fn<1, ArithF32>() : ir_batch_fn<2, ArithF32>();
+}
+}  // namespace
+
+int krylov_ir_batch_max_ctas(rbffd_ctx *ctx, int nr, int inner) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ir_batch_kernel(nr, inner), KB_NT,
+                                                    0) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * ctx->num_sms;
+}
+
+int krylov_ir_batch_launch(rbffd_ctx *ctx, int nr, int inner, int nctas, const MixedArgs *d_sys,
+                           const int *d_cta_sys, const int *d_cta_first) {
+  if (nctas < 1 || nctas > krylov_ir_batch_max_ctas(ctx, nr, inner)) {
+    set_error("krylov_ir_batch_launch: %d CTAs are not co-resident", nctas);
+    return RBFFD_EINVAL;
+  }
+  void *kargs[] = {(void *)&d_sys, (void *)&d_cta_sys, (void *)&d_cta_first};
+  cudaError_t e = cudaLaunchCooperativeKernel(ir_batch_kernel(nr, inner), dim3(nctas),
+                                              dim3(KB_NT), kargs, 0, ctx->stream);
+  ctx->launches++;
+  if (e != cudaSuccess) {
+    set_error("cooperative launch of k_bicgstab_ir_batch failed: %s", cudaGetErrorString(e));
     return RBFFD_ECUDA;
   }
   return RBFFD_OK;

@@ -160,12 +160,12 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
   free_amg(P);
   P->precond = d->precond;
   if (P->precond == RBFFD_PRECOND_AMG) {
-    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, P->kblocks1 * 32, &P->amg_mem,
+    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, P->kblocks1, 32, &P->amg_mem,
                         &P->amg_bytes, &P->amg, &P->amg_host, &P->amg_info));
   } else if (P->precond == RBFFD_PRECOND_AMG_FGMRES) {
     P->fg_blocks = fgmres_max_blocks(ctx);
     if (P->fg_blocks > P->kblocks1) P->fg_blocks = P->kblocks1;
-    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, P->fg_blocks * 32, &P->amg_mem,
+    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, P->fg_blocks, 32, &P->amg_mem,
                         &P->amg_bytes, &P->amgf, &P->amgf_host, &P->amg_info));
     // FP64 restart residual and partial sums, then the FP32 Arnoldi basis
     // (m + 1 vectors) and directions (m)

@@ -215,9 +215,8 @@ extern "C" int rbffd_server_submit(rbffd_server *s, const rbffd_problem_desc *d,
   if (!s || !d || !sp || !ticket || d->n < 1 || !d->x || !d->y || !d->tag || !d->nx || !d->ny ||
       !d->ubc || !d->vbc || sp->max_outer < 1 || sp->max_steps < 1 || !(sp->dt > 0))
     return RBFFD_EINVAL;
-  if (d->precision != RBFFD_PREC_FP64) {
-    set_error("rbffd_server_submit: requests run their momentum solves in RBFFD_PREC_FP64 "
-              "(any p' solver)");
+  if (d->precision != RBFFD_PREC_FP64 && d->precond == RBFFD_PRECOND_JACOBI) {
+    set_error("rbffd_server_submit: a mixed-precision request needs a multigrid p' solver");
     return RBFFD_EINVAL;
   }
   Request *r = new Request();

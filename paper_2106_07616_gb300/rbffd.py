@@ -464,9 +464,10 @@ class Server:
         self.n = {}
 
     def submit(self, fp, dt=None, resid_tol=1e-6, max_steps=2000, max_outer=20,
-               krylov_tol=1e-12, krylov_maxit=10000, criterion=0, precond=PRECOND_JACOBI):
+               krylov_tol=1e-12, krylov_maxit=10000, criterion=0, precond=PRECOND_JACOBI,
+               precision=PREC_FP64):
         keep = {}
-        d = make_desc(fp, PREC_FP64, keep, precond)
+        d = make_desc(fp, precision, keep, precond)
         sp = SolveParams(fp.dt if dt is None else dt, resid_tol, max_steps, max_outer,
                          krylov_tol, krylov_maxit, 0.0, 0, criterion)
         t = C.c_uint64(0)

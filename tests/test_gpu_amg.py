@@ -165,3 +165,46 @@ def test_batch_with_fgmres_members_matches_alone():
     for k in ("u", "v", "p"):
         assert rel_l2(B.problems[0].get(k), O.get(k)) <= 1e-8, k
     B.close()
+
+
+def test_batch_with_mixed_precision_members_matches_alone():
+    """Mixed-precision members (FP32 or float-float momentum BiCGSTAB inside
+    FP64 refinement, batched per inner arithmetic, symmetry-line members as
+    single-RHS pairs) beside FP64 ones; each result equals the member solved
+    alone and the oracle."""
+    fps = [clouds.kovasznay(30, dt=0.4), clouds.cavity(40, dt=0.05),
+           clouds.channel(symmetry=True), clouds.kovasznay(30, seed=7, dt=0.4),
+           clouds.cavity(24, seed=3, dt=0.05)]
+    cfg = [(rbffd.PREC_MIXED, rbffd.PRECOND_AMG_FGMRES),
+           (rbffd.PREC_MIXED, rbffd.PRECOND_AMG_FGMRES),
+           (rbffd.PREC_MIXED, rbffd.PRECOND_AMG_FGMRES),
+           (rbffd.PREC_MIXED_FF, rbffd.PRECOND_AMG),
+           (rbffd.PREC_FP64, rbffd.PRECOND_AMG_FGMRES)]
+    alone = [rbffd.Problem(ctx(), fp, pr, precond=pc) for fp, (pr, pc) in zip(fps, cfg)]
+    for fp, P in zip(fps, alone):
+        for _ in range(3):
+            P.simple_iterate(fp.dt)
+    B = rbffd.Batch(ctx(), [rbffd.Problem(ctx(), fp, pr, precond=pc)
+                            for fp, (pr, pc) in zip(fps, cfg)])
+    for _ in range(3):
+        d, its, status = B.iterate([fp.dt for fp in fps])
+        assert np.all(status == 0)
+    for i in range(len(fps)):
+        for k in ("u", "v", "p"):
+            e = rel_l2(B.problems[i].get(k), alone[i].get(k))
+            assert e <= 1e-8, (i, k, e)
+    for i in (0, 2):
+        O = oracle.Problem(fps[i], krylov_tol=1e-12)
+        for _ in range(3):
+            O.simple_iterate(fps[i].dt)
+        for k in ("u", "v", "p"):
+            assert rel_l2(B.problems[i].get(k), O.get(k)) <= 1e-8, (i, k)
+    B.close()
+
+
+def test_batch_rejects_mixed_members_with_jacobi():
+    fp = clouds.kovasznay(30, dt=0.4)
+    P = rbffd.Problem(ctx(), fp, rbffd.PREC_MIXED)
+    with pytest.raises(rbffd.RbffdError) as e:
+        rbffd.Batch(ctx(), [P])
+    assert e.value.code == rbffd.EINVAL

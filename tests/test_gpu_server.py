@@ -46,28 +46,28 @@ def test_server_results_match_solves_alone():
 
 
 def test_server_mixes_pressure_solvers():
-    """Requests with flexible GMRES, multigrid BiCGSTAB and Jacobi p' solvers
-    run in the same batched iterations; each result matches the request
-    solved alone with its own solver."""
+    """Requests with flexible GMRES, multigrid BiCGSTAB and Jacobi p' solvers,
+    one with mixed-precision momentum, run in the same batched iterations;
+    each result matches the request solved alone with its own solvers."""
     ctx = rbffd.Context(0)
     S = rbffd.Server(ctx)
     fps = requests()
-    pcs = [rbffd.PRECOND_AMG_FGMRES, rbffd.PRECOND_AMG, rbffd.PRECOND_AMG_FGMRES,
-           rbffd.PRECOND_JACOBI]
-    tickets = [S.submit(fp, resid_tol=TOL, max_steps=3000, precond=pc)
-               for fp, pc in zip(fps, pcs)]
+    cfg = [(rbffd.PREC_MIXED, rbffd.PRECOND_AMG_FGMRES), (rbffd.PREC_FP64, rbffd.PRECOND_AMG),
+           (rbffd.PREC_FP64, rbffd.PRECOND_AMG_FGMRES), (rbffd.PREC_FP64, rbffd.PRECOND_JACOBI)]
+    tickets = [S.submit(fp, resid_tol=TOL, max_steps=3000, precond=pc, precision=pr)
+               for fp, (pr, pc) in zip(fps, cfg)]
     S.drain()
     solo_ctx = rbffd.Context(0)
-    for fp, pc, t in zip(fps, pcs, tickets):
+    for fp, (pr, pc), t in zip(fps, cfg, tickets):
         r = S.poll(t, fields=True)
         assert r["state"] == 2
-        P = rbffd.Problem(solo_ctx, fp, precond=pc)
+        P = rbffd.Problem(solo_ctx, fp, pr, precond=pc)
         rc, st = P.solve_steady(fp.dt, resid_tol=TOL, max_steps=3000, check=False)
         assert r["status"] == rc
         if rc == 0:
             assert r["resid"][2] <= TOL and st["resid"][2] <= TOL
             for k in ("u", "v"):
-                assert rel_l2(r[k], P.get(k)) <= 20 * TOL, (fp.name, pc, k)
+                assert rel_l2(r[k], P.get(k)) <= 20 * TOL, (fp.name, pr, pc, k)
         P.close()
     S.close()
 
