@@ -297,7 +297,10 @@ def run_serve(args):
            "resid_tol": args.resid_tol, "wall_s": wall, "failures": fails[:12],
            "steps_ok": [r["steps"] for r in ok], "outer_ok": [r["outer"] for r in ok],
            "R_ok": [float(r["resid"][2]) for r in ok], "max_steps": args.max_steps,
-           "precond": args.precond,
+           "precond": args.precond, "precision": args.precision,
+           "dtype": ("f32x2+f64" if args.precision == "ff" else
+                     "f32+f64" if args.precision == "mixed" or args.precond == "fgmres"
+                     else "f64"),
            "config": {"workload": f"serve{args.count or 48}",
                       "description": "Poisson arrivals 20/s; Kovasznay Re 20-60 / cavity "
                                      "Re 10-400 / cylinder Re 10-40, N log-uniform [5k,50k], "
