@@ -281,7 +281,8 @@ typedef struct {
 typedef struct {
   int32_t iters[3];   /* BiCGSTAB iterations: u~, v~, p' (inner FP32 ones if mixed) */
   double relres[3];   /* final FP64 relative residuals */
-  int32_t sweeps[3];  /* defect-correction sweeps (mixed precision; 0 otherwise) */
+  int32_t sweeps[3];  /* restarts: defect-correction sweeps (mixed precision), BiCGSTAB
+                       * restarts after a (near) breakdown, FGMRES restarts */
 } rbffd_iter_stats;
 
 /* One outer iteration (paper Sec. 3.2 steps 2-7):

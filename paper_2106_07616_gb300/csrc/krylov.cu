@@ -30,7 +30,7 @@ namespace rbffd {
 namespace {
 
 // slots of the partials array (x NR for the right-hand sides)
-enum { S_BB = 0, S_RR, S_RHV, S_SS, S_RHS, S_TT, S_TS, S_RHT, S_COUNT };
+enum { S_BB = 0, S_RR, S_RHV, S_SS, S_RHS, S_TT, S_TS, S_RHT, S_RHR, S_COUNT };
 
 using kdev::MAXB;
 
@@ -52,9 +52,10 @@ struct KScalars {
 //                                                           -> omega, rho' = (r^,s) - omega (r^,t)
 //   D: x += alpha p^ + omega s^, r = s - omega t, and already the next
 //      p = r + beta (p - omega v), p^ = p/d with beta = (rho'/rho)(alpha/omega);
-//      partial (r, r)                                      -> |r| test
+//      partials (r, r), (r^, r)                            -> |r| test
 // The next direction is formed before the |r| test; if the test stops the
-// solve it is simply unused.  rho' equals (r^, r) in exact arithmetic.
+// solve it is simply unused.  rho' equals (r^, r) in exact arithmetic; the
+// directly summed (r^, r) replaces it for the next iteration (phase D).
 // The solve of one system by the nb CTAs lb = 0..nb-1 that share it (the
 // whole grid for a single system; a subrange of a batched launch).
 // AMGP: the preconditioner is a V-cycle of the hierarchy A.amg instead of
@@ -325,9 +326,9 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
         omg[k] = ks[k].omega;
         bet[k] = ks[k].beta;
       }
-      double acc[NR];
+      double acc[2 * NR];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) acc[k] = 0.0;
+      for (int k = 0; k < 2 * NR; ++k) acc[k] = 0.0;
       for (int i = tid; i < n; i += stride) {
         const double di = __ldg(A.dinv + i);
 #pragma unroll
@@ -342,18 +343,22 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
             const double ri = A.w[k].s[i] - omg[k] * A.w[k].t[i];
             A.w[k].r[i] = ri;
             acc[k] += ri * ri;
+            acc[NR + k] += A.w[k].rh[i] * ri;
             const double pi = ri + bet[k] * (A.w[k].p[i] - omg[k] * A.w[k].v[i]);
             A.w[k].p[i] = pi;
             if constexpr (!AMGP) A.w[k].ph[i] = pi * di;
           }
         }
       }
-      double *outs[NR];
+      double *outs[2 * NR];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) outs[k] = (run[k] && !half[k]) ? P(S_RR, k) : nullptr;
-      kdev::block_partials<NT, NR>(acc, sred, outs, lb);
-      double tot[NR];
-      ok = kdev::exchange<NR>(A.flags, err, epoch++, outs, tot, stot, lb, nb);
+      for (int k = 0; k < NR; ++k) {
+        outs[k] = (run[k] && !half[k]) ? P(S_RR, k) : nullptr;
+        outs[NR + k] = (run[k] && !half[k]) ? P(S_RHR, k) : nullptr;
+      }
+      kdev::block_partials<NT, 2 * NR>(acc, sred, outs, lb);
+      double tot[2 * NR];
+      ok = kdev::exchange<2 * NR>(A.flags, err, epoch++, outs, tot, stot, lb, nb);
       if (!ok) break;
       if (leader) {
 #pragma unroll
@@ -380,6 +385,15 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
             continue;
           }
           if (c.it >= A.maxit) { c.state = KRY_NOCONV; continue; }
+          // The update took rho_new as (r^,s) - omega (r^,t), equal to
+          // (r^, r) in exact arithmetic (it saves a grid exchange) but
+          // summed from two products that cancel.  The next iteration uses
+          // the directly summed (r^, r) instead: with the fused value alone,
+          // the 200 x 200 cavity p' system with Jacobi (~3e6 condition)
+          // diverged for some summation orders.  (Restarting whenever r^
+          // and r were nearly orthogonal was tried too: it restarted every
+          // few hundred iterations and stalled the 150k cylinder.)
+          c.rho = tot[NR + k];
         }
       }
       __syncthreads();
@@ -471,8 +485,6 @@ int krylov_blocks_for(rbffd_ctx *ctx, int n, int nr) {
   return (int)(want < cap ? want : cap);
 }
 
-// Largest T <= 8 whose groups (32 / T per warp) still cover every row in
-// one pass; 1 when the rows outnumber the threads.
 // threads per row: the most that still cover a CTA's ceil(n / nblocks)
 // rows (kdev::cta_rows) in one pass of its warps
 int krylov_threads_per_row(int n, int nr, int nblocks) {

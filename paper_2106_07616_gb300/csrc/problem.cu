@@ -646,7 +646,7 @@ extern "C" int simple_iterate(rbffd_problem *P, const rbffd_step_params *sp, dou
     for (int k = 0; k < 3; ++k) {
       stats->iters[k] = r.kout[k].iters;
       stats->relres[k] = r.kout[k].relres;
-      stats->sweeps[k] = mixed ? r.kout[k].restarts : 0;
+      stats->sweeps[k] = r.kout[k].restarts;
     }
   }
   if (delta_out) *delta_out = r.rec.delta;

@@ -35,7 +35,9 @@ def test_server_results_match_solves_alone():
         r = S.poll(t, fields=True)
         assert r["state"] == 2
         rc, st, P = solve_alone(solo_ctx, fp)
-        assert r["status"] == rc
+        # a request that fails alone fails in the mix too; which error ends
+        # it (steps exhausted, divergence) depends on rounding
+        assert (r["status"] == 0) == (rc == 0), (r["status"], rc)
         if rc != 0:
             continue
         assert r["resid"][2] <= TOL and st["resid"][2] <= TOL
@@ -63,7 +65,7 @@ def test_server_mixes_pressure_solvers():
         assert r["state"] == 2
         P = rbffd.Problem(solo_ctx, fp, pr, precond=pc)
         rc, st = P.solve_steady(fp.dt, resid_tol=TOL, max_steps=3000, check=False)
-        assert r["status"] == rc
+        assert (r["status"] == 0) == (rc == 0), (r["status"], rc)
         if rc == 0:
             assert r["resid"][2] <= TOL and st["resid"][2] <= TOL
             for k in ("u", "v"):
