@@ -459,7 +459,7 @@ def run_native(args):
         P.reload(desc=desc)
         for k, a in (init if start is None else start).items():
             P.set(k, a)
-        it, _ = P.time_step(fp.dt, 1e-4, max_outer=args.outer)
+        it, _ = P.time_step(fp.dt, 1e-4, max_outer=args.outer, krylov_maxit=100000)
         return it
 
     for _ in range(args.warmup):

@@ -13,6 +13,7 @@
 
 #include "batch.cuh"
 #include "fgmres.cuh"
+#include "krylov_dev.cuh"
 #include "ops.cuh"
 #include "problem.cuh"
 
@@ -113,6 +114,25 @@ int BatchScratch::reserve(rbffd_ctx *c, int members) {
   return RBFFD_OK;
 }
 
+// CTAs of each system of a batched launch of at most cmax co-resident CTAs:
+// one each, the rest in proportion to the rows, capped by the system's
+// partial-sum capacity cap[i], by 8 threads per row, and by the kdev::MAXB
+// CTAs the partial sums of one system are laid out for.
+static std::vector<int> split_ctas(const std::vector<int> &rows, const std::vector<int> &cap,
+                                   int cmax) {
+  const int m = (int)rows.size();
+  std::vector<int> nb(m, 1);
+  const long long total = std::accumulate(rows.begin(), rows.end(), 0LL);
+  const int left = cmax - m;
+  for (int i = 0; i < m && total > 0; ++i) {
+    const int extra = (int)((double)left * rows[i] / (double)total);
+    int c = std::min(cap[i], (int)((rows[i] * 8LL + KB_NT - 1) / KB_NT));
+    c = std::min(c, kdev::MAXB);
+    nb[i] = std::max(1, std::min(1 + extra, c));
+  }
+  return nb;
+}
+
 // One batched Krylov launch for the systems args[0..m) (args filled except
 // nblocks, tpr, flags and bar, which are set here), with table slot `slot`.
 static int launch_krylov(BatchScratch &S, int slot, int nr, std::vector<KrylovArgs> &args,
@@ -126,16 +146,10 @@ static int launch_krylov(BatchScratch &S, int slot, int nr, std::vector<KrylovAr
   }
   // one CTA each, the rest in proportion to the rows, each capped by what
   // its partial-sum buffers hold and by 8 threads per row
-  std::vector<int> nb(m, 1);
-  long long total = std::accumulate(rows.begin(), rows.end(), 0LL);
-  int left = cmax - m;
-  for (int i = 0; i < m && total > 0; ++i) {
-    int extra = (int)((double)left * rows[i] / (double)total);
-    int cap = std::min(args[i].nblocks, (int)((rows[i] * 8LL + KB_NT - 1) / KB_NT));
-    cap = std::min(cap, 160);  // the grid exchange polls at most 160 CTAs
-    nb[i] = std::max(1, std::min(1 + extra, cap));
-  }
-  int nctas = std::accumulate(nb.begin(), nb.end(), 0);
+  std::vector<int> cap(m);
+  for (int i = 0; i < m; ++i) cap[i] = args[i].nblocks;
+  const std::vector<int> nb = split_ctas(rows, cap, cmax);
+  const int nctas = std::accumulate(nb.begin(), nb.end(), 0);
   char *hb = (char *)S.hmem;
   char *db = (char *)S.dmem;
   KrylovArgs *hsys = (KrylovArgs *)(hb + S.off_sys[slot]);
@@ -184,16 +198,10 @@ static int launch_mixed(BatchScratch &S, int slot, int nr, int inner,
     set_error("batch: %d members exceed the %d co-resident CTAs of one launch", m, cmax);
     return RBFFD_EINVAL;
   }
-  std::vector<int> nb(m, 1);
-  long long total = std::accumulate(rows.begin(), rows.end(), 0LL);
-  int left = cmax - m;
-  for (int i = 0; i < m && total > 0; ++i) {
-    int extra = (int)((double)left * rows[i] / (double)total);
-    int cap = std::min(args[i].nblocks, (int)((rows[i] * 8LL + KB_NT - 1) / KB_NT));
-    cap = std::min(cap, 160);
-    nb[i] = std::max(1, std::min(1 + extra, cap));
-  }
-  int nctas = std::accumulate(nb.begin(), nb.end(), 0);
+  std::vector<int> cap(m);
+  for (int i = 0; i < m; ++i) cap[i] = args[i].nblocks;
+  const std::vector<int> nb = split_ctas(rows, cap, cmax);
+  const int nctas = std::accumulate(nb.begin(), nb.end(), 0);
   char *hb = (char *)S.hmem;
   char *db = (char *)S.dmem;
   MixedArgs *hsys = (MixedArgs *)(hb + S.off_sys[slot]);
@@ -240,16 +248,8 @@ static int launch_fgmres(BatchScratch &S, int slot, std::vector<FgmresArgs> &arg
     set_error("batch: %d members exceed the %d co-resident CTAs of one launch", m, cmax);
     return RBFFD_EINVAL;
   }
-  std::vector<int> nb(m, 1);
-  long long total = std::accumulate(rows.begin(), rows.end(), 0LL);
-  int left = cmax - m;
-  for (int i = 0; i < m && total > 0; ++i) {
-    int extra = (int)((double)left * rows[i] / (double)total);
-    int cap = (int)((rows[i] * 8LL + KB_NT - 1) / KB_NT);
-    cap = std::min(cap, 160);  // partial sums are laid out for at most 160 CTAs
-    nb[i] = std::max(1, std::min(1 + extra, cap));
-  }
-  int nctas = std::accumulate(nb.begin(), nb.end(), 0);
+  const std::vector<int> nb = split_ctas(rows, std::vector<int>(m, kdev::MAXB), cmax);
+  const int nctas = std::accumulate(nb.begin(), nb.end(), 0);
   char *hb = (char *)S.hmem;
   char *db = (char *)S.dmem;
   FgmresArgs *hsys = (FgmresArgs *)(hb + S.off_sys[slot]);
