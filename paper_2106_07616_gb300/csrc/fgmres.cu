@@ -186,15 +186,10 @@ __device__ __forceinline__ void block_combine(int r0, int r1, int n, const UT *U
 }
 
 struct FgState {
-  double bnorm, beta, beta_prev, scale, relres;
+  double bnorm, beta, scale, relres;
   float hn, hinv;
-  int it, restarts, state, k, stop, stall;
+  int it, restarts, state, k, stop;
 };
-
-// A restart that does not halve the true residual counts as stalled; this
-// many in a row end the solve (KRY_NOCONV): the FP32 Arnoldi process has
-// stopped contracting, which happens when cond(A M^-1) * eps_FP32 is near 1.
-constexpr int FG_STALLS = 3;
 
 }  // namespace
 
@@ -232,7 +227,7 @@ __device__ __forceinline__ void fgmres_body(const FgmresArgs &A, const int lb, c
     st.relres = 1.0;
     st.it = st.restarts = 0;
     st.state = KRY_RUNNING;
-    st.stop = st.stall = 0;
+    st.stop = 0;
   }
   __syncthreads();
 
@@ -254,12 +249,10 @@ __device__ __forceinline__ void fgmres_body(const FgmresArgs &A, const int lb, c
       st.beta = sqrt(tot64[1]);
       st.scale = st.beta > 0.0 ? 1.0 / st.beta : 0.0;
       st.relres = st.bnorm > 0.0 ? st.beta / st.bnorm : 0.0;
-      if (!first) st.stall = st.beta > 0.5 * st.beta_prev ? st.stall + 1 : 0;
-      st.beta_prev = st.beta;
       if (st.bnorm == 0.0) st.state = KRY_OK;
       else if (!(st.relres == st.relres)) st.state = KRY_DIVERGED;
       else if (st.relres <= A.tol) st.state = KRY_OK;
-      else if (st.it >= A.maxit || st.stall >= FG_STALLS) st.state = KRY_NOCONV;
+      else if (st.it >= A.maxit) st.state = KRY_NOCONV;
     }
     __syncthreads();
     return true;
