@@ -546,8 +546,9 @@ def run_native(args):
                              "FP64 refinement)"}.get(
                            args.precision, "k_bicgstab<1> (pressure-correction BiCGSTAB, persistent)")),
             "launches": kp["launches"], "avg_launch_ms": kp["ms"] / max(kp["launches"], 1),
-            "bytes_per_unit": (f"q(8+4)+16 + one FP32 V-cycle + Gram-Schmidt over the basis "
-                               f"per row-iteration (pcorr_bytes)" if args.precond == "fgmres" else
+            "bytes_per_unit": (f"q(4+4)+8 (FP32 SpMV) + one FP32 V-cycle + FP32 Gram-Schmidt "
+                               f"over the basis per row-step (pcorr_bytes)"
+                               if args.precond == "fgmres" else
                                f"2q(8+4)+14*8 + 2 V-cycles (~2q(8+4)+64) = "
                                f"{2 * fp.q * 12 + 112 + 2 * (fp.q * 12 + 64)} B per row-iteration "
                                f"+ the coarse levels' operators"
