@@ -69,6 +69,22 @@ def workload(name: str):
     return fp, desc
 
 
+def combine_ranks(total_ms, total_units, device="cpu"):
+    """Whole-job timing over the ranks of the default process group: the
+    slowest rank's time and the units every rank processed (each rank runs
+    its own replica: weak scaling, no collective on the data path).  One
+    rank, or no process group: the inputs."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), float(total_units)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(total_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def solver_codes(args, rbffd):
     """(precision, p' preconditioner) library codes of the command line."""
     prec = {"mixed": rbffd.PREC_MIXED, "ff": rbffd.PREC_MIXED_FF,
@@ -495,14 +511,7 @@ def run_native(args):
     ko = ctx.kernel_stat("outer")
     ctx.profile(False)
 
-    if world > 1:
-        t = torch.tensor([total_ms, float(total_it)], dtype=torch.float64, device=f"cuda:{local}")
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms_max, all_it = float(tmax[0]), float(t[1])
-    else:
-        total_ms_max, all_it = total_ms, float(total_it)
+    total_ms_max, all_it = combine_ranks(total_ms, total_it, f"cuda:{local}")
     value = all_it / (total_ms_max / 1e3)
 
     # ---- end to end through the C ABI from pinned host buffers
