@@ -93,13 +93,16 @@ enum {
  * residual, so it changes the iteration count, not the solution. */
 enum {
   RBFFD_PRECOND_JACOBI = 0, /* diagonal scaling (default) */
-  RBFFD_PRECOND_AMG = 1,    /* one V-cycle of a smoothed-aggregation multigrid hierarchy,
-                               built on the host when the problem is built (RBFFD_PREC_FP64
-                               only); two cycles per BiCGSTAB iteration, FP64 */
+  RBFFD_PRECOND_AMG = 1,    /* one V-cycle of a smoothed-aggregation multigrid hierarchy;
+                               two cycles per BiCGSTAB iteration, FP64 */
   RBFFD_PRECOND_AMG_FGMRES = 2 /* the same hierarchy stored in FP32, one cycle per step of
-                               a flexible GMRES(30) instead of BiCGSTAB (RBFFD_PREC_FP64
-                               only; not in batches or the request server) */
+                               a flexible GMRES(30) instead of BiCGSTAB */
 };
+/* The hierarchy's host part is built on a thread of its own, started when
+ * the problem is built (create, reload); the first call that needs it (the
+ * first outer iteration or step, a batch iteration, rbffd_problem_amg_info)
+ * waits for it and uploads it, and returns its errors (RBFFD_ESINGULAR for
+ * a singular coarsest matrix, RBFFD_ENOMEM). */
 #define RBFFD_AMG_MAX_LEVELS 10
 
 typedef struct rbffd_ctx rbffd_ctx;

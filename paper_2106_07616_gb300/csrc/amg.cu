@@ -19,13 +19,16 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
 #include <memory>
+#include <thread>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
 
 #include "amg.cuh"
+#include "amg_job.cuh"
 #include "krylov_dev.cuh"
 
 namespace rbffd {
@@ -657,22 +660,61 @@ int amg_analyze(int n, const int32_t *rowptr, const int32_t *col, const double *
   return RBFFD_OK;
 }
 
+// ---- the build as a job: the host part (copy of the packed matrix, the
+// hierarchy, its staging) runs on a host thread of its own, the device part
+// (allocation, upload) on the caller's thread, so the host part overlaps
+// the device work the caller issues meanwhile.
+struct CsrOff {
+  size_t ptr = 0, col = 0, val = 0;
+  int grp = 1;
+};
+struct LevelOff {
+  CsrOff S, R, P;
+  size_t b = 0, z = 0, y = 0;
+};
+
+struct AmgJob {
+  int device = 0, n = 0, q = 0, ldn = 0, nblocks = 0, wpb = 0;
+  const int32_t *dcol = nullptr;
+  const double *dval = nullptr;
+  cudaEvent_t ready = nullptr;  // the packed matrix is written (caller's stream)
+  std::thread th;
+  int rc = RBFFD_OK;
+  char err[256] = "";
+  std::chrono::steady_clock::time_point t0;
+  Hierarchy H;
+  Staging S;
+  std::vector<LevelOff> off;
+  size_t o_dev = 0, o_s0 = 0, o_a0 = 0, o_cinv = 0;
+  int ts0 = 1;
+  bool low = false;  // the cycle's type is FP32
+};
+
+namespace {
+
 template <typename T>
-int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
-              int nblocks, int wpb, void **mem, size_t *bytes, const AmgDevT<T> **dev,
-              AmgDevT<T> *host_view, AmgInfo *info) {
-  *mem = nullptr;
-  *bytes = 0;
-  *dev = nullptr;
-  const auto t0 = std::chrono::steady_clock::now();
+int host_part(AmgJob &J) {
+  const int n = J.n, q = J.q, ldn = J.ldn;
   std::vector<int32_t> hcol((size_t)q * ldn);
   std::vector<double> hval((size_t)q * ldn);
-  RBFFD_CK(cudaMemcpyAsync(hcol.data(), col, hcol.size() * 4, cudaMemcpyDeviceToHost,
-                           ctx->stream));
-  RBFFD_CK(cudaMemcpyAsync(hval.data(), val, hval.size() * 8, cudaMemcpyDeviceToHost,
-                           ctx->stream));
-  RBFFD_CK(cudaStreamSynchronize(ctx->stream));
-  Hierarchy H;
+  {
+    // the copies wait for the packed matrix on a stream of their own
+    cudaStream_t cs = nullptr;
+    RBFFD_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const bool okc =
+        cudaStreamWaitEvent(cs, J.ready, 0) == cudaSuccess &&
+        cudaMemcpyAsync(hcol.data(), J.dcol, hcol.size() * 4, cudaMemcpyDeviceToHost, cs) ==
+            cudaSuccess &&
+        cudaMemcpyAsync(hval.data(), J.dval, hval.size() * 8, cudaMemcpyDeviceToHost, cs) ==
+            cudaSuccess &&
+        cudaStreamSynchronize(cs) == cudaSuccess;
+    cudaStreamDestroy(cs);
+    if (!okc) {
+      set_error("amg: copy of the p' matrix failed");
+      return RBFFD_ECUDA;
+    }
+  }
+  Hierarchy &H = J.H;
   RBFFD_TRY(build_hierarchy(from_ell(n, q, ldn, hcol, hval), H));
   const int L = (int)H.A.size();
   // level 0's S in the solve's ELL layout: s_e = -w_i a_e w_c (+ 2 w_i on the diagonal)
@@ -696,11 +738,7 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
   }
 
   // ---- pack everything into one staging buffer, then one upload
-  Staging S;
-  struct CsrOff {
-    size_t ptr = 0, col = 0, val = 0;
-    int grp = 1;
-  };
+  Staging &S = J.S;
   auto put_csr = [&](const Csr &M, int grp) {
     CsrOff o;
     o.ptr = S.put(M.ptr);
@@ -710,31 +748,26 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
     return o;
   };
   // lanes per row for the launch's CTAs (see Shape)
-  const Grid W{nblocks > 0 ? nblocks : 128, wpb > 0 ? wpb : 32};
+  const Grid W{J.nblocks > 0 ? J.nblocks : 128, J.wpb > 0 ? J.wpb : 32};
   std::vector<int> gS(L, 1), gR(L, 1), gP(L, 1);
-  int ts0 = 1;
   for (int l = 0; l + 1 < L; ++l) {
     const Shape r = shape(H.R[l]);
     if (l == 0)
-      lanes_level0(n, q, r, W, ts0, gR[0]);
+      lanes_level0(n, q, r, W, J.ts0, gR[0]);
     else
       lanes_pair(shape(H.S[l]), r, W, gS[l], gR[l]);
     gP[l] = lanes_alone(shape(H.P[l]), W);
   }
-  struct Off {
-    CsrOff S, R, P;
-    size_t b = 0, z = 0, y = 0;
-  };
-  std::vector<Off> off(L);
+  std::vector<LevelOff> &off = J.off;
+  off.assign(L, LevelOff());
   // an FP32 cycle's solve (flexible GMRES) runs its inner SpMVs on level
   // 0's matrix in FP32 too: a rounded copy of the ELL values
-  const bool low = sizeof(T) < sizeof(double);
-  size_t o_dev = 0, o_s0 = 0, o_a0 = 0, o_cinv = 0;
+  J.low = sizeof(T) < sizeof(double);
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) S.fill_pass();
-    o_dev = S.take(sizeof(AmgDevT<T>));
-    o_s0 = S.put_as<T>(s0);
-    o_a0 = low ? S.put_as<T>(hval) : 0;
+    J.o_dev = S.take(sizeof(AmgDevT<T>));
+    J.o_s0 = S.put_as<T>(s0);
+    J.o_a0 = J.low ? S.put_as<T>(hval) : 0;
     for (int l = 0; l < L; ++l) {
       if (l > 0) off[l].S = put_csr(H.S[l], l + 1 < L ? gS[l] : 1);
       if (l + 1 < L) {
@@ -745,8 +778,65 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
       off[l].z = S.take(sizeof(T) * H.A[l].n);
       off[l].y = S.take(sizeof(T) * H.A[l].n);
     }
-    o_cinv = S.put_as<T>(H.cinv);
+    J.o_cinv = S.put_as<T>(H.cinv);
   }
+  return RBFFD_OK;
+}
+
+void join(AmgJob *J) {
+  if (J->th.joinable()) J->th.join();
+  if (J->ready) cudaEventDestroy(J->ready);
+  J->ready = nullptr;
+}
+
+}  // namespace
+
+template <typename T>
+int amg_build_begin(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
+                    const double *val, int nblocks, int wpb, AmgJob **job) {
+  *job = nullptr;
+  AmgJob *J = new AmgJob();
+  J->device = ctx->device;
+  J->n = n;
+  J->q = q;
+  J->ldn = ldn;
+  J->nblocks = nblocks;
+  J->wpb = wpb;
+  J->dcol = col;
+  J->dval = val;
+  J->t0 = std::chrono::steady_clock::now();
+  if (cudaEventCreateWithFlags(&J->ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(J->ready, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    join(J);
+    delete J;
+    set_error("amg: event for the hierarchy build failed");
+    return RBFFD_ECUDA;
+  }
+  J->th = std::thread([J] {
+    cudaSetDevice(J->device);
+    J->rc = host_part<T>(*J);
+    if (J->rc != RBFFD_OK) snprintf(J->err, sizeof(J->err), "%s", rbffd_last_error());
+  });
+  *job = J;
+  return RBFFD_OK;
+}
+
+template <typename T>
+int amg_build_end(rbffd_ctx *ctx, AmgJob *J, void **mem, size_t *bytes,
+                  const AmgDevT<T> **dev, AmgDevT<T> *host_view, AmgInfo *info) {
+  *mem = nullptr;
+  *bytes = 0;
+  *dev = nullptr;
+  join(J);
+  std::unique_ptr<AmgJob> own(J);
+  if (J->rc != RBFFD_OK) {
+    set_error("%s", J->err);
+    return J->rc;
+  }
+  const Hierarchy &H = J->H;
+  Staging &S = J->S;
+  const int L = (int)H.A.size();
   void *dmem = nullptr;
   RBFFD_TRY(dev_alloc(ctx, &dmem, S.size));
   char *base = (char *)dmem;
@@ -761,21 +851,22 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
   AmgDevT<T> h;
   memset(&h, 0, sizeof(h));
   h.nlev = L;
-  h.cinv = (const T *)(base + o_cinv);
-  h.s0 = (const T *)(base + o_s0);
-  h.ts0 = ts0;
-  h.a0 = low ? (const T *)(base + o_a0) : nullptr;
+  h.cinv = (const T *)(base + J->o_cinv);
+  h.s0 = (const T *)(base + J->o_s0);
+  h.ts0 = J->ts0;
+  h.a0 = J->low ? (const T *)(base + J->o_a0) : nullptr;
   for (int l = 0; l < L; ++l) {
     AmgLevelT<T> &v = h.lev[l];
+    const LevelOff &o = J->off[l];
     v.n = H.A[l].n;
-    v.S = csr_at(off[l].S, l > 0);
-    v.R = csr_at(off[l].R, l + 1 < L);
-    v.P = csr_at(off[l].P, l + 1 < L);
-    v.b = l > 0 ? (T *)(base + off[l].b) : nullptr;
-    v.z = (T *)(base + off[l].z);
-    v.y = (T *)(base + off[l].y);
+    v.S = csr_at(o.S, l > 0);
+    v.R = csr_at(o.R, l + 1 < L);
+    v.P = csr_at(o.P, l + 1 < L);
+    v.b = l > 0 ? (T *)(base + o.b) : nullptr;
+    v.z = (T *)(base + o.z);
+    v.y = (T *)(base + o.y);
   }
-  memcpy(S.buf + o_dev, &h, sizeof(h));
+  memcpy(S.buf + J->o_dev, &h, sizeof(h));
   if (cudaMemcpyAsync(dmem, S.buf, S.size, cudaMemcpyHostToDevice, ctx->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
@@ -785,17 +876,36 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
   }
   *mem = dmem;
   *bytes = S.size;
-  *dev = (const AmgDevT<T> *)(base + o_dev);
+  *dev = (const AmgDevT<T> *)(base + J->o_dev);
   if (host_view) *host_view = h;
-  fill_info(H, ms_since(t0), info);
+  fill_info(H, ms_since(J->t0), info);
   return RBFFD_OK;
 }
 
-template int amg_build<double>(rbffd_ctx *, int, int, int, const int32_t *, const double *, int, int,
-                               void **, size_t *, const AmgDevT<double> **, AmgDevT<double> *,
-                               AmgInfo *);
-template int amg_build<float>(rbffd_ctx *, int, int, int, const int32_t *, const double *, int, int,
-                              void **, size_t *, const AmgDevT<float> **, AmgDevT<float> *,
-                              AmgInfo *);
+void amg_build_abandon(AmgJob *J) {
+  if (!J) return;
+  join(J);
+  delete J;
+}
+
+template <typename T>
+int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
+              int nblocks, int wpb, void **mem, size_t *bytes, const AmgDevT<T> **dev,
+              AmgDevT<T> *host_view, AmgInfo *info) {
+  AmgJob *J = nullptr;
+  RBFFD_TRY(amg_build_begin<T>(ctx, n, q, ldn, col, val, nblocks, wpb, &J));
+  return amg_build_end<T>(ctx, J, mem, bytes, dev, host_view, info);
+}
+
+#define RBFFD_AMG_INSTANCES(T)                                                                  \
+  template int amg_build<T>(rbffd_ctx *, int, int, int, const int32_t *, const double *, int,  \
+                            int, void **, size_t *, const AmgDevT<T> **, AmgDevT<T> *,         \
+                            AmgInfo *);                                                        \
+  template int amg_build_begin<T>(rbffd_ctx *, int, int, int, const int32_t *, const double *, \
+                                  int, int, AmgJob **);                                        \
+  template int amg_build_end<T>(rbffd_ctx *, AmgJob *, void **, size_t *, const AmgDevT<T> **, \
+                                AmgDevT<T> *, AmgInfo *);
+RBFFD_AMG_INSTANCES(double)
+RBFFD_AMG_INSTANCES(float)
 
 }  // namespace rbffd

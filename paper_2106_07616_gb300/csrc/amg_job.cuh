@@ -1,0 +1,27 @@
+// amg_job.cuh -- the multigrid hierarchy build of amg.cuh split in two, so
+// that its host part runs on a thread of its own while the device works.
+#pragma once
+#include "amg.cuh"
+
+namespace rbffd {
+
+// The same build in two halves.  amg_build_begin records an event on the
+// context's stream after the packed matrix's producers and returns at
+// once: a host thread of its own copies the matrix (on a stream of its own,
+// after that event) and builds the hierarchy and its staging.  The caller
+// may issue more device work meanwhile; amg_build_end, on the caller's
+// thread, waits for the host part, allocates and uploads (stream-ordered)
+// and fills the outputs as amg_build does, and frees the job (errors of the
+// host part are returned there).  amg_build_abandon joins and frees a job
+// that is not needed any more.  The packed matrix must not change until
+// amg_build_end or amg_build_abandon returns.
+struct AmgJob;
+template <typename T>
+int amg_build_begin(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
+                    const double *val, int nblocks, int wpb, AmgJob **job);
+template <typename T>
+int amg_build_end(rbffd_ctx *ctx, AmgJob *job, void **mem, size_t *bytes,
+                  const AmgDevT<T> **dev, AmgDevT<T> *host_view, AmgInfo *info);
+void amg_build_abandon(AmgJob *job);
+
+}  // namespace rbffd

@@ -525,12 +525,15 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
   rbffd_ctx *ctx = P[0]->ctx;
   for (int i = 0; i < m; ++i) {
     if (P[i]->ctx != ctx ||
-        (P[i]->precision != RBFFD_PREC_FP64 && !P[i]->amg && !P[i]->amgf)) {
+        (P[i]->precision != RBFFD_PREC_FP64 && P[i]->precond == RBFFD_PRECOND_JACOBI)) {
       set_error("batch: members must share one context; mixed-precision members need a "
                 "multigrid p' solver");
       return RBFFD_EINVAL;
     }
   }
+  // hierarchies still being built are finished before anything is issued
+  // (the iteration may be captured as a graph)
+  for (int i = 0; i < m; ++i) RBFFD_TRY(amg_ready(P[i]));
   // a member with symmetry lines solves u~ and v~ as two single-RHS systems
   // (their rows differ there), so a launch may hold up to 2m systems
   RBFFD_TRY(S.reserve(ctx, 2 * m));
@@ -643,7 +646,8 @@ extern "C" int rbffd_batch_create(rbffd_ctx *ctx, int32_t count, rbffd_problem *
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
     if (!members[i] || members[i]->ctx != ctx ||
-        (members[i]->precision != RBFFD_PREC_FP64 && !members[i]->amg && !members[i]->amgf)) {
+        (members[i]->precision != RBFFD_PREC_FP64 &&
+         members[i]->precond == RBFFD_PRECOND_JACOBI)) {
       set_error("rbffd_batch_create: member %d is null, on another context, or mixed-precision "
                 "with a Jacobi p' solver", i);
       return RBFFD_EINVAL;

@@ -74,6 +74,8 @@ int check_desc(const rbffd_problem_desc *d) {
 }
 
 void free_amg(rbffd_problem *P) {
+  if (P->amg_job) amg_build_abandon(P->amg_job);
+  P->amg_job = nullptr;
   if (P->amg_mem) dev_free(P->ctx, P->amg_mem, P->amg_bytes);
   if (P->fg_mem) dev_free(P->ctx, P->fg_mem, P->fg_bytes);
   P->fg_mem = nullptr;
@@ -159,14 +161,17 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
   RBFFD_TRY(ops_pack(P));
   free_amg(P);
   P->precond = d->precond;
+  // the multigrid hierarchy's host part runs on a thread of its own from
+  // here; the first p' solve (amg_ready) waits for it and uploads it, so
+  // it overlaps the device work issued meanwhile (the first momentum solve)
   if (P->precond == RBFFD_PRECOND_AMG) {
-    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, P->kblocks1, 32, &P->amg_mem,
-                        &P->amg_bytes, &P->amg, &P->amg_host, &P->amg_info));
+    RBFFD_TRY(amg_build_begin<double>(ctx, P->n, P->q, P->ldn, P->col, P->Pp, P->kblocks1, 32,
+                                      &P->amg_job));
   } else if (P->precond == RBFFD_PRECOND_AMG_FGMRES) {
     P->fg_blocks = fgmres_max_blocks(ctx);
     if (P->fg_blocks > P->kblocks1) P->fg_blocks = P->kblocks1;
-    RBFFD_TRY(amg_build(ctx, P->n, P->q, P->ldn, P->col, P->Pp, P->fg_blocks, 32, &P->amg_mem,
-                        &P->amg_bytes, &P->amgf, &P->amgf_host, &P->amg_info));
+    RBFFD_TRY(amg_build_begin<float>(ctx, P->n, P->q, P->ldn, P->col, P->Pp, P->fg_blocks, 32,
+                                     &P->amg_job));
     // FP64 restart residual and partial sums, then the FP32 Arnoldi basis
     // (m + 1 vectors) and directions (m)
     P->fg_m = FG_MAXM;
@@ -214,7 +219,23 @@ int krylov_status_code(int s) {
   }
 }
 
-// Issue one outer iteration (no host synchronisation).
+}  // namespace
+
+int rbffd::amg_ready(rbffd_problem *P) {
+  if (!P->amg_job) return RBFFD_OK;
+  AmgJob *J = P->amg_job;
+  P->amg_job = nullptr;
+  if (P->precond == RBFFD_PRECOND_AMG)
+    return amg_build_end<double>(P->ctx, J, &P->amg_mem, &P->amg_bytes, &P->amg, &P->amg_host,
+                                 &P->amg_info);
+  return amg_build_end<float>(P->ctx, J, &P->amg_mem, &P->amg_bytes, &P->amgf, &P->amgf_host,
+                              &P->amg_info);
+}
+
+namespace {
+
+// Issue one outer iteration (no host synchronisation beyond the first p'
+// solve's wait for a hierarchy still being built).
 // The momentum solves run in the problem's precision: FP64 BiCGSTAB, or
 // (mixed) FP32 / float-float BiCGSTAB inside FP64 refinement.  The p'
 // solve follows its preconditioner: with Jacobi it takes the same
@@ -324,6 +345,7 @@ int issue_outer(rbffd_problem *P, const rbffd_step_params *sp) {
   RBFFD_TRY(ops_divergence(P, sp));
 
   // ---- pressure correction
+  RBFFD_TRY(amg_ready(P));
   prof_begin(ctx, 1);
   if (P->amgf) {
     FgmresArgs f;
@@ -603,6 +625,10 @@ static void report_levels(const AmgInfo &I, bool have_any, int32_t *levels, int3
 extern "C" int rbffd_problem_amg_info(const rbffd_problem *P, int32_t *levels, int32_t *rows,
                                       int64_t *nnz, double *setup_ms) {
   if (!P) return RBFFD_EINVAL;
+  // a hierarchy still being built is finished first (the call is logically
+  // const: it changes no result, only when the upload happens)
+  RBFFD_CK(cudaSetDevice(P->ctx->device));
+  RBFFD_TRY(amg_ready(const_cast<rbffd_problem *>(P)));
   report_levels(P->amg_info, P->amg != nullptr || P->amgf != nullptr, levels, rows, nnz,
                 setup_ms);
   return RBFFD_OK;

@@ -2,6 +2,7 @@
 #pragma once
 #include "common.cuh"
 #include "amg.cuh"
+#include "amg_job.cuh"
 #include "knn.cuh"
 #include "krylov.cuh"
 
@@ -71,6 +72,8 @@ struct rbffd_problem {
   const rbffd::AmgDev *amg = nullptr;  // device copy of the level table
   rbffd::AmgDev amg_host{};             // host copy (device pointers)
   rbffd::AmgInfo amg_info{};
+  // the hierarchy's host part while it is being built (amg_ready finishes it)
+  rbffd::AmgJob *amg_job = nullptr;
   // flexible GMRES with an FP32 hierarchy (RBFFD_PRECOND_AMG_FGMRES): the
   // FP32 level table and the basis / direction vectors and partials
   const rbffd::AmgDevF *amgf = nullptr;
@@ -92,4 +95,8 @@ int problem_step_end(rbffd_problem *P, double *change);
 double pcorr_bytes(const rbffd_problem *P, int iters);
 // Steady stopping test of solve_steady and of the request server.
 bool steady_done(const rbffd_solve_params *s, double R, double change);
+// Finish the multigrid hierarchy whose host part a build started (upload
+// on the problem's stream); a no-op when none is pending.  Every use of
+// the hierarchy calls it first.
+int amg_ready(rbffd_problem *P);
 }  // namespace rbffd

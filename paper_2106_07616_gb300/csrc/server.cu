@@ -104,6 +104,14 @@ struct rbffd_server {
         r = queue.front();
       }
       int rc = rbffd_problem_create(ctx, &r->desc, &r->P);
+      if (rc == RBFFD_OK) {
+        // the hierarchy's device memory counts against the budget now
+        rc = rbffd::amg_ready(r->P);
+        if (rc != RBFFD_OK) {
+          rbffd_problem_destroy(r->P);
+          r->P = nullptr;
+        }
+      }
       if (rc == RBFFD_ENOMEM && !running.empty()) return;  // wait for memory
       {
         std::lock_guard<std::mutex> g(mu);
