@@ -40,6 +40,12 @@ constexpr int AMG_NCOARSE_MAX = 600;
 constexpr double AMG_THETA = 0.08;  // strength threshold
 constexpr double AMG_OMEGA = 2.0 / 3.0;
 
+// Work (entries a loop touches) below which it runs on the calling thread
+// alone: an OpenMP fork and join costs tens of microseconds on a 16-core
+// host, more than a coarse level's whole loop.
+constexpr long long AMG_PAR_WORK = 1 << 17;
+inline bool par(long long work) { return work >= AMG_PAR_WORK; }
+
 struct Csr {
   int n = 0, m = 0;  // rows, columns
   std::vector<int32_t> ptr, col;
@@ -56,7 +62,8 @@ Csr from_ell(int n, int q, int ldn, const std::vector<int32_t> &col,
     const size_t e = (size_t)j * ldn + i;
     return val[e] != 0.0 || col[e] == i;
   };
-#pragma omp parallel for schedule(static)
+  const bool pa = par((long long)n * q);
+#pragma omp parallel for schedule(static) if (pa)
   for (int i = 0; i < n; ++i) {
     int c = 0;
     for (int j = 0; j < q; ++j) c += kept(i, j);
@@ -65,7 +72,7 @@ Csr from_ell(int n, int q, int ldn, const std::vector<int32_t> &col,
   for (int i = 0; i < n; ++i) A.ptr[i + 1] += A.ptr[i];
   A.col.resize(A.ptr[n]);
   A.val.resize(A.ptr[n]);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (pa)
   for (int i = 0; i < n; ++i) {
     int k = A.ptr[i];
     for (int j = 0; j < q; ++j)
@@ -80,27 +87,38 @@ Csr from_ell(int n, int q, int ldn, const std::vector<int32_t> &col,
 
 std::vector<double> diagonal(const Csr &A) {
   std::vector<double> d(A.n, 0.0);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (par(A.nnz()))
   for (int i = 0; i < A.n; ++i)
     for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
       if (A.col[k] == i) d[i] += A.val[k];
   return d;
 }
 
+// Rows per dynamically scheduled chunk: about 16 chunks a thread, at most
+// 256 rows (the coarse-row products R A and R A P have a few thousand heavy
+// rows, which fixed large chunks leave to a few threads).
+int row_chunk(int n) {
+  const int c = n / (16 * std::max(1, omp_get_max_threads()));
+  return std::max(1, std::min(256, c));
+}
+
 // A CSR matrix whose row i is produced by row(i, mark, emit): `mark` is a
 // per-thread int array of m entries (the row index marks a column as seen),
 // emit(c, v) adds v at column c.  Two parallel passes -- sizes, then values
 // into place -- so no per-row allocation; column order = first emission.
+// `work`: about how many emissions the rows make (threads or not).
 template <typename RowFn>
-Csr build_rows(int n, int m, RowFn &&row) {
+Csr build_rows(int n, int m, long long work, RowFn &&row) {
   Csr C;
   C.n = n;
   C.m = m;
   C.ptr.assign(n + 1, 0);
-#pragma omp parallel
+  const int chunk = row_chunk(n);
+  const bool pa = par(work);
+#pragma omp parallel if (pa)
   {
     std::vector<int32_t> mark(m, -1);
-#pragma omp for schedule(dynamic, 256)
+#pragma omp for schedule(dynamic, chunk)
     for (int i = 0; i < n; ++i) {
       int cnt = 0;
       row(i, mark, [&](int c, double) {
@@ -115,10 +133,10 @@ Csr build_rows(int n, int m, RowFn &&row) {
   for (int i = 0; i < n; ++i) C.ptr[i + 1] += C.ptr[i];
   C.col.resize(C.ptr[n]);
   C.val.resize(C.ptr[n]);
-#pragma omp parallel
+#pragma omp parallel if (pa)
   {
     std::vector<int32_t> mark(m, -1), where(m, 0);
-#pragma omp for schedule(dynamic, 256)
+#pragma omp for schedule(dynamic, chunk)
     for (int i = 0; i < n; ++i) {
       int o = C.ptr[i];
       row(i, mark, [&](int c, double v) {
@@ -147,7 +165,7 @@ Csr transpose(const Csr &A) {
   T.ptr.assign(A.m + 1, 0);
   T.col.resize(A.col.size());
   T.val.resize(A.val.size());
-  const int nt = A.nnz() < (1 << 16) ? 1 : std::max(1, omp_get_max_threads());
+  const int nt = par(A.nnz()) ? std::max(1, omp_get_max_threads()) : 1;
   const size_t m1 = (size_t)A.m + 1;
   std::vector<int32_t> at((size_t)nt * m1, 0);  // per range: count, then start, per column
   auto range = [&](int t, int &lo, int &hi) {
@@ -194,9 +212,13 @@ double rho_estimate(const Csr &A, const std::vector<double> &dinv) {
   const int nch = (A.n + CHUNK - 1) / CHUNK;
   std::vector<double> x(A.n), y(A.n), px(nch), py(nch);
   for (int i = 0; i < A.n; ++i) x[i] = 1.0 + 0.5 * (double)((i * 7919) % 13) / 13.0;
-  double lam = 1.0;
+  double lam = 1.0, sc = 1.0;
+  bool stop = false;
+  // one parallel region for all the steps (a fork per step costs more
+  // than a coarse level's product); the norms are summed by one thread
+#pragma omp parallel if (par(A.nnz()))
   for (int it = 0; it < 12; ++it) {
-#pragma omp parallel for schedule(static)
+#pragma omp for schedule(static)
     for (int c = 0; c < nch; ++c) {
       double sx = 0.0, sy = 0.0;
       const int e = std::min(A.n, (c + 1) * CHUNK);
@@ -210,15 +232,22 @@ double rho_estimate(const Csr &A, const std::vector<double> &dinv) {
       px[c] = sx;
       py[c] = sy;
     }
-    double nx = 0.0, ny = 0.0;
-    for (int c = 0; c < nch; ++c) {
-      nx += px[c];
-      ny += py[c];
+#pragma omp single
+    {
+      double nx = 0.0, ny = 0.0;
+      for (int c = 0; c < nch; ++c) {
+        nx += px[c];
+        ny += py[c];
+      }
+      if (!(ny > 0.0)) {
+        stop = true;
+      } else {
+        lam = std::sqrt(ny / nx);
+        sc = 1.0 / std::sqrt(ny);
+      }
     }
-    if (!(ny > 0.0)) break;
-    lam = std::sqrt(ny / nx);
-    const double sc = 1.0 / std::sqrt(ny);
-#pragma omp parallel for schedule(static)
+    if (stop) break;
+#pragma omp for schedule(static)
     for (int i = 0; i < A.n; ++i) x[i] = y[i] * sc;
   }
   return lam;
@@ -230,7 +259,8 @@ void strength(const Csr &A, double theta, std::vector<int32_t> &sp, std::vector<
   const int n = A.n;
   std::vector<char> st(A.nnz(), 0);
   std::vector<int32_t> cnt(n + 1, 0);
-#pragma omp parallel for schedule(static)
+  const bool pa = par(A.nnz());
+#pragma omp parallel for schedule(static) if (pa)
   for (int i = 0; i < n; ++i) {
     double mx = 0.0;
     for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
@@ -249,14 +279,14 @@ void strength(const Csr &A, double theta, std::vector<int32_t> &sp, std::vector<
   for (int i = 0; i < n; ++i) S1.ptr[i + 1] += S1.ptr[i];
   S1.col.resize(S1.ptr[n]);
   S1.val.assign(S1.ptr[n], 1.0);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (pa)
   for (int i = 0; i < n; ++i) {
     int w = S1.ptr[i];
     for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
       if (st[k]) S1.col[w++] = A.col[k];
   }
   const Csr S1T = transpose(S1);
-  Csr U = build_rows(n, n, [&](int i, std::vector<int32_t> &, auto &&emit) {
+  Csr U = build_rows(n, n, 2 * S1.nnz(), [&](int i, std::vector<int32_t> &, auto &&emit) {
     for (int k = S1.ptr[i]; k < S1.ptr[i + 1]; ++k) emit(S1.col[k], 1.0);
     for (int k = S1T.ptr[i]; k < S1T.ptr[i + 1]; ++k) emit(S1T.col[k], 1.0);
   });
@@ -297,7 +327,7 @@ int aggregate(int n, const std::vector<int32_t> &sp, const std::vector<int32_t> 
 // P = T - w D^-1 A T, T[i, agg[i]] = 1
 Csr smoothed_prolongator(const Csr &A, const std::vector<double> &dinv,
                          const std::vector<int32_t> &agg, int na, double w) {
-  Csr P = build_rows(A.n, na, [&](int i, std::vector<int32_t> &, auto &&emit) {
+  Csr P = build_rows(A.n, na, A.nnz(), [&](int i, std::vector<int32_t> &, auto &&emit) {
     emit(agg[i], 1.0);
     for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) emit(agg[A.col[k]], -w * dinv[i] * A.val[k]);
   });
@@ -320,7 +350,8 @@ Csr smoothed_prolongator(const Csr &A, const std::vector<double> &dinv,
 // C = A B (Gustavson: row i of C accumulates the rows of B picked by row i
 // of A, columns in order of first appearance)
 Csr spgemm(const Csr &A, const Csr &B) {
-  return build_rows(A.n, B.m, [&](int i, std::vector<int32_t> &, auto &&emit) {
+  const long long per = B.n > 0 ? std::max(1LL, B.nnz() / B.n) : 1;
+  return build_rows(A.n, B.m, A.nnz() * per, [&](int i, std::vector<int32_t> &, auto &&emit) {
     for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
       const int r = A.col[k];
       const double a = A.val[k];
@@ -340,10 +371,11 @@ Csr minus_scaled(const Csr &X, const Csr &Y, const std::vector<double> &w, bool 
   C.col = Y.col;
   C.val.resize(Y.val.size());
   int bad = 0;
-#pragma omp parallel
+  const int chunk = row_chunk(Y.n);
+#pragma omp parallel if (par(Y.nnz()))
   {
     std::vector<int32_t> pos(Y.m, -1);
-#pragma omp for schedule(dynamic, 512)
+#pragma omp for schedule(dynamic, chunk)
     for (int i = 0; i < Y.n; ++i) {
       for (int k = Y.ptr[i]; k < Y.ptr[i + 1]; ++k) {
         C.val[k] = -(cols ? w[Y.col[k]] : w[i]) * Y.val[k];
@@ -397,7 +429,8 @@ Csr smoother_matrix(const Csr &A, const std::vector<double> &w) {
   S.n = S.m = A.n;
   S.ptr.assign(A.n + 1, 0);
   std::vector<char> has(A.n, 0);
-#pragma omp parallel for schedule(static)
+  const bool pa = par(A.nnz());
+#pragma omp parallel for schedule(static) if (pa)
   for (int i = 0; i < A.n; ++i) {
     for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) has[i] |= A.col[k] == i;
     S.ptr[i + 1] = A.ptr[i + 1] - A.ptr[i] + !has[i];
@@ -405,7 +438,7 @@ Csr smoother_matrix(const Csr &A, const std::vector<double> &w) {
   for (int i = 0; i < A.n; ++i) S.ptr[i + 1] += S.ptr[i];
   S.col.resize(S.ptr[A.n]);
   S.val.resize(S.ptr[A.n]);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (pa)
   for (int i = 0; i < A.n; ++i) {
     int o = S.ptr[i];
     bool diag = false;
@@ -637,7 +670,7 @@ struct Staging {
     if (buf) {
       T *d = reinterpret_cast<T *>(buf + at);
       const long long m = (long long)v.size();
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (par(m))
       for (long long k = 0; k < m; ++k) d[k] = (T)v[k];
     }
     return at;
@@ -681,7 +714,7 @@ struct AmgJob {
   std::thread th;
   int rc = RBFFD_OK;
   char err[256] = "";
-  std::chrono::steady_clock::time_point t0;
+  double host_ms = 0;  // copy, hierarchy and staging, from the matrix being ready
   Hierarchy H;
   Staging S;
   std::vector<LevelOff> off;
@@ -697,12 +730,16 @@ int host_part(AmgJob &J) {
   const int n = J.n, q = J.q, ldn = J.ldn;
   std::vector<int32_t> hcol((size_t)q * ldn);
   std::vector<double> hval((size_t)q * ldn);
+  if (cudaEventSynchronize(J.ready) != cudaSuccess) {
+    set_error("amg: wait for the p' matrix failed");
+    return RBFFD_ECUDA;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
   {
-    // the copies wait for the packed matrix on a stream of their own
+    // the copies run on a stream of their own (the caller's may hold more work)
     cudaStream_t cs = nullptr;
     RBFFD_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     const bool okc =
-        cudaStreamWaitEvent(cs, J.ready, 0) == cudaSuccess &&
         cudaMemcpyAsync(hcol.data(), J.dcol, hcol.size() * 4, cudaMemcpyDeviceToHost, cs) ==
             cudaSuccess &&
         cudaMemcpyAsync(hval.data(), J.dval, hval.size() * 8, cudaMemcpyDeviceToHost, cs) ==
@@ -721,7 +758,7 @@ int host_part(AmgJob &J) {
   std::vector<double> s0((size_t)q * ldn, 0.0);
   {
     const std::vector<double> &w = H.W[0];
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (par((long long)n * q))
     for (int i = 0; i < n; ++i) {
       bool diag = false;
       for (int j = 0; j < q; ++j) {
@@ -780,6 +817,7 @@ int host_part(AmgJob &J) {
     }
     J.o_cinv = S.put_as<T>(H.cinv);
   }
+  J.host_ms = ms_since(t0);
   return RBFFD_OK;
 }
 
@@ -804,7 +842,6 @@ int amg_build_begin(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
   J->wpb = wpb;
   J->dcol = col;
   J->dval = val;
-  J->t0 = std::chrono::steady_clock::now();
   if (cudaEventCreateWithFlags(&J->ready, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventRecord(J->ready, ctx->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -878,7 +915,7 @@ int amg_build_end(rbffd_ctx *ctx, AmgJob *J, void **mem, size_t *bytes,
   *bytes = S.size;
   *dev = (const AmgDevT<T> *)(base + J->o_dev);
   if (host_view) *host_view = h;
-  fill_info(H, ms_since(J->t0), info);
+  fill_info(H, J->host_ms, info);
   return RBFFD_OK;
 }
 
