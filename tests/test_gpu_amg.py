@@ -74,6 +74,31 @@ def test_amg_reload_and_fallbacks():
     assert len(P.amg_info()) >= 2
 
 
+@pytest.mark.parametrize("pc", [rbffd.PRECOND_AMG, rbffd.PRECOND_AMG_FGMRES])
+def test_pending_hierarchy_dropped_or_finished(pc):
+    """The hierarchy's host part runs on a thread of its own from the build
+    on: a problem destroyed or rebuilt while it runs drops it, and the
+    first solve after back-to-back rebuilds gives the iterate of a problem
+    whose hierarchy was finished before its first solve."""
+    fp = clouds.kovasznay(30, dt=0.4)
+    for _ in range(3):
+        rbffd.Problem(ctx(), fp, precond=pc).close()  # destroyed mid-build
+    A = rbffd.Problem(ctx(), fp, precond=pc)
+    A.reload(fp, precond=pc)
+    A.reload(fp, precond=pc)  # two pending builds dropped
+    B = rbffd.Problem(ctx(), fp, precond=pc)
+    assert B.amg_info() == A.amg_info()  # finishes both builds
+    for X in (A, B):
+        for k, a in (fp.initial or {}).items():
+            X.set(k, a)
+    da, sa = A.simple_iterate(fp.dt, krylov_tol=1e-12)
+    db, sb = B.simple_iterate(fp.dt, krylov_tol=1e-12)
+    assert sa["relres"][2] <= 1e-12 and sb["relres"][2] <= 1e-12
+    assert abs(da - db) <= 1e-10 * abs(db)
+    for k in ("u", "v", "p"):
+        assert rel_l2(A.get(k), B.get(k)) <= 1e-10, k
+
+
 @pytest.mark.parametrize("prec", [rbffd.PREC_MIXED, rbffd.PREC_MIXED_FF])
 @pytest.mark.parametrize("pc", [rbffd.PRECOND_AMG, rbffd.PRECOND_AMG_FGMRES])
 @pytest.mark.parametrize("case", ["kovasznay30", "channel_sym"])
