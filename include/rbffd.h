@@ -32,7 +32,8 @@ extern "C" {
 enum {
   RBFFD_OK = 0,
   RBFFD_EINVAL = -1,     /* bad argument (sizes, q < m, q > n, null pointer) */
-  RBFFD_ENOMEM = -2,     /* device allocation failed or HBM budget exceeded */
+  RBFFD_ENOMEM = -2,     /* device allocation failed, HBM budget exceeded, or host memory
+                            or a host thread could not be had */
   RBFFD_ESINGULAR = -3,  /* a local collocation matrix had an exactly zero pivot */
   RBFFD_ENOCONV = -4,    /* a Krylov solve or the outer loop hit its limit */
   RBFFD_EDIVERGED = -5,  /* a non-finite value appeared */

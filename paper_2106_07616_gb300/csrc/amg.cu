@@ -27,6 +27,7 @@
 #include <omp.h>
 #endif
 
+#include "abi_guard.cuh"
 #include "amg.cuh"
 #include "amg_job.cuh"
 #include "krylov_dev.cuh"
@@ -850,11 +851,19 @@ int amg_build_begin(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
     set_error("amg: event for the hierarchy build failed");
     return RBFFD_ECUDA;
   }
-  J->th = std::thread([J] {
-    cudaSetDevice(J->device);
-    J->rc = host_part<T>(*J);
-    if (J->rc != RBFFD_OK) snprintf(J->err, sizeof(J->err), "%s", rbffd_last_error());
+  const int rc = guarded([&] {
+    J->th = std::thread([J] {
+      cudaSetDevice(J->device);
+      J->rc = guarded([J] { return host_part<T>(*J); });
+      if (J->rc != RBFFD_OK) snprintf(J->err, sizeof(J->err), "%s", rbffd_last_error());
+    });
+    return RBFFD_OK;
   });
+  if (rc != RBFFD_OK) {
+    join(J);
+    delete J;
+    return rc;
+  }
   *job = J;
   return RBFFD_OK;
 }

@@ -11,6 +11,7 @@
 #include <numeric>
 #include <vector>
 
+#include "abi_guard.cuh"
 #include "batch.cuh"
 #include "fgmres.cuh"
 #include "krylov_dev.cuh"
@@ -642,29 +643,31 @@ struct rbffd_batch {
 
 extern "C" int rbffd_batch_create(rbffd_ctx *ctx, int32_t count, rbffd_problem *const *members,
                                   rbffd_batch **out) {
-  if (!ctx || !out || count < 1 || !members) return RBFFD_EINVAL;
-  *out = nullptr;
-  for (int i = 0; i < count; ++i) {
-    if (!members[i] || members[i]->ctx != ctx ||
-        (members[i]->precision != RBFFD_PREC_FP64 &&
-         members[i]->precond == RBFFD_PRECOND_JACOBI)) {
-      set_error("rbffd_batch_create: member %d is null, on another context, or mixed-precision "
-                "with a Jacobi p' solver", i);
-      return RBFFD_EINVAL;
+  return guarded([&]() -> int {
+    if (!ctx || !out || count < 1 || !members) return RBFFD_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+      if (!members[i] || members[i]->ctx != ctx ||
+          (members[i]->precision != RBFFD_PREC_FP64 &&
+           members[i]->precond == RBFFD_PRECOND_JACOBI)) {
+        set_error("rbffd_batch_create: member %d is null, on another context, or mixed-precision "
+                  "with a Jacobi p' solver", i);
+        return RBFFD_EINVAL;
+      }
     }
-  }
-  rbffd_batch *b = new rbffd_batch();
-  b->ctx = ctx;
-  ctx_ref(ctx);
-  b->members.assign(members, members + count);
-  int rc = b->scratch.reserve(ctx, count);
-  if (rc != RBFFD_OK) {
-    delete b;
-    ctx_unref(ctx);
-    return rc;
-  }
-  *out = b;
-  return RBFFD_OK;
+    rbffd_batch *b = new rbffd_batch();
+    b->ctx = ctx;
+    ctx_ref(ctx);
+    b->members.assign(members, members + count);
+    int rc = b->scratch.reserve(ctx, count);
+    if (rc != RBFFD_OK) {
+      delete b;
+      ctx_unref(ctx);
+      return rc;
+    }
+    *out = b;
+    return RBFFD_OK;
+  });
 }
 
 extern "C" void rbffd_batch_destroy(rbffd_batch *b) {
@@ -677,51 +680,55 @@ extern "C" void rbffd_batch_destroy(rbffd_batch *b) {
 
 extern "C" int rbffd_batch_graph_stats(const rbffd_batch *b, int64_t *captures,
                                        int64_t *replays, int64_t *kernels) {
-  if (!b) return RBFFD_EINVAL;
-  if (captures) *captures = b->scratch.captures;
-  if (replays) *replays = b->scratch.replays;
-  if (kernels) *kernels = b->scratch.graph_off ? 0 : b->scratch.graph_launches;
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!b) return RBFFD_EINVAL;
+    if (captures) *captures = b->scratch.captures;
+    if (replays) *replays = b->scratch.replays;
+    if (kernels) *kernels = b->scratch.graph_off ? 0 : b->scratch.graph_launches;
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int rbffd_batch_iterate(rbffd_batch *b, const rbffd_step_params *sp,
                                    const double *dt, const int32_t *active, double *deltas,
                                    rbffd_iter_stats *stats, int32_t *status) {
-  if (!b || !sp) return RBFFD_EINVAL;
-  if (!(sp->dt > 0) || !(sp->krylov_tol > 0) || sp->krylov_maxit < 1 || sp->alpha[0] == 0.0)
-    return RBFFD_EINVAL;
-  RBFFD_CK(cudaSetDevice(b->ctx->device));
-  const int count = (int)b->members.size();
-  std::vector<rbffd_problem *> act;
-  std::vector<int> where;
-  for (int i = 0; i < count; ++i)
-    if (!active || active[i]) {
-      act.push_back(b->members[i]);
-      where.push_back(i);
+  return guarded([&]() -> int {
+    if (!b || !sp) return RBFFD_EINVAL;
+    if (!(sp->dt > 0) || !(sp->krylov_tol > 0) || sp->krylov_maxit < 1 || sp->alpha[0] == 0.0)
+      return RBFFD_EINVAL;
+    RBFFD_CK(cudaSetDevice(b->ctx->device));
+    const int count = (int)b->members.size();
+    std::vector<rbffd_problem *> act;
+    std::vector<int> where;
+    for (int i = 0; i < count; ++i)
+      if (!active || active[i]) {
+        act.push_back(b->members[i]);
+        where.push_back(i);
+      }
+    std::vector<double> d(act.size());
+    std::vector<rbffd_iter_stats> st(act.size());
+    std::vector<int> sts(act.size());
+    std::vector<rbffd_step_params> own(act.size(), *sp);
+    std::vector<const rbffd_step_params *> spv(act.size());
+    for (size_t k = 0; k < act.size(); ++k) {
+      if (dt) {
+        if (!(dt[where[k]] > 0)) return RBFFD_EINVAL;
+        own[k].dt = dt[where[k]];
+      }
+      spv[k] = &own[k];
     }
-  std::vector<double> d(act.size());
-  std::vector<rbffd_iter_stats> st(act.size());
-  std::vector<int> sts(act.size());
-  std::vector<rbffd_step_params> own(act.size(), *sp);
-  std::vector<const rbffd_step_params *> spv(act.size());
-  for (size_t k = 0; k < act.size(); ++k) {
-    if (dt) {
-      if (!(dt[where[k]] > 0)) return RBFFD_EINVAL;
-      own[k].dt = dt[where[k]];
+    int rc = batch_iterate(b->scratch, act.data(), (int)act.size(), spv.data(), d.data(),
+                           st.data(), sts.data());
+    if (rc != RBFFD_OK) return rc;
+    int worst = RBFFD_OK;
+    for (size_t k = 0; k < act.size(); ++k) {
+      const int i = where[k];
+      if (deltas) deltas[i] = d[k];
+      if (stats) stats[i] = st[k];
+      if (status) status[i] = sts[k];
+      if (sts[k] != RBFFD_OK && worst == RBFFD_OK) worst = sts[k];
     }
-    spv[k] = &own[k];
-  }
-  int rc = batch_iterate(b->scratch, act.data(), (int)act.size(), spv.data(), d.data(),
-                         st.data(), sts.data());
-  if (rc != RBFFD_OK) return rc;
-  int worst = RBFFD_OK;
-  for (size_t k = 0; k < act.size(); ++k) {
-    const int i = where[k];
-    if (deltas) deltas[i] = d[k];
-    if (stats) stats[i] = st[k];
-    if (status) status[i] = sts[k];
-    if (sts[k] != RBFFD_OK && worst == RBFFD_OK) worst = sts[k];
-  }
-  if (worst != RBFFD_OK && !status) set_error("a batch member's solve failed (%d)", worst);
-  return status ? RBFFD_OK : worst;
+    if (worst != RBFFD_OK && !status) set_error("a batch member's solve failed (%d)", worst);
+    return status ? RBFFD_OK : worst;
+  });
 }

@@ -1,6 +1,7 @@
 // context.cu -- context lifetime, error text, budgeted allocation.
 #include <cstring>
 
+#include "abi_guard.cuh"
 #include "common.cuh"
 
 namespace rbffd {
@@ -60,37 +61,39 @@ extern "C" const char *rbffd_last_error(void) { return g_err; }
 
 extern "C" int rbffd_ctx_create(rbffd_ctx **out, int device, size_t hbm_budget_bytes,
                                 void *cuda_stream) {
-  if (!out) return RBFFD_EINVAL;
-  *out = nullptr;
-  int ndev = 0;
-  RBFFD_CK(cudaGetDeviceCount(&ndev));
-  if (device < 0 || device >= ndev) {
-    set_error("device %d out of range (%d devices)", device, ndev);
-    return RBFFD_EINVAL;
-  }
-  RBFFD_CK(cudaSetDevice(device));
-  rbffd_ctx *c = new rbffd_ctx();
-  c->device = device;
-  c->budget = hbm_budget_bytes;
-  cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (e != cudaSuccess) {
-    delete c;
-    set_error("cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
-    return RBFFD_ECUDA;
-  }
-  if (cuda_stream) {
-    c->stream = (cudaStream_t)cuda_stream;
-  } else {
-    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  return guarded([&]() -> int {
+    if (!out) return RBFFD_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    RBFFD_CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) {
+      set_error("device %d out of range (%d devices)", device, ndev);
+      return RBFFD_EINVAL;
+    }
+    RBFFD_CK(cudaSetDevice(device));
+    rbffd_ctx *c = new rbffd_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
       delete c;
-      set_error("cudaStreamCreate: %s", cudaGetErrorString(e));
+      set_error("cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
       return RBFFD_ECUDA;
     }
-    c->own_stream = true;
-  }
-  *out = c;
-  return RBFFD_OK;
+    if (cuda_stream) {
+      c->stream = (cudaStream_t)cuda_stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        delete c;
+        set_error("cudaStreamCreate: %s", cudaGetErrorString(e));
+        return RBFFD_ECUDA;
+      }
+      c->own_stream = true;
+    }
+    *out = c;
+    return RBFFD_OK;
+  });
 }
 
 static void ctx_free(rbffd_ctx *ctx) {
@@ -117,20 +120,24 @@ extern "C" void rbffd_ctx_destroy(rbffd_ctx *ctx) {
 }
 
 extern "C" int rbffd_ctx_profile(rbffd_ctx *ctx, int enable) {
-  if (!ctx) return RBFFD_EINVAL;
-  RBFFD_CK(cudaSetDevice(ctx->device));
-  if (enable && !ctx->ev[0]) {
-    for (int k = 0; k < 8; ++k) RBFFD_CK(cudaEventCreate(&ctx->ev[k]));
-  }
-  memset(ctx->kst, 0, sizeof(ctx->kst));
-  ctx->prof = enable != 0;
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!ctx) return RBFFD_EINVAL;
+    RBFFD_CK(cudaSetDevice(ctx->device));
+    if (enable && !ctx->ev[0]) {
+      for (int k = 0; k < 8; ++k) RBFFD_CK(cudaEventCreate(&ctx->ev[k]));
+    }
+    memset(ctx->kst, 0, sizeof(ctx->kst));
+    ctx->prof = enable != 0;
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int rbffd_ctx_kernel_stat(const rbffd_ctx *ctx, int32_t which, rbffd_kernel_stat *out) {
-  if (!ctx || !out || which < 0 || which >= RBFFD_KSTAT_COUNT) return RBFFD_EINVAL;
-  *out = ctx->kst[which];
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!ctx || !out || which < 0 || which >= RBFFD_KSTAT_COUNT) return RBFFD_EINVAL;
+    *out = ctx->kst[which];
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int64_t rbffd_ctx_launch_count(const rbffd_ctx *ctx) { return ctx ? ctx->launches : 0; }

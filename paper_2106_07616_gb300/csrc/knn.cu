@@ -11,6 +11,7 @@
 // the nearest image and wraps the ring around the grid, each column (row)
 // visited once at its smallest offset; a cell at wrapped offset r + 1 is
 // still at least r cells away, so the clearance bound holds.
+#include "abi_guard.cuh"
 #include "common.cuh"
 #include "knn.cuh"
 
@@ -274,19 +275,21 @@ using namespace rbffd;
 
 extern "C" int rbffd_build_stencils(rbffd_ctx *ctx, int32_t n, const double *x, const double *y,
                                     const int8_t *tag, int32_t q, int32_t *idx) {
-  if (!ctx || !x || !y || !idx || n < 1 || q < 1 || q > n || q > 129) {
-    set_error("rbffd_build_stencils: bad arguments (n=%d q=%d)", n, q);
-    return RBFFD_EINVAL;
-  }
-  RBFFD_CK(cudaSetDevice(ctx->device));
-  KnnLayout lay;
-  knn_workspace_bytes(n, &lay);
-  void *ws = nullptr;
-  RBFFD_TRY(dev_alloc(ctx, &ws, lay.bytes));
-  int rc = knn_run(ctx, ws, lay, n, x, y, tag, q, idx, 0.0, 0.0);
-  cudaStreamSynchronize(ctx->stream);
-  dev_free(ctx, ws, lay.bytes);
-  return rc;
+  return guarded([&]() -> int {
+    if (!ctx || !x || !y || !idx || n < 1 || q < 1 || q > n || q > 129) {
+      set_error("rbffd_build_stencils: bad arguments (n=%d q=%d)", n, q);
+      return RBFFD_EINVAL;
+    }
+    RBFFD_CK(cudaSetDevice(ctx->device));
+    KnnLayout lay;
+    knn_workspace_bytes(n, &lay);
+    void *ws = nullptr;
+    RBFFD_TRY(dev_alloc(ctx, &ws, lay.bytes));
+    int rc = knn_run(ctx, ws, lay, n, x, y, tag, q, idx, 0.0, 0.0);
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, ws, lay.bytes);
+    return rc;
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -334,26 +337,28 @@ static int static_scratch(int device, void **out) {
 extern "C" int rbffd_build_stencils_static(rbffd_ctx *ctx, int32_t n, const double *x,
                                            const double *y, const int8_t *tag, int32_t q,
                                            int32_t *idx) {
-  if (!ctx || !x || !y || !idx || n < 1 || q < 1 || q > n || q > 129) {
-    set_error("rbffd_build_stencils_static: bad arguments (n=%d q=%d)", n, q);
-    return RBFFD_EINVAL;
-  }
-  if (n > RBFFD_STATIC_MAX_POINTS) {
-    set_error("rbffd_build_stencils_static: n=%d exceeds the static limit of %d points", n,
-              RBFFD_STATIC_MAX_POINTS);
-    return RBFFD_EINVAL;
-  }
-  KnnLayout lay;
-  knn_workspace_bytes(n, &lay);
-  if (lay.bytes > sizeof(g_knn_scratch)) {
-    set_error("rbffd_build_stencils_static: workspace of %zu bytes exceeds the %zu-byte array",
-              lay.bytes, sizeof(g_knn_scratch));
-    return RBFFD_EINVAL;
-  }
-  RBFFD_CK(cudaSetDevice(ctx->device));
-  void *ws = nullptr;
-  RBFFD_TRY(static_scratch(ctx->device, &ws));
-  // knn_run clears the counters, cursors and error word it reads before
-  // writing them, so the contents left by an earlier call do not matter.
-  return knn_run(ctx, ws, lay, n, x, y, tag, q, idx, 0.0, 0.0);
+  return guarded([&]() -> int {
+    if (!ctx || !x || !y || !idx || n < 1 || q < 1 || q > n || q > 129) {
+      set_error("rbffd_build_stencils_static: bad arguments (n=%d q=%d)", n, q);
+      return RBFFD_EINVAL;
+    }
+    if (n > RBFFD_STATIC_MAX_POINTS) {
+      set_error("rbffd_build_stencils_static: n=%d exceeds the static limit of %d points", n,
+                RBFFD_STATIC_MAX_POINTS);
+      return RBFFD_EINVAL;
+    }
+    KnnLayout lay;
+    knn_workspace_bytes(n, &lay);
+    if (lay.bytes > sizeof(g_knn_scratch)) {
+      set_error("rbffd_build_stencils_static: workspace of %zu bytes exceeds the %zu-byte array",
+                lay.bytes, sizeof(g_knn_scratch));
+      return RBFFD_EINVAL;
+    }
+    RBFFD_CK(cudaSetDevice(ctx->device));
+    void *ws = nullptr;
+    RBFFD_TRY(static_scratch(ctx->device, &ws));
+    // knn_run clears the counters, cursors and error word it reads before
+    // writing them, so the contents left by an earlier call do not matter.
+    return knn_run(ctx, ws, lay, n, x, y, tag, q, idx, 0.0, 0.0);
+  });
 }

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <vector>
 
+#include "abi_guard.cuh"
 #include "fgmres.cuh"
 #include "ops.cuh"
 #include "problem.cuh"
@@ -445,155 +446,159 @@ rbffd_step_params step_from(const rbffd_solve_params *s) {
 
 extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
                                     rbffd_problem **out) {
-  if (!ctx || !out) return RBFFD_EINVAL;
-  *out = nullptr;
-  RBFFD_TRY(check_desc(d));
-  RBFFD_CK(cudaSetDevice(ctx->device));
-  rbffd_problem *P = new rbffd_problem();
-  P->ctx = ctx;
-  ctx_ref(ctx);
-  P->n = d->n;
-  P->q = d->q;
-  P->degree = d->degree;
-  P->precision = d->precision;
-  P->ldn = (int)round_up(d->n, 128);
-  const int n = P->n, q = P->q;
-  const size_t nq = (size_t)n * q, lq = (size_t)P->ldn * q;
-  knn_workspace_bytes(n, &P->knn_lay);
-  P->kblocks1 = krylov_blocks_for(ctx, n, 1);
-  P->kblocks2 = krylov_blocks_for(ctx, n, 2);
-  const bool mixed = d->precision != RBFFD_PREC_FP64;
-  P->inner = d->precision == RBFFD_PREC_MIXED_FF ? INNER_FF : INNER_F32;
-  const size_t es = P->inner == INNER_FF ? 8 : 4;  // bytes per inner value
-  if (mixed) {
-    int c1 = krylov_ir_max_blocks(ctx, 1, P->inner), c2 = krylov_ir_max_blocks(ctx, 2, P->inner);
-    if (P->kblocks1 > c1) P->kblocks1 = c1;
-    if (P->kblocks2 > c2) P->kblocks2 = c2;
-  }
-  P->rblocks = ops_reduce_blocks(ctx, n);
-  // partials: room for two right-hand sides over the larger grid (a batched
-  // launch may give one member two single-RHS systems, or one system twice
-  // the CTAs)
-  const int kbmax = P->kblocks1 > P->kblocks2 ? P->kblocks1 : P->kblocks2;
-  size_t npart = krylov_partials_doubles(2, kbmax);
-  Carver c;
-  size_t o_x = c.take<double>(n), o_y = c.take<double>(n), o_nx = c.take<double>(n),
-         o_ny = c.take<double>(n), o_ubc = c.take<double>(n), o_vbc = c.take<double>(n),
-         o_tag = c.take<int8_t>(n);
-  size_t o_idx = c.take<int32_t>(nq), o_wx = c.take<double>(nq), o_wy = c.take<double>(nq),
-         o_wl = c.take<double>(nq);
-  size_t o_col = c.take<int32_t>(lq), o_Wx = c.take<double>(lq), o_Wy = c.take<double>(lq),
-         o_Wl = c.take<double>(lq), o_Pp = c.take<double>(lq), o_Am = c.take<double>(lq),
-         o_Am2 = c.take<double>(lq);
-  size_t o_pd = c.take<double>(P->ldn), o_md = c.take<double>(P->ldn),
-         o_md2 = c.take<double>(P->ldn);
-  size_t o_f[14];
-  for (int k = 0; k < 14; ++k) o_f[k] = c.take<double>(n);
-  size_t o_kv[16];
-  for (int k = 0; k < 16; ++k) o_kv[k] = c.take<double>(n);
-  size_t o_part = c.take<double>(npart), o_rpart = c.take<double>(7 * (size_t)P->rblocks);
-  size_t o_bar = c.take<GridBarrier>(1);
-  size_t o_flags = c.take<unsigned int>(256);
-  size_t o_rec = c.take<Readback>(1);
-  size_t o_fs = c.take<int>(1);
-  size_t o_knn = c.take<char>(P->knn_lay.bytes);
-  size_t o_p32 = 0, o_a32 = 0, o_pd32 = 0, o_md32 = 0, o_mv[18] = {}, o_part64 = 0, o_part32 = 0;
-  size_t o_a32b = 0, o_md32b = 0;
-  if (mixed) {
-    o_p32 = c.take<char>(lq * es);
-    o_a32 = c.take<char>(lq * es);
-    o_a32b = c.take<char>(lq * es);
-    o_pd32 = c.take<char>(P->ldn * es);
-    o_md32 = c.take<char>(P->ldn * es);
-    o_md32b = c.take<char>(P->ldn * es);
-    for (int k = 0; k < 18; ++k) o_mv[k] = c.take<char>((size_t)n * es);
-    int kb = P->kblocks1 > P->kblocks2 ? P->kblocks1 : P->kblocks2;
-    o_part64 = c.take<double>(krylov_ir_partials64(2, kb));
-    o_part32 = c.take<char>(krylov_ir_partials_inner_bytes(2, kb, P->inner));
-  }
-  P->bytes = c.off;
-  int rc = dev_alloc(ctx, &P->mem, P->bytes);
-  if (rc != RBFFD_OK) {
-    delete P;
-    ctx_unref(ctx);
-    return rc;
-  }
-  char *b = (char *)P->mem;
-  P->x = (double *)(b + o_x);
-  P->y = (double *)(b + o_y);
-  P->nx = (double *)(b + o_nx);
-  P->ny = (double *)(b + o_ny);
-  P->ubc = (double *)(b + o_ubc);
-  P->vbc = (double *)(b + o_vbc);
-  P->tag = (int8_t *)(b + o_tag);
-  P->idx_rm = (int32_t *)(b + o_idx);
-  P->wx_rm = (double *)(b + o_wx);
-  P->wy_rm = (double *)(b + o_wy);
-  P->wl_rm = (double *)(b + o_wl);
-  P->col = (int32_t *)(b + o_col);
-  P->Wx = (double *)(b + o_Wx);
-  P->Wy = (double *)(b + o_Wy);
-  P->Wl = (double *)(b + o_Wl);
-  P->Pp = (double *)(b + o_Pp);
-  P->Am = (double *)(b + o_Am);
-  P->Am2 = (double *)(b + o_Am2);
-  P->p_dinv = (double *)(b + o_pd);
-  P->m_dinv = (double *)(b + o_md);
-  P->m_dinv2 = (double *)(b + o_md2);
-  double **f[14] = {&P->u,  &P->v,  &P->p,  &P->p2, &P->un, &P->vn, &P->unm1,
-                    &P->vnm1, &P->ut, &P->vt, &P->pc, &P->bu, &P->bv, &P->bp};
-  for (int k = 0; k < 14; ++k) *f[k] = (double *)(b + o_f[k]);
-  for (int r = 0; r < 2; ++r) {
-    double **w[8] = {&P->kv[r].r, &P->kv[r].rh, &P->kv[r].p, &P->kv[r].v,
-                     &P->kv[r].ph, &P->kv[r].s, &P->kv[r].sh, &P->kv[r].t};
-    for (int k = 0; k < 8; ++k) *w[k] = (double *)(b + o_kv[r * 8 + k]);
-  }
-  P->part = (double *)(b + o_part);
-  P->rpart = (double *)(b + o_rpart);
-  P->bar = (GridBarrier *)(b + o_bar);
-  P->flags = (unsigned int *)(b + o_flags);
-  P->rec = (IterRecord *)(b + o_rec);
-  P->kout = (KrylovOut *)((char *)P->rec + sizeof(IterRecord));
-  P->d_first_singular = (int *)(b + o_fs);
-  P->knn_ws = (void *)(b + o_knn);
-  if (mixed) {
-    P->Pin = (void *)(b + o_p32);
-    P->Ain = (void *)(b + o_a32);
-    P->pdin = (void *)(b + o_pd32);
-    P->mdin = (void *)(b + o_md32);
-    P->Ain2 = (void *)(b + o_a32b);
-    P->mdin2 = (void *)(b + o_md32b);
-    for (int r = 0; r < 2; ++r) {
-      void **w[9] = {&P->mv[r].r, &P->mv[r].rh, &P->mv[r].p0, &P->mv[r].p1, &P->mv[r].v0,
-                     &P->mv[r].v1, &P->mv[r].s, &P->mv[r].t, &P->mv[r].d};
-      for (int k = 0; k < 9; ++k) *w[k] = (void *)(b + o_mv[r * 9 + k]);
+  return guarded([&]() -> int {
+    if (!ctx || !out) return RBFFD_EINVAL;
+    *out = nullptr;
+    RBFFD_TRY(check_desc(d));
+    RBFFD_CK(cudaSetDevice(ctx->device));
+    rbffd_problem *P = new rbffd_problem();
+    P->ctx = ctx;
+    ctx_ref(ctx);
+    P->n = d->n;
+    P->q = d->q;
+    P->degree = d->degree;
+    P->precision = d->precision;
+    P->ldn = (int)round_up(d->n, 128);
+    const int n = P->n, q = P->q;
+    const size_t nq = (size_t)n * q, lq = (size_t)P->ldn * q;
+    knn_workspace_bytes(n, &P->knn_lay);
+    P->kblocks1 = krylov_blocks_for(ctx, n, 1);
+    P->kblocks2 = krylov_blocks_for(ctx, n, 2);
+    const bool mixed = d->precision != RBFFD_PREC_FP64;
+    P->inner = d->precision == RBFFD_PREC_MIXED_FF ? INNER_FF : INNER_F32;
+    const size_t es = P->inner == INNER_FF ? 8 : 4;  // bytes per inner value
+    if (mixed) {
+      int c1 = krylov_ir_max_blocks(ctx, 1, P->inner), c2 = krylov_ir_max_blocks(ctx, 2, P->inner);
+      if (P->kblocks1 > c1) P->kblocks1 = c1;
+      if (P->kblocks2 > c2) P->kblocks2 = c2;
     }
-    P->part64 = (double *)(b + o_part64);
-    P->partin = (void *)(b + o_part32);
-  }
-  if (cudaMemsetAsync(P->mem, 0, P->bytes, ctx->stream) != cudaSuccess) {
-    set_error("cudaMemsetAsync failed");
-    rbffd_problem_destroy(P);
-    return RBFFD_ECUDA;
-  }
-  rc = build(P, d);
-  if (rc != RBFFD_OK) {
-    rbffd_problem_destroy(P);
-    return rc;
-  }
-  *out = P;
-  return RBFFD_OK;
+    P->rblocks = ops_reduce_blocks(ctx, n);
+    // partials: room for two right-hand sides over the larger grid (a batched
+    // launch may give one member two single-RHS systems, or one system twice
+    // the CTAs)
+    const int kbmax = P->kblocks1 > P->kblocks2 ? P->kblocks1 : P->kblocks2;
+    size_t npart = krylov_partials_doubles(2, kbmax);
+    Carver c;
+    size_t o_x = c.take<double>(n), o_y = c.take<double>(n), o_nx = c.take<double>(n),
+           o_ny = c.take<double>(n), o_ubc = c.take<double>(n), o_vbc = c.take<double>(n),
+           o_tag = c.take<int8_t>(n);
+    size_t o_idx = c.take<int32_t>(nq), o_wx = c.take<double>(nq), o_wy = c.take<double>(nq),
+           o_wl = c.take<double>(nq);
+    size_t o_col = c.take<int32_t>(lq), o_Wx = c.take<double>(lq), o_Wy = c.take<double>(lq),
+           o_Wl = c.take<double>(lq), o_Pp = c.take<double>(lq), o_Am = c.take<double>(lq),
+           o_Am2 = c.take<double>(lq);
+    size_t o_pd = c.take<double>(P->ldn), o_md = c.take<double>(P->ldn),
+           o_md2 = c.take<double>(P->ldn);
+    size_t o_f[14];
+    for (int k = 0; k < 14; ++k) o_f[k] = c.take<double>(n);
+    size_t o_kv[16];
+    for (int k = 0; k < 16; ++k) o_kv[k] = c.take<double>(n);
+    size_t o_part = c.take<double>(npart), o_rpart = c.take<double>(7 * (size_t)P->rblocks);
+    size_t o_bar = c.take<GridBarrier>(1);
+    size_t o_flags = c.take<unsigned int>(256);
+    size_t o_rec = c.take<Readback>(1);
+    size_t o_fs = c.take<int>(1);
+    size_t o_knn = c.take<char>(P->knn_lay.bytes);
+    size_t o_p32 = 0, o_a32 = 0, o_pd32 = 0, o_md32 = 0, o_mv[18] = {}, o_part64 = 0, o_part32 = 0;
+    size_t o_a32b = 0, o_md32b = 0;
+    if (mixed) {
+      o_p32 = c.take<char>(lq * es);
+      o_a32 = c.take<char>(lq * es);
+      o_a32b = c.take<char>(lq * es);
+      o_pd32 = c.take<char>(P->ldn * es);
+      o_md32 = c.take<char>(P->ldn * es);
+      o_md32b = c.take<char>(P->ldn * es);
+      for (int k = 0; k < 18; ++k) o_mv[k] = c.take<char>((size_t)n * es);
+      int kb = P->kblocks1 > P->kblocks2 ? P->kblocks1 : P->kblocks2;
+      o_part64 = c.take<double>(krylov_ir_partials64(2, kb));
+      o_part32 = c.take<char>(krylov_ir_partials_inner_bytes(2, kb, P->inner));
+    }
+    P->bytes = c.off;
+    int rc = dev_alloc(ctx, &P->mem, P->bytes);
+    if (rc != RBFFD_OK) {
+      delete P;
+      ctx_unref(ctx);
+      return rc;
+    }
+    char *b = (char *)P->mem;
+    P->x = (double *)(b + o_x);
+    P->y = (double *)(b + o_y);
+    P->nx = (double *)(b + o_nx);
+    P->ny = (double *)(b + o_ny);
+    P->ubc = (double *)(b + o_ubc);
+    P->vbc = (double *)(b + o_vbc);
+    P->tag = (int8_t *)(b + o_tag);
+    P->idx_rm = (int32_t *)(b + o_idx);
+    P->wx_rm = (double *)(b + o_wx);
+    P->wy_rm = (double *)(b + o_wy);
+    P->wl_rm = (double *)(b + o_wl);
+    P->col = (int32_t *)(b + o_col);
+    P->Wx = (double *)(b + o_Wx);
+    P->Wy = (double *)(b + o_Wy);
+    P->Wl = (double *)(b + o_Wl);
+    P->Pp = (double *)(b + o_Pp);
+    P->Am = (double *)(b + o_Am);
+    P->Am2 = (double *)(b + o_Am2);
+    P->p_dinv = (double *)(b + o_pd);
+    P->m_dinv = (double *)(b + o_md);
+    P->m_dinv2 = (double *)(b + o_md2);
+    double **f[14] = {&P->u,  &P->v,  &P->p,  &P->p2, &P->un, &P->vn, &P->unm1,
+                      &P->vnm1, &P->ut, &P->vt, &P->pc, &P->bu, &P->bv, &P->bp};
+    for (int k = 0; k < 14; ++k) *f[k] = (double *)(b + o_f[k]);
+    for (int r = 0; r < 2; ++r) {
+      double **w[8] = {&P->kv[r].r, &P->kv[r].rh, &P->kv[r].p, &P->kv[r].v,
+                       &P->kv[r].ph, &P->kv[r].s, &P->kv[r].sh, &P->kv[r].t};
+      for (int k = 0; k < 8; ++k) *w[k] = (double *)(b + o_kv[r * 8 + k]);
+    }
+    P->part = (double *)(b + o_part);
+    P->rpart = (double *)(b + o_rpart);
+    P->bar = (GridBarrier *)(b + o_bar);
+    P->flags = (unsigned int *)(b + o_flags);
+    P->rec = (IterRecord *)(b + o_rec);
+    P->kout = (KrylovOut *)((char *)P->rec + sizeof(IterRecord));
+    P->d_first_singular = (int *)(b + o_fs);
+    P->knn_ws = (void *)(b + o_knn);
+    if (mixed) {
+      P->Pin = (void *)(b + o_p32);
+      P->Ain = (void *)(b + o_a32);
+      P->pdin = (void *)(b + o_pd32);
+      P->mdin = (void *)(b + o_md32);
+      P->Ain2 = (void *)(b + o_a32b);
+      P->mdin2 = (void *)(b + o_md32b);
+      for (int r = 0; r < 2; ++r) {
+        void **w[9] = {&P->mv[r].r, &P->mv[r].rh, &P->mv[r].p0, &P->mv[r].p1, &P->mv[r].v0,
+                       &P->mv[r].v1, &P->mv[r].s, &P->mv[r].t, &P->mv[r].d};
+        for (int k = 0; k < 9; ++k) *w[k] = (void *)(b + o_mv[r * 9 + k]);
+      }
+      P->part64 = (double *)(b + o_part64);
+      P->partin = (void *)(b + o_part32);
+    }
+    if (cudaMemsetAsync(P->mem, 0, P->bytes, ctx->stream) != cudaSuccess) {
+      set_error("cudaMemsetAsync failed");
+      rbffd_problem_destroy(P);
+      return RBFFD_ECUDA;
+    }
+    rc = build(P, d);
+    if (rc != RBFFD_OK) {
+      rbffd_problem_destroy(P);
+      return rc;
+    }
+    *out = P;
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int rbffd_problem_reload(rbffd_problem *P, const rbffd_problem_desc *d) {
-  if (!P) return RBFFD_EINVAL;
-  RBFFD_TRY(check_desc(d));
-  if (d->n != P->n || d->q != P->q || d->degree != P->degree || d->precision != P->precision) {
-    set_error("reload: n, q, degree and precision must match the problem");
-    return RBFFD_EINVAL;
-  }
-  RBFFD_CK(cudaSetDevice(P->ctx->device));
-  return build(P, d);
+  return guarded([&]() -> int {
+    if (!P) return RBFFD_EINVAL;
+    RBFFD_TRY(check_desc(d));
+    if (d->n != P->n || d->q != P->q || d->degree != P->degree || d->precision != P->precision) {
+      set_error("reload: n, q, degree and precision must match the problem");
+      return RBFFD_EINVAL;
+    }
+    RBFFD_CK(cudaSetDevice(P->ctx->device));
+    return build(P, d);
+  });
 }
 
 extern "C" void rbffd_problem_destroy(rbffd_problem *P) {
@@ -624,93 +629,101 @@ static void report_levels(const AmgInfo &I, bool have_any, int32_t *levels, int3
 
 extern "C" int rbffd_problem_amg_info(const rbffd_problem *P, int32_t *levels, int32_t *rows,
                                       int64_t *nnz, double *setup_ms) {
-  if (!P) return RBFFD_EINVAL;
-  // a hierarchy still being built is finished first (the call is logically
-  // const: it changes no result, only when the upload happens)
-  RBFFD_CK(cudaSetDevice(P->ctx->device));
-  RBFFD_TRY(amg_ready(const_cast<rbffd_problem *>(P)));
-  report_levels(P->amg_info, P->amg != nullptr || P->amgf != nullptr, levels, rows, nnz,
-                setup_ms);
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!P) return RBFFD_EINVAL;
+    // a hierarchy still being built is finished first (the call is logically
+    // const: it changes no result, only when the upload happens)
+    RBFFD_CK(cudaSetDevice(P->ctx->device));
+    RBFFD_TRY(amg_ready(const_cast<rbffd_problem *>(P)));
+    report_levels(P->amg_info, P->amg != nullptr || P->amgf != nullptr, levels, rows, nnz,
+                  setup_ms);
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int rbffd_amg_analyze(int32_t n, const int32_t *rowptr, const int32_t *col,
                                  const double *val, int32_t *levels, int32_t *rows, int64_t *nnz,
                                  double *setup_ms) {
-  if (n < 1 || !rowptr || !col || !val || rowptr[0] != 0) return RBFFD_EINVAL;
-  for (int i = 0; i < n; ++i)
-    if (rowptr[i + 1] < rowptr[i]) return RBFFD_EINVAL;
-  for (int k = 0; k < rowptr[n]; ++k)
-    if (col[k] < 0 || col[k] >= n) return RBFFD_EINVAL;
-  AmgInfo I;
-  RBFFD_TRY(amg_analyze(n, rowptr, col, val, &I));
-  report_levels(I, true, levels, rows, nnz, setup_ms);
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (n < 1 || !rowptr || !col || !val || rowptr[0] != 0) return RBFFD_EINVAL;
+    for (int i = 0; i < n; ++i)
+      if (rowptr[i + 1] < rowptr[i]) return RBFFD_EINVAL;
+    for (int k = 0; k < rowptr[n]; ++k)
+      if (col[k] < 0 || col[k] >= n) return RBFFD_EINVAL;
+    AmgInfo I;
+    RBFFD_TRY(amg_analyze(n, rowptr, col, val, &I));
+    report_levels(I, true, levels, rows, nnz, setup_ms);
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int simple_iterate(rbffd_problem *P, const rbffd_step_params *sp, double *delta_out,
                               rbffd_iter_stats *stats) {
-  if (!P) return RBFFD_EINVAL;
-  RBFFD_TRY(check_params(sp));
-  RBFFD_CK(cudaSetDevice(P->ctx->device));
-  RBFFD_TRY(issue_outer(P, sp));
-  Readback r;
-  RBFFD_TRY(read_back(P, &r));
-  if (P->ctx->prof) {
-    // inner iterations of the FP32 mixed path move 4-byte values and vectors
-    const bool mx = P->precision == RBFFD_PREC_MIXED;
-    const double sw = mx ? 4.0 : 8.0, si = 4.0, sv = mx ? 4.0 : 8.0, q = P->q, n = P->n;
-    int im = r.kout[0].iters > r.kout[1].iters ? r.kout[0].iters : r.kout[1].iters;
-    double um = n * im, upc = n * r.kout[2].iters;
-    prof_collect(P->ctx, 0, RBFFD_KSTAT_KRYLOV_MOM, um, um * (2 * q * (sw + si) + 28 * sv));
-    prof_collect(P->ctx, 1, RBFFD_KSTAT_KRYLOV_P, upc,
-                 mx ? upc * (2 * q * (sw + si) + 14 * sv) : pcorr_bytes(P, r.kout[2].iters));
-    prof_collect(P->ctx, 2, RBFFD_KSTAT_OUTER, 1.0, 0.0);
-  }
-  if (stats) {
-    const bool mixed = P->precision != RBFFD_PREC_FP64;
+  return guarded([&]() -> int {
+    if (!P) return RBFFD_EINVAL;
+    RBFFD_TRY(check_params(sp));
+    RBFFD_CK(cudaSetDevice(P->ctx->device));
+    RBFFD_TRY(issue_outer(P, sp));
+    Readback r;
+    RBFFD_TRY(read_back(P, &r));
+    if (P->ctx->prof) {
+      // inner iterations of the FP32 mixed path move 4-byte values and vectors
+      const bool mx = P->precision == RBFFD_PREC_MIXED;
+      const double sw = mx ? 4.0 : 8.0, si = 4.0, sv = mx ? 4.0 : 8.0, q = P->q, n = P->n;
+      int im = r.kout[0].iters > r.kout[1].iters ? r.kout[0].iters : r.kout[1].iters;
+      double um = n * im, upc = n * r.kout[2].iters;
+      prof_collect(P->ctx, 0, RBFFD_KSTAT_KRYLOV_MOM, um, um * (2 * q * (sw + si) + 28 * sv));
+      prof_collect(P->ctx, 1, RBFFD_KSTAT_KRYLOV_P, upc,
+                   mx ? upc * (2 * q * (sw + si) + 14 * sv) : pcorr_bytes(P, r.kout[2].iters));
+      prof_collect(P->ctx, 2, RBFFD_KSTAT_OUTER, 1.0, 0.0);
+    }
+    if (stats) {
+      const bool mixed = P->precision != RBFFD_PREC_FP64;
+      for (int k = 0; k < 3; ++k) {
+        stats->iters[k] = r.kout[k].iters;
+        stats->relres[k] = r.kout[k].relres;
+        stats->sweeps[k] = r.kout[k].restarts;
+      }
+    }
+    if (delta_out) *delta_out = r.rec.delta;
+    static const char *names[3] = {"momentum u", "momentum v", "pressure correction"};
     for (int k = 0; k < 3; ++k) {
-      stats->iters[k] = r.kout[k].iters;
-      stats->relres[k] = r.kout[k].relres;
-      stats->sweeps[k] = r.kout[k].restarts;
+      int code = krylov_status_code(r.kout[k].status);
+      if (code != RBFFD_OK) {
+        set_error("%s solve failed (status %d after %d iterations, relres %.3e)", names[k],
+                  r.kout[k].status, r.kout[k].iters, r.kout[k].relres);
+        return code;
+      }
     }
-  }
-  if (delta_out) *delta_out = r.rec.delta;
-  static const char *names[3] = {"momentum u", "momentum v", "pressure correction"};
-  for (int k = 0; k < 3; ++k) {
-    int code = krylov_status_code(r.kout[k].status);
-    if (code != RBFFD_OK) {
-      set_error("%s solve failed (status %d after %d iterations, relres %.3e)", names[k],
-                r.kout[k].status, r.kout[k].iters, r.kout[k].relres);
-      return code;
+    if (!std::isfinite(r.rec.delta)) {
+      set_error("outer iteration produced a non-finite delta");
+      return RBFFD_EDIVERGED;
     }
-  }
-  if (!std::isfinite(r.rec.delta)) {
-    set_error("outer iteration produced a non-finite delta");
-    return RBFFD_EDIVERGED;
-  }
-  return RBFFD_OK;
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int rbffd_time_step(rbffd_problem *P, const rbffd_solve_params *s, double tol_outer,
                                int32_t *outer_iters, double *change) {
-  if (!P || !s || s->max_outer < 1) return RBFFD_EINVAL;
-  rbffd_step_params sp = step_from(s);
-  int it = 0, rc = RBFFD_OK;
-  while (it < s->max_outer) {
-    double d = 0.0;
-    rc = simple_iterate(P, &sp, &d, nullptr);
-    ++it;
-    if (rc != RBFFD_OK) break;
-    if (d < tol_outer) break;
-  }
-  if (outer_iters) *outer_iters = it;
-  if (rc != RBFFD_OK) return rc;
-  RBFFD_TRY(ops_rotate(P));
-  Readback r;
-  RBFFD_TRY(read_back(P, &r));
-  if (change) *change = r.rec.change;
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!P || !s || s->max_outer < 1) return RBFFD_EINVAL;
+    rbffd_step_params sp = step_from(s);
+    int it = 0, rc = RBFFD_OK;
+    while (it < s->max_outer) {
+      double d = 0.0;
+      rc = simple_iterate(P, &sp, &d, nullptr);
+      ++it;
+      if (rc != RBFFD_OK) break;
+      if (d < tol_outer) break;
+    }
+    if (outer_iters) *outer_iters = it;
+    if (rc != RBFFD_OK) return rc;
+    RBFFD_TRY(ops_rotate(P));
+    Readback r;
+    RBFFD_TRY(read_back(P, &r));
+    if (change) *change = r.rec.change;
+    return RBFFD_OK;
+  });
 }
 
 namespace rbffd {
@@ -726,26 +739,30 @@ int problem_step_end(rbffd_problem *P, double *change) {
 
 extern "C" int rbffd_courant(rbffd_problem *P, double dt, int32_t iters, double *lambda_out,
                              double *courant_out) {
-  if (!P || iters < 2 || !(dt > 0)) return RBFFD_EINVAL;
-  RBFFD_CK(cudaSetDevice(P->ctx->device));
-  RBFFD_TRY(ops_courant(P, iters, &P->rec->pad[0]));
-  Readback r;
-  RBFFD_TRY(read_back(P, &r));
-  const int counted = iters - iters / 2;
-  const double lam = std::exp(r.rec.pad[0] / counted);
-  if (lambda_out) *lambda_out = lam;
-  if (courant_out) *courant_out = lam * dt / 2.0;
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!P || iters < 2 || !(dt > 0)) return RBFFD_EINVAL;
+    RBFFD_CK(cudaSetDevice(P->ctx->device));
+    RBFFD_TRY(ops_courant(P, iters, &P->rec->pad[0]));
+    Readback r;
+    RBFFD_TRY(read_back(P, &r));
+    const int counted = iters - iters / 2;
+    const double lam = std::exp(r.rec.pad[0] / counted);
+    if (lambda_out) *lambda_out = lam;
+    if (courant_out) *courant_out = lam * dt / 2.0;
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int rbffd_steady_residual(rbffd_problem *P, double *R3) {
-  if (!P || !R3) return RBFFD_EINVAL;
-  RBFFD_CK(cudaSetDevice(P->ctx->device));
-  RBFFD_TRY(ops_resid(P));
-  Readback r;
-  RBFFD_TRY(read_back(P, &r));
-  for (int k = 0; k < 3; ++k) R3[k] = r.rec.resid[k];
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!P || !R3) return RBFFD_EINVAL;
+    RBFFD_CK(cudaSetDevice(P->ctx->device));
+    RBFFD_TRY(ops_resid(P));
+    Readback r;
+    RBFFD_TRY(read_back(P, &r));
+    for (int k = 0; k < 3; ++k) R3[k] = r.rec.resid[k];
+    return RBFFD_OK;
+  });
 }
 
 namespace rbffd {
@@ -847,14 +864,18 @@ static int march(rbffd_problem *P, const rbffd_solve_params *s, int32_t n_steps,
 
 extern "C" int solve_steady(rbffd_problem *P, const rbffd_solve_params *s,
                             rbffd_solve_stats *st) {
-  if (!s) return RBFFD_EINVAL;
-  return march(P, s, s->max_steps, true, nullptr, nullptr, st);
+  return guarded([&]() -> int {
+    if (!s) return RBFFD_EINVAL;
+    return march(P, s, s->max_steps, true, nullptr, nullptr, st);
+  });
 }
 
 extern "C" int solve_unsteady(rbffd_problem *P, const rbffd_solve_params *s, int32_t n_steps,
                               int (*on_step)(void *, int32_t, double), void *user,
                               rbffd_solve_stats *st) {
-  return march(P, s, n_steps, false, on_step, user, st);
+  return guarded([&]() -> int {
+    return march(P, s, n_steps, false, on_step, user, st);
+  });
 }
 
 static double *field_ptr(rbffd_problem *P, int which) {
@@ -876,23 +897,27 @@ static double *field_ptr(rbffd_problem *P, int which) {
 }
 
 extern "C" int rbffd_get_field(rbffd_problem *P, int32_t which, double *out) {
-  if (!P || !out) return RBFFD_EINVAL;
-  double *f = field_ptr(P, which);
-  if (!f) return RBFFD_EINVAL;
-  RBFFD_CK(cudaSetDevice(P->ctx->device));
-  RBFFD_CK(cudaMemcpyAsync(out, f, sizeof(double) * P->n, cudaMemcpyDefault, P->ctx->stream));
-  RBFFD_CK(cudaStreamSynchronize(P->ctx->stream));
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!P || !out) return RBFFD_EINVAL;
+    double *f = field_ptr(P, which);
+    if (!f) return RBFFD_EINVAL;
+    RBFFD_CK(cudaSetDevice(P->ctx->device));
+    RBFFD_CK(cudaMemcpyAsync(out, f, sizeof(double) * P->n, cudaMemcpyDefault, P->ctx->stream));
+    RBFFD_CK(cudaStreamSynchronize(P->ctx->stream));
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int rbffd_set_field(rbffd_problem *P, int32_t which, const double *in) {
-  if (!P || !in) return RBFFD_EINVAL;
-  double *f = field_ptr(P, which);
-  if (!f) return RBFFD_EINVAL;
-  RBFFD_CK(cudaSetDevice(P->ctx->device));
-  RBFFD_CK(cudaMemcpyAsync(f, in, sizeof(double) * P->n, cudaMemcpyDefault, P->ctx->stream));
-  RBFFD_CK(cudaStreamSynchronize(P->ctx->stream));
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!P || !in) return RBFFD_EINVAL;
+    double *f = field_ptr(P, which);
+    if (!f) return RBFFD_EINVAL;
+    RBFFD_CK(cudaSetDevice(P->ctx->device));
+    RBFFD_CK(cudaMemcpyAsync(f, in, sizeof(double) * P->n, cudaMemcpyDefault, P->ctx->stream));
+    RBFFD_CK(cudaStreamSynchronize(P->ctx->stream));
+    return RBFFD_OK;
+  });
 }
 
 namespace {
@@ -906,43 +931,47 @@ __global__ void k_unpack(int n, int q, int ldn, const double *__restrict__ ell,
 
 extern "C" int rbffd_get_operators(rbffd_problem *P, int32_t *idx, double *wx, double *wy,
                                    double *wl, double *pcorr) {
-  if (!P) return RBFFD_EINVAL;
-  RBFFD_CK(cudaSetDevice(P->ctx->device));
-  cudaStream_t st = P->ctx->stream;
-  size_t nq = (size_t)P->n * P->q;
-  if (idx) RBFFD_CK(cudaMemcpyAsync(idx, P->idx_rm, nq * 4, cudaMemcpyDefault, st));
-  if (wx) RBFFD_CK(cudaMemcpyAsync(wx, P->wx_rm, nq * 8, cudaMemcpyDefault, st));
-  if (wy) RBFFD_CK(cudaMemcpyAsync(wy, P->wy_rm, nq * 8, cudaMemcpyDefault, st));
-  if (wl) RBFFD_CK(cudaMemcpyAsync(wl, P->wl_rm, nq * 8, cudaMemcpyDefault, st));
-  if (pcorr) {
-    // row-major copy of the packed pressure-correction matrix via p2 scratch
-    double *tmp = nullptr;
-    RBFFD_TRY(dev_alloc(P->ctx, (void **)&tmp, nq * 8));
-    k_unpack<<<(P->n + 255) / 256, 256, 0, st>>>(P->n, P->q, P->ldn, P->Pp, tmp);
-    int rc = after_launch(P->ctx, "k_unpack");
-    if (rc == RBFFD_OK &&
-        cudaMemcpyAsync(pcorr, tmp, nq * 8, cudaMemcpyDefault, st) != cudaSuccess)
-      rc = RBFFD_ECUDA;
-    cudaStreamSynchronize(st);
-    dev_free(P->ctx, tmp, nq * 8);
-    RBFFD_TRY(rc);
-  }
-  RBFFD_CK(cudaStreamSynchronize(st));
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!P) return RBFFD_EINVAL;
+    RBFFD_CK(cudaSetDevice(P->ctx->device));
+    cudaStream_t st = P->ctx->stream;
+    size_t nq = (size_t)P->n * P->q;
+    if (idx) RBFFD_CK(cudaMemcpyAsync(idx, P->idx_rm, nq * 4, cudaMemcpyDefault, st));
+    if (wx) RBFFD_CK(cudaMemcpyAsync(wx, P->wx_rm, nq * 8, cudaMemcpyDefault, st));
+    if (wy) RBFFD_CK(cudaMemcpyAsync(wy, P->wy_rm, nq * 8, cudaMemcpyDefault, st));
+    if (wl) RBFFD_CK(cudaMemcpyAsync(wl, P->wl_rm, nq * 8, cudaMemcpyDefault, st));
+    if (pcorr) {
+      // row-major copy of the packed pressure-correction matrix via p2 scratch
+      double *tmp = nullptr;
+      RBFFD_TRY(dev_alloc(P->ctx, (void **)&tmp, nq * 8));
+      k_unpack<<<(P->n + 255) / 256, 256, 0, st>>>(P->n, P->q, P->ldn, P->Pp, tmp);
+      int rc = after_launch(P->ctx, "k_unpack");
+      if (rc == RBFFD_OK &&
+          cudaMemcpyAsync(pcorr, tmp, nq * 8, cudaMemcpyDefault, st) != cudaSuccess)
+        rc = RBFFD_ECUDA;
+      cudaStreamSynchronize(st);
+      dev_free(P->ctx, tmp, nq * 8);
+      RBFFD_TRY(rc);
+    }
+    RBFFD_CK(cudaStreamSynchronize(st));
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int rbffd_apply(rbffd_problem *P, int32_t which, const double *x, double *y) {
-  if (!P || !x || !y) return RBFFD_EINVAL;
-  const double *val = which == RBFFD_OP_DX ? P->Wx
-                      : which == RBFFD_OP_DY ? P->Wy
-                      : which == RBFFD_OP_LAP ? P->Wl
-                      : which == RBFFD_OP_PCORR ? P->Pp
-                      : which == RBFFD_OP_MOMENTUM ? P->Am
-                      : which == RBFFD_OP_MOMENTUM_V ? (P->has_sym ? P->Am2 : P->Am)
-                      : nullptr;
-  if (!val) return RBFFD_EINVAL;
-  RBFFD_CK(cudaSetDevice(P->ctx->device));
-  RBFFD_TRY(ops_spmv(P, val, x, y));
-  RBFFD_CK(cudaStreamSynchronize(P->ctx->stream));
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!P || !x || !y) return RBFFD_EINVAL;
+    const double *val = which == RBFFD_OP_DX ? P->Wx
+                        : which == RBFFD_OP_DY ? P->Wy
+                        : which == RBFFD_OP_LAP ? P->Wl
+                        : which == RBFFD_OP_PCORR ? P->Pp
+                        : which == RBFFD_OP_MOMENTUM ? P->Am
+                        : which == RBFFD_OP_MOMENTUM_V ? (P->has_sym ? P->Am2 : P->Am)
+                        : nullptr;
+    if (!val) return RBFFD_EINVAL;
+    RBFFD_CK(cudaSetDevice(P->ctx->device));
+    RBFFD_TRY(ops_spmv(P, val, x, y));
+    RBFFD_CK(cudaStreamSynchronize(P->ctx->stream));
+    return RBFFD_OK;
+  });
 }

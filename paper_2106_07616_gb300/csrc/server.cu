@@ -24,6 +24,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "abi_guard.cuh"
 #include "batch.cuh"
 #include "problem.cuh"
 
@@ -190,113 +191,128 @@ struct rbffd_server {
           continue;
         }
       }
-      admit();
-      if (!running.empty()) step_all();
+      const int rc = guarded([&] {
+        admit();
+        if (!running.empty()) step_all();
+        return RBFFD_OK;
+      });
+      if (rc != RBFFD_OK) {  // host memory exhausted: end the running requests
+        for (Request *r : running) finish(r, rc);
+        running.clear();
+      }
     }
   }
 };
 
 extern "C" int rbffd_server_create(rbffd_ctx *ctx, const rbffd_server_params *prm,
                                    rbffd_server **out) {
-  if (!ctx || !out) return RBFFD_EINVAL;
-  *out = nullptr;
-  RBFFD_CK(cudaSetDevice(ctx->device));
-  rbffd_server *s = new rbffd_server();
-  s->ctx = ctx;
-  ctx_ref(ctx);
-  size_t budget = prm ? prm->hbm_budget_bytes : 0;
-  if (budget == 0) {
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = ctx->used + fr / 10 * 8;
-  }
-  if (budget && (ctx->budget == 0 || budget < ctx->budget)) ctx->budget = budget;
-  int cap = krylov_batch_max_ctas(ctx, 2);
-  s->max_active = (prm && prm->max_active > 0) ? prm->max_active : cap;
-  if (s->max_active > cap) s->max_active = cap;
-  s->worker = std::thread([s] { s->loop(); });
-  *out = s;
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!ctx || !out) return RBFFD_EINVAL;
+    *out = nullptr;
+    RBFFD_CK(cudaSetDevice(ctx->device));
+    rbffd_server *s = new rbffd_server();
+    s->ctx = ctx;
+    ctx_ref(ctx);
+    size_t budget = prm ? prm->hbm_budget_bytes : 0;
+    if (budget == 0) {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = ctx->used + fr / 10 * 8;
+    }
+    if (budget && (ctx->budget == 0 || budget < ctx->budget)) ctx->budget = budget;
+    int cap = krylov_batch_max_ctas(ctx, 2);
+    s->max_active = (prm && prm->max_active > 0) ? prm->max_active : cap;
+    if (s->max_active > cap) s->max_active = cap;
+    s->worker = std::thread([s] { s->loop(); });
+    *out = s;
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int rbffd_server_submit(rbffd_server *s, const rbffd_problem_desc *d,
                                    const rbffd_solve_params *sp, uint64_t *ticket) {
-  if (!s || !d || !sp || !ticket || d->n < 1 || !d->x || !d->y || !d->tag || !d->nx || !d->ny ||
-      !d->ubc || !d->vbc || sp->max_outer < 1 || sp->max_steps < 1 || !(sp->dt > 0))
-    return RBFFD_EINVAL;
-  if (d->precision != RBFFD_PREC_FP64 && d->precond == RBFFD_PRECOND_JACOBI) {
-    set_error("rbffd_server_submit: a mixed-precision request needs a multigrid p' solver");
-    return RBFFD_EINVAL;
-  }
-  Request *r = new Request();
-  const size_t n = d->n;
-  // host copies of the inputs (the caller's buffers may go away)
-  auto cp = [n](std::vector<double> &v, const double *src) { v.assign(src, src + n); };
-  cp(r->x, d->x);
-  cp(r->y, d->y);
-  cp(r->nx, d->nx);
-  cp(r->ny, d->ny);
-  cp(r->ubc, d->ubc);
-  cp(r->vbc, d->vbc);
-  r->tag.assign(d->tag, d->tag + n);
-  r->desc = *d;
-  r->desc.x = r->x.data();
-  r->desc.y = r->y.data();
-  r->desc.nx = r->nx.data();
-  r->desc.ny = r->ny.data();
-  r->desc.ubc = r->ubc.data();
-  r->desc.vbc = r->vbc.data();
-  r->desc.tag = r->tag.data();
-  r->sp = *sp;
-  r->step.dt = sp->dt;
-  r->step.alpha[0] = 1.5;
-  r->step.alpha[1] = -2.0;
-  r->step.alpha[2] = 0.5;
-  r->step.krylov_tol = sp->krylov_tol;
-  r->step.krylov_maxit = sp->krylov_maxit;
-  r->t_arrive = Clock::now();
-  {
-    std::lock_guard<std::mutex> g(s->mu);
-    r->id = s->next_id++;
-    s->all[r->id] = r;
-    s->queue.push_back(r);
-    s->unfinished++;
-  }
-  s->cv_work.notify_one();
-  *ticket = r->id;
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!s || !d || !sp || !ticket || d->n < 1 || !d->x || !d->y || !d->tag || !d->nx || !d->ny ||
+        !d->ubc || !d->vbc || sp->max_outer < 1 || sp->max_steps < 1 || !(sp->dt > 0))
+      return RBFFD_EINVAL;
+    if (d->precision != RBFFD_PREC_FP64 && d->precond == RBFFD_PRECOND_JACOBI) {
+      set_error("rbffd_server_submit: a mixed-precision request needs a multigrid p' solver");
+      return RBFFD_EINVAL;
+    }
+    Request *r = new Request();
+    const size_t n = d->n;
+    // host copies of the inputs (the caller's buffers may go away)
+    auto cp = [n](std::vector<double> &v, const double *src) { v.assign(src, src + n); };
+    cp(r->x, d->x);
+    cp(r->y, d->y);
+    cp(r->nx, d->nx);
+    cp(r->ny, d->ny);
+    cp(r->ubc, d->ubc);
+    cp(r->vbc, d->vbc);
+    r->tag.assign(d->tag, d->tag + n);
+    r->desc = *d;
+    r->desc.x = r->x.data();
+    r->desc.y = r->y.data();
+    r->desc.nx = r->nx.data();
+    r->desc.ny = r->ny.data();
+    r->desc.ubc = r->ubc.data();
+    r->desc.vbc = r->vbc.data();
+    r->desc.tag = r->tag.data();
+    r->sp = *sp;
+    r->step.dt = sp->dt;
+    r->step.alpha[0] = 1.5;
+    r->step.alpha[1] = -2.0;
+    r->step.alpha[2] = 0.5;
+    r->step.krylov_tol = sp->krylov_tol;
+    r->step.krylov_maxit = sp->krylov_maxit;
+    r->t_arrive = Clock::now();
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      r->id = s->next_id++;
+      s->all[r->id] = r;
+      s->queue.push_back(r);
+      s->unfinished++;
+    }
+    s->cv_work.notify_one();
+    *ticket = r->id;
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int rbffd_server_poll(rbffd_server *s, uint64_t ticket, rbffd_result *res, double *u,
                                  double *v, double *p) {
-  if (!s || !res) return RBFFD_EINVAL;
-  std::lock_guard<std::mutex> g(s->mu);
-  auto it = s->all.find(ticket);
-  if (it == s->all.end()) return RBFFD_EINVAL;
-  Request *r = it->second;
-  memset(res, 0, sizeof(*res));
-  res->state = r->state;
-  res->status = r->status;
-  res->steps = r->steps;
-  res->outer_iters = r->outer_total;
-  for (int k = 0; k < 3; ++k) res->resid[k] = r->resid[k];
-  if (r->state >= 1) res->queue_s = secs(r->t_arrive, r->t_admit);
-  if (r->state == 2) {
-    res->latency_s = secs(r->t_arrive, r->t_done);
-    if (r->status == RBFFD_OK && !r->u.empty()) {
-      const size_t nb = sizeof(double) * r->u.size();
-      if (u) memcpy(u, r->u.data(), nb);
-      if (v) memcpy(v, r->v.data(), nb);
-      if (p) memcpy(p, r->p.data(), nb);
+  return guarded([&]() -> int {
+    if (!s || !res) return RBFFD_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return RBFFD_EINVAL;
+    Request *r = it->second;
+    memset(res, 0, sizeof(*res));
+    res->state = r->state;
+    res->status = r->status;
+    res->steps = r->steps;
+    res->outer_iters = r->outer_total;
+    for (int k = 0; k < 3; ++k) res->resid[k] = r->resid[k];
+    if (r->state >= 1) res->queue_s = secs(r->t_arrive, r->t_admit);
+    if (r->state == 2) {
+      res->latency_s = secs(r->t_arrive, r->t_done);
+      if (r->status == RBFFD_OK && !r->u.empty()) {
+        const size_t nb = sizeof(double) * r->u.size();
+        if (u) memcpy(u, r->u.data(), nb);
+        if (v) memcpy(v, r->v.data(), nb);
+        if (p) memcpy(p, r->p.data(), nb);
+      }
     }
-  }
-  return RBFFD_OK;
+    return RBFFD_OK;
+  });
 }
 
 extern "C" int rbffd_server_drain(rbffd_server *s) {
-  if (!s) return RBFFD_EINVAL;
-  std::unique_lock<std::mutex> lk(s->mu);
-  s->cv_done.wait(lk, [s] { return s->unfinished == 0; });
-  return RBFFD_OK;
+  return guarded([&]() -> int {
+    if (!s) return RBFFD_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_done.wait(lk, [s] { return s->unfinished == 0; });
+    return RBFFD_OK;
+  });
 }
 
 extern "C" void rbffd_server_destroy(rbffd_server *s) {

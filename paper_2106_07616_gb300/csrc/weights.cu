@@ -11,6 +11,7 @@
 // oracle's unfused elimination by rounding only (a different elimination
 // order, LAPACK's, moves the 200 x 200 cavity weights by at most 4e-13
 // relative), well inside the 1e-10 the weights are held to.
+#include "abi_guard.cuh"
 #include "common.cuh"
 #include "weights.cuh"
 
@@ -222,36 +223,38 @@ using namespace rbffd;
 extern "C" int rbffd_weights(rbffd_ctx *ctx, int32_t n, const double *x, const double *y,
                              int32_t q, const int32_t *idx, int32_t degree, double *wx,
                              double *wy, double *wl, int32_t *first_singular) {
-  if (!ctx || !x || !y || !idx || weights_check_args(n, q, degree) != RBFFD_OK) {
-    set_error("rbffd_weights: bad arguments (n=%d q=%d degree=%d)", n, q, degree);
-    return RBFFD_EINVAL;
-  }
-  RBFFD_CK(cudaSetDevice(ctx->device));
-  int *dfs = nullptr;
-  RBFFD_TRY(dev_alloc(ctx, (void **)&dfs, sizeof(int)));
-  int big = 0x7fffffff;
-  int rc = RBFFD_OK;
-  if (cudaMemcpyAsync(dfs, &big, sizeof(int), cudaMemcpyHostToDevice, ctx->stream) !=
-      cudaSuccess) {
-    rc = RBFFD_ECUDA;
-  } else {
-    rc = weights_run(ctx, n, x, y, q, idx, degree, wx, wy, wl, dfs, 0.0, 0.0);
-  }
-  int hfs = big;
-  if (rc == RBFFD_OK) {
-    if (cudaMemcpyAsync(&hfs, dfs, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-      set_error("rbffd_weights: read-back failed");
-      rc = RBFFD_ECUDA;
+  return guarded([&]() -> int {
+    if (!ctx || !x || !y || !idx || weights_check_args(n, q, degree) != RBFFD_OK) {
+      set_error("rbffd_weights: bad arguments (n=%d q=%d degree=%d)", n, q, degree);
+      return RBFFD_EINVAL;
     }
-  }
-  cudaStreamSynchronize(ctx->stream);
-  dev_free(ctx, dfs, sizeof(int));
-  if (first_singular) *first_singular = (rc == RBFFD_OK && hfs != big) ? hfs : -1;
-  if (rc == RBFFD_OK && hfs != big) {
-    set_error("rbffd_weights: singular collocation matrix at point %d", hfs);
-    return RBFFD_ESINGULAR;
-  }
-  return rc;
+    RBFFD_CK(cudaSetDevice(ctx->device));
+    int *dfs = nullptr;
+    RBFFD_TRY(dev_alloc(ctx, (void **)&dfs, sizeof(int)));
+    int big = 0x7fffffff;
+    int rc = RBFFD_OK;
+    if (cudaMemcpyAsync(dfs, &big, sizeof(int), cudaMemcpyHostToDevice, ctx->stream) !=
+        cudaSuccess) {
+      rc = RBFFD_ECUDA;
+    } else {
+      rc = weights_run(ctx, n, x, y, q, idx, degree, wx, wy, wl, dfs, 0.0, 0.0);
+    }
+    int hfs = big;
+    if (rc == RBFFD_OK) {
+      if (cudaMemcpyAsync(&hfs, dfs, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        set_error("rbffd_weights: read-back failed");
+        rc = RBFFD_ECUDA;
+      }
+    }
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, dfs, sizeof(int));
+    if (first_singular) *first_singular = (rc == RBFFD_OK && hfs != big) ? hfs : -1;
+    if (rc == RBFFD_OK && hfs != big) {
+      set_error("rbffd_weights: singular collocation matrix at point %d", hfs);
+      return RBFFD_ESINGULAR;
+    }
+    return rc;
+  });
 }
