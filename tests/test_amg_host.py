@@ -60,3 +60,34 @@ def test_bad_csr_rejected():
     with pytest.raises(rbffd.RbffdError) as e:
         rbffd.amg_analyze(rowptr, bad, vals)
     assert e.value.code == rbffd.EINVAL
+
+
+def test_hierarchy_does_not_depend_on_the_thread_count(tmp_path):
+    """Loops run in parallel only above a work threshold and with row chunks
+    sized to the thread count; the hierarchy is the same on one thread and
+    on four.  The 80 x 80 cavity's p' matrix (192 000 entries) crosses the
+    threshold on level 0 and not on the coarse levels."""
+    import json
+    import os
+    import subprocess
+    import sys
+    fp = clouds.cavity(80, dt=0.05)
+    ops = oracle.Problem(fp).operators()
+    pv, idx = ops["pval"], ops["idx"]
+    keep = (pv != 0) | (idx == np.arange(fp.n)[:, None])
+    rowptr = np.concatenate([[0], np.cumsum(keep.sum(1))])
+    path = tmp_path / "pp.npz"
+    np.savez(path, rowptr=rowptr, col=idx[keep], val=pv[keep])
+    code = ("import json, sys, numpy as np\n"
+            "from paper_2106_07616_gb300 import rbffd\n"
+            "d = np.load(sys.argv[1])\n"
+            "print(json.dumps(rbffd.amg_analyze(d['rowptr'], d['col'], d['val'])[0]))\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = []
+    for threads in ("1", "4"):
+        env = dict(os.environ, OMP_NUM_THREADS=threads)
+        r = subprocess.run([sys.executable, "-c", code, str(path)], env=env, cwd=root,
+                           capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr
+        out.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    assert out[0] == out[1] and len(out[0]) >= 2 and out[0][0][1] > (1 << 17)
