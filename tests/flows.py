@@ -46,16 +46,17 @@ def poiseuille(n_side=24, seed=12, degree=3, q=20, rho=1.0, mu=0.2, dt=0.1):
 
 
 def accelerating(n_side=20, seed=13, degree=3, q=20, rho=0.9, mu=0.03, dt=0.25, a=(0.4, -0.2),
-                 b=(0.3, 0.5)):
-    """Uniform flow accelerating linearly in time:
-    u = a0 + b0 t, v = a1 + b1 t, p = -rho (b0 x + b1 y).
-    BDF2 differentiates a linear function of time exactly."""
+                 b=(0.3, 0.5), c=(0.0, 0.0)):
+    """Uniform flow whose velocity is a polynomial of degree <= 2 in time:
+    u = a0 + b0 t + c0 t^2, v = a1 + b1 t + c1 t^2, and
+    p = -rho ((b0 + 2 c0 t) x + (b1 + 2 c1 t) y).
+    BDF2 differentiates such a function of time exactly."""
     fp = _box(n_side, seed, degree, q, rho, mu, dt)
 
     def at(t):
-        u = np.full(fp.n, a[0] + b[0] * t)
-        v = np.full(fp.n, a[1] + b[1] * t)
-        p = -rho * (b[0] * fp.x + b[1] * fp.y)
+        u = np.full(fp.n, a[0] + b[0] * t + c[0] * t * t)
+        v = np.full(fp.n, a[1] + b[1] * t + c[1] * t * t)
+        p = -rho * ((b[0] + 2 * c[0] * t) * fp.x + (b[1] + 2 * c[1] * t) * fp.y)
         return u, v, p
 
     fp.at = at
