@@ -141,6 +141,26 @@ def test_bdf2_accelerating_flow_gpu():
     assert np.abs(P.get("p") - p2).max() < 1e-9
 
 
+def test_bdf2_quadratic_in_time_fixed_point_gpu():
+    """The paper's BDF2 coefficients (Sec. 3) make a uniform flow quadratic
+    in time, with its exact history, a fixed point of the step at t + dt:
+    the GPU step started there stays there."""
+    fp = flows.accelerating(c=(0.7, -0.4))
+    P = rbffd.Problem(ctx(), fp)
+    t0 = 1.0
+    u1, v1, _ = fp.at(t0 - fp.dt)
+    u0, v0, _ = fp.at(t0)
+    u2, v2, p2 = fp.at(t0 + fp.dt)
+    for k, a in (("unm1", u1), ("vnm1", v1), ("un", u0), ("vn", v0), ("u", u2), ("v", v2),
+                 ("p", p2), ("ubc", u2), ("vbc", v2)):
+        P.set(k, a)
+    it, ch = P.time_step(fp.dt, 1e-10, max_outer=10, krylov_tol=1e-13)
+    assert it <= 2
+    assert np.abs(P.get("un") - u2).max() < 1e-10
+    assert np.abs(P.get("vn") - v2).max() < 1e-10
+    assert np.abs(P.get("p") - p2).max() < 1e-9
+
+
 def test_solve_steady_reaches_tolerance_like_oracle():
     fp = clouds.kovasznay(30, dt=0.4)
     P, O = _pair(fp, tol=1e-10)
