@@ -126,3 +126,31 @@ def test_steady_error_criterion_matches_manual_march():
     assert steps == info["steps"]
     for k in ("u", "v", "p"):
         np.testing.assert_array_equal(A.get(k), B.get(k))
+
+
+def test_unsteady_driver_follows_the_outer_tolerance_rule():
+    """The unsteady driver marches n steps with the outer tolerance of
+    Sec. 3 (1e-4 on the first step, then min(1e-4, dt eps_s) with dt eps_s
+    the mean change of u and v over the last step): a march driven one time
+    step at a time with that rule takes the same outer iterations and lands
+    on the same fields, bit for bit.  A small step (2e-4) keeps the change
+    per step near 1e-4, so the rule's minimum is taken on some steps."""
+    fp = clouds.decaying(33, 2, degree=3, dt=2e-4)
+    A = oracle.Problem(fp, krylov_tol=1e-12)
+    B = oracle.Problem(fp, krylov_tol=1e-12)
+    for X in (A, B):
+        for k, a in fp.initial.items():
+            X.set(k, a)
+    n = 12
+    rc, info = A.solve_unsteady(fp.dt, n, max_outer=20)
+    assert rc == 0 and info["steps"] == n
+    tol_outer, outer, tols = 1e-4, 0, []
+    for _ in range(n):
+        it, change, _ = B.time_step(fp.dt, tol_outer, 20)
+        outer += it
+        tols.append(tol_outer)
+        tol_outer = min(1e-4, change)
+    assert outer == info["outer"] and change == info["change"]
+    assert min(tols) < 1e-4  # the rule took the measured change on some steps
+    for k in ("u", "v", "p", "un", "unm1"):
+        np.testing.assert_array_equal(A.get(k), B.get(k))
