@@ -261,7 +261,9 @@ void rbffd_problem_destroy(rbffd_problem *prob);
 size_t rbffd_problem_bytes(const rbffd_problem *prob);
 /* Multigrid hierarchy of the p' preconditioner: *levels (0 with Jacobi),
  * rows and nonzeros per level (arrays of RBFFD_AMG_MAX_LEVELS, nullable)
- * and the host time its build took (nullable). */
+ * and the host time its build took (nullable): the copy of the p' matrix,
+ * the hierarchy and its staging, from the moment the matrix is ready (not
+ * the upload).  Finishes a build still running first. */
 int rbffd_problem_amg_info(const rbffd_problem *prob, int32_t *levels, int32_t *rows,
                            int64_t *nnz, double *setup_ms);
 /* The same hierarchy built on the host only, for a CSR matrix (host arrays:
