@@ -154,3 +154,23 @@ def test_unsteady_driver_follows_the_outer_tolerance_rule():
     assert min(tols) < 1e-4  # the rule took the measured change on some steps
     for k in ("u", "v", "p", "un", "unm1"):
         np.testing.assert_array_equal(A.get(k), B.get(k))
+
+
+def test_oracle_does_not_depend_on_the_thread_count():
+    """The oracle's OpenMP loops run over points and rows and its dot
+    products are serial in index order, so clouds, weights and outer
+    iterates are bit-identical on one thread and on four."""
+    fp = clouds.kovasznay(20, dt=0.4)
+    before = oracle.set_threads(0)  # 0 leaves the count as it is
+    out = []
+    try:
+        for t in (1, 4):
+            oracle.set_threads(t)
+            O = oracle.Problem(fp, krylov_tol=1e-12)
+            for _ in range(3):
+                O.simple_iterate(fp.dt)
+            out.append([O.get(k) for k in ("u", "v", "p")] + list(O.operators().values()))
+    finally:
+        oracle.set_threads(before)
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
