@@ -99,6 +99,11 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
   P->gen = ++generation;
   rbffd_ctx *ctx = P->ctx;
   cudaStream_t st = ctx->stream;
+  // a hierarchy build still running reads the packed p' matrix: drop it
+  // (and the old hierarchy) before anything of the problem is rewritten.
+  // Until the build succeeds the problem has no hierarchy, and says so.
+  free_amg(P);
+  P->precond = RBFFD_PRECOND_JACOBI;
   const size_t nb = (size_t)d->n * sizeof(double);
   RBFFD_CK(cudaMemcpyAsync(P->x, d->x, nb, cudaMemcpyDefault, st));
   RBFFD_CK(cudaMemcpyAsync(P->y, d->y, nb, cudaMemcpyDefault, st));
@@ -160,7 +165,6 @@ int build(rbffd_problem *P, const rbffd_problem_desc *d) {
                         P->wl_rm, P->d_first_singular, P->per[0], P->per[1]));
   prof_end(ctx, 0);
   RBFFD_TRY(ops_pack(P));
-  free_amg(P);
   P->precond = d->precond;
   // the multigrid hierarchy's host part runs on a thread of its own from
   // here; the first p' solve (amg_ready) waits for it and uploads it, so
