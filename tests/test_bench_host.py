@@ -44,3 +44,26 @@ def test_peak_is_measured_when_present_else_the_fallback(tmp_path, monkeypatch):
     assert bench.read_peaks() == (bench.FALLBACK_HBM_GBS, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6792.7}))
     assert bench.read_peaks() == (6792.7, "measured")
+
+
+def test_batched_workload_follows_its_recipe():
+    """The batched workload: Kovasznay and cavity instances on square
+    lattices of 1k to 64k points, degree 2..5, q = 2m (m = (k+1)(k+2)/2
+    appended monomials), seeded per instance, the same on every call."""
+    a = bench.batch_instances(12)
+    b = bench.batch_instances(12)
+    assert [fp.n for fp in a] == [fp.n for fp in b]
+    assert all(np_equal(x.x, y.x) for x, y in zip(a, b))
+    kinds = set()
+    for fp in a:
+        k = fp.degree
+        assert 2 <= k <= 5 and fp.q == (k + 1) * (k + 2)
+        side = round(fp.n ** 0.5)
+        assert side * side == fp.n and 31 * 31 <= fp.n <= 253 * 253, fp.n
+        kinds.add(fp.name.rstrip("0123456789"))
+    assert len(kinds) == 2, kinds
+
+
+def np_equal(x, y):
+    import numpy as np
+    return np.array_equal(x, y)
