@@ -185,8 +185,11 @@ int rbffd_build_stencils(rbffd_ctx *ctx, int32_t n, const double *x, const doubl
  *   - n is limited to RBFFD_STATIC_MAX_POINTS; larger n returns RBFFD_EINVAL
  *     with a message, before anything runs on the GPU.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current, once per device even
+ *     when several host threads make their first call together.
+ *   - Like rbffd_build_stencils, every call synchronises the context's
+ *     stream (it reads the kernels' error word back to the host), so it must
+ *     not be called while that stream is being captured into a CUDA graph.
  *   - All calls share the one array and it keeps the last call's contents
  *     (the call clears what it needs cleared).  Calls that overlap on the GPU
  *     -- from two streams, or two contexts on one device -- race on it: issue
@@ -322,14 +325,16 @@ typedef struct {
   int32_t inner_maxit;
   int32_t criterion;      /* steady stop: 0 = R <= resid_tol; 1 = the paper's steady
                              error (Sec. 4.1): (mean|u^{n+1}-u^n| + mean|v^{n+1}-v^n|)/dt
-                             <= resid_tol */
+                             <= resid_tol; 2 = exactly max_steps steps (no steady
+                             test; the solve ends with RBFFD_OK) */
 } rbffd_solve_params;
 
 typedef struct {
   int32_t steps;
   int64_t outer_iters;
   int64_t krylov_iters[3]; /* totals: u~, v~, p' */
-  double resid[3];         /* R_m, R_c, R of the final state (steady only) */
+  double resid[4];         /* R_m, R_c, R, lambda of the final state (steady only;
+                              rbffd_steady_residual) */
   double change;           /* mean|u^{n+1}-u^n| + mean|v^{n+1}-v^n| of the last step */
 } rbffd_solve_stats;
 
@@ -356,10 +361,20 @@ int solve_unsteady(rbffd_problem *prob, const rbffd_solve_params *params, int32_
 
 /* Relative residual of the discrete steady equations over interior rows,
  * vector norms over both components:
- *   R_m = |rho (u.grad)u - mu lap u + grad p| / (|rho (u.grad)u| + |mu lap u| + |grad p|)
- *   R_c = |Dx u + Dy v| / |grad u|
- * R3 (host, 3 doubles) = R_m, R_c, max of the two. */
-int rbffd_steady_residual(rbffd_problem *prob, double *R3);
+ *   R_m = |rho (u.grad)u - mu lap u + grad p - f| / (|rho (u.grad)u| + |mu lap u|
+ *         + |grad p| + |f|)
+ *   d   = Dx u + Dy v at interior rows, lambda = its mean
+ *   R_c = |d - lambda| / |grad u| for a pinned problem (no outlet), else
+ *         |d| / |grad u|.
+ * Why lambda is taken out: with Neumann rows only, the p' equation (paper
+ * Sec. 3, Eq. pressure poisson; Sec. 3.1) is singular and solvable only for
+ * a compatible right-hand side; the library solves it for the compatible
+ * part of (rho a1/dt) div u~, so the part of the divergence that no
+ * pressure correction can remove is a constant over the interior rows, and
+ * a steady state satisfies continuity up to that constant lambda (a
+ * discretisation defect that falls with the point spacing).
+ * R4 (host, 4 doubles) = R_m, R_c, R = max(R_m, R_c), lambda. */
+int rbffd_steady_residual(rbffd_problem *prob, double *R4);
 
 /* Courant number of the explicit-Euler stability bound quoted in the paper
  * (Sec. 3.2, after the solution steps): lambda * dt / 2, with lambda the
@@ -448,7 +463,13 @@ typedef struct {
   double latency_s;     /* arrival -> result (seconds), when done */
   int32_t steps;        /* time steps taken */
   int64_t outer_iters;  /* outer iterations taken */
-  double resid[3];      /* R_m, R_c, R at the last step */
+  double resid[4];      /* R_m, R_c, R, lambda at the last step */
+  int32_t admit_attempts; /* admission tries that built or finished the request's
+                             multigrid hierarchy (1 unless device memory was short:
+                             the problem is built once and only the hierarchy's
+                             upload is retried) */
+  double arrive_s, admit_s, done_s; /* submission, admission and completion, in
+                                       seconds since the server was created */
 } rbffd_result;
 int rbffd_server_create(rbffd_ctx *ctx, const rbffd_server_params *params, rbffd_server **out);
 /* desc arrays are host pointers, copied before the call returns; ticket

@@ -83,6 +83,8 @@ def lib():
                                          C.c_int, _dp]
         L.orc_solve_unsteady.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_int, _dp]
         L.orc_apply.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
+        L.orc_get_compat.argtypes = [C.c_void_p, _dp]
+        L.orc_set_compat.argtypes = [C.c_void_p, C.c_int]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_set_threads.restype = C.c_int
         L.orc_monomial_exponents.argtypes = [C.c_int, _ip, _ip]
@@ -257,9 +259,24 @@ class Problem:
         return out[0], out[1]
 
     def steady_residual(self):
-        r = np.zeros(3)
+        """(R_m, R_c, R, lambda): lambda is the mean interior divergence, the
+        constant that the compatible p' equation leaves in continuity."""
+        r = np.zeros(4)
         lib().orc_steady_residual(self.h, r)
         return r
+
+    def set_compat(self, on):
+        """Switch the compatible p' source on or off (off plants the plain pin)."""
+        rc = lib().orc_set_compat(self.h, int(bool(on)))
+        if rc:
+            raise ValueError("no compatibility on a problem with an outlet")
+
+    def compat(self):
+        """The left null vector psi of the pure-Neumann p' operator (None
+        when an outlet fixes the pressure level)."""
+        out = np.zeros(self.n)
+        rc = lib().orc_get_compat(self.h, out)
+        return None if rc else out
 
     def solve_steady(self, dt, resid_tol=1e-8, max_steps=10000, max_outer=20, criterion=0):
         out = np.zeros(4)

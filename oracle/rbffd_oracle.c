@@ -22,7 +22,7 @@
  *   Sec. 3.2 "Summary of Solution Steps": step order of the outer loop and
  *       the adaptive outer tolerance min(1e-4, dt*eps_s).
  *
- * Readings where the paper is silent (all listed in the design doc):
+ * Readings where the paper is silent:
  *   - cloud = the q nearest points, self first, others by (d^2, index);
  *   - local coordinates shifted to the centre and scaled by the stencil
  *     radius h = max |x_j - x_c| (weights are invariant in exact arithmetic);
@@ -490,6 +490,11 @@ typedef struct {
   double *wx, *wy, *wl;
   int64_t *rowptr;
   csr_t Dx, Dy, Dl, Pp, Am, Av; /* Pp: pressure correction; Am, Av: momentum u, v */
+  /* compatibility of the pinned p' equation: left null vector psi of the  */
+  /* pure-Neumann operator and psi . e_I (NULL / 0 when an outlet fixes p) */
+  double *psi;
+  double psi_eI;
+  int psi_off; /* 1: compatibility switched off (orc_set_compat) */
   /* fields: iterate (u, v, p) and the two previous time levels */
   double *u, *v, *p, *un, *vn, *unm1, *vnm1;
   /* work */
@@ -518,11 +523,70 @@ void orc_problem_destroy(orc_problem *P) {
   if (!P) return;
   free(P->x); free(P->y); free(P->nx); free(P->ny); free(P->ubc); free(P->vbc); free(P->tag);
   free(P->idx); free(P->wx); free(P->wy); free(P->wl); free(P->rowptr);
-  free(P->Pp.val); free(P->Am.val); free(P->Av.val);
+  free(P->Pp.val); free(P->Am.val); free(P->Av.val); free(P->psi);
   free(P->u); free(P->v); free(P->p); free(P->un); free(P->vn); free(P->unm1); free(P->vnm1);
   free(P->ut); free(P->vt); free(P->pc); free(P->bu); free(P->bv); free(P->bp);
   free(P->w1); free(P->w2); free(P->w3); free(P->w4);
   free(P);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Solvability of the pressure-correction equation (Sec. 3, Eq. (pressure   */
+/* poisson) with the homogeneous Neumann rows of Sec. 3.1).  With Neumann   */
+/* rows only (no outlet) the discrete operator L_N -- Laplacian weights at  */
+/* interior rows, n.grad weights at boundary rows -- maps constants to zero */
+/* (every row of weights sums to zero), so it is singular, and L_N p' = b  */
+/* has a solution only when psi . b = 0 for the left null vector psi       */
+/* (psi^T L_N = 0).  This is the discrete form of the condition that the    */
+/* source of a Neumann problem integrate to the prescribed boundary flux   */
+/* (zero here).  The divergence of u~ does not meet it exactly, so the      */
+/* source is made compatible before the solve:                             */
+/*     b~ = b - (psi . b / psi . e_I) e_I,   e_I = 1 at interior rows,      */
+/* i.e. the part of the divergence that no pressure correction can remove  */
+/* is a constant lambda over the interior rows.  The pin row (identity)     */
+/* then only fixes the free constant of p'.                                 */
+/* psi is computed once per problem.  With M = L_N with its pin row         */
+/* replaced by the identity (the stored p' matrix) and l = the pin's        */
+/* Neumann row, psi solves M^T psi = e_pin - l; then psi^T L_N = (1 -      */
+/* psi_pin)(e_pin - l)^T, and applying both sides to the constant vector    */
+/* (L_N 1 = 0, l . 1 = 0) gives psi_pin = 1, so psi^T L_N = 0.              */
+static int compat_vector(orc_problem *P) {
+  int n = P->n, q = P->q, pin = P->pin;
+  int64_t nnz = (int64_t)n * q;
+  /* M^T as CSR: column counts, prefix sums, then entries in row order */
+  csr_t T;
+  T.n = n;
+  T.rowptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  T.col = (int32_t *)malloc(sizeof(int32_t) * (size_t)nnz);
+  T.val = (double *)malloc(sizeof(double) * (size_t)nnz);
+  double *rhs = dvec(n);
+  P->psi = dvec(n);
+  int64_t *fill = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+  int rc = ORC_OK;
+  if (!T.rowptr || !T.col || !T.val || !rhs || !P->psi || !fill) { rc = ORC_ENOMEM; goto out; }
+  for (int64_t e = 0; e < nnz; ++e) T.rowptr[P->idx[e] + 1]++;
+  for (int j = 0; j < n; ++j) T.rowptr[j + 1] = T.rowptr[j + 1] + T.rowptr[j];
+  for (int i = 0; i < n; ++i)
+    for (int64_t e = P->rowptr[i]; e < P->rowptr[i + 1]; ++e) {
+      int j = P->idx[e];
+      int64_t slot = T.rowptr[j] + fill[j]++;
+      T.col[slot] = i;
+      T.val[slot] = P->Pp.val[e];
+    }
+  /* right-hand side e_pin - l, l = n.grad weights of the pin's cloud */
+  rhs[pin] = 1.0;
+  for (int64_t e = P->rowptr[pin]; e < P->rowptr[pin + 1]; ++e)
+    rhs[P->idx[e]] = rhs[P->idx[e]] - (P->nx[pin] * P->wx[e] + P->ny[pin] * P->wy[e]);
+  krylov_stats_t st;
+  rc = bicgstab(&T, rhs, P->psi, P->ktol, P->kmaxit, &st);
+  if (rc) goto out;
+  P->psi_eI = 0.0;
+  for (int i = 0; i < n; ++i)
+    if (P->tag[i] == TAG_INTERIOR) P->psi_eI = P->psi_eI + P->psi[i];
+  if (P->psi_eI == 0.0) rc = ORC_ESINGULAR;
+out:
+  free(T.rowptr); free(T.col); free(T.val); free(rhs); free(fill);
+  return rc;
 }
 
 /* Build stencils, weights, the operator CSR matrices and the pressure-      */
@@ -624,6 +688,10 @@ int orc_problem_create2(int n, int q, int degree, const double *x, const double 
         val = nx[i] * P->wx[e] + ny[i] * P->wy[e];
       pval[e] = val;
     }
+  if (pin >= 0) {
+    rc = compat_vector(P);
+    if (rc) { orc_problem_destroy(P); return rc; }
+  }
   /* initial state: u = v = p = 0 in the interior, BC values on the boundary */
   for (int i = 0; i < n; ++i) {
     double u0 = tag[i] == TAG_INTERIOR ? 0.0 : ubc[i];
@@ -761,6 +829,12 @@ int orc_simple_iterate(orc_problem *P, double dt, double a1, double a2, double a
   csr_spmv(&P->Dy, P->vt, P->w2);
   for (int i = 0; i < n; ++i)
     P->bp[i] = P->tag[i] == TAG_INTERIOR ? (rho * a1 / dt) * (P->w1[i] + P->w2[i]) : 0.0;
+  /* pure-Neumann p' (pinned): make the source compatible (compat_vector) */
+  if (P->psi && !P->psi_off) {
+    double cshift = dot(n, P->psi, P->bp) / P->psi_eI;
+    for (int i = 0; i < n; ++i)
+      if (P->tag[i] == TAG_INTERIOR) P->bp[i] = P->bp[i] - cshift;
+  }
   for (int i = 0; i < n; ++i) P->pc[i] = 0.0;
   rc = bicgstab(&P->Pp, P->bp, P->pc, P->ktol, P->kmaxit, &sp);
   if (rc) return rc;
@@ -918,10 +992,14 @@ int orc_courant(orc_problem *P, double dt, int iters, double *out) {
 /* interior rows (vector norms over both velocity components):              */
 /*   r = rho (u.grad) u - mu lap u + grad p - f   (f: the body force)       */
 /*   R_m = |r|_2 / (|rho (u.grad) u|_2 + |mu lap u|_2 + |grad p|_2 + |f|_2)  */
-/*   R_c = |Dx u + Dy v|_2 / |grad u|_2,  |grad u|^2 = sum of the squares of */
-/*         Dx u, Dy u, Dx v, Dy v                                           */
-/* out: R_m, R_c, R = max(R_m, R_c).                                         */
-int orc_steady_residual(orc_problem *P, double *R3) {
+/*   d = Dx u + Dy v at interior rows;  lambda = mean of d                  */
+/*   R_c = |d - lambda|_2 / |grad u|_2 when the p' equation is pinned (its   */
+/*         source is made compatible, so a steady state satisfies           */
+/*         continuity up to the constant lambda: compat_vector), else       */
+/*         |d|_2 / |grad u|_2;  |grad u|^2 = sum of the squares of Dx u,     */
+/*         Dy u, Dx v, Dy v                                                 */
+/* out: R_m, R_c, R = max(R_m, R_c), lambda.                                 */
+int orc_steady_residual(orc_problem *P, double *R4) {
   int n = P->n;
   double *gxu = dvec(n), *gyu = dvec(n), *lu = dvec(n), *gxv = dvec(n), *gyv = dvec(n),
          *lv = dvec(n), *gpx = dvec(n), *gpy = dvec(n);
@@ -932,7 +1010,8 @@ int orc_steady_residual(orc_problem *P, double *R3) {
   csr_spmv(&P->Dx, P->u, gxu); csr_spmv(&P->Dy, P->u, gyu); csr_spmv(&P->Dl, P->u, lu);
   csr_spmv(&P->Dx, P->v, gxv); csr_spmv(&P->Dy, P->v, gyv); csr_spmv(&P->Dl, P->v, lv);
   csr_spmv(&P->Dx, P->p, gpx); csr_spmv(&P->Dy, P->p, gpy);
-  double nr = 0, sa = 0, sd = 0, sp = 0, nc = 0, sg = 0, sf = 0;
+  double nr = 0, sa = 0, sd = 0, sp = 0, sg = 0, sf = 0, sdiv = 0;
+  int n_int = 0;
   const double fx = P->force[0], fy = P->force[1];
   for (int i = 0; i < n; ++i) {
     if (P->tag[i] != TAG_INTERIOR) continue;
@@ -945,15 +1024,24 @@ int orc_steady_residual(orc_problem *P, double *R3) {
     sd += du * du + dv * dv;
     sp += gpx[i] * gpx[i] + gpy[i] * gpy[i];
     sf += fx * fx + fy * fy;
-    double rc = gxu[i] + gyv[i];
-    nc += rc * rc;
+    sdiv += gxu[i] + gyv[i];
+    n_int++;
     sg += gxu[i] * gxu[i] + gyu[i] * gyu[i] + gxv[i] * gxv[i] + gyv[i] * gyv[i];
+  }
+  double lambda = n_int > 0 ? sdiv / n_int : 0.0;
+  double shift = P->psi && !P->psi_off ? lambda : 0.0;
+  double nc = 0;
+  for (int i = 0; i < n; ++i) {
+    if (P->tag[i] != TAG_INTERIOR) continue;
+    double rc = gxu[i] + gyv[i] - shift;
+    nc += rc * rc;
   }
   double den_m = sqrt(sa) + sqrt(sd) + sqrt(sp) + sqrt(sf);
   double den_c = sqrt(sg);
-  R3[0] = den_m > 0 ? sqrt(nr) / den_m : sqrt(nr);
-  R3[1] = den_c > 0 ? sqrt(nc) / den_c : sqrt(nc);
-  R3[2] = R3[0] > R3[1] ? R3[0] : R3[1];
+  R4[0] = den_m > 0 ? sqrt(nr) / den_m : sqrt(nr);
+  R4[1] = den_c > 0 ? sqrt(nc) / den_c : sqrt(nc);
+  R4[2] = R4[0] > R4[1] ? R4[0] : R4[1];
+  R4[3] = lambda;
   free(gxu); free(gyu); free(lu); free(gxv); free(gyv); free(lv); free(gpx); free(gpy);
   return ORC_OK;
 }
@@ -974,7 +1062,7 @@ int orc_solve_steady(orc_problem *P, double dt, double resid_tol, int max_steps,
  * Sec. 4.1, (mean|u^{n+1}-u^n| + mean|v^{n+1}-v^n|) / dt <= resid_tol. */
 int orc_solve_steady_c(orc_problem *P, double dt, double resid_tol, int max_steps, int max_outer,
                        int criterion, double *out) {
-  double tol = 1e-4, R3[3], R = 1.0, change = 0.0;
+  double tol = 1e-4, R3[4], R = 1.0, change = 0.0;
   int steps = 0;
   long total_outer = 0;
   int rc = ORC_OK;
@@ -1036,5 +1124,22 @@ int orc_apply(orc_problem *P, int which, const double *xv, double *yv) {
            : which == 3 ? &P->Pp : which == 4 ? &P->Am : which == 5 ? &P->Av : NULL;
   if (!A) return ORC_EINVAL;
   csr_spmv(A, xv, yv);
+  return ORC_OK;
+}
+
+/* The left null vector psi of the pure-Neumann p' operator (compat_vector); */
+/* ORC_EINVAL when the problem has an outlet (no compatibility needed).      */
+int orc_get_compat(orc_problem *P, double *out) {
+  if (!P->psi) return ORC_EINVAL;
+  memcpy(out, P->psi, sizeof(double) * P->n);
+  return ORC_OK;
+}
+
+/* Switch the compatible p' source off (on = 0: the pin alone, whose dropped */
+/* Neumann row is then violated whenever the source is incompatible) or     */
+/* back on.  Used by the tests to plant that reading.                      */
+int orc_set_compat(orc_problem *P, int on) {
+  if (!P->psi) return ORC_EINVAL;
+  P->psi_off = on ? 0 : 1;
   return ORC_OK;
 }

@@ -869,14 +869,16 @@ int amg_build_begin(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
 }
 
 template <typename T>
-int amg_build_end(rbffd_ctx *ctx, AmgJob *J, void **mem, size_t *bytes,
+int amg_build_end(rbffd_ctx *ctx, AmgJob **job, void **mem, size_t *bytes,
                   const AmgDevT<T> **dev, AmgDevT<T> *host_view, AmgInfo *info) {
   *mem = nullptr;
   *bytes = 0;
   *dev = nullptr;
+  AmgJob *J = *job;
   join(J);
-  std::unique_ptr<AmgJob> own(J);
   if (J->rc != RBFFD_OK) {
+    *job = nullptr;
+    std::unique_ptr<AmgJob> own(J);
     set_error("%s", J->err);
     return J->rc;
   }
@@ -884,7 +886,12 @@ int amg_build_end(rbffd_ctx *ctx, AmgJob *J, void **mem, size_t *bytes,
   Staging &S = J->S;
   const int L = (int)H.A.size();
   void *dmem = nullptr;
-  RBFFD_TRY(dev_alloc(ctx, &dmem, S.size));
+  // no device memory for the upload: the finished host part stays with the
+  // caller (*job unchanged), which may retry once memory has been freed
+  const int arc = dev_alloc(ctx, &dmem, S.size);
+  if (arc != RBFFD_OK) return arc;
+  *job = nullptr;
+  std::unique_ptr<AmgJob> own(J);
   char *base = (char *)dmem;
   auto csr_at = [&](const CsrOff &o, bool have) {
     AmgCsrT<T> c;
@@ -940,7 +947,9 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
               AmgDevT<T> *host_view, AmgInfo *info) {
   AmgJob *J = nullptr;
   RBFFD_TRY(amg_build_begin<T>(ctx, n, q, ldn, col, val, nblocks, wpb, &J));
-  return amg_build_end<T>(ctx, J, mem, bytes, dev, host_view, info);
+  const int rc = amg_build_end<T>(ctx, &J, mem, bytes, dev, host_view, info);
+  amg_build_abandon(J);  // still set only when the upload found no memory
+  return rc;
 }
 
 #define RBFFD_AMG_INSTANCES(T)                                                                  \
@@ -949,7 +958,7 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
                             AmgInfo *);                                                        \
   template int amg_build_begin<T>(rbffd_ctx *, int, int, int, const int32_t *, const double *, \
                                   int, int, AmgJob **);                                        \
-  template int amg_build_end<T>(rbffd_ctx *, AmgJob *, void **, size_t *, const AmgDevT<T> **, \
+  template int amg_build_end<T>(rbffd_ctx *, AmgJob **, void **, size_t *, const AmgDevT<T> **, \
                                 AmgDevT<T> *, AmgInfo *);
 RBFFD_AMG_INSTANCES(double)
 RBFFD_AMG_INSTANCES(float)

@@ -535,6 +535,7 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
   // hierarchies still being built are finished before anything is issued
   // (the iteration may be captured as a graph)
   for (int i = 0; i < m; ++i) RBFFD_TRY(amg_ready(P[i]));
+  for (int i = 0; i < m; ++i) RBFFD_TRY(compat_ready(P[i]));
   // a member with symmetry lines solves u~ and v~ as two single-RHS systems
   // (their rows differ there), so a launch may hold up to 2m systems
   RBFFD_TRY(S.reserve(ctx, 2 * m));

@@ -11,6 +11,7 @@
 // the nearest image and wraps the ring around the grid, each column (row)
 // visited once at its smallest offset; a cell at wrapped offset r + 1 is
 // still at least r cells away, so the clearance bound holds.
+#include <mutex>
 #include "abi_guard.cuh"
 #include "common.cuh"
 #include "knn.cuh"
@@ -311,22 +312,30 @@ static __device__ __align__(256) unsigned char g_knn_scratch[RBFFD_STATIC_SCRATC
 
 // Device address of g_knn_scratch per device.  In host code the symbol is
 // only a host-side stand-in, so the address has to be asked of the runtime,
-// once per device, with that device current.
+// once per device, with that device current.  The lookup runs under one
+// std::once_flag per device, so host threads that make their first call on
+// one device at the same time do not race on the cached pointer; the result
+// (the address, or the CUDA error of the lookup) is published by call_once.
 static void *g_knn_scratch_ptr[64] = {nullptr};
+static cudaError_t g_knn_scratch_err[64];
+static std::once_flag g_knn_scratch_once[64];
 
 static int static_scratch(int device, void **out) {
   if (device < 0 || device >= 64) {
     set_error("rbffd_build_stencils_static: device %d not supported", device);
     return RBFFD_EINVAL;
   }
-  if (!g_knn_scratch_ptr[device]) {
+  std::call_once(g_knn_scratch_once[device], [device]() {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_knn_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      set_error("cudaGetSymbolAddress(static cloud scratch) failed: %s", cudaGetErrorString(e));
-      return RBFFD_ECUDA;
-    }
-    g_knn_scratch_ptr[device] = p;
+    if (e == cudaSuccess && p == nullptr) e = cudaErrorInvalidSymbol;
+    g_knn_scratch_err[device] = e;
+    g_knn_scratch_ptr[device] = e == cudaSuccess ? p : nullptr;
+  });
+  if (g_knn_scratch_err[device] != cudaSuccess) {
+    set_error("cudaGetSymbolAddress(static cloud scratch) failed: %s",
+              cudaGetErrorString(g_knn_scratch_err[device]));
+    return RBFFD_ECUDA;
   }
   *out = g_knn_scratch_ptr[device];
   return RBFFD_OK;

@@ -147,28 +147,99 @@ __global__ void k_momentum(int n, int q, int ldn, const int32_t *__restrict__ co
 }
 
 // S6: right-hand side of Eq. (pressure poisson) at interior rows, zero at
-// the Neumann rows and at the pinned row.
-__global__ void k_divergence(int n, int q, int ldn, const int32_t *__restrict__ col,
-                             const double *__restrict__ Wx, const double *__restrict__ Wy,
-                             const int8_t *__restrict__ tag, const double *__restrict__ ut,
-                             const double *__restrict__ vt, double coef,
-                             double *__restrict__ bp, double *__restrict__ pc) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  pc[i] = 0.0;  // initial guess of the p' solve
-  if (tag[i] != 0) {
-    bp[i] = 0.0;
-    return;
-  }
-  double dx = 0.0, dy = 0.0;
+// the Neumann rows and at the pinned row, with the block partials of the
+// sum of the right-hand side and of the interior row count (for k_center).
+__global__ void __launch_bounds__(RT) k_divergence(
+    int n, int q, int ldn, const int32_t *__restrict__ col, const double *__restrict__ Wx,
+    const double *__restrict__ Wy, const int8_t *__restrict__ tag,
+    const double *__restrict__ ut, const double *__restrict__ vt, double coef,
+    double *__restrict__ bp, double *__restrict__ pc, double *__restrict__ part) {
+  __shared__ double sred[RT / 32];
+  double sb = 0.0, sn = 0.0;
+  for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
+    pc[i] = 0.0;  // initial guess of the p' solve
+    if (tag[i] != 0) {
+      bp[i] = 0.0;
+      continue;
+    }
+    double dx = 0.0, dy = 0.0;
 #pragma unroll 4
-  for (int j = 0; j < q; ++j) {
-    int64_t e = (int64_t)j * ldn + i;
-    const int c = col[e];
-    dx += Wx[e] * ut[c];
-    dy += Wy[e] * vt[c];
+    for (int j = 0; j < q; ++j) {
+      int64_t e = (int64_t)j * ldn + i;
+      const int c = col[e];
+      dx += Wx[e] * ut[c];
+      dy += Wy[e] * vt[c];
+    }
+    const double b = coef * (dx + dy);
+    bp[i] = b;
+    sb += b;
+    sn += 1.0;
   }
-  bp[i] = coef * (dx + dy);
+  sb = block_sum<RT>(sb, sred);
+  sn = block_sum<RT>(sn, sred);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sb;
+    part[gridDim.x + blockIdx.x] = sn;
+  }
+}
+
+// Pinned problems: take c0 e_I away from the interior rows of the p'
+// right-hand side before the solve, c0 = the total shift c of the last p'
+// solve (rec->cshift; 0 after a build).  This is the first, approximate
+// part of the compatible shift c e_I (compat_shift removes the rest
+// exactly, so c0 only has to be close): after one compatible correction
+// the divergence left in u is about (dt / rho a1) c e_I, so the next
+// right-hand side is about c e_I plus what changed.  Without it the
+// right-hand side tends to c e_I near convergence, which is incompatible,
+// and the pinned solve of it is dominated by the pin's large response
+// (the p' solve's accuracy floor grows with |x|, and an FP32 inner solve
+// cannot resolve it).  The plain interior mean is no substitute: psi
+// weights the rows roughly by the area around each point.
+__global__ void __launch_bounds__(RT) k_center(int n, const int8_t *__restrict__ tag,
+                                               double *__restrict__ bp,
+                                               const IterRecord *__restrict__ rec) {
+  const double c0 = rec->cshift;
+  for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT)
+    if (tag[i] == RBFFD_TAG_INTERIOR) bp[i] -= c0;
+}
+
+// Compatible pressure correction (pinned problems: no outlet fixes the
+// pressure level).  The p' equation with Neumann rows only is singular and
+// solvable only for a right-hand side b with psi . b = 0 (psi: its left
+// null vector); the divergence of u~ does not meet that exactly.  Its
+// compatible solution is p' = M^{-1} (b - c e_I), e_I = 1 at interior rows,
+// M = the stored p' matrix (pin row = identity), with c such that the
+// pin's own Neumann row holds as well.  k_center has already taken c0 e_I
+// away (b' = b - c0 e_I is what the solve saw), so by linearity
+//   p' = M^{-1} b' - c1 z,   z = M^{-1} e_I (solved once per build),
+//   c1 = (G_pin . M^{-1} b') / (G_pin . z),   G_pin = the pin's n . grad row,
+// since G_pin . p' = 0 is the dropped equation; c = c0 + c1 is stored for
+// the next solve.  Warp 0 of every block computes c1 in the same order
+// (bit-identical in all blocks); z == null (an outlet fixes the level)
+// gives c1 = 0.
+__device__ __forceinline__ double compat_shift(int q, int ldn, int pin,
+                                               const int32_t *__restrict__ col,
+                                               const double *__restrict__ Wx,
+                                               const double *__restrict__ Wy, double npx,
+                                               double npy, const double *__restrict__ pc,
+                                               const double *__restrict__ z, double *s_c) {
+  if (threadIdx.x < 32) {
+    double a = 0.0, b = 0.0;
+    if (z) {
+      for (int j = threadIdx.x; j < q; j += 32) {
+        const int64_t e = (int64_t)j * ldn + pin;
+        const double g = npx * Wx[e] + npy * Wy[e];
+        const int c = col[e];
+        a += g * pc[c];
+        b += g * z[c];
+      }
+      a = warp_sum(a);
+      b = warp_sum(b);
+    }
+    if (threadIdx.x == 0) *s_c = z ? a / b : 0.0;
+  }
+  __syncthreads();
+  return *s_c;
 }
 
 // S8 (p += p' inside) fused with S9 (boundary pressure, Eq. normal momentum;
@@ -177,21 +248,30 @@ __global__ void k_divergence(int n, int q, int ldn, const int32_t *__restrict__ 
 //   sum_j G_ij p_j = N . [ -rho (a1 u~ + a2 u^n + a3 u^{n-1})/dt
 //                          - rho (u~ . grad) u~ + mu Lap u~ ]_i,
 // solved for p_i with every other p_j at its value after the interior
-// update (p_j + p'_j inside, old p_j on the boundary).  Writes p_out.
-__global__ void k_pressure(int n, int q, int ldn, const int32_t *__restrict__ col,
-                           const double *__restrict__ Wx, const double *__restrict__ Wy,
-                           const double *__restrict__ Wl, const int8_t *__restrict__ tag,
-                           const double *__restrict__ nx, const double *__restrict__ ny,
-                           const double *__restrict__ p, const double *__restrict__ pc,
-                           const double *__restrict__ ut, const double *__restrict__ vt,
-                           const double *__restrict__ un, const double *__restrict__ vn,
-                           const double *__restrict__ unm1, const double *__restrict__ vnm1,
-                           double rho, double mu, double dt, double a1, double a2, double a3,
-                           double fx, double fy, double *__restrict__ p_out) {
+// update (p_j + p'_j inside, old p_j on the boundary).  Writes p_out and
+// the compatible p' (compat_shift) to pcs; pc and z are only read.
+__global__ void __launch_bounds__(RT) k_pressure(
+    int n, int q, int ldn, const int32_t *__restrict__ col, const double *__restrict__ Wx,
+    const double *__restrict__ Wy, const double *__restrict__ Wl,
+    const int8_t *__restrict__ tag, const double *__restrict__ nx,
+    const double *__restrict__ ny, const double *__restrict__ p,
+    const double *__restrict__ pc, const double *__restrict__ z, int pin,
+    const double *__restrict__ ut, const double *__restrict__ vt,
+    const double *__restrict__ un, const double *__restrict__ vn,
+    const double *__restrict__ unm1, const double *__restrict__ vnm1, double rho, double mu,
+    double dt, double a1, double a2, double a3, double fx, double fy,
+    double *__restrict__ p_out, double *__restrict__ pcs, IterRecord *__restrict__ rec) {
+  __shared__ double s_c;
+  const double cs = compat_shift(q, ldn, pin, col, Wx, Wy, z ? nx[pin] : 0.0,
+                                 z ? ny[pin] : 0.0, pc, z, &s_c);
+  // only this thread touches cshift in this kernel (k_center read it before)
+  if (z && blockIdx.x == 0 && threadIdx.x == 0) rec->cshift += cs;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const double pci = z ? pc[i] - cs * z[i] : pc[i];
+  pcs[i] = pci;
   if (tag[i] == RBFFD_TAG_INTERIOR) {
-    p_out[i] = p[i] + pc[i];
+    p_out[i] = p[i] + pci;
     return;
   }
   if (tag[i] == RBFFD_TAG_OUTFLOW) {
@@ -215,7 +295,7 @@ __global__ void k_pressure(int n, int q, int ldn, const int32_t *__restrict__ co
     if (c == i) {
       gii += g;
     } else {
-      const double pj = tag[c] == 0 ? p[c] + pc[c] : p[c];
+      const double pj = tag[c] == 0 ? p[c] + (z ? pc[c] - cs * z[c] : pc[c]) : p[c];
       off += g * pj;
     }
   }
@@ -230,12 +310,13 @@ __global__ void k_pressure(int n, int q, int ldn, const int32_t *__restrict__ co
 // S8 velocity correction, Eqs. (u:correction), (v:correction), of every
 // component that is not prescribed (row_kind != ROW_ID: interior, outlets,
 // the tangential component on symmetry lines), with the block partials of
-// sum|du| and sum|dv| for Delta (S10).
+// sum|du| and sum|dv| for Delta (S10).  pcs: the compatible p' that
+// k_pressure wrote; it is also copied into pc (the p' field of the step).
 __global__ void __launch_bounds__(RT) k_correct(
     int n, int q, int ldn, const int32_t *__restrict__ col, const double *__restrict__ Wx,
     const double *__restrict__ Wy, const int8_t *__restrict__ tag,
     const double *__restrict__ nx, const double *__restrict__ ny,
-    const double *__restrict__ pc, const double *__restrict__ ut,
+    const double *__restrict__ pcs, double *__restrict__ pc, const double *__restrict__ ut,
     const double *__restrict__ vt, double c, double *__restrict__ u, double *__restrict__ v,
     const double *__restrict__ pnew, double *__restrict__ p, double *__restrict__ part) {
   __shared__ double sred[RT / 32];
@@ -245,6 +326,7 @@ __global__ void __launch_bounds__(RT) k_correct(
     // the buffers an outer iteration uses stay the same, so it can be
     // captured and replayed)
     p[i] = pnew[i];
+    pc[i] = pcs[i];
     double unew = ut[i], vnew = vt[i];
     const int t = tag[i];
     if (t != RBFFD_TAG_DIRICHLET) {
@@ -252,7 +334,7 @@ __global__ void __launch_bounds__(RT) k_correct(
 #pragma unroll 4
       for (int j = 0; j < q; ++j) {
         int64_t e = (int64_t)j * ldn + i;
-        const double pj = pc[col[e]];
+        const double pj = pcs[col[e]];
         gx += Wx[e] * pj;
         gy += Wy[e] * pj;
       }
@@ -308,7 +390,7 @@ __global__ void __launch_bounds__(RT) k_rotate(int n, const double *__restrict__
 
 // Steady residual partials over interior rows (see rbffd_steady_residual):
 // slots 0 |r|^2, 1 |rho (u.grad)u|^2, 2 |mu Lap u|^2, 3 |grad p|^2,
-// 4 |div u|^2, 5 |grad u|^2.
+// 4 |div u|^2, 5 |grad u|^2, 6 |f|^2, 7 sum div u, 8 interior rows.
 __global__ void __launch_bounds__(RT) k_resid(int n, int q, int ldn,
                                               const int32_t *__restrict__ col,
                                               const double *__restrict__ Wx,
@@ -321,7 +403,7 @@ __global__ void __launch_bounds__(RT) k_resid(int n, int q, int ldn,
                                               double mu, double fx, double fy,
                                               double *__restrict__ part) {
   __shared__ double sred[RT / 32];
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  double acc[RESID_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
     if (tag[i] != 0) continue;
     double gxu = 0, gyu = 0, lu = 0, gxv = 0, gyv = 0, lv = 0, gpx = 0, gpy = 0;
@@ -345,10 +427,12 @@ __global__ void __launch_bounds__(RT) k_resid(int n, int q, int ldn,
     acc[3] += gpx * gpx + gpy * gpy;
     const double dc = gxu + gyv;
     acc[4] += dc * dc;
+    acc[7] += dc;
+    acc[8] += 1.0;
     acc[5] += gxu * gxu + gyu * gyu + gxv * gxv + gyv * gyv;
   }
 #pragma unroll
-  for (int s = 0; s < 7; ++s) {
+  for (int s = 0; s < RESID_SLOTS; ++s) {
     double t = block_sum<RT>(acc[s], sred);
     if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
   }
@@ -356,9 +440,12 @@ __global__ void __launch_bounds__(RT) k_resid(int n, int q, int ldn,
 
 // Fixed-order sums of the partials into the iteration record.
 // mode 0: delta = (S0 + S1) / n   mode 1: change = (S0 + S1) / n
-// mode 2: steady residual from the seven sums of k_resid.
+// mode 2: steady residual from the sums of k_resid; compat (pinned
+// problems, whose compatible p' leaves continuity satisfied up to a
+// constant lambda = mean interior divergence): R_c of d - lambda, with
+// |d - lambda|^2 = S4 - S7^2 / S8.
 __global__ void k_finalize(const double *__restrict__ part, int nb, int n, int mode,
-                           IterRecord *rec) {
+                           IterRecord *rec, int compat = 0) {
   if (threadIdx.x >= 32) return;
   if (mode == 0 || mode == 1) {
     double a = warp_sum_array(part, nb);
@@ -371,16 +458,23 @@ __global__ void k_finalize(const double *__restrict__ part, int nb, int n, int m
         rec->change = d;
     }
   } else {
-    double s[7];
-    for (int k = 0; k < 7; ++k) s[k] = warp_sum_array(part + k * nb, nb);
+    double s[RESID_SLOTS];
+    for (int k = 0; k < RESID_SLOTS; ++k) s[k] = warp_sum_array(part + k * nb, nb);
     if (threadIdx.x == 0) {
+      const double lambda = s[8] > 0 ? s[7] / s[8] : 0.0;
+      double nc = s[4];
+      if (compat && s[8] > 0) {
+        nc = s[4] - s[7] * (s[7] / s[8]);
+        if (nc < 0.0) nc = 0.0;
+      }
       double dm = sqrt(s[1]) + sqrt(s[2]) + sqrt(s[3]) + sqrt(s[6]);
       double dc = sqrt(s[5]);
       double rm = dm > 0 ? sqrt(s[0]) / dm : sqrt(s[0]);
-      double rc = dc > 0 ? sqrt(s[4]) / dc : sqrt(s[4]);
+      double rc = dc > 0 ? sqrt(nc) / dc : sqrt(nc);
       rec->resid[0] = rm;
       rec->resid[1] = rc;
       rec->resid[2] = rm > rc ? rm : rc;
+      rec->resid[3] = lambda;
     }
   }
 }
@@ -466,6 +560,16 @@ __global__ void k_cd_start(int n, double *__restrict__ x, double *logacc) {
   if (i < n) x[i] = 1.0 + 0.5 * (double)((i * 7919) % 13) / 13.0;
 }
 
+// Right-hand side e_I (1 at interior rows, 0 elsewhere) and a zero initial
+// guess, for the once-per-build solve z = M^{-1} e_I of the compatible p'.
+__global__ void k_interior_ones(int n, const int8_t *__restrict__ tag, double *__restrict__ b,
+                                double *__restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  b[i] = tag[i] == RBFFD_TAG_INTERIOR ? 1.0 : 0.0;
+  x[i] = 0.0;
+}
+
 // ------------------------------------------------------------------ host
 
 static inline int grid_of(int n) { return (n + RT - 1) / RT; }
@@ -489,25 +593,29 @@ int ops_momentum(rbffd_problem *P, const rbffd_step_params *sp) {
 
 int ops_divergence(rbffd_problem *P, const rbffd_step_params *sp) {
   double coef = P->rho * sp->alpha[0] / sp->dt;
-  k_divergence<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(P->n, P->q, P->ldn, P->col, P->Wx,
-                                                          P->Wy, P->tag, P->ut, P->vt, coef,
-                                                          P->bp, P->pc);
-  return after_launch(P->ctx, "k_divergence");
+  k_divergence<<<P->rblocks, RT, 0, P->ctx->stream>>>(P->n, P->q, P->ldn, P->col, P->Wx,
+                                                      P->Wy, P->tag, P->ut, P->vt, coef, P->bp,
+                                                      P->pc, P->rpart);
+  RBFFD_TRY(after_launch(P->ctx, "k_divergence"));
+  if (!P->compat) return RBFFD_OK;
+  k_center<<<P->rblocks, RT, 0, P->ctx->stream>>>(P->n, P->tag, P->bp, P->rec);
+  return after_launch(P->ctx, "k_center");
 }
 
 int ops_pressure(rbffd_problem *P, const rbffd_step_params *sp) {
   k_pressure<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(
       P->n, P->q, P->ldn, P->col, P->Wx, P->Wy, P->Wl, P->tag, P->nx, P->ny, P->p, P->pc,
-      P->ut, P->vt, P->un, P->vn, P->unm1, P->vnm1, P->rho, P->mu, sp->dt, sp->alpha[0],
-      sp->alpha[1], sp->alpha[2], P->force[0], P->force[1], P->p2);
+      P->compat ? P->zc : nullptr, P->pin < 0 ? 0 : P->pin, P->ut, P->vt, P->un, P->vn,
+      P->unm1, P->vnm1, P->rho, P->mu, sp->dt, sp->alpha[0], sp->alpha[1], sp->alpha[2],
+      P->force[0], P->force[1], P->p2, P->pcs, P->rec);
   return after_launch(P->ctx, "k_pressure");
 }
 
 int ops_correct(rbffd_problem *P, const rbffd_step_params *sp) {
   double c = sp->dt / (P->rho * sp->alpha[0]);
   k_correct<<<P->rblocks, RT, 0, P->ctx->stream>>>(P->n, P->q, P->ldn, P->col, P->Wx, P->Wy,
-                                                   P->tag, P->nx, P->ny, P->pc, P->ut, P->vt, c,
-                                                   P->u, P->v, P->p2, P->p, P->rpart);
+                                                   P->tag, P->nx, P->ny, P->pcs, P->pc, P->ut,
+                                                   P->vt, c, P->u, P->v, P->p2, P->p, P->rpart);
   RBFFD_TRY(after_launch(P->ctx, "k_correct"));
   k_finalize<<<1, 32, 0, P->ctx->stream>>>(P->rpart, P->rblocks, P->n, 0, P->rec);
   return after_launch(P->ctx, "k_finalize");
@@ -526,7 +634,8 @@ int ops_resid(rbffd_problem *P) {
                                                  P->Wl, P->tag, P->u, P->v, P->p, P->rho, P->mu,
                                                  P->force[0], P->force[1], P->rpart);
   RBFFD_TRY(after_launch(P->ctx, "k_resid"));
-  k_finalize<<<1, 32, 0, P->ctx->stream>>>(P->rpart, P->rblocks, P->n, 2, P->rec);
+  k_finalize<<<1, 32, 0, P->ctx->stream>>>(P->rpart, P->rblocks, P->n, 2, P->rec,
+                                            P->compat ? 1 : 0);
   return after_launch(P->ctx, "k_finalize");
 }
 
@@ -547,6 +656,11 @@ int ops_courant(rbffd_problem *P, int iters, double *logacc) {
     RBFFD_TRY(after_launch(P->ctx, "k_cd_scale"));
   }
   return RBFFD_OK;
+}
+
+int ops_interior_ones(rbffd_problem *P, double *b, double *x) {
+  k_interior_ones<<<grid_of(P->n), RT, 0, P->ctx->stream>>>(P->n, P->tag, b, x);
+  return after_launch(P->ctx, "k_interior_ones");
 }
 
 int ops_spmv(rbffd_problem *P, const double *val, const double *x, double *y) {

@@ -10,8 +10,12 @@
 struct IterRecord {
   double delta;
   double change;
-  double resid[3];
-  double pad[3];
+  double resid[4];  // R_m, R_c, R, lambda (rbffd_steady_residual)
+  double pad[1];
+  // total compatible shift c of the last p' solve (ops.cu: k_center,
+  // compat_shift): the next solve takes it away from its right-hand side
+  // first; zero after a build
+  double cshift;
 };
 
 struct rbffd_problem {
@@ -45,6 +49,12 @@ struct rbffd_problem {
   void *partin = nullptr;
   // fields
   double *u, *v, *p, *p2, *un, *vn, *unm1, *vnm1, *ut, *vt, *pc, *bu, *bv, *bp;
+  // compatible p' of a pinned problem (no outlet): z = M^{-1} e_I, solved
+  // once per build by compat_ready, and the shifted p' of the iteration
+  // (ops.cu: compat_shift)
+  double *zc, *pcs;
+  bool compat = false;   // pin >= 0: the p' equation has Neumann rows only
+  bool z_ready = false;  // zc holds z for the current build
   // Krylov workspace: 8 vectors x 2 right-hand sides
   rbffd::KrylovVecs kv[2];
   double *part;       // Krylov partials
@@ -74,6 +84,10 @@ struct rbffd_problem {
   rbffd::AmgInfo amg_info{};
   // the hierarchy's host part while it is being built (amg_ready finishes it)
   rbffd::AmgJob *amg_job = nullptr;
+  // status of a hierarchy build that failed for good (not for want of
+  // device memory): every later p' solve returns it, until a reload
+  int amg_err = 0;
+  char amg_errmsg[160] = {0};
   // flexible GMRES with an FP32 hierarchy (RBFFD_PRECOND_AMG_FGMRES): the
   // FP32 level table and the basis / direction vectors and partials
   const rbffd::AmgDevF *amgf = nullptr;
@@ -94,9 +108,15 @@ int problem_step_end(rbffd_problem *P, double *change);
 // iterations (the roofline numerator of the p' kernel statistics).
 double pcorr_bytes(const rbffd_problem *P, int iters);
 // Steady stopping test of solve_steady and of the request server.
-bool steady_done(const rbffd_solve_params *s, double R, double change);
+bool steady_done(const rbffd_solve_params *s, double R, double change, int steps);
 // Finish the multigrid hierarchy whose host part a build started (upload
 // on the problem's stream); a no-op when none is pending.  Every use of
 // the hierarchy calls it first.
 int amg_ready(rbffd_problem *P);
+// Solve z = M^{-1} e_I with the problem's p' solver once per build (pinned
+// problems only; a no-op otherwise or when done).  Synchronises the stream:
+// call it before any graph capture.
+int compat_ready(rbffd_problem *P);
+// partial-sum slots of the steady residual reduction (ops.cu: k_resid)
+constexpr int RESID_SLOTS = 9;
 }  // namespace rbffd

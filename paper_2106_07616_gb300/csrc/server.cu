@@ -52,8 +52,9 @@ struct Request {
   double tol = 1e-4;
   int outer_in_step = 0;
   int steps = 0;
+  int admit_attempts = 0;  // hierarchy uploads tried (the build itself runs once)
   int64_t outer_total = 0;
-  double resid[3] = {1, 1, 1};
+  double resid[4] = {1, 1, 1, 0};
   std::vector<double> u, v, p;
 };
 
@@ -73,6 +74,7 @@ struct rbffd_server {
   bool stop = false;
   int fatal = RBFFD_OK;
   BatchScratch scratch;
+  Clock::time_point t0 = Clock::now();  // the clock of rbffd_result admit_s / done_s
 
   void finish(Request *r, int status) {
     r->status = status;
@@ -104,23 +106,27 @@ struct rbffd_server {
         if (queue.empty() || (int)running.size() >= max_active) return;
         r = queue.front();
       }
-      int rc = rbffd_problem_create(ctx, &r->desc, &r->P);
+      // A request whose problem was built on an earlier attempt keeps it:
+      // only its hierarchy upload, which found no device memory then, is
+      // retried (the clouds, weights, operators and the host part of the
+      // hierarchy are not built again).
+      int rc = r->P ? RBFFD_OK : rbffd_problem_create(ctx, &r->desc, &r->P);
       if (rc == RBFFD_OK) {
+        ++r->admit_attempts;
         // the hierarchy's device memory counts against the budget now
         rc = rbffd::amg_ready(r->P);
-        if (rc != RBFFD_OK) {
-          rbffd_problem_destroy(r->P);
-          r->P = nullptr;
-        }
+        if (rc == RBFFD_OK) rc = rbffd::compat_ready(r->P);
+        if (rc == RBFFD_ENOMEM && !running.empty()) return;  // keep r->P; wait for memory
+      } else {
+        r->P = nullptr;
+        if (rc == RBFFD_ENOMEM && !running.empty()) return;  // wait for memory
       }
-      if (rc == RBFFD_ENOMEM && !running.empty()) return;  // wait for memory
       {
         std::lock_guard<std::mutex> g(mu);
         queue.pop_front();
       }
       if (rc != RBFFD_OK) {
-        r->P = nullptr;
-        finish(r, rc);
+        finish(r, rc);  // frees a problem built on the way
         continue;
       }
       r->t_admit = Clock::now();
@@ -166,7 +172,7 @@ struct rbffd_server {
         r->steps++;
         r->outer_in_step = 0;
         r->tol = change < 1e-4 ? change : 1e-4;
-        if (steady_done(&r->sp, r->resid[2], change)) {
+        if (steady_done(&r->sp, r->resid[2], change, r->steps)) {
           finish(r, RBFFD_OK);
           continue;
         }
@@ -291,7 +297,11 @@ extern "C" int rbffd_server_poll(rbffd_server *s, uint64_t ticket, rbffd_result 
     res->status = r->status;
     res->steps = r->steps;
     res->outer_iters = r->outer_total;
-    for (int k = 0; k < 3; ++k) res->resid[k] = r->resid[k];
+    for (int k = 0; k < 4; ++k) res->resid[k] = r->resid[k];
+    res->admit_attempts = r->admit_attempts;
+    res->arrive_s = secs(s->t0, r->t_arrive);
+    if (r->state >= 1) res->admit_s = secs(s->t0, r->t_admit);
+    if (r->state == 2) res->done_s = secs(s->t0, r->t_done);
     if (r->state >= 1) res->queue_s = secs(r->t_arrive, r->t_admit);
     if (r->state == 2) {
       res->latency_s = secs(r->t_arrive, r->t_done);

@@ -62,7 +62,7 @@ class SolveParams(C.Structure):
 
 class SolveStats(C.Structure):
     _fields_ = [("steps", C.c_int32), ("outer_iters", C.c_int64),
-                ("krylov_iters", C.c_int64 * 3), ("resid", C.c_double * 3),
+                ("krylov_iters", C.c_int64 * 3), ("resid", C.c_double * 4),
                 ("change", C.c_double)]
 
 
@@ -80,7 +80,8 @@ class ServerParams(C.Structure):
 class Result(C.Structure):
     _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("queue_s", C.c_double),
                 ("latency_s", C.c_double), ("steps", C.c_int32), ("outer_iters", C.c_int64),
-                ("resid", C.c_double * 3)]
+                ("resid", C.c_double * 4), ("admit_attempts", C.c_int32),
+                ("arrive_s", C.c_double), ("admit_s", C.c_double), ("done_s", C.c_double)]
 
 
 STEP_CB = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int32, C.c_double)
@@ -361,7 +362,8 @@ class Problem:
         return it.value, ch.value
 
     def steady_residual(self):
-        r = (C.c_double * 3)()
+        """(R_m, R_c, R, lambda); see rbffd_steady_residual."""
+        r = (C.c_double * 4)()
         _check(load().rbffd_steady_residual(self.h, r), "rbffd_steady_residual")
         return np.array(list(r))
 
@@ -486,7 +488,8 @@ class Server:
                "rbffd_server_poll")
         out = {"state": r.state, "status": r.status, "queue_s": r.queue_s,
                "latency_s": r.latency_s, "steps": r.steps, "outer": r.outer_iters,
-               "resid": list(r.resid)}
+               "resid": list(r.resid), "admit_attempts": r.admit_attempts,
+               "arrive_s": r.arrive_s, "admit_s": r.admit_s, "done_s": r.done_s}
         if fields:
             out.update(u=u, v=v, p=p)
         return out
