@@ -147,6 +147,10 @@ def batch_instances(count=256, seed=4):
 
 
 def run_batch(args):
+    print(json.dumps(batch_line(args)), flush=True)
+
+
+def batch_line(args):
     """Many instances per step: S1-S3 for every member, then one batched
     outer iteration (both Krylov solves of all members in one launch each)."""
     import torch
@@ -243,10 +247,14 @@ def run_batch(args):
            "krylov_mom": {"launches": km["launches"], "ms": km["ms"],
                           "algorithmic_GBps": km["bytes"] / (km["ms"] / 1e3) / 1e9 if km["ms"] else None},
            "peak_hbm_GBps": peak, "peak_source": src, "clocks": clk.summary()}
-    print(json.dumps(out), flush=True)
+    for P in probs:
+        P.close()
+    B.close()
+    ctx.close()
+    return out
 
 
-def serve_requests(count, seed=5, n_lo=5000.0, n_hi=50000.0):
+def serve_requests(count, seed=5, n_lo=5000.0, n_hi=50000.0, cfl=10.0):
     """Serving workload: steady solves of three geometries drawn uniformly --
     Kovasznay (Re 20-60), lid-driven cavity (Re 10-400) and flow past a
     cylinder (Re 10-40, the paper's steady range) -- N log-uniform on
@@ -264,25 +272,32 @@ def serve_requests(count, seed=5, n_lo=5000.0, n_hi=50000.0):
         if kind == 0:
             re = float(rng.uniform(20.0, 60.0))
             fp = clouds.kovasznay(side, seed=5000 + i, degree=k, q=q, re=re,
-                                  dt=20.0 / (side - 1))
+                                  dt=cfl * 2.0 / (side - 1))
         elif kind == 1:
             re = float(rng.uniform(10.0, 400.0))
-            fp = clouds.cavity(side, seed=5000 + i, degree=k, q=q, re=re, dt=10.0 / (side - 1))
+            fp = clouds.cavity(side, seed=5000 + i, degree=k, q=q, re=re,
+                               dt=cfl / (side - 1))
         else:
             re = float(rng.uniform(10.0, 40.0))
             h0 = 0.1 * float(np.sqrt(5000.0 / n))
-            fp = clouds.cylinder(int(n), seed=5000 + i, degree=k, q=q, re=re, dt=10.0 * h0,
+            fp = clouds.cylinder(int(n), seed=5000 + i, degree=k, q=q, re=re, dt=cfl * h0,
                                  h0=h0, hmax=0.5)
         reqs.append((t, fp))
     return reqs
 
 
 def run_serve(args):
+    print(json.dumps(serve_line(args)), flush=True)
+
+
+def serve_line(args, n_hi=None):
     import torch  # noqa: F401
 
     from paper_2106_07616_gb300 import _build, rbffd
     _build.build()
-    reqs = serve_requests(args.count or 48)
+    n_hi = float(n_hi or args.serve_n_hi)
+    cfl = args.serve_cfl if args.resid_tol < 1e-6 else 10.0
+    reqs = serve_requests(args.count or 48, n_hi=n_hi, cfl=cfl)
     ctx = rbffd.Context(0)
     S = rbffd.Server(ctx)
     t0 = time.perf_counter()
@@ -318,10 +333,12 @@ def run_serve(args):
                      "f32+f64" if args.precision == "mixed" or args.precond == "fgmres"
                      else "f64"),
            "config": {"workload": f"serve{args.count or 48}",
-                      "description": "Poisson arrivals 20/s; Kovasznay Re 20-60 / cavity "
-                                     "Re 10-400 / cylinder Re 10-40, N log-uniform [5k,50k], "
-                                     "degree {3,4}, q=2m; continuous batching in one server"}}
-    print(json.dumps(out), flush=True)
+                      "description": (f"Poisson arrivals 20/s; Kovasznay Re 20-60 / cavity "
+                                      f"Re 10-400 / cylinder Re 10-40, N log-uniform "
+                                      f"[5k,{n_hi / 1e3:.0f}k], degree {{3,4}}, q=2m, dt = "
+                                      f"{cfl:g} x spacing; continuous batching in one server")}}
+    ctx.close()
+    return out
 
 
 def read_peaks():
@@ -435,6 +452,119 @@ def run_reference(args):
            "e2e": {"value": value, "unit": "outer_iter/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def time_steps(step, stream, flush, steps):
+    """CUDA-event time of `steps` calls of step() (L2 flushed before each,
+    outside the events); returns (ms, outer iterations)."""
+    import torch
+    total_ms, total_it = 0.0, 0
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        total_it += step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    return total_ms, total_it
+
+
+def march_rate(P, fp, init, stream, flush, first=20, count=20):
+    """Outer iterations per second of a developed march: from rest, steps
+    0..first-1 untimed, then `count` steps timed, each with the paper's
+    adaptive outer tolerance (1e-4, then min(1e-4, change)) and no rebuild."""
+    for k, a in init.items():
+        P.set(k, a)
+    tol = [1e-4]
+
+    def one():
+        it, ch = P.time_step(fp.dt, tol[0], max_outer=20, krylov_maxit=100000)
+        tol[0] = min(1e-4, ch)
+        return it
+
+    for _ in range(first):
+        one()
+    ms, it = time_steps(one, stream, flush, count)
+    return {"value": it / (ms / 1e3), "unit": "outer_iter/s", "steps": f"{first}..{first + count - 1}",
+            "outer_iters": it, "ms": ms}
+
+
+def bench_extras(args, ctx, stream, fp, dev, desc_dev, init, flush, P):
+    """Keys beside the headline (one GPU, rank 0): the plain FP64 GPU path on
+    the same step (FP64 Jacobi BiCGSTAB for momentum and p', the paper's
+    solver) and the ratio the mixed-precision path reaches against it; the
+    outer-iteration rate of a developed march (no rebuild) for both paths;
+    the batched workload and the request server."""
+    from paper_2106_07616_gb300 import rbffd
+    res = {}
+    d64 = rbffd.desc_from_pointers(fp.n, fp.q, fp.degree, fp.pin, fp.rho, fp.mu, rbffd.PREC_FP64,
+                                   dev["x"], dev["y"], dev["tag"], dev["nx"], dev["ny"],
+                                   dev["ubc"], dev["vbc"], rbffd.PRECOND_JACOBI)
+    Q = rbffd.Problem(ctx, desc=d64)
+
+    def step64():
+        Q.reload(desc=d64)
+        for k, a in init.items():
+            Q.set(k, a)
+        it, _ = Q.time_step(fp.dt, 1e-4, max_outer=args.outer, krylov_maxit=100000)
+        return it
+
+    step64()
+    n64 = max(2, min(args.steps, 3))
+    ms64, it64 = time_steps(step64, stream, flush, n64)
+    v64 = it64 / (ms64 / 1e3)
+    res["fp64_plain"] = {
+        "value": v64, "unit": "outer_iter/s", "steps": n64, "ms_per_step": ms64 / n64,
+        "outer_iters_per_step": it64 / n64,
+        "path": "FP64 BiCGSTAB with Jacobi for momentum and p' (the paper's solver), same step, "
+                "same 1e-12 FP64 relative residual per solve"}
+    P.reload(desc=desc_dev)
+    Q.reload(desc=d64)
+    m_mixed = march_rate(P, fp, init, stream, flush)
+    m_64 = march_rate(Q, fp, init, stream, flush)
+    res["march"] = {"default": m_mixed, "fp64_plain": m_64,
+                    "ratio": m_mixed["value"] / m_64["value"]}
+    res["north_star_ratio"] = {
+        "first_step": res_ratio(v_default_step(P, desc_dev, init, fp, args, stream, flush), v64),
+        "march": res["march"]["ratio"],
+        "note": "mixed-precision path (FGMRES with FP32 Arnoldi and V-cycle for p', FP32 "
+                "BiCGSTAB in FP64 refinement for momentum) over the plain FP64 GPU path "
+                "(FP64 Jacobi BiCGSTAB for both), same step, same FP64 residual per solve"}
+    Q.close()
+    # the batched and served workloads, at sizes that keep this run short
+    ba = argparse.Namespace(**vars(args))
+    ba.count, ba.steps, ba.warmup = args.batch_count, 2, 1
+    ba.precond, ba.precision = "amg", "fp64"
+    b = batch_line(ba)
+    res["batch"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "e2e", "roofline",
+                                      "krylov_p", "krylov_mom", "config", "gpu_launches")}
+    sa = argparse.Namespace(**vars(args))
+    sa.count, sa.resid_tol, sa.criterion, sa.max_steps = args.serve_count, 1e-8, 0, 20000
+    sa.precond, sa.precision = "amg", "fp64"
+    sv = serve_line(sa, n_hi=args.serve_key_n_hi)
+    res["serve"] = {k: sv[k] for k in ("p50", "p99", "unit", "solves_per_s", "requests", "ok",
+                                       "failed", "failures", "resid_tol", "criterion", "wall_s",
+                                       "config", "steps_ok", "R_ok")}
+    return res
+
+
+def res_ratio(a, b):
+    return a / b if b else None
+
+
+def v_default_step(P, desc_dev, init, fp, args, stream, flush):
+    """The default path's step rate again, on the same flushed-L2 timing as
+    the plain FP64 arm beside it."""
+    def step():
+        P.reload(desc=desc_dev)
+        for k, a in init.items():
+            P.set(k, a)
+        it, _ = P.time_step(fp.dt, 1e-4, max_outer=args.outer, krylov_maxit=100000)
+        return it
+    ms, it = time_steps(step, stream, flush, 3)
+    return it / (ms / 1e3)
 
 
 def run_native(args):
@@ -580,6 +710,10 @@ def run_native(args):
         "outer": {"count": ko["launches"], "ms": ko["ms"]},
     }
 
+    extras = {}
+    if rank == 0 and world == 1 and args.workload == "cavity200" and not args.no_extras:
+        extras = bench_extras(args, ctx, stream, fp, dev, desc_dev, init, flush, P)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         t, it, cores = cpu_oracle_step(fp, args.outer)
@@ -604,6 +738,7 @@ def run_native(args):
                           "parallelism": f"replicas x{world}"},
                "e2e": e2e, "gpu_launches": launches, "roofline": roof,
                "cpu_baseline": cpu, "clocks": clocks, "kernels": kernels}
+        out.update(extras)
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -618,12 +753,24 @@ def main():
     ap.add_argument("--workload", default="cavity200")
     ap.add_argument("--outer", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain-FP64, march, batch and serve keys of the default line")
     ap.add_argument("--count", type=int, default=None,
                     help="instances (batch, default 256) / requests (serve, default 48)")
     ap.add_argument("--resid-tol", type=float, default=1e-5)
     ap.add_argument("--criterion", type=int, default=1,
                     help="serve: 0 = steady residual R, 1 = the paper's steady error change/dt")
     ap.add_argument("--max-steps", type=int, default=1000)
+    ap.add_argument("--serve-n-hi", type=float, default=20000.0,
+                    help="serve: largest request (points)")
+    ap.add_argument("--serve-cfl", type=float, default=0.75,
+                    help="serve at a residual below 1e-6: dt = this x the point spacing")
+    ap.add_argument("--batch-count", type=int, default=256,
+                    help="instances of the batch key of the default line")
+    ap.add_argument("--serve-key-n-hi", type=float, default=10000.0,
+                    help="largest request of the serve key of the default line")
+    ap.add_argument("--serve-count", type=int, default=6,
+                    help="requests of the serve key of the default line")
     ap.add_argument("--precond", default=None, choices=["jacobi", "amg", "fgmres"],
                     help="preconditioner of the pressure-correction BiCGSTAB")
     ap.add_argument("--precision", default=None, choices=["mixed", "ff", "fp64"],

@@ -152,7 +152,17 @@ typedef struct {
   int64_t launches;
   double ms;     /* summed device time */
   double units;  /* units of work processed */
-  double bytes;  /* algorithmic bytes (flops for WEIGHTS) */
+  double bytes;  /* Bound of every device-side wait (the grid exchanges and barriers of the
+ * persistent Krylov kernels) of the launches this context issues from now
+ * on: 2^log2_cycles SM clock cycles; 0 restores the default 2^31 (about a
+ * second at 2 GHz).  A wait that runs out makes its block record a timeout
+ * and leave; the other blocks leave at their next wait, and the call returns
+ * RBFFD_ETIMEOUT with the solve's outputs unspecified.  Nothing is left
+ * running and the context stays usable.  The paper has no counterpart: this
+ * is failure handling of the library.  Errors: RBFFD_EINVAL outside 0..40. */
+int rbffd_ctx_set_wait_limit(rbffd_ctx *ctx, int32_t log2_cycles);
+
+/* algorithmic bytes (flops for WEIGHTS) */
 } rbffd_kernel_stat;
 int rbffd_ctx_profile(rbffd_ctx *ctx, int enable);
 int rbffd_ctx_kernel_stat(const rbffd_ctx *ctx, int32_t which, rbffd_kernel_stat *out);

@@ -180,7 +180,7 @@ static int launch_krylov(BatchScratch &S, int slot, int nr, std::vector<KrylovAr
                            S.off_flags[slot] - S.off_sys[slot], cudaMemcpyHostToDevice,
                            ctx->stream));
   RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * nctas, ctx->stream));
-  RBFFD_CK(cudaMemsetAsync(dbars, 0, sizeof(GridBarrier) * m, ctx->stream));
+  RBFFD_TRY(reset_barriers(ctx, dbars, m));
   RBFFD_TRY(krylov_batch_launch(ctx, nr, nctas, (const KrylovArgs *)(db + S.off_sys[slot]),
                                 (const int *)(db + S.off_cta_sys[slot]),
                                 (const int *)(db + S.off_cta_first[slot]), amg));
@@ -231,7 +231,7 @@ static int launch_mixed(BatchScratch &S, int slot, int nr, int inner,
                            S.off_flags[slot] - S.off_sys[slot], cudaMemcpyHostToDevice,
                            ctx->stream));
   RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * nctas, ctx->stream));
-  RBFFD_CK(cudaMemsetAsync(dbars, 0, sizeof(GridBarrier) * m, ctx->stream));
+  RBFFD_TRY(reset_barriers(ctx, dbars, m));
   return krylov_ir_batch_launch(ctx, nr, inner, nctas, (const MixedArgs *)(db + S.off_sys[slot]),
                                 (const int *)(db + S.off_cta_sys[slot]),
                                 (const int *)(db + S.off_cta_first[slot]));
@@ -273,10 +273,79 @@ static int launch_fgmres(BatchScratch &S, int slot, std::vector<FgmresArgs> &arg
                            S.off_flags[slot] - S.off_sys[slot], cudaMemcpyHostToDevice,
                            ctx->stream));
   RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * nctas, ctx->stream));
-  RBFFD_CK(cudaMemsetAsync(dbars, 0, sizeof(GridBarrier) * m, ctx->stream));
+  RBFFD_TRY(reset_barriers(ctx, dbars, m));
   return fgmres_batch_launch(ctx, nctas, (const FgmresArgs *)(db + S.off_sys[slot]),
                              (const int *)(db + S.off_cta_sys[slot]),
                              (const int *)(db + S.off_cta_first[slot]));
+}
+
+// One batched pressure-correction solve M x_i = b_i of the members sel
+// (one launch per solver: Jacobi BiCGSTAB, multigrid BiCGSTAB, flexible
+// GMRES), issued on the context's stream with no host synchronisation.
+// Its outcome goes to each member's kout[2].  a1 holds the members'
+// common Krylov arguments.
+static int launch_pcorr(BatchScratch &S, rbffd_problem *const *P, const std::vector<int> &sel,
+                        const std::vector<const double *> &b, const std::vector<double *> &x,
+                        const std::vector<double> &tol, const std::vector<int> &maxit) {
+  std::vector<KrylovArgs> pj, pa;
+  std::vector<FgmresArgs> pf;
+  std::vector<int> rj, ra, rf;
+  for (size_t s = 0; s < sel.size(); ++s) {
+    rbffd_problem *Q = P[sel[s]];
+    if (Q->amgf) {
+      FgmresArgs f;
+      memset(&f, 0, sizeof(f));
+      f.n = Q->n;
+      f.q = Q->q;
+      f.ldn = Q->ldn;
+      f.tpr = 1;
+      f.m = Q->fg_m;
+      f.col = Q->col;
+      f.val = Q->Pp;
+      f.val32 = Q->amgf_host.a0;
+      f.b = b[s];
+      f.x = x[s];
+      f.r = Q->fgR;
+      f.V = Q->fgV;
+      f.Z = Q->fgZ;
+      f.part = Q->fgpart;
+      f.out = Q->kout + 2;
+      f.tol = tol[s];
+      f.maxit = maxit[s];
+      f.amg = Q->amgf;
+      pf.push_back(f);
+      rf.push_back(Q->n);
+      continue;
+    }
+    KrylovArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = Q->n;
+    a.q = Q->q;
+    a.ldn = Q->ldn;
+    a.col = Q->col;
+    a.part = Q->part;
+    a.tol = tol[s];
+    a.maxit = maxit[s];
+    a.val = Q->Pp;
+    a.dinv = Q->p_dinv;
+    a.b[0] = b[s];
+    a.x[0] = x[s];
+    a.w[0] = Q->kv[0];
+    a.out = Q->kout + 2;
+    a.nblocks = 2 * std::max(Q->kblocks1, Q->kblocks2);
+    if (Q->amg) {
+      a.amg = Q->amg;
+      pa.push_back(a);
+      ra.push_back(Q->n);
+    } else {
+      pj.push_back(a);
+      rj.push_back(Q->n);
+    }
+  }
+  if (!pj.empty()) RBFFD_TRY(launch_krylov(S, 2, 1, pj, rj));
+  if (!pa.empty()) RBFFD_TRY(launch_krylov(S, 3, 1, pa, ra, true));
+  if (!pf.empty()) RBFFD_TRY(launch_fgmres(S, 4, pf, rf));
+  return RBFFD_OK;
 }
 
 // Issue one batched outer iteration on the context's stream, ending with
@@ -287,7 +356,7 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
   rbffd_ctx *ctx = P[0]->ctx;
   // momentum predictor of every member, then one launch for the two-RHS
   // solves of all members (and one for the single-RHS pairs, if any)
-  std::vector<KrylovArgs> a2, a1s, a1(m);
+  std::vector<KrylovArgs> a2, a1s;
   std::vector<int> rows2, rows1s;
   // mixed-precision members by inner arithmetic (0 FP32, 1 float-float)
   std::vector<MixedArgs> x2[2], x1s[2];
@@ -351,17 +420,6 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
         xr1s[ia].push_back(Q->n);
         xr1s[ia].push_back(Q->n);
       }
-      // the fields a multigrid-BiCGSTAB p' launch takes from a1[i]
-      KrylovArgs a;
-      memset(&a, 0, sizeof(a));
-      a.n = Q->n;
-      a.q = Q->q;
-      a.ldn = Q->ldn;
-      a.col = Q->col;
-      a.part = Q->part;
-      a.tol = sp->krylov_tol;
-      a.maxit = sp->krylov_maxit;
-      a1[i] = a;
       continue;
     }
     KrylovArgs a;
@@ -404,7 +462,6 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
       rows1s.push_back(P[i]->n);
       rows1s.push_back(P[i]->n);
     }
-    a1[i] = a;
   }
   prof_begin(ctx, 0);
   if (!a2.empty()) RBFFD_TRY(launch_krylov(S, 0, 2, a2, rows2));
@@ -417,58 +474,20 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
   prof_end(ctx, 0);
   // p' solves: one launch per solver -- Jacobi BiCGSTAB, multigrid
   // BiCGSTAB, flexible GMRES
-  std::vector<KrylovArgs> pj, pa;
-  std::vector<FgmresArgs> pf;
-  std::vector<int> rj, ra, rf;
+  std::vector<const double *> bs(m);
+  std::vector<double *> xs(m);
+  std::vector<double> tols(m);
+  std::vector<int> maxits(m), sel(m);
   for (int i = 0; i < m; ++i) {
     RBFFD_TRY(ops_divergence(P[i], spv[i]));
-    if (P[i]->amgf) {
-      FgmresArgs f;
-      memset(&f, 0, sizeof(f));
-      f.n = P[i]->n;
-      f.q = P[i]->q;
-      f.ldn = P[i]->ldn;
-      f.tpr = 1;
-      f.m = P[i]->fg_m;
-      f.col = P[i]->col;
-      f.val = P[i]->Pp;
-      f.val32 = P[i]->amgf_host.a0;
-      f.b = P[i]->bp;
-      f.x = P[i]->pc;
-      f.r = P[i]->fgR;
-      f.V = P[i]->fgV;
-      f.Z = P[i]->fgZ;
-      f.part = P[i]->fgpart;
-      f.out = P[i]->kout + 2;
-      f.tol = spv[i]->krylov_tol;
-      f.maxit = spv[i]->krylov_maxit;
-      f.amg = P[i]->amgf;
-      pf.push_back(f);
-      rf.push_back(P[i]->n);
-      continue;
-    }
-    a1[i].val = P[i]->Pp;
-    a1[i].dinv = P[i]->p_dinv;
-    a1[i].b[0] = P[i]->bp;
-    a1[i].b[1] = nullptr;
-    a1[i].x[0] = P[i]->pc;
-    a1[i].x[1] = nullptr;
-    a1[i].w[0] = P[i]->kv[0];
-    a1[i].out = P[i]->kout + 2;
-    a1[i].nblocks = 2 * std::max(P[i]->kblocks1, P[i]->kblocks2);
-    if (P[i]->amg) {
-      a1[i].amg = P[i]->amg;
-      pa.push_back(a1[i]);
-      ra.push_back(P[i]->n);
-    } else {
-      pj.push_back(a1[i]);
-      rj.push_back(P[i]->n);
-    }
+    bs[i] = P[i]->bp;
+    xs[i] = P[i]->pc;
+    tols[i] = spv[i]->krylov_tol;
+    maxits[i] = spv[i]->krylov_maxit;
+    sel[i] = i;
   }
   prof_begin(ctx, 1);
-  if (!pj.empty()) RBFFD_TRY(launch_krylov(S, 2, 1, pj, rj));
-  if (!pa.empty()) RBFFD_TRY(launch_krylov(S, 3, 1, pa, ra, true));
-  if (!pf.empty()) RBFFD_TRY(launch_fgmres(S, 4, pf, rf));
+  RBFFD_TRY(launch_pcorr(S, P, sel, bs, xs, tols, maxits));
   prof_end(ctx, 1);
   for (int i = 0; i < m; ++i) {
     RBFFD_TRY(ops_pressure(P[i], spv[i]));
@@ -519,6 +538,52 @@ static std::vector<uint64_t> graph_key(rbffd_problem *const *P, int m,
   return k;
 }
 
+// The compatible p' of the pinned members built since their last
+// iteration needs z = M^{-1} e_I (problem.cu: compat_ready): solved here for
+// all of them in one batched launch per solver, before anything is issued
+// or captured.  The launch tables it writes are those a captured iteration
+// copies at replay, so a captured graph is dropped first (a build changes
+// the graph key anyway).
+static int batch_compat(BatchScratch &S, rbffd_problem *const *P, int m) {
+  std::vector<int> sel;
+  for (int i = 0; i < m; ++i)
+    if (P[i]->compat && !P[i]->z_ready) sel.push_back(i);
+  if (sel.empty()) return RBFFD_OK;
+  rbffd_ctx *ctx = P[0]->ctx;
+  S.drop_graph();
+  std::vector<const double *> b;
+  std::vector<double *> x;
+  for (int i : sel) {
+    RBFFD_TRY(ops_interior_ones(P[i], P[i]->pcs, P[i]->zc));
+    b.push_back(P[i]->pcs);
+    x.push_back(P[i]->zc);
+  }
+  std::vector<double> tol;
+  std::vector<int> maxit;
+  for (int i : sel) {
+    tol.push_back(compat_tol(P[i]));
+    maxit.push_back(compat_maxit(P[i]));
+  }
+  RBFFD_TRY(launch_pcorr(S, P, sel, b, x, tol, maxit));
+  std::vector<KrylovOut> ko(sel.size());
+  for (size_t s = 0; s < sel.size(); ++s)
+    RBFFD_CK(cudaMemcpyAsync(&ko[s], P[sel[s]]->kout + 2, sizeof(KrylovOut),
+                             cudaMemcpyDeviceToHost, ctx->stream));
+  RBFFD_CK(cudaStreamSynchronize(ctx->stream));
+  for (size_t s = 0; s < sel.size(); ++s) {
+    int rc = status_of(ko[s].status);
+    // the same acceptance as compat_ready (z carries the pin's response)
+    if (rc == RBFFD_ENOCONV && ko[s].relres <= compat_accept()) rc = RBFFD_OK;
+    if (rc != RBFFD_OK) {
+      set_error("batch member %d: compatible p': the solve of M z = e_I ended with status %d "
+                "(relres %.3e)", sel[s], rc, ko[s].relres);
+      return rc;
+    }
+    P[sel[s]]->z_ready = true;
+  }
+  return RBFFD_OK;
+}
+
 int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
                   const rbffd_step_params *const *spv, double *deltas, rbffd_iter_stats *stats,
                   int *status) {
@@ -535,10 +600,10 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
   // hierarchies still being built are finished before anything is issued
   // (the iteration may be captured as a graph)
   for (int i = 0; i < m; ++i) RBFFD_TRY(amg_ready(P[i]));
-  for (int i = 0; i < m; ++i) RBFFD_TRY(compat_ready(P[i]));
   // a member with symmetry lines solves u~ and v~ as two single-RHS systems
   // (their rows differ there), so a launch may hold up to 2m systems
   RBFFD_TRY(S.reserve(ctx, 2 * m));
+  RBFFD_TRY(batch_compat(S, P, m));
   // replay the captured iteration when it was captured for exactly these
   // members, builds and step parameters.  A new set runs directly once and
   // is captured when it comes back, so one-off iterations (a rebuild before

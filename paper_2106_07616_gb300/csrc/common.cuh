@@ -1,6 +1,7 @@
 // common.cuh -- shared host/device helpers of the CUDA path (context,
 // errors, launch accounting, deterministic reductions, bounded grid barrier).
 #pragma once
+#include <cstddef>
 
 #include <cuda/atomic>
 #include <cuda_runtime.h>
@@ -19,6 +20,9 @@ struct rbffd_ctx {
   size_t budget = 0;  // 0 = no cap
   size_t used = 0;
   int64_t launches = 0;
+  // device-side waits of this context's launches: 2^wait_log2 cycles (0:
+  // the default 2^31), rbffd_ctx_set_wait_limit
+  int wait_log2 = 0;
   // pinned host scratch for small read-backs
   void *pinned = nullptr;
   size_t pinned_bytes = 0;
@@ -155,14 +159,27 @@ struct GridBarrier {
   unsigned int count;
   unsigned int gen;
   int err;
-  int pad;
+  // bound of every device-side wait of the launch: 2^wait_log2 clock cycles
+  // (0: the default 2^31, about a second); set per context
+  // (rbffd_ctx_set_wait_limit) when the barrier is reset before a launch
+  int wait_log2;
 };
+static_assert(offsetof(GridBarrier, wait_log2) == offsetof(GridBarrier, err) + sizeof(int),
+              "wait_cycles() reads the limit beside the error word");
+
+// The wait bound of a barrier, given its error word (the limit is the next
+// word of the same GridBarrier).
+__device__ __forceinline__ long long wait_cycles(const int *err) {
+  const int s = err[1];
+  return 1ll << (s > 0 ? s : 31);
+}
 
 // Grid-wide barrier for a cooperative launch: arrive with a release
 // fetch_add, the last arriver publishes the next generation with a release
 // store, the others poll it with acquire loads.  Every wait is bounded:
-// after ~2^31 clock cycles (about a second) the block records a timeout in
-// bar->err and goes on; callers test the return value and leave the kernel.
+// after 2^wait_log2 clock cycles (default 2^31, about a second) the block
+// records a timeout in bar->err and goes on; callers test the return value
+// and leave the kernel.
 __device__ __forceinline__ bool grid_sync(GridBarrier *bar, unsigned int nblocks,
                                           unsigned int &gen) {
   __shared__ int s_ok;
@@ -178,7 +195,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *bar, unsigned int nblocks
     } else {
       long long t0 = clock64();
       while (g.load(cuda::memory_order_acquire) == gen) {
-        if (clock64() - t0 > (1ll << 31)) {
+        if (clock64() - t0 > wait_cycles(&bar->err)) {
           er.store(1, cuda::memory_order_relaxed);
           break;
         }
@@ -190,5 +207,9 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *bar, unsigned int nblocks
   __syncthreads();
   return s_ok != 0;
 }
+
+// Zero the barriers bars[0..m) on the context's stream and give them the
+// context's wait limit (one kernel, so it can be captured in a graph).
+int reset_barriers(rbffd_ctx *ctx, GridBarrier *bars, int m);
 
 }  // namespace rbffd

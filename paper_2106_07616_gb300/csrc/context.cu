@@ -119,6 +119,36 @@ extern "C" void rbffd_ctx_destroy(rbffd_ctx *ctx) {
   if (ctx->refs == 0) ctx_free(ctx);
 }
 
+namespace rbffd {
+
+__global__ void k_reset_barriers(GridBarrier *bars, int m, int wait_log2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  bars[i].count = 0;
+  bars[i].gen = 0;
+  bars[i].err = 0;
+  bars[i].wait_log2 = wait_log2;
+}
+
+int reset_barriers(rbffd_ctx *ctx, GridBarrier *bars, int m) {
+  if (m < 1) return RBFFD_OK;
+  k_reset_barriers<<<(m + 127) / 128, 128, 0, ctx->stream>>>(bars, m, ctx->wait_log2);
+  return after_launch(ctx, "k_reset_barriers");
+}
+
+}  // namespace rbffd
+
+extern "C" int rbffd_ctx_set_wait_limit(rbffd_ctx *ctx, int32_t log2_cycles) {
+  return guarded([&]() -> int {
+    if (!ctx || log2_cycles < 0 || log2_cycles > 40) {
+      set_error("rbffd_ctx_set_wait_limit: log2_cycles must be 0 (default) or 1..40");
+      return RBFFD_EINVAL;
+    }
+    ctx->wait_log2 = log2_cycles;
+    return RBFFD_OK;
+  });
+}
+
 extern "C" int rbffd_ctx_profile(rbffd_ctx *ctx, int enable) {
   return guarded([&]() -> int {
     if (!ctx) return RBFFD_EINVAL;

@@ -444,7 +444,7 @@ int fgmres_launch(rbffd_ctx *ctx, int nblocks, const FgmresArgs &args) {
     set_error("fgmres_launch: bad arguments (blocks %d, m %d)", nblocks, args.m);
     return RBFFD_EINVAL;
   }
-  RBFFD_CK(cudaMemsetAsync(args.bar, 0, sizeof(GridBarrier), ctx->stream));
+  RBFFD_TRY(reset_barriers(ctx, args.bar, 1));
   RBFFD_CK(cudaMemsetAsync(args.flags, 0, sizeof(unsigned int) * nblocks, ctx->stream));
   void *kargs[] = {(void *)&args};
   cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_fgmres<FNT>, dim3(nblocks),

@@ -42,8 +42,22 @@ using kdev::MAXB;
 // (GB300 issues FP64 at a small fraction of its FP32 rate).
 struct KScalars {
   double bnorm, rho, rho_prev, alpha, omega, beta, relres, snorm;
+  double best;  // smallest relative residual of the solve so far
   int it, restarts, state, need_init, first, half, run;
+  int save;     // the iterate entering the next update is the best so far
+  int restore;  // restart from the best iterate (xb) instead of x
+  int blowups;  // restarts from the best iterate so far
 };
+
+// Residual growth over the best that counts as a blow-up, and how many
+// restarts from the best iterate a solve may make.  BiCGSTAB's residual is
+// erratic: healthy solves were seen to rise 1.8e4-fold over their start in
+// the first iterations and recover.  On the 200 x 200 cavity p' system with
+// Jacobi (condition ~3e6) a rounding-dependent loss of the recurrence took
+// the residual from below 1e-6 to 1e14 instead; a non-finite residual (a
+// near-breakdown's division) is treated the same way.
+constexpr double KRY_BLOWUP = 1e10;
+constexpr int KRY_MAX_BLOWUPS = 8;
 
 // One BiCGSTAB iteration as four grid exchanges:
 //   A: v = A p^,            partial (r^, v)                -> alpha
@@ -87,6 +101,8 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
       KScalars &c = ks[k];
       c.bnorm = c.rho = c.rho_prev = c.alpha = c.omega = 1.0;
       c.beta = c.relres = c.snorm = 0.0;
+      c.best = 1e300;
+      c.save = c.restore = c.blowups = 0;
       c.it = c.restarts = 0;
       c.state = KRY_RUNNING;
       c.need_init = 1;
@@ -101,13 +117,30 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
 
   for (;;) {
     // ---------------- (re)start: r = b - A x, r^ = r, p = r, p^ = r / d
-    bool ini[NR], any_init = false;
+    bool ini[NR], any_init = false, rst[NR], any_rst = false;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
       ini[k] = ks[k].state == KRY_RUNNING && ks[k].need_init;
       any_init |= ini[k];
+      rst[k] = ini[k] && ks[k].restore;
+      any_rst |= rst[k];
     }
     __syncthreads();
+    if (any_rst) {
+      // back to the best iterate, published before the restart's SpMV
+      for (int i = tid; i < n; i += stride) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+          if (rst[k]) A.x[k][i] = A.w[k].xb[i];
+      }
+      ok = kdev::exchange<0, double>(A.flags, err, epoch++, nullptr, nullptr, stot, lb, nb);
+      if (!ok) break;
+      if (leader) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+          if (rst[k]) ks[k].restore = 0;
+      }
+    }
     if (any_init) {
       double acc[2 * NR];
 #pragma unroll
@@ -156,6 +189,10 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
           c.relres = sqrt(rr) / c.bnorm;
           if (!(c.relres == c.relres)) { c.state = KRY_DIVERGED; continue; }
           if (c.relres <= A.tol) { c.state = KRY_OK; continue; }
+          if (c.relres < c.best) {
+            c.best = c.relres;
+            c.save = 1;
+          }
           c.rho = rr;  // (r^, r) with r^ = r
           if (c.rho == 0.0) c.state = KRY_NOCONV;
         }
@@ -295,9 +332,9 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
           const double rhs = tot[5 * k + 3], rht = tot[5 * k + 4];
           c.it++;
           c.snorm = sqrt(ss);
-          if (!(c.snorm == c.snorm)) {
-            c.state = KRY_DIVERGED;
-            c.run = 0;
+          if (!(c.snorm == c.snorm) || c.snorm > 1e300) {
+            c.run = 0;  // phase D leaves this system alone; it restarts or ends there
+            c.half = 2;
             continue;
           }
           if (c.snorm / c.bnorm <= A.tol) {
@@ -316,15 +353,23 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
 
     // ---------------- D: x and r updates, next direction, partial (r, r)
     {
-      bool half[NR];
+      bool half[NR], sav[NR];
       double alp[NR], omg[NR], bet[NR];
 #pragma unroll
+      bool bad[NR];
       for (int k = 0; k < NR; ++k) {
+        bad[k] = ks[k].half == 2;  // non-finite s: restart from the best iterate
         run[k] = ks[k].run != 0;
-        half[k] = ks[k].half != 0;
+        half[k] = ks[k].half == 1;
+        sav[k] = ks[k].save != 0;
         alp[k] = ks[k].alpha;
         omg[k] = ks[k].omega;
         bet[k] = ks[k].beta;
+      }
+      __syncthreads();
+      if (leader) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) ks[k].save = 0;
       }
       double acc[2 * NR];
 #pragma unroll
@@ -335,6 +380,8 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
         for (int k = 0; k < NR; ++k) {
           if (!run[k]) continue;
           const double phi = A.w[k].ph[i];
+          // x still holds the iterate whose residual was the best so far
+          if (sav[k]) A.w[k].xb[i] = A.x[k][i];
           if (half[k]) {
             A.x[k][i] = A.x[k][i] + alp[k] * phi;
           } else {
@@ -364,6 +411,22 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
           KScalars &c = ks[k];
+          // the recurrence has run away (or produced a non-finite value):
+          // restart from the best iterate, a bounded number of times
+          auto blowup = [&](int final_state) {
+            if (c.blowups >= KRY_MAX_BLOWUPS || c.it >= A.maxit) {
+              c.state = final_state;
+            } else {
+              c.blowups++;
+              c.restore = 1;
+              c.need_init = 1;
+            }
+          };
+          if (bad[k]) {
+            c.half = 0;
+            blowup(KRY_DIVERGED);
+            continue;
+          }
           if (!run[k]) continue;
           if (half[k]) {
             c.relres = c.snorm / c.bnorm;
@@ -372,8 +435,18 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
           }
           const double rn = sqrt(tot[k]);
           c.relres = rn / c.bnorm;
-          if (!(rn == rn)) { c.state = KRY_DIVERGED; continue; }
+          if (!(rn == rn) || rn > 1e300) {
+            blowup(KRY_DIVERGED);
+            continue;
+          }
           if (c.relres <= A.tol) { c.state = KRY_OK; continue; }
+          if (c.relres < c.best) {
+            c.best = c.relres;
+            c.save = 1;  // copied to xb when the next update reads x
+          } else if (c.relres > KRY_BLOWUP * c.best) {
+            blowup(KRY_NOCONV);
+            continue;
+          }
           if (c.omega == 0.0 || c.rho == 0.0) {
             // breakdown: restart from the current x (at most 3 times)
             if (c.restarts >= 3) {
@@ -404,7 +477,7 @@ __device__ __forceinline__ void bicgstab_body(const KrylovArgs &A, const int lb,
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
       A.out[k].iters = ks[k].it;
-      A.out[k].restarts = ks[k].restarts;
+      A.out[k].restarts = ks[k].restarts + ks[k].blowups;
       A.out[k].status = ok ? ks[k].state : KRY_TIMEOUT;
       A.out[k].relres = ks[k].relres;
     }
@@ -505,7 +578,7 @@ int krylov_launch(rbffd_ctx *ctx, int nr, int nblocks, const KrylovArgs &args) {
     set_error("krylov_launch: %d blocks exceed the limit %d", nblocks, MAXB);
     return RBFFD_EINVAL;
   }
-  RBFFD_CK(cudaMemsetAsync(args.bar, 0, sizeof(GridBarrier), ctx->stream));
+  RBFFD_TRY(reset_barriers(ctx, args.bar, 1));
   RBFFD_CK(cudaMemsetAsync(args.flags, 0, sizeof(unsigned int) * nblocks, ctx->stream));
   void *kargs[] = {(void *)&args};
   cudaError_t e;

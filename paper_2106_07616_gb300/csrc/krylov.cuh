@@ -9,6 +9,7 @@ enum { KRY_RUNNING = 1, KRY_OK = 0, KRY_NOCONV = -4, KRY_DIVERGED = -5, KRY_TIME
 
 struct KrylovVecs {
   double *r, *rh, *p, *v, *ph, *s, *sh, *t;
+  double *xb;  // the iterate with the smallest residual so far (restart point)
 };
 
 struct KrylovOut {

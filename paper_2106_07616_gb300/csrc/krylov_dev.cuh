@@ -174,7 +174,7 @@ __device__ __forceinline__ bool exchange(unsigned int *flags, int *err, unsigned
         ok = false;
         break;
       }
-      if (clock64() - t0 > (1ll << 31)) {
+      if (clock64() - t0 > wait_cycles(err)) {
         ok = false;
         atomicExch(err, 1);
         break;

@@ -587,7 +587,7 @@ int krylov_ir_launch(rbffd_ctx *ctx, int nr, int nblocks, const MixedArgs &args)
     set_error("krylov_ir_launch: %d blocks not co-resident", nblocks);
     return RBFFD_EINVAL;
   }
-  RBFFD_CK(cudaMemsetAsync(args.bar, 0, sizeof(GridBarrier), ctx->stream));
+  RBFFD_TRY(reset_barriers(ctx, args.bar, 1));
   RBFFD_CK(cudaMemsetAsync(args.flags, 0, sizeof(unsigned int) * nblocks, ctx->stream));
   void *kargs[] = {(void *)&args};
   const void *fn;

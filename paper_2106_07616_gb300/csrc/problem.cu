@@ -500,6 +500,20 @@ rbffd_step_params step_from(const rbffd_solve_params *s) {
 
 }  // namespace
 
+double rbffd::compat_tol(const rbffd_problem *P) {
+  // multigrid paths: flexible GMRES's floor for z sits near 1e-10 (see
+  // compat_ready); Jacobi BiCGSTAB aims at the parity tolerance and stops
+  // at its own floor (FP32-inner p' solves of small problems were seen to
+  // stall with a 1e-9 z and converge with the 3.4e-10 one)
+  return (P->amg || P->amgf) ? 1e-9 : 1e-12;
+}
+
+int rbffd::compat_maxit(const rbffd_problem *P) {
+  // a multigrid-preconditioned solve that has not reached the target by then
+  // sits at its accuracy floor; Jacobi BiCGSTAB needs thousands of steps
+  return (P->amg || P->amgf) ? 1000 : 50000;
+}
+
 // z = M^{-1} e_I of the compatible p' (ops.cu: compat_shift), solved once
 // per build with the problem's p' preconditioner in FP64 arithmetic
 // (flexible GMRES keeps its FP32 Arnoldi process inside FP64 restarts; a
@@ -507,21 +521,27 @@ rbffd_step_params step_from(const rbffd_solve_params *s) {
 // is far from compatible, so z carries the pin's large response and its
 // solve can stall above the 1e-12 parity tolerance, at the floor
 // eps kappa |M| |z| / |e_I| of a solve (3.4e-10 with Jacobi BiCGSTAB on the
-// 200^2 cavity, kappa ~ 3e6): a result whose FP64 relative residual reached
-// 1e-9 is kept.  The error of z enters p' only through c z, where c is the
-// small incompatible fraction of the source, so it moves p' by about
-// 1e-9 of the pin's response to that fraction.
+// 200^2 cavity, kappa ~ 3e6; flexible GMRES's floor, which grows with
+// |z|, sat near 1e-10 there and a 1e-10 target ran the solve to a
+// 3000-step cap on every build): with a multigrid preconditioner the
+// solve aims at 1e-9 (the accuracy the parity tests hold the fields to 1e-8
+// with), with Jacobi at 1e-12 (compat_tol), with a step cap by
+// preconditioner (compat_maxit); a result that reached 1e-9
+// (compat_accept) is kept.  The error of z enters p' only through c z,
+// where c is the incompatible fraction of the source (small after
+// k_center), so it moves p' by about 1e-9 of the pin's response to that
+// fraction.
 int rbffd::compat_ready(rbffd_problem *P) {
   if (!P->compat || P->z_ready) return RBFFD_OK;
   RBFFD_TRY(amg_ready(P));
   // the right-hand side e_I goes to pcs, scratch until k_pressure writes it:
   // bp may already hold the divergence of the iteration being issued
   RBFFD_TRY(ops_interior_ones(P, P->pcs, P->zc));
-  RBFFD_TRY(issue_pcorr(P, 1e-12, 20000, 0.0, 0, P->pcs, P->zc, true));
+  RBFFD_TRY(issue_pcorr(P, compat_tol(P), compat_maxit(P), 0.0, 0, P->pcs, P->zc, true));
   Readback r;
   RBFFD_TRY(read_back(P, &r));
   int rc = krylov_status_code(r.kout[2].status);
-  if (rc == RBFFD_ENOCONV && r.kout[2].relres <= 1e-9) rc = RBFFD_OK;
+  if (rc == RBFFD_ENOCONV && r.kout[2].relres <= compat_accept()) rc = RBFFD_OK;
   if (rc != RBFFD_OK) {
     set_error("compatible p': the solve of M z = e_I ended with status %d (relres %.3e)", rc,
               r.kout[2].relres);
@@ -579,8 +599,8 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
            o_md2 = c.take<double>(P->ldn);
     size_t o_f[16];
     for (int k = 0; k < 16; ++k) o_f[k] = c.take<double>(n);
-    size_t o_kv[16];
-    for (int k = 0; k < 16; ++k) o_kv[k] = c.take<double>(n);
+    size_t o_kv[18];
+    for (int k = 0; k < 18; ++k) o_kv[k] = c.take<double>(n);
     size_t o_part = c.take<double>(npart), o_rpart = c.take<double>(RESID_SLOTS * (size_t)P->rblocks);
     size_t o_bar = c.take<GridBarrier>(1);
     size_t o_flags = c.take<unsigned int>(256);
@@ -634,9 +654,9 @@ extern "C" int rbffd_problem_create(rbffd_ctx *ctx, const rbffd_problem_desc *d,
                       &P->ut, &P->vt, &P->pc, &P->bu, &P->bv, &P->bp, &P->zc, &P->pcs};
     for (int k = 0; k < 16; ++k) *f[k] = (double *)(b + o_f[k]);
     for (int r = 0; r < 2; ++r) {
-      double **w[8] = {&P->kv[r].r, &P->kv[r].rh, &P->kv[r].p, &P->kv[r].v,
-                       &P->kv[r].ph, &P->kv[r].s, &P->kv[r].sh, &P->kv[r].t};
-      for (int k = 0; k < 8; ++k) *w[k] = (double *)(b + o_kv[r * 8 + k]);
+      double **w[9] = {&P->kv[r].r,  &P->kv[r].rh, &P->kv[r].p, &P->kv[r].v, &P->kv[r].ph,
+                       &P->kv[r].s,  &P->kv[r].sh, &P->kv[r].t, &P->kv[r].xb};
+      for (int k = 0; k < 9; ++k) *w[k] = (double *)(b + o_kv[r * 9 + k]);
     }
     P->part = (double *)(b + o_part);
     P->rpart = (double *)(b + o_rpart);

@@ -117,6 +117,10 @@ int amg_ready(rbffd_problem *P);
 // problems only; a no-op otherwise or when done).  Synchronises the stream:
 // call it before any graph capture.
 int compat_ready(rbffd_problem *P);
+// tolerance, step cap and acceptance of the z solve (problem.cu)
+double compat_tol(const rbffd_problem *P);
+constexpr double compat_accept() { return 1e-9; }
+int compat_maxit(const rbffd_problem *P);
 // partial-sum slots of the steady residual reduction (ops.cu: k_resid)
 constexpr int RESID_SLOTS = 9;
 }  // namespace rbffd

@@ -4,13 +4,24 @@
 // RBF_interp_mat_vec_L_solve).
 //
 // The matrix build uses explicit round-to-nearest intrinsics (no fused
-// multiply-add), as the oracle does.  The elimination and the back
-// substitution -- the O(N^3) part, and on GB300 bound by the FP64 pipe --
-// use one fused multiply-add per update instead of a product and a
-// difference: half the FP64 instructions.  The weights then differ from the
-// oracle's unfused elimination by rounding only (a different elimination
-// order, LAPACK's, moves the 200 x 200 cavity weights by at most 4e-13
-// relative), well inside the 1e-10 the weights are held to.
+// multiply-add), as the oracle does.  On GB300 the kernel is bound by the
+// FP64 pipe (about 2 FMA lanes per clock per SM), so every FP64 instruction
+// counts and the kernel spends them only on the arithmetic itself:
+//   - the elimination and the back substitution use one fused multiply-add
+//     per update instead of a product and a difference;
+//   - the trailing update of step k deals the (N-k-1) x (W-k-1) elements
+//     over the 32 lanes in row-major order, so every FP64 instruction of
+//     the warp carries 32 useful updates (lanes that owned whole columns
+//     left 35% of them idle at N = 45);
+//   - the multipliers use one reciprocal of the pivot per step, and the
+//     scalings by 1/h and 1/h^2 one reciprocal each, instead of a division
+//     per element (an FP64 division is a sequence of FP64 instructions);
+//   - Phi is symmetric: each r^3 (and its square root) is computed once for
+//     the upper triangle and stored twice.
+// The weights then differ from the oracle's unfused, dividing elimination
+// by rounding only (a different elimination order, LAPACK's, moves the
+// 200 x 200 cavity weights by at most 4e-13 relative), well inside the
+// 1e-10 the weights are held to.
 #include "abi_guard.cuh"
 #include "common.cuh"
 #include "weights.cuh"
@@ -72,18 +83,32 @@ __global__ void k_weights(int n, const double *__restrict__ x, const double *__r
     for (int o = 16; o > 0; o >>= 1) d2m = fmax(d2m, __shfl_xor_sync(0xffffffffu, d2m, o));
     double h = __dsqrt_rn(d2m);
     if (h == 0.0) h = 1.0;
+    const double hinv = __drcp_rn(h);
     for (int a = lane; a < q; a += 32) {
       int j = cl[a];
-      xi[a] = __ddiv_rn(pdiff(x[j], xc, Lx), h);
-      eta[a] = __ddiv_rn(pdiff(y[j], yc, Ly), h);
+      xi[a] = __dmul_rn(pdiff(x[j], xc, Lx), hinv);
+      eta[a] = __dmul_rn(pdiff(y[j], yc, Ly), hinv);
     }
     __syncwarp();
-    // Phi block: r^3
-    for (int e = lane; e < q * q; e += 32) {
-      int a = e / q, b = e - a * q;
-      double dx = __dsub_rn(xi[a], xi[b]), dy = __dsub_rn(eta[a], eta[b]);
-      double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-      M[a * LD + b] = __dmul_rn(__dmul_rn(r, r), r);
+    // Phi block: r^3, symmetric with a zero diagonal; the q(q-1)/2 pairs
+    // a < b of the upper triangle are dealt over the lanes in row-major
+    // order (row a holds q-1-a of them)
+    for (int a = lane; a < q; a += 32) M[a * LD + a] = 0.0;
+    {
+      // pair number e -> (a, b): past the end of row a (b >= q) it goes on
+      // at b - q positions into row a + 1, whose first pair is (a+1, a+2)
+      const int P = q * (q - 1) / 2;
+      int a = 0, b = 1 + lane;
+      while (a < q - 1 && b >= q) { b += a + 2 - q; ++a; }
+      for (int e = lane; e < P; e += 32) {
+        double dx = __dsub_rn(xi[a], xi[b]), dy = __dsub_rn(eta[a], eta[b]);
+        double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+        const double r3 = __dmul_rn(__dmul_rn(r, r), r);
+        M[a * LD + b] = r3;
+        M[b * LD + a] = r3;
+        b += 32;
+        while (a < q - 1 && b >= q) { b += a + 2 - q; ++a; }
+      }
     }
     // P and P^T blocks
     for (int e = lane; e < q * m; e += 32) {
@@ -116,19 +141,24 @@ __global__ void k_weights(int n, const double *__restrict__ x, const double *__r
     // LU with partial pivoting; the right-hand sides ride along
     bool singular = false;
     for (int k = 0; k < N; ++k) {
-      double best = -1.0;
+      // pivot search on the bit patterns of |a|: for finite doubles with the
+      // sign bit cleared, unsigned 64-bit order is the order of the values,
+      // so this picks exactly the row an FP64 comparison would (ties to the
+      // lowest row) while keeping the compares off the FP64 pipe
+      unsigned long long best = 0ull;
       int piv = N;
       for (int r = k + lane; r < N; r += 32) {
-        double a = fabs(M[r * LD + k]);
-        if (a > best) { best = a; piv = r; }
+        const unsigned long long a =
+            (unsigned long long)__double_as_longlong(M[r * LD + k]) & 0x7fffffffffffffffull;
+        if (piv == N || a > best) { best = a; piv = r; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int op = __shfl_xor_sync(0xffffffffu, piv, o);
-        if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, piv, o);
+        if (op < N && (piv == N || ob > best || (ob == best && op < piv))) { best = ob; piv = op; }
       }
-      if (best == 0.0) { singular = true; break; }
+      if (best == 0ull) { singular = true; break; }
       if (piv != k) {
         for (int c = k + lane; c < W; c += 32) {
           double t = M[k * LD + c];
@@ -137,13 +167,27 @@ __global__ void k_weights(int n, const double *__restrict__ x, const double *__r
         }
         __syncwarp();
       }
-      const double akk = M[k * LD + k];
-      for (int r = k + 1 + lane; r < N; r += 32) M[r * LD + k] = __ddiv_rn(M[r * LD + k], akk);
+      const double kinv = __drcp_rn(M[k * LD + k]);
+      for (int r = k + 1 + lane; r < N; r += 32) M[r * LD + k] = __dmul_rn(M[r * LD + k], kinv);
       __syncwarp();
-      for (int c = k + 1 + lane; c < W; c += 32) {
-        const double akc = M[k * LD + c];
-        for (int r = k + 1; r < N; ++r)
-          M[r * LD + c] = __fma_rn(-M[r * LD + k], akc, M[r * LD + c]);
+      {
+        // trailing update, element e = (r - k - 1) * Cc + (c - k - 1) on lane e % 32
+        const int Cc = W - k - 1, E = (N - k - 1) * Cc;
+        int r = k + 1 + lane / Cc, c = k + 1 + lane % Cc;
+        int e = lane;
+        // two elements per trip: their loads go out before either update
+        for (; e + 32 < E; e += 64) {
+          int r2 = r, c2 = c + 32;
+          while (c2 >= W) { c2 -= Cc; ++r2; }
+          const double l1 = M[r * LD + k], u1 = M[k * LD + c], a1 = M[r * LD + c];
+          const double l2 = M[r2 * LD + k], u2 = M[k * LD + c2], a2 = M[r2 * LD + c2];
+          M[r * LD + c] = __fma_rn(-l1, u1, a1);
+          M[r2 * LD + c2] = __fma_rn(-l2, u2, a2);
+          r = r2;
+          c = c2 + 32;
+          while (c >= W) { c -= Cc; ++r; }
+        }
+        if (e < E) M[r * LD + c] = __fma_rn(-M[r * LD + k], M[k * LD + c], M[r * LD + c]);
       }
       __syncwarp();
     }
@@ -168,12 +212,12 @@ __global__ void k_weights(int n, const double *__restrict__ x, const double *__r
       }
       __syncwarp();
     }
-    const double h2 = __dmul_rn(h, h);
+    const double h2inv = __drcp_rn(__dmul_rn(h, h));
     for (int a = lane; a < q; a += 32) {
       int64_t o = (int64_t)i * q + a;
-      if (wx) wx[o] = __ddiv_rn(M[a * LD + N + 0], h);
-      if (wy) wy[o] = __ddiv_rn(M[a * LD + N + 1], h);
-      if (wl) wl[o] = __ddiv_rn(M[a * LD + N + 2], h2);
+      if (wx) wx[o] = __dmul_rn(M[a * LD + N + 0], hinv);
+      if (wy) wy[o] = __dmul_rn(M[a * LD + N + 1], hinv);
+      if (wl) wl[o] = __dmul_rn(M[a * LD + N + 2], h2inv);
     }
     __syncwarp();
   }
@@ -183,8 +227,11 @@ int weights_config(int q, int degree, int *wpb, size_t *smem) {
   int m = (degree + 1) * (degree + 2) / 2;
   int N = q + m, LD = (N + 3) | 1;
   size_t per = (size_t)(N * LD + 2 * q) * sizeof(double);
-  int w = (int)((200 * 1024) / per);
-  if (w > 8) w = 8;
+  // as many warps as shared memory holds, up to 12 (N = 45: 12 x 18 KB):
+  // the FP64 pipe needs several warps per scheduler to hide the shared-
+  // memory latency in front of each update
+  int w = (int)((224 * 1024) / per);
+  if (w > 12) w = 12;
   if (w < 1) return RBFFD_EINVAL;
   *wpb = w;
   *smem = per * w;

@@ -126,6 +126,7 @@ def load(path: str = LIB_PATH):
         "solve_unsteady": (C.c_int, [vp, C.POINTER(SolveParams), i32, STEP_CB, vp,
                                      C.POINTER(SolveStats)]),
         "rbffd_steady_residual": (C.c_int, [vp, C.POINTER(dbl)]),
+        "rbffd_ctx_set_wait_limit": (C.c_int, [vp, i32]),
         "rbffd_get_field": (C.c_int, [vp, i32, vp]),
         "rbffd_set_field": (C.c_int, [vp, i32, vp]),
         "rbffd_get_operators": (C.c_int, [vp, vp, vp, vp, vp, vp]),
@@ -175,6 +176,12 @@ class Context:
         _check(L.rbffd_ctx_create(C.byref(h), device, hbm_budget, s), "rbffd_ctx_create")
         self.h = h
         self.device = device
+
+    def set_wait_limit(self, log2_cycles: int):
+        """Bound of the device-side waits of later launches: 2^log2_cycles
+        cycles, 0 for the default (rbffd_ctx_set_wait_limit)."""
+        _check(load().rbffd_ctx_set_wait_limit(self.h, int(log2_cycles)),
+               "rbffd_ctx_set_wait_limit")
 
     def close(self):
         if getattr(self, "h", None) is not None:

@@ -47,7 +47,7 @@ def test_stencils_with_boundaries_bit_exact(make):
     assert np.array_equal(gpu_knn(fp.x, fp.y, fp.q, fp.tag), oracle.knn(fp.x, fp.y, fp.q, fp.tag))
 
 
-@pytest.mark.parametrize("degree,q", [(1, 6), (2, 12), (3, 20), (4, 30), (5, 42)])
+@pytest.mark.parametrize("degree,q", [(1, 6), (2, 12), (3, 20), (4, 30), (5, 42), (6, 56)])
 def test_weights_parity(degree, q):
     x, y = clouds.jittered_grid(30, seed=degree)
     idx = oracle.knn(x, y, q)

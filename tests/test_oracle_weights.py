@@ -36,7 +36,7 @@ def lop(a, b, x, y, op):
     return t
 
 
-@pytest.mark.parametrize("degree,q", [(1, 6), (2, 12), (3, 20), (4, 30), (5, 42)])
+@pytest.mark.parametrize("degree,q", [(1, 6), (2, 12), (3, 20), (4, 30), (5, 42), (6, 56)])
 def test_polynomial_reproduction(degree, q):
     """sum_j w_j P(x_j) = L P(x_c) for every appended monomial: the
     constraint rows of Eq. (RBF_interp_mat_vec) make this exact."""
