@@ -101,7 +101,8 @@ int BatchScratch::reserve(rbffd_ctx *c, int members) {
   for (int k = 0; k < NSLOT; ++k) {
     off_sys[k] = take(std::max({sizeof(KrylovArgs), sizeof(FgmresArgs), sizeof(MixedArgs)}) * cap);
     off_cta_sys[k] = take(sizeof(int) * maxc);
-    off_cta_first[k] = take(sizeof(int) * cap);
+    team_words = 4 * maxc + cap;
+    off_cta_first[k] = take(sizeof(int) * team_words);
     off_flags[k] = take(sizeof(unsigned int) * maxc);
     off_bars[k] = take(sizeof(GridBarrier) * cap);
   }
@@ -115,29 +116,120 @@ int BatchScratch::reserve(rbffd_ctx *c, int members) {
   return RBFFD_OK;
 }
 
-// CTAs of each system of a batched launch of at most cmax co-resident CTAs:
-// one each, the rest in proportion to the rows, capped by the system's
-// partial-sum capacity cap[i], by 8 threads per row, and by the kdev::MAXB
-// CTAs the partial sums of one system are laid out for.
-static std::vector<int> split_ctas(const std::vector<int> &rows, const std::vector<int> &cap,
-                                   int cmax) {
-  const int m = (int)rows.size();
-  std::vector<int> nb(m, 1);
-  const long long total = std::accumulate(rows.begin(), rows.end(), 0LL);
-  const int left = cmax - m;
-  for (int i = 0; i < m && total > 0; ++i) {
-    const int extra = (int)((double)left * rows[i] / (double)total);
-    int c = std::min(cap[i], (int)((rows[i] * 8LL + KB_NT - 1) / KB_NT));
-    c = std::min(c, kdev::MAXB);
-    nb[i] = std::max(1, std::min(1 + extra, c));
+// Persistent work list of a batched launch: the CTAs form nteams teams of
+// `team` consecutive CTAs; every system goes to one team, and a team solves
+// its systems one after another (the kernels loop over the team's list).
+// The host plans it from an estimate of each system's work (its rows times
+// the iterations its last solve took, 1 before any):
+//   - the team size makes the largest system fit a team's average share of
+//     the work (team >= cmax * wmax / total), so no single system outlasts
+//     the rest, capped by what every system's partial sums hold (cap[i]) and
+//     by 8 threads per row of the smallest system's rows per CTA;
+//   - teams = cmax / team (at most one per system, and then larger teams);
+//   - largest work first, each system to the least-loaded team (LPT).
+// Tables (device copies of the host arrays): cta_team[c] = the team of CTA
+// c; team info[4 t ..] = first CTA, CTAs, list begin, list end, the list
+// being positions in the same array (after the 4 * nteams info words)
+// holding system indices.  Returns the CTAs launched; nb[i] = CTAs of
+// system i's team.
+struct TeamPlan {
+  int nctas = 0;
+  std::vector<int> cta_team, info_and_list, nb;
+};
+
+static TeamPlan plan_teams(const std::vector<double> &work, const std::vector<int> &cap,
+                           const std::vector<int> &rows, int cmax) {
+  const int m = (int)work.size();
+  TeamPlan T;
+  double total = 0.0, wmax = 0.0;
+  int capmin = kdev::MAXB, rmin = 1 << 30;
+  for (int i = 0; i < m; ++i) {
+    total += work[i];
+    wmax = std::max(wmax, work[i]);
+    capmin = std::min(capmin, cap[i]);
+    rmin = std::min(rmin, rows[i]);
   }
-  return nb;
+  // CTAs beyond 8 threads per row of the smallest system only add waits
+  const int rowcap = std::max(1, (int)((rmin * 8LL + KB_NT - 1) / KB_NT));
+  const int tmax = std::max(1, std::min(capmin, kdev::MAXB));
+  int team = total > 0 ? (int)std::ceil(cmax * wmax / total) : 1;
+  team = std::max(1, std::min(team, tmax));
+  int nteams = std::max(1, std::min(cmax / team, m));
+  // fewer teams than the grid holds: spread the CTAs over them
+  team = std::max(1, std::min({cmax / nteams, tmax, std::max(team, rowcap)}));
+  T.nctas = nteams * team;
+  std::vector<int> order(m);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return work[a] > work[b]; });
+  std::vector<double> load(nteams, 0.0);
+  std::vector<std::vector<int>> lists(nteams);
+  for (int i : order) {
+    int best = 0;
+    for (int t = 1; t < nteams; ++t)
+      if (load[t] < load[best]) best = t;
+    load[best] += work[i];
+    lists[best].push_back(i);
+  }
+  T.cta_team.resize(T.nctas);
+  for (int c = 0; c < T.nctas; ++c) T.cta_team[c] = c / team;
+  T.info_and_list.assign(4 * nteams, 0);
+  T.nb.assign(m, team);
+  for (int t = 0; t < nteams; ++t) {
+    T.info_and_list[4 * t] = t * team;
+    T.info_and_list[4 * t + 1] = team;
+    T.info_and_list[4 * t + 2] = (int)T.info_and_list.size();
+    for (int i : lists[t]) T.info_and_list.push_back(i);
+    T.info_and_list[4 * t + 3] = (int)T.info_and_list.size();
+  }
+  return T;
+}
+
+// Work of one of a member's solves for the work-list plan: its rows times
+// the iterations its last solve of that kind took (1 before any).
+static double work_of(const rbffd_problem *Q, int kind) {
+  return (double)Q->n * (double)std::max(1, Q->it_hist[kind]);
+}
+
+// Copy a launch's system arguments (m of `argbytes` each, already in the
+// pinned host slot) and its work-list tables to the device, stream-ordered
+// (captured as copies of the pinned host tables).
+static int put_tables(BatchScratch &S, int slot, const TeamPlan &T, int m, size_t argbytes) {
+  char *hb = (char *)S.hmem;
+  char *db = (char *)S.dmem;
+  if ((int)T.cta_team.size() > S.maxc || (int)T.info_and_list.size() > S.team_words) {
+    set_error("batch: work-list tables exceed their slots");
+    return RBFFD_EINVAL;
+  }
+  memcpy(hb + S.off_cta_sys[slot], T.cta_team.data(), sizeof(int) * T.cta_team.size());
+  memcpy(hb + S.off_cta_first[slot], T.info_and_list.data(),
+         sizeof(int) * T.info_and_list.size());
+  RBFFD_CK(cudaMemcpyAsync(db + S.off_sys[slot], hb + S.off_sys[slot], argbytes * m,
+                           cudaMemcpyHostToDevice, S.ctx->stream));
+  RBFFD_CK(cudaMemcpyAsync(db + S.off_cta_sys[slot], hb + S.off_cta_sys[slot],
+                           sizeof(int) * T.cta_team.size(), cudaMemcpyHostToDevice,
+                           S.ctx->stream));
+  RBFFD_CK(cudaMemcpyAsync(db + S.off_cta_first[slot], hb + S.off_cta_first[slot],
+                           sizeof(int) * T.info_and_list.size(), cudaMemcpyHostToDevice,
+                           S.ctx->stream));
+  return RBFFD_OK;
+}
+
+// Threads per row: cover a CTA's rows (kdev::cta_rows) in one pass.
+static int tpr_for(int n, int nb) {
+  const long long R = (n + (long long)nb - 1) / nb;
+  int T = 1;
+  for (int t = 2; t <= 8; ++t)
+    if ((long long)(32 / t) * (KB_NT / 32) >= R) T = t;
+  return T;
 }
 
 // One batched Krylov launch for the systems args[0..m) (args filled except
-// nblocks, tpr, flags and bar, which are set here), with table slot `slot`.
+// nblocks, tpr, flags and bar, which are set here), with table slot `slot`,
+// planned as a persistent work list from the systems' work (plan_teams).
 static int launch_krylov(BatchScratch &S, int slot, int nr, std::vector<KrylovArgs> &args,
-                         const std::vector<int> &rows, bool amg = false) {
+                         const std::vector<double> &work, const std::vector<int> &rows,
+                         bool amg = false) {
   rbffd_ctx *ctx = S.ctx;
   const int m = (int)args.size();
   const int cmax = krylov_batch_max_ctas(ctx, nr);
@@ -145,43 +237,26 @@ static int launch_krylov(BatchScratch &S, int slot, int nr, std::vector<KrylovAr
     set_error("batch: %d members exceed the %d co-resident CTAs of one launch", m, cmax);
     return RBFFD_EINVAL;
   }
-  // one CTA each, the rest in proportion to the rows, each capped by what
-  // its partial-sum buffers hold and by 8 threads per row
   std::vector<int> cap(m);
   for (int i = 0; i < m; ++i) cap[i] = args[i].nblocks;
-  const std::vector<int> nb = split_ctas(rows, cap, cmax);
-  const int nctas = std::accumulate(nb.begin(), nb.end(), 0);
+  const TeamPlan T = plan_teams(work, cap, rows, cmax);
   char *hb = (char *)S.hmem;
   char *db = (char *)S.dmem;
   KrylovArgs *hsys = (KrylovArgs *)(hb + S.off_sys[slot]);
-  int *hcs = (int *)(hb + S.off_cta_sys[slot]);
-  int *hcf = (int *)(hb + S.off_cta_first[slot]);
   unsigned int *dflags = (unsigned int *)(db + S.off_flags[slot]);
   GridBarrier *dbars = (GridBarrier *)(db + S.off_bars[slot]);
-  int c = 0;
   for (int i = 0; i < m; ++i) {
     KrylovArgs a = args[i];
-    a.nblocks = nb[i];
-    // threads per row: cover a CTA's rows (kdev::cta_rows) in one pass
-    const long long R = (a.n + (long long)nb[i] - 1) / nb[i];
-    int T = 1;
-    for (int t = 2; t <= 8; ++t)
-      if ((long long)(32 / t) * (KB_NT / 32) >= R) T = t;
-    a.tpr = T;
-    a.flags = dflags + c;
+    a.nblocks = T.nb[i];
+    a.tpr = tpr_for(a.n, a.nblocks);
+    a.flags = dflags + i;  // one arrival counter per system
     a.bar = dbars + i;
     hsys[i] = a;
-    hcf[i] = c;
-    for (int k = 0; k < nb[i]; ++k) hcs[c + k] = i;
-    c += nb[i];
   }
-  // the slot's host tables are contiguous from off_sys to off_flags
-  RBFFD_CK(cudaMemcpyAsync(db + S.off_sys[slot], hb + S.off_sys[slot],
-                           S.off_flags[slot] - S.off_sys[slot], cudaMemcpyHostToDevice,
-                           ctx->stream));
-  RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * nctas, ctx->stream));
+  RBFFD_TRY(put_tables(S, slot, T, m, sizeof(KrylovArgs)));
+  RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * m, ctx->stream));
   RBFFD_TRY(reset_barriers(ctx, dbars, m));
-  RBFFD_TRY(krylov_batch_launch(ctx, nr, nctas, (const KrylovArgs *)(db + S.off_sys[slot]),
+  RBFFD_TRY(krylov_batch_launch(ctx, nr, T.nctas, (const KrylovArgs *)(db + S.off_sys[slot]),
                                 (const int *)(db + S.off_cta_sys[slot]),
                                 (const int *)(db + S.off_cta_first[slot]), amg));
   return RBFFD_OK;
@@ -189,9 +264,11 @@ static int launch_krylov(BatchScratch &S, int slot, int nr, std::vector<KrylovAr
 
 // One batched mixed-precision launch (FP32 or float-float BiCGSTAB inside
 // FP64 refinement) for the momentum systems args[0..m) of one inner
-// arithmetic, with table slot `slot`: CTAs split as in launch_krylov.
+// arithmetic, with table slot `slot`: a persistent work list as in
+// launch_krylov.
 static int launch_mixed(BatchScratch &S, int slot, int nr, int inner,
-                        std::vector<MixedArgs> &args, const std::vector<int> &rows) {
+                        std::vector<MixedArgs> &args, const std::vector<double> &work,
+                        const std::vector<int> &rows) {
   rbffd_ctx *ctx = S.ctx;
   const int m = (int)args.size();
   const int cmax = krylov_ir_batch_max_ctas(ctx, nr, inner);
@@ -201,47 +278,33 @@ static int launch_mixed(BatchScratch &S, int slot, int nr, int inner,
   }
   std::vector<int> cap(m);
   for (int i = 0; i < m; ++i) cap[i] = args[i].nblocks;
-  const std::vector<int> nb = split_ctas(rows, cap, cmax);
-  const int nctas = std::accumulate(nb.begin(), nb.end(), 0);
+  const TeamPlan T = plan_teams(work, cap, rows, cmax);
   char *hb = (char *)S.hmem;
   char *db = (char *)S.dmem;
   MixedArgs *hsys = (MixedArgs *)(hb + S.off_sys[slot]);
-  int *hcs = (int *)(hb + S.off_cta_sys[slot]);
-  int *hcf = (int *)(hb + S.off_cta_first[slot]);
   unsigned int *dflags = (unsigned int *)(db + S.off_flags[slot]);
   GridBarrier *dbars = (GridBarrier *)(db + S.off_bars[slot]);
-  int c = 0;
   for (int i = 0; i < m; ++i) {
     MixedArgs a = args[i];
-    a.nblocks = nb[i];
-    // threads per row: cover a CTA's rows (kdev::cta_rows) in one pass
-    const long long R = (a.n + (long long)nb[i] - 1) / nb[i];
-    int T = 1;
-    for (int t = 2; t <= 8; ++t)
-      if ((long long)(32 / t) * (KB_NT / 32) >= R) T = t;
-    a.tpr = T;
-    a.flags = dflags + c;
+    a.nblocks = T.nb[i];
+    a.tpr = tpr_for(a.n, a.nblocks);
+    a.flags = dflags + i;
     a.bar = dbars + i;
     hsys[i] = a;
-    hcf[i] = c;
-    for (int k = 0; k < nb[i]; ++k) hcs[c + k] = i;
-    c += nb[i];
   }
-  RBFFD_CK(cudaMemcpyAsync(db + S.off_sys[slot], hb + S.off_sys[slot],
-                           S.off_flags[slot] - S.off_sys[slot], cudaMemcpyHostToDevice,
-                           ctx->stream));
-  RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * nctas, ctx->stream));
+  RBFFD_TRY(put_tables(S, slot, T, m, sizeof(MixedArgs)));
+  RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * m, ctx->stream));
   RBFFD_TRY(reset_barriers(ctx, dbars, m));
-  return krylov_ir_batch_launch(ctx, nr, inner, nctas, (const MixedArgs *)(db + S.off_sys[slot]),
+  return krylov_ir_batch_launch(ctx, nr, inner, T.nctas, (const MixedArgs *)(db + S.off_sys[slot]),
                                 (const int *)(db + S.off_cta_sys[slot]),
                                 (const int *)(db + S.off_cta_first[slot]));
 }
 
 // One batched flexible-GMRES launch for the pressure-correction systems
 // args[0..m) (filled except nblocks, flags and bar), with table slot `slot`:
-// CTAs split as in launch_krylov.
+// a persistent work list as in launch_krylov.
 static int launch_fgmres(BatchScratch &S, int slot, std::vector<FgmresArgs> &args,
-                         const std::vector<int> &rows) {
+                         const std::vector<double> &work, const std::vector<int> &rows) {
   rbffd_ctx *ctx = S.ctx;
   const int m = (int)args.size();
   const int cmax = fgmres_batch_max_ctas(ctx);
@@ -249,32 +312,24 @@ static int launch_fgmres(BatchScratch &S, int slot, std::vector<FgmresArgs> &arg
     set_error("batch: %d members exceed the %d co-resident CTAs of one launch", m, cmax);
     return RBFFD_EINVAL;
   }
-  const std::vector<int> nb = split_ctas(rows, std::vector<int>(m, kdev::MAXB), cmax);
-  const int nctas = std::accumulate(nb.begin(), nb.end(), 0);
+  const TeamPlan T = plan_teams(work, std::vector<int>(m, kdev::MAXB), rows, cmax);
   char *hb = (char *)S.hmem;
   char *db = (char *)S.dmem;
   FgmresArgs *hsys = (FgmresArgs *)(hb + S.off_sys[slot]);
-  int *hcs = (int *)(hb + S.off_cta_sys[slot]);
-  int *hcf = (int *)(hb + S.off_cta_first[slot]);
   unsigned int *dflags = (unsigned int *)(db + S.off_flags[slot]);
   GridBarrier *dbars = (GridBarrier *)(db + S.off_bars[slot]);
-  int c = 0;
   for (int i = 0; i < m; ++i) {
     FgmresArgs a = args[i];
-    a.nblocks = nb[i];
-    a.flags = dflags + c;
+    a.nblocks = T.nb[i];
+    a.tpr = tpr_for(a.n, a.nblocks);
+    a.flags = dflags + i;
     a.bar = dbars + i;
     hsys[i] = a;
-    hcf[i] = c;
-    for (int k = 0; k < nb[i]; ++k) hcs[c + k] = i;
-    c += nb[i];
   }
-  RBFFD_CK(cudaMemcpyAsync(db + S.off_sys[slot], hb + S.off_sys[slot],
-                           S.off_flags[slot] - S.off_sys[slot], cudaMemcpyHostToDevice,
-                           ctx->stream));
-  RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * nctas, ctx->stream));
+  RBFFD_TRY(put_tables(S, slot, T, m, sizeof(FgmresArgs)));
+  RBFFD_CK(cudaMemsetAsync(dflags, 0, sizeof(unsigned int) * m, ctx->stream));
   RBFFD_TRY(reset_barriers(ctx, dbars, m));
-  return fgmres_batch_launch(ctx, nctas, (const FgmresArgs *)(db + S.off_sys[slot]),
+  return fgmres_batch_launch(ctx, T.nctas, (const FgmresArgs *)(db + S.off_sys[slot]),
                              (const int *)(db + S.off_cta_sys[slot]),
                              (const int *)(db + S.off_cta_first[slot]));
 }
@@ -290,6 +345,7 @@ static int launch_pcorr(BatchScratch &S, rbffd_problem *const *P, const std::vec
   std::vector<KrylovArgs> pj, pa;
   std::vector<FgmresArgs> pf;
   std::vector<int> rj, ra, rf;
+  std::vector<double> wj, wa, wf;
   for (size_t s = 0; s < sel.size(); ++s) {
     rbffd_problem *Q = P[sel[s]];
     if (Q->amgf) {
@@ -315,6 +371,7 @@ static int launch_pcorr(BatchScratch &S, rbffd_problem *const *P, const std::vec
       f.amg = Q->amgf;
       pf.push_back(f);
       rf.push_back(Q->n);
+      wf.push_back(work_of(Q, 1));
       continue;
     }
     KrylovArgs a;
@@ -337,14 +394,16 @@ static int launch_pcorr(BatchScratch &S, rbffd_problem *const *P, const std::vec
       a.amg = Q->amg;
       pa.push_back(a);
       ra.push_back(Q->n);
+      wa.push_back(work_of(Q, 1));
     } else {
       pj.push_back(a);
       rj.push_back(Q->n);
+      wj.push_back(work_of(Q, 1));
     }
   }
-  if (!pj.empty()) RBFFD_TRY(launch_krylov(S, 2, 1, pj, rj));
-  if (!pa.empty()) RBFFD_TRY(launch_krylov(S, 3, 1, pa, ra, true));
-  if (!pf.empty()) RBFFD_TRY(launch_fgmres(S, 4, pf, rf));
+  if (!pj.empty()) RBFFD_TRY(launch_krylov(S, 2, 1, pj, wj, rj));
+  if (!pa.empty()) RBFFD_TRY(launch_krylov(S, 3, 1, pa, wa, ra, true));
+  if (!pf.empty()) RBFFD_TRY(launch_fgmres(S, 4, pf, wf, rf));
   return RBFFD_OK;
 }
 
@@ -358,9 +417,11 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
   // solves of all members (and one for the single-RHS pairs, if any)
   std::vector<KrylovArgs> a2, a1s;
   std::vector<int> rows2, rows1s;
+  std::vector<double> work2, work1s;
   // mixed-precision members by inner arithmetic (0 FP32, 1 float-float)
   std::vector<MixedArgs> x2[2], x1s[2];
   std::vector<int> xr2[2], xr1s[2];
+  std::vector<double> xw2[2], xw1s[2];
   for (int i = 0; i < m; ++i) {
     const rbffd_step_params *sp = spv[i];
     RBFFD_TRY(ops_momentum(P[i], sp));
@@ -397,6 +458,7 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
       if (!Q->has_sym) {
         x2[ia].push_back(x);
         xr2[ia].push_back(Q->n);
+        xw2[ia].push_back(work_of(Q, 0));
       } else {
         // the u~ and v~ systems differ on symmetry lines: two single-RHS
         // systems, the second on its own partial sums (second half)
@@ -419,6 +481,8 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
         x1s[ia].push_back(xv);
         xr1s[ia].push_back(Q->n);
         xr1s[ia].push_back(Q->n);
+        xw1s[ia].push_back(work_of(Q, 0));
+        xw1s[ia].push_back(work_of(Q, 0));
       }
       continue;
     }
@@ -445,6 +509,7 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
     if (!P[i]->has_sym) {
       a2.push_back(a);
       rows2.push_back(P[i]->n);
+      work2.push_back(work_of(P[i], 0));
     } else {
       KrylovArgs au = a;
       au.b[1] = nullptr;
@@ -461,15 +526,19 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
       a1s.push_back(av);
       rows1s.push_back(P[i]->n);
       rows1s.push_back(P[i]->n);
+      work1s.push_back(work_of(P[i], 0));
+      work1s.push_back(work_of(P[i], 0));
     }
   }
   prof_begin(ctx, 0);
-  if (!a2.empty()) RBFFD_TRY(launch_krylov(S, 0, 2, a2, rows2));
-  if (!a1s.empty()) RBFFD_TRY(launch_krylov(S, 1, 1, a1s, rows1s));
+  if (!a2.empty()) RBFFD_TRY(launch_krylov(S, 0, 2, a2, work2, rows2));
+  if (!a1s.empty()) RBFFD_TRY(launch_krylov(S, 1, 1, a1s, work1s, rows1s));
   for (int ia = 0; ia < 2; ++ia) {
     const int inner = ia ? INNER_FF : INNER_F32;
-    if (!x2[ia].empty()) RBFFD_TRY(launch_mixed(S, 5 + 2 * ia, 2, inner, x2[ia], xr2[ia]));
-    if (!x1s[ia].empty()) RBFFD_TRY(launch_mixed(S, 6 + 2 * ia, 1, inner, x1s[ia], xr1s[ia]));
+    if (!x2[ia].empty())
+      RBFFD_TRY(launch_mixed(S, 5 + 2 * ia, 2, inner, x2[ia], xw2[ia], xr2[ia]));
+    if (!x1s[ia].empty())
+      RBFFD_TRY(launch_mixed(S, 6 + 2 * ia, 1, inner, x1s[ia], xw1s[ia], xr1s[ia]));
   }
   prof_end(ctx, 0);
   // p' solves: one launch per solver -- Jacobi BiCGSTAB, multigrid
@@ -677,6 +746,11 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
     }
     prof_collect(ctx, 0, RBFFD_KSTAT_KRYLOV_MOM, um, bm);
     prof_collect(ctx, 1, RBFFD_KSTAT_KRYLOV_P, up, bp);
+  }
+  // iteration history for the next plan of the work lists (plan_teams)
+  for (int i = 0; i < m; ++i) {
+    P[i]->it_hist[0] = std::max(mo[i].iters[0], mo[i].iters[1]);
+    P[i]->it_hist[1] = mo[i].iters[2];
   }
   int rc = RBFFD_OK;
   for (int i = 0; i < m; ++i) {

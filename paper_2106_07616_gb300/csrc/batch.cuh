@@ -21,6 +21,7 @@ struct BatchScratch {
   static constexpr int NSLOT = 9;
   rbffd_ctx *ctx = nullptr;
   int cap = 0, maxc = 0;
+  int team_words = 0;  // ints of one work-list table slot (4 per team + the lists)
   void *dmem = nullptr, *hmem = nullptr;
   size_t dbytes = 0, hbytes = 0;
   // per slot: sys args, CTA -> system, first CTA of each system (one

@@ -552,10 +552,17 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir_batch(const MixedArgs *__res
                                                           const int *__restrict__ cta_sys,
                                                           const int *__restrict__ cta_first) {
   __shared__ MixedArgs A;
-  const int s = cta_sys[blockIdx.x];
-  if (threadIdx.x == 0) A = sys[s];
-  __syncthreads();
-  bicgstab_ir_body<NR, NT, IA>(A, blockIdx.x - cta_first[s], A.nblocks);
+  // persistent work list (batch.cu: plan_teams): this CTA's team solves
+  // the systems cta_first[j0 .. j1) one after another
+  const int t = cta_sys[blockIdx.x];
+  const int c0 = cta_first[4 * t], nc = cta_first[4 * t + 1];
+  const int j0 = cta_first[4 * t + 2], j1 = cta_first[4 * t + 3];
+  for (int j = j0; j < j1; ++j) {
+    __syncthreads();
+    if (threadIdx.x == 0) A = sys[cta_first[j]];
+    __syncthreads();
+    bicgstab_ir_body<NR, NT, IA>(A, blockIdx.x - c0, nc);
+  }
 }
 
 namespace {

@@ -774,6 +774,8 @@ extern "C" int simple_iterate(rbffd_problem *P, const rbffd_step_params *sp, dou
     RBFFD_TRY(issue_outer(P, sp));
     Readback r;
     RBFFD_TRY(read_back(P, &r));
+    P->it_hist[0] = r.kout[0].iters > r.kout[1].iters ? r.kout[0].iters : r.kout[1].iters;
+    P->it_hist[1] = r.kout[2].iters;
     if (P->ctx->prof) {
       // inner iterations of the FP32 mixed path move 4-byte values and vectors
       const bool mx = P->precision == RBFFD_PREC_MIXED;

@@ -54,6 +54,9 @@ struct rbffd_problem {
   // (ops.cu: compat_shift)
   double *zc, *pcs;
   bool compat = false;   // pin >= 0: the p' equation has Neumann rows only
+  // iterations of the last momentum [0] and p' [1] solves (the work
+  // estimate of the batched work lists; 0 before any)
+  int it_hist[2] = {0, 0};
   bool z_ready = false;  // zc holds z for the current build
   // Krylov workspace: 8 vectors x 2 right-hand sides
   rbffd::KrylovVecs kv[2];
