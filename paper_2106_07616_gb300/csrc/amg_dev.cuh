@@ -31,9 +31,11 @@ constexpr int CC = AMG_CSR_CHUNK;
 
 // zadd (may be null): z(i) is added to the row's sum, loaded with the row
 // pointers instead of after the sum.
+// xs (may be null): x[0 .. xlen) staged in shared memory, gathered from there.
 template <typename T, typename XT, typename F>
 __device__ __forceinline__ void csr_rows(const AmgCsrT<T> &M, int nrows, const XT *x, int wglobal,
-                                         int nwarps, F &&f, const T *zadd = nullptr) {
+                                         int nwarps, F &&f, const T *zadd = nullptr,
+                                         const XT *xs = nullptr, int xlen = 0) {
   const int lane = threadIdx.x & 31;
   const int G = M.grp, rpw = 32 / G, g = lane / G, lg = lane - g * G;
   for (int base = wglobal * rpw; base < nrows; base += nwarps * rpw) {
@@ -53,7 +55,7 @@ __device__ __forceinline__ void csr_rows(const AmgCsrT<T> &M, int nrows, const X
         }
 #pragma unroll
         for (int u = 0; u < CC; ++u)
-          if (c[u] >= 0) t += a[u] * T(__ldcg(x + c[u]));
+          if (c[u] >= 0) t += a[u] * T(kdev::win_get<XT>(xs, 0, xlen, x, c[u]));
       }
     }
     for (int o = G >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
@@ -137,8 +139,13 @@ __device__ __forceinline__ bool vcycle(const AmgDevT<T> *__restrict__ G, const C
     const AmgLevelT<T> &Lv = G->lev[l];
     const T *z = Lv.z;
     if (l == 0) {
+      // level 1's y is gathered by every row of level 0: staged whole in
+      // shared memory when it fits (kdev::win_stage)
+      const int n1 = G->lev[1].n;
+      const T *ys = kdev::win_cap() >= n1 ? kdev::win_stage<T>(G->lev[1].y, 0, n1) : nullptr;
       csr_rows(
-          Lv.P, Lv.n, G->lev[1].y, wfw, c.nwarps, [&](int i, T t) { out[i] = OT(t); }, z);
+          Lv.P, Lv.n, G->lev[1].y, wfw, c.nwarps, [&](int i, T t) { out[i] = OT(t); }, z, ys,
+          ys ? n1 : 0);
     } else {
       T *res = Lv.y;
       csr_rows(

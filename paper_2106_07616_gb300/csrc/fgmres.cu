@@ -44,6 +44,9 @@ constexpr int FNT = 1024;
 constexpr int FG_D = FG_MAXM + 2;  // most dot products one exchange reduces
 constexpr int LDH = FG_MAXM + 1;   // leading dimension of the Hessenberg matrix
 constexpr int GB = 8;              // loads a lane keeps in flight in the loops below
+// dynamic shared memory of the single-problem launch: windows of up to
+// 4 096 entries (two FP64 vectors' worth; kdev::win_cap)
+constexpr int FG_WIN_BYTES = 64 * 1024;
 using kdev::MAXB;
 
 // barrier `id` among the first `nthreads` threads that reach it (a multiple
@@ -65,6 +68,10 @@ __device__ __forceinline__ void block_spmv(int r0, int r1, int q, int ldn, int T
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gpw = 32 / T, g = lane / T, lg = lane - g * T;
   const bool active = g < gpw;
+  // x's window over this block's rows, staged in shared memory (win_init)
+  const kdev::RowWindow rw = kdev::row_window();
+  const int wlen = kdev::win_cap() > 0 ? rw.w1 - rw.w0 : 0;
+  const XT *wb = wlen > 0 ? kdev::win_stage<XT>(x, rw.w0, rw.w1) : nullptr;
   for (int base = r0 + warp * gpw; base < r1; base += nw * gpw) {
     const int i = base + g;
     const bool valid = active && i < r1;
@@ -82,7 +89,7 @@ __device__ __forceinline__ void block_spmv(int r0, int r1, int q, int ldn, int T
         }
 #pragma unroll
         for (int u = 0; u < kdev::CH; ++u)
-          if (c[u] >= 0) s += AT(a[u]) * AT(__ldcg(x + c[u]));
+          if (c[u] >= 0) s += AT(a[u]) * AT(kdev::win_get<XT>(wb, rw.w0, wlen, x, c[u]));
       }
     }
     AT tot = s;
@@ -216,6 +223,9 @@ __device__ __forceinline__ void fgmres_body(const FgmresArgs &A, const int lb, c
   int Tb = 1;
   for (int t = 2; t <= 8; ++t)
     if ((32 / t) * (NT / 32) >= R) Tb = t;
+  // the column window of this block's rows for the staged gathers of every
+  // level-0 SpMV (the solve's own and the cycle's smoother share the columns)
+  kdev::win_init(n, A.q, A.ldn, A.col, r0, r1);
   double *p64 = (double *)A.part;  // 2 x MAXB
   float *part0 = (float *)(p64 + 2 * MAXB), *part1 = part0 + FG_D * MAXB;
   float *fred = reinterpret_cast<float *>(sred);
@@ -453,9 +463,13 @@ int fgmres_launch(rbffd_ctx *ctx, int nblocks, const FgmresArgs &args) {
   }
   RBFFD_TRY(reset_barriers(ctx, args.bar, 1));
   RBFFD_CK(cudaMemsetAsync(args.flags, 0, sizeof(unsigned int) * nblocks, ctx->stream));
+  // shared memory for the staged windows of the gathered vectors
+  // (kdev::win_init); one CTA per SM either way (1024 threads)
+  RBFFD_CK(cudaFuncSetAttribute((const void *)k_fgmres<FNT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, FG_WIN_BYTES));
   void *kargs[] = {(void *)&args};
   cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_fgmres<FNT>, dim3(nblocks),
-                                              dim3(FNT), kargs, 0, ctx->stream);
+                                              dim3(FNT), kargs, FG_WIN_BYTES, ctx->stream);
   ctx->launches++;
   if (e != cudaSuccess) {
     set_error("cooperative launch of k_fgmres failed: %s", cudaGetErrorString(e));

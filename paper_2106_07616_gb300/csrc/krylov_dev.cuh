@@ -2,6 +2,8 @@
 // kernels: a T-threads-per-row ELL SpMV, block partial sums and the
 // grid-wide publish/wait/reduce exchange (an arrival counter).
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "inner_arith.cuh"
 
@@ -32,6 +34,95 @@ __device__ __forceinline__ float ld_cg(const float *p) { return __ldcg(p); }
 __device__ __forceinline__ ff ld_cg(const ff *p) {
   const float2 t = __ldcg(reinterpret_cast<const float2 *>(p));
   return ff(t.x, t.y);
+}
+
+// ---- windows of gathered vectors staged in shared memory ------------------
+// A launch may give its CTAs dynamic shared memory; then every CTA finds,
+// once per launch (win_init), the column window [w0, w1) that its own rows'
+// ELL entries reach -- the clouds keep it a few lattice lines wide in
+// row-major or Morton order -- and every level-0 SpMV stages that window of
+// the gathered vector into shared memory first (one coalesced pass from L2,
+// after the exchange that published the vector) and gathers from there:
+// one 4- or 8-byte shared-memory read per nonzero instead of one 32-byte L2
+// sector.  Columns outside the window (a window wider than the buffer keeps
+// the part around the CTA's own rows) are read from L2 as before.  Without
+// dynamic shared memory the capacity is zero and nothing is staged.
+extern __shared__ __align__(16) unsigned char kdev_dyn[];
+
+__device__ __forceinline__ unsigned int dyn_smem_bytes() {
+  unsigned int r;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+
+// window capacity in entries: room for two FP64 vectors (two right-hand sides)
+__device__ __forceinline__ int win_cap() { return (int)(dyn_smem_bytes() / 16u); }
+
+struct RowWindow {
+  int w0, w1;
+};
+__device__ __forceinline__ RowWindow &row_window() {
+  __shared__ RowWindow w;
+  return w;
+}
+
+// The window of the rows [r0, r1) of an ELL [q][ldn] column array (all
+// threads of the CTA call it; ends with a barrier).
+__device__ __forceinline__ void win_init(int n, int q, int ldn, const int32_t *__restrict__ col,
+                                         int r0, int r1) {
+  __shared__ int s_lo, s_hi;
+  const int cap = win_cap();
+  const int R = r1 - r0;
+  if (threadIdx.x == 0) {
+    s_lo = 0x7fffffff;
+    s_hi = -1;
+  }
+  __syncthreads();
+  if (cap > 0 && R > 0) {
+    int lo = 0x7fffffff, hi = -1;
+    for (int e = threadIdx.x; e < R * q; e += blockDim.x) {
+      const int j = e / R, i = r0 + (e - j * R);
+      const int c = __ldg(col + (int64_t)j * ldn + i);
+      lo = min(lo, c);
+      hi = max(hi, c);
+    }
+    atomicMin(&s_lo, lo);
+    atomicMax(&s_hi, hi);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    RowWindow &w = row_window();
+    if (cap <= 0 || R <= 0 || s_hi < s_lo) {
+      w.w0 = w.w1 = 0;
+    } else if (s_hi - s_lo + 1 <= cap) {
+      w.w0 = s_lo;
+      w.w1 = s_hi + 1;
+    } else {  // keep the part around the CTA's own rows
+      int w0 = (r0 + r1) / 2 - cap / 2;
+      w0 = max(0, min(w0, n - cap));
+      w.w0 = w0;
+      w.w1 = min(n, w0 + cap);
+    }
+  }
+  __syncthreads();
+}
+
+// Stage x[w0 .. w1) into the k-th buffer (all threads of the CTA; the
+// barriers keep the previous use of the buffer and this copy apart).
+template <typename XT>
+__device__ __forceinline__ const XT *win_stage(const XT *x, int w0, int w1, int k = 0) {
+  XT *buf = reinterpret_cast<XT *>(kdev_dyn + (size_t)k * win_cap() * sizeof(double));
+  __syncthreads();
+  for (int t = threadIdx.x; t < w1 - w0; t += blockDim.x) buf[t] = __ldcg(x + w0 + t);
+  __syncthreads();
+  return buf;
+}
+
+// x(c) from the staged window when it holds c, else from L2
+template <typename XT>
+__device__ __forceinline__ XT win_get(const XT *buf, int w0, int wlen, const XT *x, int c) {
+  const unsigned int o = (unsigned int)(c - w0);
+  return o < (unsigned int)wlen ? buf[o] : __ldcg(x + c);
 }
 
 // The contiguous rows [r0, r1) of the CTA that warp `wglobal` belongs to
@@ -69,6 +160,14 @@ __device__ __forceinline__ void spmv_rows(int n, int q, int ldn, int T,
   const int wpb = blockDim.x >> 5;
   int r0, r1, w;
   cta_rows(n, wglobal, nwarps, wpb, r0, r1, w);
+  // the gathered vectors' window, staged (see win_init)
+  using X = typename std::remove_const<XT>::type;
+  const RowWindow rw = row_window();
+  const int wlen = win_cap() > 0 ? rw.w1 - rw.w0 : 0;
+  const X *wb[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k)
+    wb[k] = wlen > 0 ? win_stage<X>(xs[k], rw.w0, rw.w1, k) : nullptr;
   for (int base = r0 + w * gpw; base < r1; base += wpb * gpw) {
     const int i = base + g;
     const bool valid = active && i < r1;
@@ -90,7 +189,8 @@ __device__ __forceinline__ void spmv_rows(int n, int q, int ldn, int T,
         for (int u = 0; u < CH; ++u) {
           if (c[u] >= 0) {
 #pragma unroll
-            for (int k = 0; k < NR; ++k) s[k] += AT(a[u]) * AT(__ldcg(xs[k] + c[u]));
+            for (int k = 0; k < NR; ++k)
+              s[k] += AT(a[u]) * AT(win_get<X>(wb[k], rw.w0, wlen, xs[k], c[u]));
           }
         }
       }
