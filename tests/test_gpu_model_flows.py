@@ -21,26 +21,73 @@ def mean_spacing(fp):
 
 @pytest.mark.parametrize("degree", [3, 4])
 def test_couette_error_falls_under_refinement(degree):
-    """Marched from rest to the paper's steady error of 2e-7: the L1 error of
-    u, v against the closed form falls under refinement at a slope of at
-    least 1.  The paper reports slopes of k - 1 to k + 1; on these clouds the
-    slope is about 1.3 (k = 3) and 1.4 (k = 4), a property of the discrete
-    steady solution (marching from the exact fields ends at the same error),
-    not of the march."""
-    errs, hs = [], []
+    """Marched from rest to the paper's steady error of 2e-7 (Sec. 4.1): the
+    L1 errors of u and v against the closed form fall under refinement at a
+    slope of at least 1.2, and the paper's own fit -- one line through the
+    12 points of the u, v, p and divergence errors on the three clouds --
+    at least 1.4.  The paper prints 3.47 for degree 3; the discrete steady
+    solution of this reading (a Newton solve of the discrete equations on
+    these clouds) falls at 1.34 (u), 1.35 (v), 1.43 (p) and 2.56 (the
+    continuity constant), 1.67 in the 12-point fit: the interior Laplacian's
+    O(h^(k-1)) truncation sets it, and on three clouds its near-wall part
+    keeps the fit below the asymptotic k - 1.  The readings that came closer
+    to 3.47 made the outer iteration diverge."""
+    errs, hs, pts = [], [], []
     for h in (0.036, 0.026, 0.018):
         fp = clouds.couette(h, degree=degree)
         P = rbffd.Problem(ctx(), fp, precond=rbffd.PRECOND_AMG)
         rc, st = P.solve_steady(fp.dt, resid_tol=2e-7, max_steps=12000, criterion=1,
                                 krylov_tol=1e-12, krylov_maxit=20000)
-        inter = fp.tag == 0
-        e = (np.abs(P.get("u") - fp.exact["u"])[inter].mean() +
-             np.abs(P.get("v") - fp.exact["v"])[inter].mean())
-        errs.append(e)
+        inner = fp.tag == 0
+        u, v, p = P.get("u"), P.get("v"), P.get("p")
+        eu = np.abs(u - fp.exact["u"])[inner].mean()
+        ev = np.abs(v - fp.exact["v"])[inner].mean()
+        dp = p - fp.exact["p"]
+        ep = np.abs(dp - dp.mean()).mean()
+        ops = P.operators()  # host copies of the weights
+        div = (ops["wx"] * u[ops["idx"]]).sum(axis=1) + (ops["wy"] * v[ops["idx"]]).sum(axis=1)
+        ed = np.abs(div)[inner].mean()
+        errs.append(eu + ev)
+        pts.append((eu, ev, ep, ed))
         hs.append(mean_spacing(fp))
+        P.close()
     slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
     assert errs[0] > errs[1] > errs[2], errs
-    assert slope >= 1.0, (slope, errs)
+    assert slope >= 1.2, (slope, errs)
+    pts = np.array(pts)
+    fit12 = np.polyfit(np.concatenate([np.log(hs)] * 4), np.log(pts.T.ravel()), 1)[0]
+    assert fit12 >= 1.4, (fit12, pts)
+
+
+def test_kovasznay_error_decays_under_refinement():
+    """Kovasznay flow (Re 40, degree 3) on 25^2, 50^2 and 100^2 clouds,
+    marched to R <= 1e-7 with dt = 0.5 x the lattice spacing (the fastest
+    to a tight residual: the slow pressure mode contracts most per step when
+    the time term dominates): the L1 errors of u and v against the closed
+    form fall at a slope of at least 1.6 (the discrete steady solution's own
+    error, computed by a Newton solve of the discrete equations, falls at
+    1.87 (u) and 2.03 (v) on these clouds: the Laplacian's order k - 1), and
+    the continuity constant lambda falls faster than the error."""
+    hs, eu, ev, lam = [], [], [], []
+    for ns in (25, 50, 100):
+        h = 2.0 / (ns - 1)
+        fp = clouds.kovasznay(ns, dt=0.5 * h)
+        P = rbffd.Problem(ctx(), fp, precond=rbffd.PRECOND_AMG)
+        rc, st = P.solve_steady(fp.dt, resid_tol=1e-7, max_steps=40000, krylov_tol=1e-12,
+                                krylov_maxit=20000)
+        assert st["resid"][2] <= 1e-7, (ns, st)
+        inner = fp.tag == 0
+        eu.append(np.abs(P.get("u") - fp.exact["u"])[inner].mean())
+        ev.append(np.abs(P.get("v") - fp.exact["v"])[inner].mean())
+        lam.append(abs(st["resid"][3]))
+        hs.append(h)
+        P.close()
+    for e in (eu, ev):
+        slope = np.polyfit(np.log(hs), np.log(e), 1)[0]
+        assert 1.6 <= slope <= 4.0, (slope, e)
+    assert lam[0] > lam[1] > lam[2], lam
+    lam_slope = np.polyfit(np.log(hs), np.log(lam), 1)[0]
+    assert lam_slope > np.polyfit(np.log(hs), np.log(eu), 1)[0], (lam, eu)
 
 
 def test_couette_steps_match_oracle():
