@@ -176,10 +176,12 @@ def batch_line(args):
         for P, fp in zip(probs, fps):
             P.reload(fp, prec, precond=pc)
 
-    for _ in range(args.warmup):
+    # the work-list autotuner runs on the first nine iterations of the batch
+    for _ in range(max(args.warmup, 9)):
         reload_all()
         iterate_all()
     torch.cuda.synchronize()
+    tuned, scales, costs = B.tuning()
     l0 = ctx.launches
     total_ms, outer = 0.0, 0
     with ClockSampler(0) as clk:
@@ -246,7 +248,13 @@ def batch_line(args):
                         "frac_of_hbm": (kp["bytes"] / (kp["ms"] / 1e3) / 1e9) / peak if kp["ms"] else None},
            "krylov_mom": {"launches": km["launches"], "ms": km["ms"],
                           "algorithmic_GBps": km["bytes"] / (km["ms"] / 1e3) / 1e9 if km["ms"] else None},
-           "peak_hbm_GBps": peak, "peak_source": src, "clocks": clk.summary()}
+           "peak_hbm_GBps": peak, "peak_source": src, "clocks": clk.summary(),
+           "autotune": {"tuned": tuned, "team_scale_per_slot": scales,
+                        "ms_per_row_iteration": costs.tolist(),
+                        "candidates": [1.0, 2.0, 0.5, 4.0],
+                        "slots": ["momentum 2-RHS", "momentum 1-RHS", "p' jacobi",
+                                  "p' multigrid", "p' fgmres", "mixed f32 2-RHS",
+                                  "mixed f32 single", "mixed ff 2-RHS", "mixed ff single"]}}
     for P in probs:
         P.close()
     B.close()
@@ -539,7 +547,8 @@ def bench_extras(args, ctx, stream, fp, dev, desc_dev, init, flush, P):
     ba.precond, ba.precision = "amg", "fp64"
     b = batch_line(ba)
     res["batch"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "e2e", "roofline",
-                                      "krylov_p", "krylov_mom", "config", "gpu_launches")}
+                                      "krylov_p", "krylov_mom", "config", "gpu_launches",
+                                      "autotune")}
     sa = argparse.Namespace(**vars(args))
     sa.count, sa.resid_tol, sa.criterion, sa.max_steps = args.serve_count, 1e-8, 0, 20000
     sa.precond, sa.precision = "amg", "fp64"

@@ -447,6 +447,31 @@ int rbffd_batch_iterate(rbffd_batch *batch, const rbffd_step_params *params, con
 int rbffd_batch_graph_stats(const rbffd_batch *batch, int64_t *captures, int64_t *replays,
                             int64_t *kernels);
 
+/* Launch-shape autotuner of the batched Krylov launches (the library's own
+ * tuning; the paper solves one problem at a time).  Each launch runs as a
+ * persistent work list: teams of CTAs, each solving its share of the
+ * members one after another, the team size planned from the members' work
+ * (rows x last iteration count).  The first nine iterations of a batch run
+ * directly: one untimed at the planned team size, then eight with it
+ * scaled by 1, 2, 1/2, 4, 4, 1/2, 2, 1 (threads per row follow from it);
+ * each launch is timed with CUDA events and its time divided by the work
+ * it did; every launch slot then keeps the scale of least average cost.  The nine slots: momentum with u~ and v~ as two right-hand sides,
+ * momentum as single-RHS systems (members with symmetry lines), p' Jacobi
+ * BiCGSTAB, p' multigrid BiCGSTAB, p' flexible GMRES, and the
+ * mixed-precision momentum launches (FP32 two-RHS/single, float-float
+ * two-RHS/single).  tuned (nullable): 1 once done.  scales
+ * (nullable, 9): the current scale per slot.  cost (nullable, 9 x 4, slot
+ * major): ms per row-iteration of each candidate, the mean of its two
+ * timings (0: slot unused).
+ * Errors: RBFFD_EINVAL (null batch). */
+int rbffd_batch_tuning(const rbffd_batch *batch, int32_t *tuned, double *scales, double *cost);
+
+/* Switches the work-list autotuner on (on != 0, the default: it starts over
+ * at the batch's next iteration) or off (every slot keeps the planned team
+ * size, scale 1).  Either way the tuning state is cleared.  Results do not
+ * depend on it beyond the order of partial sums.  Errors: RBFFD_EINVAL. */
+int rbffd_batch_set_autotune(rbffd_batch *batch, int on);
+
 /* -------------------------------------------------------------- serving */
 
 /* A request server with continuous batching (the serving workload; the

@@ -64,6 +64,9 @@ void BatchScratch::drop_graph() {
 }
 
 BatchScratch::~BatchScratch() {
+  for (auto &e : ev)
+    for (cudaEvent_t x : e)
+      if (x) cudaEventDestroy(x);
   if (ctx) {
     drop_graph();
     dev_free(ctx, dmem, dbytes);
@@ -138,7 +141,7 @@ struct TeamPlan {
 };
 
 static TeamPlan plan_teams(const std::vector<double> &work, const std::vector<int> &cap,
-                           const std::vector<int> &rows, int cmax) {
+                           const std::vector<int> &rows, int cmax, double scale = 1.0) {
   const int m = (int)work.size();
   TeamPlan T;
   double total = 0.0, wmax = 0.0;
@@ -153,6 +156,7 @@ static TeamPlan plan_teams(const std::vector<double> &work, const std::vector<in
   const int rowcap = std::max(1, (int)((rmin * 8LL + KB_NT - 1) / KB_NT));
   const int tmax = std::max(1, std::min(capmin, kdev::MAXB));
   int team = total > 0 ? (int)std::ceil(cmax * wmax / total) : 1;
+  team = std::max(1, (int)std::lround(team * scale));  // the autotuner's scale
   team = std::max(1, std::min(team, tmax));
   int nteams = std::max(1, std::min(cmax / team, m));
   // fewer teams than the grid holds: spread the CTAs over them
@@ -183,6 +187,16 @@ static TeamPlan plan_teams(const std::vector<double> &work, const std::vector<in
     T.info_and_list[4 * t + 3] = (int)T.info_and_list.size();
   }
   return T;
+}
+
+// Autotuner events around the launch of one slot (only while tuning; such
+// iterations are never captured).
+static int tune_mark(BatchScratch &S, int slot, int end) {
+  if (!S.timing) return RBFFD_OK;
+  if (!S.ev[slot][end]) RBFFD_CK(cudaEventCreate(&S.ev[slot][end]));
+  RBFFD_CK(cudaEventRecord(S.ev[slot][end], S.ctx->stream));
+  S.slot_used[slot] = true;
+  return RBFFD_OK;
 }
 
 // Work of one of a member's solves for the work-list plan: its rows times
@@ -239,7 +253,7 @@ static int launch_krylov(BatchScratch &S, int slot, int nr, std::vector<KrylovAr
   }
   std::vector<int> cap(m);
   for (int i = 0; i < m; ++i) cap[i] = args[i].nblocks;
-  const TeamPlan T = plan_teams(work, cap, rows, cmax);
+  const TeamPlan T = plan_teams(work, cap, rows, cmax, S.scale[slot]);
   char *hb = (char *)S.hmem;
   char *db = (char *)S.dmem;
   KrylovArgs *hsys = (KrylovArgs *)(hb + S.off_sys[slot]);
@@ -278,7 +292,7 @@ static int launch_mixed(BatchScratch &S, int slot, int nr, int inner,
   }
   std::vector<int> cap(m);
   for (int i = 0; i < m; ++i) cap[i] = args[i].nblocks;
-  const TeamPlan T = plan_teams(work, cap, rows, cmax);
+  const TeamPlan T = plan_teams(work, cap, rows, cmax, S.scale[slot]);
   char *hb = (char *)S.hmem;
   char *db = (char *)S.dmem;
   MixedArgs *hsys = (MixedArgs *)(hb + S.off_sys[slot]);
@@ -312,7 +326,7 @@ static int launch_fgmres(BatchScratch &S, int slot, std::vector<FgmresArgs> &arg
     set_error("batch: %d members exceed the %d co-resident CTAs of one launch", m, cmax);
     return RBFFD_EINVAL;
   }
-  const TeamPlan T = plan_teams(work, std::vector<int>(m, kdev::MAXB), rows, cmax);
+  const TeamPlan T = plan_teams(work, std::vector<int>(m, kdev::MAXB), rows, cmax, S.scale[slot]);
   char *hb = (char *)S.hmem;
   char *db = (char *)S.dmem;
   FgmresArgs *hsys = (FgmresArgs *)(hb + S.off_sys[slot]);
@@ -346,6 +360,7 @@ static int launch_pcorr(BatchScratch &S, rbffd_problem *const *P, const std::vec
   std::vector<FgmresArgs> pf;
   std::vector<int> rj, ra, rf;
   std::vector<double> wj, wa, wf;
+  std::vector<std::pair<int, int>> mj, ma, mf;
   for (size_t s = 0; s < sel.size(); ++s) {
     rbffd_problem *Q = P[sel[s]];
     if (Q->amgf) {
@@ -372,6 +387,7 @@ static int launch_pcorr(BatchScratch &S, rbffd_problem *const *P, const std::vec
       pf.push_back(f);
       rf.push_back(Q->n);
       wf.push_back(work_of(Q, 1));
+      mf.push_back({sel[s], 1});
       continue;
     }
     KrylovArgs a;
@@ -395,15 +411,32 @@ static int launch_pcorr(BatchScratch &S, rbffd_problem *const *P, const std::vec
       pa.push_back(a);
       ra.push_back(Q->n);
       wa.push_back(work_of(Q, 1));
+      ma.push_back({sel[s], 1});
     } else {
       pj.push_back(a);
       rj.push_back(Q->n);
       wj.push_back(work_of(Q, 1));
+      mj.push_back({sel[s], 1});
     }
   }
-  if (!pj.empty()) RBFFD_TRY(launch_krylov(S, 2, 1, pj, wj, rj));
-  if (!pa.empty()) RBFFD_TRY(launch_krylov(S, 3, 1, pa, wa, ra, true));
-  if (!pf.empty()) RBFFD_TRY(launch_fgmres(S, 4, pf, wf, rf));
+  if (!pj.empty()) {
+    RBFFD_TRY(tune_mark(S, 2, 0));
+    RBFFD_TRY(launch_krylov(S, 2, 1, pj, wj, rj));
+    S.slot_sys[2] = mj;
+    RBFFD_TRY(tune_mark(S, 2, 1));
+  }
+  if (!pa.empty()) {
+    RBFFD_TRY(tune_mark(S, 3, 0));
+    RBFFD_TRY(launch_krylov(S, 3, 1, pa, wa, ra, true));
+    S.slot_sys[3] = ma;
+    RBFFD_TRY(tune_mark(S, 3, 1));
+  }
+  if (!pf.empty()) {
+    RBFFD_TRY(tune_mark(S, 4, 0));
+    RBFFD_TRY(launch_fgmres(S, 4, pf, wf, rf));
+    S.slot_sys[4] = mf;
+    RBFFD_TRY(tune_mark(S, 4, 1));
+  }
   return RBFFD_OK;
 }
 
@@ -418,6 +451,7 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
   std::vector<KrylovArgs> a2, a1s;
   std::vector<int> rows2, rows1s;
   std::vector<double> work2, work1s;
+  std::vector<std::pair<int, int>> mem2, mem1s, xmem2[2], xmem1s[2];
   // mixed-precision members by inner arithmetic (0 FP32, 1 float-float)
   std::vector<MixedArgs> x2[2], x1s[2];
   std::vector<int> xr2[2], xr1s[2];
@@ -459,6 +493,7 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
         x2[ia].push_back(x);
         xr2[ia].push_back(Q->n);
         xw2[ia].push_back(work_of(Q, 0));
+        xmem2[ia].push_back({i, 0});
       } else {
         // the u~ and v~ systems differ on symmetry lines: two single-RHS
         // systems, the second on its own partial sums (second half)
@@ -483,6 +518,8 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
         xr1s[ia].push_back(Q->n);
         xw1s[ia].push_back(work_of(Q, 0));
         xw1s[ia].push_back(work_of(Q, 0));
+        xmem1s[ia].push_back({i, 0});
+        xmem1s[ia].push_back({i, 0});
       }
       continue;
     }
@@ -510,6 +547,7 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
       a2.push_back(a);
       rows2.push_back(P[i]->n);
       work2.push_back(work_of(P[i], 0));
+      mem2.push_back({i, 0});
     } else {
       KrylovArgs au = a;
       au.b[1] = nullptr;
@@ -528,17 +566,37 @@ static int issue_batch(BatchScratch &S, rbffd_problem *const *P, int m,
       rows1s.push_back(P[i]->n);
       work1s.push_back(work_of(P[i], 0));
       work1s.push_back(work_of(P[i], 0));
+      mem1s.push_back({i, 0});
+      mem1s.push_back({i, 0});
     }
   }
   prof_begin(ctx, 0);
-  if (!a2.empty()) RBFFD_TRY(launch_krylov(S, 0, 2, a2, work2, rows2));
-  if (!a1s.empty()) RBFFD_TRY(launch_krylov(S, 1, 1, a1s, work1s, rows1s));
+  if (!a2.empty()) {
+    RBFFD_TRY(tune_mark(S, 0, 0));
+    RBFFD_TRY(launch_krylov(S, 0, 2, a2, work2, rows2));
+    S.slot_sys[0] = mem2;
+    RBFFD_TRY(tune_mark(S, 0, 1));
+  }
+  if (!a1s.empty()) {
+    RBFFD_TRY(tune_mark(S, 1, 0));
+    RBFFD_TRY(launch_krylov(S, 1, 1, a1s, work1s, rows1s));
+    S.slot_sys[1] = mem1s;
+    RBFFD_TRY(tune_mark(S, 1, 1));
+  }
   for (int ia = 0; ia < 2; ++ia) {
     const int inner = ia ? INNER_FF : INNER_F32;
-    if (!x2[ia].empty())
+    if (!x2[ia].empty()) {
+      RBFFD_TRY(tune_mark(S, 5 + 2 * ia, 0));
       RBFFD_TRY(launch_mixed(S, 5 + 2 * ia, 2, inner, x2[ia], xw2[ia], xr2[ia]));
-    if (!x1s[ia].empty())
+      S.slot_sys[5 + 2 * ia] = xmem2[ia];
+      RBFFD_TRY(tune_mark(S, 5 + 2 * ia, 1));
+    }
+    if (!x1s[ia].empty()) {
+      RBFFD_TRY(tune_mark(S, 6 + 2 * ia, 0));
       RBFFD_TRY(launch_mixed(S, 6 + 2 * ia, 1, inner, x1s[ia], xw1s[ia], xr1s[ia]));
+      S.slot_sys[6 + 2 * ia] = xmem1s[ia];
+      RBFFD_TRY(tune_mark(S, 6 + 2 * ia, 1));
+    }
   }
   prof_end(ctx, 0);
   // p' solves: one launch per solver -- Jacobi BiCGSTAB, multigrid
@@ -678,10 +736,23 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
   // is captured when it comes back, so one-off iterations (a rebuild before
   // every call) pay no capture.  Live kernel timing records events per
   // phase: launched directly.
-  const bool want = !ctx->prof && !S.graph_off;
+  // the work-list autotuner's iterations run directly, timed per slot
+  S.timing = !S.tuned && !S.tune_off && !ctx->prof;
+  const double cand[BatchScratch::NCAND] = {1.0, 2.0, 0.5, 4.0};
+  const int tc = S.timing ? BatchScratch::tune_cand(S.tune_step) : -1;
+  if (S.timing) {
+    for (int k = 0; k < BatchScratch::NSLOT; ++k) {
+      S.scale[k] = tc < 0 ? 1.0 : cand[tc];
+      S.slot_used[k] = false;
+    }
+  }
+  const bool want = !ctx->prof && !S.graph_off && !S.timing;
   std::vector<uint64_t> key;
   if (want) key = graph_key(P, m, spv);
-  if (want && S.exec && key == S.key) {
+  if (S.timing) {
+    S.drop_graph();
+    RBFFD_TRY(issue_batch(S, P, m, spv));
+  } else if (want && S.exec && key == S.key) {
     RBFFD_CK(cudaGraphLaunch(S.exec, ctx->stream));
     ctx->launches += S.graph_launches;
     S.replays++;
@@ -746,6 +817,32 @@ int batch_iterate(BatchScratch &S, rbffd_problem *const *P, int m,
     }
     prof_collect(ctx, 0, RBFFD_KSTAT_KRYLOV_MOM, um, bm);
     prof_collect(ctx, 1, RBFFD_KSTAT_KRYLOV_P, up, bp);
+  }
+  if (S.timing) {
+    // time per unit of work (rows x iterations) of every slot's launch
+    for (int k = 0; k < BatchScratch::NSLOT && tc >= 0; ++k) {
+      if (!S.slot_used[k]) continue;
+      float ms = 0.0f;
+      RBFFD_CK(cudaEventElapsedTime(&ms, S.ev[k][0], S.ev[k][1]));
+      double work = 0.0;
+      for (const auto &pr : S.slot_sys[k]) {
+        const MemberOut &o = mo[pr.first];
+        const int it = pr.second == 0 ? std::max(o.iters[0], o.iters[1]) : o.iters[2];
+        work += (double)P[pr.first]->n * std::max(1, it);
+      }
+      if (work > 0.0) S.cost[k][tc] += 0.5 * ms / work;
+    }
+    S.timing = false;
+    if (++S.tune_step == BatchScratch::NTUNE) {
+      for (int k = 0; k < BatchScratch::NSLOT; ++k) {
+        int best = 0;
+        for (int c = 1; c < BatchScratch::NCAND; ++c)
+          if (S.cost[k][c] > 0.0 && (S.cost[k][best] <= 0.0 || S.cost[k][c] < S.cost[k][best]))
+            best = c;
+        S.scale[k] = cand[best];
+      }
+      S.tuned = true;
+    }
   }
   // iteration history for the next plan of the work lists (plan_teams)
   for (int i = 0; i < m; ++i) {
@@ -825,6 +922,36 @@ extern "C" int rbffd_batch_graph_stats(const rbffd_batch *b, int64_t *captures,
     if (captures) *captures = b->scratch.captures;
     if (replays) *replays = b->scratch.replays;
     if (kernels) *kernels = b->scratch.graph_off ? 0 : b->scratch.graph_launches;
+    return RBFFD_OK;
+  });
+}
+
+extern "C" int rbffd_batch_tuning(const rbffd_batch *b, int32_t *tuned, double *scales,
+                                  double *cost) {
+  return guarded([&]() -> int {
+    if (!b) return RBFFD_EINVAL;
+    const BatchScratch &S = b->scratch;
+    if (tuned) *tuned = S.tuned ? 1 : 0;
+    for (int k = 0; k < BatchScratch::NSLOT; ++k) {
+      if (scales) scales[k] = S.scale[k];
+      for (int c = 0; c < BatchScratch::NCAND; ++c)
+        if (cost) cost[k * BatchScratch::NCAND + c] = S.cost[k][c];
+    }
+    return RBFFD_OK;
+  });
+}
+
+extern "C" int rbffd_batch_set_autotune(rbffd_batch *b, int on) {
+  return guarded([&]() -> int {
+    if (!b) return RBFFD_EINVAL;
+    BatchScratch &S = b->scratch;
+    S.tune_off = !on;
+    S.tuned = false;
+    S.tune_step = 0;
+    for (int k = 0; k < BatchScratch::NSLOT; ++k) {
+      S.scale[k] = 1.0;
+      for (int c = 0; c < BatchScratch::NCAND; ++c) S.cost[k][c] = 0.0;
+    }
     return RBFFD_OK;
   });
 }

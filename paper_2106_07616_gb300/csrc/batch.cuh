@@ -35,6 +35,29 @@ struct BatchScratch {
   int64_t graph_launches = 0;    // kernels one replay launches
   bool graph_off = false;        // capture failed once: launch directly
   int64_t replays = 0, captures = 0;
+  // Work-list autotuner (batch.cu: plan_teams), its iterations run
+  // directly.  The batch's first iteration runs untimed at scale 1 (it pays
+  // the one-time costs: module loading, first launches); the next 2 NCAND
+  // each scale the planned team size of every launch slot by one
+  // candidate, in the order 0 1 2 3 3 2 1 0 so that a drift of the work from
+  // one iteration to the next cancels; each launch is timed with CUDA
+  // events and its time divided by the work it did (rows x iterations of
+  // its systems); the two costs of a candidate are averaged and every slot
+  // keeps its cheapest scale (part of the graph key).
+  static constexpr int NCAND = 4;
+  static constexpr int NTUNE = 1 + 2 * NCAND;  // iterations the tuner takes
+  static int tune_cand(int step) {             // candidate of a tuning step (-1: warm-up)
+    return step == 0 ? -1 : (step <= NCAND ? step - 1 : 2 * NCAND - step);
+  }
+  double scale[NSLOT] = {1, 1, 1, 1, 1, 1, 1, 1, 1};  // current team-size scale
+  double cost[NSLOT][NCAND] = {};  // ms per unit of work, per candidate
+  int tune_step = 0;               // tuning iterations done
+  bool tuned = false;
+  bool tune_off = false;           // autotuner switched off: every scale 1
+  bool timing = false;             // this iteration records per-slot events
+  cudaEvent_t ev[NSLOT][2] = {};
+  bool slot_used[NSLOT] = {};
+  std::vector<std::pair<int, int>> slot_sys[NSLOT];  // (member, 0 momentum / 1 p') per system
   int reserve(rbffd_ctx *c, int members);
   void drop_graph();
   ~BatchScratch();

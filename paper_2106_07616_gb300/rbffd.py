@@ -135,6 +135,8 @@ def load(path: str = LIB_PATH):
         "rbffd_batch_destroy": (None, [vp]),
         "rbffd_batch_iterate": (C.c_int, [vp, C.POINTER(StepParams), vp, vp, vp, vp, vp]),
         "rbffd_batch_graph_stats": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
+        "rbffd_batch_tuning": (C.c_int, [vp, C.POINTER(i32), C.POINTER(dbl), C.POINTER(dbl)]),
+        "rbffd_batch_set_autotune": (C.c_int, [vp, C.c_int]),
         "rbffd_server_create": (C.c_int, [vp, C.POINTER(ServerParams), C.POINTER(vp)]),
         "rbffd_server_submit": (C.c_int, [vp, C.POINTER(ProblemDesc), C.POINTER(SolveParams),
                                           C.POINTER(C.c_uint64)]),
@@ -445,6 +447,19 @@ class Batch:
         _check(load().rbffd_batch_graph_stats(self.h, C.byref(c), C.byref(r), C.byref(k)),
                "rbffd_batch_graph_stats")
         return c.value, r.value, k.value
+
+    def tuning(self):
+        """(tuned, team-size scale per launch slot, cost table 9 x 4) of the
+        work-list autotuner (rbffd_batch_tuning)."""
+        t = C.c_int32(0)
+        sc = (C.c_double * 9)()
+        cost = (C.c_double * 36)()
+        _check(load().rbffd_batch_tuning(self.h, C.byref(t), sc, cost), "rbffd_batch_tuning")
+        return bool(t.value), list(sc), np.array(list(cost)).reshape(9, 4)
+
+    def set_autotune(self, on):
+        """Switch the work-list autotuner on (restart it) or off (scale 1)."""
+        _check(load().rbffd_batch_set_autotune(self.h, 1 if on else 0), "rbffd_batch_set_autotune")
 
 
 def amg_analyze(rowptr, col, val):

@@ -24,6 +24,7 @@ def test_batch_matches_members_solved_alone():
             P.simple_iterate(fp.dt)
     # all members in one batch, each with its own dt, three outer iterations
     B = rbffd.Batch(ctx(), [rbffd.Problem(ctx(), fp) for fp in fps])
+    B.set_autotune(False)  # its iterations run directly: the graph counts below assume none
     for r in range(3):
         d, its, status = B.iterate([fp.dt for fp in fps])
         assert np.all(status == 0)
@@ -45,6 +46,7 @@ def test_batch_graph_captured_again_after_a_reload():
     fps = [clouds.kovasznay(30, dt=0.4), clouds.cavity(24, seed=3, dt=0.05)]
     alone = [rbffd.Problem(ctx(), fp, precond=rbffd.PRECOND_AMG) for fp in fps]
     B = rbffd.Batch(ctx(), [rbffd.Problem(ctx(), fp, precond=rbffd.PRECOND_AMG) for fp in fps])
+    B.set_autotune(False)
     dts = [fp.dt for fp in fps]
     for _ in range(2):
         B.iterate(dts)
@@ -71,6 +73,40 @@ def test_batch_graph_captured_again_after_a_reload():
         for k in ("u", "v", "p"):
             e = rel_l2(B.problems[i].get(k), alone[i].get(k))
             assert e <= 1e-8, (i, k, e)
+    B.close()
+
+
+def test_batch_autotuner_keeps_results_and_then_captures():
+    """The first nine iterations (one untimed, then four team sizes per launch
+    slot, each twice, mirrored order; all run directly) tune the work lists;
+    each slot keeps its cheapest.  Results stay those of the
+    members solved alone; the iterations after tuning are captured and
+    replayed as before."""
+    fps = members()
+    alone = [rbffd.Problem(ctx(), fp) for fp in fps]
+    B = rbffd.Batch(ctx(), [rbffd.Problem(ctx(), fp) for fp in fps])
+    for r in range(12):
+        d, its, status = B.iterate([fp.dt for fp in fps])
+        assert np.all(status == 0)
+        for fp, P in zip(fps, alone):
+            P.simple_iterate(fp.dt)
+        tuned, scales, cost = B.tuning()
+        assert tuned == (r >= 8), (r, tuned)
+    for i in range(len(fps)):
+        for k in ("u", "v", "p"):
+            e = rel_l2(B.problems[i].get(k), alone[i].get(k))
+            assert e <= 1e-8, (i, k, e)
+    # slots 0 (momentum, two right-hand sides) and 2 (p' Jacobi BiCGSTAB)
+    # ran: every candidate has a cost, the kept scale is the cheapest
+    cand = [1.0, 2.0, 0.5, 4.0]
+    for k in (0, 2):
+        assert np.all(cost[k] > 0), (k, cost[k])
+        assert scales[k] == cand[int(np.argmin(cost[k]))], (k, scales[k], cost[k])
+    assert all(s in cand for s in scales)
+    # iterations 10 (first of this set), 11 (captured), 12 (replayed)
+    assert B.graph_stats()[:2] == (1, 1)
+    B.set_autotune(False)
+    assert B.tuning()[0] is False and B.tuning()[1] == [1.0] * 9
     B.close()
 
 
