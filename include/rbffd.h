@@ -286,6 +286,35 @@ int rbffd_problem_amg_info(const rbffd_problem *prob, int32_t *levels, int32_t *
 int rbffd_amg_analyze(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
                       int32_t *levels, int32_t *rows, int64_t *nnz, double *setup_ms);
 
+/* The composed V-cycle (the library's own regrouping of the cycle above; no
+ * counterpart in the paper, whose preconditioner is unspecified).  The
+ * smoothing-folded V-cycle is one linear map of its right-hand side: below
+ * level 1, every deeper right-hand side is b_l = Rh_l b_1 with Rh_l the
+ * restriction straight from level 1, and the corrections of all deeper
+ * levels prolong to level 1 at once through Q = [Q_2 | Q_3 | ...].  The
+ * launches whose shared memory holds the stacked coarse vector (levels 2 to
+ * L-1, nc entries) run the cycle in four dependent phases instead of
+ * 2 L - 1, the others level by level; both give the same result up to
+ * rounding.  Built for hierarchies of three or more levels. */
+/* Whether hierarchies built on this context from now on get the composed
+ * cycle (on != 0: yes, the default).  Errors: RBFFD_EINVAL. */
+int rbffd_ctx_set_amg_compose(rbffd_ctx *ctx, int on);
+/* The problem's composed cycle (finishes a build still running first):
+ * *coarse_entries (nc; 0: not built), *chunks of its stacked restriction,
+ * *restrict_nnz and *q_nnz its entries (all nullable).  Zeros with Jacobi.
+ * Errors: RBFFD_EINVAL, the hierarchy build's errors. */
+int rbffd_problem_amg_cycle(const rbffd_problem *prob, int32_t *coarse_entries, int32_t *chunks,
+                            int64_t *restrict_nnz, int64_t *q_nnz);
+/* One cycle of the hierarchy of a CSR matrix (host arrays as in
+ * rbffd_amg_analyze) applied to b[n] on the host in FP64, level by level
+ * into out_levels[n] and composed into out_composed[n] (zeros when the
+ * composed cycle is not built for this matrix); *coarse_entries and
+ * *chunks as above (nullable).  No device work.  Errors: RBFFD_EINVAL, the
+ * build's errors. */
+int rbffd_amg_cycle_host(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                         const double *b, double *out_levels, double *out_composed,
+                         int32_t *coarse_entries, int32_t *chunks);
+
 typedef struct {
   double dt;             /* time step */
   double alpha[3];       /* BDF2: 1.5, -2, 0.5 (paper Sec. 3) */

@@ -620,9 +620,200 @@ int build_hierarchy(Csr A0, Hierarchy &H) {
   return RBFFD_OK;
 }
 
-void fill_info(const Hierarchy &H, double ms, AmgInfo *info) {
+// ---- the composed cycle (amg.cuh): the folded V-cycle is one linear map;
+// below level 1 it regroups as
+//   y_1 = S_1 b_1 + sum_{l >= 2} Q_l b_l,   b_l = Rh_l b_1,
+// with Rh_2 = R~_1, Rh_l = R~_{l-1} Rh_{l-1} (restriction straight from
+// level 1), Q_l = P~_1 ... P~_{l-1} S_l and, on the coarsest level,
+// P~_1 ... P~_{L-2} A_{L-1}^-1 (the corrections prolonged to level 1): the
+// same sums as the level-by-level cycle, so that its 2 L - 1 dependent
+// phases become four.  The rows of the stacked Rh are cut into chunks of at
+// most AMG_RCHUNK entries, each summed by one warp; coarse entry k is the
+// sum of its chunks in order.
+struct Composed {
+  Csr R;                               // Nc x n1: Rh_2; Rh_3; ... stacked
+  Csr Q;                               // n1 x Nc: [Q_2 | Q_3 | ...]
+  std::vector<int32_t> cs, kc;         // chunk c: entries [cs[c], cs[c+1]); entry k: chunks [kc[k], kc[k+1])
+  std::vector<int> seg_off, seg_grp;   // level s + 2: entries [seg_off[s], seg_off[s+1]); lanes per entry
+};
+
+// M * D with D dense row-major (m x m), every product kept
+Csr times_dense(const Csr &M, const std::vector<double> &D, int m) {
+  Csr C;
+  C.n = M.n;
+  C.m = m;
+  C.ptr.resize(M.n + 1);
+  for (int i = 0; i <= M.n; ++i) C.ptr[i] = i * m;
+  C.col.resize((size_t)M.n * m);
+  C.val.assign((size_t)M.n * m, 0.0);
+#pragma omp parallel for schedule(static) if (par(M.nnz() * m))
+  for (int i = 0; i < M.n; ++i) {
+    double *o = C.val.data() + (size_t)i * m;
+    for (int j = 0; j < m; ++j) C.col[(size_t)i * m + j] = j;
+    for (int k = M.ptr[i]; k < M.ptr[i + 1]; ++k) {
+      const double a = M.val[k];
+      const double *d = D.data() + (size_t)M.col[k] * m;
+      for (int j = 0; j < m; ++j) o[j] += a * d[j];
+    }
+  }
+  return C;
+}
+
+// Rows of A (n x ma), then of B (n x mb) as columns ma.. : [A | B]
+Csr hcat(const Csr &A, const Csr &B) {
+  Csr C;
+  C.n = A.n;
+  C.m = A.m + B.m;
+  C.ptr.assign(A.n + 1, 0);
+  for (int i = 0; i < A.n; ++i)
+    C.ptr[i + 1] = C.ptr[i] + (A.ptr[i + 1] - A.ptr[i]) + (B.ptr[i + 1] - B.ptr[i]);
+  C.col.resize(C.ptr[A.n]);
+  C.val.resize(C.ptr[A.n]);
+  for (int i = 0; i < A.n; ++i) {
+    int o = C.ptr[i];
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) C.col[o] = A.col[k], C.val[o++] = A.val[k];
+    for (int k = B.ptr[i]; k < B.ptr[i + 1]; ++k) C.col[o] = A.m + B.col[k], C.val[o++] = B.val[k];
+  }
+  return C;
+}
+
+// The composed operators, for hierarchies of three or more levels (with two
+// the cycle already has four phases or fewer); false: the level-by-level
+// cycle only.  The products are level-1-sized: small next to the build.
+bool compose(const Hierarchy &H, Composed &C) {
+  const int L = (int)H.A.size();
+  if (L < 3) return false;
+  // stacked Rh_2 .. Rh_{L-1}, each n_l x n_1
+  C = Composed();
+  C.R.m = H.A[1].n;
+  C.R.ptr.assign(1, 0);
+  C.seg_off.assign(1, 0);
+  Csr Rh;
+  for (int l = 2; l < L; ++l) {
+    Rh = l == 2 ? H.R[1] : spgemm(H.R[l - 1], Rh);
+    for (int i = 0; i < Rh.n; ++i) C.R.ptr.push_back(C.R.ptr.back() + Rh.ptr[i + 1] - Rh.ptr[i]);
+    C.R.col.insert(C.R.col.end(), Rh.col.begin(), Rh.col.end());
+    C.R.val.insert(C.R.val.end(), Rh.val.begin(), Rh.val.end());
+    C.R.n += Rh.n;
+    C.seg_off.push_back(C.R.n);
+  }
+  // Q = [Q_2 | ... | Q_{L-1}] on level 1's rows; M = P~_1 ... P~_{l-1}
+  Csr M = H.P[1], Q;
+  for (int l = 2; l < L; ++l) {
+    const Csr Ql = l + 1 < L ? spgemm(M, H.S[l]) : times_dense(M, H.cinv, H.A[l].n);
+    Q = l == 2 ? Ql : hcat(Q, Ql);
+    if (l + 1 < L) M = spgemm(M, H.P[l]);
+  }
+  C.Q = std::move(Q);
+  // chunks: a row of length len in ceil(len / AMG_RCHUNK) near-equal pieces
+  C.cs.assign(1, 0);
+  C.kc.assign(1, 0);
+  std::vector<int> maxch(L, 1);
+  for (int k = 0, s = 0; k < C.R.n; ++k) {
+    while (k >= C.seg_off[s + 1]) ++s;
+    const int a = C.R.ptr[k], len = C.R.ptr[k + 1] - a;
+    const int nch = std::max(1, (len + AMG_RCHUNK - 1) / AMG_RCHUNK);
+    for (int j = 1; j <= nch; ++j) C.cs.push_back(a + (int)((long long)len * j / nch));
+    C.kc.push_back(C.kc.back() + nch);
+    maxch[s] = std::max(maxch[s], nch);
+  }
+  // lanes per coarse entry summing its chunks: at most 4 loads a lane
+  C.seg_grp.assign(L - 2, 1);
+  for (int s = 0; s + 2 < L; ++s) {
+    int g = 1;
+    while (g < 32 && (maxch[s] + g - 1) / g > 4) g *= 2;
+    C.seg_grp[s] = g;
+  }
+  return true;
+}
+
+// The per-level V-cycle and the composed one applied on the host in FP64
+// (a check of the composition: the two agree to rounding).  The composed
+// form sums in the device's order: chunk by chunk, then the chunks of an
+// entry in order.
+void cycle_levels(const Hierarchy &H, const std::vector<double> &b0, std::vector<double> &out) {
+  const int L = (int)H.A.size();
+  auto mv = [](const Csr &M, const std::vector<double> &x) {
+    std::vector<double> y(M.n, 0.0);
+    for (int i = 0; i < M.n; ++i)
+      for (int k = M.ptr[i]; k < M.ptr[i + 1]; ++k) y[i] += M.val[k] * x[M.col[k]];
+    return y;
+  };
+  auto smooth0 = [&](const std::vector<double> &b) {  // S_0 = 2 W - W A W
+    const std::vector<double> &w = H.W[0];
+    const Csr &A = H.A[0];
+    std::vector<double> y(A.n, 0.0);
+    for (int i = 0; i < A.n; ++i) {
+      double t = 2.0 * w[i] * b[i];
+      for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) t -= w[i] * A.val[k] * w[A.col[k]] * b[A.col[k]];
+      y[i] = t;
+    }
+    return y;
+  };
+  auto dense = [&](const std::vector<double> &b) {
+    const int m = (int)b.size();
+    std::vector<double> y(m, 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) y[i] += H.cinv[(size_t)i * m + j] * b[j];
+    return y;
+  };
+  if (L == 1) {
+    out = dense(b0);
+    return;
+  }
+  std::vector<std::vector<double>> z(L), b(L);
+  b[0] = b0;
+  for (int l = 0; l + 1 < L; ++l) {
+    z[l] = l == 0 ? smooth0(b[0]) : mv(H.S[l], b[l]);
+    b[l + 1] = mv(H.R[l], b[l]);
+  }
+  std::vector<double> y = dense(b[L - 1]);
+  for (int l = L - 2; l >= 0; --l) {
+    std::vector<double> t = mv(H.P[l], y);
+    for (size_t i = 0; i < t.size(); ++i) t[i] += z[l][i];
+    y = std::move(t);
+  }
+  out = std::move(y);
+}
+
+void cycle_composed(const Hierarchy &H, const Composed &C, const std::vector<double> &b0,
+                    std::vector<double> &out) {
+  auto mv = [](const Csr &M, const std::vector<double> &x) {
+    std::vector<double> y(M.n, 0.0);
+    for (int i = 0; i < M.n; ++i)
+      for (int k = M.ptr[i]; k < M.ptr[i + 1]; ++k) y[i] += M.val[k] * x[M.col[k]];
+    return y;
+  };
+  const std::vector<double> b1 = mv(H.R[0], b0);
+  const int nch = (int)C.cs.size() - 1;
+  std::vector<double> part(nch, 0.0), cv(C.R.n, 0.0);
+  for (int c = 0; c < nch; ++c)
+    for (int k = C.cs[c]; k < C.cs[c + 1]; ++k) part[c] += C.R.val[k] * b1[C.R.col[k]];
+  for (int k = 0; k < C.R.n; ++k)
+    for (int c = C.kc[k]; c < C.kc[k + 1]; ++c) cv[k] += part[c];
+  std::vector<double> y1 = mv(H.S[1], b1);
+  const std::vector<double> q = mv(C.Q, cv);
+  for (size_t i = 0; i < y1.size(); ++i) y1[i] += q[i];
+  const std::vector<double> &w = H.W[0];
+  const Csr &A = H.A[0];
+  out.assign(A.n, 0.0);
+  for (int i = 0; i < A.n; ++i) {
+    double t = 2.0 * w[i] * b0[i];
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) t -= w[i] * A.val[k] * w[A.col[k]] * b0[A.col[k]];
+    for (int k = H.P[0].ptr[i]; k < H.P[0].ptr[i + 1]; ++k) t += H.P[0].val[k] * y1[H.P[0].col[k]];
+    out[i] = t;
+  }
+}
+
+void fill_info(const Hierarchy &H, double ms, AmgInfo *info, const Composed *C = nullptr) {
   if (!info) return;
   memset(info, 0, sizeof(*info));
+  if (C) {
+    info->comp_nc = C->R.n;
+    info->comp_chunks = (int)C->cs.size() - 1;
+    info->comp_nnz_r = C->R.nnz();
+    info->comp_nnz_q = C->Q.nnz();
+  }
   const int L = (int)H.A.size();
   info->nlev = L;
   info->setup_ms = ms;
@@ -690,7 +881,34 @@ int amg_analyze(int n, const int32_t *rowptr, const int32_t *col, const double *
   A.val.assign(val, val + rowptr[n]);
   Hierarchy H;
   RBFFD_TRY(build_hierarchy(std::move(A), H));
-  fill_info(H, ms_since(t0), info);
+  Composed C;
+  const bool comp = compose(H, C);
+  fill_info(H, ms_since(t0), info, comp ? &C : nullptr);
+  return RBFFD_OK;
+}
+
+int amg_cycle_host(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                   const double *b, double *out_levels, double *out_composed, AmgInfo *info) {
+  Csr A;
+  A.n = A.m = n;
+  A.ptr.assign(rowptr, rowptr + n + 1);
+  A.col.assign(col, col + rowptr[n]);
+  A.val.assign(val, val + rowptr[n]);
+  Hierarchy H;
+  RBFFD_TRY(build_hierarchy(std::move(A), H));
+  Composed C;
+  const bool comp = compose(H, C);
+  fill_info(H, 0.0, info, comp ? &C : nullptr);
+  const std::vector<double> b0(b, b + n);
+  std::vector<double> y;
+  cycle_levels(H, b0, y);
+  std::copy(y.begin(), y.end(), out_levels);
+  if (comp) {
+    cycle_composed(H, C, b0, y);
+    std::copy(y.begin(), y.end(), out_composed);
+  } else {
+    std::fill(out_composed, out_composed + n, 0.0);
+  }
   return RBFFD_OK;
 }
 
@@ -705,6 +923,10 @@ struct CsrOff {
 struct LevelOff {
   CsrOff S, R, P;
   size_t b = 0, z = 0, y = 0;
+};
+struct CompOff {
+  size_t rcol = 0, rval = 0, cs = 0, kc = 0, part = 0;
+  CsrOff Q;
 };
 
 struct AmgJob {
@@ -722,6 +944,10 @@ struct AmgJob {
   size_t o_dev = 0, o_s0 = 0, o_a0 = 0, o_cinv = 0;
   int ts0 = 1;
   bool low = false;  // the cycle's type is FP32
+  bool compose = true;  // build the composed cycle when it pays
+  bool comp = false;    // built
+  Composed C;
+  CompOff coff;
 };
 
 namespace {
@@ -755,6 +981,7 @@ int host_part(AmgJob &J) {
   Hierarchy &H = J.H;
   RBFFD_TRY(build_hierarchy(from_ell(n, q, ldn, hcol, hval), H));
   const int L = (int)H.A.size();
+  J.comp = J.compose && compose(H, J.C);
   // level 0's S in the solve's ELL layout: s_e = -w_i a_e w_c (+ 2 w_i on the diagonal)
   std::vector<double> s0((size_t)q * ldn, 0.0);
   {
@@ -817,6 +1044,15 @@ int host_part(AmgJob &J) {
       off[l].y = S.take(sizeof(T) * H.A[l].n);
     }
     J.o_cinv = S.put_as<T>(H.cinv);
+    if (J.comp) {
+      CompOff &co = J.coff;
+      co.rcol = S.put(J.C.R.col);
+      co.rval = S.put_as<T>(J.C.R.val);
+      co.cs = S.put(J.C.cs);
+      co.kc = S.put(J.C.kc);
+      co.Q = put_csr(J.C.Q, lanes_alone(shape(J.C.Q), W));
+      co.part = S.take(sizeof(T) * (J.C.cs.size() - 1));
+    }
   }
   J.host_ms = ms_since(t0);
   return RBFFD_OK;
@@ -843,6 +1079,7 @@ int amg_build_begin(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
   J->wpb = wpb;
   J->dcol = col;
   J->dval = val;
+  J->compose = ctx->amg_compose;
   if (cudaEventCreateWithFlags(&J->ready, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventRecord(J->ready, ctx->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -919,6 +1156,22 @@ int amg_build_end(rbffd_ctx *ctx, AmgJob **job, void **mem, size_t *bytes,
     v.z = (T *)(base + o.z);
     v.y = (T *)(base + o.y);
   }
+  if (J->comp) {
+    const Composed &C = J->C;
+    const CompOff &co = J->coff;
+    AmgCompT<T> &m = h.comp;
+    m.nc = C.R.n;
+    m.nchunk = (int)C.cs.size() - 1;
+    m.nseg = (int)C.seg_grp.size();
+    for (int s = 0; s <= m.nseg; ++s) m.seg_off[s] = C.seg_off[s];
+    for (int s = 0; s < m.nseg; ++s) m.seg_grp[s] = C.seg_grp[s];
+    m.rcol = (const int32_t *)(base + co.rcol);
+    m.rval = (const T *)(base + co.rval);
+    m.cs = (const int32_t *)(base + co.cs);
+    m.kc = (const int32_t *)(base + co.kc);
+    m.Q = csr_at(co.Q, true);
+    m.part = (T *)(base + co.part);
+  }
   memcpy(S.buf + J->o_dev, &h, sizeof(h));
   if (cudaMemcpyAsync(dmem, S.buf, S.size, cudaMemcpyHostToDevice, ctx->stream) !=
           cudaSuccess ||
@@ -931,7 +1184,7 @@ int amg_build_end(rbffd_ctx *ctx, AmgJob **job, void **mem, size_t *bytes,
   *bytes = S.size;
   *dev = (const AmgDevT<T> *)(base + J->o_dev);
   if (host_view) *host_view = h;
-  fill_info(H, J->host_ms, info);
+  fill_info(H, J->host_ms, info, J->comp ? &J->C : nullptr);
   return RBFFD_OK;
 }
 

@@ -11,6 +11,7 @@ namespace rbffd {
 
 constexpr int AMG_MAXLEV = 10;
 constexpr int AMG_CSR_CHUNK = 8;  // entries a lane loads before its gathers (CSR rows)
+constexpr int AMG_RCHUNK = 32 * AMG_CSR_CHUNK;  // entries of a composed-restriction chunk
 
 // Arithmetic of the V-cycle (operators, dense inverse, level vectors): a
 // type parameter T; the vectors it reads and writes on level 0 may be FP64
@@ -48,6 +49,36 @@ struct AmgLevelT {
   T *y;             // the level's result
 };
 
+// The composed cycle.  The folded V-cycle above is one linear map; below
+// level 1 it regroups as
+//   y_1 = S_1 b_1 + sum_{l >= 2} Q_l b_l,   b_l = Rh_l b_1,
+//   Rh_2 = R~_1,  Rh_l = R~_{l-1} Rh_{l-1}  (restriction straight from level 1),
+//   Q_l = P~_1 ... P~_{l-1} S_l, and on the coarsest level
+//   P~_1 ... P~_{L-2} A_{L-1}^-1            (corrections prolonged to level 1),
+// four dependent phases instead of 2 L - 1: (A) z_0 = S_0 b_0 and
+// b_1 = R~_0 b_0 as before; (B1) z_1 = S_1 b_1 and every deeper right-hand
+// side at once, as partial sums of chunks of the stacked Rh (each chunk one
+// warp's, AMG_RCHUNK entries at most); (B2) every CTA sums the chunks of all
+// coarse entries into shared memory (the coarse vector c, nc entries) and
+// y_1 = z_1 + Q c on level 1's rows, Q = [Q_2 | Q_3 | ...]; (C) the
+// prolongation to level 0 as before.  Built on the host for three or more
+// levels (amg.cu: compose); run by launches whose dynamic shared memory
+// holds c, the others run the level-by-level cycle.
+template <typename T>
+struct AmgCompT {
+  int nc;                      // coarse entries: rows of levels 2 .. L-1 (0: none)
+  int nchunk;                  // chunks of the stacked Rh
+  int nseg;                    // levels stacked
+  int seg_off[AMG_MAXLEV + 1];  // level s + 2: entries [seg_off[s], seg_off[s + 1])
+  int seg_grp[AMG_MAXLEV];     // lanes per entry summing its chunks (1..32)
+  const int32_t *rcol;         // stacked Rh: column (level 1) and value of each entry
+  const T *rval;
+  const int32_t *cs;           // chunk c: entries [cs[c], cs[c + 1])
+  const int32_t *kc;           // entry k: chunks [kc[k], kc[k + 1])
+  AmgCsrT<T> Q;                // n_1 x nc
+  T *part;                     // chunk sums (phase A)
+};
+
 template <typename T>
 struct AmgDevT {
   using value_type = T;
@@ -57,6 +88,7 @@ struct AmgDevT {
   int ts0;          // threads per row of level 0's S in the cycle (1..8)
   const T *a0;      // level 0's A rounded to T, same layout (FP32 only, else null)
   AmgLevelT<T> lev[AMG_MAXLEV];
+  AmgCompT<T> comp;
 };
 
 using amg_t = double;  // the cycle inside BiCGSTAB
@@ -73,6 +105,10 @@ struct AmgInfo {
   long long nnz_p[AMG_MAXLEV];  // P~_l
   double omega[AMG_MAXLEV];
   double setup_ms;              // host time of the hierarchy build
+  int comp_nc;                  // composed cycle: stacked coarse entries (0: not built)
+  int comp_chunks;              // chunks of its stacked restriction
+  long long comp_nnz_r;         // entries of the stacked restriction
+  long long comp_nnz_q;         // entries of Q
 };
 
 // Build the hierarchy of the packed p' matrix (ELL, column-major [q][ldn],
@@ -92,5 +128,11 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
 // and nonzeros in *info.
 int amg_analyze(int n, const int32_t *rowptr, const int32_t *col, const double *val,
                 AmgInfo *info);
+
+// One cycle of the hierarchy of a CSR matrix applied to b on the host in
+// FP64, level by level (out_levels) and composed (out_composed; zeros when
+// the composed cycle is not built), n entries each.
+int amg_cycle_host(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                   const double *b, double *out_levels, double *out_composed, AmgInfo *info);
 
 }  // namespace rbffd

@@ -7,6 +7,9 @@
 // cycle for L levels.  b_0 (the BiCGSTAB vector p or s) must be published
 // (an exchange since it was written) before the call.
 //
+// With the composed operators (AmgCompT) and room for the coarse vector in
+// the launch's shared memory, the same cycle runs in four phases.
+//
 // Level 0's S uses the solve's ELL columns (T threads per row); the CSR
 // operators use grp lanes per row.  The cycle computes in the hierarchy's
 // value type T (FP64 or FP32, see amg.cuh); it reads b_0 and writes its
@@ -93,6 +96,68 @@ __device__ __forceinline__ void coarse_solve(const AmgDevT<T> *__restrict__ G, i
   }
 }
 
+// ---- the composed cycle (amg.cuh: AmgCompT)
+
+// Chunk sums of the stacked restriction applied to b_1: warp w of the
+// launch (in the order given) takes chunks w, w + nwarps, ...; a chunk
+// holds at most AMG_RCHUNK = 32 x CC entries, one load of CC per lane.
+template <typename T, typename XT>
+__device__ __forceinline__ void comp_chunks(const AmgCompT<T> &C, const XT *b1, int wglobal,
+                                            int nwarps) {
+  const int lane = threadIdx.x & 31;
+  for (int ch = wglobal; ch < C.nchunk; ch += nwarps) {
+    const int s = __ldg(C.cs + ch), e = __ldg(C.cs + ch + 1);
+    int cc[CC];
+    T a[CC];
+#pragma unroll
+    for (int u = 0; u < CC; ++u) {
+      const int k = s + lane + 32 * u;
+      cc[u] = k < e ? __ldg(C.rcol + k) : -1;
+      a[u] = k < e ? __ldg(C.rval + k) : T(0);
+    }
+    T t = 0;
+#pragma unroll
+    for (int u = 0; u < CC; ++u)
+      if (cc[u] >= 0) t += a[u] * T(__ldcg(b1 + cc[u]));
+    t = kdev::wsum(t);
+    if (lane == 0) C.part[ch] = t;
+  }
+}
+
+// The coarse vector: every CTA sums the chunks of all nc entries, in order,
+// into its dynamic shared memory (all threads of the CTA; ends with a
+// barrier).  Level s + 2's entries take seg_grp[s] lanes each.
+template <typename T>
+__device__ __forceinline__ const T *comp_gather(const AmgCompT<T> &C) {
+  T *cv = reinterpret_cast<T *>(kdev::kdev_dyn);
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  __syncthreads();  // the buffer's previous use
+  for (int s = 0; s < C.nseg; ++s) {
+    const int G = C.seg_grp[s], rpw = 32 / G, g = lane / G, lg = lane - g * G;
+    const int k1 = C.seg_off[s + 1];
+    for (int base = C.seg_off[s] + wl * rpw; base < k1; base += wpb * rpw) {
+      const int k = base + g;
+      T t = 0;
+      if (k < k1) {
+        const int c1 = __ldg(C.kc + k + 1);
+#pragma unroll 4
+        for (int ch = __ldg(C.kc + k) + lg; ch < c1; ch += G) t += __ldcg(C.part + ch);
+      }
+      for (int o = G >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (k < k1 && lg == 0) cv[k] = t;
+    }
+  }
+  __syncthreads();
+  return cv;
+}
+
+// the launch runs the composed cycle: built, and its shared memory holds c
+template <typename T>
+__device__ __forceinline__ bool comp_fits(const AmgDevT<T> *__restrict__ G) {
+  const int nc = G->comp.nc;
+  return nc > 0 && kdev::dyn_smem_bytes() >= (unsigned int)nc * (unsigned int)sizeof(T);
+}
+
 // out = V-cycle(b0)
 template <typename T, typename XT, typename OT>
 __device__ __forceinline__ bool vcycle(const AmgDevT<T> *__restrict__ G, const Ctx &c,
@@ -111,6 +176,43 @@ __device__ __forceinline__ bool vcycle(const AmgDevT<T> *__restrict__ G, const C
   const int wpb = blockDim.x >> 5, nbk = c.nwarps / wpb;
   const int cta = c.wglobal / wpb, wl = c.wglobal - cta * wpb;
   const int wfw = wl * nbk + cta, wbw = (wpb - 1 - wl) * nbk + cta;
+  if (comp_fits(G)) {
+    const AmgCompT<T> &C = G->comp;
+    const AmgLevelT<T> &L0 = G->lev[0];
+    const AmgLevelT<T> &L1 = G->lev[1];
+    T *z0 = L0.z;
+    T *b1 = L1.b;
+    T *z1 = L1.z;
+    T *y1 = L1.y;
+    const int n1 = L1.n;
+    // (A) z_0 = S_0 b_0 on this CTA's rows, b_1 = R~_0 b_0
+    {
+      const XT *xs[1] = {b0};
+      kdev::spmv_rows<1, T>(c.n, c.q, c.ldn, G->ts0, c.col, G->s0, xs, c.wglobal, c.nwarps,
+                            [&](int i, const T *sb) { z0[i] = sb[0]; });
+      csr_rows(L0.R, n1, b0, wbw, c.nwarps, [&](int k, T t) { b1[k] = t; });
+    }
+    if (!sync(c, epoch)) return false;
+    // (B1) z_1 = S_1 b_1; every deeper right-hand side as chunk sums
+    csr_rows(L1.S, n1, (const T *)b1, wfw, c.nwarps, [&](int i, T t) { z1[i] = t; });
+    comp_chunks(C, (const T *)b1, wbw, c.nwarps);
+    if (!sync(c, epoch)) return false;
+    // (B2) the coarse vector in shared memory, y_1 = z_1 + Q c
+    {
+      const T *cv = comp_gather(C);
+      csr_rows(
+          C.Q, n1, cv, wfw, c.nwarps, [&](int i, T t) { y1[i] = t; }, (const T *)z1, cv, C.nc);
+    }
+    if (!sync(c, epoch)) return false;
+    // (C) out = z_0 + P~_0 y_1
+    {
+      const T *ys = kdev::win_cap() >= n1 ? kdev::win_stage<T>(y1, 0, n1) : nullptr;
+      csr_rows(
+          L0.P, L0.n, (const T *)y1, wfw, c.nwarps, [&](int i, T t) { out[i] = OT(t); },
+          (const T *)z0, ys, ys ? n1 : 0);
+    }
+    return sync(c, epoch);
+  }
   for (int l = 0; l + 1 < L; ++l) {
     const AmgLevelT<T> &Lv = G->lev[l];
     const AmgLevelT<T> &Nx = G->lev[l + 1];

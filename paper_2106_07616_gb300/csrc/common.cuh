@@ -23,6 +23,9 @@ struct rbffd_ctx {
   // device-side waits of this context's launches: 2^wait_log2 cycles (0:
   // the default 2^31), rbffd_ctx_set_wait_limit
   int wait_log2 = 0;
+  // multigrid hierarchies built on this context get the composed cycle when
+  // it pays (rbffd_ctx_set_amg_compose)
+  bool amg_compose = true;
   // pinned host scratch for small read-backs
   void *pinned = nullptr;
   size_t pinned_bytes = 0;

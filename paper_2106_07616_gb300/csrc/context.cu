@@ -149,6 +149,14 @@ extern "C" int rbffd_ctx_set_wait_limit(rbffd_ctx *ctx, int32_t log2_cycles) {
   });
 }
 
+extern "C" int rbffd_ctx_set_amg_compose(rbffd_ctx *ctx, int on) {
+  return guarded([&]() -> int {
+    if (!ctx) return RBFFD_EINVAL;
+    ctx->amg_compose = on != 0;
+    return RBFFD_OK;
+  });
+}
+
 extern "C" int rbffd_ctx_profile(rbffd_ctx *ctx, int enable) {
   return guarded([&]() -> int {
     if (!ctx) return RBFFD_EINVAL;

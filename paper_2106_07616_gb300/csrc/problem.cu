@@ -765,6 +765,43 @@ extern "C" int rbffd_amg_analyze(int32_t n, const int32_t *rowptr, const int32_t
   });
 }
 
+extern "C" int rbffd_problem_amg_cycle(const rbffd_problem *P, int32_t *coarse_entries,
+                                       int32_t *chunks, int64_t *restrict_nnz,
+                                       int64_t *q_nnz) {
+  return guarded([&]() -> int {
+    if (!P) return RBFFD_EINVAL;
+    RBFFD_CK(cudaSetDevice(P->ctx->device));
+    RBFFD_TRY(amg_ready(const_cast<rbffd_problem *>(P)));
+    const bool have = P->amg != nullptr || P->amgf != nullptr;
+    const AmgInfo &I = P->amg_info;
+    if (coarse_entries) *coarse_entries = have ? I.comp_nc : 0;
+    if (chunks) *chunks = have ? I.comp_chunks : 0;
+    if (restrict_nnz) *restrict_nnz = have ? I.comp_nnz_r : 0;
+    if (q_nnz) *q_nnz = have ? I.comp_nnz_q : 0;
+    return RBFFD_OK;
+  });
+}
+
+extern "C" int rbffd_amg_cycle_host(int32_t n, const int32_t *rowptr, const int32_t *col,
+                                    const double *val, const double *b, double *out_levels,
+                                    double *out_composed, int32_t *coarse_entries,
+                                    int32_t *chunks) {
+  return guarded([&]() -> int {
+    if (n < 1 || !rowptr || !col || !val || !b || !out_levels || !out_composed ||
+        rowptr[0] != 0)
+      return RBFFD_EINVAL;
+    for (int i = 0; i < n; ++i)
+      if (rowptr[i + 1] < rowptr[i]) return RBFFD_EINVAL;
+    for (int k = 0; k < rowptr[n]; ++k)
+      if (col[k] < 0 || col[k] >= n) return RBFFD_EINVAL;
+    AmgInfo I;
+    RBFFD_TRY(amg_cycle_host(n, rowptr, col, val, b, out_levels, out_composed, &I));
+    if (coarse_entries) *coarse_entries = I.comp_nc;
+    if (chunks) *chunks = I.comp_chunks;
+    return RBFFD_OK;
+  });
+}
+
 extern "C" int simple_iterate(rbffd_problem *P, const rbffd_step_params *sp, double *delta_out,
                               rbffd_iter_stats *stats) {
   return guarded([&]() -> int {

@@ -127,6 +127,11 @@ def load(path: str = LIB_PATH):
                                      C.POINTER(SolveStats)]),
         "rbffd_steady_residual": (C.c_int, [vp, C.POINTER(dbl)]),
         "rbffd_ctx_set_wait_limit": (C.c_int, [vp, i32]),
+        "rbffd_ctx_set_amg_compose": (C.c_int, [vp, C.c_int]),
+        "rbffd_problem_amg_cycle": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64),
+                                              C.POINTER(i64)]),
+        "rbffd_amg_cycle_host": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, C.POINTER(i32),
+                                           C.POINTER(i32)]),
         "rbffd_get_field": (C.c_int, [vp, i32, vp]),
         "rbffd_set_field": (C.c_int, [vp, i32, vp]),
         "rbffd_get_operators": (C.c_int, [vp, vp, vp, vp, vp, vp]),
@@ -184,6 +189,12 @@ class Context:
         cycles, 0 for the default (rbffd_ctx_set_wait_limit)."""
         _check(load().rbffd_ctx_set_wait_limit(self.h, int(log2_cycles)),
                "rbffd_ctx_set_wait_limit")
+
+    def set_amg_compose(self, on: bool):
+        """Whether multigrid hierarchies built from now on get the composed
+        (three-phase) cycle when it pays (rbffd_ctx_set_amg_compose)."""
+        _check(load().rbffd_ctx_set_amg_compose(self.h, 1 if on else 0),
+               "rbffd_ctx_set_amg_compose")
 
     def close(self):
         if getattr(self, "h", None) is not None:
@@ -327,6 +338,16 @@ class Problem:
                "rbffd_problem_amg_info")
         levels = [(int(rows[i]), int(nnz[i])) for i in range(lv.value)]
         return (levels, ms.value) if with_time else levels
+
+    def amg_cycle(self):
+        """The composed multigrid cycle: dict of coarse entries (0: not
+        built), chunks, restriction and Q nonzeros (rbffd_problem_amg_cycle)."""
+        nc, ch = C.c_int32(0), C.c_int32(0)
+        nr, nq = C.c_int64(0), C.c_int64(0)
+        _check(load().rbffd_problem_amg_cycle(self.h, C.byref(nc), C.byref(ch), C.byref(nr),
+                                              C.byref(nq)), "rbffd_problem_amg_cycle")
+        return {"coarse_entries": nc.value, "chunks": ch.value, "restrict_nnz": nr.value,
+                "q_nnz": nq.value}
 
     def get(self, name, out=None):
         out = np.zeros(self.n) if out is None else out
@@ -474,6 +495,23 @@ def amg_analyze(rowptr, col, val):
     _check(load().rbffd_amg_analyze(rowptr.size - 1, ptr(rowptr), ptr(col), ptr(val),
                                     C.byref(lv), rows, nnz, C.byref(ms)), "rbffd_amg_analyze")
     return [(int(rows[i]), int(nnz[i])) for i in range(lv.value)], ms.value
+
+
+def amg_cycle_host(rowptr, col, val, b):
+    """One multigrid cycle of a CSR matrix's hierarchy applied to b on the
+    host in FP64, level by level and composed: (out_levels, out_composed,
+    coarse entries, chunks); out_composed is zeros when not built."""
+    rowptr = np.ascontiguousarray(rowptr, np.int32)
+    col = np.ascontiguousarray(col, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    n = rowptr.size - 1
+    ol, oc = np.zeros(n), np.zeros(n)
+    nc, ch = C.c_int32(0), C.c_int32(0)
+    _check(load().rbffd_amg_cycle_host(n, ptr(rowptr), ptr(col), ptr(val), ptr(b), ptr(ol),
+                                       ptr(oc), C.byref(nc), C.byref(ch)),
+           "rbffd_amg_cycle_host")
+    return ol, oc, nc.value, ch.value
 
 
 class Server:

@@ -91,3 +91,52 @@ def test_hierarchy_does_not_depend_on_the_thread_count(tmp_path):
         assert r.returncode == 0, r.stderr
         out.append(json.loads(r.stdout.strip().splitlines()[-1]))
     assert out[0] == out[1] and len(out[0]) >= 2 and out[0][0][1] > (1 << 17)
+
+
+def p_prime_csr(m):
+    fp = clouds.cavity(m, dt=0.05)
+    ops = oracle.Problem(fp).operators()
+    pv, idx = ops["pval"], ops["idx"]
+    keep = (pv != 0) | (idx == np.arange(fp.n)[:, None])
+    rowptr = np.concatenate([[0], np.cumsum(keep.sum(1))])
+    return rowptr, idx[keep], pv[keep]
+
+
+@pytest.mark.parametrize("which", ["cavity120", "poisson64"])
+def test_composed_cycle_equals_the_level_by_level_cycle(which):
+    """The folded V-cycle regrouped into three phases (restriction straight
+    from level 0 to every coarse level, all corrections prolonged to level 1
+    together) is the same linear map: both forms, applied on the host in
+    FP64 to random right-hand sides, agree to rounding."""
+    A = p_prime_csr(120) if which == "cavity120" else poisson5(64)
+    n = A[0].size - 1
+    levels = rbffd.amg_analyze(*A)[0]
+    assert len(levels) >= 3
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        b = rng.standard_normal(n)
+        yl, yc, nc, chunks = rbffd.amg_cycle_host(*A, b)
+        assert nc == sum(r for r, _ in levels[2:])  # levels 2 .. L-1 stacked
+        assert chunks >= nc
+        assert np.linalg.norm(yl) > 0
+        assert np.linalg.norm(yc - yl) <= 1e-12 * np.linalg.norm(yl)
+    # linear: the cycle of a combination is the combination of the cycles
+    b1, b2 = rng.standard_normal(n), rng.standard_normal(n)
+    y1 = rbffd.amg_cycle_host(*A, b1)[1]
+    y2 = rbffd.amg_cycle_host(*A, b2)[1]
+    y12 = rbffd.amg_cycle_host(*A, 2.0 * b1 - 3.0 * b2)[1]
+    assert np.linalg.norm(y12 - (2.0 * y1 - 3.0 * y2)) <= 1e-12 * np.linalg.norm(y12)
+
+
+def test_composed_cycle_not_built_for_two_levels_or_fewer():
+    A = poisson5(12)  # 144 rows: the coarsest level at once
+    assert len(rbffd.amg_analyze(*A)[0]) == 1
+    b = np.random.default_rng(1).standard_normal(144)
+    yl, yc, nc, chunks = rbffd.amg_cycle_host(*A, b)
+    assert nc == 0 and chunks == 0 and not yc.any()
+    # one level: the cycle is the dense inverse
+    rowptr, col, val = A
+    M = np.zeros((144, 144))
+    for i in range(144):
+        M[i, col[rowptr[i]:rowptr[i + 1]]] += val[rowptr[i]:rowptr[i + 1]]
+    assert np.allclose(yl, np.linalg.solve(M, b), rtol=1e-10, atol=1e-12)

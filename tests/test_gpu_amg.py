@@ -233,3 +233,42 @@ def test_batch_rejects_mixed_members_with_jacobi():
     with pytest.raises(rbffd.RbffdError) as e:
         rbffd.Batch(ctx(), [P])
     assert e.value.code == rbffd.EINVAL
+
+
+@pytest.mark.parametrize("case", ["cavity120", "cylinder5k"])
+def test_composed_cycle_matches_oracle_and_level_cycle(case):
+    """The four-phase composed cycle (flexible GMRES launch, coarse vector in
+    shared memory) and the level-by-level cycle are the same preconditioner
+    up to FP32 rounding: both solves land on the oracle's iterates, in about
+    the same number of steps."""
+    fp = clouds.cavity(120, dt=0.05) if case == "cavity120" else CASES[case]()
+    c = ctx()
+    P = rbffd.Problem(c, fp, precond=rbffd.PRECOND_AMG_FGMRES)
+    c.set_amg_compose(False)
+    try:
+        Q = rbffd.Problem(c, fp, precond=rbffd.PRECOND_AMG_FGMRES)
+    finally:
+        c.set_amg_compose(True)
+    levels = P.amg_info()
+    assert len(levels) >= 3, levels
+    cp, cq = P.amg_cycle(), Q.amg_cycle()
+    assert cp["coarse_entries"] == sum(r for r, _ in levels[2:]) and cp["chunks"] > 0
+    assert cq["coarse_entries"] == 0
+    O = oracle.Problem(fp, krylov_tol=1e-12)
+    for X in (P, Q, O):
+        for k, a in (fp.initial or {}).items():
+            X.set(k, a)
+    for r in range(3):
+        dp, sp = P.simple_iterate(fp.dt, krylov_tol=1e-12)
+        dq, sq = Q.simple_iterate(fp.dt, krylov_tol=1e-12)
+        do, _ = O.simple_iterate(fp.dt)
+        print(case, r, sp["iters"], sq["iters"])
+        assert sp["relres"][2] <= 1e-12 and sq["relres"][2] <= 1e-12
+        assert abs(sp["iters"][2] - sq["iters"][2]) <= max(2, sq["iters"][2] // 10)
+        for d in (dp, dq):
+            assert abs(d - do) <= 1e-8 * abs(do), (r, d, do)
+        for X in (P, Q):
+            for k in ("u", "v", "p"):
+                assert rel_l2(X.get(k), O.get(k)) <= 1e-8, (r, k)
+    P.close()
+    Q.close()
