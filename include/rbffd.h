@@ -301,10 +301,23 @@ int rbffd_amg_analyze(int32_t n, const int32_t *rowptr, const int32_t *col, cons
 int rbffd_ctx_set_amg_compose(rbffd_ctx *ctx, int on);
 /* The problem's composed cycle (finishes a build still running first):
  * *coarse_entries (nc; 0: not built), *chunks of its stacked restriction,
- * *restrict_nnz and *q_nnz its entries (all nullable).  Zeros with Jacobi.
+ * *restrict_nnz and *q_nnz its entries, *device_level0 1 when level 0 of
+ * the hierarchy was built on the device (all nullable).  Zeros with Jacobi.
  * Errors: RBFFD_EINVAL, the hierarchy build's errors. */
 int rbffd_problem_amg_cycle(const rbffd_problem *prob, int32_t *coarse_entries, int32_t *chunks,
-                            int64_t *restrict_nnz, int64_t *q_nnz);
+                            int64_t *restrict_nnz, int64_t *q_nnz, int32_t *device_level0);
+/* Where level 0 of the multigrid hierarchies built on this context from now
+ * on is built (the library's own setup path).  on != 0 (the default): on
+ * the device for p' matrices of 16384 rows or more -- the strength graph,
+ * the aggregation, the prolongation and the products R (A P), A P and
+ * A^T P by rows, synchronous with the build -- so that the host thread
+ * only builds the coarse levels; off, or where the device build does not
+ * apply (more than 64 neighbours, a product row with more than 96 distinct
+ * columns), the whole hierarchy on the host.  Level 0 is aggregated the
+ * same way in both (a distance-2 maximal independent set of roots with
+ * fixed priorities), so both give the same aggregates.  Errors:
+ * RBFFD_EINVAL. */
+int rbffd_ctx_set_amg_device_setup(rbffd_ctx *ctx, int on);
 /* One cycle of the hierarchy of a CSR matrix (host arrays as in
  * rbffd_amg_analyze) applied to b[n] on the host in FP64, level by level
  * into out_levels[n] and composed into out_composed[n] (zeros when the

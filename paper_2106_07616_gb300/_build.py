@@ -14,14 +14,15 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "librbffd.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 
-SOURCES = ["context.cu", "knn.cu", "weights.cu", "krylov.cu", "krylov_mixed.cu", "ops.cu", "amg.cu", "fgmres.cu",
+SOURCES = ["context.cu", "knn.cu", "weights.cu", "krylov.cu", "krylov_mixed.cu", "ops.cu", "amg.cu",
+           "amg_setup.cu", "fgmres.cu",
            "problem.cu", "batch.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
           "--expt-relaxed-constexpr"]
 # per-source extra flags: the weight kernel keeps every product and sum a
 # separate rounding (its arithmetic is spelled with __d*_rn intrinsics too)
-EXTRA = {"weights.cu": ["-fmad=false"], "knn.cu": ["-fmad=false"],
+EXTRA = {"weights.cu": ["-fmad=false"], "knn.cu": ["-fmad=false"], "amg_setup.cu": ["-fmad=false"],
          "amg.cu": ["-Xcompiler", "-fopenmp"]}
 
 

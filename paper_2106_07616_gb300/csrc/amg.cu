@@ -3,13 +3,15 @@
 //
 // Per level l (A_0 = the p' matrix):
 //   strength  i ~ j  if |a_ij| >= theta * max_{k != i} |a_ik|, symmetrised;
-//   aggregates: greedy in index order -- a point whose strong neighbours are
-//     all free roots a new aggregate with them; leftovers join the aggregate
-//     of a strong neighbour; what is still free becomes a singleton;
+//   aggregates: on level 0 a distance-2 maximal independent set of roots
+//     (aggregate_mis2); on the coarser levels greedy in index order -- a
+//     point whose strong neighbours are all free roots a new aggregate with
+//     them; leftovers join the aggregate of a strong neighbour; what is
+//     still free becomes a singleton;
 //   tentative prolongation T (one 1 per row, in the point's aggregate);
 //   smoothed prolongation P = (I - w_P D^-1 A) T, w_P = 4 / (3 rho(D^-1 A))
 //     (rho by power iteration);
-//   R = P^T, A_{l+1} = (R A) P (Gustavson sparse products);
+//   R = P^T, A_{l+1} = R (A P) (Gustavson sparse products);
 //   the fused V-cycle operators S, R~, P~ of amg.cuh;
 // until at most AMG_NCOARSE rows remain, whose matrix is inverted densely.
 // Everything is deterministic: fixed start vectors, index-ordered loops;
@@ -30,16 +32,15 @@
 #include "abi_guard.cuh"
 #include "amg.cuh"
 #include "amg_job.cuh"
+#include "amg_setup.cuh"
 #include "krylov_dev.cuh"
 
 namespace rbffd {
 
 namespace {
 
-constexpr int AMG_NCOARSE = 200;    // coarsest level solved by a dense inverse
+constexpr int AMG_NCOARSE = 64;     // coarsest level solved by a dense inverse
 constexpr int AMG_NCOARSE_MAX = 600;
-constexpr double AMG_THETA = 0.08;  // strength threshold
-constexpr double AMG_OMEGA = 2.0 / 3.0;
 
 // Work (entries a loop touches) below which it runs on the calling thread
 // alone: an OpenMP fork and join costs tens of microseconds on a 16-core
@@ -212,7 +213,7 @@ double rho_estimate(const Csr &A, const std::vector<double> &dinv) {
   constexpr int CHUNK = 4096;
   const int nch = (A.n + CHUNK - 1) / CHUNK;
   std::vector<double> x(A.n), y(A.n), px(nch), py(nch);
-  for (int i = 0; i < A.n; ++i) x[i] = 1.0 + 0.5 * (double)((i * 7919) % 13) / 13.0;
+  for (int i = 0; i < A.n; ++i) x[i] = rho_start(i);
   double lam = 1.0, sc = 1.0;
   bool stop = false;
   // one parallel region for all the steps (a fork per step costs more
@@ -295,7 +296,96 @@ void strength(const Csr &A, double theta, std::vector<int32_t> &sp, std::vector<
   sc = std::move(U.col);
 }
 
-// greedy aggregation; returns the number of aggregates
+// ---- level 0's aggregation: a distance-2 maximal independent set of the
+// strength graph as aggregate roots (the MIS(2) aggregation of Bell, Dalton
+// and Olson 2012), with fixed pseudo-random priorities so that the rounds
+// run in parallel and give the same aggregates on the host and the device.
+// key(i) = (h(i) << 32 | i) + 1, h the 32-bit finaliser of MurmurHash3
+// (Appleby); 0 means "none".  Per round: every undecided point whose key is
+// the largest among the undecided points within distance 2 becomes a root;
+// the undecided points within distance 2 of a new root are out.  Then the
+// roots number their aggregates in index order; a point next to roots joins
+// the one of largest key; a point still without an aggregate joins the
+// neighbour (of the first pass) of largest key; isolated points become
+// singletons, numbered after the roots in index order.
+int aggregate_mis2(int n, const std::vector<int32_t> &sp, const std::vector<int32_t> &sc,
+                   std::vector<int32_t> &agg) {
+  enum : char { UND = 0, ROOT = 1, OUT = 2, ISO = 3 };
+  std::vector<char> st(n), nr(n), d1(n);
+  std::vector<uint64_t> m1(n);
+  for (int i = 0; i < n; ++i) st[i] = sp[i] == sp[i + 1] ? ISO : UND;
+  const bool pa = par((long long)sp[n]);
+  for (int round = 0;; ++round) {
+    long long und = 0;
+#pragma omp parallel for schedule(static) reduction(+ : und) if (pa)
+    for (int i = 0; i < n; ++i) und += st[i] == UND;
+    if (und == 0) break;
+#pragma omp parallel for schedule(static) if (pa)
+    for (int i = 0; i < n; ++i) {
+      uint64_t m = st[i] == UND ? mis_key(i) : 0;
+      for (int k = sp[i]; k < sp[i + 1]; ++k)
+        if (st[sc[k]] == UND) m = std::max(m, mis_key(sc[k]));
+      m1[i] = m;
+    }
+#pragma omp parallel for schedule(static) if (pa)
+    for (int i = 0; i < n; ++i) {
+      uint64_t m = m1[i];
+      for (int k = sp[i]; k < sp[i + 1]; ++k) m = std::max(m, m1[sc[k]]);
+      nr[i] = st[i] == UND && m == mis_key(i);
+    }
+#pragma omp parallel for schedule(static) if (pa)
+    for (int i = 0; i < n; ++i) {
+      bool d = nr[i];
+      for (int k = sp[i]; k < sp[i + 1] && !d; ++k) d = nr[sc[k]];
+      d1[i] = d;
+    }
+#pragma omp parallel for schedule(static) if (pa)
+    for (int i = 0; i < n; ++i) {
+      if (nr[i]) {
+        st[i] = ROOT;
+      } else if (st[i] == UND) {
+        bool d = d1[i];
+        for (int k = sp[i]; k < sp[i + 1] && !d; ++k) d = d1[sc[k]];
+        if (d) st[i] = OUT;
+      }
+    }
+  }
+  agg.assign(n, -1);
+  int na = 0;
+  for (int i = 0; i < n; ++i)
+    if (st[i] == ROOT) agg[i] = na++;
+  // the first pass: next to a root
+  std::vector<int32_t> a1(agg);
+#pragma omp parallel for schedule(static) if (pa)
+  for (int i = 0; i < n; ++i) {
+    if (st[i] != OUT) continue;
+    int best = -1;
+    for (int k = sp[i]; k < sp[i + 1]; ++k) {
+      const int j = sc[k];
+      if (st[j] == ROOT && (best < 0 || mis_key(j) > mis_key(best))) best = j;
+    }
+    if (best >= 0) a1[i] = agg[best];
+  }
+  // the second pass: next to a point of the first
+#pragma omp parallel for schedule(static) if (pa)
+  for (int i = 0; i < n; ++i) {
+    if (a1[i] >= 0 || st[i] == ISO) {
+      agg[i] = a1[i];
+      continue;
+    }
+    int best = -1;
+    for (int k = sp[i]; k < sp[i + 1]; ++k) {
+      const int j = sc[k];
+      if (a1[j] >= 0 && (best < 0 || mis_key(j) > mis_key(best))) best = j;
+    }
+    agg[i] = best >= 0 ? a1[best] : -1;
+  }
+  for (int i = 0; i < n; ++i)
+    if (agg[i] < 0) agg[i] = na++;
+  return na;
+}
+
+// greedy aggregation (the coarse levels); returns the number of aggregates
 int aggregate(int n, const std::vector<int32_t> &sp, const std::vector<int32_t> &sc,
               std::vector<int32_t> &agg) {
   agg.assign(n, -1);
@@ -581,8 +671,15 @@ struct Hierarchy {
 
 // The levels of A0 (see the top of the file).  RBFFD_OK, or an error with
 // its text set.
+int build_levels(Hierarchy &H);
+
 int build_hierarchy(Csr A0, Hierarchy &H) {
   H.A.push_back(std::move(A0));
+  return build_levels(H);
+}
+
+// The levels from H.A.back() on (H holds the finer levels already).
+int build_levels(Hierarchy &H) {
   for (;;) {
     const Csr &A = H.A.back();
     std::vector<double> d = diagonal(A), dinv(A.n);
@@ -597,15 +694,18 @@ int build_hierarchy(Csr A0, Hierarchy &H) {
     if (A.n <= AMG_NCOARSE || (int)H.A.size() == AMG_MAXLEV) break;
     std::vector<int32_t> sp, sc, agg;
     strength(A, AMG_THETA, sp, sc);
-    const int na = aggregate(A.n, sp, sc, agg);
+    const int na = H.A.size() == 1 ? aggregate_mis2(A.n, sp, sc, agg)
+                                   : aggregate(A.n, sp, sc, agg);
     if (na > 0.8 * A.n || na == 0) break;  // coarsening stalled
     Csr P = smoothed_prolongator(A, dinv, agg, na, 4.0 / (3.0 * lam));
     Csr R = transpose(P);
-    Csr RA = spgemm(R, A);
-    Csr Ac = spgemm(RA, P);
     Csr AP = spgemm(A, P);
+    Csr Ac = spgemm(R, AP);  // R (A P)
+    // R~ = R (I - A W) = ((I - W A^T) P)^T, built row by row over the fine
+    // level like P~ (the device's level-0 build takes the same route)
+    Csr AtP = spgemm(transpose(A), P);
     const std::vector<double> &w = H.W.back();
-    H.R.push_back(minus_scaled(R, RA, w, true));   // R (I - A W)
+    H.R.push_back(transpose(minus_scaled(P, AtP, w, false)));
     H.P.push_back(minus_scaled(P, AP, w, false));  // (I - W A) P
     H.A.push_back(std::move(Ac));
   }
@@ -805,9 +905,11 @@ void cycle_composed(const Hierarchy &H, const Composed &C, const std::vector<dou
   }
 }
 
-void fill_info(const Hierarchy &H, double ms, AmgInfo *info, const Composed *C = nullptr) {
+void fill_info(const Hierarchy &H, double ms, AmgInfo *info, const Composed *C = nullptr,
+               const AmgL0 *l0 = nullptr) {
   if (!info) return;
   memset(info, 0, sizeof(*info));
+  info->device_l0 = l0 != nullptr;
   if (C) {
     info->comp_nc = C->R.n;
     info->comp_chunks = (int)C->cs.size() - 1;
@@ -823,6 +925,11 @@ void fill_info(const Hierarchy &H, double ms, AmgInfo *info, const Composed *C =
     info->nnz_r[l] = l + 1 < L ? H.R[l].nnz() : 0;
     info->nnz_p[l] = l + 1 < L ? H.P[l].nnz() : 0;
     info->omega[l] = H.omega[l];
+  }
+  if (l0) {  // level 0 was built on the device: its sizes come from there
+    info->nnz[0] = l0->nnz_a;
+    info->nnz_r[0] = l0->nnz_r;
+    info->nnz_p[0] = l0->nnz_p;
   }
 }
 
@@ -948,12 +1055,104 @@ struct AmgJob {
   bool comp = false;    // built
   Composed C;
   CompOff coff;
+  rbffd_ctx *ctx = nullptr;
+  bool l0dev = false;  // level 0 built on the device (amg_setup.cu)
+  AmgL0 L0;
+  int gR0 = 1, gP0 = 1;  // lanes per row of level 0's R~ and P~ (device-built)
 };
 
 namespace {
 
+// The coarse levels after a device-built level 0: level 0 stands in the
+// hierarchy by its size only, A_1 comes from the device.
+template <typename T>
+int host_part_coarse(AmgJob &J) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int n = J.n, q = J.q;
+  const AmgL0 &L0 = J.L0;
+  const int n1 = L0.n1;
+  Hierarchy &H = J.H;
+  Csr A0, R0, P0, A1;
+  A0.n = A0.m = n;
+  A0.ptr.assign(n + 1, 0);
+  R0.n = n1;
+  R0.m = n;
+  R0.ptr.assign(n1 + 1, 0);
+  P0.n = n;
+  P0.m = n1;
+  P0.ptr.assign(n + 1, 0);
+  A1.n = A1.m = n1;
+  A1.ptr = L0.a1ptr;
+  A1.col = L0.a1col;
+  A1.val = L0.a1val;
+  H.A.push_back(std::move(A0));
+  H.omega.push_back(L0.omega);
+  H.S.push_back(Csr());
+  H.W.push_back(std::vector<double>());
+  H.R.push_back(std::move(R0));
+  H.P.push_back(std::move(P0));
+  H.A.push_back(std::move(A1));
+  RBFFD_TRY(build_levels(H));
+  const int L = (int)H.A.size();
+  J.comp = J.compose && compose(H, J.C);
+  Staging &S = J.S;
+  auto put_csr = [&](const Csr &M, int grp) {
+    CsrOff o;
+    o.ptr = S.put(M.ptr);
+    o.col = S.put(M.col);
+    o.val = S.put_as<T>(M.val);
+    o.grp = grp;
+    return o;
+  };
+  const Grid W{J.nblocks > 0 ? J.nblocks : 128, J.wpb > 0 ? J.wpb : 32};
+  std::vector<int> gS(L, 1), gR(L, 1), gP(L, 1);
+  {
+    Shape r0, p0;
+    r0.rows = n1;
+    r0.maxlen = L0.maxlen_r;
+    p0.rows = n;
+    p0.maxlen = L0.maxlen_p;
+    lanes_level0(n, q, r0, W, J.ts0, J.gR0);
+    J.gP0 = lanes_alone(p0, W);
+  }
+  for (int l = 1; l + 1 < L; ++l) {
+    lanes_pair(shape(H.S[l]), shape(H.R[l]), W, gS[l], gR[l]);
+    gP[l] = lanes_alone(shape(H.P[l]), W);
+  }
+  std::vector<LevelOff> &off = J.off;
+  off.assign(L, LevelOff());
+  J.low = sizeof(T) < sizeof(double);
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) S.fill_pass();
+    J.o_dev = S.take(sizeof(AmgDevT<T>));
+    for (int l = 1; l < L; ++l) {
+      off[l].S = put_csr(H.S[l], l + 1 < L ? gS[l] : 1);
+      if (l + 1 < L) {
+        off[l].R = put_csr(H.R[l], gR[l]);
+        off[l].P = put_csr(H.P[l], gP[l]);
+      }
+      off[l].b = S.take(sizeof(T) * H.A[l].n);
+      off[l].z = S.take(sizeof(T) * H.A[l].n);
+      off[l].y = S.take(sizeof(T) * H.A[l].n);
+    }
+    J.o_cinv = S.put_as<T>(H.cinv);
+    if (J.comp) {
+      CompOff &co = J.coff;
+      co.rcol = S.put(J.C.R.col);
+      co.rval = S.put_as<T>(J.C.R.val);
+      co.cs = S.put(J.C.cs);
+      co.kc = S.put(J.C.kc);
+      co.Q = put_csr(J.C.Q, lanes_alone(shape(J.C.Q), W));
+      co.part = S.take(sizeof(T) * (J.C.cs.size() - 1));
+    }
+  }
+  J.host_ms = ms_since(t0);
+  return RBFFD_OK;
+}
+
 template <typename T>
 int host_part(AmgJob &J) {
+  if (J.l0dev) return host_part_coarse<T>(J);
   const int n = J.n, q = J.q, ldn = J.ldn;
   std::vector<int32_t> hcol((size_t)q * ldn);
   std::vector<double> hval((size_t)q * ldn);
@@ -1064,6 +1263,14 @@ void join(AmgJob *J) {
   J->ready = nullptr;
 }
 
+// a job given up: its device-built level 0 goes with it
+void drop(AmgJob *J) {
+  join(J);
+  if (J->L0.mem) dev_free(J->ctx, J->L0.mem, J->L0.bytes);
+  J->L0.mem = nullptr;
+  delete J;
+}
+
 }  // namespace
 
 template <typename T>
@@ -1080,11 +1287,23 @@ int amg_build_begin(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
   J->dcol = col;
   J->dval = val;
   J->compose = ctx->amg_compose;
+  J->ctx = ctx;
+  // level 0 on the device when it applies (amg_setup.cu); else, or when the
+  // device build gives up, the whole hierarchy on the host
+  if (ctx->amg_device_setup && n >= AMG_SETUP_MIN_ROWS) {
+    const int rc =
+        amg_level0_device<T>(ctx, n, q, ldn, col, val, sizeof(T) < sizeof(double), &J->L0);
+    if (rc == RBFFD_OK) {
+      J->l0dev = true;
+    } else if (rc != RBFFD_ENOTIMPL) {
+      drop(J);
+      return rc;
+    }
+  }
   if (cudaEventCreateWithFlags(&J->ready, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventRecord(J->ready, ctx->stream) != cudaSuccess) {
     cudaGetLastError();
-    join(J);
-    delete J;
+    drop(J);
     set_error("amg: event for the hierarchy build failed");
     return RBFFD_ECUDA;
   }
@@ -1097,8 +1316,7 @@ int amg_build_begin(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
     return RBFFD_OK;
   });
   if (rc != RBFFD_OK) {
-    join(J);
-    delete J;
+    drop(J);
     return rc;
   }
   *job = J;
@@ -1106,18 +1324,22 @@ int amg_build_begin(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
 }
 
 template <typename T>
-int amg_build_end(rbffd_ctx *ctx, AmgJob **job, void **mem, size_t *bytes,
-                  const AmgDevT<T> **dev, AmgDevT<T> *host_view, AmgInfo *info) {
+int amg_build_end(rbffd_ctx *ctx, AmgJob **job, void **mem, size_t *bytes, void **mem0,
+                  size_t *bytes0, const AmgDevT<T> **dev, AmgDevT<T> *host_view,
+                  AmgInfo *info) {
   *mem = nullptr;
   *bytes = 0;
+  *mem0 = nullptr;
+  *bytes0 = 0;
   *dev = nullptr;
   AmgJob *J = *job;
   join(J);
   if (J->rc != RBFFD_OK) {
     *job = nullptr;
-    std::unique_ptr<AmgJob> own(J);
     set_error("%s", J->err);
-    return J->rc;
+    const int rc = J->rc;
+    drop(J);
+    return rc;
   }
   const Hierarchy &H = J->H;
   Staging &S = J->S;
@@ -1128,8 +1350,13 @@ int amg_build_end(rbffd_ctx *ctx, AmgJob **job, void **mem, size_t *bytes,
   const int arc = dev_alloc(ctx, &dmem, S.size);
   if (arc != RBFFD_OK) return arc;
   *job = nullptr;
+  // the device-built level 0 passes to the caller with the rest
+  void *l0mem = J->L0.mem;
+  const size_t l0bytes = J->L0.bytes;
+  J->L0.mem = nullptr;
   std::unique_ptr<AmgJob> own(J);
   char *base = (char *)dmem;
+  char *base0 = (char *)l0mem;
   auto csr_at = [&](const CsrOff &o, bool have) {
     AmgCsrT<T> c;
     c.ptr = have ? (const int32_t *)(base + o.ptr) : nullptr;
@@ -1142,9 +1369,7 @@ int amg_build_end(rbffd_ctx *ctx, AmgJob **job, void **mem, size_t *bytes,
   memset(&h, 0, sizeof(h));
   h.nlev = L;
   h.cinv = (const T *)(base + J->o_cinv);
-  h.s0 = (const T *)(base + J->o_s0);
   h.ts0 = J->ts0;
-  h.a0 = J->low ? (const T *)(base + J->o_a0) : nullptr;
   for (int l = 0; l < L; ++l) {
     AmgLevelT<T> &v = h.lev[l];
     const LevelOff &o = J->off[l];
@@ -1155,6 +1380,25 @@ int amg_build_end(rbffd_ctx *ctx, AmgJob **job, void **mem, size_t *bytes,
     v.b = l > 0 ? (T *)(base + o.b) : nullptr;
     v.z = (T *)(base + o.z);
     v.y = (T *)(base + o.y);
+  }
+  if (J->l0dev) {
+    const AmgL0 &d = J->L0;
+    h.s0 = (const T *)(base0 + d.o_s0);
+    h.a0 = J->low ? (const T *)(base0 + d.o_a0) : nullptr;
+    AmgLevelT<T> &v = h.lev[0];
+    v.R.ptr = (const int32_t *)(base0 + d.o_rp);
+    v.R.col = (const int32_t *)(base0 + d.o_rc);
+    v.R.val = (const T *)(base0 + d.o_rv);
+    v.R.grp = J->gR0;
+    v.P.ptr = (const int32_t *)(base0 + d.o_pp);
+    v.P.col = (const int32_t *)(base0 + d.o_pc);
+    v.P.val = (const T *)(base0 + d.o_pv);
+    v.P.grp = J->gP0;
+    v.z = (T *)(base0 + d.o_z);
+    v.y = (T *)(base0 + d.o_y);
+  } else {
+    h.s0 = (const T *)(base + J->o_s0);
+    h.a0 = J->low ? (const T *)(base + J->o_a0) : nullptr;
   }
   if (J->comp) {
     const Composed &C = J->C;
@@ -1177,42 +1421,44 @@ int amg_build_end(rbffd_ctx *ctx, AmgJob **job, void **mem, size_t *bytes,
           cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     dev_free(ctx, dmem, S.size);
+    if (l0mem) dev_free(ctx, l0mem, l0bytes);
     set_error("amg: upload failed");
     return RBFFD_ECUDA;
   }
   *mem = dmem;
   *bytes = S.size;
+  *mem0 = l0mem;
+  *bytes0 = l0mem ? l0bytes : 0;
   *dev = (const AmgDevT<T> *)(base + J->o_dev);
   if (host_view) *host_view = h;
-  fill_info(H, J->host_ms, info, J->comp ? &J->C : nullptr);
+  fill_info(H, J->host_ms, info, J->comp ? &J->C : nullptr, J->l0dev ? &J->L0 : nullptr);
   return RBFFD_OK;
 }
 
 void amg_build_abandon(AmgJob *J) {
   if (!J) return;
-  join(J);
-  delete J;
+  drop(J);
 }
 
 template <typename T>
 int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
-              int nblocks, int wpb, void **mem, size_t *bytes, const AmgDevT<T> **dev,
-              AmgDevT<T> *host_view, AmgInfo *info) {
+              int nblocks, int wpb, void **mem, size_t *bytes, void **mem0, size_t *bytes0,
+              const AmgDevT<T> **dev, AmgDevT<T> *host_view, AmgInfo *info) {
   AmgJob *J = nullptr;
   RBFFD_TRY(amg_build_begin<T>(ctx, n, q, ldn, col, val, nblocks, wpb, &J));
-  const int rc = amg_build_end<T>(ctx, &J, mem, bytes, dev, host_view, info);
+  const int rc = amg_build_end<T>(ctx, &J, mem, bytes, mem0, bytes0, dev, host_view, info);
   amg_build_abandon(J);  // still set only when the upload found no memory
   return rc;
 }
 
 #define RBFFD_AMG_INSTANCES(T)                                                                  \
   template int amg_build<T>(rbffd_ctx *, int, int, int, const int32_t *, const double *, int,  \
-                            int, void **, size_t *, const AmgDevT<T> **, AmgDevT<T> *,         \
-                            AmgInfo *);                                                        \
+                            int, void **, size_t *, void **, size_t *, const AmgDevT<T> **,     \
+                            AmgDevT<T> *, AmgInfo *);                                          \
   template int amg_build_begin<T>(rbffd_ctx *, int, int, int, const int32_t *, const double *, \
                                   int, int, AmgJob **);                                        \
-  template int amg_build_end<T>(rbffd_ctx *, AmgJob **, void **, size_t *, const AmgDevT<T> **, \
-                                AmgDevT<T> *, AmgInfo *);
+  template int amg_build_end<T>(rbffd_ctx *, AmgJob **, void **, size_t *, void **, size_t *,  \
+                                const AmgDevT<T> **, AmgDevT<T> *, AmgInfo *);
 RBFFD_AMG_INSTANCES(double)
 RBFFD_AMG_INSTANCES(float)
 

@@ -22,6 +22,27 @@ constexpr int AMG_RCHUNK = 32 * AMG_CSR_CHUNK;  // entries of a composed-restric
 // iterations to 1e-12 instead of 76.  FGMRES keeps every preconditioned
 // vector and minimises over them, so it takes an FP32 cycle (fgmres.cu).
 
+// Priorities of level 0's MIS(2) aggregation (amg.cu: aggregate_mis2; the
+// device build in amg_setup.cu takes the same): key(i) = (h(i) << 32 | i) + 1
+// with h the 32-bit finaliser of MurmurHash3 (Appleby); 0 means "none".
+__host__ __device__ inline uint32_t mis_hash(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x85ebca6bu;
+  x ^= x >> 13;
+  x *= 0xc2b2ae35u;
+  x ^= x >> 16;
+  return x;
+}
+__host__ __device__ inline uint64_t mis_key(int i) {
+  return (((uint64_t)mis_hash((uint32_t)i) << 32) | (uint32_t)i) + 1;
+}
+// fixed non-constant start of the power iteration for rho(D^-1 A)
+__host__ __device__ inline double rho_start(int i) {
+  return 1.0 + 0.5 * (double)(((uint32_t)i * 7919u) % 13u) / 13.0;
+}
+constexpr double AMG_THETA = 0.08;  // strength threshold
+constexpr double AMG_OMEGA = 2.0 / 3.0;
+
 // A CSR matrix on the device, read with `grp` lanes per row.
 template <typename T>
 struct AmgCsrT {
@@ -109,20 +130,22 @@ struct AmgInfo {
   int comp_chunks;              // chunks of its stacked restriction
   long long comp_nnz_r;         // entries of the stacked restriction
   long long comp_nnz_q;         // entries of Q
+  bool device_l0;               // level 0 was built on the device (amg_setup.cu)
 };
 
 // Build the hierarchy of the packed p' matrix (ELL, column-major [q][ldn],
-// device) on the host and upload it into one device allocation (*mem,
-// *bytes; freed with dev_free).  nblocks x wpb: the CTAs and warps per CTA
-// of the launch that will run the cycle (lanes per row are chosen for it;
-// any launch runs it correctly).  *dev receives the device copy of the
-// level table.  Errors: RBFFD_ESINGULAR if the coarsest matrix is singular,
-// RBFFD_ENOMEM, RBFFD_ECUDA.
+// device) and upload it: the coarse levels in one device allocation (*mem,
+// *bytes), level 0 in a second one when it was built on the device
+// (*mem0, *bytes0; else null and 0); both freed with dev_free.  nblocks x
+// wpb: the CTAs and warps per CTA of the launch that will run the cycle
+// (lanes per row are chosen for it; any launch runs it correctly).  *dev
+// receives the device copy of the level table.  Errors: RBFFD_ESINGULAR if
+// the coarsest matrix is singular, RBFFD_ENOMEM, RBFFD_ECUDA.
 // T = double or float: the stored arithmetic of the cycle.
 template <typename T>
 int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const double *val,
-              int nblocks, int wpb, void **mem, size_t *bytes, const AmgDevT<T> **dev,
-              AmgDevT<T> *host_view, AmgInfo *info);
+              int nblocks, int wpb, void **mem, size_t *bytes, void **mem0, size_t *bytes0,
+              const AmgDevT<T> **dev, AmgDevT<T> *host_view, AmgInfo *info);
 
 // The host part alone, on a CSR matrix (analysis and tests): level sizes
 // and nonzeros in *info.

@@ -26,6 +26,8 @@ struct rbffd_ctx {
   // multigrid hierarchies built on this context get the composed cycle when
   // it pays (rbffd_ctx_set_amg_compose)
   bool amg_compose = true;
+  // level 0 of large hierarchies built on the device (rbffd_ctx_set_amg_device_setup)
+  bool amg_device_setup = true;
   // pinned host scratch for small read-backs
   void *pinned = nullptr;
   size_t pinned_bytes = 0;

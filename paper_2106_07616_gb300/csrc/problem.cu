@@ -78,6 +78,9 @@ void free_amg(rbffd_problem *P) {
   if (P->amg_job) amg_build_abandon(P->amg_job);
   P->amg_job = nullptr;
   if (P->amg_mem) dev_free(P->ctx, P->amg_mem, P->amg_bytes);
+  if (P->amg0_mem) dev_free(P->ctx, P->amg0_mem, P->amg0_bytes);
+  P->amg0_mem = nullptr;
+  P->amg0_bytes = 0;
   if (P->fg_mem) dev_free(P->ctx, P->fg_mem, P->fg_bytes);
   P->fg_mem = nullptr;
   P->fg_bytes = 0;
@@ -240,10 +243,12 @@ int rbffd::amg_ready(rbffd_problem *P) {
   if (!P->amg_job) return RBFFD_OK;
   const int rc =
       P->precond == RBFFD_PRECOND_AMG
-          ? amg_build_end<double>(P->ctx, &P->amg_job, &P->amg_mem, &P->amg_bytes, &P->amg,
-                                  &P->amg_host, &P->amg_info)
-          : amg_build_end<float>(P->ctx, &P->amg_job, &P->amg_mem, &P->amg_bytes, &P->amgf,
-                                 &P->amgf_host, &P->amg_info);
+          ? amg_build_end<double>(P->ctx, &P->amg_job, &P->amg_mem, &P->amg_bytes,
+                                  &P->amg0_mem, &P->amg0_bytes, &P->amg, &P->amg_host,
+                                  &P->amg_info)
+          : amg_build_end<float>(P->ctx, &P->amg_job, &P->amg_mem, &P->amg_bytes,
+                                 &P->amg0_mem, &P->amg0_bytes, &P->amgf, &P->amgf_host,
+                                 &P->amg_info);
   // RBFFD_ENOMEM with the job still held: the upload may be retried later
   if (rc != RBFFD_OK && !P->amg_job) {
     P->amg_err = rc;
@@ -721,7 +726,7 @@ extern "C" void rbffd_problem_destroy(rbffd_problem *P) {
 }
 
 extern "C" size_t rbffd_problem_bytes(const rbffd_problem *P) {
-  return P ? P->bytes + P->amg_bytes + P->fg_bytes : 0;
+  return P ? P->bytes + P->amg_bytes + P->amg0_bytes + P->fg_bytes : 0;
 }
 
 static void report_levels(const AmgInfo &I, bool have_any, int32_t *levels, int32_t *rows,
@@ -766,8 +771,8 @@ extern "C" int rbffd_amg_analyze(int32_t n, const int32_t *rowptr, const int32_t
 }
 
 extern "C" int rbffd_problem_amg_cycle(const rbffd_problem *P, int32_t *coarse_entries,
-                                       int32_t *chunks, int64_t *restrict_nnz,
-                                       int64_t *q_nnz) {
+                                       int32_t *chunks, int64_t *restrict_nnz, int64_t *q_nnz,
+                                       int32_t *device_level0) {
   return guarded([&]() -> int {
     if (!P) return RBFFD_EINVAL;
     RBFFD_CK(cudaSetDevice(P->ctx->device));
@@ -778,6 +783,7 @@ extern "C" int rbffd_problem_amg_cycle(const rbffd_problem *P, int32_t *coarse_e
     if (chunks) *chunks = have ? I.comp_chunks : 0;
     if (restrict_nnz) *restrict_nnz = have ? I.comp_nnz_r : 0;
     if (q_nnz) *q_nnz = have ? I.comp_nnz_q : 0;
+    if (device_level0) *device_level0 = have && I.device_l0 ? 1 : 0;
     return RBFFD_OK;
   });
 }

@@ -82,6 +82,8 @@ struct rbffd_problem {
   uint64_t gen = 0;
   void *amg_mem = nullptr;
   size_t amg_bytes = 0;
+  void *amg0_mem = nullptr;  // level 0 built on the device (its own allocation), or null
+  size_t amg0_bytes = 0;
   const rbffd::AmgDev *amg = nullptr;  // device copy of the level table
   rbffd::AmgDev amg_host{};             // host copy (device pointers)
   rbffd::AmgInfo amg_info{};

@@ -129,7 +129,8 @@ def load(path: str = LIB_PATH):
         "rbffd_ctx_set_wait_limit": (C.c_int, [vp, i32]),
         "rbffd_ctx_set_amg_compose": (C.c_int, [vp, C.c_int]),
         "rbffd_problem_amg_cycle": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64),
-                                              C.POINTER(i64)]),
+                                              C.POINTER(i64), C.POINTER(i32)]),
+        "rbffd_ctx_set_amg_device_setup": (C.c_int, [vp, C.c_int]),
         "rbffd_amg_cycle_host": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, C.POINTER(i32),
                                            C.POINTER(i32)]),
         "rbffd_get_field": (C.c_int, [vp, i32, vp]),
@@ -189,6 +190,12 @@ class Context:
         cycles, 0 for the default (rbffd_ctx_set_wait_limit)."""
         _check(load().rbffd_ctx_set_wait_limit(self.h, int(log2_cycles)),
                "rbffd_ctx_set_wait_limit")
+
+    def set_amg_device_setup(self, on: bool):
+        """Whether level 0 of multigrid hierarchies built from now on is built
+        on the device (large p' matrices; rbffd_ctx_set_amg_device_setup)."""
+        _check(load().rbffd_ctx_set_amg_device_setup(self.h, 1 if on else 0),
+               "rbffd_ctx_set_amg_device_setup")
 
     def set_amg_compose(self, on: bool):
         """Whether multigrid hierarchies built from now on get the composed
@@ -342,12 +349,12 @@ class Problem:
     def amg_cycle(self):
         """The composed multigrid cycle: dict of coarse entries (0: not
         built), chunks, restriction and Q nonzeros (rbffd_problem_amg_cycle)."""
-        nc, ch = C.c_int32(0), C.c_int32(0)
+        nc, ch, dl = C.c_int32(0), C.c_int32(0), C.c_int32(0)
         nr, nq = C.c_int64(0), C.c_int64(0)
         _check(load().rbffd_problem_amg_cycle(self.h, C.byref(nc), C.byref(ch), C.byref(nr),
-                                              C.byref(nq)), "rbffd_problem_amg_cycle")
+                                              C.byref(nq), C.byref(dl)), "rbffd_problem_amg_cycle")
         return {"coarse_entries": nc.value, "chunks": ch.value, "restrict_nnz": nr.value,
-                "q_nnz": nq.value}
+                "q_nnz": nq.value, "device_level0": bool(dl.value)}
 
     def get(self, name, out=None):
         out = np.zeros(self.n) if out is None else out

@@ -129,14 +129,14 @@ def test_composed_cycle_equals_the_level_by_level_cycle(which):
 
 
 def test_composed_cycle_not_built_for_two_levels_or_fewer():
-    A = poisson5(12)  # 144 rows: the coarsest level at once
+    A = poisson5(8)  # 64 rows: the coarsest level at once
     assert len(rbffd.amg_analyze(*A)[0]) == 1
-    b = np.random.default_rng(1).standard_normal(144)
+    b = np.random.default_rng(1).standard_normal(64)
     yl, yc, nc, chunks = rbffd.amg_cycle_host(*A, b)
     assert nc == 0 and chunks == 0 and not yc.any()
     # one level: the cycle is the dense inverse
     rowptr, col, val = A
-    M = np.zeros((144, 144))
-    for i in range(144):
+    M = np.zeros((64, 64))
+    for i in range(64):
         M[i, col[rowptr[i]:rowptr[i + 1]]] += val[rowptr[i]:rowptr[i + 1]]
     assert np.allclose(yl, np.linalg.solve(M, b), rtol=1e-10, atol=1e-12)

@@ -235,13 +235,13 @@ def test_batch_rejects_mixed_members_with_jacobi():
     assert e.value.code == rbffd.EINVAL
 
 
-@pytest.mark.parametrize("case", ["cavity120", "cylinder5k"])
+@pytest.mark.parametrize("case", ["cavity120", "kovasznay140"])
 def test_composed_cycle_matches_oracle_and_level_cycle(case):
     """The four-phase composed cycle (flexible GMRES launch, coarse vector in
     shared memory) and the level-by-level cycle are the same preconditioner
     up to FP32 rounding: both solves land on the oracle's iterates, in about
     the same number of steps."""
-    fp = clouds.cavity(120, dt=0.05) if case == "cavity120" else CASES[case]()
+    fp = clouds.cavity(120, dt=0.05) if case == "cavity120" else clouds.kovasznay(140, dt=0.4)
     c = ctx()
     P = rbffd.Problem(c, fp, precond=rbffd.PRECOND_AMG_FGMRES)
     c.set_amg_compose(False)
@@ -258,12 +258,15 @@ def test_composed_cycle_matches_oracle_and_level_cycle(case):
     for X in (P, Q, O):
         for k, a in (fp.initial or {}).items():
             X.set(k, a)
+    # the FP32 Arnoldi's FP64 residual floor sits near 1e-12 on the 140^2
+    # Kovasznay p' system: ask for 1e-10 there (far inside the 1e-8 parity)
+    tol = 1e-12 if case == "cavity120" else 1e-10
     for r in range(3):
-        dp, sp = P.simple_iterate(fp.dt, krylov_tol=1e-12)
-        dq, sq = Q.simple_iterate(fp.dt, krylov_tol=1e-12)
+        dp, sp = P.simple_iterate(fp.dt, krylov_tol=tol)
+        dq, sq = Q.simple_iterate(fp.dt, krylov_tol=tol)
         do, _ = O.simple_iterate(fp.dt)
         print(case, r, sp["iters"], sq["iters"])
-        assert sp["relres"][2] <= 1e-12 and sq["relres"][2] <= 1e-12
+        assert sp["relres"][2] <= tol and sq["relres"][2] <= tol
         assert abs(sp["iters"][2] - sq["iters"][2]) <= max(2, sq["iters"][2] // 10)
         for d in (dp, dq):
             assert abs(d - do) <= 1e-8 * abs(do), (r, d, do)
@@ -272,3 +275,47 @@ def test_composed_cycle_matches_oracle_and_level_cycle(case):
                 assert rel_l2(X.get(k), O.get(k)) <= 1e-8, (r, k)
     P.close()
     Q.close()
+
+
+@pytest.mark.parametrize("pc", [rbffd.PRECOND_AMG, rbffd.PRECOND_AMG_FGMRES])
+def test_device_level0_matches_host_build(pc):
+    """Level 0 built on the device (strength, MIS(2) aggregation, P, the
+    products) against the whole hierarchy built on the host from the same
+    p' matrix: the same aggregates, hence the same level sizes and level-1
+    pattern; both solves give the oracle's iterates in about as many steps."""
+    fp = clouds.cavity(160, dt=0.05)  # 25 600 rows: above the device build's threshold
+    c = ctx()
+    D = rbffd.Problem(c, fp, precond=pc)
+    c.set_amg_device_setup(False)
+    try:
+        H = rbffd.Problem(c, fp, precond=pc)
+    finally:
+        c.set_amg_device_setup(True)
+    assert D.amg_cycle()["device_level0"] and not H.amg_cycle()["device_level0"]
+    ld, lh = D.amg_info(), H.amg_info()
+    print("device", ld, "host", lh)
+    assert ld[0] == lh[0] and ld[1] == lh[1], (ld, lh)
+    assert len(ld) == len(lh)
+    for (nd, zd), (nh, zh) in zip(ld[2:], lh[2:]):
+        assert abs(nd - nh) <= 0.02 * nh and abs(zd - zh) <= 0.05 * zh
+    # the host analysis of the same matrix agrees too
+    ops = D.operators()
+    pv, idx = ops["pval"], ops["idx"]
+    keep = (pv != 0) | (idx == np.arange(fp.n)[:, None])
+    rowptr = np.concatenate([[0], np.cumsum(keep.sum(1))])
+    la = rbffd.amg_analyze(rowptr, idx[keep], pv[keep])[0]
+    assert la[0] == ld[0] and la[1] == ld[1], (la, ld)
+    O = oracle.Problem(fp, krylov_tol=1e-12)
+    for r in range(2):
+        dd, sd = D.simple_iterate(fp.dt, krylov_tol=1e-12)
+        dh, sh = H.simple_iterate(fp.dt, krylov_tol=1e-12)
+        do, _ = O.simple_iterate(fp.dt)
+        print(pc, r, sd["iters"], sh["iters"])
+        assert abs(sd["iters"][2] - sh["iters"][2]) <= max(2, sh["iters"][2] // 10)
+        for d in (dd, dh):
+            assert abs(d - do) <= 1e-8 * abs(do), (r, d, do)
+        for X in (D, H):
+            for k in ("u", "v", "p"):
+                assert rel_l2(X.get(k), O.get(k)) <= 1e-8, (r, k)
+    D.close()
+    H.close()
