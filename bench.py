@@ -98,10 +98,11 @@ KRYLOV_PROFILES = {
     # preconditioner: (committed ncu summary, kernel sources it was taken from)
     "jacobi": ("k_bicgstab_fp64_cavity200.md", ("krylov.cu", "krylov_dev.cuh", "common.cuh")),
     "amg": ("k_bicgstab_amg_fp64_cavity200.md",
-            ("krylov.cu", "krylov_dev.cuh", "common.cuh", "amg_dev.cuh", "amg.cuh")),
+            ("krylov.cu", "krylov_dev.cuh", "common.cuh", "amg_dev.cuh", "amg.cuh", "amg.cu",
+             "amg_setup.cu")),
     "fgmres": ("k_fgmres_cavity200.md",
                ("fgmres.cu", "fgmres.cuh", "krylov_dev.cuh", "common.cuh", "amg_dev.cuh",
-                "amg.cuh")),
+                "amg.cuh", "amg.cu", "amg_setup.cu")),
 }
 
 
