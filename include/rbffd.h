@@ -536,7 +536,7 @@ typedef struct {
 typedef struct {
   int32_t state;        /* 0 queued, 1 running, 2 done */
   int32_t status;       /* when done: RBFFD_OK, or the error that ended it */
-  double queue_s;       /* arrival -> admission (seconds) */
+  double queue_s;       /* arrival -> admission (seconds; 0 if never admitted) */
   double latency_s;     /* arrival -> result (seconds), when done */
   int32_t steps;        /* time steps taken */
   int64_t outer_iters;  /* outer iterations taken */
@@ -547,6 +547,8 @@ typedef struct {
                              upload is retried) */
   double arrive_s, admit_s, done_s; /* submission, admission and completion, in
                                        seconds since the server was created */
+  int32_t builds;       /* builds of the request's problem (clouds, weights, operators):
+                           1, or more only when a build itself found no device memory */
 } rbffd_result;
 int rbffd_server_create(rbffd_ctx *ctx, const rbffd_server_params *params, rbffd_server **out);
 /* desc arrays are host pointers, copied before the call returns; ticket

@@ -53,6 +53,8 @@ struct Request {
   int outer_in_step = 0;
   int steps = 0;
   int admit_attempts = 0;  // hierarchy uploads tried (the build itself runs once)
+  int builds = 0;          // problem builds (clouds, weights, operators) made
+  bool admitted = false;   // joined the running batch (t_admit set)
   int64_t outer_total = 0;
   double resid[4] = {1, 1, 1, 0};
   std::vector<double> u, v, p;
@@ -110,7 +112,11 @@ struct rbffd_server {
       // only its hierarchy upload, which found no device memory then, is
       // retried (the clouds, weights, operators and the host part of the
       // hierarchy are not built again).
-      int rc = r->P ? RBFFD_OK : rbffd_problem_create(ctx, &r->desc, &r->P);
+      int rc = RBFFD_OK;
+      if (!r->P) {
+        ++r->builds;
+        rc = rbffd_problem_create(ctx, &r->desc, &r->P);
+      }
       if (rc == RBFFD_OK) {
         ++r->admit_attempts;
         // the hierarchy's device memory counts against the budget now
@@ -130,6 +136,7 @@ struct rbffd_server {
         continue;
       }
       r->t_admit = Clock::now();
+      r->admitted = true;
       r->state = 1;
       running.push_back(r);
     }
@@ -299,10 +306,11 @@ extern "C" int rbffd_server_poll(rbffd_server *s, uint64_t ticket, rbffd_result 
     res->outer_iters = r->outer_total;
     for (int k = 0; k < 4; ++k) res->resid[k] = r->resid[k];
     res->admit_attempts = r->admit_attempts;
+    res->builds = r->builds;
     res->arrive_s = secs(s->t0, r->t_arrive);
-    if (r->state >= 1) res->admit_s = secs(s->t0, r->t_admit);
+    if (r->admitted) res->admit_s = secs(s->t0, r->t_admit);
     if (r->state == 2) res->done_s = secs(s->t0, r->t_done);
-    if (r->state >= 1) res->queue_s = secs(r->t_arrive, r->t_admit);
+    if (r->admitted) res->queue_s = secs(r->t_arrive, r->t_admit);
     if (r->state == 2) {
       res->latency_s = secs(r->t_arrive, r->t_done);
       if (r->status == RBFFD_OK && !r->u.empty()) {

@@ -81,7 +81,8 @@ class Result(C.Structure):
     _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("queue_s", C.c_double),
                 ("latency_s", C.c_double), ("steps", C.c_int32), ("outer_iters", C.c_int64),
                 ("resid", C.c_double * 4), ("admit_attempts", C.c_int32),
-                ("arrive_s", C.c_double), ("admit_s", C.c_double), ("done_s", C.c_double)]
+                ("arrive_s", C.c_double), ("admit_s", C.c_double), ("done_s", C.c_double),
+                ("builds", C.c_int32)]
 
 
 STEP_CB = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int32, C.c_double)
@@ -556,7 +557,8 @@ class Server:
         out = {"state": r.state, "status": r.status, "queue_s": r.queue_s,
                "latency_s": r.latency_s, "steps": r.steps, "outer": r.outer_iters,
                "resid": list(r.resid), "admit_attempts": r.admit_attempts,
-               "arrive_s": r.arrive_s, "admit_s": r.admit_s, "done_s": r.done_s}
+               "arrive_s": r.arrive_s, "admit_s": r.admit_s, "done_s": r.done_s,
+               "builds": r.builds}
         if fields:
             out.update(u=u, v=v, p=p)
         return out

@@ -122,3 +122,43 @@ def test_server_admits_by_budget_and_reports_bad_requests():
     assert all(r["status"] == 0 for r in res), res
     assert max(r["queue_s"] for r in res) > 0.0
     S.close()
+
+
+def test_admission_retries_only_the_hierarchy_upload():
+    """A request whose problem fits the budget but whose multigrid hierarchy
+    does not (while another request runs) keeps its built problem: only the
+    upload is retried until the running request frees its memory, and the
+    clouds, weights and operators are built once."""
+    probe = rbffd.Context(0)
+    small = clouds.kovasznay(50, dt=0.4)
+    big = clouds.kovasznay(125, dt=0.4)  # 15 625 rows: the hierarchy is built on the host
+    A = rbffd.Problem(probe, small, precond=rbffd.PRECOND_AMG)
+    A.amg_info()  # uploads the hierarchy
+    full_a = A.nbytes
+    B = rbffd.Problem(probe, big, precond=rbffd.PRECOND_AMG)
+    base_b = B.nbytes  # before the upload
+    B.amg_info()
+    hier_b = B.nbytes - base_b
+    print("bytes: small", full_a, "big", base_b, "+ hierarchy", hier_b)
+    # the big request fits whole once the small one is gone, with half the
+    # small one's size to spare for the batch's tables; while the small one
+    # runs only the big problem fits, not its hierarchy as well
+    assert hier_b > full_a // 2 + (2 << 20), (hier_b, full_a)
+    A.close()
+    B.close()
+    probe.close()
+    ctx = rbffd.Context(0)
+    S = rbffd.Server(ctx, hbm_budget=base_b + hier_b + full_a // 2)
+    ta = S.submit(small, resid_tol=0.0, max_steps=300, criterion=2, precond=rbffd.PRECOND_AMG)
+    t0 = time.time()
+    while S.poll(ta)["state"] < 1 and time.time() - t0 < 60:
+        time.sleep(0.002)
+    tb = S.submit(big, resid_tol=0.0, max_steps=3, criterion=2, precond=rbffd.PRECOND_AMG)
+    S.drain()
+    ra, rb = S.poll(ta), S.poll(tb)
+    assert ra["status"] == 0 and rb["status"] == 0, (ra, rb)
+    assert ra["builds"] == 1 and rb["builds"] == 1, (ra, rb)
+    assert rb["admit_attempts"] >= 2, rb  # the upload waited for the small request
+    assert rb["admit_s"] >= ra["done_s"] - 1e-3, (ra, rb)
+    S.close()
+    ctx.close()
