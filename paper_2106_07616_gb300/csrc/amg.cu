@@ -1288,17 +1288,21 @@ int amg_build_begin(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
   J->dval = val;
   J->compose = ctx->amg_compose;
   J->ctx = ctx;
-  // level 0 on the device when it applies (amg_setup.cu); else, or when the
-  // device build gives up, the whole hierarchy on the host
+  // level 0 on the device when it applies (amg_setup.cu), on the caller's
+  // stream before it goes on (issued from the job's thread beside a running
+  // persistent solve, the setup's short kernels and readbacks took 16 ms
+  // instead of 3.6); else, or when the device build gives up, the whole
+  // hierarchy on the host
   if (ctx->amg_device_setup && n >= AMG_SETUP_MIN_ROWS) {
-    const int rc =
-        amg_level0_device<T>(ctx, n, q, ldn, col, val, sizeof(T) < sizeof(double), &J->L0);
+    const int rc = amg_level0_device<T>(ctx, ctx->stream, n, q, ldn, col, val,
+                                        sizeof(T) < sizeof(double), &J->L0);
     if (rc == RBFFD_OK) {
       J->l0dev = true;
     } else if (rc != RBFFD_ENOTIMPL) {
       drop(J);
       return rc;
     }
+    cudaGetLastError();
   }
   if (cudaEventCreateWithFlags(&J->ready, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventRecord(J->ready, ctx->stream) != cudaSuccess) {

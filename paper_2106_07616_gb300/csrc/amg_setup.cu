@@ -42,32 +42,29 @@ inline int nblk(long long n) { return (int)std::max<long long>(1, (n + SNT - 1) 
 // ---- stream-ordered scratch, counted against the context's budget
 struct Scratch {
   rbffd_ctx *ctx;
+  cudaStream_t st;
   std::vector<std::pair<void *, size_t>> held;
-  explicit Scratch(rbffd_ctx *c) : ctx(c) {}
+  Scratch(rbffd_ctx *c, cudaStream_t s) : ctx(c), st(s) {}
   template <typename T>
   int take(T **p, size_t n) {
     *p = nullptr;
     const size_t bytes = std::max<size_t>(1, n) * sizeof(T);
-    if (ctx->budget && ctx->used + bytes > ctx->budget) {
-      set_error("device budget exceeded in the multigrid setup: %zu + %zu > %zu bytes",
-                ctx->used, bytes, ctx->budget);
-      return RBFFD_ENOMEM;
-    }
+    if (!dev_reserve(ctx, bytes)) return RBFFD_ENOMEM;
     void *v = nullptr;
-    if (cudaMallocAsync(&v, bytes, ctx->stream) != cudaSuccess) {
+    if (cudaMallocAsync(&v, bytes, st) != cudaSuccess) {
       cudaGetLastError();
+      dev_release(ctx, bytes);
       set_error("multigrid setup: cudaMallocAsync(%zu) failed", bytes);
       return RBFFD_ENOMEM;
     }
-    ctx->used += bytes;
     held.emplace_back(v, bytes);
     *p = (T *)v;
     return RBFFD_OK;
   }
   ~Scratch() {
     for (auto &h : held) {
-      cudaFreeAsync(h.first, ctx->stream);
-      ctx->used -= h.second;
+      cudaFreeAsync(h.first, st);
+      dev_release(ctx, h.second);
     }
   }
 };
@@ -701,12 +698,11 @@ void keep_pool(int device) {
 }
 
 template <typename T>
-int amg_level0_device(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
-                      const double *val, bool low, AmgL0 *out) {
+int amg_level0_device(rbffd_ctx *ctx, cudaStream_t st, int n, int q, int ldn,
+                      const int32_t *col, const double *val, bool low, AmgL0 *out) {
   if (q > 64 || n < 1) return RBFFD_ENOTIMPL;
   keep_pool(ctx->device);
-  cudaStream_t st = ctx->stream;
-  Scratch S(ctx);
+  Scratch S(ctx, st);
   const long long nq = (long long)n * q;
   // ---- rows, strength, transposes
   double *dinv, *w, *x, *y, *part, *sc, *om;
@@ -977,9 +973,9 @@ int amg_level0_device(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col,
   return RBFFD_OK;
 }
 
-template int amg_level0_device<double>(rbffd_ctx *, int, int, int, const int32_t *,
-                                       const double *, bool, AmgL0 *);
-template int amg_level0_device<float>(rbffd_ctx *, int, int, int, const int32_t *,
-                                      const double *, bool, AmgL0 *);
+template int amg_level0_device<double>(rbffd_ctx *, cudaStream_t, int, int, int,
+                                       const int32_t *, const double *, bool, AmgL0 *);
+template int amg_level0_device<float>(rbffd_ctx *, cudaStream_t, int, int, int,
+                                      const int32_t *, const double *, bool, AmgL0 *);
 
 }  // namespace rbffd

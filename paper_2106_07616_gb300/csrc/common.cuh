@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 
@@ -18,7 +19,9 @@ struct rbffd_ctx {
   bool own_stream = false;
   int num_sms = 0;
   size_t budget = 0;  // 0 = no cap
-  size_t used = 0;
+  // device bytes held (dev_reserve / dev_release: the multigrid build's
+  // host thread allocates beside the caller)
+  std::atomic<size_t> used{0};
   int64_t launches = 0;
   // device-side waits of this context's launches: 2^wait_log2 cycles (0:
   // the default 2^31), rbffd_ctx_set_wait_limit
@@ -100,6 +103,10 @@ void ctx_unref(rbffd_ctx *ctx);
 // Device allocation charged to the context's budget.
 int dev_alloc(rbffd_ctx *ctx, void **p, size_t bytes);
 void dev_free(rbffd_ctx *ctx, void *p, size_t bytes);
+// count `bytes` against the context's budget (false: it would exceed it;
+// the error text is set) / give them back
+bool dev_reserve(rbffd_ctx *ctx, size_t bytes);
+void dev_release(rbffd_ctx *ctx, size_t bytes);
 // Small pinned host buffer of at least `bytes` (owned by the context).
 int pinned(rbffd_ctx *ctx, size_t bytes, void **out);
 

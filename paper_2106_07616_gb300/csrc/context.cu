@@ -17,28 +17,38 @@ void set_error(const char *fmt, ...) {
 
 void clear_error() { g_err[0] = 0; }
 
+bool dev_reserve(rbffd_ctx *ctx, size_t bytes) {
+  size_t cur = ctx->used.load();
+  do {
+    if (ctx->budget && cur + bytes > ctx->budget) {
+      set_error("device budget exceeded: %zu + %zu > %zu bytes", cur, bytes, ctx->budget);
+      return false;
+    }
+  } while (!ctx->used.compare_exchange_weak(cur, cur + bytes));
+  return true;
+}
+
+void dev_release(rbffd_ctx *ctx, size_t bytes) { ctx->used.fetch_sub(bytes); }
+
 int dev_alloc(rbffd_ctx *ctx, void **p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return RBFFD_OK;
-  if (ctx->budget && ctx->used + bytes > ctx->budget) {
-    set_error("device budget exceeded: %zu + %zu > %zu bytes", ctx->used, bytes, ctx->budget);
-    return RBFFD_ENOMEM;
-  }
+  if (!dev_reserve(ctx, bytes)) return RBFFD_ENOMEM;
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
+    dev_release(ctx, bytes);
     set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
     return RBFFD_ENOMEM;
   }
-  ctx->used += bytes;
   return RBFFD_OK;
 }
 
 void dev_free(rbffd_ctx *ctx, void *p, size_t bytes) {
   if (!p) return;
   cudaFree(p);
-  ctx->used -= bytes;
+  dev_release(ctx, bytes);
 }
 
 int pinned(rbffd_ctx *ctx, size_t bytes, void **out) {

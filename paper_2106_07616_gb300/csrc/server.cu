@@ -229,7 +229,7 @@ extern "C" int rbffd_server_create(rbffd_ctx *ctx, const rbffd_server_params *pr
     size_t budget = prm ? prm->hbm_budget_bytes : 0;
     if (budget == 0) {
       size_t fr = 0, tot = 0;
-      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = ctx->used + fr / 10 * 8;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = ctx->used.load() + fr / 10 * 8;
     }
     if (budget && (ctx->budget == 0 || budget < ctx->budget)) ctx->budget = budget;
     int cap = krylov_batch_max_ctas(ctx, 2);
