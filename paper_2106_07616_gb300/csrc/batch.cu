@@ -699,8 +699,12 @@ static int batch_compat(BatchScratch &S, rbffd_problem *const *P, int m) {
   RBFFD_CK(cudaStreamSynchronize(ctx->stream));
   for (size_t s = 0; s < sel.size(); ++s) {
     int rc = status_of(ko[s].status);
-    // the same acceptance as compat_ready (z carries the pin's response)
+    // the same acceptance and fallback as compat_ready (z carries the pin's
+    // response; a stalled multigrid solve is redone with FP64 Jacobi)
     if (rc == RBFFD_ENOCONV && ko[s].relres <= compat_accept()) rc = RBFFD_OK;
+    rbffd_problem *Q = P[sel[s]];
+    if ((rc == RBFFD_ENOCONV || rc == RBFFD_EDIVERGED) && (Q->amg || Q->amgf))
+      rc = compat_fallback(Q, &ko[s].relres);
     if (rc != RBFFD_OK) {
       set_error("batch member %d: compatible p': the solve of M z = e_I ended with status %d "
                 "(relres %.3e)", sel[s], rc, ko[s].relres);

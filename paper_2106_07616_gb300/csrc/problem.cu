@@ -273,10 +273,10 @@ namespace {
 // mixed-precision Jacobi BiCGSTAB, or FP64 BiCGSTAB with the FP64
 // hierarchy's V-cycle or Jacobi.  Its outcome goes to kout[2].
 int issue_pcorr(rbffd_problem *P, double tol, int maxit, double inner_tol, int inner_maxit,
-                const double *b, double *x, bool fp64_only = false) {
+                const double *b, double *x, bool fp64_only = false, bool jacobi = false) {
   rbffd_ctx *ctx = P->ctx;
   const bool mixed = P->precision != RBFFD_PREC_FP64 && !fp64_only;
-  if (P->amgf) {
+  if (P->amgf && !jacobi) {
     FgmresArgs f;
     memset(&f, 0, sizeof(f));
     f.n = P->n;
@@ -301,7 +301,7 @@ int issue_pcorr(rbffd_problem *P, double tol, int maxit, double inner_tol, int i
     f.amg = P->amgf;
     return fgmres_launch(ctx, P->fg_blocks, f);
   }
-  if (mixed && !P->amg) {
+  if (mixed && !P->amg && !jacobi) {
     MixedArgs m;
     memset(&m, 0, sizeof(m));
     m.inner = P->inner;
@@ -341,7 +341,7 @@ int issue_pcorr(rbffd_problem *P, double tol, int maxit, double inner_tol, int i
   a.maxit = maxit;
   a.val = P->Pp;
   a.dinv = P->p_dinv;
-  a.amg = P->amg;  // V-cycle preconditioner, or null (Jacobi)
+  a.amg = jacobi ? nullptr : P->amg;  // V-cycle preconditioner, or null (Jacobi)
   a.b[0] = b;
   a.x[0] = x;
   a.w[0] = P->kv[0];
@@ -536,6 +536,17 @@ int rbffd::compat_maxit(const rbffd_problem *P) {
 // where c is the incompatible fraction of the source (small after
 // k_center), so it moves p' by about 1e-9 of the pin's response to that
 // fraction.
+int rbffd::compat_fallback(rbffd_problem *P, double *relres) {
+  RBFFD_TRY(ops_interior_ones(P, P->pcs, P->zc));
+  RBFFD_TRY(issue_pcorr(P, compat_accept(), 50000, 0.0, 0, P->pcs, P->zc, true, true));
+  Readback r;
+  RBFFD_TRY(read_back(P, &r));
+  int rc = krylov_status_code(r.kout[2].status);
+  if (rc == RBFFD_ENOCONV && r.kout[2].relres <= compat_accept()) rc = RBFFD_OK;
+  if (relres) *relres = r.kout[2].relres;
+  return rc;
+}
+
 int rbffd::compat_ready(rbffd_problem *P) {
   if (!P->compat || P->z_ready) return RBFFD_OK;
   RBFFD_TRY(amg_ready(P));
@@ -547,6 +558,10 @@ int rbffd::compat_ready(rbffd_problem *P) {
   RBFFD_TRY(read_back(P, &r));
   int rc = krylov_status_code(r.kout[2].status);
   if (rc == RBFFD_ENOCONV && r.kout[2].relres <= compat_accept()) rc = RBFFD_OK;
+  // a multigrid solve that stalls (the FP32 Arnoldi process on some
+  // high-degree p' systems) is redone with FP64 Jacobi BiCGSTAB
+  if ((rc == RBFFD_ENOCONV || rc == RBFFD_EDIVERGED) && (P->amg || P->amgf))
+    rc = compat_fallback(P, &r.kout[2].relres);
   if (rc != RBFFD_OK) {
     set_error("compatible p': the solve of M z = e_I ended with status %d (relres %.3e)", rc,
               r.kout[2].relres);

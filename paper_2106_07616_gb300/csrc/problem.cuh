@@ -126,6 +126,10 @@ int compat_ready(rbffd_problem *P);
 double compat_tol(const rbffd_problem *P);
 constexpr double compat_accept() { return 1e-9; }
 int compat_maxit(const rbffd_problem *P);
+// z solved again, from zero, with FP64 Jacobi BiCGSTAB to compat_accept()
+// (up to 50 000 steps): for a multigrid solve of z that stalled.  Waits for
+// it; *relres (nullable) receives its relative residual.
+int compat_fallback(rbffd_problem *P, double *relres);
 // partial-sum slots of the steady residual reduction (ops.cu: k_resid)
 constexpr int RESID_SLOTS = 9;
 }  // namespace rbffd

@@ -319,3 +319,30 @@ def test_device_level0_matches_host_build(pc):
                 assert rel_l2(X.get(k), O.get(k)) <= 1e-8, (r, k)
     D.close()
     H.close()
+
+
+def test_stalled_z_solve_falls_back_to_fp64_jacobi():
+    """On the degree-5 (q = 42) Kovasznay cloud of 182^2 points the FP32
+    Arnoldi process stalls on z = M^-1 e_I of the compatible p' (4e-4 after
+    its 1000-step cap).  The solve is redone with FP64 Jacobi BiCGSTAB, and
+    the flexible GMRES path then gives the FP64 multigrid path's fields,
+    alone and in a batch."""
+    fp = clouds.kovasznay(182, seed=4112, degree=5, q=42, dt=20.0 / 181)
+    c = ctx()
+    F = rbffd.Problem(c, fp, precond=rbffd.PRECOND_AMG_FGMRES)
+    A = rbffd.Problem(c, fp, precond=rbffd.PRECOND_AMG)
+    for r in range(2):
+        F.simple_iterate(fp.dt, krylov_tol=1e-10)
+        A.simple_iterate(fp.dt, krylov_tol=1e-10)
+    for k in ("u", "v", "p"):
+        assert rel_l2(F.get(k), A.get(k)) <= 1e-8, k
+    G = rbffd.Problem(c, fp, precond=rbffd.PRECOND_AMG_FGMRES)
+    B = rbffd.Batch(c, [G])
+    for r in range(2):
+        d, its, status = B.iterate([fp.dt], krylov_tol=1e-10)
+        assert np.all(status == 0)
+    for k in ("u", "v", "p"):
+        assert rel_l2(G.get(k), A.get(k)) <= 1e-8, k
+    B.close()
+    for X in (F, A):
+        X.close()
