@@ -111,6 +111,28 @@ __device__ __forceinline__ void spmv_rows_gen(int n, int q, int ldn, int T,
   const int wpb = blockDim.x >> 5;
   int r0, r1, w;
   kdev::cta_rows(n, wglobal, nwarps, wpb, r0, r1, w);
+  // With dynamic shared memory (kdev::win_init ran), the operand is formed
+  // once per entry of this CTA's column window into shared memory (one
+  // coalesced pass over its source vectors) and gathered from there: one
+  // shared-memory read per stored entry instead of the source vectors'
+  // gathers from L2.  Columns outside the window form it directly.  Either
+  // way g computes the same value.
+  const kdev::RowWindow rw = kdev::row_window();
+  const int wlen = kdev::win_cap() > 0 ? rw.w1 - rw.w0 : 0;
+  S *wb[NR];
+  if (wlen > 0) {
+    __syncthreads();  // the buffers' previous use
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      wb[k] = reinterpret_cast<S *>(kdev::kdev_dyn + (size_t)k * kdev::win_cap() * 8);
+      for (int t = threadIdx.x; t < wlen; t += blockDim.x) wb[k][t] = g(k, rw.w0 + t);
+    }
+    __syncthreads();
+  }
+  auto gw = [&](int k, int c) -> S {
+    const unsigned int o = (unsigned int)(c - rw.w0);
+    return o < (unsigned int)wlen ? wb[k][o] : g(k, c);
+  };
   for (int base = r0 + w * gpw; base < r1; base += wpb * gpw) {
     const int i = base + gi;
     const bool valid = active && i < r1;
@@ -132,7 +154,7 @@ __device__ __forceinline__ void spmv_rows_gen(int n, int q, int ldn, int T,
         for (int u = 0; u < CH; ++u) {
           if (c[u] >= 0) {
 #pragma unroll
-            for (int k = 0; k < NR; ++k) IA::madd(s[k], a[u], g(k, c[u]));
+            for (int k = 0; k < NR; ++k) IA::madd(s[k], a[u], gw(k, c[u]));
           }
         }
       }
@@ -542,6 +564,13 @@ __device__ __forceinline__ void bicgstab_ir_body(const MixedArgs &A, const int l
 
 template <int NR, int NT, class IA>
 __global__ void __launch_bounds__(NT) k_bicgstab_ir(MixedArgs A) {
+  // this CTA's column window for the staged SpMV operands (kdev::win_init)
+  {
+    const int wpb = NT / 32;
+    int r0, r1, w;
+    kdev::cta_rows(A.n, blockIdx.x * wpb, gridDim.x * wpb, wpb, r0, r1, w);
+    kdev::win_init(A.n, A.q, A.ldn, A.col, r0, r1);
+  }
   bicgstab_ir_body<NR, NT, IA>(A, blockIdx.x, gridDim.x);
 }
 
@@ -568,15 +597,25 @@ __global__ void __launch_bounds__(NT) k_bicgstab_ir_batch(const MixedArgs *__res
 namespace {
 constexpr int MT1 = 1024;
 constexpr int MT2 = 512;
+// dynamic shared memory of the single-problem launch: the staged column
+// windows (kdev::win_cap: two 8-byte slots an entry, 4 096 entries)
+constexpr int IR_WIN_BYTES = 64 * 1024;
 
 template <class IA>
 int max_blocks_ia(rbffd_ctx *ctx, int nr) {
   int per_sm = 0;
   cudaError_t e;
-  if (nr == 1)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_ir<1, MT1, IA>, MT1, 0);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_ir<2, MT2, IA>, MT2, 0);
+  if (nr == 1) {
+    cudaFuncSetAttribute(k_bicgstab_ir<1, MT1, IA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         IR_WIN_BYTES);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_ir<1, MT1, IA>, MT1,
+                                                      IR_WIN_BYTES);
+  } else {
+    cudaFuncSetAttribute(k_bicgstab_ir<2, MT2, IA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         IR_WIN_BYTES);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab_ir<2, MT2, IA>, MT2,
+                                                      IR_WIN_BYTES);
+  }
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return 0;
@@ -605,7 +644,8 @@ int krylov_ir_launch(rbffd_ctx *ctx, int nr, int nblocks, const MixedArgs &args)
   else
     fn = nr == 1 ? (const void *)k_bicgstab_ir<1, MT1, ArithF32>
                  : (const void *)k_bicgstab_ir<2, MT2, ArithF32>;
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(nt), kargs, 0, ctx->stream);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(nt), kargs, IR_WIN_BYTES,
+                                              ctx->stream);
   ctx->launches++;
   if (e != cudaSuccess) {
     set_error("cooperative launch of k_bicgstab_ir failed: %s", cudaGetErrorString(e));
