@@ -167,6 +167,14 @@ extern "C" int rbffd_ctx_set_amg_compose(rbffd_ctx *ctx, int on) {
   });
 }
 
+extern "C" int rbffd_ctx_set_fgmres_reorth(rbffd_ctx *ctx, int on) {
+  return guarded([&]() -> int {
+    if (!ctx) return RBFFD_EINVAL;
+    ctx->fgmres_reorth = on != 0;
+    return RBFFD_OK;
+  });
+}
+
 extern "C" int rbffd_ctx_set_amg_device_setup(rbffd_ctx *ctx, int on) {
   return guarded([&]() -> int {
     if (!ctx) return RBFFD_EINVAL;

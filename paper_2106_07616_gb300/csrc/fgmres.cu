@@ -297,13 +297,16 @@ __device__ __forceinline__ void fgmres_body(const FgmresArgs &A, const int lb, c
       block_dots(r0, r1, n, w, V, j + 1, part0, lb);
       if (!reduce_all(c, part0, j + 2, tot, epoch)) { ok = false; break; }
       if ((int)threadIdx.x <= j) H[threadIdx.x + LDH * j] = tot[threadIdx.x];
-      // w' = w - sum h_i v_i; reorthogonalisation dots (w', v_i), (w', w')
-      block_combine<float>(r0, r1, n, V, j + 1, tot, w, w, -1.0f, 1.0f, fred, 0, NT, 0);
-      block_dots(r0, r1, n, w, V, j + 1, part1, lb);
-      if (!reduce_all(c, part1, j + 2, tot, epoch)) { ok = false; break; }
-      // column j += the reorthogonalisation coefficients c_i;
+      if (A.reorth) {
+        // w' = w - sum h_i v_i; reorthogonalisation dots (w', v_i), (w', w')
+        block_combine<float>(r0, r1, n, V, j + 1, tot, w, w, -1.0f, 1.0f, fred, 0, NT, 0);
+        block_dots(r0, r1, n, w, V, j + 1, part1, lb);
+        if (!reduce_all(c, part1, j + 2, tot, epoch)) { ok = false; break; }
+        // column j += the reorthogonalisation coefficients c_i
+        if ((int)threadIdx.x <= j) H[threadIdx.x + LDH * j] += tot[threadIdx.x];
+      }
       // h_{j+1,j} = sqrt((w', w') - sum c_i^2) by warp 0 in a fixed order
-      if ((int)threadIdx.x <= j) H[threadIdx.x + LDH * j] += tot[threadIdx.x];
+      // (one pass: sqrt((w, w) - sum h_i^2), and v_{j+1} below from w)
       if (threadIdx.x < 32) {
         float q2 = 0.0f;
         for (int i = threadIdx.x; i <= j; i += 32) q2 += tot[i] * tot[i];

@@ -28,6 +28,9 @@ struct FgmresArgs {
   double tol;           // relative residual to reach
   int maxit;            // cap on Arnoldi steps over all restarts
   const AmgDevF *amg;   // the FP32 hierarchy
+  int reorth;           // 1: classical Gram-Schmidt with one reorthogonalisation
+                        // (two reductions a step); 0: one pass, the norm by
+                        // Pythagoras (one reduction, one grid exchange fewer)
 };
 
 size_t fgmres_partials_bytes(int nblocks);

@@ -132,6 +132,7 @@ def load(path: str = LIB_PATH):
         "rbffd_problem_amg_cycle": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64),
                                               C.POINTER(i64), C.POINTER(i32)]),
         "rbffd_ctx_set_amg_device_setup": (C.c_int, [vp, C.c_int]),
+        "rbffd_ctx_set_fgmres_reorth": (C.c_int, [vp, C.c_int]),
         "rbffd_amg_cycle_host": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, C.POINTER(i32),
                                            C.POINTER(i32)]),
         "rbffd_get_field": (C.c_int, [vp, i32, vp]),
@@ -191,6 +192,12 @@ class Context:
         cycles, 0 for the default (rbffd_ctx_set_wait_limit)."""
         _check(load().rbffd_ctx_set_wait_limit(self.h, int(log2_cycles)),
                "rbffd_ctx_set_wait_limit")
+
+    def set_fgmres_reorth(self, on: bool):
+        """Flexible GMRES with one reorthogonalisation (True, the default) or
+        one Gram-Schmidt pass (rbffd_ctx_set_fgmres_reorth)."""
+        _check(load().rbffd_ctx_set_fgmres_reorth(self.h, 1 if on else 0),
+               "rbffd_ctx_set_fgmres_reorth")
 
     def set_amg_device_setup(self, on: bool):
         """Whether level 0 of multigrid hierarchies built from now on is built
