@@ -346,3 +346,23 @@ def test_stalled_z_solve_falls_back_to_fp64_jacobi():
     B.close()
     for X in (F, A):
         X.close()
+
+
+def test_one_pass_gram_schmidt_matches_oracle():
+    """Flexible GMRES with one Gram-Schmidt pass (the norm by Pythagoras,
+    one grid exchange fewer a step) still stops on the FP64 true residual
+    and gives the oracle's iterates."""
+    fp = clouds.cavity(60, dt=0.05)
+    c = rbffd.Context(0)
+    c.set_fgmres_reorth(False)
+    P = rbffd.Problem(c, fp, precond=rbffd.PRECOND_AMG_FGMRES)
+    O = oracle.Problem(fp, krylov_tol=1e-12)
+    for r in range(3):
+        dg, sg = P.simple_iterate(fp.dt, krylov_tol=1e-12)
+        do, _ = O.simple_iterate(fp.dt)
+        assert sg["relres"][2] <= 1e-12
+        assert abs(dg - do) <= 1e-8 * abs(do), (r, dg, do)
+        for k in ("u", "v", "p"):
+            assert rel_l2(P.get(k), O.get(k)) <= 1e-8, (r, k)
+    P.close()
+    c.close()
