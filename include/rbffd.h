@@ -335,6 +335,17 @@ int rbffd_ctx_set_fgmres_reorth(rbffd_ctx *ctx, int on);
 int rbffd_amg_cycle_host(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
                          const double *b, double *out_levels, double *out_composed,
                          int32_t *coarse_entries, int32_t *chunks);
+/* Level 0's aggregates of the hierarchy of a CSR matrix (host arrays as in
+ * rbffd_amg_analyze), on the host: agg[n] receives each row's aggregate,
+ * *naggs their number.  The aggregation: strength |a_ij| >= 0.08 max_k
+ * |a_ik| (k != i), symmetrised; a distance-2 maximal independent set of
+ * roots with fixed priorities key(i) = (h(i) 2^32 | i) + 1, h the 32-bit
+ * finaliser of MurmurHash3; points next to roots join the root of largest
+ * key, the rest the first-pass neighbour of largest key, isolated points
+ * become singletons after the roots (index order).  The device build gives
+ * the same aggregates.  No device work.  Errors: RBFFD_EINVAL. */
+int rbffd_amg_aggregates_host(int32_t n, const int32_t *rowptr, const int32_t *col,
+                              const double *val, int32_t *agg, int32_t *naggs);
 
 typedef struct {
   double dt;             /* time step */

@@ -994,6 +994,20 @@ int amg_analyze(int n, const int32_t *rowptr, const int32_t *col, const double *
   return RBFFD_OK;
 }
 
+int amg_aggregates_host(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                        int32_t *agg, int32_t *naggs) {
+  Csr A;
+  A.n = A.m = n;
+  A.ptr.assign(rowptr, rowptr + n + 1);
+  A.col.assign(col, col + rowptr[n]);
+  A.val.assign(val, val + rowptr[n]);
+  std::vector<int32_t> sp, sc, a;
+  strength(A, AMG_THETA, sp, sc);
+  *naggs = aggregate_mis2(n, sp, sc, a);
+  std::copy(a.begin(), a.end(), agg);
+  return RBFFD_OK;
+}
+
 int amg_cycle_host(int n, const int32_t *rowptr, const int32_t *col, const double *val,
                    const double *b, double *out_levels, double *out_composed, AmgInfo *info) {
   Csr A;

@@ -152,6 +152,11 @@ int amg_build(rbffd_ctx *ctx, int n, int q, int ldn, const int32_t *col, const d
 int amg_analyze(int n, const int32_t *rowptr, const int32_t *col, const double *val,
                 AmgInfo *info);
 
+// Level 0's aggregates of a CSR matrix on the host (aggregate_mis2 on its
+// strength graph): agg[n], *naggs.
+int amg_aggregates_host(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                        int32_t *agg, int32_t *naggs);
+
 // One cycle of the hierarchy of a CSR matrix applied to b on the host in
 // FP64, level by level (out_levels) and composed (out_composed; zeros when
 // the composed cycle is not built), n entries each.

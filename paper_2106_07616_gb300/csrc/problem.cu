@@ -804,6 +804,19 @@ extern "C" int rbffd_problem_amg_cycle(const rbffd_problem *P, int32_t *coarse_e
   });
 }
 
+extern "C" int rbffd_amg_aggregates_host(int32_t n, const int32_t *rowptr, const int32_t *col,
+                                         const double *val, int32_t *agg, int32_t *naggs) {
+  return guarded([&]() -> int {
+    if (n < 1 || !rowptr || !col || !val || !agg || !naggs || rowptr[0] != 0)
+      return RBFFD_EINVAL;
+    for (int i = 0; i < n; ++i)
+      if (rowptr[i + 1] < rowptr[i]) return RBFFD_EINVAL;
+    for (int k = 0; k < rowptr[n]; ++k)
+      if (col[k] < 0 || col[k] >= n) return RBFFD_EINVAL;
+    return amg_aggregates_host(n, rowptr, col, val, agg, naggs);
+  });
+}
+
 extern "C" int rbffd_amg_cycle_host(int32_t n, const int32_t *rowptr, const int32_t *col,
                                     const double *val, const double *b, double *out_levels,
                                     double *out_composed, int32_t *coarse_entries,

@@ -135,6 +135,7 @@ def load(path: str = LIB_PATH):
         "rbffd_ctx_set_fgmres_reorth": (C.c_int, [vp, C.c_int]),
         "rbffd_amg_cycle_host": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, C.POINTER(i32),
                                            C.POINTER(i32)]),
+        "rbffd_amg_aggregates_host": (C.c_int, [i32, vp, vp, vp, vp, C.POINTER(i32)]),
         "rbffd_get_field": (C.c_int, [vp, i32, vp]),
         "rbffd_set_field": (C.c_int, [vp, i32, vp]),
         "rbffd_get_operators": (C.c_int, [vp, vp, vp, vp, vp, vp]),
@@ -510,6 +511,20 @@ def amg_analyze(rowptr, col, val):
     _check(load().rbffd_amg_analyze(rowptr.size - 1, ptr(rowptr), ptr(col), ptr(val),
                                     C.byref(lv), rows, nnz, C.byref(ms)), "rbffd_amg_analyze")
     return [(int(rows[i]), int(nnz[i])) for i in range(lv.value)], ms.value
+
+
+def amg_aggregates_host(rowptr, col, val):
+    """Level 0's multigrid aggregates of a CSR matrix, on the host:
+    (agg per row, number of aggregates)."""
+    rowptr = np.ascontiguousarray(rowptr, np.int32)
+    col = np.ascontiguousarray(col, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    n = rowptr.size - 1
+    agg = np.zeros(n, np.int32)
+    na = C.c_int32(0)
+    _check(load().rbffd_amg_aggregates_host(n, ptr(rowptr), ptr(col), ptr(val), ptr(agg),
+                                            C.byref(na)), "rbffd_amg_aggregates_host")
+    return agg, na.value
 
 
 def amg_cycle_host(rowptr, col, val, b):

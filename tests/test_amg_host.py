@@ -140,3 +140,100 @@ def test_composed_cycle_not_built_for_two_levels_or_fewer():
     for i in range(64):
         M[i, col[rowptr[i]:rowptr[i + 1]]] += val[rowptr[i]:rowptr[i + 1]]
     assert np.allclose(yl, np.linalg.solve(M, b), rtol=1e-10, atol=1e-12)
+
+
+def _fmix32(h):
+    """MurmurHash3's 32-bit finaliser (Appleby), written out."""
+    h ^= h >> 16
+    h = (h * 0x85EBCA6B) & 0xFFFFFFFF
+    h ^= h >> 13
+    h = (h * 0xC2B2AE35) & 0xFFFFFFFF
+    h ^= h >> 16
+    return h
+
+
+def _mis2_aggregates(rowptr, col, val, theta=0.08):
+    """Level-0 aggregation from its definition, plain Python: the symmetric
+    strength graph; rounds in which every undecided point whose priority is
+    the largest among undecided points within distance 2 becomes a root and
+    the undecided points within distance 2 of a new root drop out; then
+    aggregates numbered by root index, points next to roots joining the root
+    of largest priority, the rest the first-pass neighbour of largest
+    priority, isolated points as singletons after the roots."""
+    n = len(rowptr) - 1
+    nb = [set() for _ in range(n)]
+    for i in range(n):
+        cs, vs = col[rowptr[i]:rowptr[i + 1]], val[rowptr[i]:rowptr[i + 1]]
+        off = [abs(v) for c, v in zip(cs, vs) if c != i]
+        mx = max(off) if off else 0.0
+        for c, v in zip(cs, vs):
+            if c != i and mx > 0.0 and abs(v) >= theta * mx:
+                nb[i].add(int(c))
+                nb[int(c)].add(i)
+    key = [((_fmix32(i) << 32) | i) + 1 for i in range(n)]
+    state = ["iso" if not nb[i] else "und" for i in range(n)]
+    while "und" in state:
+        m1 = [max([key[j] for j in nb[i] | {i} if state[j] == "und"], default=0) for i in range(n)]
+        m2 = [max(m1[j] for j in nb[i] | {i}) for i in range(n)]
+        new = {i for i in range(n) if state[i] == "und" and m2[i] == key[i]}
+        near = new | {i for i in range(n) if nb[i] & new}
+        near2 = near | {i for i in range(n) if nb[i] & near}
+        for i in range(n):
+            if i in new:
+                state[i] = "root"
+            elif state[i] == "und" and i in near2:
+                state[i] = "out"
+    roots = [i for i in range(n) if state[i] == "root"]
+    num = {r: k for k, r in enumerate(roots)}
+    first = [num.get(i, -1) for i in range(n)]
+    for i in range(n):
+        if state[i] == "out":
+            rs = [j for j in nb[i] if state[j] == "root"]
+            if rs:
+                first[i] = num[max(rs, key=lambda j: key[j])]
+    agg = list(first)
+    for i in range(n):
+        if first[i] < 0 and state[i] != "iso":
+            cand = [j for j in nb[i] if first[j] >= 0]
+            if cand:
+                agg[i] = first[max(cand, key=lambda j: key[j])]
+    na = len(roots)
+    for i in range(n):
+        if agg[i] < 0:
+            agg[i] = na
+            na += 1
+    return np.array(agg), na
+
+
+def test_level0_aggregation_follows_its_definition():
+    """The host's level-0 aggregation (the device build gives the same) is
+    the MIS(2) aggregation written out above, exactly, on a Laplacian grid
+    and on a p' matrix; the aggregates are connected in the strength graph,
+    and the priority hash is MurmurHash3's finaliser."""
+    assert _fmix32(0) == 0 and _fmix32(1) == 0x514E28B7
+    for A in (poisson5(24), p_prime_csr(30)):
+        agg, na = rbffd.amg_aggregates_host(*A)
+        ref, nr = _mis2_aggregates(*A)
+        assert na == nr and np.array_equal(agg, ref), (na, nr)
+        assert agg.min() == 0 and agg.max() == na - 1
+        # every aggregate is connected in the (symmetric) strength graph
+        rowptr, col, val = A
+        n = len(rowptr) - 1
+        nb = [set() for _ in range(n)]
+        for i in range(n):
+            cs, vs = col[rowptr[i]:rowptr[i + 1]], val[rowptr[i]:rowptr[i + 1]]
+            off = [abs(v) for c, v in zip(cs, vs) if c != i]
+            mx = max(off) if off else 0.0
+            for c, v in zip(cs, vs):
+                if c != i and mx > 0 and abs(v) >= 0.08 * mx:
+                    nb[i].add(int(c)); nb[int(c)].add(i)
+        for a in range(na):
+            mem = set(np.nonzero(agg == a)[0].tolist())
+            seen, stack = set(), [next(iter(mem))]
+            while stack:
+                i = stack.pop()
+                if i in seen:
+                    continue
+                seen.add(i)
+                stack.extend(j for j in nb[i] if j in mem)
+            assert seen == mem, a
