@@ -33,10 +33,10 @@ struct AmgL0 {
 // Level 0 of the packed p' matrix (ELL [q][ldn] on the device, n rows) on
 // stream st (the caller's); low: also A in FP32 (the flexible GMRES cycle).
 // Synchronises st a few times (the MIS(2) rounds, the sizes of the
-// products).  RBFFD_ENOTIMPL: the device build
-// does not apply (q > 64, a row wider than AMG_SETUP_DMAX, a pattern the
-// device's P~ or R~ does not cover, coarsening stalled); nothing is kept,
-// the caller builds on the host.  RBFFD_ENOMEM, RBFFD_ECUDA.
+// products).  RBFFD_ENOTIMPL: the device build does not apply (q > 64, a
+// row wider than AMG_SETUP_DMAX, a pattern the device's P~ or R~ does not
+// cover, coarsening stalled); nothing is kept, the caller builds on the
+// host.  RBFFD_ENOMEM, RBFFD_ECUDA.
 template <typename T>
 int amg_level0_device(rbffd_ctx *ctx, cudaStream_t st, int n, int q, int ldn,
                       const int32_t *col, const double *val, bool low, AmgL0 *out);
