@@ -319,13 +319,16 @@ int rbffd_problem_amg_cycle(const rbffd_problem *prob, int32_t *coarse_entries, 
  * RBFFD_EINVAL. */
 int rbffd_ctx_set_amg_device_setup(rbffd_ctx *ctx, int on);
 /* Orthogonalisation of the flexible GMRES Arnoldi process for solves issued
- * on this context from now on (the library's own choice): on != 0 (the
+ * on this context from now on (the library's own choice): mode 1 (the
  * default), classical Gram-Schmidt with one reorthogonalisation, two
  * reductions a step; 0, one classical pass with the new norm by Pythagoras
  * (h_{j+1,j}^2 = |w|^2 - sum h_{ij}^2), one reduction and one grid exchange
- * fewer a step.  Either way a solve stops on its FP64 true residual.
- * Errors: RBFFD_EINVAL. */
-int rbffd_ctx_set_fgmres_reorth(rbffd_ctx *ctx, int on);
+ * fewer a step; 2, two passes with the second delayed to the next step
+ * (DCGS2, Bielich et al. 2022): one reduction a step, every basis vector
+ * still orthogonalised twice, a restart's last column completed by one more
+ * reduction.  Either way a solve stops on its FP64 true residual.
+ * Errors: RBFFD_EINVAL (mode outside 0..2). */
+int rbffd_ctx_set_fgmres_reorth(rbffd_ctx *ctx, int mode);
 /* One cycle of the hierarchy of a CSR matrix (host arrays as in
  * rbffd_amg_analyze) applied to b[n] on the host in FP64, level by level
  * into out_levels[n] and composed into out_composed[n] (zeros when the

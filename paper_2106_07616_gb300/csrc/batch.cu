@@ -384,7 +384,7 @@ static int launch_pcorr(BatchScratch &S, rbffd_problem *const *P, const std::vec
       f.tol = tol[s];
       f.maxit = maxit[s];
       f.amg = Q->amgf;
-      f.reorth = Q->ctx->fgmres_reorth ? 1 : 0;
+      f.reorth = Q->ctx->fgmres_reorth;
       pf.push_back(f);
       rf.push_back(Q->n);
       wf.push_back(work_of(Q, 1));

@@ -31,9 +31,9 @@ struct rbffd_ctx {
   bool amg_compose = true;
   // level 0 of large hierarchies built on the device (rbffd_ctx_set_amg_device_setup)
   bool amg_device_setup = true;
-  // flexible GMRES: classical Gram-Schmidt with one reorthogonalisation
-  // (true) or one pass (rbffd_ctx_set_fgmres_reorth)
-  bool fgmres_reorth = true;
+  // flexible GMRES's Gram-Schmidt (rbffd_ctx_set_fgmres_reorth): 0 one
+  // pass, 1 two passes a step, 2 two passes with the second delayed
+  int fgmres_reorth = 1;
   // pinned host scratch for small read-backs
   void *pinned = nullptr;
   size_t pinned_bytes = 0;

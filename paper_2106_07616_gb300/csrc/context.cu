@@ -167,10 +167,13 @@ extern "C" int rbffd_ctx_set_amg_compose(rbffd_ctx *ctx, int on) {
   });
 }
 
-extern "C" int rbffd_ctx_set_fgmres_reorth(rbffd_ctx *ctx, int on) {
+extern "C" int rbffd_ctx_set_fgmres_reorth(rbffd_ctx *ctx, int mode) {
   return guarded([&]() -> int {
-    if (!ctx) return RBFFD_EINVAL;
-    ctx->fgmres_reorth = on != 0;
+    if (!ctx || mode < 0 || mode > 2) {
+      set_error("rbffd_ctx_set_fgmres_reorth: mode must be 0, 1 or 2");
+      return RBFFD_EINVAL;
+    }
+    ctx->fgmres_reorth = mode;
     return RBFFD_OK;
   });
 }

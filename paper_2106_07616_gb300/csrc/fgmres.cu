@@ -41,7 +41,7 @@ namespace rbffd {
 namespace {
 
 constexpr int FNT = 1024;
-constexpr int FG_D = FG_MAXM + 2;  // most dot products one exchange reduces
+constexpr int FG_D = FG_MAXM + 2;  // dot products one exchange reduces (2 FG_D delayed)
 constexpr int LDH = FG_MAXM + 1;   // leading dimension of the Hessenberg matrix
 constexpr int GB = 8;              // loads a lane keeps in flight in the loops below
 // dynamic shared memory of the single-problem launch: windows of up to
@@ -124,6 +124,35 @@ __device__ __forceinline__ void block_dots(int r0, int r1, int n, const float *w
   }
 }
 
+// The one reduction of a step with delayed reorthogonalisation: over rows
+// [r0, r1), the products (u, V_i) for i < j, (w, V_i) for i < j, (u, u) and
+// (u, w), 2 j + 2 in all, partial d of block lb to part[d * MAXB + lb]
+// (u: the step's once-orthogonalised basis vector, w = A z_j).
+__device__ __forceinline__ void block_dots2(int r0, int r1, int n, const float *u,
+                                            const float *w, const float *V, int j, float *part,
+                                            int lb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int d = warp; d < 2 * j + 2; d += nw) {
+    const float *x = d < j ? u : (d < 2 * j ? w : u);
+    const float *y = d < j ? V + (size_t)d * n
+                           : (d < 2 * j ? V + (size_t)(d - j) * n : (d == 2 * j ? u : w));
+    float t = 0.0f;
+    for (int r = r0 + lane; r < r1; r += 32 * GB) {
+      float a[GB], b[GB];
+#pragma unroll
+      for (int k = 0; k < GB; ++k) {
+        const int rr = r + 32 * k;
+        a[k] = rr < r1 ? __ldcg(x + rr) : 0.0f;
+        b[k] = rr < r1 ? __ldcg(y + rr) : 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < GB; ++k) t += a[k] * b[k];
+    }
+    t = kdev::wsum(t);
+    if (lane == 0) part[d * MAXB + lb] = t;
+  }
+}
+
 // After every block has published its partials: exchange, then the D totals
 // in a fixed order into tot[0..D).  False if a wait gave up.
 template <typename T>
@@ -194,7 +223,7 @@ __device__ __forceinline__ void block_combine(int r0, int r1, int n, const UT *U
 
 struct FgState {
   double bnorm, beta, scale, relres;
-  float hn, hinv;
+  float hn, hinv, hjj;
   int it, restarts, state, k, stop;
 };
 
@@ -206,7 +235,7 @@ template <int NT>
 __device__ __forceinline__ void fgmres_body(const FgmresArgs &A, const int lb, const int nb) {
   __shared__ float H[LDH * FG_MAXM];
   __shared__ float cs[FG_MAXM], sn[FG_MAXM], g[FG_MAXM + 1], y[FG_MAXM];
-  __shared__ float tot[FG_D];
+  __shared__ float tot[2 * FG_D];  // up to 2 m + 2 totals (delayed reorthogonalisation)
   __shared__ double tot64[2];
   __shared__ double stot[16];
   __shared__ double sred[2 * NT];
@@ -286,6 +315,122 @@ __device__ __forceinline__ void fgmres_body(const FgmresArgs &A, const int lb, c
       if (!amgdev::sync(c, epoch)) { ok = false; break; }
     }
     int j = 0;
+    // column jc of H rotated by the previous Givens rotations and a new one
+    // (hn: its subdiagonal entry), the residual estimate updated (thread 0)
+    auto rotate = [&](int jc, float hn) {
+      float hc = H[LDH * jc];
+      for (int i = 0; i < jc; ++i) {
+        const float b = H[i + 1 + LDH * jc];
+        H[i + LDH * jc] = cs[i] * hc + sn[i] * b;
+        hc = -sn[i] * hc + cs[i] * b;
+      }
+      const float a = hc, b = hn;
+      const float rr = sqrtf(a * a + b * b);
+      const float ri = rr > 0.0f ? 1.0f / rr : 0.0f;
+      cs[jc] = rr > 0.0f ? a * ri : 1.0f;
+      sn[jc] = rr > 0.0f ? b * ri : 0.0f;
+      H[jc + LDH * jc] = rr;
+      H[jc + 1 + LDH * jc] = 0.0f;
+      g[jc + 1] = -sn[jc] * g[jc];
+      g[jc] = cs[jc] * g[jc];
+      st.it++;
+      st.k = jc + 1;
+      const double est = fabs((double)g[jc + 1]) * st.beta / st.bnorm;
+      st.stop = !(est == est) ? 2 : (est <= A.tol || hn == 0.0f || st.it >= A.maxit) ? 1 : 0;
+    };
+    if (A.reorth == 2) {
+      // Delayed reorthogonalisation (DCGS2, Bielich et al. 2022), one
+      // reduction a step.  Slot j holds u_j, orthogonalised once and not
+      // normalised; z_j = M^-1 u_j (flexible GMRES takes any direction: only
+      // w = A z_j must be expanded in the orthonormal basis).  The step's
+      // reduction gives a = V^T u_j, b = V^T w, (u_j, u_j), (u_j, w); then
+      // v_j = (u_j - V a) / alpha completes column j - 1 (+ a, alpha below
+      // the diagonal), column j gets b and h_jj = ((u_j, w) - a.b) / alpha,
+      // and u_{j+1} = w - V b - h_jj v_j.  The last column of a restart is
+      // completed by one more reduction.
+      bool last = true;  // the loop ran to m: column m - 1 still to complete
+      for (; j < m; ++j) {
+        float *uj = V + (size_t)j * n, *w = V + (size_t)(j + 1) * n, *zj = Z + (size_t)j * n;
+        if (!amgdev::vcycle(A.amg, c, uj, zj, epoch)) { ok = false; break; }
+        block_spmv<float>(r0, r1, A.q, A.ldn, Tb, A.col, A.val32, zj,
+                          [&](int i, float az) { w[i] = az; });
+        __syncthreads();
+        block_dots2(r0, r1, n, uj, w, V, j, part0, lb);
+        if (!reduce_all(c, part0, 2 * j + 2, tot, epoch)) { ok = false; break; }
+        if (threadIdx.x < 32) {
+          float aa = 0.0f, ab = 0.0f;
+          for (int i = threadIdx.x; i < j; i += 32) {
+            aa += tot[i] * tot[i];
+            ab += tot[i] * tot[j + i];
+          }
+          aa = kdev::wsum(aa);
+          ab = kdev::wsum(ab);
+          if (leader) {
+            float al = 1.0f;  // v_0 = r / beta is normalised already
+            if (j > 0) {
+              const float al2 = tot[2 * j] - aa;
+              al = al2 > 0.0f ? sqrtf(al2) : 0.0f;
+            }
+            st.hn = al;
+            st.hinv = al > 0.0f ? 1.0f / al : 0.0f;
+            st.hjj = al > 0.0f ? (tot[2 * j + 1] - ab) / al : 0.0f;
+            st.stop = 0;
+            if (j > 0) {
+              for (int i = 0; i < j; ++i) H[i + LDH * (j - 1)] += tot[i];
+              rotate(j - 1, al);
+            }
+          }
+        }
+        __syncthreads();
+        if (st.stop == 2) {
+          if (leader) st.state = KRY_DIVERGED;
+          __syncthreads();
+          last = false;
+          break;
+        }
+        if (st.stop) {
+          last = false;
+          break;
+        }
+        // v_j = (u_j - sum a_i v_i) / alpha in place (v_0 as it is)
+        if (j > 0) block_combine<float>(r0, r1, n, V, j, tot, uj, uj, -1.0f, st.hinv, fred, 0, NT, 0);
+        // column j: b_i above, h_jj on the diagonal; coefficients of u_{j+1}
+        if ((int)threadIdx.x <= j) {
+          const float h = (int)threadIdx.x < j ? tot[j + threadIdx.x] : st.hjj;
+          H[threadIdx.x + LDH * j] = h;
+          y[threadIdx.x] = h;
+        }
+        __syncthreads();
+        // u_{j+1} = w - sum_{i <= j} h_ij v_i
+        block_combine<float>(r0, r1, n, V, j + 1, y, w, w, -1.0f, 1.0f, fred, 0, NT, 0);
+        if (j + 1 == m) break;
+        if (!amgdev::sync(c, epoch)) { ok = false; break; }
+      }
+      if (!ok || st.state != KRY_RUNNING) break;
+      if (last) {
+        // column m - 1: (u_m, v_i), i < m, and (u_m, u_m)
+        float *um = V + (size_t)m * n;
+        block_dots(r0, r1, n, um, V, m, part0, lb);
+        if (!reduce_all(c, part0, m + 1, tot, epoch)) { ok = false; break; }
+        if (threadIdx.x < 32) {
+          float aa = 0.0f;
+          for (int i = threadIdx.x; i < m; i += 32) aa += tot[i] * tot[i];
+          aa = kdev::wsum(aa);
+          if (leader) {
+            const float al2 = tot[m] - aa;
+            const float al = al2 > 0.0f ? sqrtf(al2) : 0.0f;
+            for (int i = 0; i < m; ++i) H[i + LDH * (m - 1)] += tot[i];
+            rotate(m - 1, al);
+          }
+        }
+        __syncthreads();
+        if (st.stop == 2) {
+          if (leader) st.state = KRY_DIVERGED;
+          __syncthreads();
+          break;
+        }
+      }
+    } else {
     for (; j < m; ++j) {
       float *vj = V + (size_t)j * n, *w = V + (size_t)(j + 1) * n, *zj = Z + (size_t)j * n;
       // z_j = M^-1 v_j (FP32 cycle), published by its last exchange
@@ -358,6 +503,7 @@ __device__ __forceinline__ void fgmres_body(const FgmresArgs &A, const int lb, c
       }
       if (st.stop || j + 1 == m) break;
       if (!amgdev::sync(c, epoch)) { ok = false; break; }
+    }
     }
     if (!ok || st.state != KRY_RUNNING) break;
     // ---- y = H^-1 g on the k columns (upper triangular), x += beta Z y in FP64

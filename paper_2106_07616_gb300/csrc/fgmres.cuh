@@ -30,7 +30,9 @@ struct FgmresArgs {
   const AmgDevF *amg;   // the FP32 hierarchy
   int reorth;           // 1: classical Gram-Schmidt with one reorthogonalisation
                         // (two reductions a step); 0: one pass, the norm by
-                        // Pythagoras (one reduction, one grid exchange fewer)
+                        // Pythagoras (one reduction, one grid exchange fewer);
+                        // 2: two passes, the second delayed to the next step's
+                        // reduction (one reduction a step)
 };
 
 size_t fgmres_partials_bytes(int nblocks);

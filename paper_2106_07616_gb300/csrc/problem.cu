@@ -299,7 +299,7 @@ int issue_pcorr(rbffd_problem *P, double tol, int maxit, double inner_tol, int i
     f.tol = tol;
     f.maxit = maxit;
     f.amg = P->amgf;
-    f.reorth = ctx->fgmres_reorth ? 1 : 0;
+    f.reorth = ctx->fgmres_reorth;
     return fgmres_launch(ctx, P->fg_blocks, f);
   }
   if (mixed && !P->amg && !jacobi) {

@@ -194,10 +194,11 @@ class Context:
         _check(load().rbffd_ctx_set_wait_limit(self.h, int(log2_cycles)),
                "rbffd_ctx_set_wait_limit")
 
-    def set_fgmres_reorth(self, on: bool):
-        """Flexible GMRES with one reorthogonalisation (True, the default) or
-        one Gram-Schmidt pass (rbffd_ctx_set_fgmres_reorth)."""
-        _check(load().rbffd_ctx_set_fgmres_reorth(self.h, 1 if on else 0),
+    def set_fgmres_reorth(self, mode):
+        """Flexible GMRES's Gram-Schmidt (rbffd_ctx_set_fgmres_reorth): 0 one
+        pass, 1 (True) two passes a step, 2 two passes with the second
+        delayed (one reduction a step)."""
+        _check(load().rbffd_ctx_set_fgmres_reorth(self.h, int(mode)),
                "rbffd_ctx_set_fgmres_reorth")
 
     def set_amg_device_setup(self, on: bool):

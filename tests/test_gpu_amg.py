@@ -348,13 +348,15 @@ def test_stalled_z_solve_falls_back_to_fp64_jacobi():
         X.close()
 
 
-def test_one_pass_gram_schmidt_matches_oracle():
-    """Flexible GMRES with one Gram-Schmidt pass (the norm by Pythagoras,
-    one grid exchange fewer a step) still stops on the FP64 true residual
-    and gives the oracle's iterates."""
+@pytest.mark.parametrize("mode", [0, 2])
+def test_other_gram_schmidt_modes_match_oracle(mode):
+    """Flexible GMRES with one Gram-Schmidt pass (mode 0: the norm by
+    Pythagoras) or with the second pass delayed to the next step's reduction
+    (mode 2) -- one grid exchange fewer a step either way -- still stops on
+    the FP64 true residual and gives the oracle's iterates."""
     fp = clouds.cavity(60, dt=0.05)
     c = rbffd.Context(0)
-    c.set_fgmres_reorth(False)
+    c.set_fgmres_reorth(mode)
     P = rbffd.Problem(c, fp, precond=rbffd.PRECOND_AMG_FGMRES)
     O = oracle.Problem(fp, krylov_tol=1e-12)
     for r in range(3):
