@@ -535,6 +535,20 @@ int rbffd_batch_tuning(const rbffd_batch *batch, int32_t *tuned, double *scales,
  * size, scale 1).  Either way the tuning state is cleared.  Results do not
  * depend on it beyond the order of partial sums.  Errors: RBFFD_EINVAL. */
 int rbffd_batch_set_autotune(rbffd_batch *batch, int on);
+/* The batched launches' work-list planner on its own (host only, no device
+ * work; the library's own scheduling).  m solves with work[i] (rows x
+ * iterations), cap[i] (most CTAs the solve's partial sums allow) and
+ * rows[i]; cmax co-resident CTAs; scale: the autotuner's team-size factor
+ * (1 = as planned).  The CTAs form *nteams teams of *team_size (the team
+ * gives the largest solve its share of the grid, at most every cap[i], at
+ * least enough CTAs for 8 threads a row of the smallest solve when the grid
+ * has room); the solves, largest work first, each go to the least-loaded
+ * team (LPT).  member_team[m] (host) receives each solve's team;
+ * *nctas = *nteams x *team_size (all three nullable).  Errors:
+ * RBFFD_EINVAL. */
+int rbffd_plan_work_lists(int32_t m, const double *work, const int32_t *cap, const int32_t *rows,
+                          int32_t cmax, double scale, int32_t *nctas, int32_t *team_size,
+                          int32_t *nteams, int32_t *member_team);
 
 /* -------------------------------------------------------------- serving */
 

@@ -189,6 +189,33 @@ static TeamPlan plan_teams(const std::vector<double> &work, const std::vector<in
   return T;
 }
 
+// The planner on its own, for the host tests (no device work): the team of
+// every member and the plan's sizes.
+extern "C" int rbffd_plan_work_lists(int32_t m, const double *work, const int32_t *cap,
+                                     const int32_t *rows, int32_t cmax, double scale,
+                                     int32_t *nctas, int32_t *team_size, int32_t *nteams,
+                                     int32_t *member_team) {
+  return guarded([&]() -> int {
+    if (m < 1 || cmax < 1 || !work || !cap || !rows || !member_team || !(scale > 0.0))
+      return RBFFD_EINVAL;
+    for (int i = 0; i < m; ++i)
+      if (!(work[i] >= 0.0) || cap[i] < 1 || rows[i] < 1) return RBFFD_EINVAL;
+    const TeamPlan T = plan_teams(std::vector<double>(work, work + m),
+                                  std::vector<int>(cap, cap + m), std::vector<int>(rows, rows + m),
+                                  cmax, scale);
+    // every team has the same size; nctas = teams x size
+    const int size = T.nb[0], teams = T.nctas / size;
+    for (int i = 0; i < m; ++i) member_team[i] = -1;
+    for (int t = 0; t < teams; ++t)
+      for (int k = T.info_and_list[4 * t + 2]; k < T.info_and_list[4 * t + 3]; ++k)
+        member_team[T.info_and_list[k]] = t;
+    if (nctas) *nctas = T.nctas;
+    if (team_size) *team_size = size;
+    if (nteams) *nteams = teams;
+    return RBFFD_OK;
+  });
+}
+
 // Autotuner events around the launch of one slot (only while tuning; such
 // iterations are never captured).
 static int tune_mark(BatchScratch &S, int slot, int end) {

@@ -146,6 +146,8 @@ def load(path: str = LIB_PATH):
         "rbffd_batch_graph_stats": (C.c_int, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
         "rbffd_batch_tuning": (C.c_int, [vp, C.POINTER(i32), C.POINTER(dbl), C.POINTER(dbl)]),
         "rbffd_batch_set_autotune": (C.c_int, [vp, C.c_int]),
+        "rbffd_plan_work_lists": (C.c_int, [i32, vp, vp, vp, i32, dbl, C.POINTER(i32),
+                                            C.POINTER(i32), C.POINTER(i32), vp]),
         "rbffd_server_create": (C.c_int, [vp, C.POINTER(ServerParams), C.POINTER(vp)]),
         "rbffd_server_submit": (C.c_int, [vp, C.POINTER(ProblemDesc), C.POINTER(SolveParams),
                                           C.POINTER(C.c_uint64)]),
@@ -512,6 +514,20 @@ def amg_analyze(rowptr, col, val):
     _check(load().rbffd_amg_analyze(rowptr.size - 1, ptr(rowptr), ptr(col), ptr(val),
                                     C.byref(lv), rows, nnz, C.byref(ms)), "rbffd_amg_analyze")
     return [(int(rows[i]), int(nnz[i])) for i in range(lv.value)], ms.value
+
+
+def plan_work_lists(work, cap, rows, cmax, scale=1.0):
+    """The batched launches' work-list plan (rbffd_plan_work_lists): (team of
+    each solve, CTAs, team size, teams)."""
+    work = np.ascontiguousarray(work, np.float64)
+    cap = np.ascontiguousarray(cap, np.int32)
+    rows = np.ascontiguousarray(rows, np.int32)
+    team = np.zeros(work.size, np.int32)
+    nc, ts, nt = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    _check(load().rbffd_plan_work_lists(work.size, ptr(work), ptr(cap), ptr(rows), int(cmax),
+                                        float(scale), C.byref(nc), C.byref(ts), C.byref(nt),
+                                        ptr(team)), "rbffd_plan_work_lists")
+    return team, nc.value, ts.value, nt.value
 
 
 def amg_aggregates_host(rowptr, col, val):
